@@ -1,0 +1,444 @@
+"""Ciphertext-level oracle: BGV operations (plain C) and the HEGMM executor.
+
+Test infrastructure (see ``oracle/__init__.py``).  The ring and scheme
+arithmetic lives in ``he_oracle.c``; this module loads it through ctypes,
+adds slot encoding (Python + the C NTT mod t), decryption with an exact
+big-integer CRT, and runs Algorithms 1 and 2 of the paper on ciphertexts,
+using the plans of ``oracle.slots``.
+
+Slot layout (BGV with t = 1 mod 2N): the slot vector is one row of S = N/2
+slots; slot j of row 0 is the evaluation of the plaintext at
+zeta^(5^j mod 2N), slot j of row 1 the evaluation at zeta^(-5^j), with
+zeta = 3^((t-1)/2N) mod t.  HE-Rot by z (Section 2.1) is the automorphism
+X -> X^g, g = 5^(z mod S) mod 2N: it rotates both rows left by z.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import slots as SL
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "he_oracle.c")
+_LIB = os.path.join(_HERE, "libhe_oracle.so")
+
+u64p = ctypes.POINTER(ctypes.c_uint64)
+i64p = ctypes.POINTER(ctypes.c_int64)
+intp = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile he_oracle.c into libhe_oracle.so with gcc (plain C, -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.or_new.restype = ctypes.c_void_p
+        L.or_new.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_free.argtypes = [ctypes.c_void_p]
+        L.or_get_primes.argtypes = [ctypes.c_void_p, u64p]
+        L.or_get_psi.restype = ctypes.c_uint64
+        L.or_get_psi.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_is_prime.restype = ctypes.c_int
+        L.or_is_prime.argtypes = [ctypes.c_uint64]
+        L.or_find_primes.restype = ctypes.c_int
+        L.or_find_primes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p]
+        for name in ("or_mix64",):
+            getattr(L, name).restype = ctypes.c_uint64
+            getattr(L, name).argtypes = [ctypes.c_uint64]
+        L.or_stream.restype = ctypes.c_uint64
+        L.or_stream.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        L.or_draw.restype = ctypes.c_uint64
+        L.or_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        L.or_ntt.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p]
+        L.or_intt.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p]
+        L.or_negacyclic_schoolbook.argtypes = [u64p, u64p, ctypes.c_int, ctypes.c_uint64, u64p]
+        L.or_polymul.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_sample_secret.argtypes = [ctypes.c_void_p, ctypes.c_uint64, i64p]
+        L.or_gen_evk.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, i64p, u64p, u64p]
+        L.or_encrypt.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, i64p, i64p, u64p]
+        L.or_decrypt_residues.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, u64p, u64p]
+        L.or_automorph.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p, ctypes.c_uint64, u64p]
+        L.or_automorph_int.argtypes = [ctypes.c_void_p, i64p, ctypes.c_uint64, i64p]
+        L.or_modup.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.or_ks_inner.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_moddown.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.or_keyswitch.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_rotate.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_uint64, u64p, u64p]
+        L.or_rotate_hoisted.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_uint64, u64p, u64p]
+        L.or_add.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, u64p, u64p, u64p]
+        L.or_cmult.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_tensor.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
+        L.or_mult_relin.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p, u64p]
+        L.or_modswitch.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.or_to_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p]
+        L.or_to_coeff.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p]
+        _lib = L
+    return _lib
+
+
+def P(a: np.ndarray):
+    """ctypes pointer to a contiguous uint64 array."""
+    assert a.dtype == np.uint64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(u64p)
+
+
+def PI(a: np.ndarray):
+    assert a.dtype == np.int64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(i64p)
+
+
+def PINT(idx: List[int]):
+    arr = (ctypes.c_int * len(idx))(*idx)
+    return arr
+
+
+def mix64(z: int) -> int:
+    return lib().or_mix64(z)
+
+
+def is_prime(n: int) -> bool:
+    return bool(lib().or_is_prime(n))
+
+
+class Oracle:
+    """BGV over R_Q, Q = q_0 ... q_{L-1}, with K special primes, for one preset."""
+
+    def __init__(self, preset):
+        self.pre = preset
+        self.N = preset.N
+        self.S = preset.N // 2
+        self.L = preset.L
+        self.K = preset.K
+        self.alpha = preset.alpha
+        self.t = preset.t
+        self.ctx = lib().or_new(preset.logN, preset.t, preset.L, preset.qbits, preset.K, preset.alpha, preset.eta)
+        if not self.ctx:
+            raise RuntimeError("oracle: parameter set not available")
+        pr = np.zeros(self.L + self.K, dtype=np.uint64)
+        lib().or_get_primes(self.ctx, P(pr))
+        self.primes = [int(x) for x in pr]
+        self.zeta = int(lib().or_get_psi(self.ctx, -1))
+        # slot j of row 0 <-> NTT index (5^j mod 2N - 1)/2 of the oracle's
+        # natural-order negacyclic NTT mod t; row 1 <-> (-5^j mod 2N - 1)/2.
+        two_n = 2 * self.N
+        self.slot_pos0 = np.array([((pow(5, j, two_n)) - 1) // 2 for j in range(self.S)], dtype=np.int64)
+        self.slot_pos1 = np.array([((-pow(5, j, two_n)) % two_n - 1) // 2 for j in range(self.S)], dtype=np.int64)
+        self.sk: Optional[np.ndarray] = None
+        self.keys: Dict[int, np.ndarray] = {}   # galois element (0 = relin) -> evk in NTT form
+        self.key_seed = None
+        self.counts = {}
+
+    def __del__(self):
+        try:
+            if self.ctx:
+                lib().or_free(self.ctx)
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- NTT
+    def ntt(self, a: np.ndarray, pi: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().or_ntt(self.ctx, pi, P(a))
+        return a
+
+    def intt(self, a: np.ndarray, pi: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().or_intt(self.ctx, pi, P(a))
+        return a
+
+    # ------------------------------------------------------------ encoding
+    def encode(self, row0, row1=None) -> np.ndarray:
+        """Slot vectors (values mod t) -> centred plaintext coefficients (int64)."""
+        ev = np.zeros(self.N, dtype=np.uint64)
+        r0 = np.zeros(self.S, dtype=np.int64)
+        r0[: len(row0)] = np.asarray(row0, dtype=np.int64) % self.t
+        ev[self.slot_pos0] = r0.astype(np.uint64)
+        if row1 is not None:
+            r1 = np.zeros(self.S, dtype=np.int64)
+            r1[: len(row1)] = np.asarray(row1, dtype=np.int64) % self.t
+            ev[self.slot_pos1] = r1.astype(np.uint64)
+        m = self.intt(ev, -1).astype(np.int64)
+        m[m > (self.t - 1) // 2] -= self.t
+        return m
+
+    def decode(self, coeffs) -> Tuple[np.ndarray, np.ndarray]:
+        """Plaintext coefficients (any integers) -> (row 0, row 1) slot values mod t."""
+        c = (np.asarray(coeffs, dtype=np.int64) % self.t).astype(np.uint64)
+        ev = self.ntt(c, -1).astype(np.int64)
+        return ev[self.slot_pos0], ev[self.slot_pos1]
+
+    def residues(self, m: np.ndarray, lv: int) -> np.ndarray:
+        """Signed coefficients -> residues over q_0..q_{lv-1}, [lv][N] uint64."""
+        out = np.empty((lv, self.N), dtype=np.uint64)
+        for i in range(lv):
+            out[i] = (np.asarray(m, dtype=object) % self.primes[i]).astype(np.uint64)
+        return out
+
+    def plaintext_eval(self, m: np.ndarray, lv: int) -> np.ndarray:
+        """Plaintext in the form or_cmult expects (NTT of residues)."""
+        r = self.residues(m, lv)
+        lib().or_to_eval(self.ctx, lv, PINT(list(range(lv))), P(r))
+        return r
+
+    # ------------------------------------------------------------- keys
+    def galois(self, z: int) -> int:
+        """Galois element of a left rotation by z (negative z: S + z)."""
+        return pow(5, z % self.S, 2 * self.N)
+
+    def secret(self, seed: int) -> np.ndarray:
+        s = np.zeros(self.N, dtype=np.int64)
+        lib().or_sample_secret(self.ctx, seed, PI(s))
+        return s
+
+    def _evk(self, seed: int, gtag: int, sprime_res: np.ndarray, eval_form: bool = True) -> np.ndarray:
+        nk = self.L + self.K
+        dnum = -(-self.L // self.alpha)
+        evk = np.zeros((dnum, 2, nk, self.N), dtype=np.uint64)
+        lib().or_gen_evk(self.ctx, seed, gtag, PI(self.sk), P(np.ascontiguousarray(sprime_res)), P(evk))
+        if eval_form:
+            flat = evk.reshape(-1, self.N)
+            lib().or_to_eval(self.ctx, flat.shape[0], PINT([r % nk for r in range(flat.shape[0])]), P(flat))
+        return evk
+
+    def sprime_galois(self, g: int) -> np.ndarray:
+        sg = np.zeros(self.N, dtype=np.int64)
+        lib().or_automorph_int(self.ctx, PI(self.sk), g, PI(sg))
+        nk = self.L + self.K
+        out = np.empty((nk, self.N), dtype=np.uint64)
+        for i in range(nk):
+            out[i] = (sg % self.primes[i]).astype(np.uint64)
+        return out
+
+    def sprime_square(self) -> np.ndarray:
+        nk = self.L + self.K
+        out = np.empty((nk, self.N), dtype=np.uint64)
+        for i in range(nk):
+            sr = (self.sk % self.primes[i]).astype(np.uint64)
+            o = np.zeros(self.N, dtype=np.uint64)
+            lib().or_polymul(self.ctx, i, P(sr), P(sr), P(o))
+            out[i] = o
+        return out
+
+    def keygen(self, seed: int, galois_elements=()):
+        """Secret key, relinearisation key and the listed Galois keys."""
+        self.key_seed = seed
+        self.sk = self.secret(seed)
+        self.keys = {0: self._evk(seed, 0, self.sprime_square())}
+        for g in galois_elements:
+            self.add_galois_key(g)
+
+    def add_galois_key(self, g: int):
+        if g not in self.keys:
+            self.keys[g] = self._evk(self.key_seed, g, self.sprime_galois(g))
+
+    def evk_coeff(self, g: int) -> np.ndarray:
+        """A key in coefficient form (for comparison with exported keys)."""
+        sp = self.sprime_square() if g == 0 else self.sprime_galois(g)
+        return self._evk(self.key_seed, g, sp, eval_form=False)
+
+    # ------------------------------------------------------- encryption
+    def encrypt(self, m: np.ndarray, seed: int, stream: int) -> np.ndarray:
+        ct = np.zeros((2, self.L, self.N), dtype=np.uint64)
+        mm = np.ascontiguousarray(m, dtype=np.int64)
+        lib().or_encrypt(self.ctx, seed, stream, PI(self.sk), PI(mm), P(ct))
+        return ct
+
+    def decrypt(self, ct: np.ndarray, lv: Optional[int] = None):
+        """Returns (plaintext coefficients mod t, noise bits, budget bits).
+
+        v = [c0 + c1 s]_Q with an exact CRT, centred; the plaintext is v mod t;
+        noise bits = log2 max |v|, budget = log2(Q/2).
+        """
+        lv = ct.shape[1] if lv is None else lv
+        v = np.zeros((lv, self.N), dtype=np.uint64)
+        lib().or_decrypt_residues(self.ctx, lv, PI(self.sk), P(np.ascontiguousarray(ct)), P(v))
+        Q = 1
+        for i in range(lv):
+            Q *= self.primes[i]
+        acc = np.zeros(self.N, dtype=object)
+        for i in range(lv):
+            qi = self.primes[i]
+            Qi = Q // qi
+            coef = Qi * pow(Qi % qi, -1, qi)
+            acc = acc + v[i].astype(object) * coef
+        acc = acc % Q
+        half = Q // 2
+        acc = np.where(acc > half, acc - Q, acc)
+        mx = max(abs(int(x)) for x in acc)
+        noise = math.log2(mx) if mx > 0 else 0.0
+        m = np.array([int(x) % self.t for x in acc], dtype=np.int64)
+        return m, noise, math.log2(Q / 2)
+
+    def decrypt_slots(self, ct: np.ndarray) -> np.ndarray:
+        m, _, _ = self.decrypt(ct)
+        return self.decode(m)[0]
+
+    # -------------------------------------------------------- operations
+    def rotate(self, ct: np.ndarray, z: int, hoisted: bool = False) -> np.ndarray:
+        lv = ct.shape[1]
+        if z % self.S == 0:
+            return ct.copy()
+        g = self.galois(z)
+        self.add_galois_key(g)
+        out = np.zeros_like(ct)
+        fn = lib().or_rotate_hoisted if hoisted else lib().or_rotate
+        fn(self.ctx, lv, P(np.ascontiguousarray(ct)), g, P(self.keys[g]), P(out))
+        self.counts["rot"] = self.counts.get("rot", 0) + 1
+        return out
+
+    def cmult(self, ct: np.ndarray, pt_eval: np.ndarray) -> np.ndarray:
+        lv = ct.shape[1]
+        out = np.zeros_like(ct)
+        lib().or_cmult(self.ctx, lv, P(np.ascontiguousarray(ct)), P(np.ascontiguousarray(pt_eval[:lv])), P(out))
+        self.counts["cmult"] = self.counts.get("cmult", 0) + 1
+        return out
+
+    def add(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        lv = a.shape[1]
+        out = np.zeros_like(a)
+        lib().or_add(self.ctx, lv, a.shape[0], P(np.ascontiguousarray(a)), P(np.ascontiguousarray(b)), P(out))
+        return out
+
+    def mult_relin(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        lv = a.shape[1]
+        out = np.zeros_like(a)
+        lib().or_mult_relin(self.ctx, lv, P(np.ascontiguousarray(a)), P(np.ascontiguousarray(b)), P(self.keys[0]), P(out))
+        self.counts["mult"] = self.counts.get("mult", 0) + 1
+        return out
+
+    def tensor(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        lv = a.shape[1]
+        d = np.zeros((3, lv, self.N), dtype=np.uint64)
+        lib().or_tensor(self.ctx, lv, P(np.ascontiguousarray(a)), P(np.ascontiguousarray(b)), P(d))
+        return d
+
+    def keyswitch(self, x: np.ndarray, g: int) -> np.ndarray:
+        lv = x.shape[0]
+        out = np.zeros((2, lv, self.N), dtype=np.uint64)
+        lib().or_keyswitch(self.ctx, lv, P(np.ascontiguousarray(x)), P(self.keys[g]), P(out))
+        return out
+
+    def modswitch(self, ct: np.ndarray) -> np.ndarray:
+        lv = ct.shape[1]
+        out = np.zeros((2, lv - 1, self.N), dtype=np.uint64)
+        lib().or_modswitch(self.ctx, lv, P(np.ascontiguousarray(ct)), P(out))
+        self.counts["modswitch"] = self.counts.get("modswitch", 0) + 1
+        return out
+
+    def modup(self, x: np.ndarray) -> np.ndarray:
+        lv = x.shape[0]
+        nd = -(-lv // self.alpha)
+        D = np.zeros((nd, lv + self.K, self.N), dtype=np.uint64)
+        lib().or_modup(self.ctx, lv, P(np.ascontiguousarray(x)), P(D))
+        return D
+
+    def moddown(self, u: np.ndarray, lv: int) -> np.ndarray:
+        out = np.zeros((lv, self.N), dtype=np.uint64)
+        lib().or_moddown(self.ctx, lv, P(np.ascontiguousarray(u)), P(out))
+        return out
+
+    def automorph(self, a: np.ndarray, g: int, prime_idx: List[int]) -> np.ndarray:
+        out = np.zeros_like(a)
+        lib().or_automorph(self.ctx, len(prime_idx), PINT(prime_idx), P(np.ascontiguousarray(a)), g, P(out))
+        return out
+
+
+# --------------------------------------------------------------------------
+# HEGMM on ciphertexts (Algorithms 1 and 2)
+# --------------------------------------------------------------------------
+
+
+def mask_scale(o: Oracle) -> int:
+    """Mask entry value: 1, or [q_drop]_t when the product level drops primes.
+
+    A modulus switch multiplies the message by q_drop^-1 mod t; encoding the
+    eps/omega masks with q_drop cancels that factor on both operands.
+    """
+    s = 1
+    for i in range(o.pre.ms_drop):
+        s = s * o.primes[o.L - 1 - i] % o.t
+    return s
+
+
+class HEGMM:
+    """Runs a plan of ``oracle.slots`` on ciphertexts, op by op."""
+
+    def __init__(self, o: Oracle):
+        self.o = o
+        self._mask_cache: Dict[Tuple, np.ndarray] = {}
+
+    def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
+        key = (tuple(dsts), scale, lv)
+        if key not in self._mask_cache:
+            v = np.zeros(self.o.S, dtype=np.int64)
+            v[dsts] = scale
+            self._mask_cache[key] = self.o.plaintext_eval(self.o.encode(v), lv)
+        return self._mask_cache[key]
+
+    def galois_needed(self, plan: SL.Plan) -> List[int]:
+        zs = set()
+        for e, om in plan.iters:
+            zs.update(d for d in e if d % self.o.S)
+            zs.update(d for d in om if d % self.o.S)
+        zs.update(z for z in plan.extract if z % self.o.S)
+        return sorted({self.o.galois(z) for z in zs})
+
+    def encrypt_inputs(self, plan: SL.Plan, A, B, seed: int = 1, streams=(0, 1)):
+        o = self.o
+        ctA = o.encrypt(o.encode(plan.a_layout(A) % o.t), seed, streams[0])
+        ctB = o.encrypt(o.encode(plan.b_layout(B) % o.t), seed, streams[1])
+        return ctA, ctB
+
+    def lt(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
+        """sum_d u_d (.) Rot(ct, d), diagonals in ascending d (Eq. lintrans)."""
+        lv = ct.shape[1]
+        acc = None
+        for d in sorted(diags):
+            r = self.o.rotate(ct, d)
+            term = self.o.cmult(r, self.mask_eval(diags[d], scale, lv))
+            acc = term if acc is None else self.o.add(acc, term)
+        return acc
+
+    def run(self, plan: SL.Plan, ctA: np.ndarray, ctB: np.ndarray) -> np.ndarray:
+        o = self.o
+        for g in self.galois_needed(plan):
+            o.add_galois_key(g)
+        scale = mask_scale(o)
+        C = None
+        for e, om in plan.iters:
+            a = self.lt(ctA, e, scale)
+            b = self.lt(ctB, om, scale)
+            for _ in range(o.pre.ms_drop):
+                a = o.modswitch(a)
+                b = o.modswitch(b)
+            prod = o.mult_relin(a, b)
+            C = prod if C is None else o.add(C, prod)
+        out = C
+        for z in plan.extract:
+            out = o.add(out, o.rotate(C, z))
+        return out
+
+    def result(self, plan: SL.Plan, ct: np.ndarray) -> np.ndarray:
+        slots = self.o.decrypt_slots(ct)
+        Cm = np.zeros((plan.m, plan.n), dtype=np.int64)
+        for i in range(plan.m):
+            for j in range(plan.n):
+                Cm[i, j] = slots[plan.result_slot(i, j)]
+        return Cm
