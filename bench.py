@@ -1,0 +1,371 @@
+"""Benchmark: encrypted HEGMM products per second on one GB300 (or N replicas).
+
+Workload (the medium configuration): ring N=8192, t=65537, five chain primes
+below 2^40 plus one special prime (dnum=5); products A 16x32 . B 32x24 and
+A 32x8 . B 8x48, each with Algorithm 1 (HEGMM) and Algorithm 2
+(HEGMM-Enhanced), entries uniform in [-8, 7] mod t, seed 0.  One step = these
+four encrypted products.  Operands are encrypted before the timed region and
+stay resident in HBM; the per-step working set (Galois keys of all four
+plans, about 2.4 GB) is far larger than L2, and L2 is also flushed between
+timed steps (outside the per-step CUDA events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the plain CPU oracle
+(oracle/) on this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload as W  # noqa: E402
+
+PRESET = W.MEDIUM
+SHAPES = W.MEDIUM_SHAPES
+ALGS = (1, 2)
+METRIC = "HEGMM encrypted matmuls/s (N=8192 ring, 16x32x24 + 32x8x48, Alg 1 + Alg 2)"
+UNIT = "matmul/s"
+KEY_SEED = 7
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK = 6800.0
+
+
+def workload_config(extra=None):
+    cfg = {
+        "workload": "medium: N=8192, t=65537, 5x40-bit + 1 special prime, dnum=5; "
+                    "A16x32.B32x24 and A32x8.B8x48, Algorithm 1 and Algorithm 2 each; entries U[-8,7] seed 0",
+        "products_per_step": len(SHAPES) * len(ALGS),
+        "l2": "flushed between timed steps (256 MiB write) and per-step key working set > L2",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+
+
+_oracle_cache = {}
+
+
+def oracle_sample(nrot=6, ncm=6, nmul=2):
+    """Times the oracle on a bounded sample of the workload.
+
+    The oracle executes a product as a fixed sequence of HE-Rot, HE-CMult,
+    HE-Add and HE-Mult calls (no reuse between iterations), so its time per
+    step is the op counts of the four plans times the measured time of each
+    op.  The sample runs ``nrot`` rotations (distinct offsets), ``ncm``
+    mask products and additions and ``nmul`` relinearised products at the
+    workload's parameters; key generation is excluded.
+    Returns (estimated seconds per step, description).
+    """
+    from oracle import he as OH
+    from oracle import slots as SL
+
+    if "o" not in _oracle_cache:
+        o = OH.Oracle(PRESET)
+        o.keygen(KEY_SEED)
+        for z in range(1, nrot + 1):
+            o.add_galois_key(o.galois(z))
+        _oracle_cache["o"] = o
+    o = _oracle_cache["o"]
+    x = np.arange(o.S) % o.t
+    ct = o.encrypt(o.encode(x), 1, 0)
+    pt = o.plaintext_eval(o.encode((x * 3) % o.t), o.L)
+    t0 = time.perf_counter()
+    for z in range(1, nrot + 1):
+        o.rotate(ct, z)
+    t_rot = (time.perf_counter() - t0) / nrot
+    t0 = time.perf_counter()
+    for _ in range(ncm):
+        r = o.cmult(ct, pt)
+    t_cm = (time.perf_counter() - t0) / ncm
+    t0 = time.perf_counter()
+    for _ in range(ncm):
+        o.add(ct, r)
+    t_add = (time.perf_counter() - t0) / ncm
+    t0 = time.perf_counter()
+    for _ in range(nmul):
+        o.mult_relin(ct, r)
+    t_mul = (time.perf_counter() - t0) / nmul
+    total = 0.0
+    for (m, l, n) in SHAPES:
+        for alg in ALGS:
+            c = SL.make_plan(m, l, n, alg).counts()
+            total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
+    desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=8192/L=5; "
+            "per-step time = op counts of the 4 plans x measured op times (%.1f/%.1f/%.1f/%.1f ms "
+            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, t_rot * 1e3, t_cm * 1e3, t_add * 1e3,
+                                                       t_mul * 1e3))
+    return total, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample()
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        t, desc = oracle_sample()
+        times.append(t)
+    sec = statistics.mean(times)
+    value = len(SHAPES) * len(ALGS) / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm as H
+
+    stream = torch.cuda.Stream(device=dev)
+    ctx = H.Context.from_preset(PRESET, stream=stream.cuda_stream)
+    prods = []
+    for (m, l, n) in SHAPES:
+        A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
+        for alg in ALGS:
+            prods.append((m, l, n, alg, A, Bm))
+    ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_1)
+    ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_2)
+    ops = []
+    for i, (m, l, n, alg, A, Bm) in enumerate(prods):
+        ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 1 + rank, 2 * i)
+        cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, alg), 1 + rank, 2 * i + 1)
+        ops.append((ca, cb))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        outs = []
+        cnts = []
+        for (m, l, n, alg, _, _), (ca, cb) in zip(prods, ops):
+            c, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, alg)
+            outs.append(c)
+            cnts.append(cnt)
+        return outs, cnts
+
+    # warm-up (builds plans, masks) and a correctness check of every product
+    for w in range(max(args.warmup, 1)):
+        outs, cnts = step()
+    for (m, l, n, alg, A, Bm), c in zip(prods, outs):
+        got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
+        assert (got == (A @ Bm) % PRESET.t).all(), "wrong product %dx%dx%d alg %d" % (m, l, n, alg)
+    ksw_per_step = sum(c["ksw"] for c in cnts)
+    paper_rot_per_step = sum(c["rot"] for c in cnts)
+    del outs
+
+    clk = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    time.sleep(0.3)
+    ctx.hegmm_kernel_reset()
+    ctx.hegmm_set_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        outs, _ = step()
+        ev[k][1].record(stream)
+        del outs
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    ctx.hegmm_set_timing(False)
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    per_step = len(prods)
+    value = per_step * world / (ms / 1e3)
+    stats = ctx.hegmm_kernel_stats()
+
+    # e2e: host ciphertexts (coefficient domain, pinned) -> import -> product -> export
+    host_in = []
+    for (m, l, n, alg, _, _), (ca, cb) in zip(prods, ops):
+        ha = torch.from_numpy(ctx.hegmm_ct_export(ca)).pin_memory()
+        hb = torch.from_numpy(ctx.hegmm_ct_export(cb)).pin_memory()
+        host_in.append((ha, hb))
+    lv1 = ctx.level_after_product
+    host_out = [torch.empty((2, lv1, ctx.N), dtype=torch.uint64).pin_memory() for _ in prods]
+    h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in)
+    d2h = sum(o.numel() * 8 for o in host_out)
+
+    def e2e_step():
+        for (m, l, n, alg, _, _), (ha, hb), ho in zip(prods, host_in, host_out):
+            ia = ctx.hegmm_ct_import(ha.numpy())
+            ib = ctx.hegmm_ct_import(hb.numpy())
+            c, _ = ctx.hegmm_matmul(ia, ib, m, l, n, alg)
+            ctx.hegmm_ct_export(c, ho.numpy())
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) * 1e3 / args.steps
+
+    # roofline of the dominant kernel
+    dom = max(stats.items(), key=lambda kv: kv[1][0])
+    name, (kms, kn, kbytes) = dom
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    hbm_peak = peaks.get("hbm_gbs")
+    roof = {"kernel": name, "launches": kn, "avg_launch_us": kms * 1e3 / max(kn, 1),
+            "share_of_kernel_time": kms / max(sum(v[0] for v in stats.values()), 1e-9)}
+    if name.startswith("ntt"):
+        roof.update({"bound": "alu", "unit": "Gbutterfly/s"})
+        logN = PRESET.logN
+        bfly = kbytes / (2 * 8 * (1 << logN)) * (1 << (logN - 1)) * logN
+        roof["achieved"] = bfly / (kms / 1e3) / 1e9
+        roof["peak"] = None
+        roof["frac"] = None
+    else:
+        peak = hbm_peak or HBM_FALLBACK
+        roof.update({"bound": "hbm", "unit": "GB/s", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": peak,
+                     "peak_source": "measured" if hbm_peak else "fallback"})
+        roof["frac"] = roof["achieved"] / peak
+    roof["traffic"] = None
+    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_02238_gb300", "csrc", "kernels.cu"), "rb").read()).hexdigest()[:12]
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            if tj.get("kernels_sha") == src_sha and name in tj.get("per_unit_bytes", {}):
+                units = kbytes / tj["algorithmic_bytes_per_unit"][name]
+                roof["traffic"] = tj["per_unit_bytes"][name] * units / max(kn, 1)
+        except Exception:
+            pass
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": workload_config({"parallelism": "replicas" if world > 1 else "single-gpu"}),
+        "keyswitches_per_s": ksw_per_step * world / (ms / 1e3),
+        "paper_rotations_per_step": paper_rot_per_step,
+        "keyswitches_per_step": ksw_per_step,
+        "wall_s_timed": wall,
+        "e2e": {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": int(sum(v[1] for v in stats.values()) / max(args.steps, 1)) * args.steps,
+        "roofline": roof,
+        "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in stats.items() if v[1]},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        sec, desc = oracle_sample()
+        line["cpu_baseline"] = {"value": len(prods) / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

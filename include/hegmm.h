@@ -1,0 +1,217 @@
+/*
+ * hegmm.h -- C ABI of the GB300 (sm_103a) HEGMM library.
+ *
+ * HEGMM (arXiv 2405.02238) multiplies an encrypted m x l matrix A by an
+ * encrypted l x n matrix B.  Each matrix is packed into the slots of one
+ * ciphertext; the cloud computes
+ *     A.B = sum_k eps^k(sigma(A)) (.) omega^k(tau(B))        (Eq. elementwise)
+ * where each transform is a linear transformation evaluated by rotations and
+ * plaintext-mask products, sum_z u_z (.) Rot(x; z)            (Eq. lintrans),
+ * sequenced as Algorithm 1 (HEGMM, l iterations) or Algorithm 2
+ * (HEGMM-Enhanced, min(m,l,n) iterations plus t-1 extraction rotations).
+ * The HE operations of Section 2.1 (HE-Add, HE-Mult, HE-CMult, HE-Rot) are
+ * realised as RNS-BGV over Z_Q[X]/(X^N+1): negacyclic NTTs, Galois
+ * automorphisms with hybrid key switching (ModUp, key inner product,
+ * ModDown), mask products and tensoring with relinearisation.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: 0 (HEGMM_OK) or a negative HEGMM_E* code; after an error
+ *    hegmm_last_error(ctx) returns a message.  No entry point aborts the
+ *    process; a CUDA error is reported as HEGMM_ECUDA.
+ *  - Every call is ordered on the context's CUDA stream (the stream handle
+ *    given to hegmm_ctx_create, e.g. a PyTorch stream).  Calls that return
+ *    host data (decrypt, export) synchronise that stream.
+ *  - Handles (hegmm_ctx, hegmm_pt, hegmm_ct) and their device memory are
+ *    owned by the library and released by the matching *_destroy call.
+ *    Host arrays passed in are owned by the caller and only read during the
+ *    call; host output arrays are owned by the caller and must be large
+ *    enough for the sizes stated at each function.
+ *  - Slots: a ciphertext holds two rows of S = N/2 slots; rotations are
+ *    cyclic within a row.  Matrices use row 0.  Plaintext values are
+ *    integers mod t (the plaintext modulus, a prime with t = 1 mod 2N).
+ *  - Ciphertexts on the device are [2][level][N] uint64 residues in the
+ *    NTT domain.  Exported / imported host ciphertexts are [2][level][N]
+ *    uint64 in the coefficient domain, component 0 then 1, chain prime i
+ *    at index i, residues in [0, q_i).
+ */
+#ifndef HEGMM_H
+#define HEGMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HEGMM_OK 0
+#define HEGMM_EINVAL (-1)   /* bad argument or parameter set */
+#define HEGMM_ENOMEM (-2)   /* device or host allocation failed */
+#define HEGMM_ESHAPE (-3)   /* the product does not fit one slot row */
+#define HEGMM_ENOKEY (-4)   /* a rotation has no Galois key */
+#define HEGMM_ECUDA (-5)    /* a CUDA call failed */
+#define HEGMM_ETIMEOUT (-6) /* a bounded device wait ran out */
+
+#define HEGMM_ALG_AUTO 0 /* Algorithm 2 if it fits S slots, else Algorithm 1 */
+#define HEGMM_ALG_1 1    /* Algorithm 1 (HEGMM) */
+#define HEGMM_ALG_2 2    /* Algorithm 2 (HEGMM-Enhanced) */
+
+#define HEGMM_ROLE_A 0
+#define HEGMM_ROLE_B 1
+
+typedef struct hegmm_ctx hegmm_ctx; /* parameters, tables, keys, plans, stream */
+typedef struct hegmm_pt hegmm_pt;   /* device plaintext, NTT domain */
+typedef struct hegmm_ct hegmm_ct;   /* device ciphertext [2][level][N], NTT domain */
+
+/* Ring and modulus-chain parameters.  Chain primes q_0 > ... > q_{L-1} are
+ * the L largest primes below 2^qbits with q = 1 mod 2N; the K special
+ * primes are the next K such primes.  A key-switching digit is alpha
+ * consecutive chain primes (dnum = L / alpha digits).  Errors are centred
+ * binomial with parameter eta; the secret is ternary.  ms_drop chain primes
+ * are removed by a modulus switch before every ciphertext product (0 or 1).
+ * Limits: 10 <= logN <= 14, 2 <= L, 1 <= K, L + K <= 24, qbits <= 60,
+ * alpha divides L, K >= alpha (so P >= every digit modulus up to a bit). */
+typedef struct {
+    int logN;
+    uint64_t t;
+    int L;
+    int qbits;
+    int K;
+    int alpha;
+    int eta;
+    int ms_drop;
+} hegmm_params;
+
+/* Operation counts of one product.  rot/cmult/mult follow the paper's
+ * counting (one HE-Rot per non-zero diagonal of every transform, one
+ * HE-CMult per diagonal, one HE-Mult per iteration); ksw is the number of
+ * key switches actually executed (rotations shared between iterations of
+ * the same source ciphertext are computed once), modup the number of hoisted
+ * ModUps. */
+typedef struct {
+    long long rot, cmult, add, mult, relin, extract, ksw, modup, modswitch;
+} hegmm_opcount;
+
+/* Creates a context: finds the primes, builds NTT and base-conversion
+ * tables on the device.  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream) on which every later call is ordered; the caller keeps it
+ * alive until hegmm_ctx_destroy.  Errors: HEGMM_EINVAL for parameters
+ * outside the limits, HEGMM_ENOMEM, HEGMM_ECUDA. */
+int hegmm_ctx_create(const hegmm_params *params, void *cuda_stream, hegmm_ctx **out);
+void hegmm_ctx_destroy(hegmm_ctx *ctx);
+const char *hegmm_last_error(const hegmm_ctx *ctx);
+
+/* Copies the L + K primes (chain then special) into out[L + K]. */
+int hegmm_get_primes(const hegmm_ctx *ctx, uint64_t *out);
+
+/* Key generation from one seed: ternary secret s, the relinearisation key
+ * (s^2 -> s) and the Galois keys of every rotation that the plans of the
+ * listed products need.  shapes_mln holds n_shapes triples (m, l, n); alg is
+ * HEGMM_ALG_* and is resolved per shape.  A later call with the same seed
+ * adds keys; a different seed replaces all keys.  Keys stay resident in
+ * device memory.  Errors: HEGMM_ESHAPE if a shape fits no algorithm. */
+int hegmm_keygen(hegmm_ctx *ctx, uint64_t seed, const int *shapes_mln, int n_shapes, int alg);
+
+/* Adds Galois keys for left rotations by z[0..count) (negative z rotates
+ * right); requires a previous hegmm_keygen. */
+int hegmm_keygen_rotations(hegmm_ctx *ctx, const int *z, int count);
+
+/* Copies a key to the host in the coefficient domain, layout
+ * [dnum][2][L+K][N] (component 0 = b_j, 1 = a_j).  which = 0 selects the
+ * relinearisation key, otherwise which is a Galois element g (odd, < 2N).
+ * Errors: HEGMM_ENOKEY. */
+int hegmm_key_export(hegmm_ctx *ctx, uint64_t which, uint64_t *host);
+
+/* Client-side preprocessing of a plaintext matrix (Algorithm 1 step 1,
+ * Algorithm 2 lines 1-18): sigma (role A) or tau (role B), the duplication
+ * and eps^0 / omega^0 of Algorithm 2, flattening in the plan's order, and
+ * slot encoding.  mat is row-major (m x l for role A, l x n for role B),
+ * entries taken mod t (negative values wrap).  *out is a new plaintext.
+ * Errors: HEGMM_ESHAPE. */
+int hegmm_encode(hegmm_ctx *ctx, int role, const int64_t *mat, int m, int l, int n, int alg, hegmm_pt **out);
+
+/* Encodes count <= S slot values (row 0; the rest zero) into a plaintext. */
+int hegmm_encode_slots(hegmm_ctx *ctx, const uint64_t *slots, int count, hegmm_pt **out);
+
+/* Secret-key encryption: c1 = a, c0 = -a s + t e + m, with a and e drawn
+ * from the counter-mode SplitMix64 streams of (seed, stream_id). */
+int hegmm_encrypt(hegmm_ctx *ctx, const hegmm_pt *pt, uint64_t seed, uint64_t stream_id, hegmm_ct **out);
+
+/* The encrypted product C = A.B of an m x l and an l x n matrix (Algorithm 1
+ * or 2 of the paper), on ciphertexts made by hegmm_encode + hegmm_encrypt
+ * (or imported) for the same (m, l, n, alg).  *C is a new ciphertext; cnt
+ * (may be NULL) receives the operation counts.  Errors: HEGMM_ESHAPE,
+ * HEGMM_ENOKEY (keygen did not cover this shape), HEGMM_EINVAL (operand
+ * level does not match). */
+int hegmm_matmul(hegmm_ctx *ctx, const hegmm_ct *A, const hegmm_ct *B, int m, int l, int n, int alg,
+                 hegmm_ct **C, hegmm_opcount *cnt);
+
+/* count independent products in one call; mln holds count triples, A[i],
+ * B[i] the operands, C[i] receives new ciphertexts.  Products are batched
+ * into shared kernel launches.  On error no C[i] is returned. */
+int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
+                       const int *mln, int alg, hegmm_ct **C);
+
+/* Decrypts a product of hegmm_matmul and reads C (m x n, row-major, values
+ * in [0, t)) from the plan's result slots.  Synchronises the stream. */
+int hegmm_decrypt(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int alg, uint64_t *out);
+
+/* Decrypts all S row-0 slots into out[S].  Synchronises the stream. */
+int hegmm_decrypt_slots(hegmm_ctx *ctx, const hegmm_ct *ct, uint64_t *out);
+
+/* Single HE operations (Section 2.1), each returning a new ciphertext. */
+int hegmm_rotate(hegmm_ctx *ctx, const hegmm_ct *ct, int z, hegmm_ct **out);
+/* Hoisted rotations: one ModUp of ct shared by count rotations. */
+int hegmm_rotate_many(hegmm_ctx *ctx, const hegmm_ct *ct, const int *z, int count, hegmm_ct **outs);
+int hegmm_cmult(hegmm_ctx *ctx, const hegmm_ct *ct, const hegmm_pt *pt, hegmm_ct **out);
+int hegmm_add(hegmm_ctx *ctx, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out);
+int hegmm_mult(hegmm_ctx *ctx, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out); /* tensor + relin */
+int hegmm_modswitch(hegmm_ctx *ctx, const hegmm_ct *ct, hegmm_ct **out);          /* drop last prime */
+
+/* Level (number of chain primes) of a ciphertext. */
+int hegmm_ct_level(const hegmm_ct *ct);
+
+/* Host <-> device ciphertext transfer in the coefficient domain,
+ * host layout [2][level][N].  Export synchronises the stream. */
+int hegmm_ct_export(hegmm_ctx *ctx, const hegmm_ct *ct, uint64_t *host);
+int hegmm_ct_import(hegmm_ctx *ctx, const uint64_t *host, int level, hegmm_ct **out);
+
+/* Waits for all work queued on the context's stream. */
+int hegmm_sync(hegmm_ctx *ctx);
+
+void hegmm_pt_destroy(hegmm_pt *pt);
+void hegmm_ct_destroy(hegmm_ct *ct);
+
+/* Host-only planner queries (no context, no GPU).  slots = S = N/2.
+ * hegmm_plan_counts fills the operation counts of hegmm_matmul for the
+ * shape (ksw counts each distinct rotation offset of an operand once, plus
+ * one key switch per HE-Mult and per extraction rotation).
+ * hegmm_plan_describe writes the plan as ints into buf[cap] and returns the
+ * number of ints it needs (call with cap = 0 to size the buffer), or a
+ * negative HEGMM_E* code:
+ *   alg, case ('1','A','B','L'), column_major, iterations, extractions,
+ *   then per iteration, for eps then omega: number of diagonals, and per
+ *   diagonal its offset d, its slot count c and the c destination slots;
+ *   then the extraction offsets; then the m*n result slots (row-major).
+ * hegmm_plan_layout writes the client-side slot vector of role A or B for
+ * the plan (values mod t) into out[cap] and returns its length. */
+int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *out);
+int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int cap);
+int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t,
+                      uint64_t *out, int cap);
+
+/* Per-kernel device timing: while enabled, every launch of the library's
+ * kernels is bracketed by CUDA events on the context stream and its
+ * duration added to the kernel's bucket.  kind indexes the table named by
+ * hegmm_kernel_name (0 .. hegmm_kernel_kinds()-1).  Reading the stats
+ * synchronises the stream; hegmm_kernel_reset zeroes them. */
+int hegmm_set_timing(hegmm_ctx *ctx, int enable);
+int hegmm_kernel_kinds(void);
+const char *hegmm_kernel_name(int kind);
+int hegmm_kernel_stats(hegmm_ctx *ctx, int kind, double *total_ms, long long *launches, double *bytes);
+int hegmm_kernel_reset(hegmm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEGMM_H */

@@ -1,0 +1,181 @@
+// device.cuh -- per-thread building blocks of the HEGMM kernels.
+//
+// Functions are __host__ __device__ so the index arithmetic can be checked on
+// the CPU; 128-bit products use __umul64hi on the device and unsigned
+// __int128 on the host.
+#pragma once
+#include <stdint.h>
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+#ifdef __CUDACC__
+#define HDI __host__ __device__ __forceinline__
+#else
+#define HDI inline
+#endif
+
+namespace hg {
+
+HDI u64 mulhi(u64 a, u64 b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (u64)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+HDI u64 addm(u64 a, u64 b, u64 q) {
+    u64 r = a + b;
+    return r >= q ? r - q : r;
+}
+
+HDI u64 subm(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// a w mod q for a < 2^64, w < q < 2^63, wp = floor(w 2^64 / q)  (Shoup).
+HDI u64 mulsh(u64 a, u64 w, u64 wp, u64 q) {
+    u64 h = mulhi(a, wp);
+    u64 r = a * w - h * q;
+    return r >= q ? r - q : r;
+}
+
+// a b 2^-64 mod q for a < 2^64, b < q, qinv = q^-1 mod 2^64 (Montgomery).
+HDI u64 montmul(u64 a, u64 b, u64 q, u64 qinv) {
+    u64 lo = a * b, hi = mulhi(a, b);
+    u64 mh = mulhi(lo * qinv, q);
+    return hi >= mh ? hi - mh : hi - mh + q;
+}
+
+struct Acc {
+    u64 lo, hi;
+};
+
+HDI void mac(Acc &a, u64 x, u64 y) {
+    u64 lo = x * y, hi = mulhi(x, y);
+    u64 n = a.lo + lo;
+    a.hi += hi + (n < lo ? 1 : 0);
+    a.lo = n;
+}
+
+// (hi 2^64 + lo) 2^-64 mod q for a value below q 2^64.
+HDI u64 montred(Acc a, u64 q, u64 qinv) {
+    u64 mh = mulhi(a.lo * qinv, q);
+    return a.hi >= mh ? a.hi - mh : a.hi - mh + q;
+}
+
+// v mod r for any v < 2^64; br = floor(2^64 / r).
+HDI u64 redc64(u64 v, u64 r, u64 br) { return mulsh(v, 1, br, r); }
+
+// Centred value of v in [0, p) reduced into [0, r); pr = p mod r.
+HDI u64 centred(u64 v, u64 p, u64 pr, u64 r, u64 br) {
+    u64 vr = redc64(v, r, br);
+    return v <= (p - 1) / 2 ? vr : subm(vr, pr, r);
+}
+
+HDI u32 brev_bits(u32 x, int bits) {
+#ifdef __CUDA_ARCH__
+    return __brev(x) >> (32 - bits);
+#else
+    u32 r = 0;
+    for (int i = 0; i < bits; i++) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+#endif
+}
+
+// NTT-domain automorphism X -> X^g: position c holds the evaluation at
+// psi^(2 brev(c) + 1); the output at c reads the input at the position of
+// exponent (2 brev(c) + 1) g mod 2N.
+HDI u32 auto_src(u32 c, u32 g, int logN) {
+    u32 e = 2u * brev_bits(c, logN) + 1u;
+    u32 eg = (u32)(((u64)e * g) & ((2ull << logN) - 1));
+    return brev_bits((eg - 1u) >> 1, logN);
+}
+
+// Padded shared-memory index: one spare word every 16 keeps the strided
+// butterfly accesses of every pass at two wavefronts per warp.
+HDI int pad16(int i) { return i + (i >> 4); }
+
+// Forward negacyclic NTT (Cooley-Tukey, bit-reversed psi powers): one group
+// of 2^R elements through stages s0 .. s0+R-1.  Group g covers elements
+// base + k tl, k < 2^R.  psi[k] = psi^brev(k), psis its Shoup companion.
+template <int R>
+HDI void ntt_fwd_group(u64 *sm, int g, int s0, int logN, const u64 *psi, const u64 *psis, u64 q) {
+    const int ltl = logN - s0 - R;
+    const int tl = 1 << ltl;
+    const int B = g >> ltl, o = g & (tl - 1);
+    const int base = (B << (ltl + R)) + o;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int half = 1 << (R - 1 - r);
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) {
+            if (k & half) continue;
+            const int idx = ((1 << s0) << r) + (B << r) + (k >> (R - r));
+            const u64 w = psi[idx], wp = psis[idx];
+            const u64 U = x[k];
+            const u64 V = mulsh(x[k + half], w, wp, q);
+            x[k] = addm(U, V, q);
+            x[k + half] = subm(U, V, q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
+}
+
+// Inverse negacyclic NTT (Gentleman-Sande, bit-reversed psi^-1 powers): one
+// group through the stages of butterfly distance 2^u0 .. 2^(u0+R-1).
+template <int R>
+HDI void ntt_inv_group(u64 *sm, int g, int u0, int logN, const u64 *ipsi, const u64 *ipsis, u64 q) {
+    const int tl = 1 << u0;
+    const int B = g >> u0, o = g & (tl - 1);
+    const int base = (B << (u0 + R)) + o;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int dist = 1 << r;
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) {
+            if (k & dist) continue;
+            const int idx = (1 << (logN - u0 - r - 1)) + (B << (R - 1 - r)) + (k >> (r + 1));
+            const u64 w = ipsi[idx], wp = ipsis[idx];
+            const u64 U = x[k], V = x[k + dist];
+            x[k] = addm(U, V, q);
+            x[k + dist] = mulsh(subm(U, V, q), w, wp, q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) in counter mode.
+constexpr u64 SM_GAMMA = 0x9E3779B97F4A7C15ull;
+
+HDI u64 mix64(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+HDI u64 rng_stream(u64 seed, u64 domain, u64 obj) { return mix64(seed ^ mix64((domain << 48) | obj)); }
+HDI u64 rng_draw(u64 stream, u64 idx) { return mix64(stream + (idx + 1) * SM_GAMMA); }
+
+// Centred binomial sample: popcount(low eta bits) - popcount(next eta bits).
+HDI long long cbd_sample(u64 r, int eta) {
+    const u64 m = (1ull << eta) - 1;
+#ifdef __CUDA_ARCH__
+    return (long long)__popcll(r & m) - (long long)__popcll((r >> eta) & m);
+#else
+    return (long long)__builtin_popcountll(r & m) - (long long)__builtin_popcountll((r >> eta) & m);
+#endif
+}
+
+// Random-stream domains (shared definition with every other implementation
+// of the same scheme conventions).
+enum { DOM_SK = 1, DOM_KEY_A = 2, DOM_KEY_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5 };
+
+}  // namespace hg

@@ -1,0 +1,235 @@
+// internal.h -- host-side structures and kernel launchers of the HEGMM library.
+// Not part of the ABI (include/hegmm.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hegmm.h"
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+namespace hg {
+
+constexpr int MAXM = 25;      // L + K primes plus t
+constexpr int PAT_MAX = 64;   // inner entries of a limb pattern
+
+// Per-modulus constants in device memory.
+struct ModDev {
+    u64 q;
+    u64 qinv;   // q^-1 mod 2^64
+    u64 r2;     // 2^128 mod q
+    u64 barr;   // floor(2^64 / q)
+    u64 ninv;   // N^-1 mod q
+    u64 ninv_sh;
+    u64 tq;     // t mod q
+    u64 tq_sh;
+};
+
+// A batch of limbs: limb b = outer * inner + i lives at
+//   (outer_ptrs ? outer_ptrs[outer] : base + outer * outer_stride) + off[i] * N
+// in modulus mod[i].
+struct LimbPat {
+    u64 *base;
+    u64 *const *outer_ptrs;
+    long long outer_stride;
+    int inner;
+    int count;
+    unsigned short off[PAT_MAX];
+    unsigned char mod[PAT_MAX];
+};
+
+// One key-switching inner product: u[c][e] = sum_j D[j][e][perm_g] * key[j][c][gp(e)].
+struct RotDesc {
+    const u64 *D;   // [nd][ne][N] hoisted ModUp digits (NTT domain)
+    const u64 *key; // [dnum][2][L+K][N] Montgomery NTT
+    u64 *u;         // [2][ne][N]
+    u32 g;          // Galois element (1 = none)
+    u32 pad;
+};
+
+// One polynomial of an exact division with t-corrected rounding (ModDown /
+// modulus switch): out = (u_keep - t y~) D^-1 (+ add, optionally permuted by g).
+struct DivDesc {
+    const u64 *u;   // keep limbs [nkeep][N]; drop limbs follow at u + nkeep * N
+    u64 *tmp;       // [nkeep][N] scratch
+    u64 *out;       // [nkeep][N]
+    const u64 *add; // [nkeep][N] or null
+    u32 g;          // automorphism applied to add (1 = none)
+    u32 pad;
+};
+
+// A product output of the linear-transformation accumulation:
+// out[c][i] (+)= sum over terms src[c][i] * mask[i].
+struct LtTerm {
+    const u64 *src;  // ciphertext [2][lv][N]
+    const u64 *mask; // [lv][N] Montgomery NTT
+};
+
+struct Tensor3 {
+    const u64 *a, *b;  // [2][lv][N]
+    u64 *d;            // [3][lv][N]
+};
+
+enum KernelKind {
+    K_NTT_FWD = 0,
+    K_NTT_INV,
+    K_MODUP,
+    K_KSW_IP,
+    K_DIV_CONV,
+    K_DIV_COMBINE,
+    K_LT_ACC,
+    K_TENSOR,
+    K_SUM,
+    K_POINTWISE,
+    K_SAMPLE,
+    K_CODEC,
+    K_NUM
+};
+
+struct ModUpTab {
+    int lv = 0, ne = 0, nd = 0;
+    u64 *d = nullptr;  // see build_modup_tab
+};
+
+struct DivTab {
+    int nkeep = 0, ndrop = 0;
+    std::vector<int> keep, drop;  // global modulus indices
+    u64 *d = nullptr;             // see build_div_tab
+};
+
+struct ExecPlan;
+
+struct Ctx {
+    hegmm_params prm{};
+    int logN = 0, N = 0, S = 0, L = 0, K = 0, alpha = 0, dnum = 0, np = 0, tmod = 0, nmod = 0;
+    u64 t = 0;
+    u64 q[MAXM]{};
+    u64 psi[MAXM]{};
+    ModDev hmod[MAXM]{};
+    ModDev *d_mods = nullptr;
+    u64 *d_tw = nullptr;  // [nmod][4][N]: psi_rev, shoup, psi_inv_rev, shoup
+    cudaStream_t st = nullptr;
+    std::string err;
+    int nsm = 148;
+
+    bool have_sk = false;
+    u64 key_seed = 0;
+    u64 *d_s = nullptr;   // [np][N] NTT, normal form
+    u64 *d_sR = nullptr;  // [np][N] NTT, Montgomery form
+    std::map<u64, u64 *> keys;  // Galois element -> key; 0 = relinearisation
+
+    std::map<int, ModUpTab> modup;
+    std::map<std::pair<int, int>, DivTab> divs;  // (level, 0 = ModDown / 1 = modswitch)
+    std::vector<int> slot_pos0, slot_pos1;       // slot -> NTT position mod t
+    std::map<std::tuple<int, int, int, int>, ExecPlan *> plans;
+    u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
+    std::map<int, u64 *> crt;        // level -> CRT-to-t table
+
+    bool timing = false;
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> evpool;
+    double stat_ms[K_NUM]{};
+    long long stat_n[K_NUM]{};
+    double stat_bytes[K_NUM]{};
+
+    // ext index e of the key-switching basis at level lv -> global modulus
+    int gidx(int lv, int e) const { return e < lv ? e : L + (e - lv); }
+    int digits(int lv) const { return (lv + alpha - 1) / alpha; }
+    size_t limb_bytes() const { return (size_t)N * 8; }
+    size_t key_words() const { return (size_t)dnum * 2 * np * N; }
+};
+
+// Times one launch when timing is enabled.
+struct Launch {
+    Ctx *c;
+    int kind;
+    double bytes;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Launch(Ctx *c_, int kind_, double bytes_);
+    ~Launch();
+};
+
+// ---------------------------------------------------------------- kernels.cu
+int init_kernels(Ctx *c);
+int ntt_fwd(Ctx *c, const LimbPat &p);
+int ntt_inv(Ctx *c, const LimbPat &p);
+// ModUp base conversion of n inputs: xc (coeff, lv limbs) and xn (NTT, lv
+// limbs) -> D [nd][ne][N] (own limbs copied from xn in NTT form, others in
+// coefficient form, to be forward transformed).
+int modup_conv(Ctx *c, int lv, int n, const u64 *xc, long long xc_stride, const u64 *xn, long long xn_stride,
+               u64 *D, long long D_stride);
+int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot);
+int div_conv(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
+int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
+int lt_accumulate(Ctx *c, int lv, const LtTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout,
+                  int accumulate);
+int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
+// out[poly] = sum_k in[k][poly] over nk inputs with stride in_stride words; npolylimbs = 2*lv
+int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate);
+// pointwise helpers over [npoly][lv][N]
+int pw_add(Ctx *c, int lv, int npoly, const u64 *a, const u64 *b, u64 *out);
+int pw_mont(Ctx *c, int lv, int npoly, const u64 *a, const u64 *bR, int b_per_limb, u64 *out);
+int pw_to_mont(Ctx *c, const LimbPat &p);                  // x -> x R
+int pw_from_mont(Ctx *c, const LimbPat &p);                // x R -> x
+int sample_uniform(Ctx *c, const LimbPat &p, u64 stream, const int *gprime_of_inner);
+int sample_cbd_t(Ctx *c, const LimbPat &p, u64 stream, int eta);   // t * e mod q
+int sample_ternary(Ctx *c, const LimbPat &p, u64 stream);
+int key_digit_combine(Ctx *c, u64 *kb, u64 *ka, const u64 *sprime, const u64 *d_Pmod, int lo, int hi);
+int encrypt_combine(Ctx *c, int lv, u64 *ct, const u64 *pt);
+int decrypt_dot(Ctx *c, int lv, const u64 *ct, u64 *v);
+int crt_to_t(Ctx *c, int lv, const u64 *v, const u64 *tab, u64 *out);
+int lift_from_t(Ctx *c, int lv, const u64 *m, u64 *out, int nbatch = 1);
+int permute_limbs(Ctx *c, int nlimb, const u64 *in, u64 *out, u32 g);
+
+// ---------------------------------------------------------------- tables / memory
+int build_modup_tab(Ctx *c, int lv);
+int build_div_tab(Ctx *c, int lv, int kind);
+u64 *dalloc(Ctx *c, size_t words);
+void dfree(Ctx *c, void *p);
+int set_err(Ctx *c, int code, const std::string &msg);
+int cuda_check(Ctx *c, const char *where);
+LimbPat pat_ct(Ctx *c, u64 *base, int npoly, int lv, long long poly_stride_words = -1);
+
+// ---------------------------------------------------------------- exec.cu
+int rotate_hoisted(Ctx *c, const hegmm_ct *in, const int *z, int count, hegmm_ct **outs);
+int mult_relin(Ctx *c, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out);
+int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out);
+int matmul(Ctx *c, const hegmm_ct *A, const hegmm_ct *B, int m, int l, int n, int alg, hegmm_ct **C,
+           hegmm_opcount *cnt);
+int matmul_batch(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+                 hegmm_ct **C);
+int prepare_plan(Ctx *c, int m, int l, int n, int alg);
+void free_plans(Ctx *c);
+hegmm_ct *new_ct(Ctx *c, int level);
+u64 galois_of(Ctx *c, long long z);
+int ensure_galois_key(Ctx *c, u64 g);
+
+}  // namespace hg
+
+struct hegmm_ctx {
+    hg::Ctx c;
+};
+
+struct hegmm_pt {
+    hg::Ctx *ctx;
+    u64 *d;       // [L][N] NTT domain, normal form
+    u64 *d_mont;  // [L][N] NTT domain, Montgomery form
+    int level;
+};
+
+struct hegmm_ct {
+    hg::Ctx *ctx;
+    u64 *d;  // [2][level][N] NTT domain
+    int level;
+};

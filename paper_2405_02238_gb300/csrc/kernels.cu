@@ -1,0 +1,592 @@
+// kernels.cu -- CUDA kernels of the HEGMM library (sm_103a) and their launchers.
+//
+// Data layout: every polynomial is a sequence of limbs, one limb = N uint64
+// residues of one modulus; ciphertexts are [2][level][N]; ModUp digits are
+// [digits][level + K][N]; keys are [dnum][2][L + K][N] in Montgomery form.
+// All kernels are grid-strided over the N coefficients of each limb, so
+// consecutive threads touch consecutive words (coalesced 256-byte warps).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace hg {
+
+// ------------------------------------------------------------------ timing
+
+Launch::Launch(Ctx *c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
+    if (!c->timing) return;
+    if (c->evpool.size() < 2) {
+        for (int i = 0; i < 64; i++) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->evpool.push_back(e);
+        }
+    }
+    a = c->evpool.back();
+    c->evpool.pop_back();
+    b = c->evpool.back();
+    c->evpool.pop_back();
+    cudaEventRecord(a, c->st);
+}
+
+Launch::~Launch() {
+    if (!a) return;
+    cudaEventRecord(b, c->st);
+    c->pending.push_back({kind, a, b, bytes});
+}
+
+// ------------------------------------------------------------------ helpers
+
+static __device__ __forceinline__ u64 *pat_ptr(const LimbPat &p, int b, int N, int &mod) {
+    const int outer = b / p.inner, in = b - outer * p.inner;
+    u64 *base = p.outer_ptrs ? p.outer_ptrs[outer] : p.base + (long long)outer * p.outer_stride;
+    mod = p.mod[in];
+    return base + (size_t)p.off[in] * N;
+}
+
+static inline dim3 grid_coef(int N, int y, int z) { return dim3((unsigned)((N + 255) / 256), (unsigned)y, (unsigned)z); }
+
+// ------------------------------------------------------------------ NTT
+// One CTA per limb.  The limb is staged in (padded) shared memory; radix-8
+// passes run three butterfly stages in registers per group of eight
+// elements, so N = 2^14 takes five shared-memory passes.
+
+template <bool INV>
+__global__ void __launch_bounds__(1024) k_ntt(LimbPat p, const ModDev *__restrict__ mods, const u64 *__restrict__ tw,
+                                             int logN) {
+    extern __shared__ u64 sm[];
+    const int N = 1 << logN;
+    int mi;
+    u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
+    const u64 q = mods[mi].q;
+    const u64 *T = tw + (size_t)mi * 4 * N + (INV ? 2 * (size_t)N : 0);
+    for (int i = threadIdx.x * 2; i < N; i += blockDim.x * 2) {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
+        const int pi = pad16(i);
+        sm[pi] = v.x;
+        sm[pi + 1] = v.y;
+    }
+    __syncthreads();
+    for (int s0 = 0; s0 < logN;) {
+        const int R = logN - s0 < 3 ? logN - s0 : 3;
+        const int G = N >> R;
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            if (!INV) {
+                if (R == 3) ntt_fwd_group<3>(sm, g, s0, logN, T, T + N, q);
+                else if (R == 2) ntt_fwd_group<2>(sm, g, s0, logN, T, T + N, q);
+                else ntt_fwd_group<1>(sm, g, s0, logN, T, T + N, q);
+            } else {
+                if (R == 3) ntt_inv_group<3>(sm, g, s0, logN, T, T + N, q);
+                else if (R == 2) ntt_inv_group<2>(sm, g, s0, logN, T, T + N, q);
+                else ntt_inv_group<1>(sm, g, s0, logN, T, T + N, q);
+            }
+        }
+        __syncthreads();
+        s0 += R;
+    }
+    const u64 ninv = mods[mi].ninv, ninv_sh = mods[mi].ninv_sh;
+    for (int i = threadIdx.x * 2; i < N; i += blockDim.x * 2) {
+        const int pi = pad16(i);
+        ulonglong2 v;
+        v.x = sm[pi];
+        v.y = sm[pi + 1];
+        if (INV) {
+            v.x = mulsh(v.x, ninv, ninv_sh, q);
+            v.y = mulsh(v.y, ninv, ninv_sh, q);
+        }
+        *reinterpret_cast<ulonglong2 *>(ptr + i) = v;
+    }
+}
+
+static size_t ntt_smem(int N) { return (size_t)(N + N / 16) * 8; }
+static int ntt_threads(int N) { return std::min(1024, N / 8); }
+
+int init_kernels(Ctx *c) {
+    size_t sm = ntt_smem(c->N);
+    if (cudaFuncSetAttribute(k_ntt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return cuda_check(c, "ntt smem attribute");
+    return HEGMM_OK;
+}
+
+int ntt_fwd(Ctx *c, const LimbPat &p) {
+    if (p.count <= 0) return HEGMM_OK;
+    Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes());
+    k_ntt<false><<<p.count, ntt_threads(c->N), ntt_smem(c->N), c->st>>>(p, c->d_mods, c->d_tw, c->logN);
+    return cuda_check(c, "ntt_fwd");
+}
+
+int ntt_inv(Ctx *c, const LimbPat &p) {
+    if (p.count <= 0) return HEGMM_OK;
+    Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes());
+    k_ntt<true><<<p.count, ntt_threads(c->N), ntt_smem(c->N), c->st>>>(p, c->d_mods, c->d_tw, c->logN);
+    return cuda_check(c, "ntt_inv");
+}
+
+// ------------------------------------------------------------------ ModUp
+// Table (build_modup_tab): [nd][alpha] x {hinv, hinv_sh}, then
+// [nd][alpha][ne] x {hat mod r, shoup, q_i mod r}.
+
+constexpr int MAX_ALPHA = 4;
+
+__global__ void k_modup(int lv, int ne, int nd, int alpha, int L, int logN, const ModDev *__restrict__ mods,
+                        const u64 *__restrict__ tab, const u64 *__restrict__ xc, long long xc_stride,
+                        const u64 *__restrict__ xn, long long xn_stride, u64 *__restrict__ D, long long D_stride) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int j = blockIdx.y, o = blockIdx.z;
+    const u64 *x = xc + o * xc_stride;
+    const u64 *xv = xn + o * xn_stride;
+    u64 *Dj = D + o * D_stride + (size_t)j * ne * N;
+    const int lo = j * alpha;
+    const int ns = min(alpha, lv - lo);
+    const u64 *tinv = tab + (size_t)j * alpha * 2;
+    const u64 *thm = tab + (size_t)nd * alpha * 2 + (size_t)j * alpha * ne * 3;
+    u64 y[MAX_ALPHA];
+#pragma unroll
+    for (int ii = 0; ii < MAX_ALPHA; ii++)
+        if (ii < ns) y[ii] = mulsh(x[(size_t)(lo + ii) * N + c], tinv[2 * ii], tinv[2 * ii + 1], mods[lo + ii].q);
+    for (int e = 0; e < ne; e++) {
+        if (e >= lo && e < lo + ns) {
+            Dj[(size_t)e * N + c] = xv[(size_t)e * N + c];
+            continue;
+        }
+        const int gm = e < lv ? e : L + (e - lv);
+        const u64 r = mods[gm].q, br = mods[gm].barr;
+        u64 acc = 0;
+#pragma unroll
+        for (int ii = 0; ii < MAX_ALPHA; ii++) {
+            if (ii >= ns) break;
+            const u64 *h = thm + ((size_t)ii * ne + e) * 3;
+            const u64 v = centred(y[ii], mods[lo + ii].q, h[2], r, br);
+            acc = addm(acc, mulsh(v, h[0], h[1], r), r);
+        }
+        Dj[(size_t)e * N + c] = acc;
+    }
+}
+
+int modup_conv(Ctx *c, int lv, int n, const u64 *xc, long long xc_stride, const u64 *xn, long long xn_stride, u64 *D,
+               long long D_stride) {
+    auto it = c->modup.find(lv);
+    if (it == c->modup.end()) {
+        int rc = build_modup_tab(c, lv);
+        if (rc) return rc;
+        it = c->modup.find(lv);
+    }
+    const ModUpTab &tb = it->second;
+    Launch t(c, K_MODUP, (double)n * (lv + (double)tb.nd * tb.ne) * c->limb_bytes());
+    k_modup<<<grid_coef(c->N, tb.nd, n), 256, 0, c->st>>>(lv, tb.ne, tb.nd, c->alpha, c->L, c->logN, c->d_mods, tb.d,
+                                                            xc, xc_stride, xn, xn_stride, D, D_stride);
+    return cuda_check(c, "modup");
+}
+
+// ------------------------------------------------------------------ key-switching inner product
+// u[c][e] = sum_j D_j[e][auto_g(.)] * key[j][c][gp(e)], fused with the
+// NTT-domain automorphism of the hoisted digits; 128-bit accumulation, one
+// Montgomery reduction (keys are stored times 2^64).
+
+__global__ void k_ksw_ip(int lv, int ne, int nd, int np, int L, int logN, const ModDev *__restrict__ mods,
+                         const RotDesc *__restrict__ rots) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int e = blockIdx.y;
+    const RotDesc d = rots[blockIdx.z];
+    const int gm = e < lv ? e : L + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv;
+    const u32 src = d.g == 1 ? (u32)c : auto_src((u32)c, d.g, logN);
+    Acc a0{0, 0}, a1{0, 0};
+    for (int j = 0; j < nd; j++) {
+        const u64 x = d.D[((size_t)j * ne + e) * N + src];
+        const u64 k0 = d.key[(((size_t)j * 2 + 0) * np + gm) * N + c];
+        const u64 k1 = d.key[(((size_t)j * 2 + 1) * np + gm) * N + c];
+        mac(a0, x, k0);
+        mac(a1, x, k1);
+    }
+    d.u[(size_t)e * N + c] = montred(a0, q, qinv);
+    d.u[((size_t)ne + e) * N + c] = montred(a1, q, qinv);
+}
+
+int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
+    if (nrot <= 0) return HEGMM_OK;
+    const int ne = lv + c->K, nd = c->digits(lv);
+    // algorithmic bytes: key (2 nd ne limbs) + digits read + u written
+    Launch t(c, K_KSW_IP, (double)nrot * (2.0 * nd * ne + nd * ne + 2.0 * ne) * c->limb_bytes());
+    k_ksw_ip<<<grid_coef(c->N, ne, nrot), 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots);
+    return cuda_check(c, "ksw_ip");
+}
+
+// ------------------------------------------------------------------ exact division by D with t-correction
+// Table (build_div_tab): [ndrop] x {coef, coef_sh}; [nkeep][ndrop] x {hat,
+// hat_sh, d_k mod q_i}; [nkeep] x {Dinv, Dinv_sh, t mod q_i, shoup};
+// then the modulus indices keep[nkeep], drop[ndrop] as u64.
+
+constexpr int MAX_DROP = 4;
+
+__global__ void k_div_conv(int nkeep, int ndrop, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ tab,
+                           const DivDesc *__restrict__ desc) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const DivDesc d = desc[blockIdx.y];
+    const u64 *tA = tab;
+    const u64 *tB = tA + 2 * ndrop;
+    const u64 *tC = tB + (size_t)3 * nkeep * ndrop;
+    const u64 *tI = tC + (size_t)4 * nkeep;
+    u64 z[MAX_DROP], dq[MAX_DROP];
+#pragma unroll
+    for (int k = 0; k < MAX_DROP; k++) {
+        if (k >= ndrop) break;
+        dq[k] = mods[tI[nkeep + k]].q;
+        z[k] = mulsh(d.u[(size_t)(nkeep + k) * N + c], tA[2 * k], tA[2 * k + 1], dq[k]);
+    }
+    for (int i = 0; i < nkeep; i++) {
+        const ModDev &M = mods[tI[i]];
+        u64 acc = 0;
+#pragma unroll
+        for (int k = 0; k < MAX_DROP; k++) {
+            if (k >= ndrop) break;
+            const u64 *h = tB + ((size_t)i * ndrop + k) * 3;
+            acc = addm(acc, mulsh(centred(z[k], dq[k], h[2], M.q, M.barr), h[0], h[1], M.q), M.q);
+        }
+        d.tmp[(size_t)i * N + c] = acc;
+    }
+}
+
+__global__ void k_div_combine(int nkeep, int ndrop, int logN, const ModDev *__restrict__ mods,
+                              const u64 *__restrict__ tab, const DivDesc *__restrict__ desc) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const DivDesc d = desc[blockIdx.z];
+    const u64 *tC = tab + 2 * ndrop + (size_t)3 * nkeep * ndrop;
+    const u64 *tI = tC + (size_t)4 * nkeep;
+    const u64 q = mods[tI[i]].q;
+    const u64 *k = tC + 4 * i;
+    u64 v = subm(d.u[(size_t)i * N + c], mulsh(d.tmp[(size_t)i * N + c], k[2], k[3], q), q);
+    v = mulsh(v, k[0], k[1], q);
+    if (d.add) {
+        const u32 s = d.g == 1 ? (u32)c : auto_src((u32)c, d.g, logN);
+        v = addm(v, d.add[(size_t)i * N + s], q);
+    }
+    d.out[(size_t)i * N + c] = v;
+}
+
+int div_conv(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    Launch t(c, K_DIV_CONV, (double)npoly * (tab.ndrop + tab.nkeep) * c->limb_bytes());
+    k_div_conv<<<grid_coef(c->N, npoly, 1), 256, 0, c->st>>>(tab.nkeep, tab.ndrop, c->logN, c->d_mods, tab.d, d_desc);
+    return cuda_check(c, "div_conv");
+}
+
+int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    Launch t(c, K_DIV_COMBINE, (double)npoly * 4.0 * tab.nkeep * c->limb_bytes());
+    k_div_combine<<<grid_coef(c->N, tab.nkeep, npoly), 256, 0, c->st>>>(tab.nkeep, tab.ndrop, c->logN, c->d_mods,
+                                                                        tab.d, d_desc);
+    return cuda_check(c, "div_combine");
+}
+
+// ------------------------------------------------------------------ linear-transformation accumulation
+// out[o][comp][i] (+)= sum_{terms of o} src[comp][i] * mask[i]  (HE-CMult + HE-Add of Eq. lintrans)
+
+__global__ void k_lt_acc(int lv, int logN, const ModDev *__restrict__ mods, const LtTerm *__restrict__ terms,
+                         const int *__restrict__ off, u64 *const *__restrict__ outs, int accumulate) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int pl = blockIdx.y, o = blockIdx.z;
+    const int i = pl % lv;
+    const u64 q = mods[i].q, qinv = mods[i].qinv;
+    u64 *out = outs[o] + (size_t)pl * N;
+    u64 acc = accumulate ? out[c] : 0;
+    const int t0 = off[o], t1 = off[o + 1];
+    for (int t = t0; t < t1; t++) {
+        const LtTerm tm = terms[t];
+        acc = addm(acc, montmul(tm.src[(size_t)pl * N + c], tm.mask[(size_t)i * N + c], q, qinv), q);
+    }
+    out[c] = acc;
+}
+
+int lt_accumulate(Ctx *c, int lv, const LtTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout,
+                  int accumulate) {
+    if (nout <= 0) return HEGMM_OK;
+    Launch t(c, K_LT_ACC, 0.0);
+    k_lt_acc<<<grid_coef(c->N, 2 * lv, nout), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_terms, d_off, d_outs,
+                                                               accumulate);
+    return cuda_check(c, "lt_acc");
+}
+
+// ------------------------------------------------------------------ tensor (HE-Mult before relinearisation)
+
+__global__ void k_tensor(int lv, int logN, const ModDev *__restrict__ mods, const Tensor3 *__restrict__ ts) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const Tensor3 T = ts[blockIdx.z];
+    const ModDev M = mods[i];
+    const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
+    const u64 a0 = T.a[o0], a1 = T.a[o1];
+    const u64 b0 = montmul(T.b[o0], M.r2, M.q, M.qinv);  // b R
+    const u64 b1 = montmul(T.b[o1], M.r2, M.q, M.qinv);
+    T.d[o0] = montmul(a0, b0, M.q, M.qinv);
+    T.d[o1] = addm(montmul(a0, b1, M.q, M.qinv), montmul(a1, b0, M.q, M.qinv), M.q);
+    T.d[((size_t)2 * lv + i) * N + c] = montmul(a1, b1, M.q, M.qinv);
+}
+
+int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n) {
+    if (n <= 0) return HEGMM_OK;
+    Launch t(c, K_TENSOR, (double)n * 7.0 * lv * c->limb_bytes());
+    k_tensor<<<grid_coef(c->N, lv, n), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_t);
+    return cuda_check(c, "tensor");
+}
+
+// ------------------------------------------------------------------ sums and pointwise ops
+
+__global__ void k_sum(int lv, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ in, long long stride,
+                      int nk, u64 *__restrict__ out, int accumulate) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int pl = blockIdx.y;
+    const u64 q = mods[pl % lv].q;
+    u64 acc = accumulate ? out[(size_t)pl * N + c] : 0;
+    for (int k = 0; k < nk; k++) acc = addm(acc, in[k * stride + (size_t)pl * N + c], q);
+    out[(size_t)pl * N + c] = acc;
+}
+
+int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate) {
+    Launch t(c, K_SUM, (double)(nk + 1) * 2 * lv * c->limb_bytes());
+    k_sum<<<grid_coef(c->N, 2 * lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, in, in_stride, nk, out, accumulate);
+    return cuda_check(c, "sum");
+}
+
+__global__ void k_add(int lv, int logN, const ModDev *__restrict__ mods, const u64 *a, const u64 *b, u64 *out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const size_t o = (size_t)blockIdx.y * N + c;
+    out[o] = addm(a[o], b[o], mods[blockIdx.y % lv].q);
+}
+
+int pw_add(Ctx *c, int lv, int npoly, const u64 *a, const u64 *b, u64 *out) {
+    Launch t(c, K_POINTWISE, 3.0 * npoly * lv * c->limb_bytes());
+    k_add<<<grid_coef(c->N, npoly * lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, a, b, out);
+    return cuda_check(c, "add");
+}
+
+// out[p][i] = a[p][i] * bR[i or p*lv+i] (Montgomery)
+__global__ void k_mont(int lv, int logN, const ModDev *__restrict__ mods, const u64 *a, const u64 *bR, int b_per_limb,
+                       u64 *out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int pl = blockIdx.y, i = pl % lv;
+    const size_t o = (size_t)pl * N + c;
+    const u64 b = bR[(size_t)(b_per_limb ? i : pl) * N + c];
+    out[o] = montmul(a[o], b, mods[i].q, mods[i].qinv);
+}
+
+int pw_mont(Ctx *c, int lv, int npoly, const u64 *a, const u64 *bR, int b_per_limb, u64 *out) {
+    Launch t(c, K_POINTWISE, 3.0 * npoly * lv * c->limb_bytes());
+    k_mont<<<grid_coef(c->N, npoly * lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, a, bR, b_per_limb, out);
+    return cuda_check(c, "mont");
+}
+
+template <int MODE>  // 0: x -> x R, 1: x R -> x
+__global__ void k_mont_conv(LimbPat p, int logN, const ModDev *__restrict__ mods) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int mi;
+    u64 *ptr = pat_ptr(p, blockIdx.y, N, mi);
+    const ModDev M = mods[mi];
+    ptr[c] = montmul(ptr[c], MODE == 0 ? M.r2 : 1, M.q, M.qinv);
+}
+
+int pw_to_mont(Ctx *c, const LimbPat &p) {
+    Launch t(c, K_POINTWISE, 2.0 * p.count * c->limb_bytes());
+    k_mont_conv<0><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods);
+    return cuda_check(c, "to_mont");
+}
+
+int pw_from_mont(Ctx *c, const LimbPat &p) {
+    Launch t(c, K_POINTWISE, 2.0 * p.count * c->limb_bytes());
+    k_mont_conv<1><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods);
+    return cuda_check(c, "from_mont");
+}
+
+__global__ void k_permute(int logN, const u64 *in, u64 *out, u32 g) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const size_t b = (size_t)blockIdx.y * N;
+    out[b + c] = in[b + auto_src((u32)c, g, logN)];
+}
+
+int permute_limbs(Ctx *c, int nlimb, const u64 *in, u64 *out, u32 g) {
+    Launch t(c, K_POINTWISE, 2.0 * nlimb * c->limb_bytes());
+    k_permute<<<grid_coef(c->N, nlimb, 1), 256, 0, c->st>>>(c->logN, in, out, g);
+    return cuda_check(c, "permute");
+}
+
+// ------------------------------------------------------------------ sampling (coefficient domain)
+
+template <int KIND>  // 0 uniform mod q (index gp N + c), 1 t * CBD(eta), 2 ternary
+__global__ void k_sample(LimbPat p, int logN, const ModDev *__restrict__ mods, u64 stream, int eta) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int mi;
+    u64 *ptr = pat_ptr(p, blockIdx.y, N, mi);
+    const ModDev M = mods[mi];
+    u64 v;
+    if (KIND == 0) {
+        v = rng_draw(stream, (u64)mi * N + c) % M.q;
+    } else if (KIND == 1) {
+        const long long e = cbd_sample(rng_draw(stream, (u64)c), eta);
+        const u64 r = e >= 0 ? (u64)e : M.q - (u64)(-e);
+        v = mulsh(r, M.tq, M.tq_sh, M.q);
+    } else {
+        const u64 r = rng_draw(stream, (u64)c) % 3;
+        v = r == 0 ? M.q - 1 : (r == 1 ? 0 : 1);
+    }
+    ptr[c] = v;
+}
+
+int sample_uniform(Ctx *c, const LimbPat &p, u64 stream, const int *) {
+    Launch t(c, K_SAMPLE, 1.0 * p.count * c->limb_bytes());
+    k_sample<0><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods, stream, 0);
+    return cuda_check(c, "sample_uniform");
+}
+
+int sample_cbd_t(Ctx *c, const LimbPat &p, u64 stream, int eta) {
+    Launch t(c, K_SAMPLE, 1.0 * p.count * c->limb_bytes());
+    k_sample<1><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods, stream, eta);
+    return cuda_check(c, "sample_cbd");
+}
+
+int sample_ternary(Ctx *c, const LimbPat &p, u64 stream) {
+    Launch t(c, K_SAMPLE, 1.0 * p.count * c->limb_bytes());
+    k_sample<2><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods, stream, 0);
+    return cuda_check(c, "sample_ternary");
+}
+
+// ------------------------------------------------------------------ keys, encryption, decryption
+
+// One digit j of a switching key from s' to s (NTT domain):
+//   b = t e - a s + [P]_{q_i} s' on the primes of digit j, t e - a s elsewhere;
+// both b and a are then stored times 2^64 (Montgomery form).
+__global__ void k_key_combine(int np, int logN, const ModDev *__restrict__ mods, u64 *kb, u64 *ka,
+                              const u64 *__restrict__ sR, const u64 *__restrict__ sprime, const u64 *__restrict__ Pmod,
+                              int lo, int hi) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const ModDev M = mods[i];
+    const size_t o = (size_t)i * N + c;
+    const u64 a = ka[o];
+    u64 b = subm(kb[o], montmul(a, sR[o], M.q, M.qinv), M.q);
+    if (i >= lo && i < hi) b = addm(b, mulsh(sprime[o], Pmod[2 * i], Pmod[2 * i + 1], M.q), M.q);
+    kb[o] = montmul(b, M.r2, M.q, M.qinv);
+    ka[o] = montmul(a, M.r2, M.q, M.qinv);
+}
+
+int key_digit_combine(Ctx *c, u64 *kb, u64 *ka, const u64 *sprime, const u64 *d_Pmod, int lo, int hi) {
+    Launch t(c, K_POINTWISE, 6.0 * c->np * c->limb_bytes());
+    k_key_combine<<<grid_coef(c->N, c->np, 1), 256, 0, c->st>>>(c->np, c->logN, c->d_mods, kb, ka, c->d_sR, sprime,
+                                                               d_Pmod, lo, hi);
+    return cuda_check(c, "key_combine");
+}
+
+// c0 = t e + m - a s (NTT domain), c1 = a.
+__global__ void k_enc_combine(int lv, int logN, const ModDev *__restrict__ mods, u64 *ct, const u64 *__restrict__ pt,
+                              const u64 *__restrict__ sR) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const ModDev M = mods[i];
+    const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
+    const u64 v = addm(ct[o0], pt[o0], M.q);
+    ct[o0] = subm(v, montmul(ct[o1], sR[o0], M.q, M.qinv), M.q);
+}
+
+int encrypt_combine(Ctx *c, int lv, u64 *ct, const u64 *pt) {
+    Launch t(c, K_POINTWISE, 4.0 * lv * c->limb_bytes());
+    k_enc_combine<<<grid_coef(c->N, lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, ct, pt, c->d_sR);
+    return cuda_check(c, "enc_combine");
+}
+
+// v = c0 + c1 s (NTT domain)
+__global__ void k_dec_dot(int lv, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ ct,
+                          const u64 *__restrict__ sR, u64 *v) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const ModDev M = mods[i];
+    const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
+    v[o0] = addm(ct[o0], montmul(ct[o1], sR[o0], M.q, M.qinv), M.q);
+}
+
+int decrypt_dot(Ctx *c, int lv, const u64 *ct, u64 *v) {
+    Launch t(c, K_CODEC, 3.0 * lv * c->limb_bytes());
+    k_dec_dot<<<grid_coef(c->N, lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, ct, c->d_sR, v);
+    return cuda_check(c, "dec_dot");
+}
+
+// Centred v (coefficient residues over q_0..q_{lv-1}) reduced mod t.
+// y_i = [v_i (Q/q_i)^-1]_{q_i}; k = round(sum y_i / q_i) (exact while |v| is
+// far below Q/2); v = sum y_i (Q/q_i) - k Q.  tab per i: {hinv, hinv_sh,
+// (Q/q_i) mod t, q_i as double bits}, then Q mod t.
+__global__ void k_crt_t(int lv, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ v,
+                        const u64 *__restrict__ tab, u64 t, u64 *out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    double frac = 0.0;
+    u64 acc = 0;
+    for (int i = 0; i < lv; i++) {
+        const u64 *tb = tab + 4 * i;
+        const u64 y = mulsh(v[(size_t)i * N + c], tb[0], tb[1], mods[i].q);
+        frac += (double)y / __longlong_as_double((long long)tb[3]);
+        acc = (acc + (y % t) * tb[2]) % t;
+    }
+    const u64 k = (u64)llrint(frac);
+    const u64 Qt = tab[4 * lv];
+    out[c] = (acc + t - (k % t) * Qt % t) % t;
+}
+
+int crt_to_t(Ctx *c, int lv, const u64 *v, const u64 *tab, u64 *out) {
+    Launch t(c, K_CODEC, (double)(lv + 1) * c->limb_bytes());
+    k_crt_t<<<grid_coef(c->N, 1, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, v, tab, c->t, out);
+    return cuda_check(c, "crt_t");
+}
+
+// m in [0, t) -> centred -> residues over q_0..q_{lv-1}
+__global__ void k_lift_t(int lv, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ m, u64 t,
+                         u64 *out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y, b = blockIdx.z;
+    const u64 q = mods[i].q;
+    const u64 x = m[(size_t)b * N + c];
+    out[((size_t)b * lv + i) * N + c] = x <= (t - 1) / 2 ? x % q : q - (t - x) % q;
+}
+
+int lift_from_t(Ctx *c, int lv, const u64 *m, u64 *out, int nbatch) {
+    Launch t(c, K_CODEC, (double)nbatch * (lv + 1) * c->limb_bytes());
+    k_lift_t<<<grid_coef(c->N, lv, nbatch), 256, 0, c->st>>>(lv, c->logN, c->d_mods, m, c->t, out);
+    return cuda_check(c, "lift_t");
+}
+
+}  // namespace hg

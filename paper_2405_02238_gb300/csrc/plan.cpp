@@ -1,0 +1,251 @@
+// plan.cpp -- host planner for Algorithms 1 and 2 (see plan.h).
+#include "plan.h"
+
+#include <algorithm>
+#include <set>
+
+#include "../../include/hegmm.h"
+
+namespace hg {
+
+static inline int imod(long long a, int b) {
+    long long r = a % b;
+    return (int)(r < 0 ? r + b : r);
+}
+
+int alg1_length(int m, int l, int n) { return std::max(m * l, std::max(l * n, m * n)); }
+
+static void alg2_shape(int m, int l, int n, char &kase, int &p, int &t, int &M, int &Np, int &WA, int &HB) {
+    p = std::min(m, std::min(l, n));
+    if (p == m) {
+        kase = 'A';
+        t = (l + p - 1) / p;
+    } else if (p == n) {
+        kase = 'B';
+        t = (l + p - 1) / p;
+    } else {
+        kase = 'L';
+        t = 1;
+    }
+    M = kase == 'A' ? t * m : m;
+    Np = kase == 'B' ? t * n : n;
+    WA = std::max(l, Np);
+    HB = std::max(l, M);
+}
+
+int alg2_length(int m, int l, int n) {
+    char k;
+    int p, t, M, Np, WA, HB;
+    alg2_shape(m, l, n, k, p, t, M, Np, WA, HB);
+    return std::max(M * WA, std::max(HB * Np, M * Np));
+}
+
+int resolve_alg(int m, int l, int n, int alg, int S) {
+    if (m <= 0 || l <= 0 || n <= 0) return 0;
+    if (alg == 1) return alg1_length(m, l, n) <= S ? 1 : 0;
+    if (alg == 2) return alg2_length(m, l, n) <= S ? 2 : 0;
+    if (alg2_length(m, l, n) <= S) return 2;
+    if (alg1_length(m, l, n) <= S) return 1;
+    return 0;
+}
+
+// Group a destination -> source slot map by offset d = src - dst.
+static std::vector<Diag> group(const std::vector<std::pair<int, int>> &dst_src) {
+    std::map<int, std::vector<int>> g;
+    for (auto &ds : dst_src) g[ds.second - ds.first].push_back(ds.first);
+    std::vector<Diag> out;
+    for (auto &kv : g) {
+        Diag d;
+        d.d = kv.first;
+        d.dst = kv.second;
+        std::sort(d.dst.begin(), d.dst.end());
+        out.push_back(d);
+    }
+    return out;
+}
+
+HostPlan make_host_plan(int m, int l, int n, int alg) {
+    HostPlan P;
+    P.m = m;
+    P.l = l;
+    P.n = n;
+    P.alg = alg;
+    if (alg == 1) {
+        // Algorithm 1, column-major: A0 = sigma(A) (m x l), B0 = tau(B) (l x n);
+        // eps^k_{m x n}: (i, j) <- (i, [j+k]_l); omega^k_{m x n}: (i, j) <- ([i+k]_l, j).
+        P.kase = '1';
+        P.col = true;
+        P.p = l;
+        P.t = 1;
+        P.M = m;
+        P.Np = n;
+        P.a_rows = m;
+        P.a_cols = l;
+        P.b_rows = l;
+        P.b_cols = n;
+        P.res_rows = m;
+        P.res_cols = n;
+        P.length = alg1_length(m, l, n);
+        for (int k = 0; k < l; k++) {
+            std::vector<std::pair<int, int>> e, o;
+            for (int i = 0; i < m; i++)
+                for (int j = 0; j < n; j++) {
+                    const int dst = P.flat(i, j, m, n);
+                    e.push_back({dst, P.flat(i, (j + k) % l, m, l)});
+                    o.push_back({dst, P.flat((i + k) % l, j, l, n)});
+                }
+            PlanIter it;
+            it.eps = group(e);
+            it.omg = group(o);
+            P.iters.push_back(it);
+        }
+        return P;
+    }
+    alg2_shape(m, l, n, P.kase, P.p, P.t, P.M, P.Np, P.WA, P.HB);
+    P.col = P.kase != 'B';
+    P.a_rows = P.M;
+    P.a_cols = P.WA;
+    P.b_rows = P.HB;
+    P.b_cols = P.Np;
+    P.res_rows = P.M;
+    P.res_cols = P.Np;
+    P.length = alg2_length(m, l, n);
+    std::vector<char> seen(l, 0);
+    for (int k = 0; k < P.p; k++) {
+        std::vector<char> keep(P.t, 0);
+        for (int h = 0; h < P.t; h++) {
+            const int ph = (k + h * P.p) % l;
+            keep[h] = !seen[ph];
+            seen[ph] = 1;
+        }
+        std::vector<std::pair<int, int>> e, o;
+        for (int i = 0; i < P.M; i++)
+            for (int j = 0; j < P.Np; j++) {
+                const int dst = P.flat(i, j, P.M, P.Np);
+                const bool kept = P.kase == 'A' ? keep[i / m] : (P.kase == 'B' ? keep[j / n] : true);
+                if (kept) {
+                    // stored column of sA holding sigma(Abar) column [j+k]_l
+                    int cc = j + k;
+                    while (cc >= P.WA) cc -= l;
+                    e.push_back({dst, P.flat(i, cc, P.M, P.WA)});
+                }
+                int rr = i + k;
+                while (rr >= P.HB) rr -= l;
+                o.push_back({dst, P.flat(rr, j, P.HB, P.Np)});
+            }
+        PlanIter it;
+        it.eps = group(e);
+        it.omg = group(o);
+        P.iters.push_back(it);
+    }
+    for (int h = 1; h < P.t; h++) P.extract.push_back(h * P.p);
+    return P;
+}
+
+std::vector<uint64_t> HostPlan::a_slots(const int64_t *A, uint64_t tm) const {
+    std::vector<uint64_t> v((size_t)a_rows * a_cols, 0);
+    for (int i = 0; i < a_rows; i++)
+        for (int c = 0; c < a_cols; c++) {
+            // Algorithm 1: sigma(A)_{i,c} = A_{i,[i+c]_l}.
+            // Algorithm 2: eps^0(sigma(Abar))_{i,c} = Abar_{i,[i+c]_l}, Abar row i = A row i mod m.
+            const int src_row = (alg == 2 && kase == 'A') ? i % m : i;
+            const int64_t x = A[(size_t)src_row * l + imod((long long)i + c, l)];
+            v[flat(i, c, a_rows, a_cols)] = (uint64_t)imod(x, (int)tm);
+        }
+    return v;
+}
+
+std::vector<uint64_t> HostPlan::b_slots(const int64_t *B, uint64_t tm) const {
+    std::vector<uint64_t> v((size_t)b_rows * b_cols, 0);
+    for (int r = 0; r < b_rows; r++)
+        for (int j = 0; j < b_cols; j++) {
+            // tau(Bbar)_{r,j} = Bbar_{[r+j]_l, j}; Bbar column j = B column j mod n.
+            const int src_col = (alg == 2 && kase == 'B') ? j % n : j;
+            const int64_t x = B[(size_t)imod((long long)r + j, l) * n + src_col];
+            v[flat(r, j, b_rows, b_cols)] = (uint64_t)imod(x, (int)tm);
+        }
+    return v;
+}
+
+long long HostPlan::paper_rot() const {
+    long long r = 0;
+    for (auto &it : iters) {
+        for (auto &d : it.eps) r += d.d != 0;
+        for (auto &d : it.omg) r += d.d != 0;
+    }
+    return r + (long long)extract.size();
+}
+
+long long HostPlan::paper_cmult() const {
+    long long r = 0;
+    for (auto &it : iters) r += (long long)it.eps.size() + (long long)it.omg.size();
+    return r;
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" {
+
+int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *out) {
+    if (!out || slots <= 0) return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::set<long long> zs[2];
+    for (auto &it : P.iters)
+        for (int s = 0; s < 2; s++)
+            for (auto &d : (s == 0 ? it.eps : it.omg)) {
+                long long z = ((long long)d.d % slots + slots) % slots;
+                if (z) zs[s].insert(z);
+            }
+    const long long ni = (long long)P.iters.size(), ne = (long long)P.extract.size();
+    out->rot = P.paper_rot();
+    out->cmult = P.paper_cmult();
+    out->mult = ni;
+    out->relin = ni;
+    out->extract = ne;
+    out->add = out->cmult - 2 * ni + (ni - 1) + ne;
+    out->ksw = (long long)zs[0].size() + (long long)zs[1].size() + ni + ne;
+    out->modup = 2 + ni + (ne > 0 ? 1 : 0);
+    out->modswitch = 0;
+    return HEGMM_OK;
+}
+
+int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int cap) {
+    if (slots <= 0 || cap < 0 || (cap > 0 && !buf)) return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::vector<int> v{a, (int)P.kase, P.col ? 1 : 0, (int)P.iters.size(), (int)P.extract.size()};
+    for (auto &it : P.iters)
+        for (int s = 0; s < 2; s++) {
+            const auto &ds = s == 0 ? it.eps : it.omg;
+            v.push_back((int)ds.size());
+            for (auto &d : ds) {
+                v.push_back(d.d);
+                v.push_back((int)d.dst.size());
+                v.insert(v.end(), d.dst.begin(), d.dst.end());
+            }
+        }
+    v.insert(v.end(), P.extract.begin(), P.extract.end());
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < n; j++) v.push_back(P.result_slot(i, j));
+    for (int i = 0; i < cap && i < (int)v.size(); i++) buf[i] = v[i];
+    return (int)v.size();
+}
+
+int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t, uint64_t *out,
+                      int cap) {
+    if (!mat || slots <= 0 || (role != 0 && role != 1) || t < 2) return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::vector<uint64_t> v = role == 0 ? P.a_slots(mat, t) : P.b_slots(mat, t);
+    if (cap < (int)v.size() || !out) return (int)v.size();
+    for (size_t i = 0; i < v.size(); i++) out[i] = v[i];
+    return (int)v.size();
+}
+
+}  // extern "C"

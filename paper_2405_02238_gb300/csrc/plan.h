@@ -1,0 +1,59 @@
+// plan.h -- host planner: the linear transformations of Algorithms 1 and 2.
+//
+// For a product A (m x l) . B (l x n) the planner fixes, following
+// arXiv 2405.02238 Section 3:
+//  * the client-side slot layouts: sigma(A) / tau(B) for Algorithm 1; for
+//    Algorithm 2 the duplicated operand and eps^0_{M x max(l,N')}(sigma(Abar)),
+//    omega^0_{max(l,M) x N'}(tau(Bbar)) (Algorithm 2, lines 1-18);
+//  * per iteration k the diagonals {d: destination slots} of eps^k and
+//    omega^k as linear transformations (Eq. lintrans), d = source - destination
+//    slot, with Algorithm 2's first-occurrence keep mask folded into eps^k;
+//  * Algorithm 2's extraction rotations h p (h = 1..t-1) and the result slots.
+// Algorithm 2 checks p = m first, then p = n, else the l-case; its initial
+// C <- sA (.) tB is taken as C <- 0 (the loop already covers k = 0).
+#pragma once
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+namespace hg {
+
+struct Diag {
+    int d;                 // rotation offset (left), |d| < S
+    std::vector<int> dst;  // destination slots where the mask is non-zero
+};
+
+struct PlanIter {
+    std::vector<Diag> eps, omg;  // ascending d
+};
+
+struct HostPlan {
+    int m = 0, l = 0, n = 0, alg = 0;
+    char kase = '1';     // '1' (Algorithm 1), 'A', 'B', 'L' (Algorithm 2 cases)
+    bool col = true;     // column-major flattening
+    int p = 0, t = 1, M = 0, Np = 0, WA = 0, HB = 0;
+    int a_rows = 0, a_cols = 0, b_rows = 0, b_cols = 0;
+    int res_rows = 0, res_cols = 0;
+    int length = 0;      // largest slot vector used
+    std::vector<PlanIter> iters;
+    std::vector<int> extract;
+
+    int flat(int i, int j, int rows, int cols) const { return col ? i + j * rows : i * cols + j; }
+    int result_slot(int i, int j) const { return flat(i, j, res_rows, res_cols); }
+    // Slot vectors of the client-side layouts; values mod t.
+    std::vector<uint64_t> a_slots(const int64_t *A, uint64_t t) const;
+    std::vector<uint64_t> b_slots(const int64_t *B, uint64_t t) const;
+    // Paper-style counts: one HE-Rot per non-zero diagonal, one CMult per diagonal.
+    long long paper_rot() const;
+    long long paper_cmult() const;
+};
+
+// Number of slots Algorithm 1 / 2 needs for (m, l, n).
+int alg1_length(int m, int l, int n);
+int alg2_length(int m, int l, int n);
+// AUTO: Algorithm 2 if it fits S slots, else Algorithm 1, else 0.
+int resolve_alg(int m, int l, int n, int alg, int S);
+HostPlan make_host_plan(int m, int l, int n, int alg);
+
+}  // namespace hg

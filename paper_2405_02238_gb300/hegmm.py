@@ -1,0 +1,357 @@
+"""ctypes binding of libhegmm.so (include/hegmm.h), argument marshalling only.
+
+Every function here has the name of the C entry point it calls and only
+converts arguments and results; all work runs in the library's CUDA
+kernels.  If the library cannot be loaded the import fails loudly: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhegmm.so")
+
+HEGMM_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
+ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
+ROLE_A, ROLE_B = 0, 1
+
+
+class HegmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class hegmm_params(ctypes.Structure):
+    _fields_ = [
+        ("logN", ctypes.c_int),
+        ("t", ctypes.c_uint64),
+        ("L", ctypes.c_int),
+        ("qbits", ctypes.c_int),
+        ("K", ctypes.c_int),
+        ("alpha", ctypes.c_int),
+        ("eta", ctypes.c_int),
+        ("ms_drop", ctypes.c_int),
+    ]
+
+
+class hegmm_opcount(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in
+                ("rot", "cmult", "add", "mult", "relin", "extract", "ksw", "modup", "modswitch")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+u64p = ctypes.POINTER(ctypes.c_uint64)
+i64p = ctypes.POINTER(ctypes.c_int64)
+intp = ctypes.POINTER(ctypes.c_int)
+vp = ctypes.c_void_p
+
+_SIGS = {
+    "hegmm_ctx_create": (ctypes.c_int, [ctypes.POINTER(hegmm_params), vp, ctypes.POINTER(vp)]),
+    "hegmm_ctx_destroy": (None, [vp]),
+    "hegmm_last_error": (ctypes.c_char_p, [vp]),
+    "hegmm_get_primes": (ctypes.c_int, [vp, u64p]),
+    "hegmm_keygen": (ctypes.c_int, [vp, ctypes.c_uint64, intp, ctypes.c_int, ctypes.c_int]),
+    "hegmm_keygen_rotations": (ctypes.c_int, [vp, intp, ctypes.c_int]),
+    "hegmm_key_export": (ctypes.c_int, [vp, ctypes.c_uint64, u64p]),
+    "hegmm_encode": (ctypes.c_int, [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(vp)]),
+    "hegmm_encode_slots": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_encrypt": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(vp)]),
+    "hegmm_matmul": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(vp), ctypes.POINTER(hegmm_opcount)]),
+    "hegmm_matmul_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp,
+                                          ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_decrypt": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p]),
+    "hegmm_decrypt_slots": (ctypes.c_int, [vp, vp, u64p]),
+    "hegmm_rotate": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_rotate_many": (ctypes.c_int, [vp, vp, intp, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_cmult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
+    "hegmm_add": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
+    "hegmm_mult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
+    "hegmm_modswitch": (ctypes.c_int, [vp, vp, ctypes.POINTER(vp)]),
+    "hegmm_ct_level": (ctypes.c_int, [vp]),
+    "hegmm_ct_export": (ctypes.c_int, [vp, vp, u64p]),
+    "hegmm_ct_import": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_sync": (ctypes.c_int, [vp]),
+    "hegmm_pt_destroy": (None, [vp]),
+    "hegmm_ct_destroy": (None, [vp]),
+    "hegmm_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+    "hegmm_kernel_kinds": (ctypes.c_int, []),
+    "hegmm_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "hegmm_kernel_stats": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+    "hegmm_kernel_reset": (ctypes.c_int, [vp]),
+    "hegmm_plan_counts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(hegmm_opcount)]),
+    "hegmm_plan_describe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           intp, ctypes.c_int]),
+    "hegmm_plan_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, i64p, ctypes.c_uint64, u64p, ctypes.c_int]),
+}
+
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libhegmm.so and declares every entry point of include/hegmm.h."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("libhegmm.so not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def hegmm_plan_counts(m: int, l: int, n: int, alg: int, slots: int) -> dict:
+    cnt = hegmm_opcount()
+    rc = load().hegmm_plan_counts(m, l, n, alg, slots, ctypes.byref(cnt))
+    if rc != HEGMM_OK:
+        raise HegmmError(rc, "plan_counts")
+    return cnt.as_dict()
+
+
+def hegmm_plan_describe(m: int, l: int, n: int, alg: int, slots: int) -> List[int]:
+    lib = load()
+    need = lib.hegmm_plan_describe(m, l, n, alg, slots, None, 0)
+    if need < 0:
+        raise HegmmError(need, "plan_describe")
+    buf = (ctypes.c_int * need)()
+    lib.hegmm_plan_describe(m, l, n, alg, slots, buf, need)
+    return list(buf)
+
+
+def hegmm_plan_layout(m: int, l: int, n: int, alg: int, slots: int, role: int, mat, t: int) -> np.ndarray:
+    lib = load()
+    a = np.ascontiguousarray(mat, dtype=np.int64)
+    need = lib.hegmm_plan_layout(m, l, n, alg, slots, role, a.ctypes.data_as(i64p), t, None, 0)
+    if need < 0:
+        raise HegmmError(need, "plan_layout")
+    out = np.zeros(need, dtype=np.uint64)
+    lib.hegmm_plan_layout(m, l, n, alg, slots, role, a.ctypes.data_as(i64p), t, out.ctypes.data_as(u64p), need)
+    return out
+
+
+def _u64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def _ptr(a: np.ndarray, t=u64p):
+    return a.ctypes.data_as(t)
+
+
+class Context:
+    """Owns one hegmm_ctx; methods are thin wrappers of the C entry points."""
+
+    def __init__(self, logN, t, L, qbits, K, alpha, eta=21, ms_drop=0, stream=None):
+        self.lib = load()
+        self.params = hegmm_params(logN, t, L, qbits, K, alpha, eta, ms_drop)
+        if stream is None:
+            import torch
+
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = vp()
+        rc = self.lib.hegmm_ctx_create(ctypes.byref(self.params), vp(stream), ctypes.byref(h))
+        if rc != HEGMM_OK:
+            raise HegmmError(rc, "hegmm_ctx_create")
+        self.h = h
+        self.N = 1 << logN
+        self.S = self.N // 2
+        self.L = L
+        self.K = K
+        self.t = t
+        self.level_after_product = L - ms_drop
+
+    @classmethod
+    def from_preset(cls, p, stream=None):
+        return cls(p.logN, p.t, p.L, p.qbits, p.K, p.alpha, p.eta, p.ms_drop, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hegmm_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc != HEGMM_OK:
+            msg = self.lib.hegmm_last_error(self.h)
+            raise HegmmError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    # ------------------------------------------------------------ wrappers
+    def hegmm_get_primes(self) -> List[int]:
+        out = np.zeros(self.L + self.K, dtype=np.uint64)
+        self._check(self.lib.hegmm_get_primes(self.h, _ptr(out)), "get_primes")
+        return [int(x) for x in out]
+
+    def hegmm_keygen(self, seed: int, shapes: Sequence[Tuple[int, int, int]] = (), alg: int = ALG_AUTO):
+        arr = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
+        self._check(self.lib.hegmm_keygen(self.h, seed, arr.ctypes.data_as(intp), len(shapes), alg), "keygen")
+
+    def hegmm_keygen_rotations(self, zs: Sequence[int]):
+        arr = np.ascontiguousarray(np.array(zs, dtype=np.int32))
+        self._check(self.lib.hegmm_keygen_rotations(self.h, arr.ctypes.data_as(intp), len(zs)), "keygen_rotations")
+
+    def hegmm_key_export(self, which: int) -> np.ndarray:
+        dnum = self.params.L // self.params.alpha
+        out = np.zeros((dnum, 2, self.L + self.K, self.N), dtype=np.uint64)
+        self._check(self.lib.hegmm_key_export(self.h, which, _ptr(out)), "key_export")
+        return out
+
+    def hegmm_encode(self, role: int, mat: np.ndarray, m: int, l: int, n: int, alg: int = ALG_AUTO) -> "Plaintext":
+        a = np.ascontiguousarray(mat, dtype=np.int64)
+        out = vp()
+        self._check(self.lib.hegmm_encode(self.h, role, _ptr(a, i64p), m, l, n, alg, ctypes.byref(out)), "encode")
+        return Plaintext(self, out)
+
+    def hegmm_encode_slots(self, slots) -> "Plaintext":
+        a = _u64(slots)
+        out = vp()
+        self._check(self.lib.hegmm_encode_slots(self.h, _ptr(a), len(a), ctypes.byref(out)), "encode_slots")
+        return Plaintext(self, out)
+
+    def hegmm_encrypt(self, pt: "Plaintext", seed: int, stream_id: int) -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_encrypt(self.h, pt.h, seed, stream_id, ctypes.byref(out)), "encrypt")
+        return Ciphertext(self, out)
+
+    def hegmm_matmul(self, A: "Ciphertext", B: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO):
+        out = vp()
+        cnt = hegmm_opcount()
+        self._check(self.lib.hegmm_matmul(self.h, A.h, B.h, m, l, n, alg, ctypes.byref(out), ctypes.byref(cnt)),
+                    "matmul")
+        return Ciphertext(self, out), cnt.as_dict()
+
+    def hegmm_matmul_batch(self, As, Bs, shapes, alg: int = ALG_AUTO):
+        n = len(As)
+        pa = (vp * n)(*[a.h for a in As])
+        pb = (vp * n)(*[b.h for b in Bs])
+        mln = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
+        outs = (vp * n)()
+        self._check(self.lib.hegmm_matmul_batch(self.h, n, pa, pb, mln.ctypes.data_as(intp), alg, outs),
+                    "matmul_batch")
+        return [Ciphertext(self, vp(outs[i])) for i in range(n)]
+
+    def hegmm_decrypt(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO) -> np.ndarray:
+        out = np.zeros((m, n), dtype=np.uint64)
+        self._check(self.lib.hegmm_decrypt(self.h, ct.h, m, l, n, alg, _ptr(out)), "decrypt")
+        return out
+
+    def hegmm_decrypt_slots(self, ct: "Ciphertext") -> np.ndarray:
+        out = np.zeros(self.S, dtype=np.uint64)
+        self._check(self.lib.hegmm_decrypt_slots(self.h, ct.h, _ptr(out)), "decrypt_slots")
+        return out
+
+    def hegmm_rotate(self, ct: "Ciphertext", z: int) -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_rotate(self.h, ct.h, z, ctypes.byref(out)), "rotate")
+        return Ciphertext(self, out)
+
+    def hegmm_rotate_many(self, ct: "Ciphertext", zs: Sequence[int]) -> List["Ciphertext"]:
+        arr = np.ascontiguousarray(np.array(zs, dtype=np.int32))
+        outs = (vp * len(zs))()
+        self._check(self.lib.hegmm_rotate_many(self.h, ct.h, arr.ctypes.data_as(intp), len(zs), outs), "rotate_many")
+        return [Ciphertext(self, vp(outs[i])) for i in range(len(zs))]
+
+    def hegmm_cmult(self, ct: "Ciphertext", pt: "Plaintext") -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_cmult(self.h, ct.h, pt.h, ctypes.byref(out)), "cmult")
+        return Ciphertext(self, out)
+
+    def hegmm_add(self, a: "Ciphertext", b: "Ciphertext") -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_add(self.h, a.h, b.h, ctypes.byref(out)), "add")
+        return Ciphertext(self, out)
+
+    def hegmm_mult(self, a: "Ciphertext", b: "Ciphertext") -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_mult(self.h, a.h, b.h, ctypes.byref(out)), "mult")
+        return Ciphertext(self, out)
+
+    def hegmm_modswitch(self, ct: "Ciphertext") -> "Ciphertext":
+        out = vp()
+        self._check(self.lib.hegmm_modswitch(self.h, ct.h, ctypes.byref(out)), "modswitch")
+        return Ciphertext(self, out)
+
+    def hegmm_ct_export(self, ct: "Ciphertext", out: Optional[np.ndarray] = None) -> np.ndarray:
+        lv = self.lib.hegmm_ct_level(ct.h)
+        if out is None:
+            out = np.zeros((2, lv, self.N), dtype=np.uint64)
+        self._check(self.lib.hegmm_ct_export(self.h, ct.h, _ptr(out)), "ct_export")
+        return out
+
+    def hegmm_ct_import(self, host: np.ndarray) -> "Ciphertext":
+        a = _u64(host)
+        lv = a.shape[1]
+        out = vp()
+        self._check(self.lib.hegmm_ct_import(self.h, _ptr(a), lv, ctypes.byref(out)), "ct_import")
+        return Ciphertext(self, out)
+
+    def hegmm_sync(self):
+        self._check(self.lib.hegmm_sync(self.h), "sync")
+
+    def hegmm_set_timing(self, enable: bool):
+        self._check(self.lib.hegmm_set_timing(self.h, int(bool(enable))), "set_timing")
+
+    def hegmm_kernel_stats(self):
+        """{kernel name: (total ms, launches, algorithmic bytes)}."""
+        out = {}
+        for k in range(self.lib.hegmm_kernel_kinds()):
+            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            self._check(self.lib.hegmm_kernel_stats(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
+                        "kernel_stats")
+            out[self.lib.hegmm_kernel_name(k).decode()] = (ms.value, n.value, b.value)
+        return out
+
+    def hegmm_kernel_reset(self):
+        self._check(self.lib.hegmm_kernel_reset(self.h), "kernel_reset")
+
+
+class Plaintext:
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                self.ctx.lib.hegmm_pt_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Ciphertext:
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+
+    @property
+    def level(self) -> int:
+        return self.ctx.lib.hegmm_ct_level(self.h)
+
+    def __del__(self):
+        try:
+            if self.h and self.ctx.h:
+                self.ctx.lib.hegmm_ct_destroy(self.h)
+        except Exception:
+            pass
