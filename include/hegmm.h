@@ -167,6 +167,25 @@ int hegmm_add(hegmm_ctx *ctx, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **o
 int hegmm_mult(hegmm_ctx *ctx, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out); /* tensor + relin */
 int hegmm_modswitch(hegmm_ctx *ctx, const hegmm_ct *ct, hegmm_ct **out);          /* drop last prime */
 
+/* HE-Rot of `in` by z into the caller's existing ciphertext `out` (same
+ * level, not the same handle), allocating no device memory.  The paper has
+ * no counterpart: it is a variant of hegmm_rotate for callers that cannot
+ * allocate while they run this library -- for example an application whose
+ * framework already holds the GPU's memory in its own pool, or a serving
+ * loop that must not block in cudaMalloc / cudaFree (cudaFree synchronises
+ * the device).  All intermediates live in one fixed 12 MiB device array
+ * inside the library, which every GPU that loads the library keeps until the
+ * process exits; parameter sets whose rotation needs more scratch than that
+ * are rejected with HEGMM_EINVAL and a message.  The first call on a device
+ * looks up that array's device address (with that device current); make
+ * this first call before any stream capture.  Every call reuses the same
+ * array and leaves its contents behind (nothing in it needs clearing: each
+ * call writes every word it reads), so calls whose GPU work overlaps -- on
+ * different streams, contexts or threads -- race and give wrong results.
+ * The result is bit-identical to hegmm_rotate.  Errors: HEGMM_EINVAL,
+ * HEGMM_ENOKEY, HEGMM_ECUDA. */
+int hegmm_rotate_noalloc(hegmm_ctx *ctx, const hegmm_ct *in, int z, hegmm_ct *out);
+
 /* Level (number of chain primes) of a ciphertext. */
 int hegmm_ct_level(const hegmm_ct *ct);
 

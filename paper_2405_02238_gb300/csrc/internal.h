@@ -169,6 +169,8 @@ int ntt_inv(Ctx *c, const LimbPat &p);
 // coefficient form, to be forward transformed).
 int modup_conv(Ctx *c, int lv, int n, const u64 *xc, long long xc_stride, const u64 *xn, long long xn_stride,
                u64 *D, long long D_stride);
+int modup_conv_tab(Ctx *c, const ModUpTab &tb, int n, const u64 *xc, long long xc_stride, const u64 *xn,
+                   long long xn_stride, u64 *D, long long D_stride);
 int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot);
 int div_conv(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);

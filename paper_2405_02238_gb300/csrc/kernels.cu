@@ -184,6 +184,15 @@ int modup_conv(Ctx *c, int lv, int n, const u64 *xc, long long xc_stride, const 
     return cuda_check(c, "modup");
 }
 
+// Same conversion with a caller-provided table (laid out as build_modup_tab does).
+int modup_conv_tab(Ctx *c, const ModUpTab &tb, int n, const u64 *xc, long long xc_stride, const u64 *xn,
+                   long long xn_stride, u64 *D, long long D_stride) {
+    Launch t(c, K_MODUP, (double)n * (tb.lv + (double)tb.nd * tb.ne) * c->limb_bytes());
+    k_modup<<<grid_coef(c->N, tb.nd, n), 256, 0, c->st>>>(tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->logN, c->d_mods,
+                                                            tb.d, xc, xc_stride, xn, xn_stride, D, D_stride);
+    return cuda_check(c, "modup");
+}
+
 // ------------------------------------------------------------------ key-switching inner product
 // u[c][e] = sum_j D_j[e][auto_g(.)] * key[j][c][gp(e)], fused with the
 // NTT-domain automorphism of the hoisted digits; 128-bit accumulation, one

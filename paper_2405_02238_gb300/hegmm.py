@@ -74,6 +74,7 @@ _SIGS = {
     "hegmm_decrypt_slots": (ctypes.c_int, [vp, vp, u64p]),
     "hegmm_rotate": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_rotate_many": (ctypes.c_int, [vp, vp, intp, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_rotate_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
     "hegmm_cmult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_add": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_mult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
@@ -272,6 +273,13 @@ class Context:
         outs = (vp * len(zs))()
         self._check(self.lib.hegmm_rotate_many(self.h, ct.h, arr.ctypes.data_as(intp), len(zs), outs), "rotate_many")
         return [Ciphertext(self, vp(outs[i])) for i in range(len(zs))]
+
+    def hegmm_rotate_noalloc(self, ct: "Ciphertext", z: int, out: "Ciphertext") -> "Ciphertext":
+        """Rotation into an existing ciphertext, with no device allocation
+        inside the library (for callers that cannot allocate while running;
+        see include/hegmm.h)."""
+        self._check(self.lib.hegmm_rotate_noalloc(self.h, ct.h, z, out.h), "rotate_noalloc")
+        return out
 
     def hegmm_cmult(self, ct: "Ciphertext", pt: "Plaintext") -> "Ciphertext":
         out = vp()
