@@ -284,13 +284,14 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
             pw[i] = hmul(pw[i - 1], psi, q);
             ipw[i] = hmul(ipw[i - 1], ipsi, q);
         }
+        // [m][0 = forward, 1 = inverse][k] pairs {psi^(+-brev(k)), Shoup companion}
         u64 *T = &tw[(size_t)m * 4 * N];
         for (int k = 0; k < N; k++) {
             const u32 b = brev_bits((u32)k, c->logN);
-            T[k] = pw[b];
-            T[N + k] = shoup(pw[b], q);
-            T[2 * N + k] = ipw[b];
-            T[3 * N + k] = shoup(ipw[b], q);
+            T[2 * k] = pw[b];
+            T[2 * k + 1] = shoup(pw[b], q);
+            T[2 * N + 2 * k] = ipw[b];
+            T[2 * N + 2 * k + 1] = shoup(ipw[b], q);
         }
     }
     c->d_tw = dalloc(c, tw.size());
@@ -731,9 +732,10 @@ void hegmm_ct_destroy(hegmm_ct *ct) {
     delete ct;
 }
 
-static const char *kKernelNames[K_NUM] = {"ntt_fwd",    "ntt_inv",     "modup_conv", "ksw_inner_product",
-                                          "div_conv",   "div_combine", "lt_accumulate", "tensor",
-                                          "sum",        "pointwise",   "sample",     "codec"};
+static const char *kKernelNames[K_NUM] = {"ntt_fwd",     "ntt_inv",      "modup",         "ksw_inner_product",
+                                          "div_conv",    "div_combine",  "divround_ntt",  "lt_accumulate",
+                                          "tensor",      "sum",          "pointwise",     "sample",
+                                          "codec"};
 
 int hegmm_set_timing(hegmm_ctx *h, int enable) {
     if (!h) return HEGMM_EINVAL;

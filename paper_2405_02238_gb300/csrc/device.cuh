@@ -152,6 +152,76 @@ HDI void ntt_inv_group(u64 *sm, int g, int u0, int logN, const u64 *ipsi, const 
     for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
 }
 
+// A twiddle and its Shoup companion, loaded together (one 16-byte load).
+struct alignas(16) TwPair {
+    u64 w, wp;
+};
+
+// a w mod q left in [0, 2q) (Shoup without the final correction).
+HDI u64 mulsh_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi(a, wp) * q; }
+
+// Lazy forward butterflies (Harvey): inputs and outputs in [0, 4q), q < 2^62.
+template <int R>
+HDI void ntt_fwd_group_lazy(u64 *sm, int g, int s0, int logN, const TwPair *tw, u64 q) {
+    const int ltl = logN - s0 - R;
+    const int tl = 1 << ltl;
+    const int B = g >> ltl, o = g & (tl - 1);
+    const int base = (B << (ltl + R)) + o;
+    const u64 q2 = 2 * q;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int half = 1 << (R - 1 - r);
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) {
+            if (k & half) continue;
+            const TwPair t = tw[((1 << s0) << r) + (B << r) + (k >> (R - r))];
+            u64 X = x[k];
+            X = X >= q2 ? X - q2 : X;
+            const u64 T = mulsh_lazy(x[k + half], t.w, t.wp, q);
+            x[k] = X + T;
+            x[k + half] = X - T + q2;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
+}
+
+// Lazy inverse butterflies (Harvey): inputs and outputs in [0, 2q).
+template <int R>
+HDI void ntt_inv_group_lazy(u64 *sm, int g, int u0, int logN, const TwPair *tw, u64 q) {
+    const int tl = 1 << u0;
+    const int B = g >> u0, o = g & (tl - 1);
+    const int base = (B << (u0 + R)) + o;
+    const u64 q2 = 2 * q;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int dist = 1 << r;
+#pragma unroll
+        for (int k = 0; k < (1 << R); k++) {
+            if (k & dist) continue;
+            const TwPair t = tw[(1 << (logN - u0 - r - 1)) + (B << (R - 1 - r)) + (k >> (r + 1))];
+            const u64 U = x[k], V = x[k + dist];
+            u64 X = U + V;
+            x[k] = X >= q2 ? X - q2 : X;
+            x[k + dist] = mulsh_lazy(U - V + q2, t.w, t.wp, q);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
+}
+
+// Reduce a value in [0, 4q) to [0, q).
+HDI u64 reduce4(u64 x, u64 q) {
+    x = x >= 2 * q ? x - 2 * q : x;
+    return x >= q ? x - q : x;
+}
+
 // SplitMix64 (Steele, Lea, Flood 2014) in counter mode.
 constexpr u64 SM_GAMMA = 0x9E3779B97F4A7C15ull;
 

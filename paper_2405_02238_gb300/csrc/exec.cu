@@ -100,8 +100,10 @@ static int modup(Ctx *c, int lv, int n, const u64 *xn, long long xn_stride, u64 
                           cudaMemcpyDeviceToDevice, c->st);
     }
     if ((rc = ntt_inv(c, pat_ct(c, xc, n, lv)))) return rc;
-    if ((rc = modup_conv(c, lv, n, xc, (long long)lv * N, xn, xn_stride, D, (long long)nd * ne * N))) return rc;
-    return ntt_fwd(c, pat_nonown(c, lv, D, n, (long long)nd * ne * N));
+    const ModUpTab *tb = modup_tab(c, lv);
+    if (!tb) return HEGMM_ENOMEM;
+    return modup_ntt(c, *tb, pat_nonown(c, lv, D, n, (long long)nd * ne * N), xc, (long long)lv * N, xn, xn_stride, D,
+                     (long long)nd * ne * N, n);
 }
 
 // Inner product + ModDown for nrot key switches whose descriptors are on
@@ -110,11 +112,10 @@ static int ksw_moddown(Ctx *c, int lv, const RotDesc *d_rots, const DivDesc *d_d
     const DivTab *tb = div_tab(c, lv, 0);
     if (!tb) return HEGMM_ENOMEM;
     int rc;
+    (void)tmp;
     if ((rc = ksw_ip(c, lv, d_rots, nrot))) return rc;
     if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, 2 * nrot)))) return rc;
-    if ((rc = div_conv(c, *tb, d_div, 2 * nrot))) return rc;
-    if ((rc = ntt_fwd(c, pat_ct(c, tmp, 2 * nrot, lv)))) return rc;
-    return div_combine(c, *tb, d_div, 2 * nrot);
+    return divround_ntt(c, *tb, d_div, 2 * nrot);
 }
 
 // ---------------------------------------------------------------- single operations
@@ -223,10 +224,9 @@ static int modswitch_polys(Ctx *c, int lv, u64 *in, int npoly, u64 *tmp, u64 *ou
     pd.off[0] = (unsigned short)(lv - 1);
     pd.mod[0] = (unsigned char)(lv - 1);
     int rc;
+    (void)tmp;
     if ((rc = ntt_inv(c, pd))) return rc;
-    if ((rc = div_conv(c, *tb, d_desc, npoly))) return rc;
-    if ((rc = ntt_fwd(c, pat_ct(c, tmp, npoly, lv - 1)))) return rc;
-    return div_combine(c, *tb, d_desc, npoly);
+    return divround_ntt(c, *tb, d_desc, npoly);
 }
 
 int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out) {

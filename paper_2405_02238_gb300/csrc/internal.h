@@ -83,6 +83,7 @@ enum KernelKind {
     K_KSW_IP,
     K_DIV_CONV,
     K_DIV_COMBINE,
+    K_DIV_NTT,
     K_LT_ACC,
     K_TENSOR,
     K_SUM,
@@ -113,7 +114,7 @@ struct Ctx {
     u64 psi[MAXM]{};
     ModDev hmod[MAXM]{};
     ModDev *d_mods = nullptr;
-    u64 *d_tw = nullptr;  // [nmod][4][N]: psi_rev, shoup, psi_inv_rev, shoup
+    u64 *d_tw = nullptr;  // [nmod][fwd, inv][N] x {psi^(+-brev(k)), Shoup companion}
     cudaStream_t st = nullptr;
     std::string err;
     int nsm = 148;
@@ -172,6 +173,13 @@ int modup_conv(Ctx *c, int lv, int n, const u64 *xc, long long xc_stride, const 
 int modup_conv_tab(Ctx *c, const ModUpTab &tb, int n, const u64 *xc, long long xc_stride, const u64 *xn,
                    long long xn_stride, u64 *D, long long D_stride);
 int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot);
+// Fused ModDown / modulus switch: conversion, forward NTT and combine in one kernel.
+int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
+// Fused ModUp: conversion + forward NTT of every limb outside the digits'
+// own primes (nonown pattern), plus the own limbs copied in NTT form.
+int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, long long xc_stride, const u64 *xn,
+              long long xn_stride, u64 *D, long long D_stride, int n);
+const ModUpTab *modup_tab(Ctx *c, int lv);
 int div_conv(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int lt_accumulate(Ctx *c, int lv, const LtTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout,

@@ -40,8 +40,12 @@ Launch::~Launch() {
 
 // ------------------------------------------------------------------ helpers
 
+// Block b of a pattern launch: blocks are ordered modulus-major (all outers
+// of inner entry 0 first), so consecutive CTAs -- and the CTAs an SM runs
+// one after another -- use the same modulus and its twiddle table stays in L1.
 static __device__ __forceinline__ u64 *pat_ptr(const LimbPat &p, int b, int N, int &mod) {
-    const int outer = b / p.inner, in = b - outer * p.inner;
+    const int nouter = p.count / p.inner;
+    const int in = b / nouter, outer = b - in * nouter;
     u64 *base = p.outer_ptrs ? p.outer_ptrs[outer] : p.base + (long long)outer * p.outer_stride;
     mod = p.mod[in];
     return base + (size_t)p.off[in] * N;
@@ -54,76 +58,266 @@ static inline dim3 grid_coef(int N, int y, int z) { return dim3((unsigned)((N + 
 // passes run three butterfly stages in registers per group of eight
 // elements, so N = 2^14 takes five shared-memory passes.
 
-template <bool INV>
-__global__ void __launch_bounds__(1024) k_ntt(LimbPat p, const ModDev *__restrict__ mods, const u64 *__restrict__ tw,
-                                             int logN) {
+// The ring degree is a template parameter (logN = 10..14), so every pass,
+// stride and twiddle index folds to constants; butterflies are lazy
+// (Harvey): forward values stay in [0, 4q), inverse values in [0, 2q), and
+// are reduced once when the limb leaves shared memory.
+
+// Up to N = 2^13 two CTAs of 512 threads share an SM (registers 2 x 512 x 64,
+// shared memory 2 x 70 KB), so one CTA's loads and barriers overlap the
+// other's butterflies; at N = 2^14 the 139 KB limb allows one CTA per SM.
+template <int LOGN>
+struct NttCfg {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int NT = LOGN >= 14 ? 1024 : ((N / 8) < 512 ? (N / 8) : 512);
+    static constexpr int MINB = LOGN >= 14 ? 1 : 2;
+    static constexpr size_t SMEM = (size_t)(N + N / 16) * 8;
+};
+
+template <int LOGN>
+__device__ __forceinline__ void fwd_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, REM = LOGN % 3;
+#pragma unroll
+    for (int s0 = 0; s0 + 3 <= LOGN; s0 += 3) {
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_fwd_group_lazy<3>(sm, g, s0, LOGN, T, q);
+        __syncthreads();
+    }
+    if constexpr (REM != 0) {
+        for (int g = threadIdx.x; g < (N >> REM); g += NT) ntt_fwd_group_lazy<REM>(sm, g, LOGN - REM, LOGN, T, q);
+        __syncthreads();
+    }
+}
+
+template <int LOGN>
+__device__ __forceinline__ void inv_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, REM = LOGN % 3;
+#pragma unroll
+    for (int u0 = 0; u0 + 3 <= LOGN; u0 += 3) {
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, u0, LOGN, T, q);
+        __syncthreads();
+    }
+    if constexpr (REM != 0) {
+        for (int g = threadIdx.x; g < (N >> REM); g += NT) ntt_inv_group_lazy<REM>(sm, g, LOGN - REM, LOGN, T, q);
+        __syncthreads();
+    }
+}
+
+// Twiddle table layout: [modulus][0 = forward psi^brev(k), 1 = inverse][N] pairs.
+__device__ __forceinline__ const TwPair *tw_of(const TwPair *tw, int mi, int inv, int N) {
+    return tw + ((size_t)mi * 2 + inv) * N;
+}
+
+template <int LOGN, bool INV>
+__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(LimbPat p, const ModDev *__restrict__ mods,
+                                                         const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
-    const int N = 1 << logN;
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
     int mi;
     u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
     const u64 q = mods[mi].q;
-    const u64 *T = tw + (size_t)mi * 4 * N + (INV ? 2 * (size_t)N : 0);
-    for (int i = threadIdx.x * 2; i < N; i += blockDim.x * 2) {
+    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
         ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
         const int pi = pad16(i);
         sm[pi] = v.x;
         sm[pi + 1] = v.y;
     }
     __syncthreads();
-    for (int s0 = 0; s0 < logN;) {
-        const int R = logN - s0 < 3 ? logN - s0 : 3;
-        const int G = N >> R;
-        for (int g = threadIdx.x; g < G; g += blockDim.x) {
-            if (!INV) {
-                if (R == 3) ntt_fwd_group<3>(sm, g, s0, logN, T, T + N, q);
-                else if (R == 2) ntt_fwd_group<2>(sm, g, s0, logN, T, T + N, q);
-                else ntt_fwd_group<1>(sm, g, s0, logN, T, T + N, q);
-            } else {
-                if (R == 3) ntt_inv_group<3>(sm, g, s0, logN, T, T + N, q);
-                else if (R == 2) ntt_inv_group<2>(sm, g, s0, logN, T, T + N, q);
-                else ntt_inv_group<1>(sm, g, s0, logN, T, T + N, q);
-            }
-        }
-        __syncthreads();
-        s0 += R;
-    }
+    if (INV) inv_passes<LOGN>(sm, tw_of(tw, mi, 1, N), q);
+    else fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), q);
     const u64 ninv = mods[mi].ninv, ninv_sh = mods[mi].ninv_sh;
-    for (int i = threadIdx.x * 2; i < N; i += blockDim.x * 2) {
+    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
         const int pi = pad16(i);
         ulonglong2 v;
-        v.x = sm[pi];
-        v.y = sm[pi + 1];
         if (INV) {
-            v.x = mulsh(v.x, ninv, ninv_sh, q);
-            v.y = mulsh(v.y, ninv, ninv_sh, q);
+            v.x = mulsh(sm[pi], ninv, ninv_sh, q);
+            v.y = mulsh(sm[pi + 1], ninv, ninv_sh, q);
+        } else {
+            v.x = reduce4(sm[pi], q);
+            v.y = reduce4(sm[pi + 1], q);
         }
         *reinterpret_cast<ulonglong2 *>(ptr + i) = v;
     }
 }
 
-static size_t ntt_smem(int N) { return (size_t)(N + N / 16) * 8; }
-static int ntt_threads(int N) { return std::min(1024, N / 8); }
+// ModDown / modulus switch, fused: one CTA per (polynomial, kept prime q_i).
+// Prologue: y~_i = sum_k centred([u_k t^-1 (D/d_k)^-1]_{d_k}) (D/d_k) mod q_i
+// from the coefficient-form dropped limbs; forward NTT in shared memory;
+// epilogue: out_i = (u_i - t y~_i) D^-1 (+ add_i at the automorphism's index).
+// Table layout as k_div_conv (build_div_tab).
+template <int LOGN>
+__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divround_ntt(int nkeep, int ndrop, const ModDev *__restrict__ mods,
+                                                                  const u64 *__restrict__ tab,
+                                                                  const DivDesc *__restrict__ desc,
+                                                                  const TwPair *__restrict__ tw) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
+    const int npoly = gridDim.x / nkeep;  // prime-major block order (twiddles stay in L1)
+    const int i = blockIdx.x / npoly, b = blockIdx.x - i * npoly;
+    const DivDesc d = desc[b];
+    const u64 *tA = tab;
+    const u64 *tB = tA + 2 * ndrop;
+    const u64 *tC = tB + (size_t)3 * nkeep * ndrop;
+    const u64 *tI = tC + (size_t)4 * nkeep;
+    const int mi = (int)tI[i];
+    const ModDev M = mods[mi];
+    const u64 *hB = tB + (size_t)i * ndrop * 3;
+    for (int c = threadIdx.x; c < N; c += NT) {
+        u64 acc = 0;
+        for (int k = 0; k < ndrop; k++) {
+            const u64 dk = mods[tI[nkeep + k]].q;
+            const u64 z = mulsh(d.u[(size_t)(nkeep + k) * N + c], __ldg(tA + 2 * k), __ldg(tA + 2 * k + 1), dk);
+            const u64 *h = hB + 3 * k;
+            acc = addm(acc, mulsh(centred(z, dk, __ldg(h + 2), M.q, M.barr), __ldg(h), __ldg(h + 1), M.q), M.q);
+        }
+        sm[pad16(c)] = acc;
+    }
+    __syncthreads();
+    fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), M.q);
+    const u64 *k4 = tC + 4 * i;
+    const u64 Di = k4[0], Dis = k4[1], tq = k4[2], tqs = k4[3];
+    const u64 *ui = d.u + (size_t)i * N;
+    u64 *oi = d.out + (size_t)i * N;
+    for (int c = threadIdx.x; c < N; c += NT) {
+        u64 v = subm(ui[c], mulsh(sm[pad16(c)], tq, tqs, M.q), M.q);
+        v = mulsh(v, Di, Dis, M.q);
+        if (d.add) v = addm(v, d.add[(size_t)i * N + (d.g == 1 ? (u32)c : auto_src((u32)c, d.g, LOGN))], M.q);
+        oi[c] = v;
+    }
+}
+
+// ModUp, fused: one CTA per (input, digit j, prime e outside digit j):
+// prologue computes the digit's centred fast base conversion into prime e
+// from the coefficient-form source limbs, then forward NTT, then store.
+// Limb selection follows a LimbPat whose off[] = j * ne + e.
+template <int LOGN>
+__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha, int L,
+                                                               const ModDev *__restrict__ mods,
+                                                               const u64 *__restrict__ tab, const u64 *__restrict__ xc,
+                                                               long long xc_stride, const TwPair *__restrict__ tw) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
+    const int nouter = p.count / p.inner;  // prime-major block order, as pat_ptr
+    const int in = blockIdx.x / nouter, outer = blockIdx.x - in * nouter;
+    const int off = p.off[in], j = off / ne, e = off - j * ne;
+    const int mi = p.mod[in];
+    u64 *dst = (p.outer_ptrs ? p.outer_ptrs[outer] : p.base + (long long)outer * p.outer_stride) + (size_t)off * N;
+    const u64 *x = xc + outer * xc_stride;
+    const int lo = j * alpha, ns = min(alpha, lv - lo);
+    const ModDev R = mods[mi];
+    const u64 *tinv = tab + (size_t)j * alpha * 2;
+    const u64 *thm = tab + (size_t)nd * alpha * 2 + (size_t)j * alpha * ne * 3;
+    for (int c = threadIdx.x; c < N; c += NT) {
+        u64 acc = 0;
+        for (int ii = 0; ii < ns; ii++) {
+            const u64 sq = mods[lo + ii].q;
+            const u64 y = mulsh(x[(size_t)(lo + ii) * N + c], __ldg(tinv + 2 * ii), __ldg(tinv + 2 * ii + 1), sq);
+            const u64 *h = thm + ((size_t)ii * ne + e) * 3;
+            acc = addm(acc, mulsh(centred(y, sq, __ldg(h + 2), R.q, R.barr), __ldg(h), __ldg(h + 1), R.q), R.q);
+        }
+        sm[pad16(c)] = acc;
+    }
+    __syncthreads();
+    fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), R.q);
+    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
+        const int pi = pad16(i);
+        ulonglong2 v;
+        v.x = reduce4(sm[pi], R.q);
+        v.y = reduce4(sm[pi + 1], R.q);
+        *reinterpret_cast<ulonglong2 *>(dst + i) = v;
+    }
+}
+
+// The digits' own limbs: D_j = x on the primes of digit j (NTT form copy).
+__global__ void k_modup_own(int lv, int ne, int alpha, int logN, const u64 *__restrict__ xn, long long xn_stride,
+                            u64 *__restrict__ D, long long D_stride) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int e = blockIdx.y, o = blockIdx.z, j = e / alpha;
+    D[o * D_stride + ((size_t)j * ne + e) * N + c] = xn[o * xn_stride + (size_t)e * N + c];
+}
+
+template <int LOGN>
+static int set_smem_attrs() {
+    const int sm = (int)NttCfg<LOGN>::SMEM;
+    if (cudaFuncSetAttribute(k_ntt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ntt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_divround_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_modup_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+        return 1;
+    return 0;
+}
 
 int init_kernels(Ctx *c) {
-    size_t sm = ntt_smem(c->N);
-    if (cudaFuncSetAttribute(k_ntt<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
-        return cuda_check(c, "ntt smem attribute");
+    int bad = 0;
+    switch (c->logN) {
+        case 10: bad = set_smem_attrs<10>(); break;
+        case 11: bad = set_smem_attrs<11>(); break;
+        case 12: bad = set_smem_attrs<12>(); break;
+        case 13: bad = set_smem_attrs<13>(); break;
+        case 14: bad = set_smem_attrs<14>(); break;
+        default: return set_err(c, HEGMM_EINVAL, "unsupported ring degree");
+    }
+    if (bad) return cuda_check(c, "ntt shared-memory attribute");
     return HEGMM_OK;
 }
+
+#define HG_DISPATCH_LOGN(logN, KERNEL_CALL) \
+    switch (logN) {                         \
+        case 10: { constexpr int LG = 10; KERNEL_CALL; } break; \
+        case 11: { constexpr int LG = 11; KERNEL_CALL; } break; \
+        case 12: { constexpr int LG = 12; KERNEL_CALL; } break; \
+        case 13: { constexpr int LG = 13; KERNEL_CALL; } break; \
+        case 14: { constexpr int LG = 14; KERNEL_CALL; } break; \
+        default: break;                     \
+    }
 
 int ntt_fwd(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes());
-    k_ntt<false><<<p.count, ntt_threads(c->N), ntt_smem(c->N), c->st>>>(p, c->d_mods, c->d_tw, c->logN);
+    const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
+    HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, false><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
     return cuda_check(c, "ntt_fwd");
 }
 
 int ntt_inv(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes());
-    k_ntt<true><<<p.count, ntt_threads(c->N), ntt_smem(c->N), c->st>>>(p, c->d_mods, c->d_tw, c->logN);
+    const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
+    HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, true><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
     return cuda_check(c, "ntt_inv");
+}
+
+int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    // algorithmic bytes: drop limbs + u_i + add_i read, out_i written, per kept limb
+    Launch t(c, K_DIV_NTT, (double)npoly * tab.nkeep * (tab.ndrop + 3.0) * c->limb_bytes());
+    const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
+    const int grid = npoly * tab.nkeep;
+    HG_DISPATCH_LOGN(c->logN, (k_divround_ntt<LG><<<grid, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
+                                  tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw)));
+    return cuda_check(c, "divround_ntt");
+}
+
+int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, long long xc_stride, const u64 *xn,
+              long long xn_stride, u64 *D, long long D_stride, int n) {
+    Launch t(c, K_MODUP, (double)n * (tb.lv + 2.0 * (tb.nd * tb.ne)) * c->limb_bytes());
+    const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
+    if (nonown.count > 0)
+        HG_DISPATCH_LOGN(c->logN, (k_modup_ntt<LG><<<nonown.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
+                                      nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods, tb.d, xc, xc_stride, tw)));
+    k_modup_own<<<grid_coef(c->N, tb.lv, n), 256, 0, c->st>>>(tb.lv, tb.ne, c->alpha, c->logN, xn, xn_stride, D,
+                                                              D_stride);
+    return cuda_check(c, "modup_ntt");
+}
+
+const ModUpTab *modup_tab(Ctx *c, int lv) {
+    auto it = c->modup.find(lv);
+    if (it == c->modup.end()) {
+        if (build_modup_tab(c, lv)) return nullptr;
+        it = c->modup.find(lv);
+    }
+    return &it->second;
 }
 
 // ------------------------------------------------------------------ ModUp
@@ -198,26 +392,42 @@ int modup_conv_tab(Ctx *c, const ModUpTab &tb, int n, const u64 *xc, long long x
 // NTT-domain automorphism of the hoisted digits; 128-bit accumulation, one
 // Montgomery reduction (keys are stored times 2^64).
 
-__global__ void k_ksw_ip(int lv, int ne, int nd, int np, int L, int logN, const ModDev *__restrict__ mods,
-                         const RotDesc *__restrict__ rots) {
+// Each thread computes two adjacent coefficients: the key is streamed with
+// 16-byte loads, the digits are gathered at the automorphism's indices
+// (they are L2-resident: one hoisted ModUp serves every rotation).
+__global__ void __launch_bounds__(256) k_ksw_ip(int lv, int ne, int nd, int np, int L, int logN,
+                                                const ModDev *__restrict__ mods, const RotDesc *__restrict__ rots) {
     const int N = 1 << logN;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
     const int e = blockIdx.y;
     const RotDesc d = rots[blockIdx.z];
     const int gm = e < lv ? e : L + (e - lv);
     const u64 q = mods[gm].q, qinv = mods[gm].qinv;
-    const u32 src = d.g == 1 ? (u32)c : auto_src((u32)c, d.g, logN);
-    Acc a0{0, 0}, a1{0, 0};
+    const u32 s0 = d.g == 1 ? (u32)c : auto_src((u32)c, d.g, logN);
+    const u32 s1 = d.g == 1 ? (u32)c + 1 : auto_src((u32)c + 1, d.g, logN);
+    const u64 *Dp = d.D + (size_t)e * N;
+    const u64 *Kp = d.key + (size_t)gm * N + c;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N;
+    Acc a00{0, 0}, a01{0, 0}, a10{0, 0}, a11{0, 0};
+#pragma unroll 4
     for (int j = 0; j < nd; j++) {
-        const u64 x = d.D[((size_t)j * ne + e) * N + src];
-        const u64 k0 = d.key[(((size_t)j * 2 + 0) * np + gm) * N + c];
-        const u64 k1 = d.key[(((size_t)j * 2 + 1) * np + gm) * N + c];
-        mac(a0, x, k0);
-        mac(a1, x, k1);
+        const u64 x0 = __ldg(Dp + (size_t)j * dstep + s0);
+        const u64 x1 = __ldg(Dp + (size_t)j * dstep + s1);
+        const ulonglong2 k0 = __ldcs(reinterpret_cast<const ulonglong2 *>(Kp + (size_t)(2 * j) * kstep));
+        const ulonglong2 k1 = __ldcs(reinterpret_cast<const ulonglong2 *>(Kp + (size_t)(2 * j + 1) * kstep));
+        mac(a00, x0, k0.x);
+        mac(a01, x1, k0.y);
+        mac(a10, x0, k1.x);
+        mac(a11, x1, k1.y);
     }
-    d.u[(size_t)e * N + c] = montred(a0, q, qinv);
-    d.u[((size_t)ne + e) * N + c] = montred(a1, q, qinv);
+    ulonglong2 o0, o1;
+    o0.x = montred(a00, q, qinv);
+    o0.y = montred(a01, q, qinv);
+    o1.x = montred(a10, q, qinv);
+    o1.y = montred(a11, q, qinv);
+    *reinterpret_cast<ulonglong2 *>(d.u + (size_t)e * N + c) = o0;
+    *reinterpret_cast<ulonglong2 *>(d.u + ((size_t)ne + e) * N + c) = o1;
 }
 
 int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
@@ -225,7 +435,7 @@ int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
     const int ne = lv + c->K, nd = c->digits(lv);
     // algorithmic bytes: key (2 nd ne limbs) + digits read + u written
     Launch t(c, K_KSW_IP, (double)nrot * (2.0 * nd * ne + nd * ne + 2.0 * ne) * c->limb_bytes());
-    k_ksw_ip<<<grid_coef(c->N, ne, nrot), 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots);
+    k_ksw_ip<<<grid_coef(c->N / 2, ne, nrot), 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots);
     return cuda_check(c, "ksw_ip");
 }
 
