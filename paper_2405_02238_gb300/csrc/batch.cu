@@ -1,0 +1,641 @@
+// batch.cu -- HEGMM products (Algorithms 1 and 2 of arXiv 2405.02238), one
+// or many per call, executed as flattened work lists.
+//
+// A BatchPlan covers an ordered list of products (shapes may differ).  Every
+// stage of the method is one kernel launch over the flattened work items of
+// all products in the batch:
+//   1. gather the operands; one hoisted ModUp of c1 for every operand;
+//   2. every distinct rotation offset of every operand is key-switched once
+//      (the linear transformations eps^k / omega^k of all iterations of a
+//      product share their source ciphertext, so Rot(ct, d) is reused
+//      bit-identically across k), in chunks of (product, operand, offset)
+//      items: key inner product fused with the NTT-domain automorphism, then
+//      the fused ModDown; after each chunk one launch applies the masks u_d
+//      (Eq. lintrans) and accumulates every eps^k(A) / omega^k(B) output the
+//      chunk contributes to;
+//   3. optional modulus switch of all outputs;
+//   4. in chunks of (product, iteration) items: tensor, hoisted ModUp of d2,
+//      inner product with the relinearisation key, ModDown with d0 / d1 added,
+//      and the sum into each product's accumulator (HE-Mult and HE-Add of
+//      Algorithm 1 lines 5-9 / Algorithm 2 lines 19-28);
+//   5. Algorithm 2: one hoisted ModUp of each accumulator and its t-1
+//      extraction rotations by h p, summed into the caller's result.
+// Masks are encoded once per shape; descriptors once per batch composition
+// (plans are cached, least recently used evicted beyond a memory budget).
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <map>
+#include <set>
+#include <tuple>
+
+#include "device.cuh"
+#include "internal.h"
+#include "plan.h"
+
+namespace hg {
+
+struct ShapeData {
+    HostPlan hp;
+    std::vector<long long> zs[2];
+    std::map<long long, int> zidx[2];
+    std::map<std::vector<int>, int> mask_of;
+    u64 *masks = nullptr;
+    int nmask = 0;
+    hegmm_opcount cnt{};
+    const u64 *mask_ptr(Ctx *c, const std::vector<int> &dst) const {
+        return masks + (size_t)mask_of.at(dst) * c->L * c->N;
+    }
+};
+
+struct RotChunk {
+    int cnt = 0, nout = 0;
+    RotDesc *d_rots = nullptr;
+    DivDesc *d_div = nullptr;
+    LtTerm *d_terms = nullptr;
+    int *d_off = nullptr;
+    u64 **d_outs = nullptr;
+};
+
+struct RelinChunk {
+    int cnt = 0, nsum = 0;
+    Tensor3 *d_tens = nullptr;
+    RotDesc *d_rot = nullptr;
+    DivDesc *d_div = nullptr;
+    SumDesc *d_sum = nullptr;
+};
+
+struct BatchPlan {
+    std::vector<ShapeData *> shp;
+    int B = 0, lv0 = 0, lv1 = 0, O = 0, E = 0, X = 0;
+    size_t ws_bytes = 0;
+    u64 *ws = nullptr;
+    u64 *in = nullptr, *xc = nullptr, *D = nullptr, *u = nullptr, *rot = nullptr, *outs = nullptr, *ms = nullptr;
+    u64 *d3 = nullptr, *rxc = nullptr, *rD = nullptr, *ru = nullptr, *rout = nullptr, *cacc = nullptr;
+    u64 *exc = nullptr, *eD = nullptr, *eu = nullptr, *erot = nullptr;
+    LtTerm *d_id_terms = nullptr;
+    int *d_id_off = nullptr;
+    u64 **d_all_outs = nullptr;
+    std::vector<RotChunk> rchunks;
+    DivDesc *d_msdiv = nullptr;
+    std::vector<RelinChunk> lchunks;
+    RotDesc *d_erot = nullptr;
+    DivDesc *d_ediv = nullptr;
+    std::vector<SumDesc> final_tmpl;
+    SumDesc *d_final = nullptr;
+    u64 **d_inptr = nullptr;
+    hegmm_opcount cnt{};
+    std::vector<void *> allocs;
+    unsigned long long last_use = 0;
+};
+
+static void free_bplan(Ctx *c, BatchPlan *P) {
+    for (void *a : P->allocs) dfree(c, a);
+    delete P;
+}
+
+void free_plans(Ctx *c) {
+    for (auto &kv : c->bplans) free_bplan(c, kv.second);
+    c->bplans.clear();
+    c->bplan_bytes = 0;
+    for (auto &kv : c->shapes) {
+        dfree(c, kv.second->masks);
+        delete kv.second;
+    }
+    c->shapes.clear();
+}
+
+// Encode 0/1 masks (value `scale` on the listed slots) into Montgomery NTT
+// form over q_0..q_{lv-1}: out [count][lv][N].
+static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int> *> &dsts, u64 scale, u64 *out) {
+    const int N = c->N;
+    const int Bm = 256;
+    u64 *m = dalloc(c, (size_t)Bm * N);
+    if (!m) return set_err(c, HEGMM_ENOMEM, "mask encode");
+    if (!c->d_slot_pos0) {
+        c->d_slot_pos0 = upload(c, c->slot_pos0);
+        if (!c->d_slot_pos0) return set_err(c, HEGMM_ENOMEM, "slot table");
+    }
+    int rc;
+    for (size_t b0 = 0; b0 < dsts.size(); b0 += Bm) {
+        const int nb = (int)std::min<size_t>(Bm, dsts.size() - b0);
+        // slot lists of this group of masks (CSR), scattered on the device
+        std::vector<int> off{0}, slots;
+        for (int b = 0; b < nb; b++) {
+            slots.insert(slots.end(), dsts[b0 + b]->begin(), dsts[b0 + b]->end());
+            off.push_back((int)slots.size());
+        }
+        int *d_off = upload(c, off), *d_slots = upload(c, slots);
+        if (!d_off || !d_slots) return set_err(c, HEGMM_ENOMEM, "mask encode");
+        cudaMemsetAsync(m, 0, (size_t)nb * N * 8, c->st);
+        if ((rc = scatter_slots(c, d_off, d_slots, nb, scale, m))) return rc;
+        dfree(c, d_off);
+        dfree(c, d_slots);
+        LimbPat pm{};
+        pm.base = m;
+        pm.outer_stride = N;
+        pm.inner = 1;
+        pm.count = nb;
+        pm.mod[0] = (unsigned char)c->tmod;
+        u64 *o = out + b0 * lv * N;
+        if ((rc = ntt_inv(c, pm))) return rc;
+        if ((rc = lift_from_t(c, lv, m, o, nb))) return rc;
+        LimbPat pq = pat_ct(c, o, nb, lv);
+        if ((rc = ntt_fwd(c, pq))) return rc;
+        if ((rc = pw_to_mont(c, pq))) return rc;
+    }
+    dfree(c, m);
+    return cuda_check(c, "mask encode");
+}
+
+static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
+    auto key = std::make_tuple(m, l, n, alg);
+    auto it = c->shapes.find(key);
+    if (it != c->shapes.end()) {
+        *out = it->second;
+        return HEGMM_OK;
+    }
+    const int S = c->S;
+    ShapeData *sd = new ShapeData;
+    sd->hp = make_host_plan(m, l, n, alg);
+    const HostPlan &hp = sd->hp;
+    for (int s = 0; s < 2; s++) {
+        std::set<long long> zs;
+        for (auto &it2 : hp.iters)
+            for (auto &d : (s == 0 ? it2.eps : it2.omg)) {
+                long long z = ((long long)d.d % S + S) % S;
+                if (z) zs.insert(z);
+            }
+        for (long long z : zs) {
+            sd->zidx[s][z] = (int)sd->zs[s].size();
+            sd->zs[s].push_back(z);
+        }
+    }
+    auto fail = [&](int code, const char *msg) {
+        delete sd;
+        return set_err(c, code, msg);
+    };
+    for (int s = 0; s < 2; s++)
+        for (long long z : sd->zs[s])
+            if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+    for (int z : hp.extract)
+        if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
+    if (!c->keys.count(0)) return fail(HEGMM_ENOKEY, "no relinearisation key");
+    // masks: one per distinct slot set; value = product of the dropped primes mod t
+    u64 scale = 1;
+    for (int i = 0; i < c->prm.ms_drop; i++) scale = (u64)((unsigned __int128)scale * (c->q[c->L - 1 - i] % c->t) % c->t);
+    std::vector<const std::vector<int> *> mlist;
+    for (auto &it2 : hp.iters)
+        for (int s = 0; s < 2; s++)
+            for (auto &d : (s == 0 ? it2.eps : it2.omg))
+                if (!sd->mask_of.count(d.dst)) {
+                    sd->mask_of[d.dst] = (int)mlist.size();
+                    mlist.push_back(&sd->mask_of.find(d.dst)->first);
+                }
+    sd->nmask = (int)mlist.size();
+    sd->masks = dalloc(c, (size_t)sd->nmask * c->L * c->N);
+    if (!sd->masks) return fail(HEGMM_ENOMEM, "plan masks");
+    int rc = encode_masks(c, c->L, mlist, scale, sd->masks);
+    if (rc) {
+        dfree(c, sd->masks);
+        delete sd;
+        return rc;
+    }
+    const long long ni = (long long)hp.iters.size(), ne = (long long)hp.extract.size();
+    hegmm_opcount &ct = sd->cnt;
+    ct.rot = hp.paper_rot();
+    ct.cmult = hp.paper_cmult();
+    ct.mult = ni;
+    ct.relin = ni;
+    ct.extract = ne;
+    ct.add = ct.cmult - 2 * ni + (ni - 1) + ne;
+    ct.ksw = (long long)sd->zs[0].size() + (long long)sd->zs[1].size() + ni + ne;
+    ct.modup = 2 + ni + (ne > 0 ? 1 : 0);
+    ct.modswitch = c->prm.ms_drop ? 2 * ni : 0;
+    c->shapes[key] = sd;
+    *out = sd;
+    return HEGMM_OK;
+}
+
+static void add_counts(hegmm_opcount &a, const hegmm_opcount &b) {
+    a.rot += b.rot;
+    a.cmult += b.cmult;
+    a.add += b.add;
+    a.mult += b.mult;
+    a.relin += b.relin;
+    a.extract += b.extract;
+    a.ksw += b.ksw;
+    a.modup += b.modup;
+    a.modswitch += b.modswitch;
+}
+
+// shapes: B entries of (m, l, n, resolved alg)
+static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, BatchPlan **out) {
+    const int N = c->N;
+    BatchPlan *P = new BatchPlan;
+    auto fail_rc = [&](int rc) {
+        free_bplan(c, P);
+        return rc;
+    };
+    P->B = (int)shapes.size();
+    for (auto &s : shapes) {
+        ShapeData *sd;
+        int rc = get_shape(c, s[0], s[1], s[2], s[3], &sd);
+        if (rc) return fail_rc(rc);
+        P->shp.push_back(sd);
+        add_counts(P->cnt, sd->cnt);
+    }
+    const int B = P->B;
+    const int lv0 = c->L, lv1 = c->L - c->prm.ms_drop;
+    P->lv0 = lv0;
+    P->lv1 = lv1;
+    const int ne0 = lv0 + c->K, nd0 = c->digits(lv0), ne1 = lv1 + c->K, nd1 = c->digits(lv1);
+    // output indexing, accumulator slots (products with extraction first)
+    std::vector<int> obase(B), niter(B), next(B), cslot(B), xfirst(B, 0);
+    int O = 0, E = 0, X = 0;
+    for (int p = 0; p < B; p++) {
+        niter[p] = (int)P->shp[p]->hp.iters.size();
+        next[p] = (int)P->shp[p]->hp.extract.size();
+        obase[p] = O;
+        O += 2 * niter[p];
+        if (next[p] > 0) E++;
+    }
+    {
+        int e = 0, f = E;
+        for (int p = 0; p < B; p++) cslot[p] = next[p] > 0 ? e++ : f++;
+        for (int p = 0; p < B; p++)
+            if (next[p] > 0) {
+                xfirst[p] = X;
+                X += next[p];
+            }
+    }
+    P->O = O;
+    P->E = E;
+    P->X = X;
+    // rotation items (p, s, zi) and relinearisation items (p, k)
+    struct RItem {
+        int p, s, zi;
+    };
+    std::vector<RItem> ritems;
+    for (int p = 0; p < B; p++)
+        for (int s = 0; s < 2; s++)
+            for (int zi = 0; zi < (int)P->shp[p]->zs[s].size(); zi++) ritems.push_back({p, s, zi});
+    std::vector<std::pair<int, int>> litems;
+    for (int p = 0; p < B; p++)
+        for (int k = 0; k < niter[p]; k++) litems.push_back({p, k});
+    const int R = (int)ritems.size(), I = (int)litems.size();
+    const size_t per_rot = (size_t)(2 * ne0 + 2 * lv0) * N * 8;
+    const size_t per_item = (size_t)(4 * lv1 + nd1 * ne1 + 2 * ne1 + 2 * lv1) * N * 8;
+    const int RC = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(R, 1), c->ws_budget / per_rot));
+    const int RK = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(I, 1), c->ws_budget / per_item));
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t w) {
+        size_t o = off;
+        off += (w + 31) & ~(size_t)31;
+        return o;
+    };
+    const size_t o_in = take((size_t)B * 4 * lv0 * N), o_xc = take((size_t)2 * B * lv0 * N),
+                 o_D = take((size_t)2 * B * nd0 * ne0 * N), o_u = take((size_t)RC * 2 * ne0 * N),
+                 o_rot = take((size_t)RC * 2 * lv0 * N), o_outs = take((size_t)O * 2 * lv0 * N),
+                 o_ms = lv1 != lv0 ? take((size_t)O * 2 * lv1 * N) : 0, o_d3 = take((size_t)RK * 3 * lv1 * N),
+                 o_rxc = take((size_t)RK * lv1 * N), o_rD = take((size_t)RK * nd1 * ne1 * N),
+                 o_ru = take((size_t)RK * 2 * ne1 * N), o_rout = take((size_t)RK * 2 * lv1 * N),
+                 o_cacc = take((size_t)B * 2 * lv1 * N), o_exc = take((size_t)std::max(E, 1) * lv1 * N),
+                 o_eD = take((size_t)std::max(E, 1) * nd1 * ne1 * N), o_eu = take((size_t)std::max(X, 1) * 2 * ne1 * N),
+                 o_erot = take((size_t)std::max(X, 1) * 2 * lv1 * N);
+    P->ws_bytes = off * 8;
+    P->ws = dalloc(c, off);
+    if (!P->ws) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch workspace"));
+    P->allocs.push_back(P->ws);
+    u64 *W = P->ws;
+    P->in = W + o_in;
+    P->xc = W + o_xc;
+    P->D = W + o_D;
+    P->u = W + o_u;
+    P->rot = W + o_rot;
+    P->outs = W + o_outs;
+    P->ms = lv1 != lv0 ? W + o_ms : nullptr;
+    P->d3 = W + o_d3;
+    P->rxc = W + o_rxc;
+    P->rD = W + o_rD;
+    P->ru = W + o_ru;
+    P->rout = W + o_rout;
+    P->cacc = W + o_cacc;
+    P->exc = W + o_exc;
+    P->eD = W + o_eD;
+    P->eu = W + o_eu;
+    P->erot = W + o_erot;
+    auto in_ct = [&](int p, int s) { return P->in + ((size_t)2 * p + s) * 2 * lv0 * N; };
+    auto out_ct = [&](int p, int s, int k) { return P->outs + ((size_t)obase[p] + s * niter[p] + k) * 2 * lv0 * N; };
+    auto keep = [&](void *ptr) {
+        if (!ptr) return false;
+        P->allocs.push_back(ptr);
+        return true;
+    };
+    // identity (d = 0) terms over all outputs; this launch also zero-initialises
+    {
+        std::vector<LtTerm> terms;
+        std::vector<int> offs{0};
+        std::vector<u64 *> outs;
+        for (int p = 0; p < B; p++) {
+            const ShapeData *sd = P->shp[p];
+            for (int s = 0; s < 2; s++)
+                for (int k = 0; k < niter[p]; k++) {
+                    for (auto &d : (s == 0 ? sd->hp.iters[k].eps : sd->hp.iters[k].omg))
+                        if (((long long)d.d % c->S) == 0) terms.push_back({in_ct(p, s), sd->mask_ptr(c, d.dst)});
+                    offs.push_back((int)terms.size());
+                    outs.push_back(out_ct(p, s, k));
+                }
+        }
+        P->d_id_terms = upload(c, terms);
+        P->d_id_off = upload(c, offs);
+        P->d_all_outs = upload(c, outs);
+        if (!keep(P->d_id_terms) || !keep(P->d_id_off) || !keep(P->d_all_outs))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
+    // rotation chunks
+    for (int r0 = 0; r0 < R; r0 += RC) {
+        RotChunk ch;
+        ch.cnt = std::min(RC, R - r0);
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        std::map<std::tuple<int, int, int>, int> slot;  // (p, s, zi) -> local slot
+        for (int r = 0; r < ch.cnt; r++) {
+            const RItem &it = ritems[r0 + r];
+            const u64 g = galois_of(c, P->shp[it.p]->zs[it.s][it.zi]);
+            slot[std::make_tuple(it.p, it.s, it.zi)] = r;
+            rd.push_back({P->D + ((size_t)2 * it.p + it.s) * nd0 * ne0 * N, c->keys[g], P->u + (size_t)r * 2 * ne0 * N,
+                          (u32)g, 0u});
+            for (int comp = 0; comp < 2; comp++) {
+                DivDesc v{};
+                v.u = P->u + ((size_t)2 * r + comp) * ne0 * N;
+                v.out = P->rot + ((size_t)2 * r + comp) * lv0 * N;
+                v.add = comp == 0 ? in_ct(it.p, it.s) : nullptr;
+                v.g = (u32)g;
+                dd.push_back(v);
+            }
+        }
+        // terms of the outputs this chunk contributes to
+        std::vector<LtTerm> terms;
+        std::vector<int> offs{0};
+        std::vector<u64 *> outs;
+        const int p_lo = ritems[r0].p, p_hi = ritems[r0 + ch.cnt - 1].p;
+        for (int p = p_lo; p <= p_hi; p++) {
+            const ShapeData *sd = P->shp[p];
+            for (int s = 0; s < 2; s++)
+                for (int k = 0; k < niter[p]; k++) {
+                    const size_t t0 = terms.size();
+                    for (auto &d : (s == 0 ? sd->hp.iters[k].eps : sd->hp.iters[k].omg)) {
+                        const long long z = ((long long)d.d % c->S + c->S) % c->S;
+                        if (!z) continue;
+                        auto f = slot.find(std::make_tuple(p, s, sd->zidx[s].at(z)));
+                        if (f == slot.end()) continue;
+                        terms.push_back({P->rot + (size_t)f->second * 2 * lv0 * N, sd->mask_ptr(c, d.dst)});
+                    }
+                    if (terms.size() > t0) {
+                        offs.push_back((int)terms.size());
+                        outs.push_back(out_ct(p, s, k));
+                    }
+                }
+        }
+        ch.nout = (int)outs.size();
+        ch.d_rots = upload(c, rd);
+        ch.d_div = upload(c, dd);
+        ch.d_terms = upload(c, terms);
+        ch.d_off = upload(c, offs);
+        ch.d_outs = upload(c, outs);
+        if (!keep(ch.d_rots) || !keep(ch.d_div) || !keep(ch.d_terms) || !keep(ch.d_off) || !keep(ch.d_outs))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        P->rchunks.push_back(ch);
+    }
+    // modulus switch of all 2 O polynomials
+    if (lv1 != lv0) {
+        std::vector<DivDesc> dd((size_t)2 * O);
+        for (int b = 0; b < 2 * O; b++) {
+            dd[b] = DivDesc{};
+            dd[b].u = P->outs + (size_t)b * lv0 * N;
+            dd[b].out = P->ms + (size_t)b * lv1 * N;
+            dd[b].g = 1;
+        }
+        P->d_msdiv = upload(c, dd);
+        if (!keep(P->d_msdiv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
+    // tensor + relinearisation chunks
+    const u64 *A1 = lv1 != lv0 ? P->ms : P->outs;
+    const u64 *rlk = c->keys[0];
+    for (int i0 = 0; i0 < I; i0 += RK) {
+        RelinChunk ch;
+        ch.cnt = std::min(RK, I - i0);
+        std::vector<Tensor3> tv;
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        std::vector<SumDesc> sv;
+        for (int r = 0; r < ch.cnt; r++) {
+            const int p = litems[i0 + r].first, k = litems[i0 + r].second;
+            const u64 *a = A1 + ((size_t)obase[p] + k) * 2 * lv1 * N;
+            const u64 *b = A1 + ((size_t)obase[p] + niter[p] + k) * 2 * lv1 * N;
+            u64 *d = P->d3 + (size_t)r * 3 * lv1 * N;
+            tv.push_back({a, b, d});
+            rd.push_back({P->rD + (size_t)r * nd1 * ne1 * N, rlk, P->ru + (size_t)r * 2 * ne1 * N, 1u, 0u});
+            for (int comp = 0; comp < 2; comp++) {
+                DivDesc v{};
+                v.u = P->ru + ((size_t)2 * r + comp) * ne1 * N;
+                v.out = P->rout + ((size_t)2 * r + comp) * lv1 * N;
+                v.add = d + (size_t)comp * lv1 * N;
+                v.g = 1;
+                dd.push_back(v);
+            }
+            if (sv.empty() || litems[i0 + r - 1].first != p || r == 0) {
+                SumDesc s{};
+                s.out = P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
+                s.init = nullptr;
+                s.items = P->rout + (size_t)r * 2 * lv1 * N;
+                s.stride = (long long)2 * lv1 * N;
+                s.count = 0;
+                sv.push_back(s);
+            }
+            sv.back().count++;
+        }
+        ch.nsum = (int)sv.size();
+        ch.d_tens = upload(c, tv);
+        ch.d_rot = upload(c, rd);
+        ch.d_div = upload(c, dd);
+        ch.d_sum = upload(c, sv);
+        if (!keep(ch.d_tens) || !keep(ch.d_rot) || !keep(ch.d_div) || !keep(ch.d_sum))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        P->lchunks.push_back(ch);
+    }
+    // extraction rotations (Algorithm 2)
+    if (X > 0) {
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        for (int p = 0; p < B; p++) {
+            if (!next[p]) continue;
+            const int e = cslot[p];
+            for (int h = 0; h < next[p]; h++) {
+                const int x = xfirst[p] + h;
+                const u64 g = galois_of(c, P->shp[p]->hp.extract[h]);
+                rd.push_back({P->eD + (size_t)e * nd1 * ne1 * N, c->keys[g], P->eu + (size_t)x * 2 * ne1 * N, (u32)g, 0u});
+                for (int comp = 0; comp < 2; comp++) {
+                    DivDesc v{};
+                    v.u = P->eu + ((size_t)2 * x + comp) * ne1 * N;
+                    v.out = P->erot + ((size_t)2 * x + comp) * lv1 * N;
+                    v.add = comp == 0 ? P->cacc + (size_t)e * 2 * lv1 * N : nullptr;
+                    v.g = (u32)g;
+                    dd.push_back(v);
+                }
+            }
+        }
+        P->d_erot = upload(c, rd);
+        P->d_ediv = upload(c, dd);
+        if (!keep(P->d_erot) || !keep(P->d_ediv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
+    // final sums (the caller's result pointers are filled in per call)
+    for (int p = 0; p < B; p++) {
+        SumDesc s{};
+        s.init = P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
+        s.items = next[p] ? P->erot + (size_t)xfirst[p] * 2 * lv1 * N : s.init;
+        s.stride = (long long)2 * lv1 * N;
+        s.count = next[p];
+        P->final_tmpl.push_back(s);
+    }
+    void *df = nullptr, *dp = nullptr;
+    if (cudaMallocAsync(&df, sizeof(SumDesc) * B, c->st) != cudaSuccess ||
+        cudaMallocAsync(&dp, sizeof(u64 *) * 2 * B, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
+    P->d_final = (SumDesc *)df;
+    P->d_inptr = (u64 **)dp;
+    keep(df);
+    keep(dp);
+    int rc = cuda_check(c, "batch plan");
+    if (rc) return fail_rc(rc);
+    *out = P;
+    return HEGMM_OK;
+}
+
+static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm_ct *const *Bc, hegmm_ct **C) {
+    const int N = c->N, B = P->B, lv0 = P->lv0, lv1 = P->lv1;
+    int rc;
+    // 1. operands and the hoisted ModUp of every c1
+    std::vector<u64 *> ptrs((size_t)2 * B);
+    for (int p = 0; p < B; p++) {
+        ptrs[2 * p] = A[p]->d;
+        ptrs[2 * p + 1] = Bc[p]->d;
+    }
+    cudaMemcpyAsync(P->d_inptr, ptrs.data(), ptrs.size() * sizeof(u64 *), cudaMemcpyHostToDevice, c->st);
+    if ((rc = gather_cts(c, lv0, P->d_inptr, 2 * B, P->in))) return rc;
+    if ((rc = modup(c, lv0, 2 * B, P->in + (size_t)lv0 * N, (long long)2 * lv0 * N, P->xc, P->D))) return rc;
+    // 2. linear transformations eps^k(A), omega^k(B) of every iteration
+    if ((rc = lt_accumulate(c, lv0, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) return rc;
+    for (auto &ch : P->rchunks) {
+        if ((rc = ksw_moddown(c, lv0, ch.d_rots, ch.d_div, ch.cnt, P->u, nullptr))) return rc;
+        if ((rc = lt_accumulate(c, lv0, ch.d_terms, ch.d_off, ch.d_outs, ch.nout, 1))) return rc;
+    }
+    // 3. modulus switch (only for chains that drop a prime before products)
+    if (lv1 != lv0)
+        if ((rc = modswitch_polys(c, lv0, P->outs, 2 * P->O, nullptr, P->ms, P->d_msdiv))) return rc;
+    // 4. HE-Mult of every iteration and the sum per product
+    cudaMemsetAsync(P->cacc, 0, (size_t)B * 2 * lv1 * N * 8, c->st);
+    for (auto &ch : P->lchunks) {
+        if ((rc = tensor(c, lv1, ch.d_tens, ch.cnt))) return rc;
+        if ((rc = modup(c, lv1, ch.cnt, P->d3 + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->rxc, P->rD))) return rc;
+        if ((rc = ksw_moddown(c, lv1, ch.d_rot, ch.d_div, ch.cnt, P->ru, nullptr))) return rc;
+        if ((rc = sum_desc(c, lv1, ch.d_sum, ch.nsum))) return rc;
+    }
+    // 5. Algorithm 2 extraction, and the results
+    if (P->X > 0) {
+        if ((rc = modup(c, lv1, P->E, P->cacc + (size_t)lv1 * N, (long long)2 * lv1 * N, P->exc, P->eD))) return rc;
+        if ((rc = ksw_moddown(c, lv1, P->d_erot, P->d_ediv, P->X, P->eu, nullptr))) return rc;
+    }
+    std::vector<SumDesc> fin = P->final_tmpl;
+    for (int p = 0; p < B; p++) fin[p].out = C[p]->d;
+    cudaMemcpyAsync(P->d_final, fin.data(), fin.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, c->st);
+    return sum_desc(c, lv1, P->d_final, B);
+}
+
+static void evict_plans(Ctx *c, size_t incoming) {
+    while (!c->bplans.empty() && c->bplan_bytes + incoming > c->plan_cache_budget) {
+        auto lru = c->bplans.begin();
+        for (auto it = c->bplans.begin(); it != c->bplans.end(); ++it)
+            if (it->second->last_use < lru->second->last_use) lru = it;
+        c->bplan_bytes -= lru->second->ws_bytes;
+        free_bplan(c, lru->second);
+        c->bplans.erase(lru);
+    }
+}
+
+int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+                hegmm_ct **C, hegmm_opcount *cnt) {
+    for (int i = 0; i < count; i++) C[i] = nullptr;
+    if (count == 0) return HEGMM_OK;
+    std::vector<std::array<int, 4>> shapes;
+    std::vector<int> key;
+    for (int i = 0; i < count; i++) {
+        const int m = mln[3 * i], l = mln[3 * i + 1], n = mln[3 * i + 2];
+        const int a = resolve_alg(m, l, n, alg, c->S);
+        if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+        if (!A[i] || !B[i]) return set_err(c, HEGMM_EINVAL, "null operand");
+        if (A[i]->level != c->L || B[i]->level != c->L) return set_err(c, HEGMM_EINVAL, "operand level does not match");
+        shapes.push_back({m, l, n, a});
+        key.insert(key.end(), {m, l, n, a});
+    }
+    BatchPlan *P;
+    auto it = c->bplans.find(key);
+    if (it != c->bplans.end()) {
+        P = it->second;
+    } else {
+        int rc = build_bplan(c, shapes, &P);
+        if (rc) return rc;
+        evict_plans(c, P->ws_bytes);
+        c->bplans[key] = P;
+        c->bplan_bytes += P->ws_bytes;
+    }
+    P->last_use = ++c->bplan_clock;
+    for (int i = 0; i < count; i++) {
+        C[i] = new_ct(c, P->lv1);
+        if (!C[i]) {
+            for (int j = 0; j <= i; j++) {
+                hegmm_ct_destroy(C[j]);
+                C[j] = nullptr;
+            }
+            return set_err(c, HEGMM_ENOMEM, "result ciphertext");
+        }
+    }
+    int rc = run_bplan(c, P, A, B, C);
+    if (!rc) rc = cuda_check(c, "matmul");
+    if (rc) {
+        for (int i = 0; i < count; i++) {
+            hegmm_ct_destroy(C[i]);
+            C[i] = nullptr;
+        }
+        return rc;
+    }
+    if (cnt) *cnt = P->cnt;
+    return HEGMM_OK;
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" {
+
+int hegmm_matmul(hegmm_ctx *h, const hegmm_ct *A, const hegmm_ct *B, int m, int l, int n, int alg, hegmm_ct **C,
+                 hegmm_opcount *cnt) {
+    if (!h || !A || !B || !C) return HEGMM_EINVAL;
+    const int mln[3] = {m, l, n};
+    return matmul_many(&h->c, 1, &A, &B, mln, alg, C, cnt);
+}
+
+int hegmm_matmul_batch(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                       int alg, hegmm_ct **C) {
+    if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
+    return matmul_many(&h->c, count, A, B, mln, alg, C, nullptr);
+}
+
+}  // extern "C"

@@ -563,6 +563,7 @@ void hegmm_ctx_destroy(hegmm_ctx *h) {
     for (auto &kv : c->divs) dfree(c, kv.second.d);
     for (auto &kv : c->crt) dfree(c, kv.second);
     dfree(c, c->d_Pmod);
+    dfree(c, c->d_slot_pos0);
     dfree(c, c->d_tw);
     dfree(c, c->d_mods);
     cudaStreamSynchronize(c->st);

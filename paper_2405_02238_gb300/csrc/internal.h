@@ -104,7 +104,18 @@ struct DivTab {
     u64 *d = nullptr;             // see build_div_tab
 };
 
-struct ExecPlan;
+struct ShapeData;
+struct BatchPlan;
+
+// out = (init ? init : out) + sum_{j < count} items[j * stride]   over [2][lv][N]
+struct SumDesc {
+    u64 *out;
+    const u64 *init;
+    const u64 *items;
+    long long stride;
+    int count;
+    int pad;
+};
 
 struct Ctx {
     hegmm_params prm{};
@@ -128,7 +139,13 @@ struct Ctx {
     std::map<int, ModUpTab> modup;
     std::map<std::pair<int, int>, DivTab> divs;  // (level, 0 = ModDown / 1 = modswitch)
     std::vector<int> slot_pos0, slot_pos1;       // slot -> NTT position mod t
-    std::map<std::tuple<int, int, int, int>, ExecPlan *> plans;
+    int *d_slot_pos0 = nullptr;                  // device copy of slot_pos0
+    std::map<std::tuple<int, int, int, int>, ShapeData *> shapes;  // per-shape plan + masks
+    std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
+    unsigned long long bplan_clock = 0;
+    size_t bplan_bytes = 0;
+    size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
+    size_t plan_cache_budget = (size_t)48 << 30;  // workspace kept by cached batch plans
     u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
     std::map<int, u64 *> crt;        // level -> CRT-to-t table
 
@@ -211,15 +228,41 @@ int set_err(Ctx *c, int code, const std::string &msg);
 int cuda_check(Ctx *c, const char *where);
 LimbPat pat_ct(Ctx *c, u64 *base, int npoly, int lv, long long poly_stride_words = -1);
 
+// batched sums (SumDesc list) and the input gather of a batch
+int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n);
+// ev[b][slot_pos0[slots[j]]] = value for j in [off[b], off[b+1]) (NTT order mod t)
+int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev);
+int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst);
+
 // ---------------------------------------------------------------- exec.cu
+// Copies a host vector into a new stream-ordered device allocation.
+template <typename T>
+T *upload(Ctx *c, const std::vector<T> &v) {
+    size_t bytes = (v.size() * sizeof(T)) > 8 ? v.size() * sizeof(T) : 8;
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!v.empty()) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st);
+    return (T *)p;
+}
+LimbPat pat_nonown(Ctx *c, int lv, u64 *D, int n, long long stride);
+LimbPat pat_drop_special(Ctx *c, int lv, u64 *u, int npoly);
+const DivTab *div_tab(Ctx *c, int lv, int kind);
+int modup(Ctx *c, int lv, int n, const u64 *xn, long long xn_stride, u64 *xc, u64 *D);
+int ksw_moddown(Ctx *c, int lv, const RotDesc *d_rots, const DivDesc *d_div, int nrot, u64 *u, u64 *tmp);
+int modswitch_polys(Ctx *c, int lv, u64 *in, int npoly, u64 *tmp, u64 *out, DivDesc *d_desc);
 int rotate_hoisted(Ctx *c, const hegmm_ct *in, const int *z, int count, hegmm_ct **outs);
 int mult_relin(Ctx *c, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out);
 int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out);
-int matmul(Ctx *c, const hegmm_ct *A, const hegmm_ct *B, int m, int l, int n, int alg, hegmm_ct **C,
-           hegmm_opcount *cnt);
-int matmul_batch(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-                 hegmm_ct **C);
-int prepare_plan(Ctx *c, int m, int l, int n, int alg);
+
+// ---------------------------------------------------------------- batch.cu
+// products i < count: A[i] (m x l) . B[i] (l x n), shapes mln[3i..3i+2],
+// algorithm alg resolved per shape; C[i] receive new ciphertexts; cnt (may
+// be null) receives the summed operation counts.
+int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+                hegmm_ct **C, hegmm_opcount *cnt);
 void free_plans(Ctx *c);
 hegmm_ct *new_ct(Ctx *c, int level);
 u64 galois_of(Ctx *c, long long z);

@@ -586,6 +586,58 @@ int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out
     return cuda_check(c, "sum");
 }
 
+// Batched sums: out = (init ? init : out) + sum_j items[j * stride], one
+// descriptor per grid.z, over the 2 lv limbs of a ciphertext.
+__global__ void k_sum_desc(int lv, int logN, const ModDev *__restrict__ mods, const SumDesc *__restrict__ ds) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int pl = blockIdx.y;
+    const SumDesc d = ds[blockIdx.z];
+    const u64 q = mods[pl % lv].q;
+    const size_t o = (size_t)pl * N + c;
+    u64 acc = d.init ? d.init[o] : d.out[o];
+    for (int j = 0; j < d.count; j++) acc = addm(acc, d.items[j * d.stride + o], q);
+    d.out[o] = acc;
+}
+
+int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n) {
+    if (n <= 0) return HEGMM_OK;
+    Launch t(c, K_SUM, 0.0);
+    k_sum_desc<<<grid_coef(c->N, 2 * lv, n), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_sums);
+    return cuda_check(c, "sum_desc");
+}
+
+__global__ void k_scatter_slots(const int *__restrict__ off, const int *__restrict__ slots,
+                                const int *__restrict__ pos, u64 value, int N, u64 *__restrict__ ev) {
+    const int b = blockIdx.x;
+    for (int j = off[b] + threadIdx.x; j < off[b + 1]; j += blockDim.x) ev[(size_t)b * N + pos[slots[j]]] = value;
+}
+
+int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev) {
+    if (nb <= 0) return HEGMM_OK;
+    Launch t(c, K_CODEC, 0.0);
+    k_scatter_slots<<<nb, 256, 0, c->st>>>(d_off, d_slots, c->d_slot_pos0, value, c->N, ev);
+    return cuda_check(c, "scatter_slots");
+}
+
+// dst[i] = *src[i] for n ciphertexts of level lv (dst contiguous).
+__global__ void k_gather_cts(int lv, int logN, u64 *const *__restrict__ src, u64 *__restrict__ dst) {
+    const int N = 1 << logN;
+    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const size_t o = (size_t)blockIdx.y * N + c;
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(src[blockIdx.z] + o);
+    *reinterpret_cast<ulonglong2 *>(dst + (size_t)blockIdx.z * 2 * lv * N + o) = v;
+}
+
+int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst) {
+    if (n <= 0) return HEGMM_OK;
+    Launch t(c, K_POINTWISE, 2.0 * n * 2 * lv * c->limb_bytes());
+    k_gather_cts<<<grid_coef(c->N / 2, 2 * lv, n), 256, 0, c->st>>>(lv, c->logN, d_src, dst);
+    return cuda_check(c, "gather_cts");
+}
+
 __global__ void k_add(int lv, int logN, const ModDev *__restrict__ mods, const u64 *a, const u64 *b, u64 *out) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;

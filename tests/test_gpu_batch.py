@@ -1,0 +1,97 @@
+"""Batched HEGMM (many products of mixed shapes per call) against the
+single-product path and the oracle.
+
+Each product in a batch must give exactly the ciphertext it gives alone
+(bit-exact), its decryption must equal A.B mod t, and a few are checked
+against the oracle's ciphertext.  The full workload is the 512-product batch
+of the medium ring (shapes m, l, n in 4..64 with ml, ln, mn <= 4096).
+"""
+import numpy as np
+import pytest
+
+import workload as W
+from oracle import he as OH
+from oracle import slots as SL
+
+pytestmark = pytest.mark.gpu
+SEED = 4321
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm
+
+    return hegmm
+
+
+@pytest.fixture(scope="module")
+def medium(H):
+    ctx = H.Context.from_preset(W.MEDIUM)
+    ctx.hegmm_keygen(SEED)
+    return ctx
+
+
+def encrypt_all(ctx, H, shapes, lo, hi, seed0=0, stream0=0):
+    As, Bs, mats = [], [], []
+    for i, (m, l, n) in enumerate(shapes):
+        A, B = W.matrices(m, l, n, lo, hi, seed=seed0 + i)
+        mats.append((A, B))
+        As.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n), 77, stream0 + 2 * i))
+        Bs.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n), 77, stream0 + 2 * i + 1))
+    return As, Bs, mats
+
+
+def test_batch_mixed_shapes_equal_single_and_oracle(H, medium):
+    ctx = medium
+    shapes = [(4, 8, 6), (5, 12, 7), (9, 4, 11), (7, 9, 2), (12, 3, 9), (3, 3, 3), (6, 40, 5), (20, 10, 30)]
+    ctx.hegmm_keygen(SEED, shapes)
+    As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE)
+    outs = ctx.hegmm_matmul_batch(As, Bs, shapes)
+    for i, (m, l, n) in enumerate(shapes):
+        single, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n)
+        assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(single)).all(), shapes[i]
+        A, B = mats[i]
+        assert (ctx.hegmm_decrypt(outs[i], m, l, n).astype(np.int64) == (A @ B) % W.MEDIUM.t).all()
+    # two products against the oracle's ciphertext
+    o = OH.Oracle(W.MEDIUM)
+    o.keygen(SEED)
+    for i in (0, 3):
+        m, l, n = shapes[i]
+        plan = SL.make_plan(m, l, n, SL.choose_alg(m, l, n, o.S))
+        ex = OH.HEGMM(o)
+        ctA, ctB = ex.encrypt_inputs(plan, *mats[i], seed=77, streams=(2 * i, 2 * i + 1))
+        assert (ctx.hegmm_ct_export(outs[i]) == ex.run(plan, ctA, ctB)).all()
+
+
+def test_batch_with_repeated_shapes(H, medium):
+    ctx = medium
+    shapes = [(4, 8, 6)] * 4 + [(6, 2, 7)] * 3
+    ctx.hegmm_keygen(SEED, shapes)
+    As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=100, stream0=1000)
+    outs = ctx.hegmm_matmul_batch(As, Bs, shapes)
+    for i, (m, l, n) in enumerate(shapes):
+        A, B = mats[i]
+        assert (ctx.hegmm_decrypt(outs[i], m, l, n).astype(np.int64) == (A @ B) % W.MEDIUM.t).all()
+    # a second call of the same batch (cached plan) gives the same ciphertexts
+    again = ctx.hegmm_matmul_batch(As, Bs, shapes)
+    for a, b in zip(outs, again):
+        assert (ctx.hegmm_ct_export(a) == ctx.hegmm_ct_export(b)).all()
+
+
+def test_batch_512_products(H, medium):
+    ctx = medium
+    shapes = W.batch_shapes(W.BATCH_COUNT, ctx.S)
+    ctx.hegmm_keygen(SEED, shapes)
+    As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=5000, stream0=5000)
+    outs = ctx.hegmm_matmul_batch(As, Bs, shapes)
+    for i, (m, l, n) in enumerate(shapes):
+        A, B = mats[i]
+        assert (ctx.hegmm_decrypt(outs[i], m, l, n).astype(np.int64) == (A @ B) % W.MEDIUM.t).all(), shapes[i]
+    # sampled products equal the single-product path bit for bit
+    for i in np.random.default_rng(0).choice(len(shapes), 6, replace=False):
+        m, l, n = shapes[i]
+        single, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n)
+        assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(single)).all(), shapes[i]
