@@ -37,6 +37,7 @@ PRESET = W.MEDIUM
 SHAPES = W.MEDIUM_SHAPES
 ALGS = (1, 2)
 METRIC = "HEGMM encrypted matmuls/s (N=8192 ring, 16x32x24 + 32x8x48, Alg 1 + Alg 2)"
+METRIC_BATCH = "HEGMM encrypted matmuls/s (batch of 512 mixed shapes, N=8192 ring)"
 UNIT = "matmul/s"
 KEY_SEED = 7
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -49,6 +50,19 @@ def workload_config(extra=None):
                     "A16x32.B32x24 and A32x8.B8x48, Algorithm 1 and Algorithm 2 each; entries U[-8,7] seed 0",
         "products_per_step": len(SHAPES) * len(ALGS),
         "l2": "flushed between timed steps (256 MiB write) and per-step key working set > L2",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def batch_config(extra=None):
+    cfg = {
+        "workload": "batch: N=8192, t=65537, 5x40-bit + 1 special prime; 512 products with m,l,n uniform in "
+                    "4..64 (ml, ln, mn <= 4096), AUTO algorithm, entries U[0,15], seed 0; one hegmm_matmul_batch "
+                    "call per algorithm group per step",
+        "products_per_step": W.BATCH_COUNT,
+        "l2": "flushed between timed steps (256 MiB write); per-step working set (keys 15 GB, masks) >> L2",
     }
     if extra:
         cfg.update(extra)
@@ -111,7 +125,7 @@ class ClockSampler:
 _oracle_cache = {}
 
 
-def oracle_sample(nrot=6, ncm=6, nmul=2):
+def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2):
     """Times the oracle on a bounded sample of the workload.
 
     The oracle executes a product as a fixed sequence of HE-Rot, HE-CMult,
@@ -152,14 +166,16 @@ def oracle_sample(nrot=6, ncm=6, nmul=2):
         o.mult_relin(ct, r)
     t_mul = (time.perf_counter() - t0) / nmul
     total = 0.0
-    for (m, l, n) in SHAPES:
-        for alg in ALGS:
-            c = SL.make_plan(m, l, n, alg).counts()
-            total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
+    if prods is None:
+        prods = [(m, l, n, alg) for (m, l, n) in SHAPES for alg in ALGS]
+    for (m, l, n, alg) in prods:
+        a = alg if alg else SL.choose_alg(m, l, n, o.S)
+        c = SL.make_plan(m, l, n, a).counts()
+        total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
     desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=8192/L=5; "
-            "per-step time = op counts of the 4 plans x measured op times (%.1f/%.1f/%.1f/%.1f ms "
-            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, t_rot * 1e3, t_cm * 1e3, t_add * 1e3,
-                                                       t_mul * 1e3))
+            "per-step time = op counts of the %d plans x measured op times (%.1f/%.1f/%.1f/%.1f ms "
+            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, len(prods), t_rot * 1e3, t_cm * 1e3,
+                                                       t_add * 1e3, t_mul * 1e3))
     return total, desc
 
 
@@ -197,6 +213,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch"],
+                    help="medium: the four medium-ring products (default); batch: 512 mixed shapes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -220,23 +238,44 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     ctx = H.Context.from_preset(PRESET, stream=stream.cuda_stream)
     prods = []
-    for (m, l, n) in SHAPES:
-        A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
-        for alg in ALGS:
-            prods.append((m, l, n, alg, A, Bm))
-    ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_1)
-    ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_2)
+    if args.workload == "batch":
+        for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
+            A, Bm = W.matrices(m, l, n, *W.BATCH_RANGE, seed=i)
+            prods.append((m, l, n, H.ALG_AUTO, A, Bm))
+        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods], H.ALG_AUTO)
+    else:
+        for (m, l, n) in SHAPES:
+            A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
+            for alg in ALGS:
+                prods.append((m, l, n, alg, A, Bm))
+        ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_1)
+        ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_2)
     ops = []
     for i, (m, l, n, alg, A, Bm) in enumerate(prods):
         ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 1 + rank, 2 * i)
         cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, alg), 1 + rank, 2 * i + 1)
         ops.append((ca, cb))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # one step = every product of the workload through hegmm_matmul_batch,
+    # per algorithm (the batch API resolves AUTO per shape)
+    groups = {}
+    for i, p in enumerate(prods):
+        groups.setdefault(p[3], []).append(i)
 
     def step():
-        outs = []
-        cnts = []
-        for (m, l, n, alg, _, _), (ca, cb) in zip(prods, ops):
+        outs = [None] * len(prods)
+        for alg, idx in groups.items():
+            res = ctx.hegmm_matmul_batch([ops[i][0] for i in idx], [ops[i][1] for i in idx],
+                                         [prods[i][:3] for i in idx], alg)
+            for i, c in zip(idx, res):
+                outs[i] = c
+        return outs
+
+    def single_path(sample):
+        """The plain path: one hegmm_matmul call per product."""
+        outs, cnts = [], []
+        for i in sample:
+            (m, l, n, alg, _, _), (ca, cb) = prods[i], ops[i]
             c, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, alg)
             outs.append(c)
             cnts.append(cnt)
@@ -244,13 +283,28 @@ def main():
 
     # warm-up (builds plans, masks) and a correctness check of every product
     for w in range(max(args.warmup, 1)):
-        outs, cnts = step()
+        outs = step()
     for (m, l, n, alg, A, Bm), c in zip(prods, outs):
         got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
         assert (got == (A @ Bm) % PRESET.t).all(), "wrong product %dx%dx%d alg %d" % (m, l, n, alg)
-    ksw_per_step = sum(c["ksw"] for c in cnts)
-    paper_rot_per_step = sum(c["rot"] for c in cnts)
     del outs
+    sample = list(range(len(prods))) if len(prods) <= 8 else list(range(0, len(prods), len(prods) // 32))
+    _, cnts = single_path(sample)
+    sc = [H.hegmm_plan_counts(m, l, n, alg, ctx.S) for (m, l, n, alg, _, _) in prods]
+    ksw_per_step = sum(c["ksw"] for c in sc)
+    paper_rot_per_step = sum(c["rot"] for c in sc)
+    # plain per-product path on the sample (warm), for comparison
+    torch.cuda.synchronize()
+    for _ in range(2):
+        single_path(sample)
+    torch.cuda.synchronize()
+    s_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    s_ev[0].record(stream)
+    for _ in range(3):
+        single_path(sample)
+    s_ev[1].record(stream)
+    torch.cuda.synchronize()
+    single_value = 3 * len(sample) / (s_ev[0].elapsed_time(s_ev[1]) / 1e3)
 
     clk = ClockSampler(local)
     if world > 1:
@@ -267,7 +321,7 @@ def main():
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
         ev[k][0].record(stream)
-        outs, _ = step()
+        outs = step()
         ev[k][1].record(stream)
         del outs
     torch.cuda.synchronize()
@@ -298,11 +352,12 @@ def main():
     d2h = sum(o.numel() * 8 for o in host_out)
 
     def e2e_step():
-        for (m, l, n, alg, _, _), (ha, hb), ho in zip(prods, host_in, host_out):
-            ia = ctx.hegmm_ct_import(ha.numpy())
-            ib = ctx.hegmm_ct_import(hb.numpy())
-            c, _ = ctx.hegmm_matmul(ia, ib, m, l, n, alg)
-            ctx.hegmm_ct_export(c, ho.numpy())
+        ins = [(ctx.hegmm_ct_import(ha.numpy()), ctx.hegmm_ct_import(hb.numpy())) for ha, hb in host_in]
+        for alg, idx in groups.items():
+            res = ctx.hegmm_matmul_batch([ins[i][0] for i in idx], [ins[i][1] for i in idx],
+                                         [prods[i][:3] for i in idx], alg)
+            for i, c in zip(idx, res):
+                ctx.hegmm_ct_export(c, host_out[i].numpy())
 
     e2e_step()
     torch.cuda.synchronize()
@@ -312,55 +367,65 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - e0) * 1e3 / args.steps
 
-    # roofline of the dominant kernel
-    dom = max(stats.items(), key=lambda kv: kv[1][0])
-    name, (kms, kn, kbytes) = dom
+    # roofline of the dominant kernel (and of the key inner product, the
+    # HBM-bound part of key switching)
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm_peak = peaks.get("hbm_gbs")
-    roof = {"kernel": name, "launches": kn, "avg_launch_us": kms * 1e3 / max(kn, 1),
-            "share_of_kernel_time": kms / max(sum(v[0] for v in stats.values()), 1e-9)}
-    if name.startswith("ntt"):
-        roof.update({"bound": "alu", "unit": "Gbutterfly/s"})
-        logN = PRESET.logN
-        bfly = kbytes / (2 * 8 * (1 << logN)) * (1 << (logN - 1)) * logN
-        roof["achieved"] = bfly / (kms / 1e3) / 1e9
-        roof["peak"] = None
-        roof["frac"] = None
-    else:
-        peak = hbm_peak or HBM_FALLBACK
-        roof.update({"bound": "hbm", "unit": "GB/s", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": peak,
-                     "peak_source": "measured" if hbm_peak else "fallback"})
-        roof["frac"] = roof["achieved"] / peak
+    bfly_peak = ctx.hegmm_peak_butterflies() / 1e9
+    total_kms = max(sum(v[0] for v in stats.values()), 1e-9)
+
+    def roofline(name):
+        kms, kn, kbytes, kwork = stats[name]
+        r = {"kernel": name, "launches": kn, "avg_launch_us": kms * 1e3 / max(kn, 1),
+             "share_of_kernel_time": kms / total_kms}
+        if kwork > 0:
+            r.update({"bound": "alu", "unit": "Gbutterfly/s", "achieved": kwork / (kms / 1e3) / 1e9,
+                      "peak": bfly_peak, "peak_source": "measured: hegmm_peak_butterflies (register-only "
+                      "lazy Shoup butterflies on every SM)"})
+        else:
+            peak = hbm_peak or HBM_FALLBACK
+            r.update({"bound": "hbm", "unit": "GB/s", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": peak,
+                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else "fallback"})
+        r["frac"] = r["achieved"] / r["peak"]
+        r["algorithmic_bytes_per_launch"] = kbytes / max(kn, 1)
+        return r
+
+    name = max(stats.items(), key=lambda kv: kv[1][0])[0]
+    roof = roofline(name)
     roof["traffic"] = None
     src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_02238_gb300", "csrc", "kernels.cu"), "rb").read()).hexdigest()[:12]
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
-            if tj.get("kernels_sha") == src_sha and name in tj.get("per_unit_bytes", {}):
-                units = kbytes / tj["algorithmic_bytes_per_unit"][name]
-                roof["traffic"] = tj["per_unit_bytes"][name] * units / max(kn, 1)
+            if tj.get("kernels_sha") == src_sha and name in tj.get("traffic_per_algorithmic_byte", {}):
+                roof["traffic"] = tj["traffic_per_algorithmic_byte"][name] * roof["algorithmic_bytes_per_launch"]
         except Exception:
             pass
 
+    batch = args.workload == "batch"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC_BATCH if batch else METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": workload_config({"parallelism": "replicas" if world > 1 else "single-gpu"}),
+        "config": (batch_config if batch else workload_config)({"parallelism": "replicas" if world > 1 else "single-gpu"}),
         "keyswitches_per_s": ksw_per_step * world / (ms / 1e3),
         "paper_rotations_per_step": paper_rot_per_step,
         "keyswitches_per_step": ksw_per_step,
+        "per_product_path": {"value": single_value * world, "unit": UNIT,
+                             "how": "one hegmm_matmul call per product, %d of the %d products, warm" % (
+                                 len(sample), len(prods))},
         "wall_s_timed": wall,
         "e2e": {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": int(sum(v[1] for v in stats.values()) / max(args.steps, 1)) * args.steps,
         "roofline": roof,
+        "roofline_key_inner_product": roofline("ksw_inner_product") if stats["ksw_inner_product"][1] else None,
         "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in stats.items() if v[1]},
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        sec, desc = oracle_sample()
+        sec, desc = oracle_sample([p[:4] for p in prods])
         line["cpu_baseline"] = {"value": len(prods) / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc}
     if rank == 0:

@@ -222,12 +222,20 @@ int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const i
  * kernels is bracketed by CUDA events on the context stream and its
  * duration added to the kernel's bucket.  kind indexes the table named by
  * hegmm_kernel_name (0 .. hegmm_kernel_kinds()-1).  Reading the stats
- * synchronises the stream; hegmm_kernel_reset zeroes them. */
+ * synchronises the stream; hegmm_kernel_reset zeroes them.  bytes is the
+ * launches' algorithmic HBM traffic (inputs read once, outputs written
+ * once); butterflies counts (N/2) log2 N per limb NTT the launches ran. */
 int hegmm_set_timing(hegmm_ctx *ctx, int enable);
 int hegmm_kernel_kinds(void);
 const char *hegmm_kernel_name(int kind);
-int hegmm_kernel_stats(hegmm_ctx *ctx, int kind, double *total_ms, long long *launches, double *bytes);
+int hegmm_kernel_stats(hegmm_ctx *ctx, int kind, double *total_ms, long long *launches, double *bytes,
+                       double *butterflies);
 int hegmm_kernel_reset(hegmm_ctx *ctx);
+
+/* Measures the integer-pipe ceiling of the NTT butterfly on this device: the
+ * lazy Shoup butterfly of the NTT kernels repeated on registers by every SM,
+ * no memory traffic.  *per_s receives butterflies per second.  Synchronous. */
+int hegmm_peak_butterflies(hegmm_ctx *ctx, double *per_s);
 
 #ifdef __cplusplus
 }

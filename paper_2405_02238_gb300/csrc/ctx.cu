@@ -757,18 +757,21 @@ static void drain(Ctx *c) {
         c->stat_ms[p.kind] += ms;
         c->stat_n[p.kind] += 1;
         c->stat_bytes[p.kind] += p.bytes;
+        c->stat_work[p.kind] += p.work;
         c->evpool.push_back(p.a);
         c->evpool.push_back(p.b);
     }
     c->pending.clear();
 }
 
-int hegmm_kernel_stats(hegmm_ctx *h, int kind, double *total_ms, long long *launches, double *bytes) {
+int hegmm_kernel_stats(hegmm_ctx *h, int kind, double *total_ms, long long *launches, double *bytes,
+                       double *butterflies) {
     if (!h || kind < 0 || kind >= K_NUM) return HEGMM_EINVAL;
     drain(&h->c);
     if (total_ms) *total_ms = h->c.stat_ms[kind];
     if (launches) *launches = h->c.stat_n[kind];
     if (bytes) *bytes = h->c.stat_bytes[kind];
+    if (butterflies) *butterflies = h->c.stat_work[kind];
     return HEGMM_OK;
 }
 
@@ -779,8 +782,14 @@ int hegmm_kernel_reset(hegmm_ctx *h) {
         h->c.stat_ms[k] = 0;
         h->c.stat_n[k] = 0;
         h->c.stat_bytes[k] = 0;
+        h->c.stat_work[k] = 0;
     }
     return HEGMM_OK;
+}
+
+int hegmm_peak_butterflies(hegmm_ctx *h, double *per_s) {
+    if (!h || !per_s) return HEGMM_EINVAL;
+    return peak_butterflies(&h->c, per_s);
 }
 
 }  // extern "C"

@@ -153,13 +153,14 @@ struct Ctx {
     struct Pending {
         int kind;
         cudaEvent_t a, b;
-        double bytes;
+        double bytes, work;
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> evpool;
     double stat_ms[K_NUM]{};
     long long stat_n[K_NUM]{};
     double stat_bytes[K_NUM]{};
+    double stat_work[K_NUM]{};  // NTT butterflies
 
     // ext index e of the key-switching basis at level lv -> global modulus
     int gidx(int lv, int e) const { return e < lv ? e : L + (e - lv); }
@@ -169,14 +170,22 @@ struct Ctx {
 };
 
 // Times one launch when timing is enabled.
+// bytes: algorithmic HBM bytes of the launch; work: NTT butterflies.
 struct Launch {
     Ctx *c;
     int kind;
-    double bytes;
+    double bytes, work;
     cudaEvent_t a = nullptr, b = nullptr;
-    Launch(Ctx *c_, int kind_, double bytes_);
+    Launch(Ctx *c_, int kind_, double bytes_, double work_ = 0.0);
     ~Launch();
 };
+
+// Butterflies of one limb NTT: (N/2) log2 N.
+inline double ntt_bfly(const Ctx *c) { return (double)(c->N / 2) * c->logN; }
+
+// Measured throughput of the lazy forward butterfly on registers (no memory
+// traffic), in butterflies per second, on the context's device.
+int peak_butterflies(Ctx *c, double *per_s);
 
 // ---------------------------------------------------------------- kernels.cu
 int init_kernels(Ctx *c);

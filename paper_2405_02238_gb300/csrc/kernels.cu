@@ -16,7 +16,7 @@ namespace hg {
 
 // ------------------------------------------------------------------ timing
 
-Launch::Launch(Ctx *c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
+Launch::Launch(Ctx *c_, int kind_, double bytes_, double work_) : c(c_), kind(kind_), bytes(bytes_), work(work_) {
     if (!c->timing) return;
     if (c->evpool.size() < 2) {
         for (int i = 0; i < 64; i++) {
@@ -35,7 +35,7 @@ Launch::Launch(Ctx *c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(by
 Launch::~Launch() {
     if (!a) return;
     cudaEventRecord(b, c->st);
-    c->pending.push_back({kind, a, b, bytes});
+    c->pending.push_back({kind, a, b, bytes, work});
 }
 
 // ------------------------------------------------------------------ helpers
@@ -274,7 +274,7 @@ int init_kernels(Ctx *c) {
 
 int ntt_fwd(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
-    Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes());
+    Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, false><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
     return cuda_check(c, "ntt_fwd");
@@ -282,7 +282,7 @@ int ntt_fwd(Ctx *c, const LimbPat &p) {
 
 int ntt_inv(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
-    Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes());
+    Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, true><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
     return cuda_check(c, "ntt_inv");
@@ -291,7 +291,8 @@ int ntt_inv(Ctx *c, const LimbPat &p) {
 int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
     if (npoly <= 0) return HEGMM_OK;
     // algorithmic bytes: drop limbs + u_i + add_i read, out_i written, per kept limb
-    Launch t(c, K_DIV_NTT, (double)npoly * tab.nkeep * (tab.ndrop + 3.0) * c->limb_bytes());
+    Launch t(c, K_DIV_NTT, (double)npoly * tab.nkeep * (tab.ndrop + 3.0) * c->limb_bytes(),
+             (double)npoly * tab.nkeep * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     const int grid = npoly * tab.nkeep;
     HG_DISPATCH_LOGN(c->logN, (k_divround_ntt<LG><<<grid, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
@@ -301,7 +302,7 @@ int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
 
 int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, long long xc_stride, const u64 *xn,
               long long xn_stride, u64 *D, long long D_stride, int n) {
-    Launch t(c, K_MODUP, (double)n * (tb.lv + 2.0 * (tb.nd * tb.ne)) * c->limb_bytes());
+    Launch t(c, K_MODUP, (double)n * (tb.lv + 2.0 * (tb.nd * tb.ne)) * c->limb_bytes(), nonown.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     if (nonown.count > 0)
         HG_DISPATCH_LOGN(c->logN, (k_modup_ntt<LG><<<nonown.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
@@ -433,8 +434,10 @@ __global__ void __launch_bounds__(256) k_ksw_ip(int lv, int ne, int nd, int np, 
 int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
     if (nrot <= 0) return HEGMM_OK;
     const int ne = lv + c->K, nd = c->digits(lv);
-    // algorithmic bytes: key (2 nd ne limbs) + digits read + u written
-    Launch t(c, K_KSW_IP, (double)nrot * (2.0 * nd * ne + nd * ne + 2.0 * ne) * c->limb_bytes());
+    // algorithmic HBM bytes per rotation: its key (2 nd ne limbs) read and u
+    // (2 ne limbs) written; the hoisted digits are shared by every rotation
+    // of a source and served from L2, so they are not counted.
+    Launch t(c, K_KSW_IP, (double)nrot * (2.0 * nd * ne + 2.0 * ne) * c->limb_bytes());
     k_ksw_ip<<<grid_coef(c->N / 2, ne, nrot), 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots);
     return cuda_check(c, "ksw_ip");
 }
@@ -612,6 +615,61 @@ __global__ void k_scatter_slots(const int *__restrict__ off, const int *__restri
                                 const int *__restrict__ pos, u64 value, int N, u64 *__restrict__ ev) {
     const int b = blockIdx.x;
     for (int j = off[b] + threadIdx.x; j < off[b + 1]; j += blockDim.x) ev[(size_t)b * N + pos[slots[j]]] = value;
+}
+
+// Butterfly throughput probe: the lazy forward butterfly of the NTT kernels,
+// repeated on registers (12 per round, the stages of one radix-8 group).
+__device__ __forceinline__ void bfly_lazy(u64 &X, u64 &Y, const TwPair &t, u64 q, u64 q2) {
+    u64 a = X >= q2 ? X - q2 : X;
+    const u64 T = mulsh_lazy(Y, t.w, t.wp, q);
+    X = a + T;
+    Y = a - T + q2;
+}
+
+__global__ void __launch_bounds__(256) k_bfly_peak(u64 q, const TwPair *__restrict__ tw, int iters, u64 *out) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    u64 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) x[k] = ((u64)gid * 8 + k) % q;
+    const TwPair t0 = tw[1], t1 = tw[2], t2 = tw[3], t3 = tw[4], t4 = tw[5], t5 = tw[6], t6 = tw[7];
+    const u64 q2 = 2 * q;
+    for (int it = 0; it < iters; it++) {
+        bfly_lazy(x[0], x[4], t0, q, q2);
+        bfly_lazy(x[1], x[5], t0, q, q2);
+        bfly_lazy(x[2], x[6], t0, q, q2);
+        bfly_lazy(x[3], x[7], t0, q, q2);
+        bfly_lazy(x[0], x[2], t1, q, q2);
+        bfly_lazy(x[1], x[3], t1, q, q2);
+        bfly_lazy(x[4], x[6], t2, q, q2);
+        bfly_lazy(x[5], x[7], t2, q, q2);
+        bfly_lazy(x[0], x[1], t3, q, q2);
+        bfly_lazy(x[2], x[3], t4, q, q2);
+        bfly_lazy(x[4], x[5], t5, q, q2);
+        bfly_lazy(x[6], x[7], t6, q, q2);
+    }
+    out[gid] = x[0] ^ x[1] ^ x[2] ^ x[3] ^ x[4] ^ x[5] ^ x[6] ^ x[7];
+}
+
+int peak_butterflies(Ctx *c, double *per_s) {
+    const int blocks = c->nsm * 8, threads = 256, iters = 4096;
+    u64 *out = dalloc(c, (size_t)blocks * threads);
+    if (!out) return set_err(c, HEGMM_ENOMEM, "butterfly probe");
+    const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_bfly_peak<<<blocks, threads, 0, c->st>>>(c->q[0], tw, iters / 8, out);
+    cudaEventRecord(a, c->st);
+    k_bfly_peak<<<blocks, threads, 0, c->st>>>(c->q[0], tw, iters, out);
+    cudaEventRecord(b, c->st);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    dfree(c, out);
+    *per_s = (double)blocks * threads * iters * 12.0 / (ms / 1e3);
+    return cuda_check(c, "butterfly probe");
 }
 
 int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev) {

@@ -89,7 +89,9 @@ _SIGS = {
     "hegmm_kernel_kinds": (ctypes.c_int, []),
     "hegmm_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "hegmm_kernel_stats": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double)]),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "hegmm_peak_butterflies": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
     "hegmm_kernel_reset": (ctypes.c_int, [vp]),
     "hegmm_plan_counts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(hegmm_opcount)]),
@@ -322,17 +324,22 @@ class Context:
         self._check(self.lib.hegmm_set_timing(self.h, int(bool(enable))), "set_timing")
 
     def hegmm_kernel_stats(self):
-        """{kernel name: (total ms, launches, algorithmic bytes)}."""
+        """{kernel name: (total ms, launches, algorithmic bytes, butterflies)}."""
         out = {}
         for k in range(self.lib.hegmm_kernel_kinds()):
-            ms, n, b = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-            self._check(self.lib.hegmm_kernel_stats(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)),
-                        "kernel_stats")
-            out[self.lib.hegmm_kernel_name(k).decode()] = (ms.value, n.value, b.value)
+            ms, n, b, w = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.hegmm_kernel_stats(self.h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                                    ctypes.byref(w)), "kernel_stats")
+            out[self.lib.hegmm_kernel_name(k).decode()] = (ms.value, n.value, b.value, w.value)
         return out
 
     def hegmm_kernel_reset(self):
         self._check(self.lib.hegmm_kernel_reset(self.h), "kernel_reset")
+
+    def hegmm_peak_butterflies(self) -> float:
+        v = ctypes.c_double()
+        self._check(self.lib.hegmm_peak_butterflies(self.h, ctypes.byref(v)), "peak_butterflies")
+        return v.value
 
 
 class Plaintext:
