@@ -151,6 +151,47 @@ int hegmm_matmul(hegmm_ctx *ctx, const hegmm_ct *A, const hegmm_ct *B, int m, in
 int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                        const int *mln, int alg, hegmm_ct **C);
 
+/* ---- Serving: continuous batching of product requests ------------------
+ * A server queues requests (two operand ciphertexts and a shape) and runs
+ * them through the batch executor of hegmm_matmul_batch.  The caller's
+ * event loop drives it: hegmm_server_poll retires finished batches (their
+ * results become available to hegmm_server_result) and admits queued
+ * requests into a new batch whenever one of the server's device streams is
+ * free and the batch's estimated workspace fits in the memory budget minus
+ * what in-flight batches hold -- so requests that arrive while others run
+ * join the next batch, and batches on different streams overlap on the GPU.
+ * Each result is bit-identical to the same product computed alone.
+ * Operands must stay alive until their request completes.  While a server
+ * exists, the context must be used from the thread that polls it. */
+typedef struct hegmm_server hegmm_server;
+
+typedef struct {
+    int max_batch;       /* products per batch (0 = 64) */
+    int streams;         /* device streams that batches rotate over (0 = 2, at most 8) */
+    uint64_t mem_budget; /* bytes of batch workspace in flight (0 = 16 GiB) */
+} hegmm_server_opts;
+
+typedef struct {
+    long long submitted, completed, failed, batches, queued, in_flight, max_batch;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit-to-completion latency */
+} hegmm_server_stats;
+
+int hegmm_server_create(hegmm_ctx *ctx, const hegmm_server_opts *opts, hegmm_server **out);
+/* Queues C = A.B; *ticket identifies the request.  Errors: HEGMM_ESHAPE,
+ * HEGMM_EINVAL (operand level). */
+int hegmm_server_submit(hegmm_server *srv, const hegmm_ct *A, const hegmm_ct *B, int m, int l, int n, int alg,
+                        uint64_t *ticket);
+/* Retires finished batches and launches new ones; with wait != 0 returns
+ * only when every submitted request has completed. */
+int hegmm_server_poll(hegmm_server *srv, int wait);
+/* If the request has completed, *C receives its result (owned by the caller)
+ * and latency_ms its submit-to-completion time; otherwise *C = NULL.
+ * Returns the request's error code if its batch failed. */
+int hegmm_server_result(hegmm_server *srv, uint64_t ticket, hegmm_ct **C, double *latency_ms);
+int hegmm_server_stats_get(hegmm_server *srv, hegmm_server_stats *out);
+/* Waits for every request, frees uncollected results and the server. */
+void hegmm_server_destroy(hegmm_server *srv);
+
 /* Decrypts a product of hegmm_matmul and reads C (m x n, row-major, values
  * in [0, t)) from the plan's result slots.  Synchronises the stream. */
 int hegmm_decrypt(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int alg, uint64_t *out);

@@ -44,6 +44,10 @@ struct ShapeData {
     std::map<std::vector<int>, int> mask_of;
     u64 *masks = nullptr;
     int nmask = 0;
+    size_t bytes = 0;
+    int refs = 0;                    // batch plans that reference these masks
+    unsigned long long last_use = 0;
+    cudaEvent_t used = nullptr;      // recorded after the last launch that read the masks
     hegmm_opcount cnt{};
     const u64 *mask_ptr(Ctx *c, const std::vector<int> &dst) const {
         return masks + (size_t)mask_of.at(dst) * c->L * c->N;
@@ -92,19 +96,42 @@ struct BatchPlan {
 };
 
 static void free_bplan(Ctx *c, BatchPlan *P) {
+    std::set<ShapeData *> uniq(P->shp.begin(), P->shp.end());
+    for (ShapeData *s : uniq) s->refs--;
     for (void *a : P->allocs) dfree(c, a);
     delete P;
+}
+
+static void free_shape(Ctx *c, ShapeData *s) {
+    if (s->used) {
+        cudaStreamWaitEvent(c->st, s->used, 0);  // the masks may have been read on another stream
+        cudaEventDestroy(s->used);
+    }
+    dfree(c, s->masks);
+    c->mask_bytes -= s->bytes;
+    delete s;
 }
 
 void free_plans(Ctx *c) {
     for (auto &kv : c->bplans) free_bplan(c, kv.second);
     c->bplans.clear();
     c->bplan_bytes = 0;
-    for (auto &kv : c->shapes) {
-        dfree(c, kv.second->masks);
-        delete kv.second;
-    }
+    for (auto &kv : c->shapes) free_shape(c, kv.second);
     c->shapes.clear();
+}
+
+// Keeps the resident masks within the context's budget: least recently used
+// shapes that no plan references are released first.
+static void evict_shapes(Ctx *c, size_t incoming) {
+    while (c->mask_bytes + incoming > c->mask_budget) {
+        auto lru = c->shapes.end();
+        for (auto it = c->shapes.begin(); it != c->shapes.end(); ++it)
+            if (it->second->refs == 0 && (lru == c->shapes.end() || it->second->last_use < lru->second->last_use))
+                lru = it;
+        if (lru == c->shapes.end()) return;  // everything is in use
+        free_shape(c, lru->second);
+        c->shapes.erase(lru);
+    }
 }
 
 // Encode 0/1 masks (value `scale` on the listed slots) into Montgomery NTT
@@ -154,6 +181,7 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
     auto key = std::make_tuple(m, l, n, alg);
     auto it = c->shapes.find(key);
     if (it != c->shapes.end()) {
+        it->second->last_use = ++c->bplan_clock;
         *out = it->second;
         return HEGMM_OK;
     }
@@ -195,14 +223,19 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
                     mlist.push_back(&sd->mask_of.find(d.dst)->first);
                 }
     sd->nmask = (int)mlist.size();
+    sd->bytes = (size_t)sd->nmask * c->L * c->N * 8;
+    evict_shapes(c, sd->bytes);
     sd->masks = dalloc(c, (size_t)sd->nmask * c->L * c->N);
     if (!sd->masks) return fail(HEGMM_ENOMEM, "plan masks");
     int rc = encode_masks(c, c->L, mlist, scale, sd->masks);
+    if (!rc && cudaStreamSynchronize(c->st) != cudaSuccess) rc = cuda_check(c, "mask encode");  // masks serve every stream
     if (rc) {
         dfree(c, sd->masks);
         delete sd;
         return rc;
     }
+    c->mask_bytes += sd->bytes;
+    sd->last_use = ++c->bplan_clock;
     const long long ni = (long long)hp.iters.size(), ne = (long long)hp.extract.size();
     hegmm_opcount &ct = sd->cnt;
     ct.rot = hp.paper_rot();
@@ -240,10 +273,15 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         return rc;
     };
     P->B = (int)shapes.size();
+    std::set<ShapeData *> held;
     for (auto &s : shapes) {
         ShapeData *sd;
         int rc = get_shape(c, s[0], s[1], s[2], s[3], &sd);
-        if (rc) return fail_rc(rc);
+        if (rc) {
+            P->shp.assign(held.begin(), held.end());  // release what this plan holds
+            return fail_rc(rc);
+        }
+        if (held.insert(sd).second) sd->refs++;  // pinned while this plan exists
         P->shp.push_back(sd);
         add_counts(P->cnt, sd->cnt);
     }
@@ -555,7 +593,14 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
     std::vector<SumDesc> fin = P->final_tmpl;
     for (int p = 0; p < B; p++) fin[p].out = C[p]->d;
     cudaMemcpyAsync(P->d_final, fin.data(), fin.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, c->st);
-    return sum_desc(c, lv1, P->d_final, B);
+    if ((rc = sum_desc(c, lv1, P->d_final, B))) return rc;
+    // mark the masks of every shape as read on this stream (for eviction)
+    std::set<ShapeData *> uniq(P->shp.begin(), P->shp.end());
+    for (ShapeData *s : uniq) {
+        if (!s->used) cudaEventCreateWithFlags(&s->used, cudaEventDisableTiming);
+        cudaEventRecord(s->used, c->st);
+    }
+    return HEGMM_OK;
 }
 
 static void evict_plans(Ctx *c, size_t incoming) {
@@ -569,8 +614,22 @@ static void evict_plans(Ctx *c, size_t incoming) {
     }
 }
 
-int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-                hegmm_ct **C, hegmm_opcount *cnt) {
+size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
+    const int a = resolve_alg(m, l, n, alg, c->S);
+    if (!a) return 0;
+    HostPlan hp = make_host_plan(m, l, n, a);
+    const size_t lv0 = c->L, lv1 = c->L - c->prm.ms_drop, ne0 = lv0 + c->K, ne1 = lv1 + c->K;
+    const size_t nd0 = c->digits((int)lv0), nd1 = c->digits((int)lv1);
+    const size_t ni = hp.iters.size(), ne = hp.extract.size();
+    size_t w = 6 * lv0 + 2 * nd0 * ne0 + ni * 4 * lv0 + (lv1 != lv0 ? ni * 4 * lv1 : 0) + 2 * lv1;
+    if (ne) w += lv1 + nd1 * ne1 + ne * (2 * ne1 + 2 * lv1);
+    return w * c->N * 8;
+}
+
+void release_plan(Ctx *c, BatchPlan *P) { free_bplan(c, P); }
+
+int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+               hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold) {
     for (int i = 0; i < count; i++) C[i] = nullptr;
     if (count == 0) return HEGMM_OK;
     std::vector<std::array<int, 4>> shapes;
@@ -585,17 +644,27 @@ int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *con
         key.insert(key.end(), {m, l, n, a});
     }
     BatchPlan *P;
-    auto it = c->bplans.find(key);
+    auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
         P = it->second;
     } else {
         int rc = build_bplan(c, shapes, &P);
         if (rc) return rc;
-        evict_plans(c, P->ws_bytes);
-        c->bplans[key] = P;
-        c->bplan_bytes += P->ws_bytes;
+        if (cache) {
+            evict_plans(c, P->ws_bytes);
+            c->bplans[key] = P;
+            c->bplan_bytes += P->ws_bytes;
+        } else {
+            *hold = P;
+        }
     }
     P->last_use = ++c->bplan_clock;
+    auto drop_uncached = [&]() {
+        if (!cache && hold && *hold) {
+            free_bplan(c, *hold);
+            *hold = nullptr;
+        }
+    };
     for (int i = 0; i < count; i++) {
         C[i] = new_ct(c, P->lv1);
         if (!C[i]) {
@@ -603,6 +672,7 @@ int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *con
                 hegmm_ct_destroy(C[j]);
                 C[j] = nullptr;
             }
+            drop_uncached();
             return set_err(c, HEGMM_ENOMEM, "result ciphertext");
         }
     }
@@ -613,10 +683,16 @@ int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *con
             hegmm_ct_destroy(C[i]);
             C[i] = nullptr;
         }
+        drop_uncached();
         return rc;
     }
     if (cnt) *cnt = P->cnt;
     return HEGMM_OK;
+}
+
+int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+                hegmm_ct **C, hegmm_opcount *cnt) {
+    return matmul_run(c, count, A, B, mln, alg, C, cnt, true, nullptr);
 }
 
 }  // namespace hg

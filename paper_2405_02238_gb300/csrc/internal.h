@@ -145,6 +145,8 @@ struct Ctx {
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
+    size_t mask_bytes = 0;
+    size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
     size_t plan_cache_budget = (size_t)48 << 30;  // workspace kept by cached batch plans
     u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
     std::map<int, u64 *> crt;        // level -> CRT-to-t table
@@ -272,6 +274,14 @@ int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out);
 // be null) receives the summed operation counts.
 int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
                 hegmm_ct **C, hegmm_opcount *cnt);
+// Same on the context's current stream; cache = false builds a plan only
+// for this call and hands it back in *hold, to be released with
+// release_plan (stream-ordered on c->st) once the work is done.
+int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+               hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold);
+void release_plan(Ctx *c, BatchPlan *P);
+// Device workspace one product adds to a batch (admission estimate).
+size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg);
 void free_plans(Ctx *c);
 hegmm_ct *new_ct(Ctx *c, int level);
 u64 galois_of(Ctx *c, long long z);

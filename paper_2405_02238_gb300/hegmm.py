@@ -49,6 +49,19 @@ class hegmm_opcount(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class hegmm_server_opts(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int), ("streams", ctypes.c_int), ("mem_budget", ctypes.c_uint64)]
+
+
+class hegmm_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in
+                ("submitted", "completed", "failed", "batches", "queued", "in_flight", "max_batch")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 u64p = ctypes.POINTER(ctypes.c_uint64)
 i64p = ctypes.POINTER(ctypes.c_int64)
 intp = ctypes.POINTER(ctypes.c_int)
@@ -92,6 +105,13 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double)]),
     "hegmm_peak_butterflies": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
+    "hegmm_server_create": (ctypes.c_int, [vp, ctypes.POINTER(hegmm_server_opts), ctypes.POINTER(vp)]),
+    "hegmm_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "hegmm_server_poll": (ctypes.c_int, [vp, ctypes.c_int]),
+    "hegmm_server_result": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double)]),
+    "hegmm_server_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(hegmm_server_stats)]),
+    "hegmm_server_destroy": (None, [vp]),
     "hegmm_kernel_reset": (ctypes.c_int, [vp]),
     "hegmm_plan_counts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(hegmm_opcount)]),
@@ -368,5 +388,56 @@ class Ciphertext:
         try:
             if self.h and self.ctx.h:
                 self.ctx.lib.hegmm_ct_destroy(self.h)
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (hegmm_server_*); driven by poll()."""
+
+    def __init__(self, ctx: Context, max_batch: int = 0, streams: int = 0, mem_budget: int = 0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        opts = hegmm_server_opts(max_batch, streams, mem_budget)
+        h = vp()
+        ctx._check(self.lib.hegmm_server_create(ctx.h, ctypes.byref(opts), ctypes.byref(h)), "server_create")
+        self.h = h
+        self._keep = {}
+
+    def hegmm_server_submit(self, A: "Ciphertext", B: "Ciphertext", m: int, l: int, n: int,
+                            alg: int = ALG_AUTO) -> int:
+        t = ctypes.c_uint64()
+        self.ctx._check(self.lib.hegmm_server_submit(self.h, A.h, B.h, m, l, n, alg, ctypes.byref(t)), "server_submit")
+        self._keep[t.value] = (A, B)  # operands must outlive the request
+        return t.value
+
+    def hegmm_server_poll(self, wait: bool = False):
+        self.ctx._check(self.lib.hegmm_server_poll(self.h, int(bool(wait))), "server_poll")
+
+    def hegmm_server_result(self, ticket: int):
+        """(Ciphertext, latency_ms) once the request has completed, else None."""
+        out = vp()
+        lat = ctypes.c_double()
+        self.ctx._check(self.lib.hegmm_server_result(self.h, ticket, ctypes.byref(out), ctypes.byref(lat)),
+                        "server_result")
+        if not out.value:
+            return None
+        self._keep.pop(ticket, None)
+        return Ciphertext(self.ctx, out), lat.value
+
+    def hegmm_server_stats_get(self) -> dict:
+        st = hegmm_server_stats()
+        self.ctx._check(self.lib.hegmm_server_stats_get(self.h, ctypes.byref(st)), "server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hegmm_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
