@@ -203,6 +203,109 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ----------------------------------------------------------------------------- serving
+
+
+def run_serve(args):
+    """Poisson arrivals on the paper ring (N=16384), swept over rates.
+
+    For each rate, min(max_requests, rate * serve_seconds) requests arrive
+    (70% m,l,n in 1..16, 25% in 17..64 fitting 8192 slots, 5% 128x16x64;
+    entries U[0,255]); the server (continuous batching) is compared with the
+    plain path that runs each request alone, in arrival order, as soon as the
+    previous one is done.  Keys and masks of every shape are prepared first.
+    """
+    import torch
+
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm as H
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    pre = W.PAPER
+    ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
+    rates = [float(r) for r in args.rates.split(",")]
+    per_rate = {}
+    for r in rates:
+        cnt = int(max(20, min(args.max_requests, r * args.serve_seconds)))
+        per_rate[r] = W.serving_requests(cnt, r, ctx.S, seed=int(r))
+    shapes = sorted({s for v in per_rate.values() for _, s in v})
+    t0 = time.perf_counter()
+    ctx.hegmm_keygen(KEY_SEED, shapes, H.ALG_AUTO)
+    ctx.hegmm_prepare(shapes, H.ALG_AUTO)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    results = []
+    for r in rates:
+        arr = per_rate[r]
+        ops = []
+        for i, (_, (m, l, n)) in enumerate(arr):
+            A, Bm = W.matrices(m, l, n, *W.PAPER_RANGE, seed=i)
+            ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n), 5, 2 * i)
+            cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n), 5, 2 * i + 1)
+            ops.append((m, l, n, A, Bm, ca, cb))
+        torch.cuda.synchronize()
+        # continuous batching
+        srv = H.Server(ctx, max_batch=args.max_batch, streams=2)
+        tickets, late = [], []
+        s0 = time.perf_counter()
+        for (at, _), (m, l, n, _, _, ca, cb) in zip(arr, ops):
+            while time.perf_counter() - s0 < at:
+                srv.hegmm_server_poll()
+            tickets.append(srv.hegmm_server_submit(ca, cb, m, l, n))
+            late.append((time.perf_counter() - s0 - at) * 1e3)  # host delay before the request was queued
+            srv.hegmm_server_poll()
+        srv.hegmm_server_poll(wait=True)
+        span = time.perf_counter() - s0
+        st = srv.hegmm_server_stats_get()
+        ok = True
+        slat = []
+        for j, (t, (m, l, n, A, Bm, _, _)) in enumerate(zip(tickets, ops)):
+            c, lm = srv.hegmm_server_result(t)
+            slat.append(lm + late[j])  # from the scheduled arrival to completion
+            if j % 16 == 0:
+                ok &= bool((ctx.hegmm_decrypt(c, m, l, n).astype(np.int64) == (A @ Bm) % pre.t).all())
+        srv.close()
+        slat.sort()
+        # plain path: each request alone, in arrival order
+        lat = []
+        s0 = time.perf_counter()
+        for (at, _), (m, l, n, _, _, ca, cb) in zip(arr, ops):
+            while time.perf_counter() - s0 < at:
+                pass
+            c, _ = ctx.hegmm_matmul(ca, cb, m, l, n)
+            torch.cuda.current_stream().synchronize()
+            stream.synchronize()
+            lat.append((time.perf_counter() - s0 - at) * 1e3)
+        pspan = time.perf_counter() - s0
+        lat.sort()
+        results.append({
+            "rate_req_per_s": r, "requests": len(arr),
+            "served": {"throughput_req_per_s": len(arr) / span, "p50_ms": slat[len(slat) // 2],
+                       "p99_ms": slat[min(len(slat) - 1, int(0.99 * len(slat)))],
+                       "server_p50_ms": st["p50_ms"], "server_p99_ms": st["p99_ms"],
+                       "batches": st["batches"], "max_batch": st["max_batch"]},
+            "plain": {"throughput_req_per_s": len(arr) / pspan, "p50_ms": lat[len(lat) // 2],
+                      "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "decrypt_checked_ok": ok,
+        })
+        del ops
+    line = {
+        "metric": "HEGMM serving: throughput and p50/p99 latency vs Poisson arrival rate (N=16384 ring)",
+        "value": max(x["served"]["throughput_req_per_s"] for x in results), "unit": "req/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; Poisson arrivals; "
+                               "70% small (1..16), 25% medium (17..64, fitting), 5% 128x16x64; entries U[0,255]",
+                   "distinct_shapes": len(shapes), "setup_s_keys_and_masks": setup_s,
+                   "max_batch": args.max_batch, "streams": 2},
+        "rates": results,
+    }
+    print(json.dumps(line))
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 
@@ -213,11 +316,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch"],
-                    help="medium: the four medium-ring products (default); batch: 512 mixed shapes")
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve"],
+                    help="medium: the four medium-ring products (default); batch: 512 mixed shapes; "
+                         "serve: Poisson arrivals on the N=16384 ring")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--max-requests", type=int, default=1500)
+    ap.add_argument("--max-batch", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     import torch.distributed as dist

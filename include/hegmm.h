@@ -151,6 +151,13 @@ int hegmm_matmul(hegmm_ctx *ctx, const hegmm_ct *A, const hegmm_ct *B, int m, in
 int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                        const int *mln, int alg, hegmm_ct **C);
 
+/* Builds and caches the per-shape plan data of the listed products (the
+ * encoded diagonal masks of every linear transformation, Eq. lintrans), so
+ * that the first product of each shape does not pay for it.  Needs the
+ * shapes' keys.  Cached masks are released least recently used first when
+ * they exceed the context's mask budget (96 GiB). */
+int hegmm_prepare(hegmm_ctx *ctx, const int *shapes_mln, int n_shapes, int alg);
+
 /* ---- Serving: continuous batching of product requests ------------------
  * A server queues requests (two operand ciphertexts and a shape) and runs
  * them through the batch executor of hegmm_matmul_batch.  The caller's

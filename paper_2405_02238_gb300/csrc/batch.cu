@@ -49,9 +49,13 @@ struct ShapeData {
     unsigned long long last_use = 0;
     cudaEvent_t used = nullptr;      // recorded after the last launch that read the masks
     hegmm_opcount cnt{};
-    const u64 *mask_ptr(Ctx *c, const std::vector<int> &dst) const {
-        return masks + (size_t)mask_of.at(dst) * c->L * c->N;
-    }
+    // per operand s and iteration k, one entry per diagonal (ascending d):
+    // the index of its rotation in zs[s] (-1 for d = 0) and of its mask
+    struct DiagRef {
+        int zi, mask;
+    };
+    std::vector<std::vector<DiagRef>> dref[2];
+    const u64 *mask_at(Ctx *c, int mi) const { return masks + (size_t)mi * c->L * c->N; }
 };
 
 struct RotChunk {
@@ -223,6 +227,14 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
                     mlist.push_back(&sd->mask_of.find(d.dst)->first);
                 }
     sd->nmask = (int)mlist.size();
+    for (int s = 0; s < 2; s++) {
+        sd->dref[s].resize(hp.iters.size());
+        for (size_t k = 0; k < hp.iters.size(); k++)
+            for (auto &d : (s == 0 ? hp.iters[k].eps : hp.iters[k].omg)) {
+                const long long z = ((long long)d.d % S + S) % S;
+                sd->dref[s][k].push_back({z ? sd->zidx[s].at(z) : -1, sd->mask_of.at(d.dst)});
+            }
+    }
     sd->bytes = (size_t)sd->nmask * c->L * c->N * 8;
     evict_shapes(c, sd->bytes);
     sd->masks = dalloc(c, (size_t)sd->nmask * c->L * c->N);
@@ -235,6 +247,8 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
         return rc;
     }
     c->mask_bytes += sd->bytes;
+    mlist.clear();
+    sd->mask_of.clear();  // only the per-diagonal indices are needed from here on
     sd->last_use = ++c->bplan_clock;
     const long long ni = (long long)hp.iters.size(), ne = (long long)hp.extract.size();
     hegmm_opcount &ct = sd->cnt;
@@ -317,9 +331,12 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         int p, s, zi;
     };
     std::vector<RItem> ritems;
+    std::vector<std::array<int, 2>> rbase(B);  // first rotation item of (p, s)
     for (int p = 0; p < B; p++)
-        for (int s = 0; s < 2; s++)
+        for (int s = 0; s < 2; s++) {
+            rbase[p][s] = (int)ritems.size();
             for (int zi = 0; zi < (int)P->shp[p]->zs[s].size(); zi++) ritems.push_back({p, s, zi});
+        }
     std::vector<std::pair<int, int>> litems;
     for (int p = 0; p < B; p++)
         for (int k = 0; k < niter[p]; k++) litems.push_back({p, k});
@@ -382,8 +399,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             const ShapeData *sd = P->shp[p];
             for (int s = 0; s < 2; s++)
                 for (int k = 0; k < niter[p]; k++) {
-                    for (auto &d : (s == 0 ? sd->hp.iters[k].eps : sd->hp.iters[k].omg))
-                        if (((long long)d.d % c->S) == 0) terms.push_back({in_ct(p, s), sd->mask_ptr(c, d.dst)});
+                    for (const auto &dr : sd->dref[s][k])
+                        if (dr.zi < 0) terms.push_back({in_ct(p, s), sd->mask_at(c, dr.mask)});
                     offs.push_back((int)terms.size());
                     outs.push_back(out_ct(p, s, k));
                 }
@@ -400,11 +417,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         ch.cnt = std::min(RC, R - r0);
         std::vector<RotDesc> rd;
         std::vector<DivDesc> dd;
-        std::map<std::tuple<int, int, int>, int> slot;  // (p, s, zi) -> local slot
         for (int r = 0; r < ch.cnt; r++) {
             const RItem &it = ritems[r0 + r];
             const u64 g = galois_of(c, P->shp[it.p]->zs[it.s][it.zi]);
-            slot[std::make_tuple(it.p, it.s, it.zi)] = r;
             rd.push_back({P->D + ((size_t)2 * it.p + it.s) * nd0 * ne0 * N, c->keys[g], P->u + (size_t)r * 2 * ne0 * N,
                           (u32)g, 0u});
             for (int comp = 0; comp < 2; comp++) {
@@ -426,12 +441,11 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             for (int s = 0; s < 2; s++)
                 for (int k = 0; k < niter[p]; k++) {
                     const size_t t0 = terms.size();
-                    for (auto &d : (s == 0 ? sd->hp.iters[k].eps : sd->hp.iters[k].omg)) {
-                        const long long z = ((long long)d.d % c->S + c->S) % c->S;
-                        if (!z) continue;
-                        auto f = slot.find(std::make_tuple(p, s, sd->zidx[s].at(z)));
-                        if (f == slot.end()) continue;
-                        terms.push_back({P->rot + (size_t)f->second * 2 * lv0 * N, sd->mask_ptr(c, d.dst)});
+                    for (const auto &dr : sd->dref[s][k]) {
+                        if (dr.zi < 0) continue;
+                        const int gi = rbase[p][s] + dr.zi;  // global rotation item
+                        if (gi < r0 || gi >= r0 + ch.cnt) continue;
+                        terms.push_back({P->rot + (size_t)(gi - r0) * 2 * lv0 * N, sd->mask_at(c, dr.mask)});
                     }
                     if (terms.size() > t0) {
                         offs.push_back((int)terms.size());
@@ -712,6 +726,19 @@ int hegmm_matmul_batch(hegmm_ctx *h, int count, const hegmm_ct *const *A, const 
                        int alg, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, alg, C, nullptr);
+}
+
+int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {
+    if (!h || n_shapes < 0 || (n_shapes && !mln)) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    for (int i = 0; i < n_shapes; i++) {
+        const int a = resolve_alg(mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], alg, c->S);
+        if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+        ShapeData *sd;
+        int rc = get_shape(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], a, &sd);
+        if (rc) return rc;
+    }
+    return HEGMM_OK;
 }
 
 }  // extern "C"
