@@ -234,6 +234,7 @@ def run_serve(args):
         per_rate[r] = W.serving_requests(cnt, r, ctx.S, seed=int(r))
     shapes = sorted({s for v in per_rate.values() for _, s in v})
     t0 = time.perf_counter()
+    ctx.hegmm_set_budgets(mask_bytes=args.mask_gib << 30)
     ctx.hegmm_keygen(KEY_SEED, shapes, H.ALG_AUTO)
     ctx.hegmm_prepare(shapes, H.ALG_AUTO)
     torch.cuda.synchronize()
@@ -321,7 +322,8 @@ def main():
                          "serve: Poisson arrivals on the N=16384 ring")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--max-requests", type=int, default=1500)
+    ap.add_argument("--max-requests", type=int, default=1000)
+    ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":

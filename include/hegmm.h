@@ -158,6 +158,13 @@ int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, cons
  * they exceed the context's mask budget (96 GiB). */
 int hegmm_prepare(hegmm_ctx *ctx, const int *shapes_mln, int n_shapes, int alg);
 
+/* Memory budgets of a context (0 leaves a value unchanged): mask_bytes caps
+ * the resident per-shape masks (default 96 GiB, least recently used shapes
+ * are released first), plan_bytes the workspace kept by cached batch plans
+ * (default 48 GiB), chunk_bytes the scratch of one chunked stage of a batch
+ * (default 1 GiB; smaller chunks mean more launches). */
+int hegmm_set_budgets(hegmm_ctx *ctx, uint64_t mask_bytes, uint64_t plan_bytes, uint64_t chunk_bytes);
+
 /* ---- Serving: continuous batching of product requests ------------------
  * A server queues requests (two operand ciphertexts and a shape) and runs
  * them through the batch executor of hegmm_matmul_batch.  The caller's
@@ -175,7 +182,9 @@ typedef struct hegmm_server hegmm_server;
 typedef struct {
     int max_batch;       /* products per batch (0 = 64) */
     int streams;         /* device streams that batches rotate over (0 = 2, at most 8) */
-    uint64_t mem_budget; /* bytes of batch workspace in flight (0 = 16 GiB) */
+    uint64_t mem_budget; /* device workspace the server preallocates, split evenly over its
+                            streams (0 = 16 GiB); a batch admits requests while their estimated
+                            workspace fits one stream's share */
 } hegmm_server_opts;
 
 typedef struct {

@@ -48,6 +48,7 @@ struct ShapeData {
     int refs = 0;                    // batch plans that reference these masks
     unsigned long long last_use = 0;
     cudaEvent_t used = nullptr;      // recorded after the last launch that read the masks
+    cudaEvent_t ready = nullptr;     // recorded when the masks are encoded
     hegmm_opcount cnt{};
     // per operand s and iteration k, one entry per diagonal (ascending d):
     // the index of its rotation in zs[s] (-1 for d = 0) and of its mask
@@ -99,6 +100,32 @@ struct BatchPlan {
     unsigned long long last_use = 0;
 };
 
+// Device memory of a plan: from the context's arena when one is set (a
+// serving stream's preallocated workspace, reset when its batch retires),
+// else a stream-ordered allocation owned by the plan.
+static void *plan_alloc(Ctx *c, BatchPlan *P, size_t bytes) {
+    bytes = (std::max<size_t>(bytes, 8) + 255) & ~(size_t)255;
+    if (c->arena && c->arena_used + bytes <= c->arena_cap) {
+        void *p = c->arena + c->arena_used;
+        c->arena_used += bytes;
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    P->allocs.push_back(p);
+    return p;
+}
+
+template <typename T>
+static T *plan_upload(Ctx *c, BatchPlan *P, const std::vector<T> &v) {
+    T *p = (T *)plan_alloc(c, P, v.size() * sizeof(T));
+    if (p && !v.empty()) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st);
+    return p;
+}
+
 static void free_bplan(Ctx *c, BatchPlan *P) {
     std::set<ShapeData *> uniq(P->shp.begin(), P->shp.end());
     for (ShapeData *s : uniq) s->refs--;
@@ -111,6 +138,7 @@ static void free_shape(Ctx *c, ShapeData *s) {
         cudaStreamWaitEvent(c->st, s->used, 0);  // the masks may have been read on another stream
         cudaEventDestroy(s->used);
     }
+    if (s->ready) cudaEventDestroy(s->ready);
     dfree(c, s->masks);
     c->mask_bytes -= s->bytes;
     delete s;
@@ -145,10 +173,6 @@ static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int>
     const int Bm = 256;
     u64 *m = dalloc(c, (size_t)Bm * N);
     if (!m) return set_err(c, HEGMM_ENOMEM, "mask encode");
-    if (!c->d_slot_pos0) {
-        c->d_slot_pos0 = upload(c, c->slot_pos0);
-        if (!c->d_slot_pos0) return set_err(c, HEGMM_ENOMEM, "slot table");
-    }
     int rc;
     for (size_t b0 = 0; b0 < dsts.size(); b0 += Bm) {
         const int nb = (int)std::min<size_t>(Bm, dsts.size() - b0);
@@ -240,7 +264,11 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
     sd->masks = dalloc(c, (size_t)sd->nmask * c->L * c->N);
     if (!sd->masks) return fail(HEGMM_ENOMEM, "plan masks");
     int rc = encode_masks(c, c->L, mlist, scale, sd->masks);
-    if (!rc && cudaStreamSynchronize(c->st) != cudaSuccess) rc = cuda_check(c, "mask encode");  // masks serve every stream
+    if (!rc) {
+        // plans on other streams wait for this event before reading the masks
+        cudaEventCreateWithFlags(&sd->ready, cudaEventDisableTiming);
+        cudaEventRecord(sd->ready, c->st);
+    }
     if (rc) {
         dfree(c, sd->masks);
         delete sd;
@@ -295,7 +323,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             P->shp.assign(held.begin(), held.end());  // release what this plan holds
             return fail_rc(rc);
         }
-        if (held.insert(sd).second) sd->refs++;  // pinned while this plan exists
+        if (held.insert(sd).second) {
+            sd->refs++;  // pinned while this plan exists
+            if (sd->ready) cudaStreamWaitEvent(c->st, sd->ready, 0);
+        }
         P->shp.push_back(sd);
         add_counts(P->cnt, sd->cnt);
     }
@@ -362,9 +393,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                  o_eD = take((size_t)std::max(E, 1) * nd1 * ne1 * N), o_eu = take((size_t)std::max(X, 1) * 2 * ne1 * N),
                  o_erot = take((size_t)std::max(X, 1) * 2 * lv1 * N);
     P->ws_bytes = off * 8;
-    P->ws = dalloc(c, off);
+    P->ws = (u64 *)plan_alloc(c, P, off * 8);
     if (!P->ws) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch workspace"));
-    P->allocs.push_back(P->ws);
     u64 *W = P->ws;
     P->in = W + o_in;
     P->xc = W + o_xc;
@@ -385,11 +415,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
     P->erot = W + o_erot;
     auto in_ct = [&](int p, int s) { return P->in + ((size_t)2 * p + s) * 2 * lv0 * N; };
     auto out_ct = [&](int p, int s, int k) { return P->outs + ((size_t)obase[p] + s * niter[p] + k) * 2 * lv0 * N; };
-    auto keep = [&](void *ptr) {
-        if (!ptr) return false;
-        P->allocs.push_back(ptr);
-        return true;
-    };
+    auto keep = [&](void *ptr) { return ptr != nullptr; };
     // identity (d = 0) terms over all outputs; this launch also zero-initialises
     {
         std::vector<LtTerm> terms;
@@ -405,9 +431,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                     outs.push_back(out_ct(p, s, k));
                 }
         }
-        P->d_id_terms = upload(c, terms);
-        P->d_id_off = upload(c, offs);
-        P->d_all_outs = upload(c, outs);
+        P->d_id_terms = plan_upload(c, P, terms);
+        P->d_id_off = plan_upload(c, P, offs);
+        P->d_all_outs = plan_upload(c, P, outs);
         if (!keep(P->d_id_terms) || !keep(P->d_id_off) || !keep(P->d_all_outs))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
@@ -454,11 +480,11 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                 }
         }
         ch.nout = (int)outs.size();
-        ch.d_rots = upload(c, rd);
-        ch.d_div = upload(c, dd);
-        ch.d_terms = upload(c, terms);
-        ch.d_off = upload(c, offs);
-        ch.d_outs = upload(c, outs);
+        ch.d_rots = plan_upload(c, P, rd);
+        ch.d_div = plan_upload(c, P, dd);
+        ch.d_terms = plan_upload(c, P, terms);
+        ch.d_off = plan_upload(c, P, offs);
+        ch.d_outs = plan_upload(c, P, outs);
         if (!keep(ch.d_rots) || !keep(ch.d_div) || !keep(ch.d_terms) || !keep(ch.d_off) || !keep(ch.d_outs))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->rchunks.push_back(ch);
@@ -472,7 +498,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             dd[b].out = P->ms + (size_t)b * lv1 * N;
             dd[b].g = 1;
         }
-        P->d_msdiv = upload(c, dd);
+        P->d_msdiv = plan_upload(c, P, dd);
         if (!keep(P->d_msdiv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // tensor + relinearisation chunks
@@ -512,10 +538,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             sv.back().count++;
         }
         ch.nsum = (int)sv.size();
-        ch.d_tens = upload(c, tv);
-        ch.d_rot = upload(c, rd);
-        ch.d_div = upload(c, dd);
-        ch.d_sum = upload(c, sv);
+        ch.d_tens = plan_upload(c, P, tv);
+        ch.d_rot = plan_upload(c, P, rd);
+        ch.d_div = plan_upload(c, P, dd);
+        ch.d_sum = plan_upload(c, P, sv);
         if (!keep(ch.d_tens) || !keep(ch.d_rot) || !keep(ch.d_div) || !keep(ch.d_sum))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->lchunks.push_back(ch);
@@ -541,8 +567,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                 }
             }
         }
-        P->d_erot = upload(c, rd);
-        P->d_ediv = upload(c, dd);
+        P->d_erot = plan_upload(c, P, rd);
+        P->d_ediv = plan_upload(c, P, dd);
         if (!keep(P->d_erot) || !keep(P->d_ediv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // final sums (the caller's result pointers are filled in per call)
@@ -554,16 +580,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         s.count = next[p];
         P->final_tmpl.push_back(s);
     }
-    void *df = nullptr, *dp = nullptr;
-    if (cudaMallocAsync(&df, sizeof(SumDesc) * B, c->st) != cudaSuccess ||
-        cudaMallocAsync(&dp, sizeof(u64 *) * 2 * B, c->st) != cudaSuccess) {
-        cudaGetLastError();
-        return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
-    }
-    P->d_final = (SumDesc *)df;
-    P->d_inptr = (u64 **)dp;
-    keep(df);
-    keep(dp);
+    P->d_final = (SumDesc *)plan_alloc(c, P, sizeof(SumDesc) * B);
+    P->d_inptr = (u64 **)plan_alloc(c, P, sizeof(u64 *) * 2 * B);
+    if (!P->d_final || !P->d_inptr) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     int rc = cuda_check(c, "batch plan");
     if (rc) return fail_rc(rc);
     *out = P;

@@ -315,7 +315,10 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         c->slot_pos1[j] = (int)brev_bits((u32)((ng - 1) / 2), c->logN);
         g = g * 5 % two_n;
     }
-    return HEGMM_OK;
+    c->d_slot_pos0 = upload(c, c->slot_pos0);
+    if (!c->d_slot_pos0) return set_err(c, HEGMM_ENOMEM, "slot table");
+    cudaStreamSynchronize(c->st);
+    return cuda_check(c, "slot table");
 }
 
 u64 galois_of(Ctx *c, long long z) {
@@ -784,6 +787,14 @@ int hegmm_kernel_reset(hegmm_ctx *h) {
         h->c.stat_bytes[k] = 0;
         h->c.stat_work[k] = 0;
     }
+    return HEGMM_OK;
+}
+
+int hegmm_set_budgets(hegmm_ctx *h, uint64_t mask_bytes, uint64_t plan_bytes, uint64_t chunk_bytes) {
+    if (!h) return HEGMM_EINVAL;
+    if (mask_bytes) h->c.mask_budget = mask_bytes;
+    if (plan_bytes) h->c.plan_cache_budget = plan_bytes;
+    if (chunk_bytes) h->c.ws_budget = std::max<uint64_t>(chunk_bytes, (uint64_t)1 << 24);
     return HEGMM_OK;
 }
 

@@ -147,6 +147,8 @@ struct Ctx {
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
+    char *arena = nullptr;                     // when set, plan memory is carved from here
+    size_t arena_cap = 0, arena_used = 0;
     size_t plan_cache_budget = (size_t)48 << 30;  // workspace kept by cached batch plans
     u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
     std::map<int, u64 *> crt;        // level -> CRT-to-t table

@@ -60,6 +60,8 @@ struct hegmm_server {
     hegmm_server_opts o;
     std::vector<cudaStream_t> streams;
     std::vector<int> busy;
+    std::vector<char *> arena;  // per stream: workspace of its current batch
+    size_t arena_cap = 0;
     cudaEvent_t inputs_ready = nullptr;
     std::deque<hg::SrvReq> queue;
     std::vector<hg::SrvBatch> flight;
@@ -120,8 +122,8 @@ static int admit(hegmm_server *s) {
         size_t bytes = 2 * c->ws_budget;  // chunk scratch of one batch
         while (!s->queue.empty() && (int)reqs.size() < s->o.max_batch) {
             const SrvReq &r = s->queue.front();
-            const bool fits = s->inflight_bytes + bytes + r.est <= s->o.mem_budget;
-            if (!fits && !(reqs.empty() && s->flight.empty())) break;
+            const bool fits = bytes + r.est <= s->arena_cap;  // the stream's arena
+            if (!fits && !reqs.empty()) break;
             bytes += r.est;
             reqs.push_back(r);
             s->queue.pop_front();
@@ -137,6 +139,9 @@ static int admit(hegmm_server *s) {
         std::vector<hegmm_ct *> outs(reqs.size(), nullptr);
         cudaStream_t old = c->st;
         c->st = s->streams[st];
+        c->arena = s->arena[st];
+        c->arena_cap = s->arena_cap;
+        c->arena_used = 0;
         cudaStreamWaitEvent(c->st, s->inputs_ready, 0);
         BatchPlan *plan = nullptr;
         int rc = HEGMM_OK;
@@ -160,6 +165,7 @@ static int admit(hegmm_server *s) {
             plans.push_back(plan);
             for (size_t k = 0; k < g.second.size(); k++) outs[g.second[k]] = o[k];
         }
+        c->arena = nullptr;
         SrvBatch sb;
         sb.stream = st;
         sb.bytes = bytes;
@@ -207,14 +213,20 @@ int hegmm_server_create(hegmm_ctx *h, const hegmm_server_opts *opts, hegmm_serve
         if (opts->mem_budget > 0) o.mem_budget = opts->mem_budget;
     }
     s->o = o;
+    s->arena_cap = (size_t)(o.mem_budget / (uint64_t)o.streams) & ~(size_t)255;
     for (int i = 0; i < o.streams; i++) {
         cudaStream_t st;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        void *a = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&a, s->arena_cap) != cudaSuccess) {
+            cudaGetLastError();
+            for (size_t k = 0; k < s->arena.size(); k++) cudaFree(s->arena[k]);
             delete s;
-            return cuda_check(c, "server streams");
+            return set_err(c, HEGMM_ENOMEM, "server streams / workspace");
         }
         s->streams.push_back(st);
         s->busy.push_back(0);
+        s->arena.push_back((char *)a);
     }
     cudaEventCreateWithFlags(&s->inputs_ready, cudaEventDisableTiming);
     cudaStreamSynchronize(c->st);  // keys and tables are complete before other streams use them
@@ -299,6 +311,7 @@ void hegmm_server_destroy(hegmm_server *s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
+    for (char *a : s->arena) cudaFree(a);
     cudaEventDestroy(s->inputs_ready);
     delete s;
 }

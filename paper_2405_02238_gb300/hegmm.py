@@ -106,6 +106,7 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_double)]),
     "hegmm_peak_butterflies": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
     "hegmm_prepare": (ctypes.c_int, [vp, intp, ctypes.c_int, ctypes.c_int]),
+    "hegmm_set_budgets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]),
     "hegmm_server_create": (ctypes.c_int, [vp, ctypes.POINTER(hegmm_server_opts), ctypes.POINTER(vp)]),
     "hegmm_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_uint64)]),
@@ -235,6 +236,9 @@ class Context:
     def hegmm_prepare(self, shapes: Sequence[Tuple[int, int, int]], alg: int = ALG_AUTO):
         arr = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
         self._check(self.lib.hegmm_prepare(self.h, arr.ctypes.data_as(intp), len(shapes), alg), "prepare")
+
+    def hegmm_set_budgets(self, mask_bytes: int = 0, plan_bytes: int = 0, chunk_bytes: int = 0):
+        self._check(self.lib.hegmm_set_budgets(self.h, mask_bytes, plan_bytes, chunk_bytes), "set_budgets")
 
     def hegmm_keygen_rotations(self, zs: Sequence[int]):
         arr = np.ascontiguousarray(np.array(zs, dtype=np.int32))
