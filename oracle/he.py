@@ -87,6 +87,9 @@ def lib():
         L.or_tensor.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
         L.or_mult_relin.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p, u64p]
         L.or_modswitch.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.or_ks_raw.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_uint64, u64p, u64p]
+        L.or_pq_lift.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
+        L.or_pq_mac.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p, u64p]
         L.or_to_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p]
         L.or_to_coeff.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p]
         _lib = L
@@ -359,6 +362,61 @@ class Oracle:
         lib().or_automorph(self.ctx, len(prime_idx), PINT(prime_idx), P(np.ascontiguousarray(a)), g, P(out))
         return out
 
+    # ------------------------------------- key switching kept in the basis PQ
+    # The inner product of a key switch produces u over the extended basis
+    # (q_0..q_{lv-1}, p_0..p_{K-1}); ModDown divides by P = prod p_k with
+    # t-corrected rounding.  Because ModDown(u + P x) = ModDown(u) + x holds
+    # exactly, sums of key-switched terms (with plaintext factors) can be
+    # formed over PQ and divided once ("double hoisting").
+
+    def ext_primes(self, lv: int) -> List[int]:
+        return list(range(lv)) + [self.L + k for k in range(self.K)]
+
+    def ks_raw(self, D: np.ndarray, tag: int) -> np.ndarray:
+        """u = <tau_g(D), evk_g> before ModDown, [2][lv+K][N] coefficient form.
+
+        D is the ModUp of c1 at its level; tag is the Galois element, or 0
+        for the relinearisation key (no automorphism)."""
+        nd, ne, _ = D.shape
+        lv = ne - self.K
+        u = np.zeros((2, ne, self.N), dtype=np.uint64)
+        g = 1 if tag == 0 else tag
+        lib().or_ks_raw(self.ctx, lv, P(np.ascontiguousarray(D)), g, P(self.keys[tag]), P(u))
+        self.counts["ksw_raw"] = self.counts.get("ksw_raw", 0) + 1
+        return u
+
+    def pq_lift(self, x: np.ndarray) -> np.ndarray:
+        """P x on the chain primes, 0 on the special primes: [lv+K][N]."""
+        lv = x.shape[0]
+        out = np.zeros((lv + self.K, self.N), dtype=np.uint64)
+        lib().or_pq_lift(self.ctx, lv, P(np.ascontiguousarray(x)), P(out))
+        return out
+
+    def pq_add(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        ne = a.shape[0]
+        out = np.empty_like(a)
+        for e, gp in enumerate(self.ext_primes(ne - self.K)):
+            out[e] = (a[e] + b[e]) % np.uint64(self.primes[gp])
+        return out
+
+    def pq_mac(self, acc: np.ndarray, a: np.ndarray, m_eval: np.ndarray) -> None:
+        """acc += m a over the extended basis (m_eval from plaintext_eval_pq)."""
+        lv = a.shape[0] - self.K
+        lib().or_pq_mac(self.ctx, lv, P(np.ascontiguousarray(a)), P(np.ascontiguousarray(m_eval)), P(acc))
+
+    def plaintext_eval_pq(self, m: np.ndarray, lv: int) -> np.ndarray:
+        """Plaintext residues over the extended basis of level lv, NTT form."""
+        ext = self.ext_primes(lv)
+        r = np.empty((len(ext), self.N), dtype=np.uint64)
+        for e, gp in enumerate(ext):
+            r[e] = (np.asarray(m, dtype=object) % self.primes[gp]).astype(np.uint64)
+        lib().or_to_eval(self.ctx, len(ext), PINT(ext), P(r))
+        return r
+
+    def moddown_pair(self, acc: np.ndarray) -> np.ndarray:
+        lv = acc.shape[1] - self.K
+        return np.stack([self.moddown(acc[0], lv), self.moddown(acc[1], lv)])
+
 
 # --------------------------------------------------------------------------
 # HEGMM on ciphertexts (Algorithms 1 and 2)
@@ -380,8 +438,19 @@ def mask_scale(o: Oracle) -> int:
 class HEGMM:
     """Runs a plan of ``oracle.slots`` on ciphertexts, op by op."""
 
-    def __init__(self, o: Oracle):
+    MODES = ("single", "double")
+
+    def __init__(self, o: Oracle, mode: str = "single"):
+        """mode "single": every key switch ends in its own ModDown, as the
+        HE operations Rot, CMult, Mult and Add compose (the paper's cost
+        model).  mode "double": the sums of key-switched terms (each linear
+        transformation, the HE-Add of the per-iteration products, the
+        extraction sum) are formed over the extended basis PQ and take one
+        ModDown each; decrypts to the same product, with lower noise."""
+        if mode not in self.MODES:
+            raise ValueError(mode)
         self.o = o
+        self.mode = mode
         self._mask_cache: Dict[Tuple, np.ndarray] = {}
 
     def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
@@ -406,8 +475,39 @@ class HEGMM:
         ctB = o.encrypt(o.encode(plan.b_layout(B) % o.t), seed, streams[1])
         return ctA, ctB
 
+    def mask_eval_pq(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
+        key = ("pq", tuple(dsts), scale, lv)
+        if key not in self._mask_cache:
+            v = np.zeros(self.o.S, dtype=np.int64)
+            v[dsts] = scale
+            self._mask_cache[key] = self.o.plaintext_eval_pq(self.o.encode(v), lv)
+        return self._mask_cache[key]
+
+    def lt_double(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
+        """Eq. lintrans with one ModUp of c1 and one ModDown per component:
+        y = ModDown(sum_d m_d (.) v_d) over PQ, v_0 = P ct and, for d != 0,
+        v_d = (u0_d + P tau_d(c0), u1_d) with u_d the inner product of the
+        hoisted key switch of tau_d(c1)."""
+        o = self.o
+        lv = ct.shape[1]
+        acc = np.zeros((2, lv + o.K, o.N), dtype=np.uint64)
+        D = o.modup(ct[1])
+        for d in sorted(diags):
+            m = self.mask_eval_pq(diags[d], scale, lv)
+            if d % o.S == 0:
+                v = [o.pq_lift(ct[0]), o.pq_lift(ct[1])]
+            else:
+                g = o.galois(d)
+                u = o.ks_raw(D, g)
+                v = [o.pq_add(u[0], o.pq_lift(o.automorph(ct[0], g, list(range(lv))))), u[1]]
+            for comp in range(2):
+                o.pq_mac(acc[comp], v[comp], m)
+        return o.moddown_pair(acc)
+
     def lt(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
         """sum_d u_d (.) Rot(ct, d), diagonals in ascending d (Eq. lintrans)."""
+        if self.mode == "double":
+            return self.lt_double(ct, diags, scale)
         lv = ct.shape[1]
         acc = None
         for d in sorted(diags):
@@ -422,14 +522,38 @@ class HEGMM:
             o.add_galois_key(g)
         scale = mask_scale(o)
         C = None
+        acc = None
         for e, om in plan.iters:
             a = self.lt(ctA, e, scale)
             b = self.lt(ctB, om, scale)
             for _ in range(o.pre.ms_drop):
                 a = o.modswitch(a)
                 b = o.modswitch(b)
+            if self.mode == "double":
+                # HE-Mult without its ModDown, summed over PQ (Eq. of C)
+                d = o.tensor(a, b)
+                u = o.ks_raw(o.modup(d[2]), 0)
+                v = np.stack([o.pq_add(u[0], o.pq_lift(d[0])), o.pq_add(u[1], o.pq_lift(d[1]))])
+                acc = v if acc is None else np.stack([o.pq_add(acc[0], v[0]), o.pq_add(acc[1], v[1])])
+                continue
             prod = o.mult_relin(a, b)
             C = prod if C is None else o.add(C, prod)
+        if self.mode == "double":
+            C = o.moddown_pair(acc)
+            if not plan.extract:
+                return C
+            lv = C.shape[1]
+            D = o.modup(C[1])
+            ex = None
+            for z in plan.extract:
+                if z % o.S == 0:
+                    v = np.stack([o.pq_lift(C[0]), o.pq_lift(C[1])])
+                else:
+                    g = o.galois(z)
+                    u = o.ks_raw(D, g)
+                    v = np.stack([o.pq_add(u[0], o.pq_lift(o.automorph(C[0], g, list(range(lv))))), u[1]])
+                ex = v if ex is None else np.stack([o.pq_add(ex[0], v[0]), o.pq_add(ex[1], v[1])])
+            return o.add(C, o.moddown_pair(ex))
         out = C
         for z in plan.extract:
             out = o.add(out, o.rotate(C, z))

@@ -609,6 +609,62 @@ void or_modswitch(const or_ctx *c, int lv, const u64 *ct, u64 *out) {
     divide_round_t(c, lv, lv - 1, pidx, ct + (size_t)lv * N, out + (size_t)(lv - 1) * N);
 }
 
+/* ------------------------------------------------------------------ */
+/* Double-hoisted linear transformation (an evaluation order of         */
+/* Eq. lintrans that defers ModDown to the sum):                        */
+/*   y = ( ModDown( sum_d m_d (u0_d + P tau_d(c0)) ),                   */
+/*         ModDown( sum_d m_d u1_d ) )                                  */
+/* with u_d the inner product of the rotation by d before ModDown, and  */
+/* the d = 0 term m_0 P c.  Everything below is over the extended basis */
+/* of level lv (q_0..q_{lv-1}, p_0..p_{K-1}).                           */
+/* ------------------------------------------------------------------ */
+
+/* Hoisted key switch without its ModDown: D is the ModUp of c1 (or_modup
+ * layout, coefficient form); the automorphism tau_g is applied to every
+ * digit (skipped for g = 1, the relinearisation key), then the inner
+ * product with evk.  u [2][lv+K][N] (coefficient form). */
+void or_ks_raw(const or_ctx *c, int lv, const u64 *D, u64 g, const u64 *evk_eval, u64 *u) {
+    int N = c->N, ne = lv + c->K, nd = digits_at(c, lv), pidx[MAXP];
+    for (int e = 0; e < ne; e++) pidx[e] = ext_prime(c, lv, e);
+    if (g == 1) { or_ks_inner(c, lv, D, evk_eval, u); return; }
+    u64 *Dg = (u64 *)malloc(sizeof(u64) * (size_t)nd * ne * N);
+    for (int j = 0; j < nd; j++) or_automorph(c, ne, pidx, D + (size_t)j * ne * N, g, Dg + (size_t)j * ne * N);
+    or_ks_inner(c, lv, Dg, evk_eval, u);
+    free(Dg);
+}
+
+/* P x on the chain primes, 0 on the special primes: out [lv+K][N]. */
+void or_pq_lift(const or_ctx *c, int lv, const u64 *x, u64 *out) {
+    int N = c->N, ne = lv + c->K;
+    for (int e = 0; e < ne; e++) {
+        u64 *o = out + (size_t)e * N;
+        if (e >= lv) {
+            for (int k = 0; k < N; k++) o[k] = 0;
+            continue;
+        }
+        u64 q = c->prime[e], Pm = 1;
+        for (int k = 0; k < c->K; k++) Pm = mulmod(Pm, c->prime[c->L + k] % q, q);
+        for (int k = 0; k < N; k++) o[k] = mulmod(x[(size_t)e * N + k], Pm, q);
+    }
+}
+
+/* acc += m * a over the extended basis; m_eval is or_ntt of the mask
+ * residues over the extended primes (coefficient-form a and acc). */
+void or_pq_mac(const or_ctx *c, int lv, const u64 *a, const u64 *m_eval, u64 *acc) {
+    int N = c->N, ne = lv + c->K;
+    u64 *f = (u64 *)malloc(sizeof(u64) * N);
+    for (int e = 0; e < ne; e++) {
+        int gp = ext_prime(c, lv, e);
+        u64 q = c->prime[gp];
+        memcpy(f, a + (size_t)e * N, sizeof(u64) * N);
+        or_ntt(c, gp, f);
+        for (int k = 0; k < N; k++) f[k] = mulmod(f[k], m_eval[(size_t)e * N + k], q);
+        or_intt(c, gp, f);
+        for (int k = 0; k < N; k++) acc[(size_t)e * N + k] = addmod(acc[(size_t)e * N + k], f[k], q);
+    }
+    free(f);
+}
+
 /* In-place forward / inverse NTT of np residue polynomials (global prime indices). */
 void or_to_eval(const or_ctx *c, int np, const int *pidx, u64 *a) {
     for (int r = 0; r < np; r++) or_ntt(c, pidx[r], a + (size_t)r * c->N);
