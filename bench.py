@@ -227,6 +227,7 @@ def run_serve(args):
     stream = torch.cuda.Stream(device=dev)
     pre = W.PAPER
     ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if args.ks_mode == "double" else H.KS_SINGLE)
     rates = [float(r) for r in args.rates.split(",")]
     per_rate = {}
     for r in rates:
@@ -301,7 +302,7 @@ def run_serve(args):
         "config": {"workload": "serving: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; Poisson arrivals; "
                                "70% small (1..16), 25% medium (17..64, fitting), 5% 128x16x64; entries U[0,255]",
                    "distinct_shapes": len(shapes), "setup_s_keys_and_masks": setup_s,
-                   "max_batch": args.max_batch, "streams": 2},
+                   "max_batch": args.max_batch, "streams": 2, "keyswitch_mode": args.ks_mode},
         "rates": results,
     }
     print(json.dumps(line))
@@ -325,6 +326,8 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1000)
     ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--ks-mode", default="double", choices=["double", "single"],
+                    help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -349,6 +352,8 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     ctx = H.Context.from_preset(PRESET, stream=stream.cuda_stream)
+    ks_code = {"double": H.KS_DOUBLE, "single": H.KS_SINGLE}
+    ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
     prods = []
     if args.workload == "batch":
         for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
@@ -452,6 +457,26 @@ def main():
     value = per_step * world / (ms / 1e3)
     stats = ctx.hegmm_kernel_stats()
 
+    # the other key-switch evaluation order on the same products, for comparison
+    other = "single" if args.ks_mode == "double" else "double"
+    ctx.hegmm_set_keyswitch_mode(ks_code[other])
+    outs = step()
+    for (m, l, n, alg, A, Bm), c in zip(prods, outs):
+        got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
+        assert (got == (A @ Bm) % PRESET.t).all(), "wrong product (%s mode)" % other
+    del outs
+    o_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        o_ev[k][0].record(stream)
+        outs = step()
+        o_ev[k][1].record(stream)
+        del outs
+    torch.cuda.synchronize()
+    other_ms = sum(a.elapsed_time(b) for a, b in o_ev) / args.steps
+    ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
+
     # e2e: host ciphertexts (coefficient domain, pinned) -> import -> product -> export
     host_in = []
     for (m, l, n, alg, _, _), (ca, cb) in zip(prods, ops):
@@ -520,7 +545,10 @@ def main():
         "metric": METRIC_BATCH if batch else METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": (batch_config if batch else workload_config)({"parallelism": "replicas" if world > 1 else "single-gpu"}),
+        "config": (batch_config if batch else workload_config)({"parallelism": "replicas" if world > 1 else "single-gpu",
+                                                                "keyswitch_mode": args.ks_mode}),
+        "other_keyswitch_mode": {"mode": other, "value": per_step * world / (other_ms / 1e3), "unit": UNIT,
+                                 "ms_per_step": other_ms},
         "keyswitches_per_s": ksw_per_step * world / (ms / 1e3),
         "paper_rotations_per_step": paper_rot_per_step,
         "keyswitches_per_step": ksw_per_step,

@@ -151,6 +151,23 @@ int hegmm_matmul(hegmm_ctx *ctx, const hegmm_ct *A, const hegmm_ct *B, int m, in
 int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                        const int *mln, int alg, hegmm_ct **C);
 
+/* How products (hegmm_matmul, hegmm_matmul_batch, the server) evaluate their
+ * sums of key switches.  The results decrypt to the same matrix product.
+ *   HEGMM_KS_SINGLE (default): every rotation and relinearisation ends in its own
+ *     ModDown, as composing the paper's HE-Rot, HE-CMult, HE-Mult and HE-Add
+ *     (Algorithms 1 and 2, Section 2.1) does; bit-identical to those
+ *     operations called one by one.
+ *   HEGMM_KS_DOUBLE: each linear transformation (Eq. lintrans),
+ *     the HE-Add over the iterations' products and the extraction sum are
+ *     formed over the extended basis PQ from the key-switch inner products
+ *     (with P tau(c0), P d0, P d1 folded in) and divided by P once
+ *     ("double hoisting"; ModDown(u + P x) = ModDown(u) + x).  Fewer
+ *     ModDowns, lower noise.
+ * Applies to products started after the call.  Errors: HEGMM_EINVAL. */
+#define HEGMM_KS_SINGLE 0
+#define HEGMM_KS_DOUBLE 1
+int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
+
 /* Builds and caches the per-shape plan data of the listed products (the
  * encoded diagonal masks of every linear transformation, Eq. lintrans), so
  * that the first product of each shape does not pay for it.  Needs the

@@ -56,7 +56,8 @@ struct ShapeData {
         int zi, mask;
     };
     std::vector<std::vector<DiagRef>> dref[2];
-    const u64 *mask_at(Ctx *c, int mi) const { return masks + (size_t)mi * c->L * c->N; }
+    // masks are kept over all L + K primes (the extended basis of level L)
+    const u64 *mask_at(Ctx *c, int mi) const { return masks + (size_t)mi * (c->L + c->K) * c->N; }
 };
 
 struct RotChunk {
@@ -79,11 +80,15 @@ struct RelinChunk {
 struct BatchPlan {
     std::vector<ShapeData *> shp;
     int B = 0, lv0 = 0, lv1 = 0, O = 0, E = 0, X = 0;
+    int dbl = 0;  // sums of key switches kept over PQ (one ModDown per sum)
     size_t ws_bytes = 0;
     u64 *ws = nullptr;
     u64 *in = nullptr, *xc = nullptr, *D = nullptr, *u = nullptr, *rot = nullptr, *outs = nullptr, *ms = nullptr;
     u64 *d3 = nullptr, *rxc = nullptr, *rD = nullptr, *ru = nullptr, *rout = nullptr, *cacc = nullptr;
     u64 *exc = nullptr, *eD = nullptr, *eu = nullptr, *erot = nullptr;
+    u64 *acc = nullptr, *cpq = nullptr, *xacc = nullptr, *xout = nullptr;  // PQ accumulators, double mode
+    DivDesc *d_ltdiv = nullptr, *d_cdiv = nullptr, *d_xdiv = nullptr;
+    SumDesc *d_xsum = nullptr;
     LtTerm *d_id_terms = nullptr;
     int *d_id_off = nullptr;
     u64 **d_all_outs = nullptr;
@@ -167,7 +172,7 @@ static void evict_shapes(Ctx *c, size_t incoming) {
 }
 
 // Encode 0/1 masks (value `scale` on the listed slots) into Montgomery NTT
-// form over q_0..q_{lv-1}: out [count][lv][N].
+// form over the first np primes of the context: out [count][np][N].
 static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int> *> &dsts, u64 scale, u64 *out) {
     const int N = c->N;
     const int Bm = 256;
@@ -259,11 +264,12 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
                 sd->dref[s][k].push_back({z ? sd->zidx[s].at(z) : -1, sd->mask_of.at(d.dst)});
             }
     }
-    sd->bytes = (size_t)sd->nmask * c->L * c->N * 8;
+    const int nm = c->L + c->K;
+    sd->bytes = (size_t)sd->nmask * nm * c->N * 8;
     evict_shapes(c, sd->bytes);
-    sd->masks = dalloc(c, (size_t)sd->nmask * c->L * c->N);
+    sd->masks = dalloc(c, (size_t)sd->nmask * nm * c->N);
     if (!sd->masks) return fail(HEGMM_ENOMEM, "plan masks");
-    int rc = encode_masks(c, c->L, mlist, scale, sd->masks);
+    int rc = encode_masks(c, nm, mlist, scale, sd->masks);
     if (!rc) {
         // plans on other streams wait for this event before reading the masks
         cudaEventCreateWithFlags(&sd->ready, cudaEventDisableTiming);
@@ -307,9 +313,10 @@ static void add_counts(hegmm_opcount &a, const hegmm_opcount &b) {
 }
 
 // shapes: B entries of (m, l, n, resolved alg)
-static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, BatchPlan **out) {
+static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, BatchPlan **out) {
     const int N = c->N;
     BatchPlan *P = new BatchPlan;
+    P->dbl = dbl;
     auto fail_rc = [&](int rc) {
         free_bplan(c, P);
         return rc;
@@ -372,8 +379,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
     for (int p = 0; p < B; p++)
         for (int k = 0; k < niter[p]; k++) litems.push_back({p, k});
     const int R = (int)ritems.size(), I = (int)litems.size();
-    const size_t per_rot = (size_t)(2 * ne0 + 2 * lv0) * N * 8;
-    const size_t per_item = (size_t)(4 * lv1 + nd1 * ne1 + 2 * ne1 + 2 * lv1) * N * 8;
+    const size_t per_rot = (size_t)(2 * ne0 + (dbl ? 0 : 2 * lv0)) * N * 8;
+    const size_t per_item = (size_t)(4 * lv1 + nd1 * ne1 + 2 * ne1 + (dbl ? 0 : 2 * lv1)) * N * 8;
     const int RC = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(R, 1), c->ws_budget / per_rot));
     const int RK = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(I, 1), c->ws_budget / per_item));
     // workspace
@@ -383,15 +390,18 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         off += (w + 31) & ~(size_t)31;
         return o;
     };
+    const size_t E1 = std::max(E, 1), X1 = std::max(X, 1);
     const size_t o_in = take((size_t)B * 4 * lv0 * N), o_xc = take((size_t)2 * B * lv0 * N),
                  o_D = take((size_t)2 * B * nd0 * ne0 * N), o_u = take((size_t)RC * 2 * ne0 * N),
-                 o_rot = take((size_t)RC * 2 * lv0 * N), o_outs = take((size_t)O * 2 * lv0 * N),
+                 o_rot = dbl ? 0 : take((size_t)RC * 2 * lv0 * N), o_outs = take((size_t)O * 2 * lv0 * N),
+                 o_acc = dbl ? take((size_t)O * 2 * ne0 * N) : 0,
                  o_ms = lv1 != lv0 ? take((size_t)O * 2 * lv1 * N) : 0, o_d3 = take((size_t)RK * 3 * lv1 * N),
                  o_rxc = take((size_t)RK * lv1 * N), o_rD = take((size_t)RK * nd1 * ne1 * N),
-                 o_ru = take((size_t)RK * 2 * ne1 * N), o_rout = take((size_t)RK * 2 * lv1 * N),
-                 o_cacc = take((size_t)B * 2 * lv1 * N), o_exc = take((size_t)std::max(E, 1) * lv1 * N),
-                 o_eD = take((size_t)std::max(E, 1) * nd1 * ne1 * N), o_eu = take((size_t)std::max(X, 1) * 2 * ne1 * N),
-                 o_erot = take((size_t)std::max(X, 1) * 2 * lv1 * N);
+                 o_ru = take((size_t)RK * 2 * ne1 * N), o_rout = dbl ? 0 : take((size_t)RK * 2 * lv1 * N),
+                 o_cacc = take((size_t)B * 2 * lv1 * N), o_cpq = dbl ? take((size_t)B * 2 * ne1 * N) : 0,
+                 o_exc = take(E1 * lv1 * N), o_eD = take(E1 * nd1 * ne1 * N), o_eu = take(X1 * 2 * ne1 * N),
+                 o_erot = dbl ? 0 : take(X1 * 2 * lv1 * N), o_xacc = dbl ? take(E1 * 2 * ne1 * N) : 0,
+                 o_xout = dbl ? take(E1 * 2 * lv1 * N) : 0;
     P->ws_bytes = off * 8;
     P->ws = (u64 *)plan_alloc(c, P, off * 8);
     if (!P->ws) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch workspace"));
@@ -400,21 +410,30 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
     P->xc = W + o_xc;
     P->D = W + o_D;
     P->u = W + o_u;
-    P->rot = W + o_rot;
+    P->rot = dbl ? nullptr : W + o_rot;
+    P->acc = dbl ? W + o_acc : nullptr;
+    P->cpq = dbl ? W + o_cpq : nullptr;
+    P->xacc = dbl ? W + o_xacc : nullptr;
+    P->xout = dbl ? W + o_xout : nullptr;
     P->outs = W + o_outs;
     P->ms = lv1 != lv0 ? W + o_ms : nullptr;
     P->d3 = W + o_d3;
     P->rxc = W + o_rxc;
     P->rD = W + o_rD;
     P->ru = W + o_ru;
-    P->rout = W + o_rout;
+    P->rout = dbl ? nullptr : W + o_rout;
     P->cacc = W + o_cacc;
     P->exc = W + o_exc;
     P->eD = W + o_eD;
     P->eu = W + o_eu;
-    P->erot = W + o_erot;
+    P->erot = dbl ? nullptr : W + o_erot;
     auto in_ct = [&](int p, int s) { return P->in + ((size_t)2 * p + s) * 2 * lv0 * N; };
     auto out_ct = [&](int p, int s, int k) { return P->outs + ((size_t)obase[p] + s * niter[p] + k) * 2 * lv0 * N; };
+    // where the linear transformations accumulate: the outputs themselves,
+    // or (double mode) their accumulators over PQ
+    auto acc_of = [&](int p, int s, int k) {
+        return dbl ? P->acc + ((size_t)obase[p] + s * niter[p] + k) * 2 * ne0 * N : out_ct(p, s, k);
+    };
     auto keep = [&](void *ptr) { return ptr != nullptr; };
     // identity (d = 0) terms over all outputs; this launch also zero-initialises
     {
@@ -428,7 +447,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                     for (const auto &dr : sd->dref[s][k])
                         if (dr.zi < 0) terms.push_back({in_ct(p, s), sd->mask_at(c, dr.mask)});
                     offs.push_back((int)terms.size());
-                    outs.push_back(out_ct(p, s, k));
+                    outs.push_back(acc_of(p, s, k));
                 }
         }
         P->d_id_terms = plan_upload(c, P, terms);
@@ -446,14 +465,15 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         for (int r = 0; r < ch.cnt; r++) {
             const RItem &it = ritems[r0 + r];
             const u64 g = galois_of(c, P->shp[it.p]->zs[it.s][it.zi]);
+            // tau_g(c0) enters through the inner product (P tau_g(c0)), see RotDesc
             rd.push_back({P->D + ((size_t)2 * it.p + it.s) * nd0 * ne0 * N, c->keys[g], P->u + (size_t)r * 2 * ne0 * N,
-                          (u32)g, 0u});
-            for (int comp = 0; comp < 2; comp++) {
+                          in_ct(it.p, it.s), nullptr, (u32)g, 0u});
+            for (int comp = 0; comp < 2 && !dbl; comp++) {
                 DivDesc v{};
                 v.u = P->u + ((size_t)2 * r + comp) * ne0 * N;
                 v.out = P->rot + ((size_t)2 * r + comp) * lv0 * N;
-                v.add = comp == 0 ? in_ct(it.p, it.s) : nullptr;
-                v.g = (u32)g;
+                v.add = nullptr;
+                v.g = 1;
                 dd.push_back(v);
             }
         }
@@ -471,23 +491,41 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
                         if (dr.zi < 0) continue;
                         const int gi = rbase[p][s] + dr.zi;  // global rotation item
                         if (gi < r0 || gi >= r0 + ch.cnt) continue;
-                        terms.push_back({P->rot + (size_t)(gi - r0) * 2 * lv0 * N, sd->mask_at(c, dr.mask)});
+                        const u64 *src = dbl ? P->u + (size_t)(gi - r0) * 2 * ne0 * N
+                                             : P->rot + (size_t)(gi - r0) * 2 * lv0 * N;
+                        terms.push_back({src, sd->mask_at(c, dr.mask)});
                     }
                     if (terms.size() > t0) {
                         offs.push_back((int)terms.size());
-                        outs.push_back(out_ct(p, s, k));
+                        outs.push_back(acc_of(p, s, k));
                     }
                 }
         }
         ch.nout = (int)outs.size();
         ch.d_rots = plan_upload(c, P, rd);
-        ch.d_div = plan_upload(c, P, dd);
+        ch.d_div = dbl ? nullptr : plan_upload(c, P, dd);
         ch.d_terms = plan_upload(c, P, terms);
         ch.d_off = plan_upload(c, P, offs);
         ch.d_outs = plan_upload(c, P, outs);
-        if (!keep(ch.d_rots) || !keep(ch.d_div) || !keep(ch.d_terms) || !keep(ch.d_off) || !keep(ch.d_outs))
+        if (!keep(ch.d_rots) || (!dbl && !keep(ch.d_div)) || !keep(ch.d_terms) || !keep(ch.d_off) || !keep(ch.d_outs))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->rchunks.push_back(ch);
+    }
+    // double mode: one ModDown per accumulated polynomial (u over PQ -> out over Q)
+    auto moddown_descs = [&](u64 *u, int ne, u64 *outp, int lv, int npoly) {
+        std::vector<DivDesc> dd((size_t)npoly);
+        for (int b = 0; b < npoly; b++) {
+            dd[b] = DivDesc{};
+            dd[b].u = u + (size_t)b * ne * N;
+            dd[b].out = outp + (size_t)b * lv * N;
+            dd[b].g = 1;
+        }
+        return plan_upload(c, P, dd);
+    };
+    if (dbl) {
+        P->d_ltdiv = moddown_descs(P->acc, ne0, P->outs, lv0, 2 * O);
+        P->d_cdiv = moddown_descs(P->cpq, ne1, P->cacc, lv1, 2 * B);
+        if (!keep(P->d_ltdiv) || !keep(P->d_cdiv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // modulus switch of all 2 O polynomials
     if (lv1 != lv0) {
@@ -517,21 +555,25 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             const u64 *b = A1 + ((size_t)obase[p] + niter[p] + k) * 2 * lv1 * N;
             u64 *d = P->d3 + (size_t)r * 3 * lv1 * N;
             tv.push_back({a, b, d});
-            rd.push_back({P->rD + (size_t)r * nd1 * ne1 * N, rlk, P->ru + (size_t)r * 2 * ne1 * N, 1u, 0u});
-            for (int comp = 0; comp < 2; comp++) {
+            // d0 / d1 enter through the inner product (P d0, P d1)
+            rd.push_back({P->rD + (size_t)r * nd1 * ne1 * N, rlk, P->ru + (size_t)r * 2 * ne1 * N, d,
+                          d + (size_t)lv1 * N, 1u, 0u});
+            for (int comp = 0; comp < 2 && !dbl; comp++) {
                 DivDesc v{};
                 v.u = P->ru + ((size_t)2 * r + comp) * ne1 * N;
                 v.out = P->rout + ((size_t)2 * r + comp) * lv1 * N;
-                v.add = d + (size_t)comp * lv1 * N;
+                v.add = nullptr;
                 v.g = 1;
                 dd.push_back(v);
             }
             if (sv.empty() || litems[i0 + r - 1].first != p || r == 0) {
+                // HE-Add of the products: of the ModDown outputs, or (double
+                // mode) of the inner-product outputs over PQ
                 SumDesc s{};
-                s.out = P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
+                s.out = dbl ? P->cpq + (size_t)cslot[p] * 2 * ne1 * N : P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
                 s.init = nullptr;
-                s.items = P->rout + (size_t)r * 2 * lv1 * N;
-                s.stride = (long long)2 * lv1 * N;
+                s.items = dbl ? P->ru + (size_t)r * 2 * ne1 * N : P->rout + (size_t)r * 2 * lv1 * N;
+                s.stride = dbl ? (long long)2 * ne1 * N : (long long)2 * lv1 * N;
                 s.count = 0;
                 sv.push_back(s);
             }
@@ -540,9 +582,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
         ch.nsum = (int)sv.size();
         ch.d_tens = plan_upload(c, P, tv);
         ch.d_rot = plan_upload(c, P, rd);
-        ch.d_div = plan_upload(c, P, dd);
+        ch.d_div = dbl ? nullptr : plan_upload(c, P, dd);
         ch.d_sum = plan_upload(c, P, sv);
-        if (!keep(ch.d_tens) || !keep(ch.d_rot) || !keep(ch.d_div) || !keep(ch.d_sum))
+        if (!keep(ch.d_tens) || !keep(ch.d_rot) || (!dbl && !keep(ch.d_div)) || !keep(ch.d_sum))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->lchunks.push_back(ch);
     }
@@ -556,28 +598,52 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
             for (int h = 0; h < next[p]; h++) {
                 const int x = xfirst[p] + h;
                 const u64 g = galois_of(c, P->shp[p]->hp.extract[h]);
-                rd.push_back({P->eD + (size_t)e * nd1 * ne1 * N, c->keys[g], P->eu + (size_t)x * 2 * ne1 * N, (u32)g, 0u});
-                for (int comp = 0; comp < 2; comp++) {
+                rd.push_back({P->eD + (size_t)e * nd1 * ne1 * N, c->keys[g], P->eu + (size_t)x * 2 * ne1 * N,
+                              P->cacc + (size_t)e * 2 * lv1 * N, nullptr, (u32)g, 0u});
+                for (int comp = 0; comp < 2 && !dbl; comp++) {
                     DivDesc v{};
                     v.u = P->eu + ((size_t)2 * x + comp) * ne1 * N;
                     v.out = P->erot + ((size_t)2 * x + comp) * lv1 * N;
-                    v.add = comp == 0 ? P->cacc + (size_t)e * 2 * lv1 * N : nullptr;
-                    v.g = (u32)g;
+                    v.add = nullptr;
+                    v.g = 1;
                     dd.push_back(v);
                 }
             }
         }
         P->d_erot = plan_upload(c, P, rd);
-        P->d_ediv = plan_upload(c, P, dd);
-        if (!keep(P->d_erot) || !keep(P->d_ediv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        P->d_ediv = dbl ? nullptr : plan_upload(c, P, dd);
+        if (!keep(P->d_erot) || (!dbl && !keep(P->d_ediv)))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        if (dbl) {
+            // sum of each product's extraction terms over PQ, then one ModDown
+            std::vector<SumDesc> xs;
+            for (int p = 0; p < B; p++) {
+                if (!next[p]) continue;
+                SumDesc s{};
+                s.out = P->xacc + (size_t)cslot[p] * 2 * ne1 * N;
+                s.init = P->eu + (size_t)xfirst[p] * 2 * ne1 * N;
+                s.items = s.init + (size_t)2 * ne1 * N;
+                s.stride = (long long)2 * ne1 * N;
+                s.count = next[p] - 1;
+                xs.push_back(s);
+            }
+            P->d_xsum = plan_upload(c, P, xs);
+            P->d_xdiv = moddown_descs(P->xacc, ne1, P->xout, lv1, 2 * E);
+            if (!keep(P->d_xsum) || !keep(P->d_xdiv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        }
     }
     // final sums (the caller's result pointers are filled in per call)
     for (int p = 0; p < B; p++) {
         SumDesc s{};
         s.init = P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
-        s.items = next[p] ? P->erot + (size_t)xfirst[p] * 2 * lv1 * N : s.init;
+        if (dbl) {
+            s.items = next[p] ? P->xout + (size_t)cslot[p] * 2 * lv1 * N : s.init;
+            s.count = next[p] ? 1 : 0;
+        } else {
+            s.items = next[p] ? P->erot + (size_t)xfirst[p] * 2 * lv1 * N : s.init;
+            s.count = next[p];
+        }
         s.stride = (long long)2 * lv1 * N;
-        s.count = next[p];
         P->final_tmpl.push_back(s);
     }
     P->d_final = (SumDesc *)plan_alloc(c, P, sizeof(SumDesc) * B);
@@ -589,8 +655,18 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, Ba
     return HEGMM_OK;
 }
 
+// ModDown of npoly accumulated polynomials over the extended basis of level lv
+static int moddown_polys(Ctx *c, int lv, u64 *u, const DivDesc *d_div, int npoly) {
+    const DivTab *tb = div_tab(c, lv, 0);
+    if (!tb) return HEGMM_ENOMEM;
+    int rc;
+    if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, npoly)))) return rc;
+    return divround_ntt(c, *tb, d_div, npoly);
+}
+
 static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm_ct *const *Bc, hegmm_ct **C) {
-    const int N = c->N, B = P->B, lv0 = P->lv0, lv1 = P->lv1;
+    const int N = c->N, B = P->B, lv0 = P->lv0, lv1 = P->lv1, K = c->K;
+    const int dbl = P->dbl, np0 = dbl ? lv0 + K : lv0, np1 = dbl ? lv1 + K : lv1;
     int rc;
     // 1. operands and the hoisted ModUp of every c1
     std::vector<u64 *> ptrs((size_t)2 * B);
@@ -602,26 +678,44 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
     if ((rc = gather_cts(c, lv0, P->d_inptr, 2 * B, P->in))) return rc;
     if ((rc = modup(c, lv0, 2 * B, P->in + (size_t)lv0 * N, (long long)2 * lv0 * N, P->xc, P->D))) return rc;
     // 2. linear transformations eps^k(A), omega^k(B) of every iteration
-    if ((rc = lt_accumulate(c, lv0, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) return rc;
+    // (double mode: the d = 0 terms enter as P ct and the rotations as their
+    // inner-product outputs u + P tau(c0), all over PQ; one ModDown per output)
+    if ((rc = lt_accumulate(c, lv0, np0, lv0, dbl, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) return rc;
     for (auto &ch : P->rchunks) {
-        if ((rc = ksw_moddown(c, lv0, ch.d_rots, ch.d_div, ch.cnt, P->u, nullptr))) return rc;
-        if ((rc = lt_accumulate(c, lv0, ch.d_terms, ch.d_off, ch.d_outs, ch.nout, 1))) return rc;
+        if (dbl) {
+            if ((rc = ksw_ip(c, lv0, ch.d_rots, ch.cnt))) return rc;
+        } else {
+            if ((rc = ksw_moddown(c, lv0, ch.d_rots, ch.d_div, ch.cnt, P->u, nullptr))) return rc;
+        }
+        if ((rc = lt_accumulate(c, lv0, np0, np0, 0, ch.d_terms, ch.d_off, ch.d_outs, ch.nout, 1))) return rc;
     }
+    if (dbl && (rc = moddown_polys(c, lv0, P->acc, P->d_ltdiv, 2 * P->O))) return rc;
     // 3. modulus switch (only for chains that drop a prime before products)
     if (lv1 != lv0)
         if ((rc = modswitch_polys(c, lv0, P->outs, 2 * P->O, nullptr, P->ms, P->d_msdiv))) return rc;
     // 4. HE-Mult of every iteration and the sum per product
-    cudaMemsetAsync(P->cacc, 0, (size_t)B * 2 * lv1 * N * 8, c->st);
+    cudaMemsetAsync(dbl ? P->cpq : P->cacc, 0, (size_t)B * 2 * np1 * N * 8, c->st);
     for (auto &ch : P->lchunks) {
         if ((rc = tensor(c, lv1, ch.d_tens, ch.cnt))) return rc;
         if ((rc = modup(c, lv1, ch.cnt, P->d3 + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->rxc, P->rD))) return rc;
-        if ((rc = ksw_moddown(c, lv1, ch.d_rot, ch.d_div, ch.cnt, P->ru, nullptr))) return rc;
-        if ((rc = sum_desc(c, lv1, ch.d_sum, ch.nsum))) return rc;
+        if (dbl) {
+            if ((rc = ksw_ip(c, lv1, ch.d_rot, ch.cnt))) return rc;
+        } else {
+            if ((rc = ksw_moddown(c, lv1, ch.d_rot, ch.d_div, ch.cnt, P->ru, nullptr))) return rc;
+        }
+        if ((rc = sum_desc(c, lv1, ch.d_sum, ch.nsum, np1))) return rc;
     }
+    if (dbl && (rc = moddown_polys(c, lv1, P->cpq, P->d_cdiv, 2 * B))) return rc;
     // 5. Algorithm 2 extraction, and the results
     if (P->X > 0) {
         if ((rc = modup(c, lv1, P->E, P->cacc + (size_t)lv1 * N, (long long)2 * lv1 * N, P->exc, P->eD))) return rc;
-        if ((rc = ksw_moddown(c, lv1, P->d_erot, P->d_ediv, P->X, P->eu, nullptr))) return rc;
+        if (dbl) {
+            if ((rc = ksw_ip(c, lv1, P->d_erot, P->X))) return rc;
+            if ((rc = sum_desc(c, lv1, P->d_xsum, P->E, lv1 + K))) return rc;
+            if ((rc = moddown_polys(c, lv1, P->xacc, P->d_xdiv, 2 * P->E))) return rc;
+        } else {
+            if ((rc = ksw_moddown(c, lv1, P->d_erot, P->d_ediv, P->X, P->eu, nullptr))) return rc;
+        }
     }
     std::vector<SumDesc> fin = P->final_tmpl;
     for (int p = 0; p < B; p++) fin[p].out = C[p]->d;
@@ -655,7 +749,8 @@ size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
     const size_t nd0 = c->digits((int)lv0), nd1 = c->digits((int)lv1);
     const size_t ni = hp.iters.size(), ne = hp.extract.size();
     size_t w = 6 * lv0 + 2 * nd0 * ne0 + ni * 4 * lv0 + (lv1 != lv0 ? ni * 4 * lv1 : 0) + 2 * lv1;
-    if (ne) w += lv1 + nd1 * ne1 + ne * (2 * ne1 + 2 * lv1);
+    if (c->ks_double) w += ni * 4 * ne0 + 2 * ne1;
+    if (ne) w += lv1 + nd1 * ne1 + ne * (2 * ne1 + 2 * lv1) + (c->ks_double ? 2 * ne1 + 2 * lv1 : 0);
     return w * c->N * 8;
 }
 
@@ -676,12 +771,14 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
         shapes.push_back({m, l, n, a});
         key.insert(key.end(), {m, l, n, a});
     }
+    const int dbl = c->ks_double ? 1 : 0;
+    key.push_back(dbl);
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
         P = it->second;
     } else {
-        int rc = build_bplan(c, shapes, &P);
+        int rc = build_bplan(c, shapes, dbl, &P);
         if (rc) return rc;
         if (cache) {
             evict_plans(c, P->ws_bytes);
@@ -745,6 +842,14 @@ int hegmm_matmul_batch(hegmm_ctx *h, int count, const hegmm_ct *const *A, const 
                        int alg, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, alg, C, nullptr);
+}
+
+int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {
+    if (!h) return HEGMM_EINVAL;
+    if (mode != HEGMM_KS_SINGLE && mode != HEGMM_KS_DOUBLE)
+        return set_err(&h->c, HEGMM_EINVAL, "key-switch mode must be HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE");
+    h->c.ks_double = mode == HEGMM_KS_DOUBLE;
+    return HEGMM_OK;
 }
 
 int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {

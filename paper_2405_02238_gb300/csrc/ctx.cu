@@ -262,6 +262,10 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         M.ninv_sh = shoup(M.ninv, q);
         M.tq = p->t % q;
         M.tq_sh = shoup(M.tq, q);
+        u64 P = 1;
+        for (int k = 0; k < p->K; k++) P = hmul(P, c->q[p->L + k] % q, q);
+        M.pR = (i >= p->L && i < p->L + p->K) ? 0 : hmul(P, r1, q);  // r1 = 2^64 mod q
+        M.pad = 0;
     }
     cudaDeviceProp prop;
     int dev = 0;

@@ -114,6 +114,7 @@ int rotate_hoisted(Ctx *c, const hegmm_ct *in, const int *z, int count, hegmm_ct
         idx.push_back(r);
         RotDesc d{};
         d.key = it->second;
+        d.add0 = in->d;  // tau_g(c0) enters the inner product as P tau_g(c0)
         d.g = (u32)g;
         rd.push_back(d);
     }
@@ -132,8 +133,8 @@ int rotate_hoisted(Ctx *c, const hegmm_ct *in, const int *z, int count, hegmm_ct
             v.u = u + ((size_t)2 * k + comp) * ne * N;
             v.tmp = tmp + ((size_t)2 * k + comp) * lv * N;
             v.out = outs[idx[k]]->d + (size_t)comp * lv * N;
-            v.add = comp == 0 ? in->d : nullptr;
-            v.g = rd[k].g;
+            v.add = nullptr;
+            v.g = 1;
             dd.push_back(v);
         }
     }
@@ -164,13 +165,14 @@ int mult_relin(Ctx *c, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out) {
     u64 *tmp = dalloc(c, (size_t)2 * lv * N);
     if (!o || !d3 || !xc || !D || !u || !tmp) return set_err(c, HEGMM_ENOMEM, "mult");
     std::vector<Tensor3> tv{{a->d, b->d, d3}};
-    std::vector<RotDesc> rd{{D, kit->second, u, 1u, 0u}};
+    // d0 / d1 enter the inner product as P d0, P d1
+    std::vector<RotDesc> rd{{D, kit->second, u, d3, d3 + (size_t)lv * N, 1u, 0u}};
     std::vector<DivDesc> dd(2);
     for (int comp = 0; comp < 2; comp++) {
         dd[comp].u = u + (size_t)comp * ne * N;
         dd[comp].tmp = tmp + (size_t)comp * lv * N;
         dd[comp].out = o->d + (size_t)comp * lv * N;
-        dd[comp].add = d3 + (size_t)comp * lv * N;
+        dd[comp].add = nullptr;
         dd[comp].g = 1;
     }
     Tensor3 *d_t = upload(c, tv);

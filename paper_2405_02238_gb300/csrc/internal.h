@@ -29,6 +29,8 @@ struct ModDev {
     u64 ninv_sh;
     u64 tq;     // t mod q
     u64 tq_sh;
+    u64 pR;     // (P mod q) 2^64 mod q, P = product of the special primes (0 on them)
+    u64 pad;
 };
 
 // A batch of limbs: limb b = outer * inner + i lives at
@@ -44,12 +46,16 @@ struct LimbPat {
     unsigned char mod[PAT_MAX];
 };
 
-// One key-switching inner product: u[c][e] = sum_j D[j][e][perm_g] * key[j][c][gp(e)].
+// One key-switching inner product: u[c][e] = sum_j D[j][e][perm_g] * key[j][c][gp(e)]
+// (+ P * add_c[e][perm_g] on the chain primes, so that ModDown(u) already
+// contains add_c: ModDown(u + P x) = ModDown(u) + x exactly).
 struct RotDesc {
-    const u64 *D;   // [nd][ne][N] hoisted ModUp digits (NTT domain)
-    const u64 *key; // [dnum][2][L+K][N] Montgomery NTT
-    u64 *u;         // [2][ne][N]
-    u32 g;          // Galois element (1 = none)
+    const u64 *D;    // [nd][ne][N] hoisted ModUp digits (NTT domain)
+    const u64 *key;  // [dnum][2][L+K][N] Montgomery NTT
+    u64 *u;          // [2][ne][N]
+    const u64 *add0; // [lv][N] or null: added to component 0 (e.g. c0 of a rotation)
+    const u64 *add1; // [lv][N] or null: added to component 1
+    u32 g;           // Galois element (1 = none), also applied to add0 / add1
     u32 pad;
 };
 
@@ -67,8 +73,8 @@ struct DivDesc {
 // A product output of the linear-transformation accumulation:
 // out[c][i] (+)= sum over terms src[c][i] * mask[i].
 struct LtTerm {
-    const u64 *src;  // ciphertext [2][lv][N]
-    const u64 *mask; // [lv][N] Montgomery NTT
+    const u64 *src;  // [2][np][N]: a ciphertext (np = lv) or a key-switch output over PQ (np = lv + K)
+    const u64 *mask; // [L + K][N] Montgomery NTT, limb = global prime index
 };
 
 struct Tensor3 {
@@ -144,6 +150,7 @@ struct Ctx {
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
+    int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
@@ -212,8 +219,13 @@ int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, 
 const ModUpTab *modup_tab(Ctx *c, int lv);
 int div_conv(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
-int lt_accumulate(Ctx *c, int lv, const LtTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout,
-                  int accumulate);
+// outs[o] (+)= sum over terms of mask (.) src, over 2 np limbs per output
+// (np = lv: the chain primes; np = lv + K: the extended basis, limb e >= lv
+// on special prime L + e - lv).  src_np: limbs per component of each source
+// (lv or np).  lift: the sources are ciphertexts over Q taken as P ct in the
+// extended basis (the sum is multiplied by P; special limbs are zero).
+int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_terms, const int *d_off,
+                  u64 *const *d_outs, int nout, int accumulate);
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
 // out[poly] = sum_k in[k][poly] over nk inputs with stride in_stride words; npolylimbs = 2*lv
 int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate);
@@ -242,7 +254,8 @@ int cuda_check(Ctx *c, const char *where);
 LimbPat pat_ct(Ctx *c, u64 *base, int npoly, int lv, long long poly_stride_words = -1);
 
 // batched sums (SumDesc list) and the input gather of a batch
-int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n);
+// np = lv (chain primes) or lv + K (extended basis), as for lt_accumulate
+int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np = 0);
 // ev[b][slot_pos0[slots[j]]] = value for j in [off[b], off[b+1]) (NTT order mod t)
 int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev);
 int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst);

@@ -396,7 +396,7 @@ int modup_conv_tab(Ctx *c, const ModUpTab &tb, int n, const u64 *xc, long long x
 // Each thread computes two adjacent coefficients: the key is streamed with
 // 16-byte loads, the digits are gathered at the automorphism's indices
 // (they are L2-resident: one hoisted ModUp serves every rotation).
-__global__ void __launch_bounds__(256) k_ksw_ip(int lv, int ne, int nd, int np, int L, int logN,
+__global__ void __launch_bounds__(256, 4) k_ksw_ip(int lv, int ne, int nd, int np, int L, int logN,
                                                 const ModDev *__restrict__ mods, const RotDesc *__restrict__ rots) {
     const int N = 1 << logN;
     const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -421,6 +421,17 @@ __global__ void __launch_bounds__(256) k_ksw_ip(int lv, int ne, int nd, int np, 
         mac(a01, x1, k0.y);
         mac(a10, x0, k1.x);
         mac(a11, x1, k1.y);
+    }
+    if (e < lv) {  // P * add on the chain primes (P = 0 mod every special prime)
+        const u64 pR = mods[gm].pR;
+        if (d.add0) {
+            mac(a00, __ldg(d.add0 + (size_t)e * N + s0), pR);
+            mac(a01, __ldg(d.add0 + (size_t)e * N + s1), pR);
+        }
+        if (d.add1) {
+            mac(a10, __ldg(d.add1 + (size_t)e * N + s0), pR);
+            mac(a11, __ldg(d.add1 + (size_t)e * N + s1), pR);
+        }
     }
     ulonglong2 o0, o1;
     o0.x = montred(a00, q, qinv);
@@ -517,30 +528,37 @@ int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
 // ------------------------------------------------------------------ linear-transformation accumulation
 // out[o][comp][i] (+)= sum_{terms of o} src[comp][i] * mask[i]  (HE-CMult + HE-Add of Eq. lintrans)
 
-__global__ void k_lt_acc(int lv, int logN, const ModDev *__restrict__ mods, const LtTerm *__restrict__ terms,
-                         const int *__restrict__ off, u64 *const *__restrict__ outs, int accumulate) {
+__global__ void k_lt_acc(int lv, int np, int src_np, int lift, int Lc, int logN, const ModDev *__restrict__ mods,
+                         const LtTerm *__restrict__ terms, const int *__restrict__ off, u64 *const *__restrict__ outs,
+                         int accumulate) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int pl = blockIdx.y, o = blockIdx.z;
-    const int i = pl % lv;
-    const u64 q = mods[i].q, qinv = mods[i].qinv;
+    const int comp = pl / np, e = pl - comp * np;
+    const int gm = e < lv ? e : Lc + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv;
     u64 *out = outs[o] + (size_t)pl * N;
-    u64 acc = accumulate ? out[c] : 0;
-    const int t0 = off[o], t1 = off[o + 1];
-    for (int t = t0; t < t1; t++) {
-        const LtTerm tm = terms[t];
-        acc = addm(acc, montmul(tm.src[(size_t)pl * N + c], tm.mask[(size_t)i * N + c], q, qinv), q);
+    u64 acc = 0;
+    if (e < src_np) {
+        const size_t so = ((size_t)comp * src_np + e) * N + c;
+        const int t0 = off[o], t1 = off[o + 1];
+        for (int t = t0; t < t1; t++) {
+            const LtTerm tm = terms[t];
+            acc = addm(acc, montmul(__ldg(tm.src + so), __ldg(tm.mask + (size_t)gm * N + c), q, qinv), q);
+        }
+        if (lift) acc = montmul(acc, mods[gm].pR, q, qinv);  // P acc (pR = P R mod q)
     }
+    if (accumulate) acc = addm(acc, out[c], q);
     out[c] = acc;
 }
 
-int lt_accumulate(Ctx *c, int lv, const LtTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout,
-                  int accumulate) {
+int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_terms, const int *d_off,
+                  u64 *const *d_outs, int nout, int accumulate) {
     if (nout <= 0) return HEGMM_OK;
     Launch t(c, K_LT_ACC, 0.0);
-    k_lt_acc<<<grid_coef(c->N, 2 * lv, nout), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_terms, d_off, d_outs,
-                                                               accumulate);
+    k_lt_acc<<<grid_coef(c->N, 2 * np, nout), 256, 0, c->st>>>(lv, np, src_np, lift, c->L, c->logN, c->d_mods,
+                                                               d_terms, d_off, d_outs, accumulate);
     return cuda_check(c, "lt_acc");
 }
 
@@ -591,23 +609,26 @@ int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out
 
 // Batched sums: out = (init ? init : out) + sum_j items[j * stride], one
 // descriptor per grid.z, over the 2 lv limbs of a ciphertext.
-__global__ void k_sum_desc(int lv, int logN, const ModDev *__restrict__ mods, const SumDesc *__restrict__ ds) {
+__global__ void k_sum_desc(int lv, int np, int Lc, int logN, const ModDev *__restrict__ mods,
+                           const SumDesc *__restrict__ ds) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int pl = blockIdx.y;
     const SumDesc d = ds[blockIdx.z];
-    const u64 q = mods[pl % lv].q;
+    const int e = pl % np;
+    const u64 q = mods[e < lv ? e : Lc + (e - lv)].q;
     const size_t o = (size_t)pl * N + c;
     u64 acc = d.init ? d.init[o] : d.out[o];
     for (int j = 0; j < d.count; j++) acc = addm(acc, d.items[j * d.stride + o], q);
     d.out[o] = acc;
 }
 
-int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n) {
+int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np) {
     if (n <= 0) return HEGMM_OK;
+    if (np <= 0) np = lv;
     Launch t(c, K_SUM, 0.0);
-    k_sum_desc<<<grid_coef(c->N, 2 * lv, n), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_sums);
+    k_sum_desc<<<grid_coef(c->N, 2 * np, n), 256, 0, c->st>>>(lv, np, c->L, c->logN, c->d_mods, d_sums);
     return cuda_check(c, "sum_desc");
 }
 

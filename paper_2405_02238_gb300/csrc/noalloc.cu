@@ -88,10 +88,10 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     u64 *u = D + (size_t)nd * ne * N;
     u64 *tmp = u + (size_t)2 * ne * N;
 
-    // Header: RotDesc at word 0, two DivDesc at word 4, ModUp table at word
+    // Header: RotDesc at word 0, two DivDesc at word 6, ModUp table at word
     // 16, ModDown table after it (same layouts as the context's tables).
     std::vector<u64> hdr(16, 0);
-    RotDesc rd{D, kit->second, u, (u32)g, 0u};
+    RotDesc rd{D, kit->second, u, nullptr, nullptr, (u32)g, 0u};
     DivDesc dd[2];
     for (int comp = 0; comp < 2; comp++) {
         dd[comp].u = u + (size_t)comp * ne * N;
@@ -101,9 +101,9 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
         dd[comp].g = (u32)g;
         dd[comp].pad = 0;
     }
-    static_assert(sizeof(RotDesc) == 32 && sizeof(DivDesc) == 40, "descriptor layout");
+    static_assert(sizeof(RotDesc) == 48 && sizeof(DivDesc) == 40, "descriptor layout");
     memcpy(&hdr[0], &rd, sizeof(rd));
-    memcpy(&hdr[4], dd, sizeof(dd));
+    memcpy(&hdr[6], dd, sizeof(dd));
     // ModUp table: [nd][a] {hinv, shoup}, [nd][a][ne] {hat mod r, shoup, q_i mod r}
     const size_t o_mu = hdr.size();
     hdr.resize(o_mu + (size_t)nd * a * 2 + (size_t)nd * a * ne * 3, 0);
@@ -179,7 +179,7 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     dt.ndrop = K;
     dt.d = S0 + o_dv;
     const RotDesc *d_rd = reinterpret_cast<const RotDesc *>(S0);
-    const DivDesc *d_dd = reinterpret_cast<const DivDesc *>(S0 + 4);
+    const DivDesc *d_dd = reinterpret_cast<const DivDesc *>(S0 + 6);
 
     // hoisted ModUp of c1
     cudaMemcpyAsync(xc, in->d + (size_t)lv * N, (size_t)lv * N * 8, cudaMemcpyDeviceToDevice, c->st);

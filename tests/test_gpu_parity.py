@@ -121,8 +121,12 @@ def test_modswitch_tiny(H):
     assert (ctx.hegmm_ct_export(p) == o.mult_relin(o.modswitch(co), o.modswitch(co))).all()
 
 
-def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0):
+MODES = ["single", "double"]
+
+
+def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"):
     pre, ctx, o = get_pair(H, name)
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if mode == "double" else H.KS_SINGLE)
     A, B = W.matrices(m, l, n, lo, hi, seed=seed)
     ctx.hegmm_keygen(SEED, [(m, l, n)], alg)
     ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 11, 100)
@@ -135,7 +139,7 @@ def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0):
     pc = plan.counts()
     assert cnt["rot"] == pc["rot"] and cnt["mult"] == pc["mult"] and cnt["cmult"] == pc["cmult"]
     if bitexact:
-        ex = OH.HEGMM(o)
+        ex = OH.HEGMM(o, mode=mode)
         ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=11, streams=(100, 101))
         assert (ctx.hegmm_ct_export(ca) == ctA).all()
         oc = ex.run(plan, ctA, ctB)
@@ -143,26 +147,30 @@ def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0):
     return cnt
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("alg", [1, 2])
-def test_hegmm_tiny_bitexact(H, alg):
-    run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE)
+def test_hegmm_tiny_bitexact(H, alg, mode):
+    run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE, mode=mode)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 1), (3, 3, 3), (5, 12, 7), (9, 4, 11), (7, 9, 2), (2, 5, 7),
                                    (5, 4, 2), (12, 3, 9)])
 def test_hegmm_tiny_edge_shapes(H, shape):
     for alg in (1, 2):
-        run_both(H, "tiny", *shape, alg, *W.TINY_RANGE, seed=sum(shape))
+        for mode in MODES:
+            run_both(H, "tiny", *shape, alg, *W.TINY_RANGE, seed=sum(shape), mode=mode)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", W.MEDIUM_SHAPES)
-def test_hegmm_medium_alg2_bitexact(H, shape):
-    run_both(H, "medium", *shape, 2, *W.MEDIUM_RANGE)
+def test_hegmm_medium_alg2_bitexact(H, shape, mode):
+    run_both(H, "medium", *shape, 2, *W.MEDIUM_RANGE, mode=mode)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", W.MEDIUM_SHAPES)
-def test_hegmm_medium_alg1(H, shape):
-    run_both(H, "medium", *shape, 1, *W.MEDIUM_RANGE, bitexact=False)
+def test_hegmm_medium_alg1(H, shape, mode):
+    run_both(H, "medium", *shape, 1, *W.MEDIUM_RANGE, bitexact=False, mode=mode)
 
 
 def test_hegmm_medium_maximum_shape(H):
@@ -170,8 +178,9 @@ def test_hegmm_medium_maximum_shape(H):
     run_both(H, "medium", 64, 64, 64, 2, *W.MEDIUM_RANGE, bitexact=False)
 
 
-def test_hegmm_paper_128x16x64_bitexact(H):
-    run_both(H, "paper", 128, 16, 64, 0, *W.PAPER_RANGE)
+@pytest.mark.parametrize("mode", MODES)
+def test_hegmm_paper_128x16x64_bitexact(H, mode):
+    run_both(H, "paper", 128, 16, 64, 0, *W.PAPER_RANGE, mode=mode)
 
 
 @pytest.mark.parametrize("shape", [(64, 64, 64), (32, 128, 16)])
@@ -179,8 +188,10 @@ def test_hegmm_paper_shapes(H, shape):
     run_both(H, "paper", *shape, 0, *W.PAPER_RANGE, bitexact=False)
 
 
-def test_batch_equals_single(H):
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_equals_single(H, mode):
     pre, ctx, o = get_pair(H, "tiny")
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if mode == "double" else H.KS_SINGLE)
     shapes = [(4, 8, 6), (3, 5, 2), (6, 2, 7)]
     ctx.hegmm_keygen(SEED, shapes, H.ALG_AUTO)
     As, Bs, Cs, mats = [], [], [], []
