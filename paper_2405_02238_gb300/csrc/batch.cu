@@ -81,6 +81,15 @@ struct BatchPlan {
     std::vector<ShapeData *> shp;
     int B = 0, lv0 = 0, lv1 = 0, O = 0, E = 0, X = 0;
     int dbl = 0;  // sums of key switches kept over PQ (one ModDown per sum)
+    int fused = 0;  // double mode: every linear transformation in one k_lt_ksw launch
+    LtKsTerm *d_ltks = nullptr;
+    int *d_ltks_off = nullptr;
+    u64 **d_ltks_outs = nullptr;
+    int ltks_items = 0;     // work items: chunks of at most lt_chunk terms of one output
+    double ltks_keyed = 0;  // key-switched terms (for the byte count)
+    u64 *part = nullptr;    // partial sums of outputs split into several items
+    SumDesc *d_ltsum = nullptr;
+    int ltsum_n = 0;
     size_t ws_bytes = 0;
     u64 *ws = nullptr;
     u64 *in = nullptr, *xc = nullptr, *D = nullptr, *u = nullptr, *rot = nullptr, *outs = nullptr, *ms = nullptr;
@@ -379,9 +388,30 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     for (int p = 0; p < B; p++)
         for (int k = 0; k < niter[p]; k++) litems.push_back({p, k});
     const int R = (int)ritems.size(), I = (int)litems.size();
+    // double mode fuses each linear transformation's inner products and mask
+    // sums into one kernel when its lazy 128-bit sums cannot overflow:
+    // (terms of an output + 2) q < 2^64
+    // Long term lists are cut into items of at most lt_chunk terms (balanced
+    // work per CTA row); the items of such an output write partial sums,
+    // added by one sum launch.
+    const int TC = std::max(1, c->lt_chunk);
+    size_t npart = 0;
+    if (dbl) {
+        size_t tmax = 0;
+        for (int p = 0; p < B; p++)
+            for (int s = 0; s < 2; s++)
+                for (const auto &v : P->shp[p]->dref[s]) {
+                    tmax = std::max(tmax, v.size());
+                    const size_t nch = (v.size() + TC - 1) / TC;
+                    if (nch > 1) npart += nch;
+                }
+        P->fused = c->lt_fused &&
+                   (unsigned __int128)(std::min<size_t>(tmax, TC) + 2) * c->q[0] < ((unsigned __int128)1 << 64);
+    }
+    const int fused = P->fused;
     const size_t per_rot = (size_t)(2 * ne0 + (dbl ? 0 : 2 * lv0)) * N * 8;
     const size_t per_item = (size_t)(4 * lv1 + nd1 * ne1 + 2 * ne1 + (dbl ? 0 : 2 * lv1)) * N * 8;
-    const int RC = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(R, 1), c->ws_budget / per_rot));
+    const int RC = fused ? 0 : (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(R, 1), c->ws_budget / per_rot));
     const int RK = (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(I, 1), c->ws_budget / per_item));
     // workspace
     size_t off = 0;
@@ -392,9 +422,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     };
     const size_t E1 = std::max(E, 1), X1 = std::max(X, 1);
     const size_t o_in = take((size_t)B * 4 * lv0 * N), o_xc = take((size_t)2 * B * lv0 * N),
-                 o_D = take((size_t)2 * B * nd0 * ne0 * N), o_u = take((size_t)RC * 2 * ne0 * N),
+                 o_D = take((size_t)2 * B * nd0 * ne0 * N), o_u = fused ? 0 : take((size_t)RC * 2 * ne0 * N),
                  o_rot = dbl ? 0 : take((size_t)RC * 2 * lv0 * N), o_outs = take((size_t)O * 2 * lv0 * N),
-                 o_acc = dbl ? take((size_t)O * 2 * ne0 * N) : 0,
+                 o_acc = dbl ? take((size_t)O * 2 * ne0 * N) : 0, o_part = fused ? take(npart * 2 * ne0 * N) : 0,
                  o_ms = lv1 != lv0 ? take((size_t)O * 2 * lv1 * N) : 0, o_d3 = take((size_t)RK * 3 * lv1 * N),
                  o_rxc = take((size_t)RK * lv1 * N), o_rD = take((size_t)RK * nd1 * ne1 * N),
                  o_ru = take((size_t)RK * 2 * ne1 * N), o_rout = dbl ? 0 : take((size_t)RK * 2 * lv1 * N),
@@ -409,9 +439,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     P->in = W + o_in;
     P->xc = W + o_xc;
     P->D = W + o_D;
-    P->u = W + o_u;
+    P->u = fused ? nullptr : W + o_u;
     P->rot = dbl ? nullptr : W + o_rot;
     P->acc = dbl ? W + o_acc : nullptr;
+    P->part = fused ? W + o_part : nullptr;
     P->cpq = dbl ? W + o_cpq : nullptr;
     P->xacc = dbl ? W + o_xacc : nullptr;
     P->xout = dbl ? W + o_xout : nullptr;
@@ -435,8 +466,64 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
         return dbl ? P->acc + ((size_t)obase[p] + s * niter[p] + k) * 2 * ne0 * N : out_ct(p, s, k);
     };
     auto keep = [&](void *ptr) { return ptr != nullptr; };
+    if (fused) {
+        // every term of every output, in the order of the outputs, cut into items
+        std::vector<LtKsTerm> terms;
+        std::vector<int> offs{0};
+        std::vector<u64 *> outs;
+        std::vector<SumDesc> sums;
+        size_t pi = 0;
+        const size_t pstride = (size_t)2 * ne0 * N;
+        for (int p = 0; p < B; p++) {
+            const ShapeData *sd = P->shp[p];
+            for (int s = 0; s < 2; s++)
+                for (int k = 0; k < niter[p]; k++) {
+                    const auto &dl = sd->dref[s][k];
+                    const int nch = std::max<int>(1, (int)((dl.size() + TC - 1) / TC));
+                    if (nch > 1) {
+                        SumDesc sm{};
+                        sm.out = acc_of(p, s, k);
+                        sm.init = P->part + pi * pstride;
+                        sm.items = sm.init + pstride;
+                        sm.stride = (long long)pstride;
+                        sm.count = nch - 1;
+                        sums.push_back(sm);
+                    }
+                    int in_item = 0;
+                    for (const auto &dr : dl) {
+                        if (in_item == TC) {  // close an item of a split output
+                            offs.push_back((int)terms.size());
+                            outs.push_back(P->part + pi++ * pstride);
+                            in_item = 0;
+                        }
+                        in_item++;
+                        LtKsTerm T{};
+                        T.ct = in_ct(p, s);
+                        T.mask = sd->mask_at(c, dr.mask);
+                        if (dr.zi >= 0) {
+                            const u64 g = galois_of(c, sd->zs[s][dr.zi]);
+                            T.D = P->D + ((size_t)2 * p + s) * nd0 * ne0 * N;
+                            T.key = c->keys[g];
+                            T.g = (u32)g;
+                            P->ltks_keyed += 1;
+                        }
+                        terms.push_back(T);
+                    }
+                    offs.push_back((int)terms.size());
+                    outs.push_back(nch > 1 ? P->part + pi++ * pstride : acc_of(p, s, k));
+                }
+        }
+        P->ltks_items = (int)outs.size();
+        P->ltsum_n = (int)sums.size();
+        P->d_ltks = plan_upload(c, P, terms);
+        P->d_ltks_off = plan_upload(c, P, offs);
+        P->d_ltks_outs = plan_upload(c, P, outs);
+        P->d_ltsum = sums.empty() ? nullptr : plan_upload(c, P, sums);
+        if (!keep(P->d_ltks) || !keep(P->d_ltks_off) || !keep(P->d_ltks_outs) || (!sums.empty() && !keep(P->d_ltsum)))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
     // identity (d = 0) terms over all outputs; this launch also zero-initialises
-    {
+    if (!fused) {
         std::vector<LtTerm> terms;
         std::vector<int> offs{0};
         std::vector<u64 *> outs;
@@ -457,7 +544,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // rotation chunks
-    for (int r0 = 0; r0 < R; r0 += RC) {
+    for (int r0 = 0; r0 < R && !fused; r0 += RC) {
         RotChunk ch;
         ch.cnt = std::min(RC, R - r0);
         std::vector<RotDesc> rd;
@@ -680,7 +767,12 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
     // 2. linear transformations eps^k(A), omega^k(B) of every iteration
     // (double mode: the d = 0 terms enter as P ct and the rotations as their
     // inner-product outputs u + P tau(c0), all over PQ; one ModDown per output)
-    if ((rc = lt_accumulate(c, lv0, np0, lv0, dbl, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) return rc;
+    if (P->fused) {
+        if ((rc = lt_ksw(c, lv0, P->d_ltks, P->d_ltks_off, P->d_ltks_outs, P->ltks_items, P->ltks_keyed))) return rc;
+        if ((rc = sum_desc(c, lv0, P->d_ltsum, P->ltsum_n, np0))) return rc;
+    } else if ((rc = lt_accumulate(c, lv0, np0, lv0, dbl, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) {
+        return rc;
+    }
     for (auto &ch : P->rchunks) {
         if (dbl) {
             if ((rc = ksw_ip(c, lv0, ch.d_rots, ch.cnt))) return rc;
@@ -773,6 +865,9 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     }
     const int dbl = c->ks_double ? 1 : 0;
     key.push_back(dbl);
+    key.push_back(dbl ? c->lt_chunk : 0);
+    key.push_back(dbl ? c->lt_fused : 0);
+    key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
@@ -850,6 +945,27 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {
         return set_err(&h->c, HEGMM_EINVAL, "key-switch mode must be HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE");
     h->c.ks_double = mode == HEGMM_KS_DOUBLE;
     return HEGMM_OK;
+}
+
+int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
+    if (!h) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (knob == HEGMM_TUNE_LT_CHUNK) {
+        if (value < 1 || value > 4096) return set_err(c, HEGMM_EINVAL, "lt_chunk must be in 1..4096");
+        c->lt_chunk = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_LT_KERNEL) {
+        if (value < 0 || value > 4) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..4");
+        c->lt_kernel = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_LT_FUSED) {
+        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "lt_fused must be 0 or 1");
+        c->lt_fused = (int)value;
+        return HEGMM_OK;
+    }
+    return set_err(c, HEGMM_EINVAL, "unknown tuning knob");
 }
 
 int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {

@@ -233,6 +233,9 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         cand -= two_n;
     }
     if (got != c->np) return set_err(c, HEGMM_EINVAL, "not enough NTT primes");
+    // the key inner product sums dnum products (+ one folded term) below q 2^64 before one reduction
+    if ((u128)(c->dnum + 2) * c->q[0] >= ((u128)1 << 64))
+        return set_err(c, HEGMM_EINVAL, "primes too large for dnum: (dnum + 2) q must stay below 2^64");
     c->q[c->tmod] = p->t;
     for (int i = 0; i < c->nmod; i++) {
         const u64 q = c->q[i];
@@ -743,7 +746,7 @@ void hegmm_ct_destroy(hegmm_ct *ct) {
 static const char *kKernelNames[K_NUM] = {"ntt_fwd",     "ntt_inv",      "modup",         "ksw_inner_product",
                                           "div_conv",    "div_combine",  "divround_ntt",  "lt_accumulate",
                                           "tensor",      "sum",          "pointwise",     "sample",
-                                          "codec"};
+                                          "codec",       "lt_keyswitch"};
 
 int hegmm_set_timing(hegmm_ctx *h, int enable) {
     if (!h) return HEGMM_EINVAL;

@@ -72,6 +72,19 @@ struct DivDesc {
 
 // A product output of the linear-transformation accumulation:
 // out[c][i] (+)= sum over terms src[c][i] * mask[i].
+// One term of a double-hoisted linear transformation (Eq. lintrans):
+// mask (.) (u_g + P tau_g(c0), u1_g) with u_g the key-switch inner product
+// of the hoisted digits D under tau_g, or, for the d = 0 term (key null),
+// mask (.) P ct.  Sums over PQ; the caller divides by P once (ModDown).
+struct LtKsTerm {
+    const u64 *D;     // hoisted digits of the source [nd][ne][N] (NTT)
+    const u64 *key;   // Galois key [nd][2][L+K][N], Montgomery NTT; null: the d = 0 term
+    const u64 *ct;    // the source ciphertext [2][lv][N] (NTT)
+    const u64 *mask;  // [L + K][N] Montgomery NTT
+    u32 g;
+    u32 pad;
+};
+
 struct LtTerm {
     const u64 *src;  // [2][np][N]: a ciphertext (np = lv) or a key-switch output over PQ (np = lv + K)
     const u64 *mask; // [L + K][N] Montgomery NTT, limb = global prime index
@@ -96,6 +109,7 @@ enum KernelKind {
     K_POINTWISE,
     K_SAMPLE,
     K_CODEC,
+    K_LT_KSW,
     K_NUM
 };
 
@@ -151,6 +165,9 @@ struct Ctx {
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
+    int lt_chunk = 32;                         // double mode: terms per k_lt_ksw work item
+    int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
+    int lt_kernel = 3;                         // fused kernel variant (coefficients per thread, CTAs per SM)
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
@@ -227,6 +244,10 @@ int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_terms, const int *d_off,
                   u64 *const *d_outs, int nout, int accumulate);
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
+// outs[o] = sum over the terms [off[o], off[o+1]) of LtKsTerm contributions,
+// over the extended basis of level lv ([2][lv+K][N] per output).  Needs
+// (terms per output + 2) * q < 2^64 for every prime (lazy 128-bit sums).
+int lt_ksw(Ctx *c, int lv, const LtKsTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout, double nterms);
 // out[poly] = sum_k in[k][poly] over nk inputs with stride in_stride words; npolylimbs = 2*lv
 int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate);
 // pointwise helpers over [npoly][lv][N]

@@ -51,6 +51,7 @@ static __device__ __forceinline__ u64 *pat_ptr(const LimbPat &p, int b, int N, i
     return base + (size_t)p.off[in] * N;
 }
 
+constexpr int kMaxGridZ = 65535;  // grid.z limit; launches over more items are split
 static inline dim3 grid_coef(int N, int y, int z) { return dim3((unsigned)((N + 255) / 256), (unsigned)y, (unsigned)z); }
 
 // ------------------------------------------------------------------ NTT
@@ -449,8 +450,155 @@ int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
     // (2 ne limbs) written; the hoisted digits are shared by every rotation
     // of a source and served from L2, so they are not counted.
     Launch t(c, K_KSW_IP, (double)nrot * (2.0 * nd * ne + 2.0 * ne) * c->limb_bytes());
-    k_ksw_ip<<<grid_coef(c->N / 2, ne, nrot), 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots);
+    for (int r0 = 0; r0 < nrot; r0 += kMaxGridZ)
+        k_ksw_ip<<<grid_coef(c->N / 2, ne, std::min(kMaxGridZ, nrot - r0)), 256, 0, c->st>>>(
+            lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_rots + r0);
     return cuda_check(c, "ksw_ip");
+}
+
+// Double-hoisted linear transformation, one CTA row per (work item, limb):
+// every term's key-switch inner product is formed in registers and enters
+// the item's sum at once (no per-rotation output in memory):
+//   acc_c = sum_terms mask * u_c,  u_0 = <tau_g(D), k_0> + P tau_g(c0),
+//   u_1 = <tau_g(D), k_1>;  d = 0 terms: u_c = P c_c (0 on special primes).
+// Both sums are lazy 128-bit Montgomery sums (terms * q^2 < q 2^64).
+// CPT coefficients per thread (1: 8-byte loads, more threads; 2: 16-byte
+// loads); MINB resident CTAs per SM (the register cap).
+template <int CPT>
+struct Coefs {
+    u64 v[CPT];
+};
+template <int CPT>
+__device__ __forceinline__ Coefs<CPT> ld_coefs(const u64 *p) {
+    Coefs<CPT> r;
+    if constexpr (CPT == 2) {
+        const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+        r.v[0] = x.x;
+        r.v[1] = x.y;
+    } else {
+        r.v[0] = __ldg(p);
+    }
+    return r;
+}
+template <int CPT>
+__device__ __forceinline__ Coefs<CPT> ld_coefs_stream(const u64 *p) {
+    Coefs<CPT> r;
+    if constexpr (CPT == 2) {
+        const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
+        r.v[0] = x.x;
+        r.v[1] = x.y;
+    } else {
+        r.v[0] = __ldcs(p);
+    }
+    return r;
+}
+template <int CPT>
+__device__ __forceinline__ void st_coefs(u64 *p, const u64 *v) {
+    if constexpr (CPT == 2) {
+        ulonglong2 x;
+        x.x = v[0];
+        x.y = v[1];
+        *reinterpret_cast<ulonglong2 *>(p) = x;
+    } else {
+        *p = v[0];
+    }
+}
+
+template <int CPT, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lt_ksw(int lv, int ne, int nd, int np, int L, int logN,
+                                                   const ModDev *__restrict__ mods, const LtKsTerm *__restrict__ terms,
+                                                   const int *__restrict__ off, u64 *const *__restrict__ outs) {
+    const int N = 1 << logN;
+    const int c = CPT * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (c >= N) return;
+    const int e = blockIdx.y, o = blockIdx.z;
+    const int gm = e < lv ? e : L + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N;
+    Acc s0[CPT], s1[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; i++) s0[i] = s1[i] = Acc{0, 0};
+    const int t1 = off[o + 1];
+    for (int t = off[o]; t < t1; t++) {
+        const LtKsTerm T = terms[t];
+        u64 u0[CPT], u1[CPT];
+        if (T.key) {
+            u32 src[CPT];
+#pragma unroll
+            for (int i = 0; i < CPT; i++) src[i] = auto_src((u32)(c + i), T.g, logN);
+            const u64 *Dp = T.D + (size_t)e * N;
+            const u64 *Kp = T.key + (size_t)gm * N + c;
+            Acc a0[CPT], a1[CPT];
+#pragma unroll
+            for (int i = 0; i < CPT; i++) a0[i] = a1[i] = Acc{0, 0};
+#pragma unroll 4
+            for (int j = 0; j < nd; j++) {
+                const Coefs<CPT> k0 = ld_coefs_stream<CPT>(Kp + (size_t)(2 * j) * kstep);
+                const Coefs<CPT> k1 = ld_coefs_stream<CPT>(Kp + (size_t)(2 * j + 1) * kstep);
+#pragma unroll
+                for (int i = 0; i < CPT; i++) {
+                    const u64 x = __ldg(Dp + (size_t)j * dstep + src[i]);
+                    mac(a0[i], x, k0.v[i]);
+                    mac(a1[i], x, k1.v[i]);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < CPT; i++) {
+                if (e < lv) mac(a0[i], __ldg(T.ct + (size_t)e * N + src[i]), pR);
+                u0[i] = montred(a0[i], q, qinv);
+                u1[i] = montred(a1[i], q, qinv);
+            }
+        } else {
+            if (e >= lv) continue;
+            const Coefs<CPT> x = ld_coefs<CPT>(T.ct + (size_t)e * N + c);
+            const Coefs<CPT> y = ld_coefs<CPT>(T.ct + ((size_t)lv + e) * N + c);
+#pragma unroll
+            for (int i = 0; i < CPT; i++) {
+                u0[i] = montmul(x.v[i], pR, q, qinv);
+                u1[i] = montmul(y.v[i], pR, q, qinv);
+            }
+        }
+        const Coefs<CPT> m = ld_coefs<CPT>(T.mask + (size_t)gm * N + c);
+#pragma unroll
+        for (int i = 0; i < CPT; i++) {
+            mac(s0[i], u0[i], m.v[i]);
+            mac(s1[i], u1[i], m.v[i]);
+        }
+    }
+    u64 *out = outs[o];
+    u64 r0[CPT], r1[CPT];
+#pragma unroll
+    for (int i = 0; i < CPT; i++) {
+        r0[i] = montred(s0[i], q, qinv);
+        r1[i] = montred(s1[i], q, qinv);
+    }
+    st_coefs<CPT>(out + (size_t)e * N + c, r0);
+    st_coefs<CPT>(out + ((size_t)ne + e) * N + c, r1);
+}
+
+template <int CPT, int MINB>
+static void launch_lt_ksw(Ctx *c, int lv, int ne, int nd, const LtKsTerm *d_terms, const int *d_off,
+                          u64 *const *d_outs, int nout) {
+    for (int o0 = 0; o0 < nout; o0 += kMaxGridZ)  // term offsets are absolute, so a slice needs no rebasing
+        k_lt_ksw<CPT, MINB><<<grid_coef(c->N / CPT, ne, std::min(kMaxGridZ, nout - o0)), 256, 0, c->st>>>(
+            lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_terms, d_off + o0, d_outs + o0);
+}
+
+int lt_ksw(Ctx *c, int lv, const LtKsTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout, double nterms) {
+    if (nout <= 0) return HEGMM_OK;
+    const int ne = lv + c->K, nd = c->digits(lv);
+    // algorithmic HBM bytes: per key-switched term its key (2 nd ne limbs)
+    // and mask (ne limbs); per output its sum (2 ne limbs) written.  Digits
+    // and sources are shared by all terms of a source and served from L2.
+    Launch t(c, K_LT_KSW, (nterms * (2.0 * nd * ne + ne) + (double)nout * 2.0 * ne) * c->limb_bytes());
+    switch (c->lt_kernel) {
+        case 1: launch_lt_ksw<2, 4>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+        case 2: launch_lt_ksw<1, 4>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+        case 3: launch_lt_ksw<1, 6>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+        case 4: launch_lt_ksw<1, 8>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+        default: launch_lt_ksw<2, 3>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+    }
+    return cuda_check(c, "lt_ksw");
 }
 
 // ------------------------------------------------------------------ exact division by D with t-correction
@@ -557,8 +705,9 @@ int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_
                   u64 *const *d_outs, int nout, int accumulate) {
     if (nout <= 0) return HEGMM_OK;
     Launch t(c, K_LT_ACC, 0.0);
-    k_lt_acc<<<grid_coef(c->N, 2 * np, nout), 256, 0, c->st>>>(lv, np, src_np, lift, c->L, c->logN, c->d_mods,
-                                                               d_terms, d_off, d_outs, accumulate);
+    for (int o0 = 0; o0 < nout; o0 += kMaxGridZ)
+        k_lt_acc<<<grid_coef(c->N, 2 * np, std::min(kMaxGridZ, nout - o0)), 256, 0, c->st>>>(
+            lv, np, src_np, lift, c->L, c->logN, c->d_mods, d_terms, d_off + o0, d_outs + o0, accumulate);
     return cuda_check(c, "lt_acc");
 }
 
@@ -583,7 +732,8 @@ __global__ void k_tensor(int lv, int logN, const ModDev *__restrict__ mods, cons
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n) {
     if (n <= 0) return HEGMM_OK;
     Launch t(c, K_TENSOR, (double)n * 7.0 * lv * c->limb_bytes());
-    k_tensor<<<grid_coef(c->N, lv, n), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_t);
+    for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
+        k_tensor<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_t + i0);
     return cuda_check(c, "tensor");
 }
 
@@ -628,7 +778,9 @@ int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np) {
     if (n <= 0) return HEGMM_OK;
     if (np <= 0) np = lv;
     Launch t(c, K_SUM, 0.0);
-    k_sum_desc<<<grid_coef(c->N, 2 * np, n), 256, 0, c->st>>>(lv, np, c->L, c->logN, c->d_mods, d_sums);
+    for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
+        k_sum_desc<<<grid_coef(c->N, 2 * np, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, np, c->L, c->logN,
+                                                                                          c->d_mods, d_sums + i0);
     return cuda_check(c, "sum_desc");
 }
 
@@ -713,7 +865,9 @@ __global__ void k_gather_cts(int lv, int logN, u64 *const *__restrict__ src, u64
 int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst) {
     if (n <= 0) return HEGMM_OK;
     Launch t(c, K_POINTWISE, 2.0 * n * 2 * lv * c->limb_bytes());
-    k_gather_cts<<<grid_coef(c->N / 2, 2 * lv, n), 256, 0, c->st>>>(lv, c->logN, d_src, dst);
+    for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
+        k_gather_cts<<<grid_coef(c->N / 2, 2 * lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(
+            lv, c->logN, d_src + i0, dst + (size_t)i0 * 2 * lv * c->N);
     return cuda_check(c, "gather_cts");
 }
 

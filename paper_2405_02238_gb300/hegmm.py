@@ -20,6 +20,7 @@ HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE = 0, 1  # hegmm_set_keyswitch_mode
+TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL = 1, 2, 3  # hegmm_set_tuning
 ROLE_A, ROLE_B = 0, 1
 
 
@@ -108,6 +109,7 @@ _SIGS = {
     "hegmm_peak_butterflies": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
     "hegmm_prepare": (ctypes.c_int, [vp, intp, ctypes.c_int, ctypes.c_int]),
     "hegmm_set_keyswitch_mode": (ctypes.c_int, [vp, ctypes.c_int]),
+    "hegmm_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
     "hegmm_set_budgets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]),
     "hegmm_server_create": (ctypes.c_int, [vp, ctypes.POINTER(hegmm_server_opts), ctypes.POINTER(vp)]),
     "hegmm_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -242,6 +244,9 @@ class Context:
     def hegmm_set_keyswitch_mode(self, mode: int):
         """KS_SINGLE: one ModDown per key switch; KS_DOUBLE: sums kept over PQ."""
         self._check(self.lib.hegmm_set_keyswitch_mode(self.h, int(mode)), "set_keyswitch_mode")
+
+    def hegmm_set_tuning(self, knob: int, value: int):
+        self._check(self.lib.hegmm_set_tuning(self.h, int(knob), int(value)), "set_tuning")
 
     def hegmm_set_budgets(self, mask_bytes: int = 0, plan_bytes: int = 0, chunk_bytes: int = 0):
         self._check(self.lib.hegmm_set_budgets(self.h, mask_bytes, plan_bytes, chunk_bytes), "set_budgets")

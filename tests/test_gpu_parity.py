@@ -153,6 +153,23 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
     run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE, mode=mode)
 
 
+@pytest.mark.parametrize("chunk,variant,fused", [(1, 3, 1), (3, 0, 1), (4096, 1, 1), (32, 2, 1), (32, 4, 1),
+                                                  (32, 3, 0)])
+def test_double_mode_executor_settings(H, chunk, variant, fused):
+    # work-item size, fused-kernel variant and the chunked path change no bit
+    pre, ctx, o = get_pair(H, "tiny")
+    ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, chunk)
+    ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, variant)
+    ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, fused)
+    try:
+        run_both(H, "tiny", 4, 8, 6, 1, *W.TINY_RANGE, mode="double")
+        run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double", seed=3)
+    finally:
+        ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
+        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 3)
+        ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, 1)
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 1), (3, 3, 3), (5, 12, 7), (9, 4, 11), (7, 9, 2), (2, 5, 7),
                                    (5, 4, 2), (12, 3, 9)])
 def test_hegmm_tiny_edge_shapes(H, shape):
