@@ -440,17 +440,22 @@ class HEGMM:
 
     MODES = ("single", "double")
 
-    def __init__(self, o: Oracle, mode: str = "single"):
+    def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False):
         """mode "single": every key switch ends in its own ModDown, as the
         HE operations Rot, CMult, Mult and Add compose (the paper's cost
         model).  mode "double": the sums of key-switched terms (each linear
         transformation, the HE-Add of the per-iteration products, the
         extraction sum) are formed over the extended basis PQ and take one
-        ModDown each; decrypts to the same product, with lower noise."""
+        ModDown each; decrypts to the same product, with lower noise.
+        lazy_relin: the per-iteration tensors (d0, d1, d2) are summed first
+        and the sum is relinearised once (one key switch per product instead
+        of one per HE-Mult); in double mode that key switch keeps P (d0, d1)
+        in its sum over PQ."""
         if mode not in self.MODES:
             raise ValueError(mode)
         self.o = o
         self.mode = mode
+        self.lazy_relin = lazy_relin
         self._mask_cache: Dict[Tuple, np.ndarray] = {}
 
     def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
@@ -523,12 +528,17 @@ class HEGMM:
         scale = mask_scale(o)
         C = None
         acc = None
+        dsum = None
         for e, om in plan.iters:
             a = self.lt(ctA, e, scale)
             b = self.lt(ctB, om, scale)
             for _ in range(o.pre.ms_drop):
                 a = o.modswitch(a)
                 b = o.modswitch(b)
+            if self.lazy_relin:
+                d = o.tensor(a, b)
+                dsum = d if dsum is None else o.add(dsum, d)
+                continue
             if self.mode == "double":
                 # HE-Mult without its ModDown, summed over PQ (Eq. of C)
                 d = o.tensor(a, b)
@@ -538,6 +548,14 @@ class HEGMM:
                 continue
             prod = o.mult_relin(a, b)
             C = prod if C is None else o.add(C, prod)
+        if self.lazy_relin:
+            # one relinearisation of the summed tensor (Eq. elementwise's
+            # sum taken before the key switch)
+            if self.mode == "double":
+                u = o.ks_raw(o.modup(dsum[2]), 0)
+                acc = np.stack([o.pq_add(u[0], o.pq_lift(dsum[0])), o.pq_add(u[1], o.pq_lift(dsum[1]))])
+            else:
+                C = o.add(np.ascontiguousarray(dsum[:2]), o.keyswitch(dsum[2], 0))
         if self.mode == "double":
             C = o.moddown_pair(acc)
             if not plan.extract:

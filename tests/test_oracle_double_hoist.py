@@ -157,3 +157,59 @@ def test_hegmm_double_mode_two_prime_digits(d2):
     ex = he.HEGMM(o, mode="double")
     ctA, ctB = ex.encrypt_inputs(plan, A, B)
     assert (ex.result(plan, ex.run(plan, ctA, ctB)) == (A @ B) % o.t).all()
+
+
+@pytest.mark.parametrize("mode", ["single", "double"])
+def test_lazy_relin_of_one_product_is_mult(tiny, mode):
+    # with a single iteration the summed tensor is the tensor itself, so the
+    # lazy relinearisation must equal HE-Mult bit for bit in either mode
+    o = tiny
+    rng = np.random.default_rng(26)
+    x, y = rng.integers(0, o.t, o.S), rng.integers(0, o.t, o.S)
+    a, b = o.encrypt(o.encode(x), 8, 0), o.encrypt(o.encode(y), 8, 1)
+    plan = SL.make_plan(1, 1, 1, 1)  # one iteration, one product
+    ex = he.HEGMM(o, mode=mode, lazy_relin=True)
+    d = o.tensor(a, b)
+    if mode == "double":
+        u = o.ks_raw(o.modup(d[2]), 0)
+        got = o.moddown_pair(np.stack([o.pq_add(u[0], o.pq_lift(d[0])), o.pq_add(u[1], o.pq_lift(d[1]))]))
+    else:
+        got = o.add(np.ascontiguousarray(d[:2]), o.keyswitch(d[2], 0))
+    assert (got == o.mult_relin(a, b)).all()
+    # and a one-iteration product run lazily equals the eager run
+    assert len(plan.iters) == 1
+    A, B = np.array([[3]]), np.array([[5]])
+    eager = he.HEGMM(o, mode=mode)
+    ctA, ctB = eager.encrypt_inputs(plan, A, B, seed=4)
+    assert (ex.run(plan, ctA, ctB) == eager.run(plan, ctA, ctB)).all()
+
+
+def test_lazy_relin_sum_decrypts_to_sum_of_products(tiny):
+    o = tiny
+    rng = np.random.default_rng(27)
+    xs = [rng.integers(0, o.t, o.S) for _ in range(6)]
+    cts = [o.encrypt(o.encode(x), 9, i) for i, x in enumerate(xs)]
+    dsum = None
+    for k in range(3):
+        d = o.tensor(cts[2 * k], cts[2 * k + 1])
+        dsum = d if dsum is None else o.add(dsum, d)
+    C = o.add(np.ascontiguousarray(dsum[:2]), o.keyswitch(dsum[2], 0))
+    want = (xs[0] * xs[1] + xs[2] * xs[3] + xs[4] * xs[5]) % o.t
+    assert (o.decrypt_slots(C) == want).all()
+
+
+@pytest.mark.parametrize("mode", ["single", "double"])
+@pytest.mark.parametrize("alg", [1, 2])
+def test_hegmm_lazy_relin_tiny(tiny, mode, alg):
+    o = tiny
+    A, B = W.matrices(4, 8, 6, *W.TINY_RANGE)
+    plan = SL.make_plan(4, 8, 6, alg)
+    ex = he.HEGMM(o, mode=mode, lazy_relin=True)
+    ctA, ctB = ex.encrypt_inputs(plan, A, B)
+    o.counts = {}
+    C = ex.run(plan, ctA, ctB)
+    assert (ex.result(plan, C) == (A @ B) % o.t).all()
+    # one relinearisation key switch per product
+    assert o.counts.get("mult", 0) == 0
+    _, noise, budget = o.decrypt(C)
+    assert noise < budget - 4
