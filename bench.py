@@ -42,6 +42,8 @@ UNIT = "matmul/s"
 KEY_SEED = 7
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
+# hegmm_set_keyswitch_mode flags per --ks-mode (KS_DOUBLE = 1, KS_LAZY_RELIN = 2)
+KS_MODES = {"double+lazy": 3, "double": 1, "single": 0, "single+lazy": 2}
 
 
 def workload_config(extra=None):
@@ -227,7 +229,7 @@ def run_serve(args):
     stream = torch.cuda.Stream(device=dev)
     pre = W.PAPER
     ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
-    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if args.ks_mode == "double" else H.KS_SINGLE)
+    ctx.hegmm_set_keyswitch_mode(KS_MODES[args.ks_mode])
     rates = [float(r) for r in args.rates.split(",")]
     per_rate = {}
     for r in rates:
@@ -326,7 +328,7 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1000)
     ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
-    ap.add_argument("--ks-mode", default="double", choices=["double", "single"],
+    ap.add_argument("--ks-mode", default="double+lazy", choices=list(KS_MODES),
                     help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -352,7 +354,7 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     ctx = H.Context.from_preset(PRESET, stream=stream.cuda_stream)
-    ks_code = {"double": H.KS_DOUBLE, "single": H.KS_SINGLE}
+    ks_code = KS_MODES
     ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
     prods = []
     if args.workload == "batch":
@@ -458,7 +460,7 @@ def main():
     stats = ctx.hegmm_kernel_stats()
 
     # the other key-switch evaluation order on the same products, for comparison
-    other = "single" if args.ks_mode == "double" else "double"
+    other = "single" if args.ks_mode != "single" else "double+lazy"
     ctx.hegmm_set_keyswitch_mode(ks_code[other])
     outs = step()
     for (m, l, n, alg, A, Bm), c in zip(prods, outs):

@@ -163,9 +163,15 @@ int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, cons
  *     (with P tau(c0), P d0, P d1 folded in) and divided by P once
  *     ("double hoisting"; ModDown(u + P x) = ModDown(u) + x).  Fewer
  *     ModDowns, lower noise.
- * Applies to products started after the call.  Errors: HEGMM_EINVAL. */
+ *   | HEGMM_KS_LAZY_RELIN (with either): the tensors (d0, d1, d2) of all
+ *     iterations of a product are summed and the sum is relinearised once
+ *     (one key switch per product instead of one per HE-Mult; the sum of
+ *     Eq. elementwise taken before the key switch).
+ * Each mode is bit-exact with the oracle's mode of the same name.  Applies
+ * to products started after the call.  Errors: HEGMM_EINVAL. */
 #define HEGMM_KS_SINGLE 0
 #define HEGMM_KS_DOUBLE 1
+#define HEGMM_KS_LAZY_RELIN 2
 int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
 
 /* Tuning knobs of the product executor (no effect on results; plans built

@@ -80,7 +80,12 @@ struct RelinChunk {
 struct BatchPlan {
     std::vector<ShapeData *> shp;
     int B = 0, lv0 = 0, lv1 = 0, O = 0, E = 0, X = 0;
-    int dbl = 0;  // sums of key switches kept over PQ (one ModDown per sum)
+    int dbl = 0;   // sums of key switches kept over PQ (one ModDown per sum)
+    int lazy = 0;  // one relinearisation per product, of its summed tensors
+    u64 *d3s = nullptr, *lxc = nullptr, *lD = nullptr, *lu = nullptr;
+    TensorSum *d_tsum = nullptr;
+    RotDesc *d_lrot = nullptr;
+    DivDesc *d_ldiv = nullptr;
     int fused = 0;  // double mode: every linear transformation in one k_lt_ksw launch
     LtKsTerm *d_ltks = nullptr;
     int *d_ltks_off = nullptr;
@@ -322,10 +327,11 @@ static void add_counts(hegmm_opcount &a, const hegmm_opcount &b) {
 }
 
 // shapes: B entries of (m, l, n, resolved alg)
-static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, BatchPlan **out) {
+static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, int lazy, BatchPlan **out) {
     const int N = c->N;
     BatchPlan *P = new BatchPlan;
     P->dbl = dbl;
+    P->lazy = lazy;
     auto fail_rc = [&](int rc) {
         free_bplan(c, P);
         return rc;
@@ -385,8 +391,15 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             for (int zi = 0; zi < (int)P->shp[p]->zs[s].size(); zi++) ritems.push_back({p, s, zi});
         }
     std::vector<std::pair<int, int>> litems;
-    for (int p = 0; p < B; p++)
+    for (int p = 0; p < B && !lazy; p++)
         for (int k = 0; k < niter[p]; k++) litems.push_back({p, k});
+    if (lazy) {
+        // lazy tensor sums: (2 iterations + 2) q < 2^64
+        int imax = 0;
+        for (int p = 0; p < B; p++) imax = std::max(imax, niter[p]);
+        if ((unsigned __int128)(2 * imax + 2) * c->q[0] >= ((unsigned __int128)1 << 64))
+            return fail_rc(set_err(c, HEGMM_EINVAL, "lazy relinearisation: too many iterations for one tensor sum"));
+    }
     const int R = (int)ritems.size(), I = (int)litems.size();
     // double mode fuses each linear transformation's inner products and mask
     // sums into one kernel when its lazy 128-bit sums cannot overflow:
@@ -431,7 +444,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                  o_cacc = take((size_t)B * 2 * lv1 * N), o_cpq = dbl ? take((size_t)B * 2 * ne1 * N) : 0,
                  o_exc = take(E1 * lv1 * N), o_eD = take(E1 * nd1 * ne1 * N), o_eu = take(X1 * 2 * ne1 * N),
                  o_erot = dbl ? 0 : take(X1 * 2 * lv1 * N), o_xacc = dbl ? take(E1 * 2 * ne1 * N) : 0,
-                 o_xout = dbl ? take(E1 * 2 * lv1 * N) : 0;
+                 o_xout = dbl ? take(E1 * 2 * lv1 * N) : 0, o_d3s = lazy ? take((size_t)B * 3 * lv1 * N) : 0,
+                 o_lxc = lazy ? take((size_t)B * lv1 * N) : 0, o_lD = lazy ? take((size_t)B * nd1 * ne1 * N) : 0,
+                 o_lu = lazy && !dbl ? take((size_t)B * 2 * ne1 * N) : 0;
     P->ws_bytes = off * 8;
     P->ws = (u64 *)plan_alloc(c, P, off * 8);
     if (!P->ws) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch workspace"));
@@ -446,6 +461,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     P->cpq = dbl ? W + o_cpq : nullptr;
     P->xacc = dbl ? W + o_xacc : nullptr;
     P->xout = dbl ? W + o_xout : nullptr;
+    P->d3s = lazy ? W + o_d3s : nullptr;
+    P->lxc = lazy ? W + o_lxc : nullptr;
+    P->lD = lazy ? W + o_lD : nullptr;
+    P->lu = lazy && !dbl ? W + o_lu : nullptr;
     P->outs = W + o_outs;
     P->ms = lv1 != lv0 ? W + o_ms : nullptr;
     P->d3 = W + o_d3;
@@ -675,6 +694,43 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->lchunks.push_back(ch);
     }
+    // lazy relinearisation: per product the sum of its iterations' tensors,
+    // one hoisted ModUp of the summed d2 and one key switch (P d0, P d1
+    // folded into the inner product)
+    if (lazy) {
+        std::vector<TensorSum> ts;
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        for (int p = 0; p < B; p++) {
+            TensorSum T{};
+            T.a = A1 + (size_t)obase[p] * 2 * lv1 * N;
+            T.b = A1 + ((size_t)obase[p] + niter[p]) * 2 * lv1 * N;
+            T.stride = (long long)2 * lv1 * N;
+            T.d = P->d3s + (size_t)p * 3 * lv1 * N;
+            T.count = niter[p];
+            ts.push_back(T);
+            u64 *u = dbl ? P->cpq + (size_t)cslot[p] * 2 * ne1 * N : P->lu + (size_t)p * 2 * ne1 * N;
+            rd.push_back({P->lD + (size_t)p * nd1 * ne1 * N, rlk, u, T.d, T.d + (size_t)lv1 * N, 1u, 0u});
+            for (int comp = 0; comp < 2 && !dbl; comp++) {
+                DivDesc v{};
+                v.u = u + (size_t)comp * ne1 * N;
+                v.out = P->cacc + ((size_t)cslot[p] * 2 + comp) * lv1 * N;
+                v.g = 1;
+                dd.push_back(v);
+            }
+        }
+        P->d_tsum = plan_upload(c, P, ts);
+        P->d_lrot = plan_upload(c, P, rd);
+        P->d_ldiv = dbl ? nullptr : plan_upload(c, P, dd);
+        if (!keep(P->d_tsum) || !keep(P->d_lrot) || (!dbl && !keep(P->d_ldiv)))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        // executed key switches and ModUps: one relinearisation per product
+        for (int p = 0; p < B; p++) {
+            P->cnt.relin -= niter[p] - 1;
+            P->cnt.ksw -= niter[p] - 1;
+            P->cnt.modup -= niter[p] - 1;
+        }
+    }
     // extraction rotations (Algorithm 2)
     if (X > 0) {
         std::vector<RotDesc> rd;
@@ -786,7 +842,17 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
     if (lv1 != lv0)
         if ((rc = modswitch_polys(c, lv0, P->outs, 2 * P->O, nullptr, P->ms, P->d_msdiv))) return rc;
     // 4. HE-Mult of every iteration and the sum per product
-    cudaMemsetAsync(dbl ? P->cpq : P->cacc, 0, (size_t)B * 2 * np1 * N * 8, c->st);
+    if (P->lazy) {
+        if ((rc = tensor_sum(c, lv1, P->d_tsum, B))) return rc;
+        if ((rc = modup(c, lv1, B, P->d3s + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->lxc, P->lD))) return rc;
+        if (dbl) {
+            if ((rc = ksw_ip(c, lv1, P->d_lrot, B))) return rc;
+        } else {
+            if ((rc = ksw_moddown(c, lv1, P->d_lrot, P->d_ldiv, B, P->lu, nullptr))) return rc;
+        }
+    } else {
+        cudaMemsetAsync(dbl ? P->cpq : P->cacc, 0, (size_t)B * 2 * np1 * N * 8, c->st);
+    }
     for (auto &ch : P->lchunks) {
         if ((rc = tensor(c, lv1, ch.d_tens, ch.cnt))) return rc;
         if ((rc = modup(c, lv1, ch.cnt, P->d3 + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->rxc, P->rD))) return rc;
@@ -863,8 +929,9 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
         shapes.push_back({m, l, n, a});
         key.insert(key.end(), {m, l, n, a});
     }
-    const int dbl = c->ks_double ? 1 : 0;
+    const int dbl = c->ks_double ? 1 : 0, lazy = c->lazy_relin ? 1 : 0;
     key.push_back(dbl);
+    key.push_back(lazy);
     key.push_back(dbl ? c->lt_chunk : 0);
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
@@ -873,7 +940,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     if (it != c->bplans.end()) {
         P = it->second;
     } else {
-        int rc = build_bplan(c, shapes, dbl, &P);
+        int rc = build_bplan(c, shapes, dbl, lazy, &P);
         if (rc) return rc;
         if (cache) {
             evict_plans(c, P->ws_bytes);
@@ -941,9 +1008,10 @@ int hegmm_matmul_batch(hegmm_ctx *h, int count, const hegmm_ct *const *A, const 
 
 int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {
     if (!h) return HEGMM_EINVAL;
-    if (mode != HEGMM_KS_SINGLE && mode != HEGMM_KS_DOUBLE)
-        return set_err(&h->c, HEGMM_EINVAL, "key-switch mode must be HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE");
-    h->c.ks_double = mode == HEGMM_KS_DOUBLE;
+    if (mode < 0 || mode > (HEGMM_KS_DOUBLE | HEGMM_KS_LAZY_RELIN))
+        return set_err(&h->c, HEGMM_EINVAL, "key-switch mode: HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE, optionally | HEGMM_KS_LAZY_RELIN");
+    h->c.ks_double = (mode & HEGMM_KS_DOUBLE) != 0;
+    h->c.lazy_relin = (mode & HEGMM_KS_LAZY_RELIN) != 0;
     return HEGMM_OK;
 }
 

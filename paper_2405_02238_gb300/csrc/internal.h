@@ -85,6 +85,17 @@ struct LtKsTerm {
     u32 pad;
 };
 
+// Sum of the tensors of count iteration products: d = sum_k (a_k0 b_k0,
+// a_k0 b_k1 + a_k1 b_k0, a_k1 b_k1), a_k = a + k stride, b_k = b + k stride.
+struct TensorSum {
+    const u64 *a;
+    const u64 *b;
+    long long stride;
+    u64 *d;  // [3][lv][N]
+    int count;
+    int pad;
+};
+
 struct LtTerm {
     const u64 *src;  // [2][np][N]: a ciphertext (np = lv) or a key-switch output over PQ (np = lv + K)
     const u64 *mask; // [L + K][N] Montgomery NTT, limb = global prime index
@@ -165,6 +176,7 @@ struct Ctx {
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
+    int lazy_relin = 0;                        // products: one relinearisation of the summed tensors
     int lt_chunk = 32;                         // double mode: terms per k_lt_ksw work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
     int lt_kernel = 3;                         // fused kernel variant (coefficients per thread, CTAs per SM)
@@ -244,6 +256,8 @@ int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_terms, const int *d_off,
                   u64 *const *d_outs, int nout, int accumulate);
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
+// n tensor sums (lazy 128-bit: (2 count + 2) q < 2^64)
+int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n);
 // outs[o] = sum over the terms [off[o], off[o+1]) of LtKsTerm contributions,
 // over the extended basis of level lv ([2][lv+K][N] per output).  Needs
 // (terms per output + 2) * q < 2^64 for every prime (lazy 128-bit sums).

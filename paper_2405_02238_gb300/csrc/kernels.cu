@@ -729,6 +729,41 @@ __global__ void k_tensor(int lv, int logN, const ModDev *__restrict__ mods, cons
     T.d[((size_t)2 * lv + i) * N + c] = montmul(a1, b1, M.q, M.qinv);
 }
 
+// One thread per coefficient of one limb of one sum; the products of all
+// iterations are summed lazily (Montgomery, b taken to b R first).
+__global__ void k_tensor_sum(int lv, int logN, const ModDev *__restrict__ mods, const TensorSum *__restrict__ ts) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int i = blockIdx.y;
+    const TensorSum T = ts[blockIdx.z];
+    const ModDev M = mods[i];
+    Acc s0{0, 0}, s1{0, 0}, s2{0, 0};
+    const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
+    for (int k = 0; k < T.count; k++) {
+        const u64 *a = T.a + (size_t)k * T.stride, *b = T.b + (size_t)k * T.stride;
+        const u64 a0 = __ldg(a + o0), a1 = __ldg(a + o1);
+        const u64 b0 = montmul(__ldg(b + o0), M.r2, M.q, M.qinv);  // b R
+        const u64 b1 = montmul(__ldg(b + o1), M.r2, M.q, M.qinv);
+        mac(s0, a0, b0);
+        mac(s1, a0, b1);
+        mac(s1, a1, b0);
+        mac(s2, a1, b1);
+    }
+    T.d[o0] = montred(s0, M.q, M.qinv);
+    T.d[o1] = montred(s1, M.q, M.qinv);
+    T.d[((size_t)2 * lv + i) * N + c] = montred(s2, M.q, M.qinv);
+}
+
+int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n) {
+    if (n <= 0) return HEGMM_OK;
+    Launch t(c, K_TENSOR, 0.0);
+    for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
+        k_tensor_sum<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, c->logN, c->d_mods,
+                                                                                            d_t + i0);
+    return cuda_check(c, "tensor_sum");
+}
+
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n) {
     if (n <= 0) return HEGMM_OK;
     Launch t(c, K_TENSOR, (double)n * 7.0 * lv * c->limb_bytes());

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhegmm.so")
 HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
-KS_SINGLE, KS_DOUBLE = 0, 1  # hegmm_set_keyswitch_mode
+KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN = 0, 1, 2  # hegmm_set_keyswitch_mode (KS_LAZY_RELIN combines)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL = 1, 2, 3  # hegmm_set_tuning
 ROLE_A, ROLE_B = 0, 1
 
@@ -242,7 +242,8 @@ class Context:
         self._check(self.lib.hegmm_prepare(self.h, arr.ctypes.data_as(intp), len(shapes), alg), "prepare")
 
     def hegmm_set_keyswitch_mode(self, mode: int):
-        """KS_SINGLE: one ModDown per key switch; KS_DOUBLE: sums kept over PQ."""
+        """KS_SINGLE: one ModDown per key switch; KS_DOUBLE: sums kept over PQ;
+        | KS_LAZY_RELIN: one relinearisation per product."""
         self._check(self.lib.hegmm_set_keyswitch_mode(self.h, int(mode)), "set_keyswitch_mode")
 
     def hegmm_set_tuning(self, knob: int, value: int):

@@ -44,10 +44,11 @@ def encrypt_all(ctx, H, shapes, lo, hi, seed0=0, stream0=0):
     return As, Bs, mats
 
 
-@pytest.mark.parametrize("mode", ["double", "single"])
+@pytest.mark.parametrize("mode", ["double+lazy", "double", "single"])
 def test_batch_mixed_shapes_equal_single_and_oracle(H, medium, mode):
     ctx = medium
-    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if mode == "double" else H.KS_SINGLE)
+    base, _, lazy = mode.partition("+")
+    ctx.hegmm_set_keyswitch_mode((H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0))
     shapes = [(4, 8, 6), (5, 12, 7), (9, 4, 11), (7, 9, 2), (12, 3, 9), (3, 3, 3), (6, 40, 5), (20, 10, 30)]
     ctx.hegmm_keygen(SEED, shapes)
     As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE)
@@ -63,7 +64,7 @@ def test_batch_mixed_shapes_equal_single_and_oracle(H, medium, mode):
     for i in (0, 3):
         m, l, n = shapes[i]
         plan = SL.make_plan(m, l, n, SL.choose_alg(m, l, n, o.S))
-        ex = OH.HEGMM(o, mode=mode)
+        ex = OH.HEGMM(o, mode=base, lazy_relin=bool(lazy))
         ctA, ctB = ex.encrypt_inputs(plan, *mats[i], seed=77, streams=(2 * i, 2 * i + 1))
         assert (ctx.hegmm_ct_export(outs[i]) == ex.run(plan, ctA, ctB)).all()
     ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)  # the library default

@@ -121,12 +121,20 @@ def test_modswitch_tiny(H):
     assert (ctx.hegmm_ct_export(p) == o.mult_relin(o.modswitch(co), o.modswitch(co))).all()
 
 
-MODES = ["single", "double"]
+MODES = ["single", "double", "single+lazy", "double+lazy"]
+
+
+def set_mode(H, ctx, mode):
+    """Sets the library's evaluation order; returns the oracle's (mode, lazy_relin)."""
+    base, _, lazy = mode.partition("+")
+    flags = (H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0)
+    ctx.hegmm_set_keyswitch_mode(flags)
+    return base, bool(lazy)
 
 
 def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"):
     pre, ctx, o = get_pair(H, name)
-    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if mode == "double" else H.KS_SINGLE)
+    base, lazy = set_mode(H, ctx, mode)
     A, B = W.matrices(m, l, n, lo, hi, seed=seed)
     ctx.hegmm_keygen(SEED, [(m, l, n)], alg)
     ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 11, 100)
@@ -138,8 +146,9 @@ def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"
     plan = SL.make_plan(m, l, n, ralg)
     pc = plan.counts()
     assert cnt["rot"] == pc["rot"] and cnt["mult"] == pc["mult"] and cnt["cmult"] == pc["cmult"]
+    assert cnt["relin"] == (1 if lazy else pc["mult"])
     if bitexact:
-        ex = OH.HEGMM(o, mode=mode)
+        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy)
         ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=11, streams=(100, 101))
         assert (ctx.hegmm_ct_export(ca) == ctA).all()
         oc = ex.run(plan, ctA, ctB)
@@ -178,7 +187,7 @@ def test_hegmm_tiny_edge_shapes(H, shape):
             run_both(H, "tiny", *shape, alg, *W.TINY_RANGE, seed=sum(shape), mode=mode)
 
 
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode", ["single", "double", "double+lazy"])
 @pytest.mark.parametrize("shape", W.MEDIUM_SHAPES)
 def test_hegmm_medium_alg2_bitexact(H, shape, mode):
     run_both(H, "medium", *shape, 2, *W.MEDIUM_RANGE, mode=mode)
@@ -195,7 +204,7 @@ def test_hegmm_medium_maximum_shape(H):
     run_both(H, "medium", 64, 64, 64, 2, *W.MEDIUM_RANGE, bitexact=False)
 
 
-@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mode", ["single", "double", "double+lazy"])
 def test_hegmm_paper_128x16x64_bitexact(H, mode):
     run_both(H, "paper", 128, 16, 64, 0, *W.PAPER_RANGE, mode=mode)
 
@@ -208,7 +217,7 @@ def test_hegmm_paper_shapes(H, shape):
 @pytest.mark.parametrize("mode", MODES)
 def test_batch_equals_single(H, mode):
     pre, ctx, o = get_pair(H, "tiny")
-    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE if mode == "double" else H.KS_SINGLE)
+    set_mode(H, ctx, mode)
     shapes = [(4, 8, 6), (3, 5, 2), (6, 2, 7)]
     ctx.hegmm_keygen(SEED, shapes, H.ALG_AUTO)
     As, Bs, Cs, mats = [], [], [], []
