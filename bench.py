@@ -375,20 +375,12 @@ def main():
         cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, alg), 1 + rank, 2 * i + 1)
         ops.append((ca, cb))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    # one step = every product of the workload through hegmm_matmul_batch,
-    # per algorithm (the batch API resolves AUTO per shape)
-    groups = {}
-    for i, p in enumerate(prods):
-        groups.setdefault(p[3], []).append(i)
+    # one step = every product of the workload in one hegmm_matmul_batch_algs call
+
+    algs = [p[3] for p in prods]
 
     def step():
-        outs = [None] * len(prods)
-        for alg, idx in groups.items():
-            res = ctx.hegmm_matmul_batch([ops[i][0] for i in idx], [ops[i][1] for i in idx],
-                                         [prods[i][:3] for i in idx], alg)
-            for i, c in zip(idx, res):
-                outs[i] = c
-        return outs
+        return ctx.hegmm_matmul_batch_algs([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs)
 
     def single_path(sample):
         """The plain path: one hegmm_matmul call per product."""
@@ -492,11 +484,9 @@ def main():
 
     def e2e_step():
         ins = [(ctx.hegmm_ct_import(ha.numpy()), ctx.hegmm_ct_import(hb.numpy())) for ha, hb in host_in]
-        for alg, idx in groups.items():
-            res = ctx.hegmm_matmul_batch([ins[i][0] for i in idx], [ins[i][1] for i in idx],
-                                         [prods[i][:3] for i in idx], alg)
-            for i, c in zip(idx, res):
-                ctx.hegmm_ct_export(c, host_out[i].numpy())
+        res = ctx.hegmm_matmul_batch_algs([a for a, _ in ins], [b for _, b in ins], [p[:3] for p in prods], algs)
+        for i, c in enumerate(res):
+            ctx.hegmm_ct_export(c, host_out[i].numpy())
 
     e2e_step()
     torch.cuda.synchronize()

@@ -193,6 +193,12 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
 #define HEGMM_TUNE_LT_KERNEL 3
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
+/* As hegmm_matmul_batch, with one algorithm per product: algs[i] in
+ * {HEGMM_ALG_AUTO, 1, 2} (algs may be NULL: AUTO for all).  Products of
+ * both algorithms share each stage's launches. */
+int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
+                            const int *mln, const int *algs, hegmm_ct **C);
+
 /* Builds and caches the per-shape plan data of the listed products (the
  * encoded diagonal masks of every linear transformation, Eq. lintrans), so
  * that the first product of each shape does not pay for it.  Needs the

@@ -915,14 +915,16 @@ size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
 void release_plan(Ctx *c, BatchPlan *P) { free_bplan(c, P); }
 
 int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-               hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold) {
+               const int *algs, hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold) {
     for (int i = 0; i < count; i++) C[i] = nullptr;
     if (count == 0) return HEGMM_OK;
     std::vector<std::array<int, 4>> shapes;
     std::vector<int> key;
     for (int i = 0; i < count; i++) {
         const int m = mln[3 * i], l = mln[3 * i + 1], n = mln[3 * i + 2];
-        const int a = resolve_alg(m, l, n, alg, c->S);
+        const int ai = algs ? algs[i] : alg;
+        if (ai < 0 || ai > 2) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1 or 2");
+        const int a = resolve_alg(m, l, n, ai, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
         if (!A[i] || !B[i]) return set_err(c, HEGMM_EINVAL, "null operand");
         if (A[i]->level != c->L || B[i]->level != c->L) return set_err(c, HEGMM_EINVAL, "operand level does not match");
@@ -983,8 +985,8 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
 }
 
 int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-                hegmm_ct **C, hegmm_opcount *cnt) {
-    return matmul_run(c, count, A, B, mln, alg, C, cnt, true, nullptr);
+                hegmm_ct **C, hegmm_opcount *cnt, const int *algs) {
+    return matmul_run(c, count, A, B, mln, alg, algs, C, cnt, true, nullptr);
 }
 
 }  // namespace hg
@@ -1004,6 +1006,12 @@ int hegmm_matmul_batch(hegmm_ctx *h, int count, const hegmm_ct *const *A, const 
                        int alg, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, alg, C, nullptr);
+}
+
+int hegmm_matmul_batch_algs(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
+                            const int *mln, const int *algs, hegmm_ct **C) {
+    if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
+    return matmul_many(&h->c, count, A, B, mln, HEGMM_ALG_AUTO, C, nullptr, algs);
 }
 
 int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {

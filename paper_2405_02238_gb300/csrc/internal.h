@@ -322,13 +322,14 @@ int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out);
 // products i < count: A[i] (m x l) . B[i] (l x n), shapes mln[3i..3i+2],
 // algorithm alg resolved per shape; C[i] receive new ciphertexts; cnt (may
 // be null) receives the summed operation counts.
+// algs (may be null): one algorithm per product, overriding alg
 int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-                hegmm_ct **C, hegmm_opcount *cnt);
+                hegmm_ct **C, hegmm_opcount *cnt, const int *algs = nullptr);
 // Same on the context's current stream; cache = false builds a plan only
 // for this call and hands it back in *hold, to be released with
 // release_plan (stream-ordered on c->st) once the work is done.
 int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-               hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold);
+               const int *algs, hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold);
 void release_plan(Ctx *c, BatchPlan *P);
 // Device workspace one product adds to a batch (admission estimate).
 size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg);

@@ -511,7 +511,9 @@ __global__ void __launch_bounds__(256, MINB) k_lt_ksw(int lv, int ne, int nd, in
     const int N = 1 << logN;
     const int c = CPT * (blockIdx.x * blockDim.x + threadIdx.x);
     if (c >= N) return;
-    const int e = blockIdx.y, o = blockIdx.z;
+    // grid (slices, items, limbs): CTAs resident together cover many items
+    // of one limb, so items that share Galois keys read them from L2
+    const int o = blockIdx.y, e = blockIdx.z;
     const int gm = e < lv ? e : L + (e - lv);
     const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
     const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N;
@@ -580,7 +582,7 @@ template <int CPT, int MINB>
 static void launch_lt_ksw(Ctx *c, int lv, int ne, int nd, const LtKsTerm *d_terms, const int *d_off,
                           u64 *const *d_outs, int nout) {
     for (int o0 = 0; o0 < nout; o0 += kMaxGridZ)  // term offsets are absolute, so a slice needs no rebasing
-        k_lt_ksw<CPT, MINB><<<grid_coef(c->N / CPT, ne, std::min(kMaxGridZ, nout - o0)), 256, 0, c->st>>>(
+        k_lt_ksw<CPT, MINB><<<grid_coef(c->N / CPT, std::min(kMaxGridZ, nout - o0), ne), 256, 0, c->st>>>(
             lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_terms, d_off + o0, d_outs + o0);
 }
 

@@ -143,28 +143,15 @@ static int admit(hegmm_server *s) {
         c->arena_cap = s->arena_cap;
         c->arena_used = 0;
         cudaStreamWaitEvent(c->st, s->inputs_ready, 0);
+        // one executor call for the whole batch; each request carries its
+        // resolved algorithm
+        std::vector<int> algs;
+        for (auto &r : reqs) algs.push_back(r.alg);
         BatchPlan *plan = nullptr;
-        int rc = HEGMM_OK;
-        // each request carries its resolved algorithm; one executor call per algorithm
-        std::map<int, std::vector<int>> groups;
-        for (int i = 0; i < (int)reqs.size(); i++) groups[reqs[i].alg].push_back(i);
         std::vector<BatchPlan *> plans;
-        for (auto &g : groups) {
-            std::vector<const hegmm_ct *> a, b;
-            std::vector<int> sh;
-            for (int i : g.second) {
-                a.push_back(A[i]);
-                b.push_back(B[i]);
-                sh.insert(sh.end(), {reqs[i].m, reqs[i].l, reqs[i].n});
-            }
-            std::vector<hegmm_ct *> o(g.second.size(), nullptr);
-            plan = nullptr;
-            rc = matmul_run(c, (int)g.second.size(), a.data(), b.data(), sh.data(), g.first, o.data(), nullptr, false,
-                            &plan);
-            if (rc) break;
-            plans.push_back(plan);
-            for (size_t k = 0; k < g.second.size(); k++) outs[g.second[k]] = o[k];
-        }
+        int rc = matmul_run(c, (int)reqs.size(), A.data(), B.data(), mln.data(), HEGMM_ALG_AUTO, algs.data(),
+                            outs.data(), nullptr, false, &plan);
+        if (!rc) plans.push_back(plan);
         c->arena = nullptr;
         SrvBatch sb;
         sb.stream = st;

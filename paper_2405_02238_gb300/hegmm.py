@@ -83,6 +83,8 @@ _SIGS = {
     "hegmm_encrypt": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(vp)]),
     "hegmm_matmul": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(vp), ctypes.POINTER(hegmm_opcount)]),
+    "hegmm_matmul_batch_algs": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp, intp,
+                                               ctypes.POINTER(vp)]),
     "hegmm_matmul_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp,
                                           ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_decrypt": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p]),
@@ -294,6 +296,19 @@ class Context:
         outs = (vp * n)()
         self._check(self.lib.hegmm_matmul_batch(self.h, n, pa, pb, mln.ctypes.data_as(intp), alg, outs),
                     "matmul_batch")
+        return [Ciphertext(self, vp(outs[i])) for i in range(n)]
+
+    def hegmm_matmul_batch_algs(self, As, Bs, shapes, algs=None):
+        """One batch with one algorithm per product (None: AUTO for all)."""
+        n = len(As)
+        pa = (vp * n)(*[a.h for a in As])
+        pb = (vp * n)(*[b.h for b in Bs])
+        mln = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
+        al = None if algs is None else np.ascontiguousarray(np.array(algs, dtype=np.int32))
+        outs = (vp * n)()
+        self._check(self.lib.hegmm_matmul_batch_algs(self.h, n, pa, pb, mln.ctypes.data_as(intp),
+                                                     None if al is None else al.ctypes.data_as(intp), outs),
+                    "matmul_batch_algs")
         return [Ciphertext(self, vp(outs[i])) for i in range(n)]
 
     def hegmm_decrypt(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO) -> np.ndarray:

@@ -99,3 +99,28 @@ def test_batch_512_products(H, medium):
         m, l, n = shapes[i]
         single, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n)
         assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(single)).all(), shapes[i]
+
+
+def test_batch_with_per_product_algorithms(H, medium):
+    # both algorithms in one call share the launches and change no bit
+    ctx = medium
+    shapes = [(4, 8, 6), (4, 8, 6), (9, 4, 11), (9, 4, 11), (3, 3, 3)]
+    algs = [1, 2, 1, 2, 0]
+    for a in (1, 2):
+        ctx.hegmm_keygen(SEED, shapes, a)
+    As, Bs, mats = [], [], []
+    for i, (m, l, n) in enumerate(shapes):  # operands encoded for their product's algorithm
+        A, B = W.matrices(m, l, n, *W.BATCH_RANGE, seed=300 + i)
+        mats.append((A, B))
+        As.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, algs[i]), 77, 3000 + 2 * i))
+        Bs.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, algs[i]), 77, 3001 + 2 * i))
+    for flags in (H.KS_SINGLE, H.KS_DOUBLE | H.KS_LAZY_RELIN):
+        ctx.hegmm_set_keyswitch_mode(flags)
+        outs = ctx.hegmm_matmul_batch_algs(As, Bs, shapes, algs)
+        for i, (m, l, n) in enumerate(shapes):
+            single, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n, algs[i])
+            assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(single)).all(), (shapes[i], algs[i])
+            A, B = mats[i]
+            got = ctx.hegmm_decrypt(outs[i], m, l, n, algs[i]).astype(np.int64)
+            assert (got == (A @ B) % W.MEDIUM.t).all()
+    ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
