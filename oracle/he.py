@@ -440,7 +440,7 @@ class HEGMM:
 
     MODES = ("single", "double")
 
-    def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False):
+    def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False, giant: bool = False):
         """mode "single": every key switch ends in its own ModDown, as the
         HE operations Rot, CMult, Mult and Add compose (the paper's cost
         model).  mode "double": the sums of key-switched terms (each linear
@@ -450,12 +450,17 @@ class HEGMM:
         lazy_relin: the per-iteration tensors (d0, d1, d2) are summed first
         and the sum is relinearised once (one key switch per product instead
         of one per HE-Mult); in double mode that key switch keeps P (d0, d1)
-        in its sum over PQ."""
+        in its sum over PQ.
+        giant: every linear transformation of an operand is evaluated as
+        Rot(sum_d u'_d (.) Rot(ct, b_d), g) with the offsets b_d shared by all
+        iterations (``slots.giant_factor``); the inner sum is evaluated in the
+        chosen mode, the outer rotation is one HE-Rot."""
         if mode not in self.MODES:
             raise ValueError(mode)
         self.o = o
         self.mode = mode
         self.lazy_relin = lazy_relin
+        self.giant = giant
         self._mask_cache: Dict[Tuple, np.ndarray] = {}
 
     def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
@@ -488,17 +493,17 @@ class HEGMM:
             self._mask_cache[key] = self.o.plaintext_eval_pq(self.o.encode(v), lv)
         return self._mask_cache[key]
 
-    def lt_double(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
+    def lt_double(self, ct: np.ndarray, terms: List[Tuple[int, List[int]]], scale: int) -> np.ndarray:
         """Eq. lintrans with one ModUp of c1 and one ModDown per component:
         y = ModDown(sum_d m_d (.) v_d) over PQ, v_0 = P ct and, for d != 0,
         v_d = (u0_d + P tau_d(c0), u1_d) with u_d the inner product of the
-        hoisted key switch of tau_d(c1)."""
+        hoisted key switch of tau_d(c1).  terms: [(d, destination slots)]."""
         o = self.o
         lv = ct.shape[1]
         acc = np.zeros((2, lv + o.K, o.N), dtype=np.uint64)
         D = o.modup(ct[1])
-        for d in sorted(diags):
-            m = self.mask_eval_pq(diags[d], scale, lv)
+        for d, dst in terms:
+            m = self.mask_eval_pq(dst, scale, lv)
             if d % o.S == 0:
                 v = [o.pq_lift(ct[0]), o.pq_lift(ct[1])]
             else:
@@ -509,17 +514,27 @@ class HEGMM:
                 o.pq_mac(acc[comp], v[comp], m)
         return o.moddown_pair(acc)
 
-    def lt(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
-        """sum_d u_d (.) Rot(ct, d), diagonals in ascending d (Eq. lintrans)."""
+    def lt_terms(self, ct: np.ndarray, terms: List[Tuple[int, List[int]]], scale: int) -> np.ndarray:
+        """sum over terms (d, slots) of u (.) Rot(ct, d), in the given order."""
         if self.mode == "double":
-            return self.lt_double(ct, diags, scale)
+            return self.lt_double(ct, terms, scale)
         lv = ct.shape[1]
         acc = None
-        for d in sorted(diags):
+        for d, dst in terms:
             r = self.o.rotate(ct, d)
-            term = self.o.cmult(r, self.mask_eval(diags[d], scale, lv))
+            term = self.o.cmult(r, self.mask_eval(dst, scale, lv))
             acc = term if acc is None else self.o.add(acc, term)
         return acc
+
+    def lt(self, ct: np.ndarray, diags: Dict[int, List[int]], scale: int) -> np.ndarray:
+        """sum_d u_d (.) Rot(ct, d), diagonals in ascending d (Eq. lintrans)."""
+        return self.lt_terms(ct, [(d, diags[d]) for d in sorted(diags)], scale)
+
+    def lt_giant(self, ct: np.ndarray, fact: Tuple[int, List[Tuple[int, List[int]]]], scale: int) -> np.ndarray:
+        """Rot(sum_b u'_b (.) Rot(ct, b), g) for one factored transformation."""
+        g, terms = fact
+        inner = self.lt_terms(ct, terms, scale)
+        return self.o.rotate(inner, g) if g % self.o.S else inner
 
     def run(self, plan: SL.Plan, ctA: np.ndarray, ctB: np.ndarray) -> np.ndarray:
         o = self.o
@@ -529,9 +544,16 @@ class HEGMM:
         C = None
         acc = None
         dsum = None
-        for e, om in plan.iters:
-            a = self.lt(ctA, e, scale)
-            b = self.lt(ctB, om, scale)
+        if self.giant:
+            fa = SL.giant_factor([e for e, _ in plan.iters], o.S)
+            fb = SL.giant_factor([om for _, om in plan.iters], o.S)
+        for k, (e, om) in enumerate(plan.iters):
+            if self.giant:
+                a = self.lt_giant(ctA, fa[k], scale)
+                b = self.lt_giant(ctB, fb[k], scale)
+            else:
+                a = self.lt(ctA, e, scale)
+                b = self.lt(ctB, om, scale)
             for _ in range(o.pre.ms_drop):
                 a = o.modswitch(a)
                 b = o.modswitch(b)

@@ -279,6 +279,74 @@ class Plan:
         }
 
 
+# --------------------------------------------------------------------------
+# Shared baby steps: an evaluation order of Eq. lintrans across iterations.
+# --------------------------------------------------------------------------
+
+# Cost of one giant rotation (its own ModUp, key switch and ModDowns) in units
+# of one baby key switch (a key read); a constant of the evaluation mode.
+GIANT_COST = 8
+
+
+def giant_factor(outputs: List[Dict[int, List[int]]], S: int,
+                 cost: int = GIANT_COST) -> List[Tuple[int, List[Tuple[int, List[int]]]]]:
+    """Rewrites each linear transformation of one operand (Eq. lintrans),
+    in execution order, as a rotation of a sum over shared offsets:
+
+        sum_d u_d (.) Rot(x, d) = Rot( sum_d u'_d (.) Rot(x, b_d), g ),
+        b_d = (d - g) mod S,  u'_d = Rot(u_d, -g)  (destination slots + g),
+
+    which holds for cyclic rotations of an S-slot row.  The rotations
+    Rot(x, b) are shared by every transformation of the operand, so a
+    transformation whose offsets are a shift of offsets already used costs
+    one giant rotation instead of its own key switches.
+
+    Greedy rule, per transformation in order, with B the non-zero offsets
+    key-switched so far: over g = 0 and every (z - b) mod S (z an offset of
+    the transformation mod S, b in B or 0), minimise
+        cost(g) = #{distinct (z - g) mod S not in B and != 0} + (cost if g != 0),
+    ties to the smaller g in [0, S); then B gains the new offsets.
+
+    Returns per transformation (g, terms) with terms [(b_d, destination
+    slots of u'_d)] in the order of the original diagonals (ascending d).
+    """
+    baby: set = set()
+    out = []
+    for diags in outputs:
+        Z = sorted({d % S for d in diags})
+        hits: Dict[int, int] = {}
+        for z in Z:
+            for b in [0] + sorted(baby):
+                g = (z - b) % S
+                hits[g] = hits.get(g, 0) + 1
+        best_g, best_c = 0, len(Z) - hits.get(0, 0)
+        for g in sorted(hits):
+            if g == 0:
+                continue
+            c = len(Z) - hits[g] + cost
+            if c < best_c:
+                best_g, best_c = g, c
+        g = best_g
+        terms = []
+        for d in sorted(diags):
+            b = (d - g) % S
+            terms.append((b, sorted((t + g) % S for t in diags[d])))
+            if b:
+                baby.add(b)
+        out.append((g, terms))
+    return out
+
+
+def apply_terms(x: np.ndarray, terms: List[Tuple[int, List[int]]], S: int, mod: int, scale: int = 1) -> np.ndarray:
+    """sum over (b, slots) of u (.) Rot(x, b), u = scale on the slots."""
+    y = np.zeros(S, dtype=np.int64)
+    for b, dst in terms:
+        mask = np.zeros(S, dtype=np.int64)
+        mask[dst] = scale
+        y = (y + mask * np.roll(x, -b)) % mod
+    return y
+
+
 def plan_alg1(m: int, l: int, n: int, order: str = "col") -> Plan:
     """Algorithm 1: sigma/tau on the client, then l iterations of eps^k, omega^k."""
     iters = []
