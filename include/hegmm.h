@@ -172,6 +172,13 @@ int hegmm_matmul_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, cons
 #define HEGMM_KS_SINGLE 0
 #define HEGMM_KS_DOUBLE 1
 #define HEGMM_KS_LAZY_RELIN 2
+/*   | HEGMM_KS_SHARED (with any of the above): every linear transformation
+ *     of an operand is evaluated as Rot(sum_d u'_d (.) Rot(ct, b_d), g):
+ *     the offsets b_d are shared by all iterations of the product (and
+ *     key-switched once per product), g is one HE-Rot per transformation
+ *     that needs it (hegmm_plan_giant gives the factorisation; its keys are
+ *     made by hegmm_keygen). */
+#define HEGMM_KS_SHARED 4
 int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
 
 /* Tuning knobs of the product executor (no effect on results; plans built
@@ -318,6 +325,12 @@ void hegmm_ct_destroy(hegmm_ct *ct);
  *   then the extraction offsets; then the m*n result slots (row-major).
  * hegmm_plan_layout writes the client-side slot vector of role A or B for
  * the plan (values mod t) into out[cap] and returns its length. */
+/* hegmm_plan_giant writes the shared-baby-step factorisation of role A (0,
+ * the eps^k) or B (1, the omega^k) used by HEGMM_KS_SHARED as ints into
+ * buf[cap] and returns the number it needs: iterations, then per iteration
+ * its giant rotation g (0: none) and term count, and per term its baby
+ * offset b in [0, S), slot count c and the c destination slots. */
+int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int *buf, int cap);
 int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *out);
 int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int cap);
 int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t,

@@ -614,6 +614,13 @@ int hegmm_keygen(hegmm_ctx *h, uint64_t seed, const int *mln, int n_shapes, int 
         }
         for (int z : P.extract)
             if (z % c->S) gs.insert(galois_of(c, z));
+        // the offsets of the shared-baby-step evaluation order as well
+        for (int s2 = 0; s2 < 2; s2++)
+            for (const GiantLT &f : giant_factor_of(P, s2, c->S)) {
+                if (f.g) gs.insert(galois_of(c, f.g));
+                for (const GTerm &t : f.terms)
+                    if (t.b) gs.insert(galois_of(c, t.b));
+            }
         for (u64 g : gs)
             if ((rc = gen_key(c, g))) return rc;
     }

@@ -182,11 +182,74 @@ long long HostPlan::paper_cmult() const {
     return r;
 }
 
+std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &outs, int S, int cost) {
+    std::set<int> baby;
+    std::vector<GiantLT> res;
+    for (const auto *ds : outs) {
+        std::set<int> Z;
+        for (const auto &d : *ds) Z.insert(imod(d.d, S));
+        std::map<int, int> hits;  // g -> #{z : (z - g) mod S in B or 0}
+        for (int z : Z) {
+            hits[z]++;  // b = 0
+            for (int b : baby) hits[imod((long long)z - b, S)]++;
+        }
+        const int nz = (int)Z.size();
+        int best_g = 0, best_c = nz - (hits.count(0) ? hits[0] : 0);
+        for (const auto &kv : hits) {
+            if (kv.first == 0) continue;
+            const int cst = nz - kv.second + cost;
+            if (cst < best_c) {
+                best_g = kv.first;
+                best_c = cst;
+            }
+        }
+        GiantLT f;
+        f.g = best_g;
+        for (const auto &d : *ds) {
+            GTerm t;
+            t.b = imod((long long)d.d - best_g, S);
+            for (int x : d.dst) t.dst.push_back(imod((long long)x + best_g, S));
+            std::sort(t.dst.begin(), t.dst.end());
+            if (t.b) baby.insert(t.b);
+            f.terms.push_back(std::move(t));
+        }
+        res.push_back(std::move(f));
+    }
+    return res;
+}
+
+std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S) {
+    std::vector<const std::vector<Diag> *> outs;
+    for (const auto &it : P.iters) outs.push_back(s == 0 ? &it.eps : &it.omg);
+    return giant_factor(outs, S);
+}
+
 }  // namespace hg
 
 using namespace hg;
 
 extern "C" {
+
+int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int *buf, int cap) {
+    if (slots <= 0 || (role != 0 && role != 1) || cap < 0 || (cap > 0 && !buf)) return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::vector<GiantLT> f = giant_factor_of(P, role, slots);
+    std::vector<int> v{(int)f.size()};
+    for (const auto &x : f) {
+        v.push_back(x.g);
+        v.push_back((int)x.terms.size());
+        for (const auto &t : x.terms) {
+            v.push_back(t.b);
+            v.push_back((int)t.dst.size());
+            v.insert(v.end(), t.dst.begin(), t.dst.end());
+        }
+    }
+    for (int i = 0; i < cap && i < (int)v.size(); i++) buf[i] = v[i];
+    return (int)v.size();
+}
+
 
 int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *out) {
     if (!out || slots <= 0) return HEGMM_EINVAL;

@@ -49,6 +49,27 @@ struct HostPlan {
     long long paper_cmult() const;
 };
 
+// Shared baby steps: the linear transformations of one operand, in
+// iteration order, each rewritten as Rot(sum_d u'_d (.) Rot(x, b_d), g) with
+// b_d = (d - g) mod S and u'_d = Rot(u_d, -g) (destination slots + g), an
+// identity of cyclic rotations of an S-slot row.  Greedy rule per
+// transformation, B = non-zero offsets used so far: over g = 0 and every
+// (z - b) mod S (z an offset mod S, b in B or 0) minimise
+//   #{distinct (z - g) mod S not in B and != 0} + (g != 0 ? cost : 0),
+// ties to the smaller g in [0, S).
+constexpr int GIANT_COST = 8;  // a giant rotation, in baby key switches
+struct GTerm {
+    int b;                 // baby offset in [0, S)
+    std::vector<int> dst;  // destination slots of u'_d
+};
+struct GiantLT {
+    int g;                     // giant rotation in [0, S); 0 = none
+    std::vector<GTerm> terms;  // in the order of the original diagonals
+};
+std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &outs, int S, int cost = GIANT_COST);
+// The factorisation of operand s (0: eps / A, 1: omega / B) of a plan.
+std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S);
+
 // Number of slots Algorithm 1 / 2 needs for (m, l, n).
 int alg1_length(int m, int l, int n);
 int alg2_length(int m, int l, int n);

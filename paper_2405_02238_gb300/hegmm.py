@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libhegmm.so")
 HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
-KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN = 0, 1, 2  # hegmm_set_keyswitch_mode (KS_LAZY_RELIN combines)
+KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL = 1, 2, 3  # hegmm_set_tuning
 ROLE_A, ROLE_B = 0, 1
 
@@ -125,6 +125,8 @@ _SIGS = {
                                          ctypes.POINTER(hegmm_opcount)]),
     "hegmm_plan_describe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            intp, ctypes.c_int]),
+    "hegmm_plan_giant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, intp, ctypes.c_int]),
     "hegmm_plan_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, i64p, ctypes.c_uint64, u64p, ctypes.c_int]),
 }
@@ -164,6 +166,16 @@ def hegmm_plan_describe(m: int, l: int, n: int, alg: int, slots: int) -> List[in
         raise HegmmError(need, "plan_describe")
     buf = (ctypes.c_int * need)()
     lib.hegmm_plan_describe(m, l, n, alg, slots, buf, need)
+    return list(buf)
+
+
+def hegmm_plan_giant(m: int, l: int, n: int, alg: int, slots: int, role: int) -> List[int]:
+    lib = load()
+    need = lib.hegmm_plan_giant(m, l, n, alg, slots, role, None, 0)
+    if need < 0:
+        raise HegmmError(need, "plan_giant")
+    buf = (ctypes.c_int * need)()
+    lib.hegmm_plan_giant(m, l, n, alg, slots, role, buf, need)
     return list(buf)
 
 

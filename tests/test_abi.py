@@ -122,3 +122,28 @@ def test_ksw_counts_share_rotations_across_iterations(H):
                 zs[1].update(d % 4096 for d in o if d % 4096)
             assert c["ksw"] == len(zs[0]) + len(zs[1]) + len(p.iters) + len(p.extract)
             assert c["ksw"] <= c["rot"] + c["mult"]
+
+
+def oracle_giant(m, l, n, alg, S, role):
+    plan = SL.make_plan(m, l, n, alg)
+    f = SL.giant_factor([it[role] for it in plan.iters], S)
+    v = [len(f)]
+    for g, terms in f:
+        v += [g, len(terms)]
+        for b, dst in terms:
+            v += [b, len(dst)] + list(dst)
+    return v
+
+
+def test_host_shared_baby_steps_match_oracle(H):
+    # the greedy factorisation is implemented twice (C++ planner, Python
+    # oracle) and must agree term for term
+    for m, l, n in list(itertools.product(range(1, 7), repeat=3)) + [(16, 32, 24), (32, 8, 48), (32, 128, 16),
+                                                                    (64, 64, 64)]:
+        for alg in (1, 2):
+            S = 8192 if max(m, l, n) > 16 else 512
+            if not SL.fits(m, l, n, alg, S):
+                continue
+            for role in (0, 1):
+                assert H.hegmm_plan_giant(m, l, n, alg, S, role) == oracle_giant(m, l, n, alg, S, role), \
+                    (m, l, n, alg, role)
