@@ -42,8 +42,9 @@ UNIT = "matmul/s"
 KEY_SEED = 7
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
-# hegmm_set_keyswitch_mode flags per --ks-mode (KS_DOUBLE = 1, KS_LAZY_RELIN = 2)
-KS_MODES = {"double+lazy": 3, "double": 1, "single": 0, "single+lazy": 2}
+# hegmm_set_keyswitch_mode flags per --ks-mode (KS_DOUBLE = 1, KS_LAZY_RELIN = 2, KS_SHARED = 4)
+KS_MODES = {"double+lazy+shared": 7, "double+lazy": 3, "double": 1, "single": 0, "single+lazy": 2,
+            "single+shared": 4}
 
 
 def workload_config(extra=None):
@@ -328,7 +329,7 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1000)
     ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
-    ap.add_argument("--ks-mode", default="double+lazy", choices=list(KS_MODES),
+    ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
                     help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -452,7 +453,7 @@ def main():
     stats = ctx.hegmm_kernel_stats()
 
     # the other key-switch evaluation order on the same products, for comparison
-    other = "single" if args.ks_mode != "single" else "double+lazy"
+    other = "single" if args.ks_mode != "single" else "double+lazy+shared"
     ctx.hegmm_set_keyswitch_mode(ks_code[other])
     outs = step()
     for (m, l, n, alg, A, Bm), c in zip(prods, outs):

@@ -184,9 +184,9 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
 /* Tuning knobs of the product executor (no effect on results; plans built
  * before the call keep their values).
  *   HEGMM_TUNE_LT_CHUNK: in HEGMM_KS_DOUBLE mode, the most terms of one
- *     linear-transformation output handled by one work item of the fused
- *     key-switch kernel (1..4096, default 32); longer outputs are split into
- *     partial sums.
+ *     linear-transformation entries (shared rotations) handled by one work
+ *     item of the fused key-switch kernel (1..4096, default 32); longer
+ *     entry lists are split into partial sums.
  * Errors: HEGMM_EINVAL (unknown knob or value out of range). */
 #define HEGMM_TUNE_LT_CHUNK 1
 /*   HEGMM_TUNE_LT_FUSED: in HEGMM_KS_DOUBLE mode, 1 (default) evaluates each
@@ -194,9 +194,9 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     distinct rotation once into a workspace chunk (chunk size set by
  *     hegmm_set_budgets' chunk_bytes) and applies the masks after each chunk. */
 #define HEGMM_TUNE_LT_FUSED 2
-/*   HEGMM_TUNE_LT_KERNEL: variant of the fused kernel, 0..4: (coefficients
- *     per thread, resident CTAs per SM) = (2, 3), (2, 4), (1, 4), (1, 6),
- *     (1, 8).  Default 3 (measured fastest on GB300 at N = 2^13). */
+/*   HEGMM_TUNE_LT_KERNEL: variant of the fused kernel for items of several
+ *     outputs, by resident CTAs per SM (its register cap): 0 = 4 (default,
+ *     measured fastest on GB300 at N = 2^13), 1 = 2, 2 = 3. */
 #define HEGMM_TUNE_LT_KERNEL 3
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 

@@ -56,8 +56,18 @@ struct ShapeData {
         int zi, mask;
     };
     std::vector<std::vector<DiagRef>> dref[2];
+    // shared baby steps: per operand and iteration the giant rotation (0: none)
+    bool shared = false;
+    std::vector<int> giant[2];
     // masks are kept over all L + K primes (the extended basis of level L)
     const u64 *mask_at(Ctx *c, int mi) const { return masks + (size_t)mi * (c->L + c->K) * c->N; }
+};
+
+struct GiantChunk {
+    int cnt = 0;
+    u64 **d_src = nullptr;
+    RotDesc *d_rot = nullptr;
+    DivDesc *d_div = nullptr;
 };
 
 struct RotChunk {
@@ -86,12 +96,11 @@ struct BatchPlan {
     TensorSum *d_tsum = nullptr;
     RotDesc *d_lrot = nullptr;
     DivDesc *d_ldiv = nullptr;
-    int fused = 0;  // double mode: every linear transformation in one k_lt_ksw launch
-    LtKsTerm *d_ltks = nullptr;
-    int *d_ltks_off = nullptr;
-    u64 **d_ltks_outs = nullptr;
-    int ltks_items = 0;     // work items: chunks of at most lt_chunk terms of one output
-    double ltks_keyed = 0;  // key-switched terms (for the byte count)
+    int fused = 0;  // double mode: every linear transformation in one k_lt_grp launch
+    LtEntry *d_lents = nullptr;
+    LtItem *d_litems[2] = {nullptr, nullptr};  // items of one output, items of several outputs
+    int lt_nitems[2] = {0, 0};  // work items: outputs x at most lt_chunk entries
+    double lt_bytes[2] = {0, 0};  // algorithmic bytes of each launch
     u64 *part = nullptr;    // partial sums of outputs split into several items
     SumDesc *d_ltsum = nullptr;
     int ltsum_n = 0;
@@ -107,6 +116,8 @@ struct BatchPlan {
     int *d_id_off = nullptr;
     u64 **d_all_outs = nullptr;
     std::vector<RotChunk> rchunks;
+    std::vector<GiantChunk> gchunks;
+    u64 *gst = nullptr, *gxc = nullptr, *gD = nullptr, *gu = nullptr;
     DivDesc *d_msdiv = nullptr;
     std::vector<RelinChunk> lchunks;
     RotDesc *d_erot = nullptr;
@@ -224,8 +235,8 @@ static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int>
     return cuda_check(c, "mask encode");
 }
 
-static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
-    auto key = std::make_tuple(m, l, n, alg);
+static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData **out) {
+    auto key = std::make_tuple(m, l, n, alg, shared);
     auto it = c->shapes.find(key);
     if (it != c->shapes.end()) {
         it->second->last_use = ++c->bplan_clock;
@@ -235,14 +246,30 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
     const int S = c->S;
     ShapeData *sd = new ShapeData;
     sd->hp = make_host_plan(m, l, n, alg);
+    sd->shared = shared != 0;
     const HostPlan &hp = sd->hp;
+    // per operand and iteration the terms (rotation offset mod S, destination
+    // slots of the mask): the plan's diagonals, or the shared-baby-step
+    // factorisation with its giant rotations
+    std::vector<std::vector<std::vector<std::pair<long long, std::vector<int>>>>> tl(2);
     for (int s = 0; s < 2; s++) {
-        std::set<long long> zs;
-        for (auto &it2 : hp.iters)
-            for (auto &d : (s == 0 ? it2.eps : it2.omg)) {
-                long long z = ((long long)d.d % S + S) % S;
-                if (z) zs.insert(z);
+        tl[s].resize(hp.iters.size());
+        sd->giant[s].assign(hp.iters.size(), 0);
+        if (sd->shared) {
+            std::vector<GiantLT> f = giant_factor_of(hp, s, S);
+            for (size_t k = 0; k < f.size(); k++) {
+                sd->giant[s][k] = f[k].g;
+                for (auto &t : f[k].terms) tl[s][k].push_back({t.b, t.dst});
             }
+        } else {
+            for (size_t k = 0; k < hp.iters.size(); k++)
+                for (auto &d : (s == 0 ? hp.iters[k].eps : hp.iters[k].omg))
+                    tl[s][k].push_back({((long long)d.d % S + S) % S, d.dst});
+        }
+        std::set<long long> zs;
+        for (auto &v : tl[s])
+            for (auto &t : v)
+                if (t.first) zs.insert(t.first);
         for (long long z : zs) {
             sd->zidx[s][z] = (int)sd->zs[s].size();
             sd->zs[s].push_back(z);
@@ -252,9 +279,12 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
         delete sd;
         return set_err(c, code, msg);
     };
-    for (int s = 0; s < 2; s++)
+    for (int s = 0; s < 2; s++) {
         for (long long z : sd->zs[s])
             if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+        for (int g : sd->giant[s])
+            if (g && !c->keys.count(galois_of(c, g))) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+    }
     for (int z : hp.extract)
         if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
     if (!c->keys.count(0)) return fail(HEGMM_ENOKEY, "no relinearisation key");
@@ -262,21 +292,18 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
     u64 scale = 1;
     for (int i = 0; i < c->prm.ms_drop; i++) scale = (u64)((unsigned __int128)scale * (c->q[c->L - 1 - i] % c->t) % c->t);
     std::vector<const std::vector<int> *> mlist;
-    for (auto &it2 : hp.iters)
+    for (size_t k = 0; k < hp.iters.size(); k++)
         for (int s = 0; s < 2; s++)
-            for (auto &d : (s == 0 ? it2.eps : it2.omg))
-                if (!sd->mask_of.count(d.dst)) {
-                    sd->mask_of[d.dst] = (int)mlist.size();
-                    mlist.push_back(&sd->mask_of.find(d.dst)->first);
+            for (auto &t : tl[s][k])
+                if (!sd->mask_of.count(t.second)) {
+                    sd->mask_of[t.second] = (int)mlist.size();
+                    mlist.push_back(&sd->mask_of.find(t.second)->first);
                 }
     sd->nmask = (int)mlist.size();
     for (int s = 0; s < 2; s++) {
         sd->dref[s].resize(hp.iters.size());
         for (size_t k = 0; k < hp.iters.size(); k++)
-            for (auto &d : (s == 0 ? hp.iters[k].eps : hp.iters[k].omg)) {
-                const long long z = ((long long)d.d % S + S) % S;
-                sd->dref[s][k].push_back({z ? sd->zidx[s].at(z) : -1, sd->mask_of.at(d.dst)});
-            }
+            for (auto &t : tl[s][k]) sd->dref[s][k].push_back({t.first ? sd->zidx[s].at(t.first) : -1, sd->mask_of.at(t.second)});
     }
     const int nm = c->L + c->K;
     sd->bytes = (size_t)sd->nmask * nm * c->N * 8;
@@ -306,8 +333,11 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, ShapeData **out) {
     ct.relin = ni;
     ct.extract = ne;
     ct.add = ct.cmult - 2 * ni + (ni - 1) + ne;
-    ct.ksw = (long long)sd->zs[0].size() + (long long)sd->zs[1].size() + ni + ne;
-    ct.modup = 2 + ni + (ne > 0 ? 1 : 0);
+    long long ngiant = 0;
+    for (int s = 0; s < 2; s++)
+        for (int g : sd->giant[s]) ngiant += g != 0;
+    ct.ksw = (long long)sd->zs[0].size() + (long long)sd->zs[1].size() + ngiant + ni + ne;
+    ct.modup = 2 + ngiant + ni + (ne > 0 ? 1 : 0);
     ct.modswitch = c->prm.ms_drop ? 2 * ni : 0;
     c->shapes[key] = sd;
     *out = sd;
@@ -327,7 +357,8 @@ static void add_counts(hegmm_opcount &a, const hegmm_opcount &b) {
 }
 
 // shapes: B entries of (m, l, n, resolved alg)
-static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, int lazy, BatchPlan **out) {
+static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, int lazy, int shared,
+                       BatchPlan **out) {
     const int N = c->N;
     BatchPlan *P = new BatchPlan;
     P->dbl = dbl;
@@ -340,7 +371,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     std::set<ShapeData *> held;
     for (auto &s : shapes) {
         ShapeData *sd;
-        int rc = get_shape(c, s[0], s[1], s[2], s[3], &sd);
+        int rc = get_shape(c, s[0], s[1], s[2], s[3], shared, &sd);
         if (rc) {
             P->shp.assign(held.begin(), held.end());  // release what this plan holds
             return fail_rc(rc);
@@ -401,27 +432,87 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             return fail_rc(set_err(c, HEGMM_EINVAL, "lazy relinearisation: too many iterations for one tensor sum"));
     }
     const int R = (int)ritems.size(), I = (int)litems.size();
-    // double mode fuses each linear transformation's inner products and mask
-    // sums into one kernel when its lazy 128-bit sums cannot overflow:
-    // (terms of an output + 2) q < 2^64
-    // Long term lists are cut into items of at most lt_chunk terms (balanced
-    // work per CTA row); the items of such an output write partial sums,
-    // added by one sum launch.
+    // Double mode evaluates all linear transformations in one grouped launch
+    // (k_lt_grp): the outputs of an operand are taken LT_GROUP iterations at
+    // a time; a group's terms become entries, one per (rotation, use) so that
+    // an entry serves each output at most once, ordered by rotation; entries
+    // are cut into items of at most lt_chunk (balanced work per CTA row, and
+    // the lazy 128-bit sums stay below q 2^64: (lt_chunk + 2) q < 2^64).  A
+    // group cut into several items writes partial sums, added by one sum
+    // launch.
     const int TC = std::max(1, c->lt_chunk);
+    struct GEnt {
+        int zi;
+        int mask[LT_GROUP];
+    };
+    struct GGroup {
+        int p, s, k0, nj, nch;
+        size_t part0;
+        std::vector<GEnt> ents;
+    };
+    // a group whose outputs share few rotations (entries >= 4/5 of its
+    // terms) is evaluated one output per item instead
+    auto make_group = [&](int p, int s, int k0, int nj) {
+        GGroup g{p, s, k0, nj, 1, 0, {}};
+        std::vector<GEnt> made;
+        std::map<int, std::vector<int>> byz;  // rotation index (-1: d = 0) -> entries
+        for (int j = 0; j < nj; j++)
+            for (const auto &dr : P->shp[p]->dref[s][k0 + j]) {
+                int idx = -1;
+                for (int x : byz[dr.zi])
+                    if (made[x].mask[j] < 0) {
+                        idx = x;
+                        break;
+                    }
+                if (idx < 0) {
+                    GEnt ge;
+                    ge.zi = dr.zi;
+                    for (int jj = 0; jj < LT_GROUP; jj++) ge.mask[jj] = -1;
+                    idx = (int)made.size();
+                    made.push_back(ge);
+                    byz[dr.zi].push_back(idx);
+                }
+                made[idx].mask[j] = dr.mask;
+            }
+        for (auto &kv : byz)
+            for (int x : kv.second) g.ents.push_back(made[x]);
+        return g;
+    };
+    std::vector<GGroup> groups;
     size_t npart = 0;
-    if (dbl) {
-        size_t tmax = 0;
+    P->fused = dbl && c->lt_fused && (unsigned __int128)(TC + 2) * c->q[0] < ((unsigned __int128)1 << 64);
+    if (P->fused) {
         for (int p = 0; p < B; p++)
             for (int s = 0; s < 2; s++)
-                for (const auto &v : P->shp[p]->dref[s]) {
-                    tmax = std::max(tmax, v.size());
-                    const size_t nch = (v.size() + TC - 1) / TC;
-                    if (nch > 1) npart += nch;
+                for (int k0 = 0; k0 < niter[p]; k0 += LT_GROUP) {
+                    const int nj = std::min(LT_GROUP, niter[p] - k0);
+                    std::vector<GGroup> gs{make_group(p, s, k0, nj)};
+                    size_t nterms = 0;
+                    for (int j = 0; j < nj; j++) nterms += P->shp[p]->dref[s][k0 + j].size();
+                    if (nj > 1 && 5 * gs[0].ents.size() >= 4 * nterms) {
+                        gs.clear();
+                        for (int j = 0; j < nj; j++) gs.push_back(make_group(p, s, k0 + j, 1));
+                    }
+                    for (auto &g : gs) {
+                        g.nch = std::max(1, (int)((g.ents.size() + TC - 1) / TC));
+                        if (g.nch > 1) {
+                            g.part0 = npart;
+                            npart += (size_t)g.nch * g.nj;
+                        }
+                        groups.push_back(std::move(g));
+                    }
                 }
-        P->fused = c->lt_fused &&
-                   (unsigned __int128)(std::min<size_t>(tmax, TC) + 2) * c->q[0] < ((unsigned __int128)1 << 64);
     }
     const int fused = P->fused;
+    // giant rotations of the shared-baby-step order: (product, operand, iteration, g)
+    std::vector<std::array<int, 4>> gitems;
+    for (int p = 0; p < B; p++)
+        for (int s = 0; s < 2; s++)
+            for (int k = 0; k < niter[p]; k++)
+                if (P->shp[p]->shared && P->shp[p]->giant[s][k]) gitems.push_back({p, s, k, P->shp[p]->giant[s][k]});
+    const int G = (int)gitems.size();
+    const size_t per_giant = (size_t)(3 * lv0 + nd0 * ne0 + 2 * ne0) * N * 8;
+    const int GCH = G ? (int)std::max<size_t>(1, std::min<size_t>((size_t)G, c->ws_budget / per_giant)) : 0;
     const size_t per_rot = (size_t)(2 * ne0 + (dbl ? 0 : 2 * lv0)) * N * 8;
     const size_t per_item = (size_t)(4 * lv1 + nd1 * ne1 + 2 * ne1 + (dbl ? 0 : 2 * lv1)) * N * 8;
     const int RC = fused ? 0 : (int)std::max<size_t>(1, std::min<size_t>((size_t)std::max(R, 1), c->ws_budget / per_rot));
@@ -446,7 +537,9 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                  o_erot = dbl ? 0 : take(X1 * 2 * lv1 * N), o_xacc = dbl ? take(E1 * 2 * ne1 * N) : 0,
                  o_xout = dbl ? take(E1 * 2 * lv1 * N) : 0, o_d3s = lazy ? take((size_t)B * 3 * lv1 * N) : 0,
                  o_lxc = lazy ? take((size_t)B * lv1 * N) : 0, o_lD = lazy ? take((size_t)B * nd1 * ne1 * N) : 0,
-                 o_lu = lazy && !dbl ? take((size_t)B * 2 * ne1 * N) : 0;
+                 o_lu = lazy && !dbl ? take((size_t)B * 2 * ne1 * N) : 0, o_gst = take((size_t)GCH * 2 * lv0 * N),
+                 o_gxc = take((size_t)GCH * lv0 * N), o_gD = take((size_t)GCH * nd0 * ne0 * N),
+                 o_gu = take((size_t)GCH * 2 * ne0 * N);
     P->ws_bytes = off * 8;
     P->ws = (u64 *)plan_alloc(c, P, off * 8);
     if (!P->ws) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch workspace"));
@@ -465,6 +558,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     P->lxc = lazy ? W + o_lxc : nullptr;
     P->lD = lazy ? W + o_lD : nullptr;
     P->lu = lazy && !dbl ? W + o_lu : nullptr;
+    P->gst = W + o_gst;
+    P->gxc = W + o_gxc;
+    P->gD = W + o_gD;
+    P->gu = W + o_gu;
     P->outs = W + o_outs;
     P->ms = lv1 != lv0 ? W + o_ms : nullptr;
     P->d3 = W + o_d3;
@@ -486,59 +583,64 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     };
     auto keep = [&](void *ptr) { return ptr != nullptr; };
     if (fused) {
-        // every term of every output, in the order of the outputs, cut into items
-        std::vector<LtKsTerm> terms;
-        std::vector<int> offs{0};
-        std::vector<u64 *> outs;
+        std::vector<LtEntry> ents;
+        std::vector<LtItem> items[2];
         std::vector<SumDesc> sums;
-        size_t pi = 0;
         const size_t pstride = (size_t)2 * ne0 * N;
-        for (int p = 0; p < B; p++) {
-            const ShapeData *sd = P->shp[p];
-            for (int s = 0; s < 2; s++)
-                for (int k = 0; k < niter[p]; k++) {
-                    const auto &dl = sd->dref[s][k];
-                    const int nch = std::max<int>(1, (int)((dl.size() + TC - 1) / TC));
-                    if (nch > 1) {
-                        SumDesc sm{};
-                        sm.out = acc_of(p, s, k);
-                        sm.init = P->part + pi * pstride;
-                        sm.items = sm.init + pstride;
-                        sm.stride = (long long)pstride;
-                        sm.count = nch - 1;
-                        sums.push_back(sm);
+        const double limb = (double)N * 8;
+        for (const auto &g : groups) {
+            const ShapeData *sd = P->shp[g.p];
+            const int kind = g.nj > 1;  // 0: one output per item, 1: several
+            for (int ch = 0; ch < g.nch; ch++) {
+                LtItem it{};
+                it.first = (int)ents.size();
+                const int e0 = ch * TC, e1 = std::min((int)g.ents.size(), e0 + TC);
+                for (int ei = e0; ei < e1; ei++) {
+                    const GEnt &ge = g.ents[ei];
+                    LtEntry E{};
+                    E.ct = in_ct(g.p, g.s);
+                    if (ge.zi >= 0) {
+                        const u64 gel = galois_of(c, sd->zs[g.s][ge.zi]);
+                        E.D = P->D + ((size_t)2 * g.p + g.s) * nd0 * ne0 * N;
+                        E.key = c->keys[gel];
+                        E.g = (u32)gel;
+                        P->lt_bytes[kind] += 2.0 * nd0 * ne0 * limb;  // the key
                     }
-                    int in_item = 0;
-                    for (const auto &dr : dl) {
-                        if (in_item == TC) {  // close an item of a split output
-                            offs.push_back((int)terms.size());
-                            outs.push_back(P->part + pi++ * pstride);
-                            in_item = 0;
+                    for (int j = 0; j < g.nj; j++)
+                        if (ge.mask[j] >= 0) {
+                            E.mask[j] = sd->mask_at(c, ge.mask[j]);
+                            P->lt_bytes[kind] += ne0 * limb;  // the mask
                         }
-                        in_item++;
-                        LtKsTerm T{};
-                        T.ct = in_ct(p, s);
-                        T.mask = sd->mask_at(c, dr.mask);
-                        if (dr.zi >= 0) {
-                            const u64 g = galois_of(c, sd->zs[s][dr.zi]);
-                            T.D = P->D + ((size_t)2 * p + s) * nd0 * ne0 * N;
-                            T.key = c->keys[g];
-                            T.g = (u32)g;
-                            P->ltks_keyed += 1;
-                        }
-                        terms.push_back(T);
-                    }
-                    offs.push_back((int)terms.size());
-                    outs.push_back(nch > 1 ? P->part + pi++ * pstride : acc_of(p, s, k));
+                    ents.push_back(E);
+                }
+                it.count = (int)ents.size() - it.first;
+                for (int j = 0; j < g.nj; j++)
+                    it.out[j] = g.nch == 1 ? acc_of(g.p, g.s, g.k0 + j)
+                                           : P->part + (g.part0 + (size_t)ch * g.nj + j) * pstride;
+                P->lt_bytes[kind] += g.nj * 2.0 * ne0 * limb;  // the sums written
+                items[kind].push_back(it);
+            }
+            if (g.nch > 1)
+                for (int j = 0; j < g.nj; j++) {
+                    SumDesc sm{};
+                    sm.out = acc_of(g.p, g.s, g.k0 + j);
+                    sm.init = P->part + (g.part0 + j) * pstride;
+                    sm.items = sm.init + (size_t)g.nj * pstride;
+                    sm.stride = (long long)(g.nj * pstride);
+                    sm.count = g.nch - 1;
+                    sums.push_back(sm);
                 }
         }
-        P->ltks_items = (int)outs.size();
         P->ltsum_n = (int)sums.size();
-        P->d_ltks = plan_upload(c, P, terms);
-        P->d_ltks_off = plan_upload(c, P, offs);
-        P->d_ltks_outs = plan_upload(c, P, outs);
+        P->d_lents = plan_upload(c, P, ents);
+        for (int kind = 0; kind < 2; kind++) {
+            P->lt_nitems[kind] = (int)items[kind].size();
+            P->d_litems[kind] = items[kind].empty() ? nullptr : plan_upload(c, P, items[kind]);
+            if (!items[kind].empty() && !keep(P->d_litems[kind]))
+                return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        }
         P->d_ltsum = sums.empty() ? nullptr : plan_upload(c, P, sums);
-        if (!keep(P->d_ltks) || !keep(P->d_ltks_off) || !keep(P->d_ltks_outs) || (!sums.empty() && !keep(P->d_ltsum)))
+        if (!keep(P->d_lents) || (!sums.empty() && !keep(P->d_ltsum)))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // identity (d = 0) terms over all outputs; this launch also zero-initialises
@@ -616,6 +718,37 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
         if (!keep(ch.d_rots) || (!dbl && !keep(ch.d_div)) || !keep(ch.d_terms) || !keep(ch.d_off) || !keep(ch.d_outs))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         P->rchunks.push_back(ch);
+    }
+    // giant rotations: each transformation output with g != 0 is rotated in
+    // place (gathered copy -> hoisted ModUp -> key switch with P tau_g(c0)
+    // folded in -> ModDown into the output)
+    for (int g0 = 0; g0 < G; g0 += GCH) {
+        GiantChunk ch;
+        ch.cnt = std::min(GCH, G - g0);
+        std::vector<u64 *> src;
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        for (int r = 0; r < ch.cnt; r++) {
+            const auto &gi = gitems[g0 + r];
+            u64 *o = out_ct(gi[0], gi[1], gi[2]);
+            src.push_back(o);
+            const u64 g = galois_of(c, gi[3]);
+            rd.push_back({P->gD + (size_t)r * nd0 * ne0 * N, c->keys[g], P->gu + (size_t)r * 2 * ne0 * N,
+                          P->gst + (size_t)r * 2 * lv0 * N, nullptr, (u32)g, 0u});
+            for (int comp = 0; comp < 2; comp++) {
+                DivDesc v{};
+                v.u = P->gu + ((size_t)2 * r + comp) * ne0 * N;
+                v.out = o + (size_t)comp * lv0 * N;
+                v.g = 1;
+                dd.push_back(v);
+            }
+        }
+        ch.d_src = plan_upload(c, P, src);
+        ch.d_rot = plan_upload(c, P, rd);
+        ch.d_div = plan_upload(c, P, dd);
+        if (!keep(ch.d_src) || !keep(ch.d_rot) || !keep(ch.d_div))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        P->gchunks.push_back(ch);
     }
     // double mode: one ModDown per accumulated polynomial (u over PQ -> out over Q)
     auto moddown_descs = [&](u64 *u, int ne, u64 *outp, int lv, int npoly) {
@@ -824,7 +957,8 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
     // (double mode: the d = 0 terms enter as P ct and the rotations as their
     // inner-product outputs u + P tau(c0), all over PQ; one ModDown per output)
     if (P->fused) {
-        if ((rc = lt_ksw(c, lv0, P->d_ltks, P->d_ltks_off, P->d_ltks_outs, P->ltks_items, P->ltks_keyed))) return rc;
+        if ((rc = lt_group(c, lv0, 1, P->d_lents, P->d_litems[0], P->lt_nitems[0], P->lt_bytes[0]))) return rc;
+        if ((rc = lt_group(c, lv0, LT_GROUP, P->d_lents, P->d_litems[1], P->lt_nitems[1], P->lt_bytes[1]))) return rc;
         if ((rc = sum_desc(c, lv0, P->d_ltsum, P->ltsum_n, np0))) return rc;
     } else if ((rc = lt_accumulate(c, lv0, np0, lv0, dbl, P->d_id_terms, P->d_id_off, P->d_all_outs, P->O, 0))) {
         return rc;
@@ -838,6 +972,12 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
         if ((rc = lt_accumulate(c, lv0, np0, np0, 0, ch.d_terms, ch.d_off, ch.d_outs, ch.nout, 1))) return rc;
     }
     if (dbl && (rc = moddown_polys(c, lv0, P->acc, P->d_ltdiv, 2 * P->O))) return rc;
+    // 2b. giant rotations of the shared-baby-step order
+    for (auto &ch : P->gchunks) {
+        if ((rc = gather_cts(c, lv0, ch.d_src, ch.cnt, P->gst))) return rc;
+        if ((rc = modup(c, lv0, ch.cnt, P->gst + (size_t)lv0 * N, (long long)2 * lv0 * N, P->gxc, P->gD))) return rc;
+        if ((rc = ksw_moddown(c, lv0, ch.d_rot, ch.d_div, ch.cnt, P->gu, nullptr))) return rc;
+    }
     // 3. modulus switch (only for chains that drop a prime before products)
     if (lv1 != lv0)
         if ((rc = modswitch_polys(c, lv0, P->outs, 2 * P->O, nullptr, P->ms, P->d_msdiv))) return rc;
@@ -931,9 +1071,10 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
         shapes.push_back({m, l, n, a});
         key.insert(key.end(), {m, l, n, a});
     }
-    const int dbl = c->ks_double ? 1 : 0, lazy = c->lazy_relin ? 1 : 0;
+    const int dbl = c->ks_double ? 1 : 0, lazy = c->lazy_relin ? 1 : 0, shared = c->lt_shared ? 1 : 0;
     key.push_back(dbl);
     key.push_back(lazy);
+    key.push_back(shared);
     key.push_back(dbl ? c->lt_chunk : 0);
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
@@ -942,7 +1083,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     if (it != c->bplans.end()) {
         P = it->second;
     } else {
-        int rc = build_bplan(c, shapes, dbl, lazy, &P);
+        int rc = build_bplan(c, shapes, dbl, lazy, shared, &P);
         if (rc) return rc;
         if (cache) {
             evict_plans(c, P->ws_bytes);
@@ -1016,10 +1157,12 @@ int hegmm_matmul_batch_algs(hegmm_ctx *h, int count, const hegmm_ct *const *A, c
 
 int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {
     if (!h) return HEGMM_EINVAL;
-    if (mode < 0 || mode > (HEGMM_KS_DOUBLE | HEGMM_KS_LAZY_RELIN))
-        return set_err(&h->c, HEGMM_EINVAL, "key-switch mode: HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE, optionally | HEGMM_KS_LAZY_RELIN");
+    if (mode < 0 || mode > (HEGMM_KS_DOUBLE | HEGMM_KS_LAZY_RELIN | HEGMM_KS_SHARED))
+        return set_err(&h->c, HEGMM_EINVAL,
+                       "key-switch mode: HEGMM_KS_SINGLE or HEGMM_KS_DOUBLE, optionally | HEGMM_KS_LAZY_RELIN | HEGMM_KS_SHARED");
     h->c.ks_double = (mode & HEGMM_KS_DOUBLE) != 0;
     h->c.lazy_relin = (mode & HEGMM_KS_LAZY_RELIN) != 0;
+    h->c.lt_shared = (mode & HEGMM_KS_SHARED) != 0;
     return HEGMM_OK;
 }
 
@@ -1032,7 +1175,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_KERNEL) {
-        if (value < 0 || value > 4) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..4");
+        if (value < 0 || value > 2) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..2");
         c->lt_kernel = (int)value;
         return HEGMM_OK;
     }
@@ -1051,7 +1194,7 @@ int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {
         const int a = resolve_alg(mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], alg, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
         ShapeData *sd;
-        int rc = get_shape(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], a, &sd);
+        int rc = get_shape(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], a, c->lt_shared, &sd);
         if (rc) return rc;
     }
     return HEGMM_OK;

@@ -72,17 +72,24 @@ struct DivDesc {
 
 // A product output of the linear-transformation accumulation:
 // out[c][i] (+)= sum over terms src[c][i] * mask[i].
-// One term of a double-hoisted linear transformation (Eq. lintrans):
-// mask (.) (u_g + P tau_g(c0), u1_g) with u_g the key-switch inner product
-// of the hoisted digits D under tau_g, or, for the d = 0 term (key null),
-// mask (.) P ct.  Sums over PQ; the caller divides by P once (ModDown).
-struct LtKsTerm {
-    const u64 *D;     // hoisted digits of the source [nd][ne][N] (NTT)
-    const u64 *key;   // Galois key [nd][2][L+K][N], Montgomery NTT; null: the d = 0 term
-    const u64 *ct;    // the source ciphertext [2][lv][N] (NTT)
-    const u64 *mask;  // [L + K][N] Montgomery NTT
+// Double-hoisted linear transformations (Eq. lintrans) of up to LT_GROUP
+// outputs of one operand per work item.  An entry is one source term shared
+// by the item's outputs: u = (<tau_g(D), k_0> + P tau_g(c0), <tau_g(D), k_1>)
+// for a rotation, u = P ct for the d = 0 term (key null); every output j of
+// the item with mask[j] != null adds mask[j] (.) u to its sum over PQ.  The
+// caller divides each sum by P once (ModDown).
+constexpr int LT_GROUP = 8;
+struct LtEntry {
+    const u64 *D;                // hoisted digits of the source [nd][ne][N] (NTT)
+    const u64 *key;              // Galois key [nd][2][L+K][N], Montgomery NTT; null: the d = 0 term
+    const u64 *ct;               // the source ciphertext [2][lv][N] (NTT)
     u32 g;
     u32 pad;
+    const u64 *mask[LT_GROUP];   // [L + K][N] Montgomery NTT per output of the item, or null
+};
+struct LtItem {
+    int first, count;            // entries [first, first + count)
+    u64 *out[LT_GROUP];          // [2][lv+K][N] per output of the item, or null
 };
 
 // Sum of the tensors of count iteration products: d = sum_k (a_k0 b_k0,
@@ -171,15 +178,16 @@ struct Ctx {
     std::map<std::pair<int, int>, DivTab> divs;  // (level, 0 = ModDown / 1 = modswitch)
     std::vector<int> slot_pos0, slot_pos1;       // slot -> NTT position mod t
     int *d_slot_pos0 = nullptr;                  // device copy of slot_pos0
-    std::map<std::tuple<int, int, int, int>, ShapeData *> shapes;  // per-shape plan + masks
+    std::map<std::tuple<int, int, int, int, int>, ShapeData *> shapes;  // per (shape, order): plan + masks
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
     int lazy_relin = 0;                        // products: one relinearisation of the summed tensors
-    int lt_chunk = 32;                         // double mode: terms per k_lt_ksw work item
+    int lt_shared = 0;                         // products: shared baby steps + giant rotations
+    int lt_chunk = 32;                         // double mode: entries per k_lt_grp work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
-    int lt_kernel = 3;                         // fused kernel variant (coefficients per thread, CTAs per SM)
+    int lt_kernel = 0;                         // grouped fused kernel variant (resident CTAs per SM)
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
@@ -258,10 +266,11 @@ int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_
 int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
 // n tensor sums (lazy 128-bit: (2 count + 2) q < 2^64)
 int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n);
-// outs[o] = sum over the terms [off[o], off[o+1]) of LtKsTerm contributions,
-// over the extended basis of level lv ([2][lv+K][N] per output).  Needs
-// (terms per output + 2) * q < 2^64 for every prime (lazy 128-bit sums).
-int lt_ksw(Ctx *c, int lv, const LtKsTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout, double nterms);
+// Every item's output sums over the extended basis of level lv.  Needs
+// (entries per item + 2) * q < 2^64 for every prime (lazy 128-bit sums).
+// bytes: the algorithmic HBM bytes of the launch (keys, masks, outputs).
+// group: 1 for items of one output each, LT_GROUP otherwise.
+int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes);
 // out[poly] = sum_k in[k][poly] over nk inputs with stride in_stride words; npolylimbs = 2*lv
 int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate);
 // pointwise helpers over [npoly][lv][N]

@@ -456,151 +456,98 @@ int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
     return cuda_check(c, "ksw_ip");
 }
 
-// Double-hoisted linear transformation, one CTA row per (work item, limb):
-// every term's key-switch inner product is formed in registers and enters
-// the item's sum at once (no per-rotation output in memory):
-//   acc_c = sum_terms mask * u_c,  u_0 = <tau_g(D), k_0> + P tau_g(c0),
-//   u_1 = <tau_g(D), k_1>;  d = 0 terms: u_c = P c_c (0 on special primes).
-// Both sums are lazy 128-bit Montgomery sums (terms * q^2 < q 2^64).
-// CPT coefficients per thread (1: 8-byte loads, more threads; 2: 16-byte
-// loads); MINB resident CTAs per SM (the register cap).
-template <int CPT>
-struct Coefs {
-    u64 v[CPT];
-};
-template <int CPT>
-__device__ __forceinline__ Coefs<CPT> ld_coefs(const u64 *p) {
-    Coefs<CPT> r;
-    if constexpr (CPT == 2) {
-        const ulonglong2 x = __ldg(reinterpret_cast<const ulonglong2 *>(p));
-        r.v[0] = x.x;
-        r.v[1] = x.y;
-    } else {
-        r.v[0] = __ldg(p);
-    }
-    return r;
-}
-template <int CPT>
-__device__ __forceinline__ Coefs<CPT> ld_coefs_stream(const u64 *p) {
-    Coefs<CPT> r;
-    if constexpr (CPT == 2) {
-        const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(p));
-        r.v[0] = x.x;
-        r.v[1] = x.y;
-    } else {
-        r.v[0] = __ldcs(p);
-    }
-    return r;
-}
-template <int CPT>
-__device__ __forceinline__ void st_coefs(u64 *p, const u64 *v) {
-    if constexpr (CPT == 2) {
-        ulonglong2 x;
-        x.x = v[0];
-        x.y = v[1];
-        *reinterpret_cast<ulonglong2 *>(p) = x;
-    } else {
-        *p = v[0];
-    }
-}
-
-template <int CPT, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_lt_ksw(int lv, int ne, int nd, int np, int L, int logN,
-                                                   const ModDev *__restrict__ mods, const LtKsTerm *__restrict__ terms,
-                                                   const int *__restrict__ off, u64 *const *__restrict__ outs) {
+// Double-hoisted linear transformations, one CTA row per (work item, limb),
+// one coefficient per thread: each entry's key-switch inner product is
+// formed once in registers and multiplied into the lazy 128-bit sums of
+// every output of the item that uses it (at most LT_GROUP), so a rotation
+// shared by the outputs of an item reads its key once:
+//   acc_j += mask_j * u,  u_0 = <tau_g(D), k_0> + P tau_g(c0),
+//   u_1 = <tau_g(D), k_1>;  d = 0 entries: u = P ct (0 on special primes).
+// grid (N / 256, items, limbs): the CTAs resident together cover many items
+// of one limb.
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, int np, int L, int logN,
+                                                   const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
+                                                   const LtItem *__restrict__ items) {
     const int N = 1 << logN;
-    const int c = CPT * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    // grid (slices, items, limbs): CTAs resident together cover many items
-    // of one limb, so items that share Galois keys read them from L2
-    const int o = blockIdx.y, e = blockIdx.z;
+    const int e = blockIdx.z;
+    const LtItem *it = items + blockIdx.y;
     const int gm = e < lv ? e : L + (e - lv);
     const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
-    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N;
-    Acc s0[CPT], s1[CPT];
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
+    Acc s0[G], s1[G];
 #pragma unroll
-    for (int i = 0; i < CPT; i++) s0[i] = s1[i] = Acc{0, 0};
-    const int t1 = off[o + 1];
-    for (int t = off[o]; t < t1; t++) {
-        const LtKsTerm T = terms[t];
-        u64 u0[CPT], u1[CPT];
-        if (T.key) {
-            u32 src[CPT];
-#pragma unroll
-            for (int i = 0; i < CPT; i++) src[i] = auto_src((u32)(c + i), T.g, logN);
-            const u64 *Dp = T.D + (size_t)e * N;
-            const u64 *Kp = T.key + (size_t)gm * N + c;
-            Acc a0[CPT], a1[CPT];
-#pragma unroll
-            for (int i = 0; i < CPT; i++) a0[i] = a1[i] = Acc{0, 0};
+    for (int j = 0; j < G; j++) s0[j] = s1[j] = Acc{0, 0};
+    const int t0 = it->first, t1 = t0 + it->count;
+    for (int t = t0; t < t1; t++) {
+        const LtEntry *E = ents + t;
+        const u64 *key = E->key;
+        u64 u0, u1;
+        if (key) {
+            const u32 src = auto_src((u32)c, E->g, logN);
+            const u64 *Dp = E->D + (size_t)e * N + src;
+            const u64 *Kp = key + moff;
+            Acc a0{0, 0}, a1{0, 0};
 #pragma unroll 4
             for (int j = 0; j < nd; j++) {
-                const Coefs<CPT> k0 = ld_coefs_stream<CPT>(Kp + (size_t)(2 * j) * kstep);
-                const Coefs<CPT> k1 = ld_coefs_stream<CPT>(Kp + (size_t)(2 * j + 1) * kstep);
-#pragma unroll
-                for (int i = 0; i < CPT; i++) {
-                    const u64 x = __ldg(Dp + (size_t)j * dstep + src[i]);
-                    mac(a0[i], x, k0.v[i]);
-                    mac(a1[i], x, k1.v[i]);
-                }
+                const u64 x = __ldg(Dp + (size_t)j * dstep);
+                mac(a0, x, __ldcs(Kp + (size_t)(2 * j) * kstep));
+                mac(a1, x, __ldcs(Kp + (size_t)(2 * j + 1) * kstep));
             }
-#pragma unroll
-            for (int i = 0; i < CPT; i++) {
-                if (e < lv) mac(a0[i], __ldg(T.ct + (size_t)e * N + src[i]), pR);
-                u0[i] = montred(a0[i], q, qinv);
-                u1[i] = montred(a1[i], q, qinv);
-            }
+            if (e < lv) mac(a0, __ldg(E->ct + (size_t)e * N + src), pR);
+            u0 = montred(a0, q, qinv);
+            u1 = montred(a1, q, qinv);
         } else {
             if (e >= lv) continue;
-            const Coefs<CPT> x = ld_coefs<CPT>(T.ct + (size_t)e * N + c);
-            const Coefs<CPT> y = ld_coefs<CPT>(T.ct + ((size_t)lv + e) * N + c);
+            u0 = montmul(__ldg(E->ct + (size_t)e * N + c), pR, q, qinv);
+            u1 = montmul(__ldg(E->ct + ((size_t)lv + e) * N + c), pR, q, qinv);
+        }
 #pragma unroll
-            for (int i = 0; i < CPT; i++) {
-                u0[i] = montmul(x.v[i], pR, q, qinv);
-                u1[i] = montmul(y.v[i], pR, q, qinv);
+        for (int j = 0; j < G; j++) {
+            const u64 *mp = E->mask[j];
+            if (mp) {
+                const u64 m = __ldg(mp + moff);
+                mac(s0[j], u0, m);
+                mac(s1[j], u1, m);
             }
         }
-        const Coefs<CPT> m = ld_coefs<CPT>(T.mask + (size_t)gm * N + c);
+    }
 #pragma unroll
-        for (int i = 0; i < CPT; i++) {
-            mac(s0[i], u0[i], m.v[i]);
-            mac(s1[i], u1[i], m.v[i]);
+    for (int j = 0; j < G; j++) {
+        u64 *o = it->out[j];
+        if (o) {
+            o[(size_t)e * N + c] = montred(s0[j], q, qinv);
+            o[((size_t)ne + e) * N + c] = montred(s1[j], q, qinv);
         }
     }
-    u64 *out = outs[o];
-    u64 r0[CPT], r1[CPT];
-#pragma unroll
-    for (int i = 0; i < CPT; i++) {
-        r0[i] = montred(s0[i], q, qinv);
-        r1[i] = montred(s1[i], q, qinv);
-    }
-    st_coefs<CPT>(out + (size_t)e * N + c, r0);
-    st_coefs<CPT>(out + ((size_t)ne + e) * N + c, r1);
 }
 
-template <int CPT, int MINB>
-static void launch_lt_ksw(Ctx *c, int lv, int ne, int nd, const LtKsTerm *d_terms, const int *d_off,
-                          u64 *const *d_outs, int nout) {
-    for (int o0 = 0; o0 < nout; o0 += kMaxGridZ)  // term offsets are absolute, so a slice needs no rebasing
-        k_lt_ksw<CPT, MINB><<<grid_coef(c->N / CPT, std::min(kMaxGridZ, nout - o0), ne), 256, 0, c->st>>>(
-            lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_terms, d_off + o0, d_outs + o0);
-}
-
-int lt_ksw(Ctx *c, int lv, const LtKsTerm *d_terms, const int *d_off, u64 *const *d_outs, int nout, double nterms) {
-    if (nout <= 0) return HEGMM_OK;
+int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes) {
+    if (nitems <= 0) return HEGMM_OK;
     const int ne = lv + c->K, nd = c->digits(lv);
-    // algorithmic HBM bytes: per key-switched term its key (2 nd ne limbs)
-    // and mask (ne limbs); per output its sum (2 ne limbs) written.  Digits
-    // and sources are shared by all terms of a source and served from L2.
-    Launch t(c, K_LT_KSW, (nterms * (2.0 * nd * ne + ne) + (double)nout * 2.0 * ne) * c->limb_bytes());
-    switch (c->lt_kernel) {
-        case 1: launch_lt_ksw<2, 4>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
-        case 2: launch_lt_ksw<1, 4>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
-        case 3: launch_lt_ksw<1, 6>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
-        case 4: launch_lt_ksw<1, 8>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
-        default: launch_lt_ksw<2, 3>(c, lv, ne, nd, d_terms, d_off, d_outs, nout); break;
+    Launch t(c, K_LT_KSW, bytes);
+    for (int i0 = 0; i0 < nitems; i0 += kMaxGridZ) {
+        const dim3 grid((unsigned)((c->N + 255) / 256), (unsigned)std::min(kMaxGridZ, nitems - i0), (unsigned)ne);
+        const LtItem *it = d_items + i0;
+        if (group == 1) {  // items of one output: few registers, six CTAs per SM
+            k_lt_grp<1, 6><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+            continue;
+        }
+        switch (c->lt_kernel) {
+            case 1:
+                k_lt_grp<LT_GROUP, 2><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+                break;
+            case 2:
+                k_lt_grp<LT_GROUP, 3><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+                break;
+            default:
+                k_lt_grp<LT_GROUP, 4><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+                break;
+        }
     }
-    return cuda_check(c, "lt_ksw");
+    return cuda_check(c, "lt_group");
 }
 
 // ------------------------------------------------------------------ exact division by D with t-correction

@@ -44,11 +44,13 @@ def encrypt_all(ctx, H, shapes, lo, hi, seed0=0, stream0=0):
     return As, Bs, mats
 
 
-@pytest.mark.parametrize("mode", ["double+lazy", "double", "single"])
+@pytest.mark.parametrize("mode", ["double+lazy+shared", "double+lazy", "double", "single"])
 def test_batch_mixed_shapes_equal_single_and_oracle(H, medium, mode):
     ctx = medium
-    base, _, lazy = mode.partition("+")
-    ctx.hegmm_set_keyswitch_mode((H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0))
+    parts = mode.split("+")
+    base, lazy, shared = parts[0], "lazy" in parts, "shared" in parts
+    ctx.hegmm_set_keyswitch_mode((H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0)
+                                 | (H.KS_SHARED if shared else 0))
     shapes = [(4, 8, 6), (5, 12, 7), (9, 4, 11), (7, 9, 2), (12, 3, 9), (3, 3, 3), (6, 40, 5), (20, 10, 30)]
     ctx.hegmm_keygen(SEED, shapes)
     As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE)
@@ -64,7 +66,7 @@ def test_batch_mixed_shapes_equal_single_and_oracle(H, medium, mode):
     for i in (0, 3):
         m, l, n = shapes[i]
         plan = SL.make_plan(m, l, n, SL.choose_alg(m, l, n, o.S))
-        ex = OH.HEGMM(o, mode=base, lazy_relin=bool(lazy))
+        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy, giant=shared)
         ctA, ctB = ex.encrypt_inputs(plan, *mats[i], seed=77, streams=(2 * i, 2 * i + 1))
         assert (ctx.hegmm_ct_export(outs[i]) == ex.run(plan, ctA, ctB)).all()
     ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)  # the library default
@@ -114,7 +116,7 @@ def test_batch_with_per_product_algorithms(H, medium):
         mats.append((A, B))
         As.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, algs[i]), 77, 3000 + 2 * i))
         Bs.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, algs[i]), 77, 3001 + 2 * i))
-    for flags in (H.KS_SINGLE, H.KS_DOUBLE | H.KS_LAZY_RELIN):
+    for flags in (H.KS_SINGLE, H.KS_DOUBLE | H.KS_LAZY_RELIN, H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED):
         ctx.hegmm_set_keyswitch_mode(flags)
         outs = ctx.hegmm_matmul_batch_algs(As, Bs, shapes, algs)
         for i, (m, l, n) in enumerate(shapes):

@@ -121,20 +121,22 @@ def test_modswitch_tiny(H):
     assert (ctx.hegmm_ct_export(p) == o.mult_relin(o.modswitch(co), o.modswitch(co))).all()
 
 
-MODES = ["single", "double", "single+lazy", "double+lazy"]
+MODES = ["single", "double", "single+lazy", "double+lazy", "single+shared", "double+lazy+shared"]
 
 
 def set_mode(H, ctx, mode):
-    """Sets the library's evaluation order; returns the oracle's (mode, lazy_relin)."""
-    base, _, lazy = mode.partition("+")
-    flags = (H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0)
+    """Sets the library's evaluation order; returns the oracle's (mode, lazy_relin, giant)."""
+    parts = mode.split("+")
+    base, lazy, shared = parts[0], "lazy" in parts, "shared" in parts
+    flags = ((H.KS_DOUBLE if base == "double" else H.KS_SINGLE) | (H.KS_LAZY_RELIN if lazy else 0)
+             | (H.KS_SHARED if shared else 0))
     ctx.hegmm_set_keyswitch_mode(flags)
-    return base, bool(lazy)
+    return base, lazy, shared
 
 
 def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"):
     pre, ctx, o = get_pair(H, name)
-    base, lazy = set_mode(H, ctx, mode)
+    base, lazy, shared = set_mode(H, ctx, mode)
     A, B = W.matrices(m, l, n, lo, hi, seed=seed)
     ctx.hegmm_keygen(SEED, [(m, l, n)], alg)
     ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 11, 100)
@@ -148,7 +150,7 @@ def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"
     assert cnt["rot"] == pc["rot"] and cnt["mult"] == pc["mult"] and cnt["cmult"] == pc["cmult"]
     assert cnt["relin"] == (1 if lazy else pc["mult"])
     if bitexact:
-        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy)
+        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy, giant=shared)
         ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=11, streams=(100, 101))
         assert (ctx.hegmm_ct_export(ca) == ctA).all()
         oc = ex.run(plan, ctA, ctB)
@@ -162,8 +164,7 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
     run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE, mode=mode)
 
 
-@pytest.mark.parametrize("chunk,variant,fused", [(1, 3, 1), (3, 0, 1), (4096, 1, 1), (32, 2, 1), (32, 4, 1),
-                                                  (32, 3, 0)])
+@pytest.mark.parametrize("chunk,variant,fused", [(1, 0, 1), (3, 1, 1), (4096, 2, 1), (32, 0, 0)])
 def test_double_mode_executor_settings(H, chunk, variant, fused):
     # work-item size, fused-kernel variant and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
@@ -173,9 +174,11 @@ def test_double_mode_executor_settings(H, chunk, variant, fused):
     try:
         run_both(H, "tiny", 4, 8, 6, 1, *W.TINY_RANGE, mode="double")
         run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double", seed=3)
+        # shared baby steps make a work item's entries serve several outputs
+        run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double+lazy+shared", seed=5)
     finally:
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
-        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 3)
+        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 0)
         ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, 1)
 
 
@@ -187,7 +190,7 @@ def test_hegmm_tiny_edge_shapes(H, shape):
             run_both(H, "tiny", *shape, alg, *W.TINY_RANGE, seed=sum(shape), mode=mode)
 
 
-@pytest.mark.parametrize("mode", ["single", "double", "double+lazy"])
+@pytest.mark.parametrize("mode", ["single", "double", "double+lazy", "double+lazy+shared"])
 @pytest.mark.parametrize("shape", W.MEDIUM_SHAPES)
 def test_hegmm_medium_alg2_bitexact(H, shape, mode):
     run_both(H, "medium", *shape, 2, *W.MEDIUM_RANGE, mode=mode)
@@ -197,6 +200,13 @@ def test_hegmm_medium_alg2_bitexact(H, shape, mode):
 @pytest.mark.parametrize("shape", W.MEDIUM_SHAPES)
 def test_hegmm_medium_alg1(H, shape, mode):
     run_both(H, "medium", *shape, 1, *W.MEDIUM_RANGE, bitexact=False, mode=mode)
+
+
+@pytest.mark.parametrize("mode", ["single+shared", "double+lazy+shared"])
+def test_hegmm_medium_alg1_shared_bitexact(H, mode):
+    # 6x10x9 under Algorithm 1: the shared-baby-step rule picks giant rotations
+    assert any(g for g, _ in SL.giant_factor([it[1] for it in SL.make_plan(6, 10, 9, 1).iters], 4096))
+    run_both(H, "medium", 6, 10, 9, 1, *W.MEDIUM_RANGE, mode=mode)
 
 
 def test_hegmm_medium_maximum_shape(H):
