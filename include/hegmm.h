@@ -198,6 +198,13 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     outputs, by resident CTAs per SM (its register cap): 0 = 4 (default,
  *     measured fastest on GB300 at N = 2^13), 1 = 2, 2 = 3. */
 #define HEGMM_TUNE_LT_KERNEL 3
+/*   HEGMM_TUNE_GIANT_COST: the cost of one giant rotation, in baby key
+ *     switches, in the greedy rule of HEGMM_KS_SHARED (1..65536, default 8).
+ *     It selects which factorisation is used, so it changes the ciphertext
+ *     bits (each value matches the oracle run with the same cost); Galois
+ *     keys the new factorisation needs are made from the context's secret
+ *     key when a plan first needs them. */
+#define HEGMM_TUNE_GIANT_COST 4
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in
@@ -326,11 +333,12 @@ void hegmm_ct_destroy(hegmm_ct *ct);
  * hegmm_plan_layout writes the client-side slot vector of role A or B for
  * the plan (values mod t) into out[cap] and returns its length. */
 /* hegmm_plan_giant writes the shared-baby-step factorisation of role A (0,
- * the eps^k) or B (1, the omega^k) used by HEGMM_KS_SHARED as ints into
+ * the eps^k) or B (1, the omega^k) used by HEGMM_KS_SHARED, for the giant
+ * cost `cost` (0: the default 8; see HEGMM_TUNE_GIANT_COST), as ints into
  * buf[cap] and returns the number it needs: iterations, then per iteration
  * its giant rotation g (0: none) and term count, and per term its baby
  * offset b in [0, S), slot count c and the c destination slots. */
-int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int *buf, int cap);
+int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int cost, int *buf, int cap);
 int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *out);
 int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int cap);
 int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t,

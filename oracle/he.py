@@ -440,7 +440,8 @@ class HEGMM:
 
     MODES = ("single", "double")
 
-    def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False, giant: bool = False):
+    def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False, giant: bool = False,
+                 giant_cost: int = SL.GIANT_COST):
         """mode "single": every key switch ends in its own ModDown, as the
         HE operations Rot, CMult, Mult and Add compose (the paper's cost
         model).  mode "double": the sums of key-switched terms (each linear
@@ -461,6 +462,7 @@ class HEGMM:
         self.mode = mode
         self.lazy_relin = lazy_relin
         self.giant = giant
+        self.giant_cost = giant_cost
         self._mask_cache: Dict[Tuple, np.ndarray] = {}
 
     def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
@@ -545,8 +547,8 @@ class HEGMM:
         acc = None
         dsum = None
         if self.giant:
-            fa = SL.giant_factor([e for e, _ in plan.iters], o.S)
-            fb = SL.giant_factor([om for _, om in plan.iters], o.S)
+            fa = SL.giant_factor([e for e, _ in plan.iters], o.S, self.giant_cost)
+            fb = SL.giant_factor([om for _, om in plan.iters], o.S, self.giant_cost)
         for k, (e, om) in enumerate(plan.iters):
             if self.giant:
                 a = self.lt_giant(ctA, fa[k], scale)

@@ -256,7 +256,7 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
         tl[s].resize(hp.iters.size());
         sd->giant[s].assign(hp.iters.size(), 0);
         if (sd->shared) {
-            std::vector<GiantLT> f = giant_factor_of(hp, s, S);
+            std::vector<GiantLT> f = giant_factor_of(hp, s, S, shared);
             for (size_t k = 0; k < f.size(); k++) {
                 sd->giant[s][k] = f[k].g;
                 for (auto &t : f[k].terms) tl[s][k].push_back({t.b, t.dst});
@@ -280,10 +280,24 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
         return set_err(c, code, msg);
     };
     for (int s = 0; s < 2; s++) {
+        // the plan's own offsets come from hegmm_keygen; those of a
+        // shared-baby-step factorisation (which depends on the giant cost)
+        // are made from the secret key on first use
         for (long long z : sd->zs[s])
-            if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+            if (!c->keys.count(galois_of(c, z))) {
+                if (!sd->shared) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+                if (int rc = ensure_galois_key(c, galois_of(c, z))) {
+                    delete sd;
+                    return rc;
+                }
+            }
         for (int g : sd->giant[s])
-            if (g && !c->keys.count(galois_of(c, g))) return fail(HEGMM_ENOKEY, "missing Galois key: run hegmm_keygen for this shape");
+            if (g && !c->keys.count(galois_of(c, g))) {
+                if (int rc = ensure_galois_key(c, galois_of(c, g))) {
+                    delete sd;
+                    return rc;
+                }
+            }
     }
     for (int z : hp.extract)
         if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
@@ -371,7 +385,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     std::set<ShapeData *> held;
     for (auto &s : shapes) {
         ShapeData *sd;
-        int rc = get_shape(c, s[0], s[1], s[2], s[3], shared, &sd);
+        int rc = get_shape(c, s[0], s[1], s[2], s[3], shared ? c->giant_cost : 0, &sd);
         if (rc) {
             P->shp.assign(held.begin(), held.end());  // release what this plan holds
             return fail_rc(rc);
@@ -1074,7 +1088,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     const int dbl = c->ks_double ? 1 : 0, lazy = c->lazy_relin ? 1 : 0, shared = c->lt_shared ? 1 : 0;
     key.push_back(dbl);
     key.push_back(lazy);
-    key.push_back(shared);
+    key.push_back(shared ? c->giant_cost : 0);
     key.push_back(dbl ? c->lt_chunk : 0);
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
@@ -1179,6 +1193,11 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         c->lt_kernel = (int)value;
         return HEGMM_OK;
     }
+    if (knob == HEGMM_TUNE_GIANT_COST) {
+        if (value < 1 || value > 65536) return set_err(c, HEGMM_EINVAL, "giant cost must be in 1..65536");
+        c->giant_cost = (int)value;
+        return HEGMM_OK;
+    }
     if (knob == HEGMM_TUNE_LT_FUSED) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "lt_fused must be 0 or 1");
         c->lt_fused = (int)value;
@@ -1194,7 +1213,7 @@ int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {
         const int a = resolve_alg(mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], alg, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
         ShapeData *sd;
-        int rc = get_shape(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], a, c->lt_shared, &sd);
+        int rc = get_shape(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], a, c->lt_shared ? c->giant_cost : 0, &sd);
         if (rc) return rc;
     }
     return HEGMM_OK;

@@ -218,10 +218,10 @@ std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &
     return res;
 }
 
-std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S) {
+std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S, int cost) {
     std::vector<const std::vector<Diag> *> outs;
     for (const auto &it : P.iters) outs.push_back(s == 0 ? &it.eps : &it.omg);
-    return giant_factor(outs, S);
+    return giant_factor(outs, S, cost);
 }
 
 }  // namespace hg
@@ -230,12 +230,12 @@ using namespace hg;
 
 extern "C" {
 
-int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int *buf, int cap) {
-    if (slots <= 0 || (role != 0 && role != 1) || cap < 0 || (cap > 0 && !buf)) return HEGMM_EINVAL;
+int hegmm_plan_giant(int m, int l, int n, int alg, int slots, int role, int cost, int *buf, int cap) {
+    if (slots <= 0 || (role != 0 && role != 1) || cost < 0 || cap < 0 || (cap > 0 && !buf)) return HEGMM_EINVAL;
     const int a = resolve_alg(m, l, n, alg, slots);
     if (!a) return HEGMM_ESHAPE;
     HostPlan P = make_host_plan(m, l, n, a);
-    std::vector<GiantLT> f = giant_factor_of(P, role, slots);
+    std::vector<GiantLT> f = giant_factor_of(P, role, slots, cost ? cost : GIANT_COST);
     std::vector<int> v{(int)f.size()};
     for (const auto &x : f) {
         v.push_back(x.g);

@@ -68,7 +68,7 @@ struct GiantLT {
 };
 std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &outs, int S, int cost = GIANT_COST);
 // The factorisation of operand s (0: eps / A, 1: omega / B) of a plan.
-std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S);
+std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S, int cost = GIANT_COST);
 
 // Number of slots Algorithm 1 / 2 needs for (m, l, n).
 int alg1_length(int m, int l, int n);

@@ -20,7 +20,7 @@ HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
-TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL = 1, 2, 3  # hegmm_set_tuning
+TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST = 1, 2, 3, 4  # hegmm_set_tuning
 ROLE_A, ROLE_B = 0, 1
 
 
@@ -126,7 +126,7 @@ _SIGS = {
     "hegmm_plan_describe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            intp, ctypes.c_int]),
     "hegmm_plan_giant": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_int, intp, ctypes.c_int]),
+                                        ctypes.c_int, ctypes.c_int, intp, ctypes.c_int]),
     "hegmm_plan_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, i64p, ctypes.c_uint64, u64p, ctypes.c_int]),
 }
@@ -169,13 +169,13 @@ def hegmm_plan_describe(m: int, l: int, n: int, alg: int, slots: int) -> List[in
     return list(buf)
 
 
-def hegmm_plan_giant(m: int, l: int, n: int, alg: int, slots: int, role: int) -> List[int]:
+def hegmm_plan_giant(m: int, l: int, n: int, alg: int, slots: int, role: int, cost: int = 0) -> List[int]:
     lib = load()
-    need = lib.hegmm_plan_giant(m, l, n, alg, slots, role, None, 0)
+    need = lib.hegmm_plan_giant(m, l, n, alg, slots, role, cost, None, 0)
     if need < 0:
         raise HegmmError(need, "plan_giant")
     buf = (ctypes.c_int * need)()
-    lib.hegmm_plan_giant(m, l, n, alg, slots, role, buf, need)
+    lib.hegmm_plan_giant(m, l, n, alg, slots, role, cost, buf, need)
     return list(buf)
 
 

@@ -124,9 +124,9 @@ def test_ksw_counts_share_rotations_across_iterations(H):
             assert c["ksw"] <= c["rot"] + c["mult"]
 
 
-def oracle_giant(m, l, n, alg, S, role):
+def oracle_giant(m, l, n, alg, S, role, cost=SL.GIANT_COST):
     plan = SL.make_plan(m, l, n, alg)
-    f = SL.giant_factor([it[role] for it in plan.iters], S)
+    f = SL.giant_factor([it[role] for it in plan.iters], S, cost)
     v = [len(f)]
     for g, terms in f:
         v += [g, len(terms)]
@@ -147,3 +147,6 @@ def test_host_shared_baby_steps_match_oracle(H):
             for role in (0, 1):
                 assert H.hegmm_plan_giant(m, l, n, alg, S, role) == oracle_giant(m, l, n, alg, S, role), \
                     (m, l, n, alg, role)
+                for cost in (1, 3, 40):
+                    assert H.hegmm_plan_giant(m, l, n, alg, S, role, cost) == \
+                        oracle_giant(m, l, n, alg, S, role, cost), (m, l, n, alg, role, cost)

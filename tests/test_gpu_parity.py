@@ -134,9 +134,10 @@ def set_mode(H, ctx, mode):
     return base, lazy, shared
 
 
-def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"):
+def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double", giant_cost=SL.GIANT_COST):
     pre, ctx, o = get_pair(H, name)
     base, lazy, shared = set_mode(H, ctx, mode)
+    ctx.hegmm_set_tuning(H.TUNE_GIANT_COST, giant_cost)
     A, B = W.matrices(m, l, n, lo, hi, seed=seed)
     ctx.hegmm_keygen(SEED, [(m, l, n)], alg)
     ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 11, 100)
@@ -150,7 +151,7 @@ def run_both(H, name, m, l, n, alg, lo, hi, bitexact=True, seed=0, mode="double"
     assert cnt["rot"] == pc["rot"] and cnt["mult"] == pc["mult"] and cnt["cmult"] == pc["cmult"]
     assert cnt["relin"] == (1 if lazy else pc["mult"])
     if bitexact:
-        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy, giant=shared)
+        ex = OH.HEGMM(o, mode=base, lazy_relin=lazy, giant=shared, giant_cost=giant_cost)
         ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=11, streams=(100, 101))
         assert (ctx.hegmm_ct_export(ca) == ctA).all()
         oc = ex.run(plan, ctA, ctB)
@@ -207,6 +208,18 @@ def test_hegmm_medium_alg1_shared_bitexact(H, mode):
     # 6x10x9 under Algorithm 1: the shared-baby-step rule picks giant rotations
     assert any(g for g, _ in SL.giant_factor([it[1] for it in SL.make_plan(6, 10, 9, 1).iters], 4096))
     run_both(H, "medium", 6, 10, 9, 1, *W.MEDIUM_RANGE, mode=mode)
+
+
+@pytest.mark.parametrize("cost", [1, 3])
+def test_shared_mode_other_giant_costs(H, cost):
+    # the giant cost picks another factorisation (and new Galois keys, made on
+    # first use); each cost is bit-exact with the oracle run at that cost
+    try:
+        run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double+lazy+shared", seed=7, giant_cost=cost)
+        run_both(H, "medium", 6, 10, 9, 1, *W.MEDIUM_RANGE, mode="single+shared", giant_cost=cost)
+    finally:
+        for name in ("tiny", "medium"):
+            get_pair(H, name)[1].hegmm_set_tuning(H.TUNE_GIANT_COST, SL.GIANT_COST)
 
 
 def test_hegmm_medium_maximum_shape(H):
