@@ -484,35 +484,45 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
     for (int t = t0; t < t1; t++) {
         const LtEntry *E = ents + t;
         const u64 *key = E->key;
+        if (!key && e >= lv) continue;  // P ct is 0 on the special primes
+        // the masks are loaded with the key and digits, so that one memory
+        // latency covers the whole entry
+        u64 mv[G];
+        unsigned used = 0;
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            const u64 *mp = E->mask[j];
+            mv[j] = 0;
+            if (mp) {
+                mv[j] = __ldg(mp + moff);
+                used |= 1u << j;
+            }
+        }
         u64 u0, u1;
         if (key) {
             const u32 src = auto_src((u32)c, E->g, logN);
             const u64 *Dp = E->D + (size_t)e * N + src;
             const u64 *Kp = key + moff;
             Acc a0{0, 0}, a1{0, 0};
+            if (e < lv) mac(a0, __ldg(E->ct + (size_t)e * N + src), pR);
 #pragma unroll 4
             for (int j = 0; j < nd; j++) {
                 const u64 x = __ldg(Dp + (size_t)j * dstep);
                 mac(a0, x, __ldcs(Kp + (size_t)(2 * j) * kstep));
                 mac(a1, x, __ldcs(Kp + (size_t)(2 * j + 1) * kstep));
             }
-            if (e < lv) mac(a0, __ldg(E->ct + (size_t)e * N + src), pR);
             u0 = montred(a0, q, qinv);
             u1 = montred(a1, q, qinv);
         } else {
-            if (e >= lv) continue;
             u0 = montmul(__ldg(E->ct + (size_t)e * N + c), pR, q, qinv);
             u1 = montmul(__ldg(E->ct + ((size_t)lv + e) * N + c), pR, q, qinv);
         }
 #pragma unroll
-        for (int j = 0; j < G; j++) {
-            const u64 *mp = E->mask[j];
-            if (mp) {
-                const u64 m = __ldg(mp + moff);
-                mac(s0[j], u0, m);
-                mac(s1[j], u1, m);
+        for (int j = 0; j < G; j++)
+            if (used & (1u << j)) {
+                mac(s0[j], u0, mv[j]);
+                mac(s1[j], u1, mv[j]);
             }
-        }
     }
 #pragma unroll
     for (int j = 0; j < G; j++) {
