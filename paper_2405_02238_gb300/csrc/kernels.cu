@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(Lim
     int mi;
     u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
     const u64 q = mods[mi].q;
+#pragma unroll 4
     for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
         ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
         const int pi = pad16(i);
@@ -162,6 +163,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divroun
     const int mi = (int)tI[i];
     const ModDev M = mods[mi];
     const u64 *hB = tB + (size_t)i * ndrop * 3;
+#pragma unroll 4
     for (int c = threadIdx.x; c < N; c += NT) {
         u64 acc = 0;
         for (int k = 0; k < ndrop; k++) {
@@ -178,6 +180,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divroun
     const u64 Di = k4[0], Dis = k4[1], tq = k4[2], tqs = k4[3];
     const u64 *ui = d.u + (size_t)i * N;
     u64 *oi = d.out + (size_t)i * N;
+#pragma unroll 4
     for (int c = threadIdx.x; c < N; c += NT) {
         u64 v = subm(ui[c], mulsh(sm[pad16(c)], tq, tqs, M.q), M.q);
         v = mulsh(v, Di, Dis, M.q);
@@ -207,6 +210,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_modup_n
     const ModDev R = mods[mi];
     const u64 *tinv = tab + (size_t)j * alpha * 2;
     const u64 *thm = tab + (size_t)nd * alpha * 2 + (size_t)j * alpha * ne * 3;
+#pragma unroll 4
     for (int c = threadIdx.x; c < N; c += NT) {
         u64 acc = 0;
         for (int ii = 0; ii < ns; ii++) {
