@@ -205,6 +205,11 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     keys the new factorisation needs are made from the context's secret
  *     key when a plan first needs them. */
 #define HEGMM_TUNE_GIANT_COST 4
+/*   HEGMM_TUNE_GRAPHS: 1 (default) replays the launch sequence of a cached
+ *     product plan (hegmm_matmul, hegmm_matmul_batch*) as a CUDA graph from
+ *     its second call on; 0 launches kernel by kernel.  While per-kernel
+ *     timing is on (hegmm_set_timing) plans always run kernel by kernel. */
+#define HEGMM_TUNE_GRAPHS 5
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in

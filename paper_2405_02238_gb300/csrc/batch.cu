@@ -128,6 +128,11 @@ struct BatchPlan {
     hegmm_opcount cnt{};
     std::vector<void *> allocs;
     unsigned long long last_use = 0;
+    // CUDA graph of the plan's launch sequence, captured on its second run
+    // (the first builds the context's lazily made tables) and replayed after
+    int runs = 0;
+    bool graph_failed = false;
+    cudaGraphExec_t exec = nullptr;
 };
 
 // Device memory of a plan: from the context's arena when one is set (a
@@ -157,6 +162,10 @@ static T *plan_upload(Ctx *c, BatchPlan *P, const std::vector<T> &v) {
 }
 
 static void free_bplan(Ctx *c, BatchPlan *P) {
+    if (P->exec) {
+        cudaStreamSynchronize(c->st);  // no replay of this graph may still be running
+        cudaGraphExecDestroy(P->exec);
+    }
     std::set<ShapeData *> uniq(P->shp.begin(), P->shp.end());
     for (ShapeData *s : uniq) s->refs--;
     for (void *a : P->allocs) dfree(c, a);
@@ -954,17 +963,13 @@ static int moddown_polys(Ctx *c, int lv, u64 *u, const DivDesc *d_div, int npoly
     return divround_ntt(c, *tb, d_div, npoly);
 }
 
-static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm_ct *const *Bc, hegmm_ct **C) {
+// The launch sequence of a plan; the operands come through P->d_inptr and
+// the results' addresses through P->d_final, both uploaded by run_bplan.
+static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
     const int N = c->N, B = P->B, lv0 = P->lv0, lv1 = P->lv1, K = c->K;
     const int dbl = P->dbl, np0 = dbl ? lv0 + K : lv0, np1 = dbl ? lv1 + K : lv1;
     int rc;
     // 1. operands and the hoisted ModUp of every c1
-    std::vector<u64 *> ptrs((size_t)2 * B);
-    for (int p = 0; p < B; p++) {
-        ptrs[2 * p] = A[p]->d;
-        ptrs[2 * p + 1] = Bc[p]->d;
-    }
-    cudaMemcpyAsync(P->d_inptr, ptrs.data(), ptrs.size() * sizeof(u64 *), cudaMemcpyHostToDevice, c->st);
     if ((rc = gather_cts(c, lv0, P->d_inptr, 2 * B, P->in))) return rc;
     if ((rc = modup(c, lv0, 2 * B, P->in + (size_t)lv0 * N, (long long)2 * lv0 * N, P->xc, P->D))) return rc;
     // 2. linear transformations eps^k(A), omega^k(B) of every iteration
@@ -1029,10 +1034,42 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
             if ((rc = ksw_moddown(c, lv1, P->d_erot, P->d_ediv, P->X, P->eu, nullptr))) return rc;
         }
     }
+    return sum_desc(c, lv1, P->d_final, B);
+}
+
+static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm_ct *const *Bc, hegmm_ct **C,
+                     bool graph) {
+    const int B = P->B;
+    int rc;
+    // this call's operands and result addresses
+    std::vector<u64 *> ptrs((size_t)2 * B);
+    for (int p = 0; p < B; p++) {
+        ptrs[2 * p] = A[p]->d;
+        ptrs[2 * p + 1] = Bc[p]->d;
+    }
+    cudaMemcpyAsync(P->d_inptr, ptrs.data(), ptrs.size() * sizeof(u64 *), cudaMemcpyHostToDevice, c->st);
     std::vector<SumDesc> fin = P->final_tmpl;
     for (int p = 0; p < B; p++) fin[p].out = C[p]->d;
     cudaMemcpyAsync(P->d_final, fin.data(), fin.size() * sizeof(SumDesc), cudaMemcpyHostToDevice, c->st);
-    if ((rc = sum_desc(c, lv1, P->d_final, B))) return rc;
+    graph = graph && !c->timing && c->use_graphs && !P->graph_failed && P->runs > 0;
+    if (graph && !P->exec) {
+        // capture once; on any failure the plan keeps running launch by launch
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            rc = run_bplan_kernels(c, P);
+            const cudaError_t e = cudaStreamEndCapture(c->st, &g);
+            if (rc || e != cudaSuccess || !g || cudaGraphInstantiate(&P->exec, g, 0) != cudaSuccess) P->exec = nullptr;
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+        if (!P->exec) P->graph_failed = true;
+    }
+    if (graph && P->exec) {
+        if (cudaGraphLaunch(P->exec, c->st) != cudaSuccess) return cuda_check(c, "graph launch");
+    } else if ((rc = run_bplan_kernels(c, P))) {
+        return rc;
+    }
+    P->runs++;
     // mark the masks of every shape as read on this stream (for eviction)
     std::set<ShapeData *> uniq(P->shp.begin(), P->shp.end());
     for (ShapeData *s : uniq) {
@@ -1125,7 +1162,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
             return set_err(c, HEGMM_ENOMEM, "result ciphertext");
         }
     }
-    int rc = run_bplan(c, P, A, B, C);
+    int rc = run_bplan(c, P, A, B, C, cache);
     if (!rc) rc = cuda_check(c, "matmul");
     if (rc) {
         for (int i = 0; i < count; i++) {
@@ -1196,6 +1233,11 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_GIANT_COST) {
         if (value < 1 || value > 65536) return set_err(c, HEGMM_EINVAL, "giant cost must be in 1..65536");
         c->giant_cost = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_GRAPHS) {
+        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "graphs must be 0 or 1");
+        c->use_graphs = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_FUSED) {

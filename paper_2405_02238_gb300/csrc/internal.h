@@ -186,6 +186,7 @@ struct Ctx {
     int lazy_relin = 0;                        // products: one relinearisation of the summed tensors
     int lt_shared = 0;                         // products: shared baby steps + giant rotations
     int giant_cost = 8;                        // shared baby steps: giant rotation cost in the greedy rule
+    int use_graphs = 1;                        // replay cached plans as CUDA graphs
     int lt_chunk = 32;                         // double mode: entries per k_lt_grp work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
     int lt_kernel = 0;                         // grouped fused kernel variant (resident CTAs per SM)

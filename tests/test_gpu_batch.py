@@ -126,3 +126,26 @@ def test_batch_with_per_product_algorithms(H, medium):
             got = ctx.hegmm_decrypt(outs[i], m, l, n, algs[i]).astype(np.int64)
             assert (got == (A @ B) % W.MEDIUM.t).all()
     ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
+
+
+def test_graph_replay_takes_each_calls_operands(H, medium):
+    # the first call of a cached plan runs launch by launch, the second is
+    # captured as a CUDA graph, later ones replay it: every call must use its
+    # own operands and write its own results
+    ctx = medium
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED)
+    shapes = [(6, 10, 9), (5, 12, 7)]
+    ctx.hegmm_keygen(SEED, shapes)
+    try:
+        for call in range(4):
+            As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=900 + 7 * call, stream0=9000 + 10 * call)
+            outs = ctx.hegmm_matmul_batch(As, Bs, shapes)
+            for i, (m, l, n) in enumerate(shapes):
+                A, B = mats[i]
+                assert (ctx.hegmm_decrypt(outs[i], m, l, n).astype(np.int64) == (A @ B) % W.MEDIUM.t).all(), call
+                ctx.hegmm_set_tuning(H.TUNE_GRAPHS, 0)
+                plain, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n)
+                ctx.hegmm_set_tuning(H.TUNE_GRAPHS, 1)
+                assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(plain)).all(), call
+    finally:
+        ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
