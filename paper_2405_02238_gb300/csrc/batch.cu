@@ -37,6 +37,19 @@
 
 namespace hg {
 
+// A group of linear-transformation outputs (iterations k0 .. k0+nj-1 of one
+// operand) evaluated by the same work items: its entries, each a rotation
+// index (-1: the d = 0 term) with the mask index of every output that uses
+// it (-1: none).
+struct GEnt {
+    int zi;
+    int mask[LT_GROUP];
+};
+struct GroupTmpl {
+    int s, k0, nj, nch;
+    std::vector<GEnt> ents;
+};
+
 struct ShapeData {
     HostPlan hp;
     std::vector<long long> zs[2];
@@ -59,6 +72,12 @@ struct ShapeData {
     // shared baby steps: per operand and iteration the giant rotation (0: none)
     bool shared = false;
     std::vector<int> giant[2];
+    // per operand and rotation index: its Galois element and key
+    std::vector<u32> zgal[2];
+    std::vector<const u64 *> zkey[2];
+    // the grouping of the fused kernel's work, for entries-per-item lt_tc
+    std::vector<GroupTmpl> groups;
+    int groups_tc = -1;
     // masks are kept over all L + K primes (the extended basis of level L)
     const u64 *mask_at(Ctx *c, int mi) const { return masks + (size_t)mi * (c->L + c->K) * c->N; }
 };
@@ -133,6 +152,10 @@ struct BatchPlan {
     int runs = 0;
     bool graph_failed = false;
     cudaGraphExec_t exec = nullptr;
+    // descriptor staging while the plan is built (see plan_upload)
+    char *dblk = nullptr;
+    size_t dblk_cap = 0, dblk_used = 0;
+    std::vector<unsigned char> hblk;
 };
 
 // Device memory of a plan: from the context's arena when one is set (a
@@ -154,10 +177,32 @@ static void *plan_alloc(Ctx *c, BatchPlan *P, size_t bytes) {
     return p;
 }
 
+// Descriptor arrays are staged on the host in blocks of device memory
+// reserved up front, so that a plan's descriptors go to the device in one
+// copy per block (flush_uploads) instead of one per array.
+static int flush_uploads(Ctx *c, BatchPlan *P) {
+    if (P->dblk && P->dblk_used)
+        if (cudaMemcpyAsync(P->dblk, P->hblk.data(), P->dblk_used, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+            return cuda_check(c, "descriptor upload");
+    P->dblk = nullptr;
+    P->dblk_used = P->dblk_cap = 0;
+    return HEGMM_OK;
+}
+
 template <typename T>
 static T *plan_upload(Ctx *c, BatchPlan *P, const std::vector<T> &v) {
-    T *p = (T *)plan_alloc(c, P, v.size() * sizeof(T));
-    if (p && !v.empty()) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->st);
+    const size_t bytes = (std::max<size_t>(v.size() * sizeof(T), 8) + 15) & ~(size_t)15;
+    if (!P->dblk || P->dblk_used + bytes > P->dblk_cap) {
+        if (flush_uploads(c, P)) return nullptr;
+        const size_t cap = std::max<size_t>(bytes, (size_t)1 << 20);
+        P->dblk = (char *)plan_alloc(c, P, cap);
+        if (!P->dblk) return nullptr;
+        P->dblk_cap = cap;
+        P->hblk.resize(cap);
+    }
+    T *p = reinterpret_cast<T *>(P->dblk + P->dblk_used);
+    if (!v.empty()) memcpy(P->hblk.data() + P->dblk_used, v.data(), v.size() * sizeof(T));
+    P->dblk_used += bytes;
     return p;
 }
 
@@ -311,6 +356,12 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
     for (int z : hp.extract)
         if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
     if (!c->keys.count(0)) return fail(HEGMM_ENOKEY, "no relinearisation key");
+    for (int s = 0; s < 2; s++)
+        for (long long z : sd->zs[s]) {
+            const u64 g = galois_of(c, z);
+            sd->zgal[s].push_back((u32)g);
+            sd->zkey[s].push_back(c->keys.at(g));
+        }
     // masks: one per distinct slot set; value = product of the dropped primes mod t
     u64 scale = 1;
     for (int i = 0; i < c->prm.ms_drop; i++) scale = (u64)((unsigned __int128)scale * (c->q[c->L - 1 - i] % c->t) % c->t);
@@ -464,23 +515,15 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     // group cut into several items writes partial sums, added by one sum
     // launch.
     const int TC = std::max(1, c->lt_chunk);
-    struct GEnt {
-        int zi;
-        int mask[LT_GROUP];
-    };
-    struct GGroup {
-        int p, s, k0, nj, nch;
-        size_t part0;
-        std::vector<GEnt> ents;
-    };
     // a group whose outputs share few rotations (entries >= 4/5 of its
-    // terms) is evaluated one output per item instead
-    auto make_group = [&](int p, int s, int k0, int nj) {
-        GGroup g{p, s, k0, nj, 1, 0, {}};
+    // terms) is evaluated one output per item instead; the grouping depends
+    // on the shape and lt_chunk only and is kept with the shape
+    auto make_group = [](const ShapeData *sd, int s, int k0, int nj) {
+        GroupTmpl g{s, k0, nj, 1, {}};
         std::vector<GEnt> made;
         std::map<int, std::vector<int>> byz;  // rotation index (-1: d = 0) -> entries
         for (int j = 0; j < nj; j++)
-            for (const auto &dr : P->shp[p]->dref[s][k0 + j]) {
+            for (const auto &dr : sd->dref[s][k0 + j]) {
                 int idx = -1;
                 for (int x : byz[dr.zi])
                     if (made[x].mask[j] < 0) {
@@ -501,30 +544,45 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             for (int x : kv.second) g.ents.push_back(made[x]);
         return g;
     };
+    struct GGroup {
+        int p;
+        const GroupTmpl *t;
+        size_t part0;
+    };
     std::vector<GGroup> groups;
     size_t npart = 0;
     P->fused = dbl && c->lt_fused && (unsigned __int128)(TC + 2) * c->q[0] < ((unsigned __int128)1 << 64);
     if (P->fused) {
-        for (int p = 0; p < B; p++)
+        for (ShapeData *sd : held) {
+            if (sd->groups_tc == TC) continue;
+            sd->groups.clear();
+            const int ni = (int)sd->hp.iters.size();
             for (int s = 0; s < 2; s++)
-                for (int k0 = 0; k0 < niter[p]; k0 += LT_GROUP) {
-                    const int nj = std::min(LT_GROUP, niter[p] - k0);
-                    std::vector<GGroup> gs{make_group(p, s, k0, nj)};
+                for (int k0 = 0; k0 < ni; k0 += LT_GROUP) {
+                    const int nj = std::min(LT_GROUP, ni - k0);
+                    std::vector<GroupTmpl> gs{make_group(sd, s, k0, nj)};
                     size_t nterms = 0;
-                    for (int j = 0; j < nj; j++) nterms += P->shp[p]->dref[s][k0 + j].size();
+                    for (int j = 0; j < nj; j++) nterms += sd->dref[s][k0 + j].size();
                     if (nj > 1 && 5 * gs[0].ents.size() >= 4 * nterms) {
                         gs.clear();
-                        for (int j = 0; j < nj; j++) gs.push_back(make_group(p, s, k0 + j, 1));
+                        for (int j = 0; j < nj; j++) gs.push_back(make_group(sd, s, k0 + j, 1));
                     }
                     for (auto &g : gs) {
                         g.nch = std::max(1, (int)((g.ents.size() + TC - 1) / TC));
-                        if (g.nch > 1) {
-                            g.part0 = npart;
-                            npart += (size_t)g.nch * g.nj;
-                        }
-                        groups.push_back(std::move(g));
+                        sd->groups.push_back(std::move(g));
                     }
                 }
+            sd->groups_tc = TC;
+        }
+        for (int p = 0; p < B; p++)
+            for (const GroupTmpl &t : P->shp[p]->groups) {
+                GGroup g{p, &t, 0};
+                if (t.nch > 1) {
+                    g.part0 = npart;
+                    npart += (size_t)t.nch * t.nj;
+                }
+                groups.push_back(g);
+            }
     }
     const int fused = P->fused;
     // giant rotations of the shared-baby-step order: (product, operand, iteration, g)
@@ -611,9 +669,12 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
         std::vector<SumDesc> sums;
         const size_t pstride = (size_t)2 * ne0 * N;
         const double limb = (double)N * 8;
-        for (const auto &g : groups) {
-            const ShapeData *sd = P->shp[g.p];
+        for (const auto &gr : groups) {
+            const GroupTmpl &g = *gr.t;
+            const ShapeData *sd = P->shp[gr.p];
             const int kind = g.nj > 1;  // 0: one output per item, 1: several
+            const u64 *ctp = in_ct(gr.p, g.s);
+            const u64 *Dp = P->D + ((size_t)2 * gr.p + g.s) * nd0 * ne0 * N;
             for (int ch = 0; ch < g.nch; ch++) {
                 LtItem it{};
                 it.first = (int)ents.size();
@@ -621,12 +682,11 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                 for (int ei = e0; ei < e1; ei++) {
                     const GEnt &ge = g.ents[ei];
                     LtEntry E{};
-                    E.ct = in_ct(g.p, g.s);
+                    E.ct = ctp;
                     if (ge.zi >= 0) {
-                        const u64 gel = galois_of(c, sd->zs[g.s][ge.zi]);
-                        E.D = P->D + ((size_t)2 * g.p + g.s) * nd0 * ne0 * N;
-                        E.key = c->keys[gel];
-                        E.g = (u32)gel;
+                        E.D = Dp;
+                        E.key = sd->zkey[g.s][ge.zi];
+                        E.g = sd->zgal[g.s][ge.zi];
                         P->lt_bytes[kind] += 2.0 * nd0 * ne0 * limb;  // the key
                     }
                     for (int j = 0; j < g.nj; j++)
@@ -638,16 +698,16 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                 }
                 it.count = (int)ents.size() - it.first;
                 for (int j = 0; j < g.nj; j++)
-                    it.out[j] = g.nch == 1 ? acc_of(g.p, g.s, g.k0 + j)
-                                           : P->part + (g.part0 + (size_t)ch * g.nj + j) * pstride;
+                    it.out[j] = g.nch == 1 ? acc_of(gr.p, g.s, g.k0 + j)
+                                           : P->part + (gr.part0 + (size_t)ch * g.nj + j) * pstride;
                 P->lt_bytes[kind] += g.nj * 2.0 * ne0 * limb;  // the sums written
                 items[kind].push_back(it);
             }
             if (g.nch > 1)
                 for (int j = 0; j < g.nj; j++) {
                     SumDesc sm{};
-                    sm.out = acc_of(g.p, g.s, g.k0 + j);
-                    sm.init = P->part + (g.part0 + j) * pstride;
+                    sm.out = acc_of(gr.p, g.s, g.k0 + j);
+                    sm.init = P->part + (gr.part0 + j) * pstride;
                     sm.items = sm.init + (size_t)g.nj * pstride;
                     sm.stride = (long long)(g.nj * pstride);
                     sm.count = g.nch - 1;
@@ -948,6 +1008,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     P->d_final = (SumDesc *)plan_alloc(c, P, sizeof(SumDesc) * B);
     P->d_inptr = (u64 **)plan_alloc(c, P, sizeof(u64 *) * 2 * B);
     if (!P->d_final || !P->d_inptr) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    if (int e = flush_uploads(c, P)) return fail_rc(e);
+    std::vector<unsigned char>().swap(P->hblk);
     int rc = cuda_check(c, "batch plan");
     if (rc) return fail_rc(rc);
     *out = P;
@@ -1093,10 +1155,25 @@ static void evict_plans(Ctx *c, size_t incoming) {
 size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
     const int a = resolve_alg(m, l, n, alg, c->S);
     if (!a) return 0;
-    HostPlan hp = make_host_plan(m, l, n, a);
+    // iterations and extractions of the shape: from its plan data when
+    // prepared, else from a host plan built once per shape
+    size_t ni, ne;
+    auto sit = c->shapes.find(std::make_tuple(m, l, n, a, c->lt_shared ? c->giant_cost : 0));
+    if (sit != c->shapes.end()) {
+        ni = sit->second->hp.iters.size();
+        ne = sit->second->hp.extract.size();
+    } else {
+        auto key = std::make_tuple(m, l, n, a);
+        auto it = c->shape_counts.find(key);
+        if (it == c->shape_counts.end()) {
+            HostPlan hp = make_host_plan(m, l, n, a);
+            it = c->shape_counts.emplace(key, std::make_pair(hp.iters.size(), hp.extract.size())).first;
+        }
+        ni = it->second.first;
+        ne = it->second.second;
+    }
     const size_t lv0 = c->L, lv1 = c->L - c->prm.ms_drop, ne0 = lv0 + c->K, ne1 = lv1 + c->K;
     const size_t nd0 = c->digits((int)lv0), nd1 = c->digits((int)lv1);
-    const size_t ni = hp.iters.size(), ne = hp.extract.size();
     size_t w = 6 * lv0 + 2 * nd0 * ne0 + ni * 4 * lv0 + (lv1 != lv0 ? ni * 4 * lv1 : 0) + 2 * lv1;
     if (c->ks_double) w += ni * 4 * ne0 + 2 * ne1;
     if (ne) w += lv1 + nd1 * ne1 + ne * (2 * ne1 + 2 * lv1) + (c->ks_double ? 2 * ne1 + 2 * lv1 : 0);

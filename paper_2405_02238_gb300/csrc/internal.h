@@ -180,6 +180,7 @@ struct Ctx {
     int *d_slot_pos0 = nullptr;                  // device copy of slot_pos0
     std::map<std::tuple<int, int, int, int, int>, ShapeData *> shapes;  // per (shape, order): plan + masks
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
+    std::map<std::tuple<int, int, int, int>, std::pair<size_t, size_t>> shape_counts;  // iterations, extractions
     unsigned long long bplan_clock = 0;
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
