@@ -186,6 +186,22 @@ def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2):
     return total, desc
 
 
+def max_over_ranks(ms: float, world: int, dist=None, device="cpu") -> float:
+    """The step time of the job: the slowest rank's (all_reduce MAX)."""
+    if world <= 1:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(products_per_rank: int, world: int, ms: float) -> float:
+    """Matmuls per second over all ranks (replicas: each rank runs its own products)."""
+    return products_per_rank * world / (ms / 1e3)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -339,6 +355,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "serve":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return None  # the serving sweep runs on one GPU: other ranks exit without work
         return run_serve(args)
 
     import torch
@@ -439,18 +457,15 @@ def main():
         ev[k][1].record(stream)
         del outs
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     torch.cuda.profiler.stop()
     wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dist if world > 1 else None, dev)
     per_step = len(prods)
-    value = per_step * world / (ms / 1e3)
+    value = whole_job_value(per_step, world, ms)
     # per-kernel device time: the same steps once more, launched kernel by
     # kernel with CUDA events on the library's stream (the timed steps above
     # replay each plan as one CUDA graph)

@@ -714,6 +714,19 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                     sums.push_back(sm);
                 }
         }
+        // one-output items in the order of their keys: the CTAs resident
+        // together then read the same Galois keys (shared across the
+        // products of a batch) from L2; sums are exact, so order is free
+        std::stable_sort(items[0].begin(), items[0].end(), [&](const LtItem &a, const LtItem &b) {
+            auto key_of = [&](const LtItem &x, int k) -> uintptr_t {
+                int seen = 0;
+                for (int t = x.first; t < x.first + x.count; t++)
+                    if (ents[t].key && seen++ == k) return (uintptr_t)ents[t].key;
+                return 0;
+            };
+            const uintptr_t a0 = key_of(a, 0), b0 = key_of(b, 0);
+            return a0 != b0 ? a0 < b0 : key_of(a, 1) < key_of(b, 1);
+        });
         P->ltsum_n = (int)sums.size();
         P->d_lents = plan_upload(c, P, ents);
         for (int kind = 0; kind < 2; kind++) {
