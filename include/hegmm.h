@@ -195,8 +195,15 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     hegmm_set_budgets' chunk_bytes) and applies the masks after each chunk. */
 #define HEGMM_TUNE_LT_FUSED 2
 /*   HEGMM_TUNE_LT_KERNEL: variant of the fused kernel for items of several
- *     outputs, by resident CTAs per SM (its register cap): 0 = 4 (default,
- *     measured fastest on GB300 at N = 2^13), 1 = 2, 2 = 3. */
+ *     outputs, by resident CTAs per SM (its register cap) and the form of
+ *     its per-output sums (lazy 128-bit, or reduced after every use):
+ *     0 = 4 lazy, 1 = 2 lazy, 2 = 3 lazy, 3 = 4 reduced, 4 = 5 reduced,
+ *     5 = 6 reduced; 6 (default) = key rows and masks staged in shared
+ *     memory by bulk asynchronous copies (TMA engine, double-buffered with
+ *     mbarriers), 2 CTAs per SM, for dnum <= 8 (else variant 0).
+ *   HEGMM_TUNE_LT_STAGED1: with variant 6, 1 stages the items of one output
+ *     the same way (3 CTAs per SM); 0 (default, measured faster at
+ *     N = 2^13) keeps them on plain loads. */
 #define HEGMM_TUNE_LT_KERNEL 3
 /*   HEGMM_TUNE_GIANT_COST: the cost of one giant rotation, in baby key
  *     switches, in the greedy rule of HEGMM_KS_SHARED (1..65536, default 8).
@@ -210,6 +217,7 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     its second call on; 0 launches kernel by kernel.  While per-kernel
  *     timing is on (hegmm_set_timing) plans always run kernel by kernel. */
 #define HEGMM_TUNE_GRAPHS 5
+#define HEGMM_TUNE_LT_STAGED1 6
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in

@@ -1316,13 +1316,18 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_KERNEL) {
-        if (value < 0 || value > 2) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..2");
+        if (value < 0 || value > 6) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..6");
         c->lt_kernel = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_GIANT_COST) {
         if (value < 1 || value > 65536) return set_err(c, HEGMM_EINVAL, "giant cost must be in 1..65536");
         c->giant_cost = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_LT_STAGED1) {
+        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "lt_staged1 must be 0 or 1");
+        c->lt_staged1 = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_GRAPHS) {

@@ -306,6 +306,10 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
     if (cudaMallocAsync(&dm, sizeof(ModDev) * c->nmod, c->st) != cudaSuccess || !c->d_tw)
         return set_err(c, HEGMM_ENOMEM, "tables");
     c->d_mods = (ModDev *)dm;
+    void *de = nullptr;
+    if (cudaMallocAsync(&de, sizeof(int), c->st) != cudaSuccess) return set_err(c, HEGMM_ENOMEM, "error flag");
+    c->d_err = (int *)de;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
     cudaMemcpyAsync(c->d_tw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice, c->st);
     cudaMemcpyAsync(c->d_mods, c->hmod, sizeof(ModDev) * c->nmod, cudaMemcpyHostToDevice, c->st);
     cudaStreamSynchronize(c->st);
@@ -537,9 +541,23 @@ static int decrypt_slots(Ctx *c, const hegmm_ct *ct, std::vector<u64> &slots) {
     cudaMemcpyAsync(ev.data(), m, (size_t)N * 8, cudaMemcpyDeviceToHost, c->st);
     dfree(c, v);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "decrypt");
+    if ((rc = device_status(c))) return rc;
     slots.resize(c->S);
     for (int j = 0; j < c->S; j++) slots[j] = ev[c->slot_pos0[j]];
     return cuda_check(c, "decrypt");
+}
+
+// HEGMM_ETIMEOUT if a kernel's bounded wait ran out since the last check
+// (the flag is cleared); synchronises the stream.
+int device_status(Ctx *c) {
+    if (!c->d_err) return HEGMM_OK;
+    int v = 0;
+    if (cudaMemcpyAsync(&v, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+        cudaStreamSynchronize(c->st) != cudaSuccess)
+        return cuda_check(c, "status");
+    if (!v) return HEGMM_OK;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st);
+    return set_err(c, HEGMM_ETIMEOUT, "a kernel's bounded wait for its staged copies ran out; its results are invalid");
 }
 
 }  // namespace hg
@@ -576,6 +594,7 @@ void hegmm_ctx_destroy(hegmm_ctx *h) {
     dfree(c, c->d_slot_pos0);
     dfree(c, c->d_tw);
     dfree(c, c->d_mods);
+    dfree(c, c->d_err);
     cudaStreamSynchronize(c->st);
     for (auto &p : c->pending) {
         cudaEventDestroy(p.a);
@@ -734,7 +753,7 @@ int hegmm_ct_import(hegmm_ctx *h, const uint64_t *host, int level, hegmm_ct **ou
 int hegmm_sync(hegmm_ctx *h) {
     if (!h) return HEGMM_EINVAL;
     if (cudaStreamSynchronize(h->c.st) != cudaSuccess) return cuda_check(&h->c, "sync");
-    return HEGMM_OK;
+    return device_status(&h->c);
 }
 
 void hegmm_pt_destroy(hegmm_pt *pt) {

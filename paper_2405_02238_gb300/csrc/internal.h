@@ -188,9 +188,11 @@ struct Ctx {
     int lt_shared = 0;                         // products: shared baby steps + giant rotations
     int giant_cost = 8;                        // shared baby steps: giant rotation cost in the greedy rule
     int use_graphs = 1;                        // replay cached plans as CUDA graphs
+    int *d_err = nullptr;                      // set by a kernel whose bounded wait ran out
     int lt_chunk = 32;                         // double mode: entries per k_lt_grp work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
-    int lt_kernel = 0;                         // grouped fused kernel variant (resident CTAs per SM)
+    int lt_kernel = 6;                         // grouped fused kernel variant (6: operands staged by TMA)
+    int lt_staged1 = 0;                        // one-output items staged by TMA as well (measured slower)
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
@@ -349,6 +351,7 @@ void free_plans(Ctx *c);
 hegmm_ct *new_ct(Ctx *c, int level);
 u64 galois_of(Ctx *c, long long z);
 int ensure_galois_key(Ctx *c, u64 g);
+int device_status(Ctx *c);
 
 }  // namespace hg
 

@@ -253,6 +253,8 @@ static int set_smem_attrs() {
     return 0;
 }
 
+static int init_staged_kernels();
+
 int init_kernels(Ctx *c) {
     int bad = 0;
     switch (c->logN) {
@@ -264,6 +266,7 @@ int init_kernels(Ctx *c) {
         default: return set_err(c, HEGMM_EINVAL, "unsupported ring degree");
     }
     if (bad) return cuda_check(c, "ntt shared-memory attribute");
+    if (init_staged_kernels()) return cuda_check(c, "staged kernel shared-memory attribute");
     return HEGMM_OK;
 }
 
@@ -469,7 +472,9 @@ int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
 //   u_1 = <tau_g(D), k_1>;  d = 0 entries: u = P ct (0 on special primes).
 // grid (N / 256, items, limbs): the CTAs resident together cover many items
 // of one limb.
-template <int G, int MINB>
+// RED: the output sums are kept reduced (one Montgomery product and a modular
+// add per use: half the registers of the lazy 128-bit sums).
+template <int G, int MINB, bool RED>
 __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, int np, int L, int logN,
                                                    const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
                                                    const LtItem *__restrict__ items) {
@@ -481,9 +486,12 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
     const int gm = e < lv ? e : L + (e - lv);
     const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
     const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
-    Acc s0[G], s1[G];
+    Acc s0[RED ? 1 : G], s1[RED ? 1 : G];
+    u64 r0[RED ? G : 1], r1[RED ? G : 1];
 #pragma unroll
-    for (int j = 0; j < G; j++) s0[j] = s1[j] = Acc{0, 0};
+    for (int j = 0; j < (RED ? 1 : G); j++) s0[j] = s1[j] = Acc{0, 0};
+#pragma unroll
+    for (int j = 0; j < (RED ? G : 1); j++) r0[j] = r1[j] = 0;
     const int t0 = it->first, t1 = t0 + it->count;
     for (int t = t0; t < t1; t++) {
         const LtEntry *E = ents + t;
@@ -524,9 +532,158 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
 #pragma unroll
         for (int j = 0; j < G; j++)
             if (used & (1u << j)) {
-                mac(s0[j], u0, mv[j]);
-                mac(s1[j], u1, mv[j]);
+                if constexpr (RED) {
+                    r0[j] = addm(r0[j], montmul(u0, mv[j], q, qinv), q);
+                    r1[j] = addm(r1[j], montmul(u1, mv[j], q, qinv), q);
+                } else {
+                    mac(s0[j], u0, mv[j]);
+                    mac(s1[j], u1, mv[j]);
+                }
             }
+    }
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        u64 *o = it->out[j];
+        if (o) {
+            if constexpr (RED) {
+                o[(size_t)e * N + c] = r0[j];
+                o[((size_t)ne + e) * N + c] = r1[j];
+            } else {
+                o[(size_t)e * N + c] = montred(s0[j], q, qinv);
+                o[((size_t)ne + e) * N + c] = montred(s1[j], q, qinv);
+            }
+        }
+    }
+}
+
+
+// The 8-output kernel with its streamed operands staged by the TMA engine:
+// one CTA per (256 coefficients, item, limb); thread 0 issues, for entry
+// t + 1, bulk copies of the key rows (2 nd rows of 2 KB) and of every used
+// mask row into the other half of a double buffer in shared memory while
+// the CTA works on entry t; the permuted digit gathers stay plain loads,
+// issued before the wait.  Every wait is bounded: on a timeout (voted over
+// the CTA) the kernel sets *err, waits (bounded) for its copies in flight
+// and leaves its outputs unwritten.
+constexpr int TMA_MAX_ND = 8;
+constexpr int TMA_SPIN = 1 << 22;
+__device__ __forceinline__ size_t tma_stage_words(int nd, int G) { return (size_t)(2 * nd + G) * 256; }
+
+template <int G, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd, int np, int L, int logN,
+                                                     const ModDev *__restrict__ mods,
+                                                     const LtEntry *__restrict__ ents,
+                                                     const LtItem *__restrict__ items, int *err) {
+    extern __shared__ __align__(128) u64 tsm[];
+    const int N = 1 << logN;
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * 256, c = c0 + tid;  // N is a multiple of 256
+    const int e = blockIdx.z;
+    const LtItem *it = items + blockIdx.y;
+    const int gm = e < lv ? e : L + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c0;
+    const size_t sw = tma_stage_words(nd, G);
+    u64 *bar = tsm + 2 * sw;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int t0 = it->first, n = it->count;
+    // producer: the copies of entry t into stage s (thread 0 only)
+    auto issue = [&](int t, int s) {
+        const LtEntry *E = ents + t;
+        u64 *st = tsm + s * sw;
+        const bool live = E->key || e < lv;
+        u32 bytes = 0;
+        if (live) {
+            if (E->key) bytes += 2u * nd * 2048u;
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (E->mask[j]) bytes += 2048u;
+        }
+        mbar_arrive_expect_tx(&bar[s], bytes);
+        if (!live) return;
+        if (E->key)
+            for (int r = 0; r < 2 * nd; r++) bulk_g2s(st + (size_t)r * 256, E->key + (size_t)r * kstep + moff, 2048u, &bar[s]);
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (E->mask[j]) bulk_g2s(st + (size_t)(2 * nd + j) * 256, E->mask[j] + moff, 2048u, &bar[s]);
+    };
+    Acc s0[G], s1[G];
+#pragma unroll
+    for (int j = 0; j < G; j++) s0[j] = s1[j] = Acc{0, 0};
+    u32 ph[2] = {0u, 0u};
+    if (tid == 0 && n > 0) issue(t0, 0);
+    bool bad = false;
+    int i = 0;
+    for (; i < n; i++) {
+        const int s = i & 1;
+        if (tid == 0 && i + 1 < n) {
+            fence_proxy_async();  // the stage was read through the generic proxy
+            issue(t0 + i + 1, s ^ 1);
+        }
+        const LtEntry *E = ents + t0 + i;
+        const u64 *key = E->key;
+        const bool live = key || e < lv;
+        // the permuted gathers first: they overlap the bulk copies
+        u64 xd[TMA_MAX_ND], x0 = 0, x1 = 0;
+        if (key) {
+            const u32 src = auto_src((u32)c, E->g, logN);
+            const u64 *Dp = E->D + (size_t)e * N + src;
+#pragma unroll
+            for (int j = 0; j < TMA_MAX_ND; j++)
+                if (j < nd) xd[j] = __ldg(Dp + (size_t)j * dstep);
+            if (e < lv) x0 = __ldg(E->ct + (size_t)e * N + src);
+        } else if (e < lv) {
+            x0 = __ldg(E->ct + (size_t)e * N + c);
+            x1 = __ldg(E->ct + ((size_t)lv + e) * N + c);
+        }
+        const bool ok = mbar_wait_bounded(&bar[s], ph[s], TMA_SPIN);
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+        }
+        ph[s] ^= 1u;
+        if (live) {
+            const u64 *st = tsm + s * sw;
+            u64 u0, u1;
+            if (key) {
+                Acc a0{0, 0}, a1{0, 0};
+                if (e < lv) mac(a0, x0, pR);
+#pragma unroll
+                for (int j = 0; j < TMA_MAX_ND; j++)
+                    if (j < nd) {
+                        mac(a0, xd[j], st[(size_t)(2 * j) * 256 + tid]);
+                        mac(a1, xd[j], st[(size_t)(2 * j + 1) * 256 + tid]);
+                    }
+                u0 = montred(a0, q, qinv);
+                u1 = montred(a1, q, qinv);
+            } else {
+                u0 = montmul(x0, pR, q, qinv);
+                u1 = montmul(x1, pR, q, qinv);
+            }
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (E->mask[j]) {
+                    const u64 m = st[(size_t)(2 * nd + j) * 256 + tid];
+                    mac(s0[j], u0, m);
+                    mac(s1[j], u1, m);
+                }
+        }
+        __syncthreads();  // the stage is read before it is filled again
+    }
+    if (bad) {
+        if (tid == 0) atomicExch(err, 1);
+        // the copies of entry i + 1 may still be in flight into the other stage
+        if (i + 1 < n) {
+            const int s = (i + 1) & 1;
+            const bool ok = mbar_wait_bounded(&bar[s], ph[s], TMA_SPIN);
+            __syncthreads_or(!ok);
+        }
+        return;
     }
 #pragma unroll
     for (int j = 0; j < G; j++) {
@@ -538,6 +695,14 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
     }
 }
 
+static int init_staged_kernels() {
+    const int smem8 = (int)((2 * (size_t)(2 * TMA_MAX_ND + LT_GROUP) * 256 + 2) * 8);
+    const int smem1 = (int)((2 * (size_t)(2 * TMA_MAX_ND + 1) * 256 + 2) * 8);
+    return cudaFuncSetAttribute(k_lt_grp_tma<LT_GROUP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem8) !=
+               cudaSuccess ||
+           cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess;
+}
+
 int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes) {
     if (nitems <= 0) return HEGMM_OK;
     const int ne = lv + c->K, nd = c->digits(lv);
@@ -545,21 +710,34 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
     for (int i0 = 0; i0 < nitems; i0 += kMaxGridZ) {
         const dim3 grid((unsigned)((c->N + 255) / 256), (unsigned)std::min(kMaxGridZ, nitems - i0), (unsigned)ne);
         const LtItem *it = d_items + i0;
-        if (group == 1) {  // items of one output: few registers, six CTAs per SM
-            k_lt_grp<1, 6><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+#define HG_LTG(G, MB, RED) \
+    k_lt_grp<G, MB, RED><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it)
+        const bool staged = c->lt_kernel == 6 && nd <= TMA_MAX_ND;
+        if (group == 1) {  // items of one output
+            if (staged && c->lt_staged1) {
+                const size_t smem = (2 * (size_t)(2 * nd + 1) * 256 + 2) * 8;
+                k_lt_grp_tma<1, 3><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it,
+                                                               c->d_err);
+            } else {
+                HG_LTG(1, 6, false);  // few registers, six CTAs per SM
+            }
+            continue;
+        }
+        if (staged) {
+            const size_t smem = (2 * (size_t)(2 * nd + LT_GROUP) * 256 + 2) * 8;
+            k_lt_grp_tma<LT_GROUP, 2><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents,
+                                                                 it, c->d_err);
             continue;
         }
         switch (c->lt_kernel) {
-            case 1:
-                k_lt_grp<LT_GROUP, 2><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
-                break;
-            case 2:
-                k_lt_grp<LT_GROUP, 3><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
-                break;
-            default:
-                k_lt_grp<LT_GROUP, 4><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
-                break;
+            case 1: HG_LTG(LT_GROUP, 2, false); break;
+            case 2: HG_LTG(LT_GROUP, 3, false); break;
+            case 3: HG_LTG(LT_GROUP, 4, true); break;
+            case 4: HG_LTG(LT_GROUP, 5, true); break;
+            case 5: HG_LTG(LT_GROUP, 6, true); break;
+            default: HG_LTG(LT_GROUP, 4, false); break;
         }
+#undef HG_LTG
     }
     return cuda_check(c, "lt_group");
 }

@@ -165,7 +165,8 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
     run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE, mode=mode)
 
 
-@pytest.mark.parametrize("chunk,variant,fused", [(1, 0, 1), (3, 1, 1), (4096, 2, 1), (32, 0, 0)])
+@pytest.mark.parametrize("chunk,variant,fused", [(1, 0, 1), (3, 1, 1), (4096, 2, 1), (32, 3, 1), (5, 4, 1), (32, 5, 1),
+                                                  (32, 6, 1), (3, 6, 1), (32, 0, 0)])
 def test_double_mode_executor_settings(H, chunk, variant, fused):
     # work-item size, fused-kernel variant and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
@@ -179,7 +180,7 @@ def test_double_mode_executor_settings(H, chunk, variant, fused):
         run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double+lazy+shared", seed=5)
     finally:
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
-        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 0)
+        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 6)
         ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, 1)
 
 
