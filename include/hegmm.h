@@ -200,7 +200,9 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     0 = 4 lazy, 1 = 2 lazy, 2 = 3 lazy, 3 = 4 reduced, 4 = 5 reduced,
  *     5 = 6 reduced; 6 (default) = key rows and masks staged in shared
  *     memory by bulk asynchronous copies (TMA engine, double-buffered with
- *     mbarriers), 2 CTAs per SM, for dnum <= 8 (else variant 0).
+ *     mbarriers), 2 CTAs per SM, for dnum <= 8 (else variant 0); 7 = the
+ *     same with a producer warp and full / empty mbarriers over 3 stages
+ *     instead of a block barrier per entry.
  *   HEGMM_TUNE_LT_STAGED1: with variant 6, 1 stages the items of one output
  *     the same way (3 CTAs per SM); 0 (default, measured faster at
  *     N = 2^13) keeps them on plain loads. */

@@ -1316,7 +1316,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_KERNEL) {
-        if (value < 0 || value > 6) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..6");
+        if (value < 0 || value > 7) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..7");
         c->lt_kernel = (int)value;
         return HEGMM_OK;
     }

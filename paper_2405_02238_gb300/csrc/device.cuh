@@ -119,6 +119,9 @@ __device__ __forceinline__ bool mbar_try_wait(u64 *bar, u32 parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(u64 *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 // Bounded wait for the phase of the given parity: false if it did not
 // complete within the limit.
 __device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity, int limit) {

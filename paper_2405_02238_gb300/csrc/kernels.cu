@@ -75,12 +75,17 @@ struct NttCfg {
     static constexpr size_t SMEM = (size_t)(N + N / 16) * 8;
 };
 
+// Register passes of radix 2^PR (PR = NTT_PASS_BITS stages per shared-memory
+// round trip), then one remainder pass.
+#ifndef NTT_PASS_BITS
+#define NTT_PASS_BITS 3
+#endif
 template <int LOGN>
 __device__ __forceinline__ void fwd_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, REM = LOGN % 3;
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, PR = NTT_PASS_BITS, REM = LOGN % PR;
 #pragma unroll
-    for (int s0 = 0; s0 + 3 <= LOGN; s0 += 3) {
-        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_fwd_group_lazy<3>(sm, g, s0, LOGN, T, q);
+    for (int s0 = 0; s0 + PR <= LOGN; s0 += PR) {
+        for (int g = threadIdx.x; g < (N >> PR); g += NT) ntt_fwd_group_lazy<PR>(sm, g, s0, LOGN, T, q);
         __syncthreads();
     }
     if constexpr (REM != 0) {
@@ -91,10 +96,10 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const TwPair *__restrict__ T
 
 template <int LOGN>
 __device__ __forceinline__ void inv_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, REM = LOGN % 3;
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, PR = NTT_PASS_BITS, REM = LOGN % PR;
 #pragma unroll
-    for (int u0 = 0; u0 + 3 <= LOGN; u0 += 3) {
-        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, u0, LOGN, T, q);
+    for (int u0 = 0; u0 + PR <= LOGN; u0 += PR) {
+        for (int g = threadIdx.x; g < (N >> PR); g += NT) ntt_inv_group_lazy<PR>(sm, g, u0, LOGN, T, q);
         __syncthreads();
     }
     if constexpr (REM != 0) {
@@ -695,11 +700,153 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
     }
 }
 
+// Warp-specialised form of k_lt_grp_tma: warp 8 (lane 0) produces, the 8
+// consumer warps compute.  S stages; full[s] completes when the copies of
+// the entry in stage s have landed (one arrival with the transaction bytes),
+// empty[s] when all 8 consumer warps have read it (one arrival per warp), so
+// no block-wide barrier is taken per entry.  Every wait is bounded; a
+// timeout anywhere sets *err, the producer then waits (bounded) for the
+// copies it issued, and no output is written.
+template <int G, int S>
+__global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, int np, int L, int logN,
+                                                    const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
+                                                    const LtItem *__restrict__ items, int *err) {
+    extern __shared__ __align__(128) u64 tsm[];
+    const int N = 1 << logN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = blockIdx.x * 256, c = c0 + tid;  // consumers: tid < 256
+    const int e = blockIdx.z;
+    const LtItem *it = items + blockIdx.y;
+    const int gm = e < lv ? e : L + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c0;
+    const size_t sw = tma_stage_words(nd, G);
+    u64 *full = tsm + S * sw, *empty = full + S;
+    if (tid == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 8);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int t0 = it->first, n = it->count;
+    bool bad = false;
+    Acc s0[G], s1[G];
+#pragma unroll
+    for (int j = 0; j < G; j++) s0[j] = s1[j] = Acc{0, 0};
+    if (warp == 8) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int i = 0; i < n; i++) {
+                const int s = i % S;
+                if (i >= S && !mbar_wait_bounded(&empty[s], (u32)((i / S - 1) & 1), TMA_SPIN)) {
+                    bad = true;
+                    break;
+                }
+                const LtEntry *E = ents + t0 + i;
+                u64 *st = tsm + s * sw;
+                const bool live = E->key || e < lv;
+                u32 bytes = 0;
+                if (live) {
+                    if (E->key) bytes += 2u * nd * 2048u;
+#pragma unroll
+                    for (int j = 0; j < G; j++)
+                        if (E->mask[j]) bytes += 2048u;
+                }
+                fence_proxy_async();
+                mbar_arrive_expect_tx(&full[s], bytes);
+                if (live) {
+                    if (E->key)
+                        for (int r = 0; r < 2 * nd; r++)
+                            bulk_g2s(st + (size_t)r * 256, E->key + (size_t)r * kstep + moff, 2048u, &full[s]);
+#pragma unroll
+                    for (int j = 0; j < G; j++)
+                        if (E->mask[j]) bulk_g2s(st + (size_t)(2 * nd + j) * 256, E->mask[j] + moff, 2048u, &full[s]);
+                }
+                issued = i + 1;
+            }
+            // every issued copy lands before the CTA can leave
+            for (int i = issued - S > 0 ? issued - S : 0; i < issued; i++)
+                if (!mbar_wait_bounded(&full[i % S], (u32)((i / S) & 1), TMA_SPIN)) bad = true;
+        }
+    } else {
+        for (int i = 0; i < n; i++) {
+            const int s = i % S;
+            const LtEntry *E = ents + t0 + i;
+            const u64 *key = E->key;
+            const bool live = key || e < lv;
+            u64 xd[TMA_MAX_ND], x0 = 0, x1 = 0;
+            if (key) {
+                const u32 src = auto_src((u32)c, E->g, logN);
+                const u64 *Dp = E->D + (size_t)e * N + src;
+#pragma unroll
+                for (int j = 0; j < TMA_MAX_ND; j++)
+                    if (j < nd) xd[j] = __ldg(Dp + (size_t)j * dstep);
+                if (e < lv) x0 = __ldg(E->ct + (size_t)e * N + src);
+            } else if (e < lv) {
+                x0 = __ldg(E->ct + (size_t)e * N + c);
+                x1 = __ldg(E->ct + ((size_t)lv + e) * N + c);
+            }
+            if (!mbar_wait_bounded(&full[s], (u32)((i / S) & 1), TMA_SPIN)) {
+                bad = true;
+                break;
+            }
+            if (live) {
+                const u64 *st = tsm + s * sw;
+                u64 u0, u1;
+                if (key) {
+                    Acc a0{0, 0}, a1{0, 0};
+                    if (e < lv) mac(a0, x0, pR);
+#pragma unroll
+                    for (int j = 0; j < TMA_MAX_ND; j++)
+                        if (j < nd) {
+                            mac(a0, xd[j], st[(size_t)(2 * j) * 256 + tid]);
+                            mac(a1, xd[j], st[(size_t)(2 * j + 1) * 256 + tid]);
+                        }
+                    u0 = montred(a0, q, qinv);
+                    u1 = montred(a1, q, qinv);
+                } else {
+                    u0 = montmul(x0, pR, q, qinv);
+                    u1 = montmul(x1, pR, q, qinv);
+                }
+#pragma unroll
+                for (int j = 0; j < G; j++)
+                    if (E->mask[j]) {
+                        const u64 m = st[(size_t)(2 * nd + j) * 256 + tid];
+                        mac(s0[j], u0, m);
+                        mac(s1[j], u1, m);
+                    }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    if (warp == 8) return;
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        u64 *o = it->out[j];
+        if (o) {
+            o[(size_t)e * N + c] = montred(s0[j], q, qinv);
+            o[((size_t)ne + e) * N + c] = montred(s1[j], q, qinv);
+        }
+    }
+}
+
+constexpr int WS_STAGES = 3;
+
 static int init_staged_kernels() {
     const int smem8 = (int)((2 * (size_t)(2 * TMA_MAX_ND + LT_GROUP) * 256 + 2) * 8);
     const int smem1 = (int)((2 * (size_t)(2 * TMA_MAX_ND + 1) * 256 + 2) * 8);
+    const int smemw = (int)((WS_STAGES * (size_t)(2 * TMA_MAX_ND + LT_GROUP) * 256 + 2 * WS_STAGES) * 8);
     return cudaFuncSetAttribute(k_lt_grp_tma<LT_GROUP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem8) !=
                cudaSuccess ||
+           cudaFuncSetAttribute(k_lt_grp_ws<LT_GROUP, WS_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smemw) != cudaSuccess ||
            cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess;
 }
 
@@ -712,7 +859,7 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
         const LtItem *it = d_items + i0;
 #define HG_LTG(G, MB, RED) \
     k_lt_grp<G, MB, RED><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it)
-        const bool staged = c->lt_kernel == 6 && nd <= TMA_MAX_ND;
+        const bool staged = (c->lt_kernel == 6 || c->lt_kernel == 7) && nd <= TMA_MAX_ND;
         if (group == 1) {  // items of one output
             if (staged && c->lt_staged1) {
                 const size_t smem = (2 * (size_t)(2 * nd + 1) * 256 + 2) * 8;
@@ -721,6 +868,12 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }
+            continue;
+        }
+        if (staged && c->lt_kernel == 7) {
+            const size_t smem = (WS_STAGES * (size_t)(2 * nd + LT_GROUP) * 256 + 2 * WS_STAGES) * 8;
+            k_lt_grp_ws<LT_GROUP, WS_STAGES><<<grid, 288, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods,
+                                                                        d_ents, it, c->d_err);
             continue;
         }
         if (staged) {

@@ -166,7 +166,7 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
 
 
 @pytest.mark.parametrize("chunk,variant,fused", [(1, 0, 1), (3, 1, 1), (4096, 2, 1), (32, 3, 1), (5, 4, 1), (32, 5, 1),
-                                                  (32, 6, 1), (3, 6, 1), (32, 0, 0)])
+                                                  (32, 6, 1), (3, 6, 1), (32, 7, 1), (2, 7, 1), (32, 0, 0)])
 def test_double_mode_executor_settings(H, chunk, variant, fused):
     # work-item size, fused-kernel variant and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
