@@ -510,12 +510,13 @@ def main():
     host_out = [torch.empty((2, lv1, ctx.N), dtype=torch.uint64).pin_memory() for _ in prods]
     h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in)
     d2h = sum(o.numel() * 8 for o in host_out)
+    host_flat = [t.numpy() for ab in host_in for t in ab]
+    host_out_np = [o.numpy() for o in host_out]
 
     def e2e_step():
-        ins = [(ctx.hegmm_ct_import(ha.numpy()), ctx.hegmm_ct_import(hb.numpy())) for ha, hb in host_in]
-        res = ctx.hegmm_matmul_batch_algs([a for a, _ in ins], [b for _, b in ins], [p[:3] for p in prods], algs)
-        for i, c in enumerate(res):
-            ctx.hegmm_ct_export(c, host_out[i].numpy())
+        cts = ctx.hegmm_ct_import_batch(host_flat)
+        res = ctx.hegmm_matmul_batch_algs(cts[0::2], cts[1::2], [p[:3] for p in prods], algs)
+        ctx.hegmm_ct_export_batch(res, host_out_np)
 
     e2e_step()
     torch.cuda.synchronize()

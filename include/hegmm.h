@@ -327,6 +327,13 @@ int hegmm_ct_level(const hegmm_ct *ct);
  * host layout [2][level][N].  Export synchronises the stream. */
 int hegmm_ct_export(hegmm_ctx *ctx, const hegmm_ct *ct, uint64_t *host);
 int hegmm_ct_import(hegmm_ctx *ctx, const uint64_t *host, int level, hegmm_ct **out);
+/* The same for count ciphertexts at once: one transform launch for all of
+ * them (and, for export, one synchronisation).  host[i] is a caller-owned
+ * [2][level][N] buffer (pinned host memory makes the copies asynchronous
+ * DMA); export needs every ciphertext at the same level.  Import returns
+ * new ciphertexts in out[i] (all NULL on error). */
+int hegmm_ct_import_batch(hegmm_ctx *ctx, int count, const uint64_t *const *host, int level, hegmm_ct **out);
+int hegmm_ct_export_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *cts, uint64_t *const *host);
 
 /* Waits for all work queued on the context's stream. */
 int hegmm_sync(hegmm_ctx *ctx);

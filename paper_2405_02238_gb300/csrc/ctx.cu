@@ -750,6 +750,73 @@ int hegmm_ct_import(hegmm_ctx *h, const uint64_t *host, int level, hegmm_ct **ou
     return HEGMM_OK;
 }
 
+// count ciphertexts' 2*level limbs as one limb pattern through a device
+// array of their addresses (ptrs: count pointers on the device)
+static LimbPat pat_cts(Ctx *c, u64 *const *ptrs, int count, int level) {
+    LimbPat p{};
+    p.base = nullptr;
+    p.outer_ptrs = ptrs;
+    p.outer_stride = 0;
+    p.inner = 2 * level;
+    p.count = 2 * level * count;
+    for (int k = 0; k < 2 * level; k++) {
+        p.off[k] = (unsigned short)k;
+        p.mod[k] = (unsigned char)(k % level);
+    }
+    (void)c;
+    return p;
+}
+
+int hegmm_ct_import_batch(hegmm_ctx *h, int count, const uint64_t *const *host, int level, hegmm_ct **out) {
+    if (!h || count < 0 || (count && (!host || !out)) || level < 1 || level > h->c.L) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (2 * level > PAT_MAX) return set_err(c, HEGMM_EINVAL, "import_batch: level too large");
+    for (int i = 0; i < count; i++) out[i] = nullptr;
+    if (!count) return HEGMM_OK;
+    std::vector<u64 *> ptrs((size_t)count);
+    const size_t bytes = (size_t)2 * level * c->N * 8;
+    for (int i = 0; i < count; i++) {
+        if (!host[i]) return set_err(c, HEGMM_EINVAL, "import_batch: null host buffer");
+        out[i] = new_ct(c, level);
+        if (!out[i]) {
+            for (int j = 0; j < i; j++) {
+                hegmm_ct_destroy(out[j]);
+                out[j] = nullptr;
+            }
+            return set_err(c, HEGMM_ENOMEM, "import_batch");
+        }
+        ptrs[i] = out[i]->d;
+        cudaMemcpyAsync(out[i]->d, host[i], bytes, cudaMemcpyHostToDevice, c->st);
+    }
+    u64 **d_ptrs = upload(c, ptrs);
+    if (!d_ptrs) return set_err(c, HEGMM_ENOMEM, "import_batch");
+    int rc = ntt_fwd(c, pat_cts(c, d_ptrs, count, level));
+    dfree(c, d_ptrs);
+    if (rc) return rc;
+    return cuda_check(c, "import_batch");
+}
+
+int hegmm_ct_export_batch(hegmm_ctx *h, int count, const hegmm_ct *const *cts, uint64_t *const *host) {
+    if (!h || count < 0 || (count && (!cts || !host))) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (!count) return HEGMM_OK;
+    const int level = cts[0] ? cts[0]->level : 0;
+    for (int i = 0; i < count; i++)
+        if (!cts[i] || !host[i] || cts[i]->level != level) return set_err(c, HEGMM_EINVAL, "export_batch: arguments");
+    const size_t w = (size_t)2 * level * c->N;
+    u64 *tmp = dalloc(c, w * count);
+    if (!tmp) return set_err(c, HEGMM_ENOMEM, "export_batch");
+    for (int i = 0; i < count; i++)
+        cudaMemcpyAsync(tmp + (size_t)i * w, cts[i]->d, w * 8, cudaMemcpyDeviceToDevice, c->st);
+    int rc = ntt_inv(c, pat_ct(c, tmp, 2 * count, level));
+    if (rc) return rc;
+    for (int i = 0; i < count; i++)
+        cudaMemcpyAsync(host[i], tmp + (size_t)i * w, w * 8, cudaMemcpyDeviceToHost, c->st);
+    dfree(c, tmp);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "export_batch");
+    return device_status(c);
+}
+
 int hegmm_sync(hegmm_ctx *h) {
     if (!h) return HEGMM_EINVAL;
     if (cudaStreamSynchronize(h->c.st) != cudaSuccess) return cuda_check(&h->c, "sync");

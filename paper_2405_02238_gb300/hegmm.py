@@ -99,6 +99,8 @@ _SIGS = {
     "hegmm_ct_level": (ctypes.c_int, [vp]),
     "hegmm_ct_export": (ctypes.c_int, [vp, vp, u64p]),
     "hegmm_ct_import": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_ct_import_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(u64p), ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_ct_export_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(u64p)]),
     "hegmm_sync": (ctypes.c_int, [vp]),
     "hegmm_pt_destroy": (None, [vp]),
     "hegmm_ct_destroy": (None, [vp]),
@@ -384,6 +386,29 @@ class Context:
         out = vp()
         self._check(self.lib.hegmm_ct_import(self.h, _ptr(a), lv, ctypes.byref(out)), "ct_import")
         return Ciphertext(self, out)
+
+    def hegmm_ct_import_batch(self, hosts) -> List["Ciphertext"]:
+        """hosts: [2][level][N] uint64 arrays (the same level); one transform launch."""
+        arrs = [_u64(h) for h in hosts]
+        n = len(arrs)
+        if n == 0:
+            return []
+        lv = arrs[0].shape[1]
+        ptrs = (u64p * n)(*[_ptr(a) for a in arrs])
+        outs = (vp * n)()
+        self._check(self.lib.hegmm_ct_import_batch(self.h, n, ptrs, lv, outs), "ct_import_batch")
+        return [Ciphertext(self, vp(outs[i])) for i in range(n)]
+
+    def hegmm_ct_export_batch(self, cts, outs) -> None:
+        """Writes each ciphertext into the matching [2][level][N] uint64 array; one synchronisation."""
+        n = len(cts)
+        if n == 0:
+            return
+        for o in outs:
+            assert o.dtype == np.uint64 and o.flags["C_CONTIGUOUS"]
+        pc = (vp * n)(*[c.h for c in cts])
+        po = (u64p * n)(*[_ptr(o) for o in outs])
+        self._check(self.lib.hegmm_ct_export_batch(self.h, n, pc, po), "ct_export_batch")
 
     def hegmm_sync(self):
         self._check(self.lib.hegmm_sync(self.h), "sync")

@@ -280,3 +280,19 @@ def test_errors(H):
     with pytest.raises(H.HegmmError) as e:
         ctx.hegmm_matmul(ms, cb, 4, 8, 6)
     assert e.value.code == -1
+
+
+def test_batched_import_export_equal_single(H):
+    pre, ctx, o = get_pair(H, "medium")
+    rng = np.random.default_rng(61)
+    cts = [enc_pair(ctx, o, rand_slots(o, 70 + i), 31, 200 + i)[0] for i in range(5)]
+    hosts = [ctx.hegmm_ct_export(ct) for ct in cts]
+    back = ctx.hegmm_ct_import_batch(hosts)
+    outs = [np.zeros_like(h) for h in hosts]
+    ctx.hegmm_ct_export_batch(back, outs)
+    for h, b, out in zip(hosts, back, outs):
+        assert (out == h).all()
+        assert (ctx.hegmm_ct_export(b) == h).all()
+        single = ctx.hegmm_ct_import(h)
+        assert (ctx.hegmm_ct_export(single) == h).all()
+    assert rng is not None
