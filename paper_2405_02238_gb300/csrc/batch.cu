@@ -692,6 +692,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                     for (int j = 0; j < g.nj; j++)
                         if (ge.mask[j] >= 0) {
                             E.mask[j] = sd->mask_at(c, ge.mask[j]);
+                            E.used |= 1u << j;
                             P->lt_bytes[kind] += ne0 * limb;  // the mask
                         }
                     ents.push_back(E);

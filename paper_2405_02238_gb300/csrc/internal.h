@@ -84,7 +84,7 @@ struct LtEntry {
     const u64 *key;              // Galois key [nd][2][L+K][N], Montgomery NTT; null: the d = 0 term
     const u64 *ct;               // the source ciphertext [2][lv][N] (NTT)
     u32 g;
-    u32 pad;
+    u32 used;                    // bit j set: mask[j] != null
     const u64 *mask[LT_GROUP];   // [L + K][N] Montgomery NTT per output of the item, or null
 };
 struct LtItem {

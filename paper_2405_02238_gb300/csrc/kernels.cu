@@ -505,16 +505,9 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
         // the masks are loaded with the key and digits, so that one memory
         // latency covers the whole entry
         u64 mv[G];
-        unsigned used = 0;
+        const unsigned used = E->used;
 #pragma unroll
-        for (int j = 0; j < G; j++) {
-            const u64 *mp = E->mask[j];
-            mv[j] = 0;
-            if (mp) {
-                mv[j] = __ldg(mp + moff);
-                used |= 1u << j;
-            }
-        }
+        for (int j = 0; j < G; j++) mv[j] = (used >> j & 1u) ? __ldg(E->mask[j] + moff) : 0;
         u64 u0, u1;
         if (key) {
             const u32 src = auto_src((u32)c, E->g, logN);
@@ -670,9 +663,10 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
                 u0 = montmul(x0, pR, q, qinv);
                 u1 = montmul(x1, pR, q, qinv);
             }
+            const u32 used = E->used;
 #pragma unroll
             for (int j = 0; j < G; j++)
-                if (E->mask[j]) {
+                if (used >> j & 1u) {
                     const u64 m = st[(size_t)(2 * nd + j) * 256 + tid];
                     mac(s0[j], u0, m);
                     mac(s1[j], u1, m);
@@ -810,9 +804,10 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, in
                     u0 = montmul(x0, pR, q, qinv);
                     u1 = montmul(x1, pR, q, qinv);
                 }
+                const u32 used = E->used;
 #pragma unroll
                 for (int j = 0; j < G; j++)
-                    if (E->mask[j]) {
+                    if (used >> j & 1u) {
                         const u64 m = st[(size_t)(2 * nd + j) * 256 + tid];
                         mac(s0[j], u0, m);
                         mac(s1[j], u1, m);
