@@ -349,6 +349,7 @@ def main():
     ap.add_argument("--max-requests", type=int, default=1000)
     ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning instead of hegmm_autotune")
     ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
                     help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
@@ -415,6 +416,11 @@ def main():
             cnts.append(cnt)
         return outs, cnts
 
+    # the library's autotuner picks the bit-neutral kernel knobs on this workload
+    tuning = None
+    if not args.no_autotune:
+        tuning = ctx.hegmm_autotune([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs,
+                                    reps=3 if len(prods) <= 64 else 1)
     # warm-up (builds plans, masks) and a correctness check of every product
     for w in range(max(args.warmup, 1)):
         outs = step()
@@ -568,7 +574,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": (batch_config if batch else workload_config)({"parallelism": "replicas" if world > 1 else "single-gpu",
-                                                                "keyswitch_mode": args.ks_mode}),
+                                                                "keyswitch_mode": args.ks_mode,
+                                                                "tuning": tuning or "defaults"}),
         "other_keyswitch_mode": {"mode": other, "value": per_step * world / (other_ms / 1e3), "unit": UNIT,
                                  "ms_per_step": other_ms},
         "keyswitches_per_s": ksw_per_step * world / (ms / 1e3),

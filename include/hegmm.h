@@ -228,6 +228,19 @@ int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                             const int *mln, const int *algs, hegmm_ct **C);
 
+/* Autotuner of the bit-neutral tuning knobs: runs the given products (as
+ * hegmm_matmul_batch_algs would) under every candidate (kernel variant 0, 3,
+ * 6, 7; entries per item 16, 32, 64; staged one-output items with 6 / 7),
+ * each timed over reps calls with CUDA events on the context stream after a
+ * plan-building and a graph-capturing call, and keeps the fastest in the
+ * context.  chosen (may be NULL) receives {kernel variant, entries per item,
+ * staged one-output items}.  Results stay bit for bit the same (every
+ * candidate is an execution order of the same sums).  Only the
+ * HEGMM_KS_DOUBLE kernels have knobs; in single mode it returns at once.
+ * Cached product plans are released (they are rebuilt on the next call). */
+int hegmm_autotune(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                   const int *algs, int reps, int *chosen);
+
 /* Builds and caches the per-shape plan data of the listed products (the
  * encoded diagonal masks of every linear transformation, Eq. lintrans), so
  * that the first product of each shape does not pay for it.  Needs the

@@ -1219,6 +1219,8 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(shared ? c->giant_cost : 0);
     key.push_back(dbl ? c->lt_chunk : 0);
     key.push_back(dbl ? c->lt_fused : 0);
+    key.push_back(dbl ? c->lt_kernel : 0);  // launch choices are baked into a plan's graph
+    key.push_back(dbl ? c->lt_staged1 : 0);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
@@ -1295,6 +1297,73 @@ int hegmm_matmul_batch_algs(hegmm_ctx *h, int count, const hegmm_ct *const *A, c
                             const int *mln, const int *algs, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, HEGMM_ALG_AUTO, C, nullptr, algs);
+}
+
+int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                   const int *algs, int reps, int *chosen) {
+    if (!h || count <= 0 || !A || !B || !mln) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (reps < 1) reps = 3;
+    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_staged1;
+    auto report = [&]() {
+        if (chosen) {
+            chosen[0] = c->lt_kernel;
+            chosen[1] = c->lt_chunk;
+            chosen[2] = c->lt_staged1;
+        }
+        return HEGMM_OK;
+    };
+    if (!c->ks_double) return report();  // the knobs only steer the double-hoisted kernels
+    const bool timing = c->timing;
+    c->timing = false;
+    std::vector<hegmm_ct *> C((size_t)count, nullptr);
+    auto run = [&]() {
+        int rc = matmul_run(c, count, A, B, mln, HEGMM_ALG_AUTO, algs, C.data(), nullptr, true, nullptr);
+        for (auto *x : C) hegmm_ct_destroy(x);
+        return rc;
+    };
+    auto drop_plans = [&]() {
+        for (auto &kv : c->bplans) free_bplan(c, kv.second);
+        c->bplans.clear();
+        c->bplan_bytes = 0;
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bk = k0, bc = ch0, bs = s0, rc = HEGMM_OK;
+    for (int kv : {0, 3, 6, 7})
+        for (int chunk : {16, 32, 64})
+            for (int st : {0, 1}) {
+                if (st && kv < 6) continue;  // staging one-output items only exists with variants 6 and 7
+                c->lt_kernel = kv;
+                c->lt_chunk = chunk;
+                c->lt_staged1 = st;
+                for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
+                if (rc) break;
+                cudaEventRecord(e0, c->st);
+                for (int r = 0; r < reps && !rc; r++) rc = run();
+                cudaEventRecord(e1, c->st);
+                if (rc || cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    bk = kv;
+                    bc = chunk;
+                    bs = st;
+                }
+                drop_plans();
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_plans();
+    c->timing = timing;
+    c->lt_kernel = rc ? k0 : bk;
+    c->lt_chunk = rc ? ch0 : bc;
+    c->lt_staged1 = rc ? s0 : bs;
+    if (rc) return rc;
+    return report();
 }
 
 int hegmm_set_keyswitch_mode(hegmm_ctx *h, int mode) {

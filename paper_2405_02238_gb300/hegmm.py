@@ -114,6 +114,8 @@ _SIGS = {
     "hegmm_prepare": (ctypes.c_int, [vp, intp, ctypes.c_int, ctypes.c_int]),
     "hegmm_set_keyswitch_mode": (ctypes.c_int, [vp, ctypes.c_int]),
     "hegmm_set_tuning": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_longlong]),
+    "hegmm_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp, intp,
+                                      ctypes.c_int, intp]),
     "hegmm_set_budgets": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]),
     "hegmm_server_create": (ctypes.c_int, [vp, ctypes.POINTER(hegmm_server_opts), ctypes.POINTER(vp)]),
     "hegmm_server_submit": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -261,6 +263,19 @@ class Context:
         """KS_SINGLE: one ModDown per key switch; KS_DOUBLE: sums kept over PQ;
         | KS_LAZY_RELIN: one relinearisation per product."""
         self._check(self.lib.hegmm_set_keyswitch_mode(self.h, int(mode)), "set_keyswitch_mode")
+
+    def hegmm_autotune(self, As, Bs, shapes, algs=None, reps: int = 3) -> dict:
+        """Times the bit-neutral tuning candidates on these products and keeps the fastest."""
+        n = len(As)
+        pa = (vp * n)(*[a.h for a in As])
+        pb = (vp * n)(*[b.h for b in Bs])
+        mln = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
+        al = None if algs is None else np.ascontiguousarray(np.array(algs, dtype=np.int32))
+        chosen = np.zeros(3, dtype=np.int32)
+        self._check(self.lib.hegmm_autotune(self.h, n, pa, pb, mln.ctypes.data_as(intp),
+                                            None if al is None else al.ctypes.data_as(intp), int(reps),
+                                            chosen.ctypes.data_as(intp)), "autotune")
+        return {"lt_kernel": int(chosen[0]), "lt_chunk": int(chosen[1]), "lt_staged1": int(chosen[2])}
 
     def hegmm_set_tuning(self, knob: int, value: int):
         self._check(self.lib.hegmm_set_tuning(self.h, int(knob), int(value)), "set_tuning")

@@ -149,3 +149,23 @@ def test_graph_replay_takes_each_calls_operands(H, medium):
                 assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(plain)).all(), call
     finally:
         ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
+
+
+def test_autotune_keeps_results(H, medium):
+    ctx = medium
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED)
+    shapes = [(6, 10, 9), (5, 12, 7), (4, 8, 6)]
+    ctx.hegmm_keygen(SEED, shapes)
+    try:
+        As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=40, stream0=400)
+        before = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_batch(As, Bs, shapes)]
+        chosen = ctx.hegmm_autotune(As, Bs, shapes, reps=1)
+        assert chosen["lt_kernel"] in (0, 3, 6, 7) and chosen["lt_chunk"] in (16, 32, 64)
+        after = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_batch(As, Bs, shapes)]
+        for x, y in zip(before, after):
+            assert (x == y).all()
+    finally:
+        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 6)
+        ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
+        ctx.hegmm_set_tuning(H.TUNE_LT_STAGED1, 0)
+        ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
