@@ -38,6 +38,7 @@ SHAPES = W.MEDIUM_SHAPES
 ALGS = (1, 2)
 METRIC = "HEGMM encrypted matmuls/s (N=8192 ring, 16x32x24 + 32x8x48, Alg 1 + Alg 2)"
 METRIC_BATCH = "HEGMM encrypted matmuls/s (batch of 512 mixed shapes, N=8192 ring)"
+METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 128x16x64, AUTO algorithm)"
 UNIT = "matmul/s"
 KEY_SEED = 7
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -55,6 +56,22 @@ def workload_config(extra=None):
         "l2": "flushed between timed steps (256 MiB write) and per-step key working set > L2",
         "launch": "each cached product plan replayed as one CUDA graph; per-kernel times from a second pass of the "
                   "same steps launched kernel by kernel with CUDA events on the library stream",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def paper_config(extra=None):
+    cfg = {
+        "workload": "paper: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; A64x64.B64x64, A32x128.B128x16 "
+                    "(Algorithm 1: Algorithm 2 would need 16384 > 8192 slots), A128x16.B16x64 (Algorithm 2); entries "
+                    "U[0,255] seed 0; one hegmm_matmul_batch_algs call per step; per_product_path = the plain "
+                    "one-product-per-launch path",
+        "products_per_step": len(W.PAPER_SHAPES),
+        "l2": "flushed between timed steps (256 MiB write); per-step key working set (about 19 GB) >> L2",
+        "launch": "the cached plan replayed as one CUDA graph; per-kernel times from a second pass of the same "
+                  "steps launched kernel by kernel with CUDA events on the library stream",
     }
     if extra:
         cfg.update(extra)
@@ -132,7 +149,7 @@ class ClockSampler:
 _oracle_cache = {}
 
 
-def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2):
+def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2, preset=None):
     """Times the oracle on a bounded sample of the workload.
 
     The oracle executes a product as a fixed sequence of HE-Rot, HE-CMult,
@@ -146,13 +163,14 @@ def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2):
     from oracle import he as OH
     from oracle import slots as SL
 
-    if "o" not in _oracle_cache:
-        o = OH.Oracle(PRESET)
+    pre = preset or PRESET
+    if pre.name not in _oracle_cache:
+        o = OH.Oracle(pre)
         o.keygen(KEY_SEED)
         for z in range(1, nrot + 1):
             o.add_galois_key(o.galois(z))
-        _oracle_cache["o"] = o
-    o = _oracle_cache["o"]
+        _oracle_cache[pre.name] = o
+    o = _oracle_cache[pre.name]
     x = np.arange(o.S) % o.t
     ct = o.encrypt(o.encode(x), 1, 0)
     pt = o.plaintext_eval(o.encode((x * 3) % o.t), o.L)
@@ -179,10 +197,10 @@ def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2):
         a = alg if alg else SL.choose_alg(m, l, n, o.S)
         c = SL.make_plan(m, l, n, a).counts()
         total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
-    desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=8192/L=5; "
+    desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=%d/L=%d; "
             "per-step time = op counts of the %d plans x measured op times (%.1f/%.1f/%.1f/%.1f ms "
-            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, len(prods), t_rot * 1e3, t_cm * 1e3,
-                                                       t_add * 1e3, t_mul * 1e3))
+            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, o.N, o.L, len(prods), t_rot * 1e3,
+                                                       t_cm * 1e3, t_add * 1e3, t_mul * 1e3))
     return total, desc
 
 
@@ -341,7 +359,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve", "paper"],
                     help="medium: the four medium-ring products (default); batch: 512 mixed shapes; "
                          "serve: Poisson arrivals on the N=16384 ring")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
@@ -377,13 +395,20 @@ def main():
     from paper_2405_02238_gb300 import hegmm as H
 
     stream = torch.cuda.Stream(device=dev)
-    ctx = H.Context.from_preset(PRESET, stream=stream.cuda_stream)
+    paper = args.workload == "paper"
+    pre = W.PAPER if paper else PRESET
+    ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
     ks_code = KS_MODES
     ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
     prods = []
     if args.workload == "batch":
         for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
             A, Bm = W.matrices(m, l, n, *W.BATCH_RANGE, seed=i)
+            prods.append((m, l, n, H.ALG_AUTO, A, Bm))
+        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods], H.ALG_AUTO)
+    elif paper:
+        for (m, l, n) in W.PAPER_SHAPES:
+            A, Bm = W.matrices(m, l, n, *W.PAPER_RANGE)
             prods.append((m, l, n, H.ALG_AUTO, A, Bm))
         ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods], H.ALG_AUTO)
     else:
@@ -426,7 +451,7 @@ def main():
         outs = step()
     for (m, l, n, alg, A, Bm), c in zip(prods, outs):
         got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
-        assert (got == (A @ Bm) % PRESET.t).all(), "wrong product %dx%dx%d alg %d" % (m, l, n, alg)
+        assert (got == (A @ Bm) % pre.t).all(), "wrong product %dx%dx%d alg %d" % (m, l, n, alg)
     del outs
     sample = list(range(len(prods))) if len(prods) <= 8 else list(range(0, len(prods), len(prods) // 32))
     _, cnts = single_path(sample)
@@ -492,7 +517,7 @@ def main():
     outs = step()
     for (m, l, n, alg, A, Bm), c in zip(prods, outs):
         got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
-        assert (got == (A @ Bm) % PRESET.t).all(), "wrong product (%s mode)" % other
+        assert (got == (A @ Bm) % pre.t).all(), "wrong product (%s mode)" % other
     del outs
     o_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for k in range(args.steps):
@@ -570,10 +595,12 @@ def main():
 
     batch = args.workload == "batch"
     line = {
-        "metric": METRIC_BATCH if batch else METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC_BATCH if batch else (METRIC_PAPER if paper else METRIC), "value": value, "unit": UNIT,
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": (batch_config if batch else workload_config)({"parallelism": "replicas" if world > 1 else "single-gpu",
+        "config": (batch_config if batch else (paper_config if paper else workload_config))({
+                                                                "parallelism": "replicas" if world > 1 else "single-gpu",
                                                                 "keyswitch_mode": args.ks_mode,
                                                                 "tuning": tuning or "defaults"}),
         "other_keyswitch_mode": {"mode": other, "value": per_step * world / (other_ms / 1e3), "unit": UNIT,
@@ -594,7 +621,8 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        sec, desc = oracle_sample([p[:4] for p in prods])
+        # a bounded sample of about 10-30 s of single-core CPU work
+        sec, desc = oracle_sample([p[:4] for p in prods], nrot=40, ncm=40, nmul=12, preset=pre)
         line["cpu_baseline"] = {"value": len(prods) / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": desc}
     if rank == 0:
