@@ -199,17 +199,12 @@ struct alignas(16) TwPair {
 // a w mod q left in [0, 2q) (Shoup without the final correction).
 HDI u64 mulsh_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi(a, wp) * q; }
 
-// Lazy forward butterflies (Harvey): inputs and outputs in [0, 4q), q < 2^62.
+// Lazy forward butterflies (Harvey) of one group of 2^R elements held in
+// registers, through stages s0 .. s0+R-1 (B: the group's block index):
+// inputs and outputs in [0, 4q), q < 2^62.
 template <int R>
-HDI void ntt_fwd_group_lazy(u64 *sm, int g, int s0, int logN, const TwPair *tw, u64 q) {
-    const int ltl = logN - s0 - R;
-    const int tl = 1 << ltl;
-    const int B = g >> ltl, o = g & (tl - 1);
-    const int base = (B << (ltl + R)) + o;
+HDI void ntt_fwd_regs(u64 *x, int B, int s0, const TwPair *tw, u64 q) {
     const u64 q2 = 2 * q;
-    u64 x[1 << R];
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int half = 1 << (R - 1 - r);
@@ -224,20 +219,30 @@ HDI void ntt_fwd_group_lazy(u64 *sm, int g, int s0, int logN, const TwPair *tw, 
             x[k + half] = X - T + q2;
         }
     }
+}
+
+// The same group staged in shared memory: group g covers elements
+// base + k tl, k < 2^R.
+template <int R>
+HDI void ntt_fwd_group_lazy(u64 *sm, int g, int s0, int logN, const TwPair *tw, u64 q) {
+    const int ltl = logN - s0 - R;
+    const int tl = 1 << ltl;
+    const int B = g >> ltl, o = g & (tl - 1);
+    const int base = (B << (ltl + R)) + o;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+    ntt_fwd_regs<R>(x, B, s0, tw, q);
 #pragma unroll
     for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
 }
 
-// Lazy inverse butterflies (Harvey): inputs and outputs in [0, 2q).
+// Lazy inverse butterflies (Harvey) of one group in registers, through the
+// stages of butterfly distance 2^u0 .. 2^(u0+R-1): inputs and outputs in
+// [0, 2q).
 template <int R>
-HDI void ntt_inv_group_lazy(u64 *sm, int g, int u0, int logN, const TwPair *tw, u64 q) {
-    const int tl = 1 << u0;
-    const int B = g >> u0, o = g & (tl - 1);
-    const int base = (B << (u0 + R)) + o;
+HDI void ntt_inv_regs(u64 *x, int B, int u0, int logN, const TwPair *tw, u64 q) {
     const u64 q2 = 2 * q;
-    u64 x[1 << R];
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int dist = 1 << r;
@@ -251,6 +256,17 @@ HDI void ntt_inv_group_lazy(u64 *sm, int g, int u0, int logN, const TwPair *tw, 
             x[k + dist] = mulsh_lazy(U - V + q2, t.w, t.wp, q);
         }
     }
+}
+
+template <int R>
+HDI void ntt_inv_group_lazy(u64 *sm, int g, int u0, int logN, const TwPair *tw, u64 q) {
+    const int tl = 1 << u0;
+    const int B = g >> u0, o = g & (tl - 1);
+    const int base = (B << (u0 + R)) + o;
+    u64 x[1 << R];
+#pragma unroll
+    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
+    ntt_inv_regs<R>(x, B, u0, logN, tw, q);
 #pragma unroll
     for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
 }

@@ -75,35 +75,35 @@ struct NttCfg {
     static constexpr size_t SMEM = (size_t)(N + N / 16) * 8;
 };
 
-// Register passes of radix 2^PR (PR = NTT_PASS_BITS stages per shared-memory
-// round trip), then one remainder pass.
-#ifndef NTT_PASS_BITS
-#define NTT_PASS_BITS 3
-#endif
+// Fused pass layout of the kernels below: the first radix-8 pass (stages
+// 0..2) runs on register values the kernel's prologue produces (no shared
+// memory round trip before it), the middle radix-8 passes through shared
+// memory, and the last pass of RL stages ends in registers that the
+// kernel's epilogue consumes directly.  Forward: group g of the first pass
+// holds elements g + k N/8, of the last pass elements (g << RL) + k;
+// inverse: the first pass holds (g << 3) + k, the last g + k 2^LAST.
 template <int LOGN>
-__device__ __forceinline__ void fwd_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, PR = NTT_PASS_BITS, REM = LOGN % PR;
+struct NttPasses {
+    static constexpr int RL = (LOGN % 3) ? (LOGN % 3) : 3;
+    static constexpr int LAST = LOGN - RL;  // first stage of the last pass
+};
+
+template <int LOGN>
+__device__ __forceinline__ void fwd_middle(u64 *sm, const TwPair *__restrict__ T, u64 q) {
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, LAST = NttPasses<LOGN>::LAST;
 #pragma unroll
-    for (int s0 = 0; s0 + PR <= LOGN; s0 += PR) {
-        for (int g = threadIdx.x; g < (N >> PR); g += NT) ntt_fwd_group_lazy<PR>(sm, g, s0, LOGN, T, q);
-        __syncthreads();
-    }
-    if constexpr (REM != 0) {
-        for (int g = threadIdx.x; g < (N >> REM); g += NT) ntt_fwd_group_lazy<REM>(sm, g, LOGN - REM, LOGN, T, q);
+    for (int s0 = 3; s0 < LAST; s0 += 3) {
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_fwd_group_lazy<3>(sm, g, s0, LOGN, T, q);
         __syncthreads();
     }
 }
 
 template <int LOGN>
-__device__ __forceinline__ void inv_passes(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, PR = NTT_PASS_BITS, REM = LOGN % PR;
+__device__ __forceinline__ void inv_middle(u64 *sm, const TwPair *__restrict__ T, u64 q) {
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, LAST = NttPasses<LOGN>::LAST;
 #pragma unroll
-    for (int u0 = 0; u0 + PR <= LOGN; u0 += PR) {
-        for (int g = threadIdx.x; g < (N >> PR); g += NT) ntt_inv_group_lazy<PR>(sm, g, u0, LOGN, T, q);
-        __syncthreads();
-    }
-    if constexpr (REM != 0) {
-        for (int g = threadIdx.x; g < (N >> REM); g += NT) ntt_inv_group_lazy<REM>(sm, g, LOGN - REM, LOGN, T, q);
+    for (int u0 = 3; u0 < LAST; u0 += 3) {
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, u0, LOGN, T, q);
         __syncthreads();
     }
 }
@@ -117,32 +117,55 @@ template <int LOGN, bool INV>
 __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(LimbPat p, const ModDev *__restrict__ mods,
                                                          const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
+    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
     int mi;
     u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
     const u64 q = mods[mi].q;
+    const TwPair *T = tw_of(tw, mi, INV ? 1 : 0, N);
+    if (INV) {
+        // coalesced 16-byte loads into shared memory (the first inverse pass
+        // reads 8 consecutive coefficients per group)
 #pragma unroll 4
-    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
-        ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
-        const int pi = pad16(i);
-        sm[pi] = v.x;
-        sm[pi + 1] = v.y;
-    }
-    __syncthreads();
-    if (INV) inv_passes<LOGN>(sm, tw_of(tw, mi, 1, N), q);
-    else fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), q);
-    const u64 ninv = mods[mi].ninv, ninv_sh = mods[mi].ninv_sh;
-    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
-        const int pi = pad16(i);
-        ulonglong2 v;
-        if (INV) {
+        for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
+            const int pi = pad16(i);
+            sm[pi] = v.x;
+            sm[pi + 1] = v.y;
+        }
+        __syncthreads();
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, 0, LOGN, T, q);
+        __syncthreads();
+        inv_middle<LOGN>(sm, T, q);
+        for (int g = threadIdx.x; g < (N >> RL); g += NT) ntt_inv_group_lazy<RL>(sm, g, LAST, LOGN, T, q);
+        __syncthreads();
+        // scaling by N^-1 with coalesced 16-byte stores
+        const u64 ninv = mods[mi].ninv, ninv_sh = mods[mi].ninv_sh;
+        for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
+            const int pi = pad16(i);
+            ulonglong2 v;
             v.x = mulsh(sm[pi], ninv, ninv_sh, q);
             v.y = mulsh(sm[pi + 1], ninv, ninv_sh, q);
-        } else {
-            v.x = reduce4(sm[pi], q);
-            v.y = reduce4(sm[pi + 1], q);
+            *reinterpret_cast<ulonglong2 *>(ptr + i) = v;
         }
-        *reinterpret_cast<ulonglong2 *>(ptr + i) = v;
+    } else {
+        for (int g = threadIdx.x; g < N / 8; g += NT) {
+            u64 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) x[k] = ptr[g + k * (N / 8)];
+            ntt_fwd_regs<3>(x, 0, 0, T, q);
+#pragma unroll
+            for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = x[k];
+        }
+        __syncthreads();
+        fwd_middle<LOGN>(sm, T, q);
+        for (int g = threadIdx.x; g < (N >> RL); g += NT) {
+            u64 x[1 << RL];
+#pragma unroll
+            for (int k = 0; k < (1 << RL); k++) x[k] = sm[pad16((g << RL) + k)];
+            ntt_fwd_regs<RL>(x, g, LAST, T, q);
+#pragma unroll
+            for (int k = 0; k < (1 << RL); k++) ptr[(g << RL) + k] = reduce4(x[k], q);
+        }
     }
 }
 
@@ -168,29 +191,48 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divroun
     const int mi = (int)tI[i];
     const ModDev M = mods[mi];
     const u64 *hB = tB + (size_t)i * ndrop * 3;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < N; c += NT) {
-        u64 acc = 0;
-        for (int k = 0; k < ndrop; k++) {
-            const u64 dk = mods[tI[nkeep + k]].q;
-            const u64 z = mulsh(d.u[(size_t)(nkeep + k) * N + c], __ldg(tA + 2 * k), __ldg(tA + 2 * k + 1), dk);
-            const u64 *h = hB + 3 * k;
-            acc = addm(acc, mulsh(centred(z, dk, __ldg(h + 2), M.q, M.barr), __ldg(h), __ldg(h + 1), M.q), M.q);
+    const TwPair *T = tw_of(tw, mi, 0, N);
+    constexpr int RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
+    // prologue fused with the first pass: the conversion of the group's 8 coefficients
+    for (int g = threadIdx.x; g < N / 8; g += NT) {
+        u64 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int c = g + k * (N / 8);
+            u64 acc = 0;
+            for (int kk = 0; kk < ndrop; kk++) {
+                const u64 dk = mods[tI[nkeep + kk]].q;
+                const u64 z = mulsh(d.u[(size_t)(nkeep + kk) * N + c], __ldg(tA + 2 * kk), __ldg(tA + 2 * kk + 1), dk);
+                const u64 *h = hB + 3 * kk;
+                acc = addm(acc, mulsh(centred(z, dk, __ldg(h + 2), M.q, M.barr), __ldg(h), __ldg(h + 1), M.q), M.q);
+            }
+            x[k] = acc;
         }
-        sm[pad16(c)] = acc;
+        ntt_fwd_regs<3>(x, 0, 0, T, M.q);
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = x[k];
     }
     __syncthreads();
-    fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), M.q);
+    fwd_middle<LOGN>(sm, T, M.q);
     const u64 *k4 = tC + 4 * i;
     const u64 Di = k4[0], Dis = k4[1], tq = k4[2], tqs = k4[3];
     const u64 *ui = d.u + (size_t)i * N;
     u64 *oi = d.out + (size_t)i * N;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < N; c += NT) {
-        u64 v = subm(ui[c], mulsh(sm[pad16(c)], tq, tqs, M.q), M.q);
-        v = mulsh(v, Di, Dis, M.q);
-        if (d.add) v = addm(v, d.add[(size_t)i * N + (d.g == 1 ? (u32)c : auto_src((u32)c, d.g, LOGN))], M.q);
-        oi[c] = v;
+    // last pass fused with the epilogue: out = (u - t y~) D^-1 (+ add at the automorphism's index)
+    for (int g = threadIdx.x; g < (N >> RL); g += NT) {
+        u64 x[1 << RL];
+        const int base = g << RL;
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) x[k] = sm[pad16(base + k)];
+        ntt_fwd_regs<RL>(x, g, LAST, T, M.q);
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) {
+            const int c = base + k;
+            u64 v = subm(ui[c], mulsh(x[k], tq, tqs, M.q), M.q);
+            v = mulsh(v, Di, Dis, M.q);
+            if (d.add) v = addm(v, d.add[(size_t)i * N + (d.g == 1 ? (u32)c : auto_src((u32)c, d.g, LOGN))], M.q);
+            oi[c] = v;
+        }
     }
 }
 
@@ -215,25 +257,37 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_modup_n
     const ModDev R = mods[mi];
     const u64 *tinv = tab + (size_t)j * alpha * 2;
     const u64 *thm = tab + (size_t)nd * alpha * 2 + (size_t)j * alpha * ne * 3;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < N; c += NT) {
-        u64 acc = 0;
-        for (int ii = 0; ii < ns; ii++) {
-            const u64 sq = mods[lo + ii].q;
-            const u64 y = mulsh(x[(size_t)(lo + ii) * N + c], __ldg(tinv + 2 * ii), __ldg(tinv + 2 * ii + 1), sq);
-            const u64 *h = thm + ((size_t)ii * ne + e) * 3;
-            acc = addm(acc, mulsh(centred(y, sq, __ldg(h + 2), R.q, R.barr), __ldg(h), __ldg(h + 1), R.q), R.q);
+    const TwPair *T = tw_of(tw, mi, 0, N);
+    constexpr int RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
+    // prologue fused with the first pass: the digit's conversion of the group's coefficients
+    for (int g = threadIdx.x; g < N / 8; g += NT) {
+        u64 xv[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int c = g + k * (N / 8);
+            u64 acc = 0;
+            for (int ii = 0; ii < ns; ii++) {
+                const u64 sq = mods[lo + ii].q;
+                const u64 y = mulsh(x[(size_t)(lo + ii) * N + c], __ldg(tinv + 2 * ii), __ldg(tinv + 2 * ii + 1), sq);
+                const u64 *h = thm + ((size_t)ii * ne + e) * 3;
+                acc = addm(acc, mulsh(centred(y, sq, __ldg(h + 2), R.q, R.barr), __ldg(h), __ldg(h + 1), R.q), R.q);
+            }
+            xv[k] = acc;
         }
-        sm[pad16(c)] = acc;
+        ntt_fwd_regs<3>(xv, 0, 0, T, R.q);
+#pragma unroll
+        for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = xv[k];
     }
     __syncthreads();
-    fwd_passes<LOGN>(sm, tw_of(tw, mi, 0, N), R.q);
-    for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
-        const int pi = pad16(i);
-        ulonglong2 v;
-        v.x = reduce4(sm[pi], R.q);
-        v.y = reduce4(sm[pi + 1], R.q);
-        *reinterpret_cast<ulonglong2 *>(dst + i) = v;
+    fwd_middle<LOGN>(sm, T, R.q);
+    for (int g = threadIdx.x; g < (N >> RL); g += NT) {
+        u64 xv[1 << RL];
+        const int base = g << RL;
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) xv[k] = sm[pad16(base + k)];
+        ntt_fwd_regs<RL>(xv, g, LAST, T, R.q);
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) dst[base + k] = reduce4(xv[k], R.q);
     }
 }
 
