@@ -348,7 +348,11 @@ int hegmm_ct_import(hegmm_ctx *ctx, const uint64_t *host, int level, hegmm_ct **
 int hegmm_ct_import_batch(hegmm_ctx *ctx, int count, const uint64_t *const *host, int level, hegmm_ct **out);
 int hegmm_ct_export_batch(hegmm_ctx *ctx, int count, const hegmm_ct *const *cts, uint64_t *const *host);
 
-/* Waits for all work queued on the context's stream. */
+/* Waits for all work queued on the context's stream.  Returns
+ * HEGMM_ETIMEOUT if, since the last check, a kernel's bounded wait for its
+ * staged copies ran out (its products are then invalid; the context stays
+ * usable).  hegmm_decrypt*, hegmm_ct_export and hegmm_ct_export_batch make
+ * the same check. */
 int hegmm_sync(hegmm_ctx *ctx);
 
 void hegmm_pt_destroy(hegmm_pt *pt);

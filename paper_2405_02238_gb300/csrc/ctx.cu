@@ -735,6 +735,7 @@ int hegmm_ct_export(hegmm_ctx *h, const hegmm_ct *ct, uint64_t *host) {
     cudaMemcpyAsync(host, tmp, w * 8, cudaMemcpyDeviceToHost, c->st);
     dfree(c, tmp);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "export");
+    if ((rc = device_status(c))) return rc;
     return cuda_check(c, "export");
 }
 
