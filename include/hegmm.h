@@ -220,6 +220,16 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     timing is on (hegmm_set_timing) plans always run kernel by kernel. */
 #define HEGMM_TUNE_GRAPHS 5
 #define HEGMM_TUNE_LT_STAGED1 6
+/*   HEGMM_TUNE_WAIT_LIMIT: polls of every bounded mbarrier wait of the staged
+ *     kernels (default 2^22, about a second); when one runs out the kernel
+ *     stops, drains its copies and the next synchronising call reports
+ *     HEGMM_ETIMEOUT.
+ *   HEGMM_TUNE_TEST_DROP: a test hook of that path: the staged kernels leave
+ *     entry number `value` of every work item unarmed, so its bounded wait
+ *     runs out (-1, the default: none).  No copy is issued for it and no memory is
+ *     touched; the GPU and the context stay usable. */
+#define HEGMM_TUNE_WAIT_LIMIT 7
+#define HEGMM_TUNE_TEST_DROP 8
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in

@@ -23,6 +23,7 @@
 // Masks are encoded once per shape; descriptors once per batch composition
 // (plans are cached, least recently used evicted beyond a memory budget).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <string.h>
 
 #include <algorithm>
@@ -36,6 +37,12 @@
 #include "plan.h"
 
 namespace hg {
+
+// NVTX range over one stage of a plan (host side; shows in profilers)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // A group of linear-transformation outputs (iterations k0 .. k0+nj-1 of one
 // operand) evaluated by the same work items: its entries, each a rotation
@@ -433,6 +440,7 @@ static void add_counts(hegmm_opcount &a, const hegmm_opcount &b) {
 // shapes: B entries of (m, l, n, resolved alg)
 static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, int dbl, int lazy, int shared,
                        BatchPlan **out) {
+    Range r("hegmm plan build");
     const int N = c->N;
     BatchPlan *P = new BatchPlan;
     P->dbl = dbl;
@@ -1045,6 +1053,7 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
     const int N = c->N, B = P->B, lv0 = P->lv0, lv1 = P->lv1, K = c->K;
     const int dbl = P->dbl, np0 = dbl ? lv0 + K : lv0, np1 = dbl ? lv1 + K : lv1;
     int rc;
+    Range all("hegmm plan launches");
     // 1. operands and the hoisted ModUp of every c1
     if ((rc = gather_cts(c, lv0, P->d_inptr, 2 * B, P->in))) return rc;
     if ((rc = modup(c, lv0, 2 * B, P->in + (size_t)lv0 * N, (long long)2 * lv0 * N, P->xc, P->D))) return rc;
@@ -1221,6 +1230,8 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back(dbl ? c->lt_kernel : 0);  // launch choices are baked into a plan's graph
     key.push_back(dbl ? c->lt_staged1 : 0);
+    key.push_back(c->wait_limit);  // kernel arguments captured in the graph
+    key.push_back(c->test_drop_entry);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
@@ -1398,6 +1409,16 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_LT_STAGED1) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "lt_staged1 must be 0 or 1");
         c->lt_staged1 = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_WAIT_LIMIT) {
+        if (value < 1 || value > (1LL << 30)) return set_err(c, HEGMM_EINVAL, "wait limit must be in 1..2^30");
+        c->wait_limit = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_TEST_DROP) {
+        if (value < -1 || value > (1LL << 30)) return set_err(c, HEGMM_EINVAL, "test drop must be -1 or an entry index");
+        c->test_drop_entry = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_GRAPHS) {

@@ -189,6 +189,8 @@ struct Ctx {
     int giant_cost = 8;                        // shared baby steps: giant rotation cost in the greedy rule
     int use_graphs = 1;                        // replay cached plans as CUDA graphs
     int *d_err = nullptr;                      // set by a kernel whose bounded wait ran out
+    int wait_limit = 1 << 22;                  // polls of a bounded mbarrier wait
+    int test_drop_entry = -1;                  // test hook: a staged entry left unarmed
     int lt_chunk = 32;                         // double mode: entries per k_lt_grp work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
     int lt_kernel = 6;                         // grouped fused kernel variant (6: operands staged by TMA)

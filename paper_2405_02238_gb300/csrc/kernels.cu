@@ -618,14 +618,14 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
 // the CTA) the kernel sets *err, waits (bounded) for its copies in flight
 // and leaves its outputs unwritten.
 constexpr int TMA_MAX_ND = 8;
-constexpr int TMA_SPIN = 1 << 22;
 __device__ __forceinline__ size_t tma_stage_words(int nd, int G) { return (size_t)(2 * nd + G) * 256; }
 
 template <int G, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd, int np, int L, int logN,
                                                      const ModDev *__restrict__ mods,
                                                      const LtEntry *__restrict__ ents,
-                                                     const LtItem *__restrict__ items, int *err) {
+                                                     const LtItem *__restrict__ items, int *err, int spin,
+                                                     int drop) {
     extern __shared__ __align__(128) u64 tsm[];
     const int N = 1 << logN;
     const int tid = threadIdx.x;
@@ -644,8 +644,10 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
     }
     __syncthreads();
     const int t0 = it->first, n = it->count;
-    // producer: the copies of entry t into stage s (thread 0 only)
+    // producer: the copies of entry t into stage s (thread 0 only); the
+    // item's entry number `drop` is left unarmed (a test of the bounded waits)
     auto issue = [&](int t, int s) {
+        if (t - it->first == drop) return;
         const LtEntry *E = ents + t;
         u64 *st = tsm + s * sw;
         const bool live = E->key || e < lv;
@@ -693,7 +695,7 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
             x0 = __ldg(E->ct + (size_t)e * N + c);
             x1 = __ldg(E->ct + ((size_t)lv + e) * N + c);
         }
-        const bool ok = mbar_wait_bounded(&bar[s], ph[s], TMA_SPIN);
+        const bool ok = mbar_wait_bounded(&bar[s], ph[s], spin);
         if (__syncthreads_or(!ok)) {
             bad = true;
             break;
@@ -733,7 +735,7 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
         // the copies of entry i + 1 may still be in flight into the other stage
         if (i + 1 < n) {
             const int s = (i + 1) & 1;
-            const bool ok = mbar_wait_bounded(&bar[s], ph[s], TMA_SPIN);
+            const bool ok = mbar_wait_bounded(&bar[s], ph[s], spin);
             __syncthreads_or(!ok);
         }
         return;
@@ -758,7 +760,7 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp_tma(int lv, int ne, int nd
 template <int G, int S>
 __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, int np, int L, int logN,
                                                     const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
-                                                    const LtItem *__restrict__ items, int *err) {
+                                                    const LtItem *__restrict__ items, int *err, int spin, int drop) {
     extern __shared__ __align__(128) u64 tsm[];
     const int N = 1 << logN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -788,9 +790,13 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, in
             int issued = 0;
             for (int i = 0; i < n; i++) {
                 const int s = i % S;
-                if (i >= S && !mbar_wait_bounded(&empty[s], (u32)((i / S - 1) & 1), TMA_SPIN)) {
+                if (i >= S && !mbar_wait_bounded(&empty[s], (u32)((i / S - 1) & 1), spin)) {
                     bad = true;
                     break;
+                }
+                if (i == drop) {  // left unarmed (a test of the bounded waits)
+                    issued = i + 1;
+                    continue;
                 }
                 const LtEntry *E = ents + t0 + i;
                 u64 *st = tsm + s * sw;
@@ -816,7 +822,7 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, in
             }
             // every issued copy lands before the CTA can leave
             for (int i = issued - S > 0 ? issued - S : 0; i < issued; i++)
-                if (!mbar_wait_bounded(&full[i % S], (u32)((i / S) & 1), TMA_SPIN)) bad = true;
+                if (!mbar_wait_bounded(&full[i % S], (u32)((i / S) & 1), spin)) bad = true;
         }
     } else {
         for (int i = 0; i < n; i++) {
@@ -836,7 +842,7 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, in
                 x0 = __ldg(E->ct + (size_t)e * N + c);
                 x1 = __ldg(E->ct + ((size_t)lv + e) * N + c);
             }
-            if (!mbar_wait_bounded(&full[s], (u32)((i / S) & 1), TMA_SPIN)) {
+            if (!mbar_wait_bounded(&full[s], (u32)((i / S) & 1), spin)) {
                 bad = true;
                 break;
             }
@@ -913,7 +919,7 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
             if (staged && c->lt_staged1) {
                 const size_t smem = (2 * (size_t)(2 * nd + 1) * 256 + 2) * 8;
                 k_lt_grp_tma<1, 3><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it,
-                                                               c->d_err);
+                                                               c->d_err, c->wait_limit, c->test_drop_entry);
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }
@@ -922,13 +928,14 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
         if (staged && c->lt_kernel == 7) {
             const size_t smem = (WS_STAGES * (size_t)(2 * nd + LT_GROUP) * 256 + 2 * WS_STAGES) * 8;
             k_lt_grp_ws<LT_GROUP, WS_STAGES><<<grid, 288, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods,
-                                                                        d_ents, it, c->d_err);
+                                                                        d_ents, it, c->d_err, c->wait_limit,
+                                                                        c->test_drop_entry);
             continue;
         }
         if (staged) {
             const size_t smem = (2 * (size_t)(2 * nd + LT_GROUP) * 256 + 2) * 8;
             k_lt_grp_tma<LT_GROUP, 2><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents,
-                                                                 it, c->d_err);
+                                                                 it, c->d_err, c->wait_limit, c->test_drop_entry);
             continue;
         }
         switch (c->lt_kernel) {

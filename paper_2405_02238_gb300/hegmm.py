@@ -21,6 +21,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_STAGED1 = 1, 2, 3, 4, 5, 6
+TUNE_WAIT_LIMIT, TUNE_TEST_DROP = 7, 8
 ROLE_A, ROLE_B = 0, 1
 
 

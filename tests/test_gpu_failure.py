@@ -1,0 +1,50 @@
+"""Failure detection on the GPU without a fault: a bounded device wait that
+runs out is reported to the host as HEGMM_ETIMEOUT and leaves the context
+usable.  The staged linear-transformation kernels get a test hook that
+leaves one entry's shared-memory stage unarmed (no copy is issued, nothing
+is written); its consumers' wait runs out after a short poll limit."""
+import numpy as np
+import pytest
+
+import workload as W
+
+pytestmark = pytest.mark.gpu
+SEED = 99
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm
+
+    return hegmm
+
+
+@pytest.mark.parametrize("variant", [6, 7])
+def test_bounded_wait_reports_timeout_and_context_survives(H, variant):
+    ctx = H.Context.from_preset(W.MEDIUM)
+    ctx.hegmm_keygen(SEED, [(6, 10, 9)], H.ALG_1)
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED)
+    ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, variant)
+    m, l, n = 6, 10, 9
+    A, B = W.matrices(m, l, n, *W.MEDIUM_RANGE)
+    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, H.ALG_1), 3, 0)
+    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, H.ALG_1), 3, 1)
+    good, _ = ctx.hegmm_matmul(ca, cb, m, l, n, H.ALG_1)
+    want = ctx.hegmm_ct_export(good)
+    # a wait that runs out: short poll limit, the first staged entry left unarmed
+    ctx.hegmm_set_tuning(H.TUNE_WAIT_LIMIT, 1 << 10)
+    ctx.hegmm_set_tuning(H.TUNE_TEST_DROP, 0)
+    ctx.hegmm_matmul(ca, cb, m, l, n, H.ALG_1)
+    with pytest.raises(H.HegmmError) as e:
+        ctx.hegmm_sync()
+    assert e.value.code == -6  # HEGMM_ETIMEOUT
+    # the flag is cleared once read, and the context computes correctly again
+    ctx.hegmm_set_tuning(H.TUNE_TEST_DROP, -1)
+    ctx.hegmm_set_tuning(H.TUNE_WAIT_LIMIT, 1 << 22)
+    ctx.hegmm_sync()
+    again, _ = ctx.hegmm_matmul(ca, cb, m, l, n, H.ALG_1)
+    assert (ctx.hegmm_ct_export(again) == want).all()
+    assert (ctx.hegmm_decrypt(again, m, l, n, H.ALG_1).astype(np.int64) == (A @ B) % W.MEDIUM.t).all()
