@@ -41,6 +41,7 @@ METRIC_BATCH = "HEGMM encrypted matmuls/s (batch of 512 mixed shapes, N=8192 rin
 METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 128x16x64, AUTO algorithm)"
 UNIT = "matmul/s"
 KEY_SEED = 7
+SERVE_ARENA_GIB = 16  # server workspace, split over its streams
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
 # hegmm_set_keyswitch_mode flags per --ks-mode (KS_DOUBLE = 1, KS_LAZY_RELIN = 2, KS_SHARED = 4)
@@ -276,8 +277,17 @@ def run_serve(args):
         per_rate[r] = W.serving_requests(cnt, r, ctx.S, seed=int(r))
     shapes = sorted({s for v in per_rate.values() for _, s in v})
     t0 = time.perf_counter()
-    ctx.hegmm_set_budgets(mask_bytes=args.mask_gib << 30)
     ctx.hegmm_keygen(KEY_SEED, shapes, H.ALG_AUTO)
+    torch.cuda.synchronize()
+    # masks take what the keys leave, less the server's arenas, the largest
+    # rate's operands and results (three ciphertexts a request) and a margin
+    free_b, _ = torch.cuda.mem_get_info(dev)
+    ct_b = 2 * pre.L * (1 << pre.logN) * 8
+    keep = (SERVE_ARENA_GIB + 8 << 30) + 3 * ct_b * max(len(v) for v in per_rate.values())
+    mask_b = min(args.mask_gib << 30, max(1 << 30, free_b - keep))
+    ctx.hegmm_set_budgets(mask_bytes=mask_b)
+    print("serve: %d shapes, %.1f GiB free after keys, mask budget %.1f GiB"
+          % (len(shapes), free_b / 2**30, mask_b / 2**30), file=sys.stderr)
     ctx.hegmm_prepare(shapes, H.ALG_AUTO)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -292,7 +302,7 @@ def run_serve(args):
             ops.append((m, l, n, A, Bm, ca, cb))
         torch.cuda.synchronize()
         # continuous batching
-        srv = H.Server(ctx, max_batch=args.max_batch, streams=2)
+        srv = H.Server(ctx, max_batch=args.max_batch, streams=2, mem_budget=SERVE_ARENA_GIB << 30)
         tickets, late = [], []
         s0 = time.perf_counter()
         for (at, _), (m, l, n, _, _, ca, cb) in zip(arr, ops):
@@ -343,10 +353,50 @@ def run_serve(args):
         "config": {"workload": "serving: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; Poisson arrivals; "
                                "70% small (1..16), 25% medium (17..64, fitting), 5% 128x16x64; entries U[0,255]",
                    "distinct_shapes": len(shapes), "setup_s_keys_and_masks": setup_s,
-                   "max_batch": args.max_batch, "streams": 2, "keyswitch_mode": args.ks_mode},
+                   "max_batch": args.max_batch, "streams": 2, "keyswitch_mode": args.ks_mode,
+                   "free_gib_after_keys": free_b / 2**30, "mask_budget_gib": mask_b / 2**30},
         "rates": results,
     }
     print(json.dumps(line))
+
+
+def run_product(args):
+    """One product of --shape on the medium ring, run twice; prints the
+    second run's per-kernel times (the small case of the ncu captures: the
+    second product's launches are the captured ones, about 2 GB on the
+    device)."""
+    import torch
+
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm as H
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    pre = PRESET
+    ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
+    ctx.hegmm_set_keyswitch_mode(KS_MODES[args.ks_mode])
+    if args.lt_kernel >= 0:
+        ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, args.lt_kernel)
+    m, l, n = (int(v) for v in args.shape.lower().split("x"))
+    A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
+    ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
+    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, args.alg), 1, 0)
+    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, args.alg), 1, 1)
+    ctx.hegmm_matmul(ca, cb, m, l, n, args.alg)
+    torch.cuda.synchronize()
+    ctx.hegmm_kernel_reset()
+    ctx.hegmm_set_timing(True)
+    c, _ = ctx.hegmm_matmul(ca, cb, m, l, n, args.alg)
+    torch.cuda.synchronize()
+    ctx.hegmm_set_timing(False)
+    if not (ctx.hegmm_decrypt(c, m, l, n, args.alg).astype(np.int64) == (A @ Bm) % pre.t).all():
+        raise SystemExit("product: decrypted result differs from A @ B mod t")
+    ks = {k: {"ms": v[0], "launches": v[1], "algorithmic_bytes": v[2], "butterflies": v[3]}
+          for k, v in ctx.hegmm_kernel_stats().items() if v[1]}
+    print(json.dumps({"workload": "product %dx%dx%d, algorithm %d, medium ring" % (m, l, n, args.alg),
+                      "keyswitch_mode": args.ks_mode, "lt_kernel": args.lt_kernel, "kernels": ks}))
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -359,9 +409,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve", "paper"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve", "paper", "product"],
                     help="medium: the four medium-ring products (default); batch: 512 mixed shapes; "
-                         "serve: Poisson arrivals on the N=16384 ring")
+                         "serve: Poisson arrivals on the N=16384 ring; product: one product of --shape on the "
+                         "medium ring, run twice (the small case the ncu captures use)")
+    ap.add_argument("--shape", default="16x32x24", help="m x l x n of --workload product")
+    ap.add_argument("--alg", type=int, default=1, help="algorithm of --workload product (1, 2; 0 = auto)")
+    ap.add_argument("--lt-kernel", type=int, default=-1,
+                    help="--workload product: HEGMM_TUNE_LT_KERNEL variant (-1 keeps the default)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--max-requests", type=int, default=1000)
@@ -377,6 +432,10 @@ def main():
         if int(os.environ.get("RANK", "0")) != 0:
             return None  # the serving sweep runs on one GPU: other ranks exit without work
         return run_serve(args)
+    if args.workload == "product":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return None  # one GPU: other ranks exit without work
+        return run_product(args)
 
     import torch
     import torch.distributed as dist

@@ -257,6 +257,39 @@ static void evict_shapes(Ctx *c, size_t incoming) {
     }
 }
 
+// Allocates from the context's stream-ordered pool.  When the device is
+// full, the least recently used masks that no plan references are released
+// (at least a GiB, or the request, at a time) and the pool gives its unused
+// memory back before the next attempt: resident masks are a cache, and a
+// plan's or a server's workspace comes before them.
+void *dalloc_evicting(Ctx *c, size_t bytes) {
+    for (;;) {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 8), c->st) == cudaSuccess) return p;
+        cudaGetLastError();
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return nullptr;
+        const size_t goal = std::max<size_t>(bytes, (size_t)1 << 30);
+        size_t freed = 0;
+        while (freed < goal) {
+            auto lru = c->shapes.end();
+            for (auto it = c->shapes.begin(); it != c->shapes.end(); ++it)
+                if (it->second->refs == 0 && (lru == c->shapes.end() || it->second->last_use < lru->second->last_use))
+                    lru = it;
+            if (lru == c->shapes.end()) break;
+            freed += lru->second->bytes;
+            free_shape(c, lru->second);
+            c->shapes.erase(lru);
+        }
+        if (!freed) return nullptr;
+        cudaStreamSynchronize(c->st);
+        cudaMemPool_t pool;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    }
+}
+
 // Encode 0/1 masks (value `scale` on the listed slots) into Montgomery NTT
 // form over the first np primes of the context: out [count][np][N].
 static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int> *> &dsts, u64 scale, u64 *out) {

@@ -67,13 +67,7 @@ int cuda_check(Ctx *c, const char *where) {
 }
 
 u64 *dalloc(Ctx *c, size_t words) {
-    void *p = nullptr;
-    if (words == 0) words = 1;
-    if (cudaMallocAsync(&p, words * 8, c->st) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return (u64 *)p;
+    return (u64 *)dalloc_evicting(c, std::max<size_t>(words, 1) * 8);
 }
 
 void dfree(Ctx *c, void *p) {

@@ -350,6 +350,7 @@ void release_plan(Ctx *c, BatchPlan *P);
 // Device workspace one product adds to a batch (admission estimate).
 size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg);
 void free_plans(Ctx *c);
+void *dalloc_evicting(Ctx *c, size_t bytes);
 hegmm_ct *new_ct(Ctx *c, int level);
 u64 galois_of(Ctx *c, long long z);
 int ensure_galois_key(Ctx *c, u64 g);

@@ -202,12 +202,16 @@ int hegmm_server_create(hegmm_ctx *h, const hegmm_server_opts *opts, hegmm_serve
     s->o = o;
     s->arena_cap = (size_t)(o.mem_budget / (uint64_t)o.streams) & ~(size_t)255;
     for (int i = 0; i < o.streams; i++) {
-        cudaStream_t st;
+        cudaStream_t st = nullptr;
         void *a = nullptr;
+        // arenas come from the context's stream-ordered pool, which also
+        // holds what evicted masks and finished plans gave back
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMalloc(&a, s->arena_cap) != cudaSuccess) {
+            !(a = dalloc_evicting(c, s->arena_cap))) {
             cudaGetLastError();
-            for (size_t k = 0; k < s->arena.size(); k++) cudaFree(s->arena[k]);
+            for (size_t k = 0; k < s->arena.size(); k++) cudaFreeAsync(s->arena[k], c->st);
+            for (auto made : s->streams) cudaStreamDestroy(made);
+            if (st) cudaStreamDestroy(st);
             delete s;
             return set_err(c, HEGMM_ENOMEM, "server streams / workspace");
         }
@@ -298,7 +302,7 @@ void hegmm_server_destroy(hegmm_server *s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (char *a : s->arena) cudaFree(a);
+    for (char *a : s->arena) cudaFreeAsync(a, s->c->st);
     cudaEventDestroy(s->inputs_ready);
     delete s;
 }
