@@ -360,11 +360,20 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def kernel_source_sha():
+    """Hash of the sources the stored ncu traffic ratio was taken on (the
+    kernels and their device arithmetic)."""
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2405_02238_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
 def run_product(args):
-    """One product of --shape on the medium ring, run twice; prints the
-    second run's per-kernel times (the small case of the ncu captures: the
-    second product's launches are the captured ones, about 2 GB on the
-    device)."""
+    """One product of --shape on the medium ring, run once and then --reps
+    times; prints the per-kernel times of the repeated runs (the small case
+    of the ncu captures: with --reps 1 the second product's launches are the
+    captured ones, about 2 GB on the device)."""
     import torch
 
     from paper_2405_02238_gb300 import build as B
@@ -379,6 +388,8 @@ def run_product(args):
     ctx.hegmm_set_keyswitch_mode(KS_MODES[args.ks_mode])
     if args.lt_kernel >= 0:
         ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, args.lt_kernel)
+    if args.lt_one >= 0:
+        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, args.lt_one)
     m, l, n = (int(v) for v in args.shape.lower().split("x"))
     A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
     ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
@@ -388,7 +399,8 @@ def run_product(args):
     torch.cuda.synchronize()
     ctx.hegmm_kernel_reset()
     ctx.hegmm_set_timing(True)
-    c, _ = ctx.hegmm_matmul(ca, cb, m, l, n, args.alg)
+    for _ in range(max(1, args.reps)):
+        c, _ = ctx.hegmm_matmul(ca, cb, m, l, n, args.alg)
     torch.cuda.synchronize()
     ctx.hegmm_set_timing(False)
     if not (ctx.hegmm_decrypt(c, m, l, n, args.alg).astype(np.int64) == (A @ Bm) % pre.t).all():
@@ -396,7 +408,8 @@ def run_product(args):
     ks = {k: {"ms": v[0], "launches": v[1], "algorithmic_bytes": v[2], "butterflies": v[3]}
           for k, v in ctx.hegmm_kernel_stats().items() if v[1]}
     print(json.dumps({"workload": "product %dx%dx%d, algorithm %d, medium ring" % (m, l, n, args.alg),
-                      "keyswitch_mode": args.ks_mode, "lt_kernel": args.lt_kernel, "kernels": ks}))
+                      "keyswitch_mode": args.ks_mode, "lt_kernel": args.lt_kernel, "lt_one": args.lt_one, "reps": args.reps,
+                      "kernels": ks}))
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -417,6 +430,9 @@ def main():
     ap.add_argument("--alg", type=int, default=1, help="algorithm of --workload product (1, 2; 0 = auto)")
     ap.add_argument("--lt-kernel", type=int, default=-1,
                     help="--workload product: HEGMM_TUNE_LT_KERNEL variant (-1 keeps the default)")
+    ap.add_argument("--reps", type=int, default=1, help="--workload product: timed products after the first")
+    ap.add_argument("--lt-one", type=int, default=-1,
+                    help="--workload product: HEGMM_TUNE_LT_ONE one-output kernel (-1 keeps the default)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--max-requests", type=int, default=1000)
@@ -642,7 +658,7 @@ def main():
     name = max(stats.items(), key=lambda kv: kv[1][0])[0]
     roof = roofline(name)
     roof["traffic"] = None
-    src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2405_02238_gb300", "csrc", "kernels.cu"), "rb").read()).hexdigest()[:12]
+    src_sha = kernel_source_sha()
     tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tfile):
         try:

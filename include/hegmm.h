@@ -203,9 +203,11 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     mbarriers), 2 CTAs per SM, for dnum <= 8 (else variant 0); 7 = the
  *     same with a producer warp and full / empty mbarriers over 3 stages
  *     instead of a block barrier per entry.
- *   HEGMM_TUNE_LT_STAGED1: with variant 6, 1 stages the items of one output
- *     the same way (3 CTAs per SM); 0 (default, measured faster at
- *     N = 2^13) keeps them on plain loads. */
+ *   HEGMM_TUNE_LT_ONE: kernel of the items of one output: 0 (default) plain
+ *     loads, 6 CTAs per SM (40 registers); 1 = key rows and masks staged by
+ *     bulk asynchronous copies, 3 CTAs per SM (only with variants 6 and 7,
+ *     else as 0); 2 = plain loads, 5 CTAs per SM (48 registers);
+ *     3 = plain loads, 4 CTAs per SM (64 registers). */
 #define HEGMM_TUNE_LT_KERNEL 3
 /*   HEGMM_TUNE_GIANT_COST: the cost of one giant rotation, in baby key
  *     switches, in the greedy rule of HEGMM_KS_SHARED (1..65536, default 8).
@@ -219,7 +221,7 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     its second call on; 0 launches kernel by kernel.  While per-kernel
  *     timing is on (hegmm_set_timing) plans always run kernel by kernel. */
 #define HEGMM_TUNE_GRAPHS 5
-#define HEGMM_TUNE_LT_STAGED1 6
+#define HEGMM_TUNE_LT_ONE 6
 /*   HEGMM_TUNE_WAIT_LIMIT: polls of every bounded mbarrier wait of the staged
  *     kernels (default 2^22, about a second); when one runs out the kernel
  *     stops, drains its copies and the next synchronising call reports
@@ -240,11 +242,12 @@ int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A,
 
 /* Autotuner of the bit-neutral tuning knobs: runs the given products (as
  * hegmm_matmul_batch_algs would) under every candidate (kernel variant 0, 3,
- * 6, 7; entries per item 16, 32, 64; staged one-output items with 6 / 7),
- * each timed over reps calls with CUDA events on the context stream after a
- * plan-building and a graph-capturing call, and keeps the fastest in the
- * context.  chosen (may be NULL) receives {kernel variant, entries per item,
- * staged one-output items}.  Results stay bit for bit the same (every
+ * 6, 7; entries per item 16, 32, 64; one-output kernel 0, and 1 with
+ * variants 6 / 7), then, from the fastest, the one-output kernels 2 and 3;
+ * each candidate is timed over reps calls with CUDA events on the context
+ * stream after a plan-building and a graph-capturing call, and the fastest
+ * is kept in the context.  chosen (may be NULL) receives {kernel variant,
+ * entries per item, one-output kernel}.  Results stay bit for bit the same (every
  * candidate is an execution order of the same sums).  Only the
  * HEGMM_KS_DOUBLE kernels have knobs; in single mode it returns at once.
  * Cached product plans are released (they are rebuilt on the next call). */

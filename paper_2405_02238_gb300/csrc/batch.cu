@@ -1262,7 +1262,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(dbl ? c->lt_chunk : 0);
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back(dbl ? c->lt_kernel : 0);  // launch choices are baked into a plan's graph
-    key.push_back(dbl ? c->lt_staged1 : 0);
+    key.push_back(dbl ? c->lt_one : 0);
     key.push_back(c->wait_limit);  // kernel arguments captured in the graph
     key.push_back(c->test_drop_entry);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
@@ -1348,12 +1348,12 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (!h || count <= 0 || !A || !B || !mln) return HEGMM_EINVAL;
     Ctx *c = &h->c;
     if (reps < 1) reps = 3;
-    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_staged1;
+    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one;
     auto report = [&]() {
         if (chosen) {
             chosen[0] = c->lt_kernel;
             chosen[1] = c->lt_chunk;
-            chosen[2] = c->lt_staged1;
+            chosen[2] = c->lt_one;
         }
         return HEGMM_OK;
     };
@@ -1376,36 +1376,46 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bk = k0, bc = ch0, bs = s0, rc = HEGMM_OK;
+    // times one candidate; false when a run failed (rc holds the error)
+    auto trial = [&](int kv, int chunk, int one) {
+        c->lt_kernel = kv;
+        c->lt_chunk = chunk;
+        c->lt_one = one;
+        for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
+        if (rc) return false;
+        cudaEventRecord(e0, c->st);
+        for (int r = 0; r < reps && !rc; r++) rc = run();
+        cudaEventRecord(e1, c->st);
+        if (rc || cudaEventSynchronize(e1) != cudaSuccess) return false;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bk = kv;
+            bc = chunk;
+            bs = one;
+        }
+        drop_plans();
+        return true;
+    };
+    bool ok = true;
     for (int kv : {0, 3, 6, 7})
         for (int chunk : {16, 32, 64})
-            for (int st : {0, 1}) {
-                if (st && kv < 6) continue;  // staging one-output items only exists with variants 6 and 7
-                c->lt_kernel = kv;
-                c->lt_chunk = chunk;
-                c->lt_staged1 = st;
-                for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
-                if (rc) break;
-                cudaEventRecord(e0, c->st);
-                for (int r = 0; r < reps && !rc; r++) rc = run();
-                cudaEventRecord(e1, c->st);
-                if (rc || cudaEventSynchronize(e1) != cudaSuccess) break;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    bk = kv;
-                    bc = chunk;
-                    bs = st;
-                }
-                drop_plans();
+            for (int one : {0, 1}) {
+                if (one && kv < 6) continue;  // staging one-output items only exists with variants 6 and 7
+                if (ok) ok = trial(kv, chunk, one);
             }
+    // the plain one-output kernel at lower occupancy, with the best of the rest
+    if (ok && bs == 0)
+        for (int one : {2, 3})
+            if (ok) ok = trial(bk, bc, one);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_plans();
     c->timing = timing;
     c->lt_kernel = rc ? k0 : bk;
     c->lt_chunk = rc ? ch0 : bc;
-    c->lt_staged1 = rc ? s0 : bs;
+    c->lt_one = rc ? s0 : bs;
     if (rc) return rc;
     return report();
 }
@@ -1439,9 +1449,9 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         c->giant_cost = (int)value;
         return HEGMM_OK;
     }
-    if (knob == HEGMM_TUNE_LT_STAGED1) {
-        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "lt_staged1 must be 0 or 1");
-        c->lt_staged1 = (int)value;
+    if (knob == HEGMM_TUNE_LT_ONE) {
+        if (value < 0 || value > 3) return set_err(c, HEGMM_EINVAL, "lt_one must be in 0..3");
+        c->lt_one = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_WAIT_LIMIT) {

@@ -50,11 +50,39 @@ struct Acc {
     u64 lo, hi;
 };
 
+// a += x y (exact 128-bit sum).  On the device the four 32 x 32-bit partial
+// products go straight into the accumulator's four words through
+// carry-chained multiply-adds: x0 y0 and x1 y1 in one chain, then the two
+// cross products at 2^32.
 HDI void mac(Acc &a, u64 x, u64 y) {
+#ifdef __CUDA_ARCH__
+    asm("{\n\t"
+        ".reg .u32 x0, x1, y0, y1, a0, a1, a2, a3;\n\t"
+        "mov.b64 {x0, x1}, %2;\n\t"
+        "mov.b64 {y0, y1}, %3;\n\t"
+        "mov.b64 {a0, a1}, %0;\n\t"
+        "mov.b64 {a2, a3}, %1;\n\t"
+        "mad.lo.cc.u32 a0, x0, y0, a0;\n\t"
+        "madc.hi.cc.u32 a1, x0, y0, a1;\n\t"
+        "madc.lo.cc.u32 a2, x1, y1, a2;\n\t"
+        "madc.hi.u32 a3, x1, y1, a3;\n\t"
+        "mad.lo.cc.u32 a1, x0, y1, a1;\n\t"
+        "madc.hi.cc.u32 a2, x0, y1, a2;\n\t"
+        "addc.u32 a3, a3, 0;\n\t"
+        "mad.lo.cc.u32 a1, x1, y0, a1;\n\t"
+        "madc.hi.cc.u32 a2, x1, y0, a2;\n\t"
+        "addc.u32 a3, a3, 0;\n\t"
+        "mov.b64 %0, {a0, a1};\n\t"
+        "mov.b64 %1, {a2, a3};\n\t"
+        "}"
+        : "+l"(a.lo), "+l"(a.hi)
+        : "l"(x), "l"(y));
+#else
     u64 lo = x * y, hi = mulhi(x, y);
     u64 n = a.lo + lo;
     a.hi += hi + (n < lo ? 1 : 0);
     a.lo = n;
+#endif
 }
 
 // (hi 2^64 + lo) 2^-64 mod q for a value below q 2^64.

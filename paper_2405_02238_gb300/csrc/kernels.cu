@@ -916,10 +916,14 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
     k_lt_grp<G, MB, RED><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it)
         const bool staged = (c->lt_kernel == 6 || c->lt_kernel == 7) && nd <= TMA_MAX_ND;
         if (group == 1) {  // items of one output
-            if (staged && c->lt_staged1) {
+            if (staged && c->lt_one == 1) {
                 const size_t smem = (2 * (size_t)(2 * nd + 1) * 256 + 2) * 8;
                 k_lt_grp_tma<1, 3><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it,
                                                                c->d_err, c->wait_limit, c->test_drop_entry);
+            } else if (c->lt_one == 2) {
+                HG_LTG(1, 5, false);
+            } else if (c->lt_one == 3) {
+                HG_LTG(1, 4, false);
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }

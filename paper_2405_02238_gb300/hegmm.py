@@ -20,7 +20,7 @@ HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
-TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_STAGED1 = 1, 2, 3, 4, 5, 6
+TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_ONE = 1, 2, 3, 4, 5, 6
 TUNE_WAIT_LIMIT, TUNE_TEST_DROP = 7, 8
 ROLE_A, ROLE_B = 0, 1
 
@@ -276,7 +276,7 @@ class Context:
         self._check(self.lib.hegmm_autotune(self.h, n, pa, pb, mln.ctypes.data_as(intp),
                                             None if al is None else al.ctypes.data_as(intp), int(reps),
                                             chosen.ctypes.data_as(intp)), "autotune")
-        return {"lt_kernel": int(chosen[0]), "lt_chunk": int(chosen[1]), "lt_staged1": int(chosen[2])}
+        return {"lt_kernel": int(chosen[0]), "lt_chunk": int(chosen[1]), "lt_one": int(chosen[2])}
 
     def hegmm_set_tuning(self, knob: int, value: int):
         self._check(self.lib.hegmm_set_tuning(self.h, int(knob), int(value)), "set_tuning")

@@ -165,14 +165,17 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
     run_both(H, "tiny", 4, 8, 6, alg, *W.TINY_RANGE, mode=mode)
 
 
-@pytest.mark.parametrize("chunk,variant,fused", [(1, 0, 1), (3, 1, 1), (4096, 2, 1), (32, 3, 1), (5, 4, 1), (32, 5, 1),
-                                                  (32, 6, 1), (3, 6, 1), (32, 7, 1), (2, 7, 1), (32, 0, 0)])
-def test_double_mode_executor_settings(H, chunk, variant, fused):
-    # work-item size, fused-kernel variant and the chunked path change no bit
+@pytest.mark.parametrize("chunk,variant,fused,one", [(1, 0, 1, 0), (3, 1, 1, 0), (4096, 2, 1, 0), (32, 3, 1, 0),
+                                                      (5, 4, 1, 0), (32, 5, 1, 0), (32, 6, 1, 0), (3, 6, 1, 1),
+                                                      (32, 7, 1, 0), (2, 7, 1, 1), (32, 7, 1, 2), (5, 0, 1, 3),
+                                                      (32, 0, 0, 0)])
+def test_double_mode_executor_settings(H, chunk, variant, fused, one):
+    # work-item size, fused-kernel variants and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
     ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, chunk)
     ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, variant)
     ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, fused)
+    ctx.hegmm_set_tuning(H.TUNE_LT_ONE, one)
     try:
         run_both(H, "tiny", 4, 8, 6, 1, *W.TINY_RANGE, mode="double")
         run_both(H, "tiny", 5, 12, 7, 1, *W.TINY_RANGE, mode="double", seed=3)
@@ -182,6 +185,7 @@ def test_double_mode_executor_settings(H, chunk, variant, fused):
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
         ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 6)
         ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, 1)
+        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 0)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 1), (3, 3, 3), (5, 12, 7), (9, 4, 11), (7, 9, 2), (2, 5, 7),
