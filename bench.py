@@ -390,6 +390,8 @@ def run_product(args):
         ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, args.lt_kernel)
     if args.lt_one >= 0:
         ctx.hegmm_set_tuning(H.TUNE_LT_ONE, args.lt_one)
+    if args.lt_chunk >= 0:
+        ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, args.lt_chunk)
     m, l, n = (int(v) for v in args.shape.lower().split("x"))
     A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
     ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
@@ -429,10 +431,12 @@ def main():
     ap.add_argument("--shape", default="16x32x24", help="m x l x n of --workload product")
     ap.add_argument("--alg", type=int, default=1, help="algorithm of --workload product (1, 2; 0 = auto)")
     ap.add_argument("--lt-kernel", type=int, default=-1,
-                    help="--workload product: HEGMM_TUNE_LT_KERNEL variant (-1 keeps the default)")
+                    help="HEGMM_TUNE_LT_KERNEL variant (-1: autotuned, or the default for --workload product); "
+                         "--lt-kernel / --lt-chunk / --lt-one given replace the autotuner")
+    ap.add_argument("--lt-chunk", type=int, default=-1, help="HEGMM_TUNE_LT_CHUNK entries per item (-1: autotuned)")
     ap.add_argument("--reps", type=int, default=1, help="--workload product: timed products after the first")
     ap.add_argument("--lt-one", type=int, default=-1,
-                    help="--workload product: HEGMM_TUNE_LT_ONE one-output kernel (-1 keeps the default)")
+                    help="HEGMM_TUNE_LT_ONE one-output kernel (-1: autotuned, or the default for --workload product)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--max-requests", type=int, default=1000)
@@ -516,9 +520,18 @@ def main():
             cnts.append(cnt)
         return outs, cnts
 
-    # the library's autotuner picks the bit-neutral kernel knobs on this workload
+    # the library's autotuner picks the bit-neutral kernel knobs on this
+    # workload, unless they are given (a profiler's serialised launches would
+    # mislead the autotuner: profiling runs pass the plain run's choice)
     tuning = None
-    if not args.no_autotune:
+    fixed = {k: v for k, v in (("lt_kernel", args.lt_kernel), ("lt_chunk", args.lt_chunk), ("lt_one", args.lt_one))
+             if v >= 0}
+    if fixed:
+        knob = {"lt_kernel": H.TUNE_LT_KERNEL, "lt_chunk": H.TUNE_LT_CHUNK, "lt_one": H.TUNE_LT_ONE}
+        for k, v in fixed.items():
+            ctx.hegmm_set_tuning(knob[k], v)
+        tuning = dict(fixed, given=True)
+    elif not args.no_autotune:
         tuning = ctx.hegmm_autotune([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs,
                                     reps=3 if len(prods) <= 64 else 1)
     # warm-up (builds plans, masks) and a correctness check of every product
