@@ -67,12 +67,22 @@ static inline dim3 grid_coef(int N, int y, int z) { return dim3((unsigned)((N + 
 // Up to N = 2^13 two CTAs of 512 threads share an SM (registers 2 x 512 x 64,
 // shared memory 2 x 70 KB), so one CTA's loads and barriers overlap the
 // other's butterflies; at N = 2^14 the 139 KB limb allows one CTA per SM.
+//
+// A launch of no more CTAs than SMs leaves every CTA an SM of its own; there
+// the NT_WIDE form (one radix-8 group per thread and pass, up to 1024
+// threads) halves the latency of each pass at N = 2^13.
 template <int LOGN>
 struct NttCfg {
     static constexpr int N = 1 << LOGN;
     static constexpr int NT = LOGN >= 14 ? 1024 : ((N / 8) < 512 ? (N / 8) : 512);
-    static constexpr int MINB = LOGN >= 14 ? 1 : 2;
+    static constexpr int NT_WIDE = (N / 8) < 1024 ? (N / 8) : 1024;
     static constexpr size_t SMEM = (size_t)(N + N / 16) * 8;
+};
+
+// CTAs per SM the register budget is set for: two up to 512 threads.
+template <int NT>
+struct NttMinBlocks {
+    static constexpr int V = NT >= 1024 ? 1 : 2;
 };
 
 // Fused pass layout of the kernels below: the first radix-8 pass (stages
@@ -88,9 +98,9 @@ struct NttPasses {
     static constexpr int LAST = LOGN - RL;  // first stage of the last pass
 };
 
-template <int LOGN>
+template <int LOGN, int NT>
 __device__ __forceinline__ void fwd_middle(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, LAST = NttPasses<LOGN>::LAST;
+    constexpr int N = 1 << LOGN, LAST = NttPasses<LOGN>::LAST;
 #pragma unroll
     for (int s0 = 3; s0 < LAST; s0 += 3) {
         for (int g = threadIdx.x; g < N / 8; g += NT) ntt_fwd_group_lazy<3>(sm, g, s0, LOGN, T, q);
@@ -98,9 +108,9 @@ __device__ __forceinline__ void fwd_middle(u64 *sm, const TwPair *__restrict__ T
     }
 }
 
-template <int LOGN>
+template <int LOGN, int NT>
 __device__ __forceinline__ void inv_middle(u64 *sm, const TwPair *__restrict__ T, u64 q) {
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, LAST = NttPasses<LOGN>::LAST;
+    constexpr int N = 1 << LOGN, LAST = NttPasses<LOGN>::LAST;
 #pragma unroll
     for (int u0 = 3; u0 < LAST; u0 += 3) {
         for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, u0, LOGN, T, q);
@@ -113,11 +123,11 @@ __device__ __forceinline__ const TwPair *tw_of(const TwPair *tw, int mi, int inv
     return tw + ((size_t)mi * 2 + inv) * N;
 }
 
-template <int LOGN, bool INV>
-__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(LimbPat p, const ModDev *__restrict__ mods,
-                                                         const TwPair *__restrict__ tw) {
+template <int LOGN, bool INV, int NT>
+__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_ntt(LimbPat p, const ModDev *__restrict__ mods,
+                                                                 const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT, RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
+    constexpr int N = 1 << LOGN, RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
     int mi;
     u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
     const u64 q = mods[mi].q;
@@ -135,7 +145,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(Lim
         __syncthreads();
         for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, 0, LOGN, T, q);
         __syncthreads();
-        inv_middle<LOGN>(sm, T, q);
+        inv_middle<LOGN, NT>(sm, T, q);
         for (int g = threadIdx.x; g < (N >> RL); g += NT) ntt_inv_group_lazy<RL>(sm, g, LAST, LOGN, T, q);
         __syncthreads();
         // scaling by N^-1 with coalesced 16-byte stores
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(Lim
             for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = x[k];
         }
         __syncthreads();
-        fwd_middle<LOGN>(sm, T, q);
+        fwd_middle<LOGN, NT>(sm, T, q);
         for (int g = threadIdx.x; g < (N >> RL); g += NT) {
             u64 x[1 << RL];
 #pragma unroll
@@ -174,13 +184,14 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_ntt(Lim
 // from the coefficient-form dropped limbs; forward NTT in shared memory;
 // epilogue: out_i = (u_i - t y~_i) D^-1 (+ add_i at the automorphism's index).
 // Table layout as k_div_conv (build_div_tab).
-template <int LOGN>
-__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divround_ntt(int nkeep, int ndrop, const ModDev *__restrict__ mods,
-                                                                  const u64 *__restrict__ tab,
-                                                                  const DivDesc *__restrict__ desc,
-                                                                  const TwPair *__restrict__ tw) {
+template <int LOGN, int NT>
+__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nkeep, int ndrop,
+                                                                          const ModDev *__restrict__ mods,
+                                                                          const u64 *__restrict__ tab,
+                                                                          const DivDesc *__restrict__ desc,
+                                                                          const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
+    constexpr int N = 1 << LOGN;
     const int npoly = gridDim.x / nkeep;  // prime-major block order (twiddles stay in L1)
     const int i = blockIdx.x / npoly, b = blockIdx.x - i * npoly;
     const DivDesc d = desc[b];
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divroun
         for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = x[k];
     }
     __syncthreads();
-    fwd_middle<LOGN>(sm, T, M.q);
+    fwd_middle<LOGN, NT>(sm, T, M.q);
     const u64 *k4 = tC + 4 * i;
     const u64 Di = k4[0], Dis = k4[1], tq = k4[2], tqs = k4[3];
     const u64 *ui = d.u + (size_t)i * N;
@@ -240,13 +251,14 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_divroun
 // prologue computes the digit's centred fast base conversion into prime e
 // from the coefficient-form source limbs, then forward NTT, then store.
 // Limb selection follows a LimbPat whose off[] = j * ne + e.
-template <int LOGN>
-__global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha, int L,
-                                                               const ModDev *__restrict__ mods,
-                                                               const u64 *__restrict__ tab, const u64 *__restrict__ xc,
-                                                               long long xc_stride, const TwPair *__restrict__ tw) {
+template <int LOGN, int NT>
+__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha,
+                                                                       int L, const ModDev *__restrict__ mods,
+                                                                       const u64 *__restrict__ tab,
+                                                                       const u64 *__restrict__ xc, long long xc_stride,
+                                                                       const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = NttCfg<LOGN>::NT;
+    constexpr int N = 1 << LOGN;
     const int nouter = p.count / p.inner;  // prime-major block order, as pat_ptr
     const int in = blockIdx.x / nouter, outer = blockIdx.x - in * nouter;
     const int off = p.off[in], j = off / ne, e = off - j * ne;
@@ -279,7 +291,7 @@ __global__ void __launch_bounds__(NttCfg<LOGN>::NT, NttCfg<LOGN>::MINB)k_modup_n
         for (int k = 0; k < 8; k++) sm[pad16(g + k * (N / 8))] = xv[k];
     }
     __syncthreads();
-    fwd_middle<LOGN>(sm, T, R.q);
+    fwd_middle<LOGN, NT>(sm, T, R.q);
     for (int g = threadIdx.x; g < (N >> RL); g += NT) {
         u64 xv[1 << RL];
         const int base = g << RL;
@@ -301,15 +313,20 @@ __global__ void k_modup_own(int lv, int ne, int alpha, int logN, const u64 *__re
     D[o * D_stride + ((size_t)j * ne + e) * N + c] = xn[o * xn_stride + (size_t)e * N + c];
 }
 
-template <int LOGN>
-static int set_smem_attrs() {
+template <int LOGN, int NT>
+static int set_smem_attrs_nt() {
     const int sm = (int)NttCfg<LOGN>::SMEM;
-    if (cudaFuncSetAttribute(k_ntt<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_ntt<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_divround_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_modup_ntt<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_ntt<LOGN, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ntt<LOGN, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_divround_ntt<LOGN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_modup_ntt<LOGN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
         return 1;
     return 0;
+}
+
+template <int LOGN>
+static int set_smem_attrs() {
+    return set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT>() || set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_WIDE>();
 }
 
 static int init_staged_kernels();
@@ -339,11 +356,28 @@ int init_kernels(Ctx *c) {
         default: break;                     \
     }
 
+// Thread count of a launch of `ctas` limb CTAs (NttCfg: the wide form when
+// every CTA has an SM of its own).
+template <int LG>
+static bool ntt_wide(const Ctx *c, long long ctas) {
+    return NttCfg<LG>::NT_WIDE > NttCfg<LG>::NT && ctas <= c->nsm;
+}
+
+template <int LG, bool INV>
+static void launch_ntt(Ctx *c, const LimbPat &p, const TwPair *tw) {
+    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr size_t SM = NttCfg<LG>::SMEM;
+    if (ntt_wide<LG>(c, p.count))
+        k_ntt<LG, INV, NW><<<p.count, NW, SM, c->st>>>(p, c->d_mods, tw);
+    else
+        k_ntt<LG, INV, NT><<<p.count, NT, SM, c->st>>>(p, c->d_mods, tw);
+}
+
 int ntt_fwd(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
-    HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, false><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
+    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, false>(c, p, tw)));
     return cuda_check(c, "ntt_fwd");
 }
 
@@ -351,8 +385,18 @@ int ntt_inv(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
-    HG_DISPATCH_LOGN(c->logN, (k_ntt<LG, true><<<p.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(p, c->d_mods, tw)));
+    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, true>(c, p, tw)));
     return cuda_check(c, "ntt_inv");
+}
+
+template <int LG>
+static void launch_divround(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
+    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr size_t SM = NttCfg<LG>::SMEM;
+    if (ntt_wide<LG>(c, grid))
+        k_divround_ntt<LG, NW><<<grid, NW, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw);
+    else
+        k_divround_ntt<LG, NT><<<grid, NT, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw);
 }
 
 int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
@@ -362,9 +406,21 @@ int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
              (double)npoly * tab.nkeep * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     const int grid = npoly * tab.nkeep;
-    HG_DISPATCH_LOGN(c->logN, (k_divround_ntt<LG><<<grid, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
-                                  tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw)));
+    HG_DISPATCH_LOGN(c->logN, (launch_divround<LG>(c, grid, tab, d_desc, tw)));
     return cuda_check(c, "divround_ntt");
+}
+
+template <int LG>
+static void launch_modup(Ctx *c, const LimbPat &nonown, const ModUpTab &tb, const u64 *xc, long long xc_stride,
+                         const TwPair *tw) {
+    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr size_t SM = NttCfg<LG>::SMEM;
+    if (ntt_wide<LG>(c, nonown.count))
+        k_modup_ntt<LG, NW><<<nonown.count, NW, SM, c->st>>>(nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods,
+                                                             tb.d, xc, xc_stride, tw);
+    else
+        k_modup_ntt<LG, NT><<<nonown.count, NT, SM, c->st>>>(nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods,
+                                                             tb.d, xc, xc_stride, tw);
 }
 
 int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, long long xc_stride, const u64 *xn,
@@ -372,8 +428,7 @@ int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, 
     Launch t(c, K_MODUP, (double)n * (tb.lv + 2.0 * (tb.nd * tb.ne)) * c->limb_bytes(), nonown.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
     if (nonown.count > 0)
-        HG_DISPATCH_LOGN(c->logN, (k_modup_ntt<LG><<<nonown.count, NttCfg<LG>::NT, NttCfg<LG>::SMEM, c->st>>>(
-                                      nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods, tb.d, xc, xc_stride, tw)));
+        HG_DISPATCH_LOGN(c->logN, (launch_modup<LG>(c, nonown, tb, xc, xc_stride, tw)));
     k_modup_own<<<grid_coef(c->N, tb.lv, n), 256, 0, c->st>>>(tb.lv, tb.ne, c->alpha, c->logN, xn, xn_stride, D,
                                                               D_stride);
     return cuda_check(c, "modup_ntt");
