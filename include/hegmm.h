@@ -240,6 +240,35 @@ int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                             const int *mln, const int *algs, hegmm_ct **C);
 
+/* Sums of products, the building block of blocked products (Section 4.4,
+ * Table 4: a matrix larger than one ciphertext is split into blocks and
+ * C_ij = sum_k A_ik B_kj).  Products are given as for hegmm_matmul_batch_algs
+ * (algs may be NULL: AUTO); group[p] in [0, ngroups) names the sum product p
+ * joins, and C[g] (ngroups new ciphertexts, owned by the caller) receives
+ * the HE-Add of the results of group g's products.  Every group needs at
+ * least one product, and all products of a group the same result layout
+ * (hegmm_decrypt decodes C[g] with any member's m, l, n, alg); Algorithm 1
+ * places C_ij at slot i + j m for every l.  Errors: HEGMM_EINVAL (bad
+ * group index, empty group, bad algorithm), HEGMM_ESHAPE (a shape that does
+ * not fit, or layouts that differ within a group), HEGMM_ENOKEY, HEGMM_ENOMEM;
+ * on error every C[g] is NULL.  All products run in one batched call, the
+ * sums in one more launch. */
+int hegmm_matmul_sum(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
+                     const int *mln, const int *algs, const int *group, int ngroups, hegmm_ct **C);
+
+/* Blocked product under Algorithm 1 (Section 4.4): an (sum rows) x
+ * (sum inner) matrix times an (sum inner) x (sum cols) matrix, split into
+ * nr x nk and nk x nc blocks.  A[i nk + k] encrypts block A_ik (rows[i] x
+ * inner[k]) and B[k nc + j] block B_kj (inner[k] x cols[j]), each encoded
+ * for Algorithm 1 with its own shape (hegmm_encode role A with m = rows[i],
+ * l = inner[k]; role B with l = inner[k], n = cols[j]; the other dimension
+ * does not change these layouts).  C[i nc + j] receives sum_k A_ik B_kj;
+ * decrypt it with hegmm_decrypt(ctx, C, rows[i], inner[0], cols[j], 1).
+ * Keys: those of every (rows[i], inner[k], cols[j]) under Algorithm 1.
+ * Block sizes must be positive; errors as hegmm_matmul_sum. */
+int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows, const int *inner, const int *cols,
+                         const hegmm_ct *const *A, const hegmm_ct *const *B, hegmm_ct **C);
+
 /* Autotuner of the bit-neutral tuning knobs: runs the given products (as
  * hegmm_matmul_batch_algs would) under every candidate (kernel variant 0, 3,
  * 6, 7; entries per item 16, 32, 64; one-output kernel 0, and 1 with

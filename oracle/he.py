@@ -601,6 +601,26 @@ class HEGMM:
             out = o.add(out, o.rotate(C, z))
         return out
 
+    def sum_products(self, items: List[Tuple[SL.Plan, np.ndarray, np.ndarray]]) -> np.ndarray:
+        """The HE-Add (Section 2.1) of the results of products that share a
+        result layout, in list order: the block sum C_ij = sum_k A_ik B_kj of
+        Section 4.4.  items: [(plan, ctA, ctB)]."""
+        if len({SL.result_layout(p) for p, _, _ in items}) != 1:
+            raise ValueError("products of one sum have different result layouts")
+        acc = None
+        for plan, a, b in items:
+            c = self.run(plan, a, b)
+            acc = c if acc is None else self.o.add(acc, c)
+        return acc
+
+    def blocked(self, rows: List[int], inner: List[int], cols: List[int], ctA, ctB):
+        """Blocked product of Section 4.4 under Algorithm 1: ctA[i][k] and
+        ctB[k][j] encrypt the Algorithm 1 layouts of blocks A_ik and B_kj;
+        returns C[i][j] = sum over k (ascending) of the products A_ik B_kj."""
+        return [[self.sum_products([(SL.make_plan(rows[i], inner[k], cols[j], 1), ctA[i][k], ctB[k][j])
+                                    for k in range(len(inner))])
+                 for j in range(len(cols))] for i in range(len(rows))]
+
     def result(self, plan: SL.Plan, ct: np.ndarray) -> np.ndarray:
         slots = self.o.decrypt_slots(ct)
         Cm = np.zeros((plan.m, plan.n), dtype=np.int64)

@@ -17,6 +17,9 @@ Paper references (arXiv 2405.02238):
 * Theorems 1-4 (Section 3.2.1) -- diagonal-count bounds.
 * Algorithm 1 (HEGMM) and Algorithm 2 (HEGMM-Enhanced), Theorems 5-6
   (Section 3.3).
+* Section 4.4 and Table 4 -- blocking: a product too large for one
+  ciphertext is split into blocks, C_ij = sum_k A_ik B_kj, each block
+  product one HEGMM product and the sum over k one HE-Add per term.
 
 Readings of points the paper leaves open (each also listed in the design
 notes):
@@ -482,6 +485,61 @@ def run_slots(plan: Plan, A: np.ndarray, B: np.ndarray, S: int, t: int) -> np.nd
         for j in range(plan.n):
             C[i, j] = out[plan.result_slot(i, j)]
     return C
+
+
+def block_bounds(sizes: List[int]) -> List[Tuple[int, int]]:
+    """[start, stop) of consecutive blocks of the given sizes (Section 4.4)."""
+    out, s = [], 0
+    for b in sizes:
+        out.append((s, s + b))
+        s += b
+    return out
+
+
+def result_layout(plan: Plan) -> Tuple[int, int, str]:
+    """What decides where C_ij sits: the result shape and the flattening order."""
+    return plan.res_shape[0], plan.res_shape[1], plan.order
+
+
+def run_blocked_slots(rows: List[int], inner: List[int], cols: List[int], A: np.ndarray, B: np.ndarray,
+                      S: int, t: int, alg: int = 1) -> np.ndarray:
+    """The blocked product of Section 4.4 on slot vectors: for every output
+    block (i, j) the slot vectors of the products A_ik B_kj (k ascending) are
+    added slot by slot, then C_ij is read from the common result slots.
+    Every product of a block must share the result layout (checked)."""
+    rb, kb, cb = block_bounds(rows), block_bounds(inner), block_bounds(cols)
+    assert A.shape == (rb[-1][1], kb[-1][1]) and B.shape == (kb[-1][1], cb[-1][1])
+    C = np.zeros((rb[-1][1], cb[-1][1]), dtype=np.int64)
+    for (r0, r1) in rb:
+        for (c0, c1) in cb:
+            acc, lay, ref = np.zeros(S, dtype=np.int64), None, None
+            for (k0, k1) in kb:
+                plan = make_plan(r1 - r0, k1 - k0, c1 - c0, alg)
+                if lay is None:
+                    lay, ref = result_layout(plan), plan
+                elif result_layout(plan) != lay:
+                    raise ValueError("block products of one output block have different result layouts")
+                acc = (acc + slot_vector(plan, A[r0:r1, k0:k1], B[k0:k1, c0:c1], S, t)) % t
+            for i in range(r1 - r0):
+                for j in range(c1 - c0):
+                    C[r0 + i, c0 + j] = acc[ref.result_slot(i, j)]
+    return C
+
+
+def slot_vector(plan: Plan, A: np.ndarray, B: np.ndarray, S: int, t: int) -> np.ndarray:
+    """The whole result slot vector of ``run_slots`` (before reading C)."""
+    a = np.zeros(S, dtype=np.int64)
+    b = np.zeros(S, dtype=np.int64)
+    va, vb = plan.a_layout(A) % t, plan.b_layout(B) % t
+    a[: len(va)] = va
+    b[: len(vb)] = vb
+    acc = np.zeros(S, dtype=np.int64)
+    for e, o in plan.iters:
+        acc = (acc + apply_lt(a, e, S, t) * apply_lt(b, o, S, t)) % t
+    out = acc.copy()
+    for z in plan.extract:
+        out = (out + np.roll(acc, -z)) % t
+    return out
 
 
 def theorem5_blocks(m: int, l: int, k: int, t: int) -> List[int]:

@@ -1318,6 +1318,79 @@ int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *con
     return matmul_run(c, count, A, B, mln, alg, algs, C, cnt, true, nullptr);
 }
 
+// Sums of products (the blocking of Section 4.4): all products in one
+// batched run, then one launch that adds each group's results.
+int matmul_sum(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+               const int *algs, const int *group, int ngroups, hegmm_ct **C) {
+    for (int g = 0; g < ngroups; g++) C[g] = nullptr;
+    if (ngroups <= 0) return set_err(c, HEGMM_EINVAL, "no groups");
+    // members of every group, and one result layout per group
+    std::vector<std::vector<int>> members((size_t)ngroups);
+    std::vector<std::array<int, 3>> layout((size_t)ngroups, {0, 0, 0});
+    for (int p = 0; p < count; p++) {
+        const int g = group[p];
+        if (g < 0 || g >= ngroups) return set_err(c, HEGMM_EINVAL, "group index out of range");
+        const int m = mln[3 * p], l = mln[3 * p + 1], n = mln[3 * p + 2];
+        const int ai = algs ? algs[p] : HEGMM_ALG_AUTO;
+        if (ai < 0 || ai > 2) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1 or 2");
+        const int a = resolve_alg(m, l, n, ai, c->S);
+        if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+        int rows, cols;
+        bool col;
+        result_layout(m, l, n, a, rows, cols, col);
+        const std::array<int, 3> lay{rows, cols, col ? 1 : 0};
+        if (members[g].empty())
+            layout[g] = lay;
+        else if (layout[g] != lay)
+            return set_err(c, HEGMM_ESHAPE, "products of one group have different result layouts");
+        members[g].push_back(p);
+    }
+    for (int g = 0; g < ngroups; g++)
+        if (members[g].empty()) return set_err(c, HEGMM_EINVAL, "empty group");
+    std::vector<hegmm_ct *> R((size_t)count, nullptr);
+    int rc = matmul_run(c, count, A, B, mln, HEGMM_ALG_AUTO, algs, R.data(), nullptr, true, nullptr);
+    if (rc) return rc;
+    const int lv = R[0]->level;
+    std::vector<const u64 *> src;
+    std::vector<int> first{0};
+    std::vector<u64 *> out;
+    for (int g = 0; g < ngroups && !rc; g++) {
+        for (int p : members[g]) src.push_back(R[p]->d);
+        first.push_back((int)src.size());
+        C[g] = new_ct(c, lv);
+        if (!C[g]) rc = set_err(c, HEGMM_ENOMEM, "result ciphertext");
+        else out.push_back(C[g]->d);
+    }
+    // pointer and offset arrays, uploaded in one block
+    const size_t nb_src = src.size() * sizeof(u64 *), nb_out = out.size() * sizeof(u64 *);
+    const size_t nb = nb_src + nb_out + first.size() * sizeof(int);
+    u64 *blk = rc ? nullptr : dalloc(c, (nb + 7) / 8);
+    if (!rc && !blk) rc = set_err(c, HEGMM_ENOMEM, "group sum descriptors");
+    if (!rc) {
+        std::vector<char> h(nb);
+        memcpy(h.data(), src.data(), nb_src);
+        memcpy(h.data() + nb_src, out.data(), nb_out);
+        memcpy(h.data() + nb_src + nb_out, first.data(), first.size() * sizeof(int));
+        if (cudaMemcpyAsync(blk, h.data(), nb, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+            rc = cuda_check(c, "group sum descriptors");
+        // pageable source: the copy is staged before cudaMemcpyAsync returns
+    }
+    if (!rc) {
+        char *b = (char *)blk;
+        rc = sum_groups(c, lv, (const u64 *const *)b, (const int *)(b + nb_src + nb_out), (u64 *const *)(b + nb_src),
+                        ngroups);
+    }
+    dfree(c, blk);
+    for (auto *r : R) hegmm_ct_destroy(r);
+    if (rc) {
+        for (int g = 0; g < ngroups; g++) {
+            hegmm_ct_destroy(C[g]);
+            C[g] = nullptr;
+        }
+    }
+    return rc;
+}
+
 }  // namespace hg
 
 using namespace hg;
@@ -1341,6 +1414,39 @@ int hegmm_matmul_batch_algs(hegmm_ctx *h, int count, const hegmm_ct *const *A, c
                             const int *mln, const int *algs, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, HEGMM_ALG_AUTO, C, nullptr, algs);
+}
+
+int hegmm_matmul_sum(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                     const int *algs, const int *group, int ngroups, hegmm_ct **C) {
+    if (!h || count <= 0 || !A || !B || !mln || !group || !C) return HEGMM_EINVAL;
+    return matmul_sum(&h->c, count, A, B, mln, algs, group, ngroups, C);
+}
+
+int hegmm_matmul_blocked(hegmm_ctx *h, int nr, int nk, int nc, const int *rows, const int *inner, const int *cols,
+                         const hegmm_ct *const *A, const hegmm_ct *const *B, hegmm_ct **C) {
+    if (!h || nr <= 0 || nk <= 0 || nc <= 0 || !rows || !inner || !cols || !A || !B || !C) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    for (int i = 0; i < nr; i++)
+        if (rows[i] <= 0) return set_err(c, HEGMM_EINVAL, "block sizes must be positive");
+    for (int k = 0; k < nk; k++)
+        if (inner[k] <= 0) return set_err(c, HEGMM_EINVAL, "block sizes must be positive");
+    for (int j = 0; j < nc; j++)
+        if (cols[j] <= 0) return set_err(c, HEGMM_EINVAL, "block sizes must be positive");
+    // products (i, k, j) in group i nc + j, Algorithm 1 (its operand layouts
+    // depend on the block's own shape only, so every block serves each product)
+    const int count = nr * nk * nc;
+    std::vector<const hegmm_ct *> pa, pb;
+    std::vector<int> mln, algs, grp;
+    for (int i = 0; i < nr; i++)
+        for (int j = 0; j < nc; j++)
+            for (int k = 0; k < nk; k++) {
+                pa.push_back(A[i * nk + k]);
+                pb.push_back(B[k * nc + j]);
+                mln.insert(mln.end(), {rows[i], inner[k], cols[j]});
+                algs.push_back(1);
+                grp.push_back(i * nc + j);
+            }
+    return matmul_sum(c, count, pa.data(), pb.data(), mln.data(), algs.data(), grp.data(), nr * nc, C);
 }
 
 int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,

@@ -307,6 +307,9 @@ LimbPat pat_ct(Ctx *c, u64 *base, int npoly, int lv, long long poly_stride_words
 // batched sums (SumDesc list) and the input gather of a batch
 // np = lv (chain primes) or lv + K (extended basis), as for lt_accumulate
 int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np = 0);
+// out[g] = sum of src[first[g] .. first[g + 1]) (ciphertexts [2][lv][N]),
+// device arrays of pointers and offsets.
+int sum_groups(Ctx *c, int lv, const u64 *const *d_src, const int *d_first, u64 *const *d_out, int ngroups);
 // ev[b][slot_pos0[slots[j]]] = value for j in [off[b], off[b+1]) (NTT order mod t)
 int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev);
 int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst);

@@ -1228,6 +1228,30 @@ int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np) {
     return cuda_check(c, "sum_desc");
 }
 
+// Group sums of whole ciphertexts: one thread per coefficient of one limb of
+// one group's output (grid: coefficients x 2 lv limbs x groups).
+__global__ void k_sum_groups(int lv, int logN, const ModDev *__restrict__ mods, const u64 *const *__restrict__ src,
+                             const int *__restrict__ first, u64 *const *__restrict__ out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int pl = blockIdx.y, g = blockIdx.z;
+    const u64 q = mods[pl % lv].q;
+    const size_t o = (size_t)pl * N + c;
+    u64 acc = 0;
+    for (int j = first[g]; j < first[g + 1]; j++) acc = addm(acc, src[j][o], q);
+    out[g][o] = acc;
+}
+
+int sum_groups(Ctx *c, int lv, const u64 *const *d_src, const int *d_first, u64 *const *d_out, int ngroups) {
+    if (ngroups <= 0) return HEGMM_OK;
+    Launch t(c, K_SUM, 0.0);
+    for (int g0 = 0; g0 < ngroups; g0 += kMaxGridZ)
+        k_sum_groups<<<grid_coef(c->N, 2 * lv, std::min(kMaxGridZ, ngroups - g0)), 256, 0, c->st>>>(
+            lv, c->logN, c->d_mods, d_src, d_first + g0, d_out + g0);
+    return cuda_check(c, "sum_groups");
+}
+
 __global__ void k_scatter_slots(const int *__restrict__ off, const int *__restrict__ slots,
                                 const int *__restrict__ pos, u64 value, int N, u64 *__restrict__ ev) {
     const int b = blockIdx.x;

@@ -40,6 +40,19 @@ int alg2_length(int m, int l, int n) {
     return std::max(M * WA, std::max(HB * Np, M * Np));
 }
 
+void result_layout(int m, int l, int n, int alg, int &rows, int &cols, bool &col) {
+    if (alg == 1) {
+        rows = m;
+        cols = n;
+        col = true;
+        return;
+    }
+    char kase;
+    int p, t, WA, HB;
+    alg2_shape(m, l, n, kase, p, t, rows, cols, WA, HB);
+    col = kase != 'B';
+}
+
 int resolve_alg(int m, int l, int n, int alg, int S) {
     if (m <= 0 || l <= 0 || n <= 0) return 0;
     if (alg == 1) return alg1_length(m, l, n) <= S ? 1 : 0;

@@ -76,5 +76,9 @@ int alg2_length(int m, int l, int n);
 // AUTO: Algorithm 2 if it fits S slots, else Algorithm 1, else 0.
 int resolve_alg(int m, int l, int n, int alg, int S);
 HostPlan make_host_plan(int m, int l, int n, int alg);
+// The result layout of a product (alg 1 or 2): C_ij sits at slot
+// i + j rows (col) or i cols + j (!col) of a rows x cols matrix; Algorithm 1
+// gives m x n column-major for every l.
+void result_layout(int m, int l, int n, int alg, int &rows, int &cols, bool &col);
 
 }  // namespace hg

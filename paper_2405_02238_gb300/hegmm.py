@@ -88,6 +88,10 @@ _SIGS = {
                                                ctypes.POINTER(vp)]),
     "hegmm_matmul_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp,
                                           ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_matmul_sum": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp, intp, intp,
+                                        ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_matmul_blocked": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, intp, intp, intp,
+                                            ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]),
     "hegmm_decrypt": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p]),
     "hegmm_decrypt_slots": (ctypes.c_int, [vp, vp, u64p]),
     "hegmm_rotate": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(vp)]),
@@ -340,6 +344,34 @@ class Context:
                                                      None if al is None else al.ctypes.data_as(intp), outs),
                     "matmul_batch_algs")
         return [Ciphertext(self, vp(outs[i])) for i in range(n)]
+
+    def hegmm_matmul_sum(self, As, Bs, shapes, group, ngroups: int, algs=None):
+        """hegmm_matmul_sum: C[g] = sum of the products p with group[p] == g."""
+        n = len(As)
+        pa = (vp * n)(*[a.h for a in As])
+        pb = (vp * n)(*[b.h for b in Bs])
+        mln = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
+        al = None if algs is None else np.ascontiguousarray(np.array(algs, dtype=np.int32))
+        gr = np.ascontiguousarray(np.array(group, dtype=np.int32))
+        outs = (vp * max(1, ngroups))()
+        self._check(self.lib.hegmm_matmul_sum(self.h, n, pa, pb, mln.ctypes.data_as(intp),
+                                              None if al is None else al.ctypes.data_as(intp),
+                                              gr.ctypes.data_as(intp), int(ngroups), outs), "matmul_sum")
+        return [Ciphertext(self, vp(outs[g])) for g in range(ngroups)]
+
+    def hegmm_matmul_blocked(self, rows, inner, cols, A_blocks, B_blocks):
+        """hegmm_matmul_blocked: A_blocks[i][k], B_blocks[k][j] (Algorithm 1
+        encodings); returns C[i][j] = sum_k A_ik B_kj."""
+        nr, nk, nc = len(rows), len(inner), len(cols)
+        pa = (vp * (nr * nk))(*[A_blocks[i][k].h for i in range(nr) for k in range(nk)])
+        pb = (vp * (nk * nc))(*[B_blocks[k][j].h for k in range(nk) for j in range(nc)])
+        r = np.ascontiguousarray(np.array(rows, dtype=np.int32))
+        q = np.ascontiguousarray(np.array(inner, dtype=np.int32))
+        s = np.ascontiguousarray(np.array(cols, dtype=np.int32))
+        outs = (vp * (nr * nc))()
+        self._check(self.lib.hegmm_matmul_blocked(self.h, nr, nk, nc, r.ctypes.data_as(intp), q.ctypes.data_as(intp),
+                                                  s.ctypes.data_as(intp), pa, pb, outs), "matmul_blocked")
+        return [[Ciphertext(self, vp(outs[i * nc + j])) for j in range(nc)] for i in range(nr)]
 
     def hegmm_decrypt(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO) -> np.ndarray:
         out = np.zeros((m, n), dtype=np.uint64)
