@@ -240,6 +240,43 @@ int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                             const int *mln, const int *algs, hegmm_ct **C);
 
+/* Linear transformations of ciphertexts (Eq. lintrans, Section 3.2.1),
+ * evaluated as the paper composes them: out = sum over the diagonals d
+ * (ascending) of HE-CMult(HE-Rot(ct, d), u_d), with the rotations of up to
+ * 64 diagonals sharing one hoisted ModUp; the result keeps ct's level.
+ * Galois keys that are missing are made from the context's secret key.
+ *
+ * hegmm_lintrans: slot j of *out takes slot src[j] of ct for j < count
+ * (src[j] < 0 and slots from count on: 0); 0 <= src[j] < slots, count <=
+ * slots (HEGMM_EINVAL otherwise).  d = src[j] - j mod slots.
+ *
+ * A plain matrix ciphertext holds M (rows x cols) column-major: slot
+ * i + j rows = M_ij.
+ * hegmm_to_layout: ct holds A (m x l, role HEGMM_ROLE_A) or B (l x n, role
+ * HEGMM_ROLE_B) as a plain matrix ciphertext; *out holds the operand layout
+ * hegmm_encode would give for (m, l, n, alg): sigma(A) / tau(B) under
+ * encryption (Section 3.2.2: at most 2 min(m,l) - 1 / 2 min(n,l) - 1
+ * diagonals, Theorems 1-2), and for Algorithm 2 the duplication and
+ * eps^0 / omega^0 as well.
+ * hegmm_from_result: ct is the result of a product (m, l, n, alg); *out
+ * holds C (m x n) as a plain matrix ciphertext, so a product can feed the
+ * next one through hegmm_to_layout (for Algorithm 1 the result already has
+ * this layout and the transformation only clears the other slots).
+ * hegmm_chain_operand: ct is the result of a product (m, l, n, alg); *out
+ * holds that m x n matrix in the layout of operand `role` of the next
+ * product (m2, l2, n2, alg2): (m2, l2) = (m, n) for role A, (l2, n2) =
+ * (m, n) for role B, else HEGMM_EINVAL.  One transformation (the
+ * composition of hegmm_from_result and hegmm_to_layout), so one mask
+ * product's noise: a chain of two products needs about twice the noise
+ * budget of one (the N = 2^14, 8 x 50-bit ring has it).
+ * Errors: HEGMM_EINVAL, HEGMM_ESHAPE (a shape that does not fit),
+ * HEGMM_ENOMEM; *out is NULL on error. */
+int hegmm_lintrans(hegmm_ctx *ctx, const hegmm_ct *ct, const int *src, int count, hegmm_ct **out);
+int hegmm_to_layout(hegmm_ctx *ctx, const hegmm_ct *ct, int role, int m, int l, int n, int alg, hegmm_ct **out);
+int hegmm_from_result(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int alg, hegmm_ct **out);
+int hegmm_chain_operand(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int alg, int role, int m2, int l2,
+                        int n2, int alg2, hegmm_ct **out);
+
 /* Sums of products, the building block of blocked products (Section 4.4,
  * Table 4: a matrix larger than one ciphertext is split into blocks and
  * C_ij = sum_k A_ik B_kj).  Products are given as for hegmm_matmul_batch_algs

@@ -601,6 +601,37 @@ class HEGMM:
             out = o.add(out, o.rotate(C, z))
         return out
 
+    def lintrans(self, ct: np.ndarray, src: List[int]) -> np.ndarray:
+        """Eq. lintrans on a ciphertext, composed of the HE operations of
+        Section 2.1 whatever the mode: the sum over diagonals d (ascending)
+        of HE-CMult(HE-Rot(ct, d), u_d); slot j of the result takes slot
+        src[j] of ct (negative: zero)."""
+        diags = SL.diagonals_of_map({j: s for j, s in enumerate(src) if s >= 0})
+        acc = np.zeros_like(ct)
+        for d in sorted(diags):
+            term = self.o.cmult(self.o.rotate(ct, d), self.mask_eval(diags[d], 1, ct.shape[1]))
+            acc = self.o.add(acc, term)
+        return acc
+
+    def to_layout(self, ct: np.ndarray, role: int, m: int, l: int, n: int, alg: int) -> np.ndarray:
+        """sigma(A) / tau(B) (and Algorithm 2's operand layout) under
+        encryption, from a plain column-major matrix ciphertext (Section
+        3.2.2 counts these transformations' HE operations)."""
+        return self.lintrans(ct, SL.layout_source(role, m, l, n, alg))
+
+    def from_result(self, ct: np.ndarray, m: int, l: int, n: int, alg: int) -> np.ndarray:
+        """A product's result as a plain column-major m x n matrix ciphertext."""
+        return self.lintrans(ct, SL.result_source(m, l, n, alg))
+
+    def chain_operand(self, ct: np.ndarray, m: int, l: int, n: int, alg: int, role: int, m2: int, l2: int, n2: int,
+                      alg2: int) -> np.ndarray:
+        """The result of product (m, l, n, alg) as operand ``role`` of product
+        (m2, l2, n2, alg2), in one transformation: the operand layout's map
+        from the plain matrix composed with the result's map into it."""
+        assert (m2, l2) == (m, n) if role == 0 else (l2, n2) == (m, n)
+        res = SL.result_source(m, l, n, alg)
+        return self.lintrans(ct, [res[s] if s >= 0 else -1 for s in SL.layout_source(role, m2, l2, n2, alg2)])
+
     def sum_products(self, items: List[Tuple[SL.Plan, np.ndarray, np.ndarray]]) -> np.ndarray:
         """The HE-Add (Section 2.1) of the results of products that share a
         result layout, in list order: the block sum C_ij = sum_k A_ik B_kj of

@@ -487,6 +487,31 @@ def run_slots(plan: Plan, A: np.ndarray, B: np.ndarray, S: int, t: int) -> np.nd
     return C
 
 
+def layout_source(role: int, m: int, l: int, n: int, alg: int) -> List[int]:
+    """The operand layout of a product (m, l, n, alg) as a slot map from the
+    plain column-major matrix (A: m x l for role 0, B: l x n for role 1; slot
+    i + j rows holds M_ij): for every destination slot the plain slot it
+    copies, -1 for zero.  sigma / tau (Section 3.1) and, for Algorithm 2, the
+    duplication and eps^0 / omega^0 only move entries, so an index matrix
+    (entry = its plain slot + 1) carried through the layout names them."""
+    plan = make_plan(m, l, n, alg)
+    rows, cols = (m, l) if role == 0 else (l, n)
+    idx = 1 + (np.arange(rows)[:, None] + np.arange(cols)[None, :] * rows)
+    v = plan.a_layout(idx) if role == 0 else plan.b_layout(idx)
+    return [int(x) - 1 for x in v]
+
+
+def result_source(m: int, l: int, n: int, alg: int) -> List[int]:
+    """The result of a product as a slot map into the plain column-major
+    m x n matrix: destination i + j m takes the result slot of C_ij."""
+    plan = make_plan(m, l, n, alg)
+    src = [-1] * (m * n)
+    for i in range(m):
+        for j in range(n):
+            src[i + j * m] = plan.result_slot(i, j)
+    return src
+
+
 def block_bounds(sizes: List[int]) -> List[Tuple[int, int]]:
     """[start, stop) of consecutive blocks of the given sizes (Section 4.4)."""
     out, s = [], 0

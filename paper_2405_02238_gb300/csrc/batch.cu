@@ -1318,6 +1318,64 @@ int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *con
     return matmul_run(c, count, A, B, mln, alg, algs, C, cnt, true, nullptr);
 }
 
+// A slot-selection linear transformation of one ciphertext (Eq. lintrans),
+// composed as the HE operations of Section 2.1: out = sum over the
+// diagonals d (ascending) of HE-CMult(HE-Rot(in, d), u_d), where slot j of
+// the output takes slot src[j] of the input (src[j] < 0: zero, slots from
+// count on: zero) and u_d is 1 on the destinations of diagonal
+// d = src - dst mod S.  The rotations of a chunk of diagonals share one
+// hoisted ModUp; Galois keys that are missing are made from the secret key.
+int lintrans(Ctx *c, const hegmm_ct *in, const int *src, int count, hegmm_ct **out) {
+    *out = nullptr;
+    const int S = c->S, N = c->N, lv = in->level;
+    if (count < 0 || count > S) return set_err(c, HEGMM_EINVAL, "slot map longer than one slot row");
+    std::map<int, std::vector<int>> diags;
+    for (int j = 0; j < count; j++) {
+        if (src[j] < 0) continue;
+        if (src[j] >= S) return set_err(c, HEGMM_EINVAL, "source slot outside the slot row");
+        diags[((src[j] - j) % S + S) % S].push_back(j);
+    }
+    hegmm_ct *acc = new_ct(c, lv);
+    if (!acc) return set_err(c, HEGMM_ENOMEM, "lintrans");
+    cudaMemsetAsync(acc->d, 0, (size_t)2 * lv * N * 8, c->st);
+    std::vector<int> zs;
+    std::vector<const std::vector<int> *> dsts;
+    for (auto &kv : diags) {
+        zs.push_back(kv.first);
+        dsts.push_back(&kv.second);
+        if (kv.first)
+            if (int rc = ensure_galois_key(c, galois_of(c, kv.first))) {
+                hegmm_ct_destroy(acc);
+                return rc;
+            }
+    }
+    constexpr int CH = 64;  // diagonals per hoisted ModUp (bounds the scratch)
+    const int nz = (int)zs.size();
+    u64 *masks = dalloc(c, (size_t)std::min(nz, CH) * lv * N);
+    u64 *term = dalloc(c, (size_t)2 * lv * N);
+    int rc = (!masks || !term) ? set_err(c, HEGMM_ENOMEM, "lintrans scratch") : HEGMM_OK;
+    for (int z0 = 0; z0 < nz && !rc; z0 += CH) {
+        const int nb = std::min(CH, nz - z0);
+        std::vector<const std::vector<int> *> part(dsts.begin() + z0, dsts.begin() + z0 + nb);
+        if ((rc = encode_masks(c, lv, part, 1, masks))) break;
+        std::vector<hegmm_ct *> rots((size_t)nb, nullptr);
+        rc = rotate_hoisted(c, in, zs.data() + z0, nb, rots.data());
+        for (int k = 0; k < nb && !rc; k++) {
+            rc = pw_mont(c, lv, 2, rots[k]->d, masks + (size_t)k * lv * N, 1, term);
+            if (!rc) rc = pw_add(c, lv, 2, acc->d, term, acc->d);
+        }
+        for (auto *r : rots) hegmm_ct_destroy(r);
+    }
+    dfree(c, masks);
+    dfree(c, term);
+    if (rc) {
+        hegmm_ct_destroy(acc);
+        return rc;
+    }
+    *out = acc;
+    return cuda_check(c, "lintrans");
+}
+
 // Sums of products (the blocking of Section 4.4): all products in one
 // batched run, then one launch that adds each group's results.
 int matmul_sum(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
@@ -1414,6 +1472,70 @@ int hegmm_matmul_batch_algs(hegmm_ctx *h, int count, const hegmm_ct *const *A, c
                             const int *mln, const int *algs, hegmm_ct **C) {
     if (!h || count < 0 || (count && (!A || !B || !mln || !C))) return HEGMM_EINVAL;
     return matmul_many(&h->c, count, A, B, mln, HEGMM_ALG_AUTO, C, nullptr, algs);
+}
+
+int hegmm_lintrans(hegmm_ctx *h, const hegmm_ct *ct, const int *src, int count, hegmm_ct **out) {
+    if (!h || !ct || !out || count < 0 || (count && !src)) return HEGMM_EINVAL;
+    return lintrans(&h->c, ct, src, count, out);
+}
+
+// The operand layout of a product as a slot map from the plain column-major
+// matrix: the layout of an index matrix whose entry (i, j) holds its plain
+// slot i + j rows plus 1 names every destination's source (-1: zero).
+static int layout_source(Ctx *c, int role, int m, int l, int n, int alg, std::vector<int> &src) {
+    if (role != HEGMM_ROLE_A && role != HEGMM_ROLE_B) return set_err(c, HEGMM_EINVAL, "role must be A or B");
+    if (m <= 0 || l <= 0 || n <= 0) return set_err(c, HEGMM_EINVAL, "dimensions must be positive");
+    const int a = resolve_alg(m, l, n, alg, c->S);
+    if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+    const HostPlan P = make_host_plan(m, l, n, a);
+    const int rows = role == HEGMM_ROLE_A ? m : l, cols = role == HEGMM_ROLE_A ? l : n;
+    std::vector<int64_t> idx((size_t)rows * cols);
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) idx[(size_t)i * cols + j] = 1 + i + (int64_t)j * rows;
+    const std::vector<uint64_t> v = role == HEGMM_ROLE_A ? P.a_slots(idx.data(), c->t) : P.b_slots(idx.data(), c->t);
+    src.assign(v.size(), -1);
+    for (size_t d = 0; d < v.size(); d++) src[d] = (int)v[d] - 1;
+    return HEGMM_OK;
+}
+
+// The result of a product as a slot map into the plain column-major m x n
+// matrix: destination i + j m takes the result slot of C_ij.
+static int result_source(Ctx *c, int m, int l, int n, int alg, std::vector<int> &src) {
+    if (m <= 0 || l <= 0 || n <= 0) return set_err(c, HEGMM_EINVAL, "dimensions must be positive");
+    const int a = resolve_alg(m, l, n, alg, c->S);
+    if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+    const HostPlan P = make_host_plan(m, l, n, a);
+    src.assign((size_t)m * n, -1);
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < n; j++) src[(size_t)i + (size_t)j * m] = P.result_slot(i, j);
+    return HEGMM_OK;
+}
+
+int hegmm_to_layout(hegmm_ctx *h, const hegmm_ct *ct, int role, int m, int l, int n, int alg, hegmm_ct **out) {
+    if (!h || !ct || !out) return HEGMM_EINVAL;
+    std::vector<int> src;
+    if (int rc = layout_source(&h->c, role, m, l, n, alg, src)) return rc;
+    return lintrans(&h->c, ct, src.data(), (int)src.size(), out);
+}
+
+int hegmm_chain_operand(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, int alg, int role, int m2, int l2,
+                        int n2, int alg2, hegmm_ct **out) {
+    if (!h || !ct || !out) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (role == HEGMM_ROLE_A ? (m2 != m || l2 != n) : (l2 != m || n2 != n))
+        return set_err(c, HEGMM_EINVAL, "the result's m x n is not the operand's shape");
+    std::vector<int> res, lay;
+    if (int rc = result_source(c, m, l, n, alg, res)) return rc;
+    if (int rc = layout_source(c, role, m2, l2, n2, alg2, lay)) return rc;
+    for (int &s : lay) s = s >= 0 ? res[s] : -1;  // one transformation: result -> plain -> operand
+    return lintrans(c, ct, lay.data(), (int)lay.size(), out);
+}
+
+int hegmm_from_result(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, int alg, hegmm_ct **out) {
+    if (!h || !ct || !out) return HEGMM_EINVAL;
+    std::vector<int> src;
+    if (int rc = result_source(&h->c, m, l, n, alg, src)) return rc;
+    return lintrans(&h->c, ct, src.data(), (int)src.size(), out);
 }
 
 int hegmm_matmul_sum(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,

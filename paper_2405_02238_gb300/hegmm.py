@@ -88,6 +88,12 @@ _SIGS = {
                                                ctypes.POINTER(vp)]),
     "hegmm_matmul_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp,
                                           ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_lintrans": (ctypes.c_int, [vp, vp, intp, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_to_layout": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(vp)]),
+    "hegmm_from_result": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(vp)]),
+    "hegmm_chain_operand": (ctypes.c_int, [vp, vp] + [ctypes.c_int] * 9 + [ctypes.POINTER(vp)]),
     "hegmm_matmul_sum": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), intp, intp, intp,
                                         ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_matmul_blocked": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, intp, intp, intp,
@@ -344,6 +350,31 @@ class Context:
                                                      None if al is None else al.ctypes.data_as(intp), outs),
                     "matmul_batch_algs")
         return [Ciphertext(self, vp(outs[i])) for i in range(n)]
+
+    def hegmm_lintrans(self, ct: "Ciphertext", src) -> "Ciphertext":
+        """hegmm_lintrans: slot j of the result takes slot src[j] (< 0: zero)."""
+        s = np.ascontiguousarray(np.array(src, dtype=np.int32))
+        out = vp()
+        self._check(self.lib.hegmm_lintrans(self.h, ct.h, s.ctypes.data_as(intp), len(s), ctypes.byref(out)),
+                    "lintrans")
+        return Ciphertext(self, out)
+
+    def hegmm_to_layout(self, ct: "Ciphertext", role: int, m: int, l: int, n: int, alg: int = ALG_AUTO):
+        out = vp()
+        self._check(self.lib.hegmm_to_layout(self.h, ct.h, role, m, l, n, alg, ctypes.byref(out)), "to_layout")
+        return Ciphertext(self, out)
+
+    def hegmm_from_result(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO):
+        out = vp()
+        self._check(self.lib.hegmm_from_result(self.h, ct.h, m, l, n, alg, ctypes.byref(out)), "from_result")
+        return Ciphertext(self, out)
+
+    def hegmm_chain_operand(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int, role: int, m2: int, l2: int,
+                            n2: int, alg2: int):
+        out = vp()
+        self._check(self.lib.hegmm_chain_operand(self.h, ct.h, m, l, n, alg, role, m2, l2, n2, alg2,
+                                                 ctypes.byref(out)), "chain_operand")
+        return Ciphertext(self, out)
 
     def hegmm_matmul_sum(self, As, Bs, shapes, group, ngroups: int, algs=None):
         """hegmm_matmul_sum: C[g] = sum of the products p with group[p] == g."""
