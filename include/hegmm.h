@@ -129,7 +129,17 @@ int hegmm_key_export(hegmm_ctx *ctx, uint64_t which, uint64_t *host);
  * Errors: HEGMM_ESHAPE. */
 int hegmm_encode(hegmm_ctx *ctx, int role, const int64_t *mat, int m, int l, int n, int alg, hegmm_pt **out);
 
-/* Encodes count <= S slot values (row 0; the rest zero) into a plaintext. */
+/* Two products in one ciphertext pair.  The slots form two rows of S = N/2;
+ * a rotation moves both rows alike and every mask of a product covers both
+ * rows, so a product computes the row-0 and the row-1 products of its
+ * operands at the cost of one.  hegmm_encode_pair lays mat0 out in row 0
+ * and mat1 (NULL: zeros, the same plaintext as hegmm_encode) in row 1, as
+ * hegmm_encode does for one matrix. */
+int hegmm_encode_pair(hegmm_ctx *ctx, int role, const int64_t *mat0, const int64_t *mat1, int m, int l, int n, int alg,
+                      hegmm_pt **out);
+
+/* Encodes count <= N slot values (slots 0..S-1 of row 0, then row 1; the
+ * rest zero) into a plaintext. */
 int hegmm_encode_slots(hegmm_ctx *ctx, const uint64_t *slots, int count, hegmm_pt **out);
 
 /* Secret-key encryption: c1 = a, c0 = -a s + t e + m, with a and e drawn
@@ -247,8 +257,9 @@ int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A,
  * Galois keys that are missing are made from the context's secret key.
  *
  * hegmm_lintrans: slot j of *out takes slot src[j] of ct for j < count
- * (src[j] < 0 and slots from count on: 0); 0 <= src[j] < slots, count <=
- * slots (HEGMM_EINVAL otherwise).  d = src[j] - j mod slots.
+ * (src[j] < 0 and slots from count on: 0); 0 <= src[j] < S, count <= S
+ * (HEGMM_EINVAL otherwise); d = src[j] - j mod S.  The masks cover both
+ * slot rows, so row 1 is transformed by the same map.
  *
  * A plain matrix ciphertext holds M (rows x cols) column-major: slot
  * i + j rows = M_ij.
@@ -383,6 +394,12 @@ int hegmm_decrypt(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int a
 
 /* Decrypts all S row-0 slots into out[S].  Synchronises the stream. */
 int hegmm_decrypt_slots(hegmm_ctx *ctx, const hegmm_ct *ct, uint64_t *out);
+/* Decrypts both slot rows into out[N] (row 0, then row 1). */
+int hegmm_decrypt_rows(hegmm_ctx *ctx, const hegmm_ct *ct, uint64_t *out);
+/* hegmm_decrypt of both rows of a product of hegmm_encode_pair operands:
+ * the row-0 product into out0, the row-1 product into out1 (m x n each). */
+int hegmm_decrypt_pair(hegmm_ctx *ctx, const hegmm_ct *ct, int m, int l, int n, int alg, uint64_t *out0,
+                       uint64_t *out1);
 
 /* Single HE operations (Section 2.1), each returning a new ciphertext. */
 int hegmm_rotate(hegmm_ctx *ctx, const hegmm_ct *ct, int z, hegmm_ct **out);

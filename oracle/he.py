@@ -293,6 +293,10 @@ class Oracle:
         m, _, _ = self.decrypt(ct)
         return self.decode(m)[0]
 
+    def decrypt_rows(self, ct: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+        m, _, _ = self.decrypt(ct)
+        return self.decode(m)
+
     # -------------------------------------------------------- operations
     def rotate(self, ct: np.ndarray, z: int, hoisted: bool = False) -> np.ndarray:
         lv = ct.shape[1]
@@ -466,11 +470,14 @@ class HEGMM:
         self._mask_cache: Dict[Tuple, np.ndarray] = {}
 
     def mask_eval(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
+        """The mask u_d of Eq. lintrans: ``scale`` on the destination slots of
+        both slot rows (a rotation moves both rows alike, so a second
+        product in row 1 is transformed the same way), 0 elsewhere."""
         key = (tuple(dsts), scale, lv)
         if key not in self._mask_cache:
             v = np.zeros(self.o.S, dtype=np.int64)
             v[dsts] = scale
-            self._mask_cache[key] = self.o.plaintext_eval(self.o.encode(v), lv)
+            self._mask_cache[key] = self.o.plaintext_eval(self.o.encode(v, v), lv)
         return self._mask_cache[key]
 
     def galois_needed(self, plan: SL.Plan) -> List[int]:
@@ -487,12 +494,20 @@ class HEGMM:
         ctB = o.encrypt(o.encode(plan.b_layout(B) % o.t), seed, streams[1])
         return ctA, ctB
 
+    def encrypt_pair(self, plan: SL.Plan, A0, B0, A1, B1, seed: int = 1, streams=(0, 1)):
+        """Two products of one plan in one ciphertext pair: the first in
+        slot row 0, the second in slot row 1."""
+        o = self.o
+        ctA = o.encrypt(o.encode(plan.a_layout(A0) % o.t, plan.a_layout(A1) % o.t), seed, streams[0])
+        ctB = o.encrypt(o.encode(plan.b_layout(B0) % o.t, plan.b_layout(B1) % o.t), seed, streams[1])
+        return ctA, ctB
+
     def mask_eval_pq(self, dsts: List[int], scale: int, lv: int) -> np.ndarray:
         key = ("pq", tuple(dsts), scale, lv)
         if key not in self._mask_cache:
             v = np.zeros(self.o.S, dtype=np.int64)
             v[dsts] = scale
-            self._mask_cache[key] = self.o.plaintext_eval_pq(self.o.encode(v), lv)
+            self._mask_cache[key] = self.o.plaintext_eval_pq(self.o.encode(v, v), lv)
         return self._mask_cache[key]
 
     def lt_double(self, ct: np.ndarray, terms: List[Tuple[int, List[int]]], scale: int) -> np.ndarray:
@@ -651,6 +666,18 @@ class HEGMM:
         return [[self.sum_products([(SL.make_plan(rows[i], inner[k], cols[j], 1), ctA[i][k], ctB[k][j])
                                     for k in range(len(inner))])
                  for j in range(len(cols))] for i in range(len(rows))]
+
+    def result_pair(self, plan: SL.Plan, ct: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+        """The products of slot rows 0 and 1."""
+        rows = self.o.decrypt_rows(ct)
+        out = []
+        for r in rows:
+            Cm = np.zeros((plan.m, plan.n), dtype=np.int64)
+            for i in range(plan.m):
+                for j in range(plan.n):
+                    Cm[i, j] = r[plan.result_slot(i, j)]
+            out.append(Cm)
+        return out[0], out[1]
 
     def result(self, plan: SL.Plan, ct: np.ndarray) -> np.ndarray:
         slots = self.o.decrypt_slots(ct)

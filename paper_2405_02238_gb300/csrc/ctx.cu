@@ -320,8 +320,10 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         c->slot_pos1[j] = (int)brev_bits((u32)((ng - 1) / 2), c->logN);
         g = g * 5 % two_n;
     }
-    c->d_slot_pos0 = upload(c, c->slot_pos0);
-    if (!c->d_slot_pos0) return set_err(c, HEGMM_ENOMEM, "slot table");
+    std::vector<int> both(c->slot_pos0);
+    both.insert(both.end(), c->slot_pos1.begin(), c->slot_pos1.end());
+    c->d_slot_pos = upload(c, both);
+    if (!c->d_slot_pos) return set_err(c, HEGMM_ENOMEM, "slot table");
     cudaStreamSynchronize(c->st);
     return cuda_check(c, "slot table");
 }
@@ -451,12 +453,13 @@ static hegmm_pt *new_pt(Ctx *c) {
     return pt;
 }
 
-// slot vector (row 0, count values mod t) -> plaintext (NTT domain over q_0..q_{L-1})
+// slot vector (count values mod t: slots 0..S-1 of row 0, then row 1) ->
+// plaintext (NTT domain over q_0..q_{L-1})
 static int encode_slots(Ctx *c, const u64 *slots, int count, hegmm_pt **out) {
-    if (count < 0 || count > c->S) return set_err(c, HEGMM_ESHAPE, "more values than slots");
-    const int N = c->N, L = c->L;
+    if (count < 0 || count > c->N) return set_err(c, HEGMM_ESHAPE, "more values than slots");
+    const int N = c->N, L = c->L, S = c->S;
     std::vector<u64> ev(N, 0);
-    for (int j = 0; j < count; j++) ev[c->slot_pos0[j]] = slots[j] % c->t;
+    for (int j = 0; j < count; j++) ev[j < S ? c->slot_pos0[j] : c->slot_pos1[j - S]] = slots[j] % c->t;
     u64 *m = dalloc(c, N);
     hegmm_pt *pt = new_pt(c);
     if (!m || !pt) return set_err(c, HEGMM_ENOMEM, "encode");
@@ -536,8 +539,11 @@ static int decrypt_slots(Ctx *c, const hegmm_ct *ct, std::vector<u64> &slots) {
     dfree(c, v);
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "decrypt");
     if ((rc = device_status(c))) return rc;
-    slots.resize(c->S);
-    for (int j = 0; j < c->S; j++) slots[j] = ev[c->slot_pos0[j]];
+    slots.resize(c->N);  // row 0, then row 1
+    for (int j = 0; j < c->S; j++) {
+        slots[j] = ev[c->slot_pos0[j]];
+        slots[c->S + j] = ev[c->slot_pos1[j]];
+    }
     return cuda_check(c, "decrypt");
 }
 
@@ -585,7 +591,7 @@ void hegmm_ctx_destroy(hegmm_ctx *h) {
     for (auto &kv : c->divs) dfree(c, kv.second.d);
     for (auto &kv : c->crt) dfree(c, kv.second);
     dfree(c, c->d_Pmod);
-    dfree(c, c->d_slot_pos0);
+    dfree(c, c->d_slot_pos);
     dfree(c, c->d_tw);
     dfree(c, c->d_mods);
     dfree(c, c->d_err);
@@ -682,6 +688,22 @@ int hegmm_encode(hegmm_ctx *h, int role, const int64_t *mat, int m, int l, int n
     return encode_slots(c, v.data(), (int)v.size(), out);
 }
 
+int hegmm_encode_pair(hegmm_ctx *h, int role, const int64_t *mat0, const int64_t *mat1, int m, int l, int n, int alg,
+                      hegmm_pt **out) {
+    if (!h || !mat0 || !out || (role != 0 && role != 1)) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    const int a = resolve_alg(m, l, n, alg, c->S);
+    if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::vector<u64> v = role == 0 ? P.a_slots(mat0, c->t) : P.b_slots(mat0, c->t);
+    v.resize(c->S, 0);
+    if (mat1) {
+        const std::vector<u64> w = role == 0 ? P.a_slots(mat1, c->t) : P.b_slots(mat1, c->t);
+        v.insert(v.end(), w.begin(), w.end());
+    }
+    return encode_slots(c, v.data(), (int)v.size(), out);
+}
+
 int hegmm_encode_slots(hegmm_ctx *h, const uint64_t *slots, int count, hegmm_pt **out) {
     if (!h || (!slots && count) || !out) return HEGMM_EINVAL;
     return encode_slots(&h->c, slots, count, out);
@@ -693,6 +715,15 @@ int hegmm_encrypt(hegmm_ctx *h, const hegmm_pt *pt, uint64_t seed, uint64_t sid,
 }
 
 int hegmm_decrypt_slots(hegmm_ctx *h, const hegmm_ct *ct, uint64_t *out) {
+    if (!h || !ct || !out) return HEGMM_EINVAL;
+    std::vector<u64> s;
+    int rc = decrypt_slots(&h->c, ct, s);
+    if (rc) return rc;
+    memcpy(out, s.data(), (size_t)h->c.S * 8);
+    return HEGMM_OK;
+}
+
+int hegmm_decrypt_rows(hegmm_ctx *h, const hegmm_ct *ct, uint64_t *out) {
     if (!h || !ct || !out) return HEGMM_EINVAL;
     std::vector<u64> s;
     int rc = decrypt_slots(&h->c, ct, s);
@@ -712,6 +743,24 @@ int hegmm_decrypt(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, int alg
     if (rc) return rc;
     for (int i = 0; i < m; i++)
         for (int j = 0; j < n; j++) out[(size_t)i * n + j] = s[P.result_slot(i, j)];
+    return HEGMM_OK;
+}
+
+int hegmm_decrypt_pair(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, int alg, uint64_t *out0,
+                       uint64_t *out1) {
+    if (!h || !ct || !out0 || !out1) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    const int a = resolve_alg(m, l, n, alg, c->S);
+    if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+    HostPlan P = make_host_plan(m, l, n, a);
+    std::vector<u64> s;
+    int rc = decrypt_slots(c, ct, s);
+    if (rc) return rc;
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j < n; j++) {
+            out0[(size_t)i * n + j] = s[P.result_slot(i, j)];
+            out1[(size_t)i * n + j] = s[c->S + P.result_slot(i, j)];
+        }
     return HEGMM_OK;
 }
 

@@ -177,7 +177,7 @@ struct Ctx {
     std::map<int, ModUpTab> modup;
     std::map<std::pair<int, int>, DivTab> divs;  // (level, 0 = ModDown / 1 = modswitch)
     std::vector<int> slot_pos0, slot_pos1;       // slot -> NTT position mod t
-    int *d_slot_pos0 = nullptr;                  // device copy of slot_pos0
+    int *d_slot_pos = nullptr;                   // device copy of slot_pos0 then slot_pos1 (N entries)
     std::map<std::tuple<int, int, int, int, int>, ShapeData *> shapes;  // per (shape, order): plan + masks
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     std::map<std::tuple<int, int, int, int>, std::pair<size_t, size_t>> shape_counts;  // iterations, extractions
@@ -310,7 +310,8 @@ int sum_desc(Ctx *c, int lv, const SumDesc *d_sums, int n, int np = 0);
 // out[g] = sum of src[first[g] .. first[g + 1]) (ciphertexts [2][lv][N]),
 // device arrays of pointers and offsets.
 int sum_groups(Ctx *c, int lv, const u64 *const *d_src, const int *d_first, u64 *const *d_out, int ngroups);
-// ev[b][slot_pos0[slots[j]]] = value for j in [off[b], off[b+1]) (NTT order mod t)
+// ev[b][slot_pos0[s]] = ev[b][slot_pos1[s]] = value for s = slots[j],
+// j in [off[b], off[b+1]) (NTT order mod t): the slot in both slot rows
 int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev);
 int gather_cts(Ctx *c, int lv, u64 *const *d_src, int n, u64 *dst);
 

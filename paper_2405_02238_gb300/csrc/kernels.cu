@@ -1254,8 +1254,12 @@ int sum_groups(Ctx *c, int lv, const u64 *const *d_src, const int *d_first, u64 
 
 __global__ void k_scatter_slots(const int *__restrict__ off, const int *__restrict__ slots,
                                 const int *__restrict__ pos, u64 value, int N, u64 *__restrict__ ev) {
-    const int b = blockIdx.x;
-    for (int j = off[b] + threadIdx.x; j < off[b + 1]; j += blockDim.x) ev[(size_t)b * N + pos[slots[j]]] = value;
+    const int b = blockIdx.x, S = N / 2;
+    for (int j = off[b] + threadIdx.x; j < off[b + 1]; j += blockDim.x) {
+        const int s = slots[j];
+        ev[(size_t)b * N + pos[s]] = value;      // row 0
+        ev[(size_t)b * N + pos[S + s]] = value;  // row 1
+    }
 }
 
 // Butterfly throughput probe: the lazy forward butterfly of the NTT kernels,
@@ -1316,7 +1320,7 @@ int peak_butterflies(Ctx *c, double *per_s) {
 int scatter_slots(Ctx *c, const int *d_off, const int *d_slots, int nb, u64 value, u64 *ev) {
     if (nb <= 0) return HEGMM_OK;
     Launch t(c, K_CODEC, 0.0);
-    k_scatter_slots<<<nb, 256, 0, c->st>>>(d_off, d_slots, c->d_slot_pos0, value, c->N, ev);
+    k_scatter_slots<<<nb, 256, 0, c->st>>>(d_off, d_slots, c->d_slot_pos, value, c->N, ev);
     return cuda_check(c, "scatter_slots");
 }
 

@@ -81,6 +81,10 @@ _SIGS = {
     "hegmm_encode": (ctypes.c_int, [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(vp)]),
     "hegmm_encode_slots": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_encode_pair": (ctypes.c_int, [vp, ctypes.c_int, i64p, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.POINTER(vp)]),
+    "hegmm_decrypt_rows": (ctypes.c_int, [vp, vp, u64p]),
+    "hegmm_decrypt_pair": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p]),
     "hegmm_encrypt": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(vp)]),
     "hegmm_matmul": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(vp), ctypes.POINTER(hegmm_opcount)]),
@@ -310,6 +314,16 @@ class Context:
         self._check(self.lib.hegmm_encode(self.h, role, _ptr(a, i64p), m, l, n, alg, ctypes.byref(out)), "encode")
         return Plaintext(self, out)
 
+    def hegmm_encode_pair(self, role: int, mat0: np.ndarray, mat1, m: int, l: int, n: int,
+                          alg: int = ALG_AUTO) -> "Plaintext":
+        """hegmm_encode_pair: mat0 in slot row 0, mat1 (None: zeros) in row 1."""
+        a = np.ascontiguousarray(mat0, dtype=np.int64)
+        b = None if mat1 is None else np.ascontiguousarray(mat1, dtype=np.int64)
+        out = vp()
+        self._check(self.lib.hegmm_encode_pair(self.h, role, _ptr(a, i64p), None if b is None else _ptr(b, i64p), m, l,
+                                               n, alg, ctypes.byref(out)), "encode_pair")
+        return Plaintext(self, out)
+
     def hegmm_encode_slots(self, slots) -> "Plaintext":
         a = _u64(slots)
         out = vp()
@@ -413,6 +427,18 @@ class Context:
         out = np.zeros(self.S, dtype=np.uint64)
         self._check(self.lib.hegmm_decrypt_slots(self.h, ct.h, _ptr(out)), "decrypt_slots")
         return out
+
+    def hegmm_decrypt_rows(self, ct: "Ciphertext") -> np.ndarray:
+        """Both slot rows: [2][S]."""
+        out = np.zeros(2 * self.S, dtype=np.uint64)
+        self._check(self.lib.hegmm_decrypt_rows(self.h, ct.h, _ptr(out)), "decrypt_rows")
+        return out.reshape(2, self.S)
+
+    def hegmm_decrypt_pair(self, ct: "Ciphertext", m: int, l: int, n: int, alg: int = ALG_AUTO):
+        o0 = np.zeros((m, n), dtype=np.uint64)
+        o1 = np.zeros((m, n), dtype=np.uint64)
+        self._check(self.lib.hegmm_decrypt_pair(self.h, ct.h, m, l, n, alg, _ptr(o0), _ptr(o1)), "decrypt_pair")
+        return o0, o1
 
     def hegmm_rotate(self, ct: "Ciphertext", z: int) -> "Ciphertext":
         out = vp()
