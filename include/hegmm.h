@@ -121,6 +121,18 @@ int hegmm_keygen_rotations(hegmm_ctx *ctx, const int *z, int count);
  * Errors: HEGMM_ENOKEY. */
 int hegmm_key_export(hegmm_ctx *ctx, uint64_t which, uint64_t *host);
 
+/* Checkpoint / warm start of an evaluation context: hegmm_key_import loads a
+ * key in hegmm_key_export's layout and domain (residues below their primes,
+ * else HEGMM_EINVAL) under `which` (0: relinearisation, else an odd Galois
+ * element < 2N); an existing key of that element is overwritten in place.
+ * A context that only imports keys (no hegmm_keygen) evaluates products of
+ * imported ciphertexts (hegmm_ct_import) but has no secret key: it cannot
+ * encrypt, decrypt or make missing keys (HEGMM_ENOKEY).  hegmm_key_list
+ * writes up to cap of the key elements held (ascending) and their number to
+ * *count.  Synchronise the stream. */
+int hegmm_key_import(hegmm_ctx *ctx, uint64_t which, const uint64_t *host);
+int hegmm_key_list(hegmm_ctx *ctx, uint64_t *which, int cap, int *count);
+
 /* Client-side preprocessing of a plaintext matrix (Algorithm 1 step 1,
  * Algorithm 2 lines 1-18): sigma (role A) or tau (role B), the duplication
  * and eps^0 / omega^0 of Algorithm 2, flattening in the plan's order, and

@@ -678,6 +678,45 @@ int hegmm_key_export(hegmm_ctx *h, uint64_t which, uint64_t *host) {
     return cuda_check(c, "key export");
 }
 
+int hegmm_key_import(hegmm_ctx *h, uint64_t which, const uint64_t *host) {
+    if (!h || !host) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (which != 0 && (which % 2 == 0 || which >= (uint64_t)2 * c->N))
+        return set_err(c, HEGMM_EINVAL, "which must be 0 or an odd Galois element below 2N");
+    const size_t w = c->key_words();
+    for (size_t i = 0; i < w; i++) {
+        const int limb = (int)((i / c->N) % c->np);
+        if (host[i] >= c->q[limb]) return set_err(c, HEGMM_EINVAL, "key residue not below its prime");
+    }
+    auto it = c->keys.find(which);
+    u64 *key = it != c->keys.end() ? it->second : dalloc(c, w);  // in place: cached plans keep their pointers
+    if (!key) return set_err(c, HEGMM_ENOMEM, "key import");
+    cudaMemcpyAsync(key, host, w * 8, cudaMemcpyHostToDevice, c->st);
+    std::vector<int> mods(c->np);
+    for (int i = 0; i < c->np; i++) mods[i] = i;
+    LimbPat p = pat_mods(key, c->np, mods.data(), 2 * c->dnum, (long long)c->np * c->N);
+    int rc;
+    if (!(rc = ntt_fwd(c, p))) rc = pw_to_mont(c, p);
+    if (rc) {
+        if (it == c->keys.end()) dfree(c, key);
+        return rc;
+    }
+    c->keys[which] = key;
+    cudaStreamSynchronize(c->st);  // the host buffer may be reused once this returns
+    return cuda_check(c, "key import");
+}
+
+int hegmm_key_list(hegmm_ctx *h, uint64_t *which, int cap, int *count) {
+    if (!h || !count || (cap > 0 && !which)) return HEGMM_EINVAL;
+    int k = 0;
+    for (auto &kv : h->c.keys) {
+        if (k < cap) which[k] = kv.first;
+        k++;
+    }
+    *count = k;
+    return HEGMM_OK;
+}
+
 int hegmm_encode(hegmm_ctx *h, int role, const int64_t *mat, int m, int l, int n, int alg, hegmm_pt **out) {
     if (!h || !mat || !out || (role != 0 && role != 1)) return HEGMM_EINVAL;
     Ctx *c = &h->c;

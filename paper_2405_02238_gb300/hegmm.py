@@ -78,6 +78,8 @@ _SIGS = {
     "hegmm_keygen": (ctypes.c_int, [vp, ctypes.c_uint64, intp, ctypes.c_int, ctypes.c_int]),
     "hegmm_keygen_rotations": (ctypes.c_int, [vp, intp, ctypes.c_int]),
     "hegmm_key_export": (ctypes.c_int, [vp, ctypes.c_uint64, u64p]),
+    "hegmm_key_import": (ctypes.c_int, [vp, ctypes.c_uint64, u64p]),
+    "hegmm_key_list": (ctypes.c_int, [vp, u64p, ctypes.c_int, intp]),
     "hegmm_encode": (ctypes.c_int, [vp, ctypes.c_int, i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(vp)]),
     "hegmm_encode_slots": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(vp)]),
@@ -307,6 +309,17 @@ class Context:
         out = np.zeros((dnum, 2, self.L + self.K, self.N), dtype=np.uint64)
         self._check(self.lib.hegmm_key_export(self.h, which, _ptr(out)), "key_export")
         return out
+
+    def hegmm_key_import(self, which: int, key: np.ndarray):
+        a = np.ascontiguousarray(key, dtype=np.uint64)
+        self._check(self.lib.hegmm_key_import(self.h, which, _ptr(a)), "key_import")
+
+    def hegmm_key_list(self):
+        n = ctypes.c_int()
+        self._check(self.lib.hegmm_key_list(self.h, None, 0, ctypes.byref(n)), "key_list")
+        out = np.zeros(max(1, n.value), dtype=np.uint64)
+        self._check(self.lib.hegmm_key_list(self.h, _ptr(out), n.value, ctypes.byref(n)), "key_list")
+        return [int(x) for x in out[: n.value]]
 
     def hegmm_encode(self, role: int, mat: np.ndarray, m: int, l: int, n: int, alg: int = ALG_AUTO) -> "Plaintext":
         a = np.ascontiguousarray(mat, dtype=np.int64)

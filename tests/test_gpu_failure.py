@@ -48,3 +48,35 @@ def test_bounded_wait_reports_timeout_and_context_survives(H, variant):
     again, _ = ctx.hegmm_matmul(ca, cb, m, l, n, H.ALG_1)
     assert (ctx.hegmm_ct_export(again) == want).all()
     assert (ctx.hegmm_decrypt(again, m, l, n, H.ALG_1).astype(np.int64) == (A @ B) % W.MEDIUM.t).all()
+
+
+def test_key_checkpoint_warm_start(H):
+    # keys exported from one context and imported into a fresh one (no
+    # hegmm_keygen, no secret key) evaluate the same product bit for bit
+    pre = W.TINY
+    src = H.Context.from_preset(pre)
+    m, l, n = 4, 8, 6
+    src.hegmm_set_keyswitch_mode(7)
+    src.hegmm_keygen(5, [(m, l, n)], 0)
+    A, B = W.matrices(m, l, n, 0, 15, seed=8)
+    ca = src.hegmm_encrypt(src.hegmm_encode(H.ROLE_A, A, m, l, n), 6, 0)
+    cb = src.hegmm_encrypt(src.hegmm_encode(H.ROLE_B, B, m, l, n), 6, 1)
+    C, _ = src.hegmm_matmul(ca, cb, m, l, n)
+    dst = H.Context.from_preset(pre)
+    dst.hegmm_set_keyswitch_mode(7)
+    ids = src.hegmm_key_list()
+    assert 0 in ids and len(ids) > 1
+    for g in ids:
+        dst.hegmm_key_import(g, src.hegmm_key_export(g))
+    assert dst.hegmm_key_list() == ids
+    da, db = dst.hegmm_ct_import(src.hegmm_ct_export(ca)), dst.hegmm_ct_import(src.hegmm_ct_export(cb))
+    D, _ = dst.hegmm_matmul(da, db, m, l, n)
+    assert (dst.hegmm_ct_export(D) == src.hegmm_ct_export(C)).all()
+    got = src.hegmm_decrypt(src.hegmm_ct_import(dst.hegmm_ct_export(D)), m, l, n).astype(np.int64)
+    assert (got == (A @ B) % pre.t).all()
+    with pytest.raises(H.HegmmError) as e:  # no secret key in the warm-started context
+        dst.hegmm_decrypt(D, m, l, n)
+    assert e.value.code == -4
+    with pytest.raises(H.HegmmError) as e:  # a residue that is not below its prime
+        dst.hegmm_key_import(0, np.full_like(src.hegmm_key_export(0), np.uint64(2**63)))
+    assert e.value.code == -1
