@@ -54,7 +54,7 @@ def test_max_over_ranks_and_value_gloo():
 
 
 def test_single_gpu_arms_leave_other_ranks_idle():
-    for arm in (["--impl", "reference"], ["--workload", "serve"]):
+    for arm in (["--impl", "reference"], ["--workload", "serve"], ["--workload", "product"], ["--workload", "blocked"]):
         env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
         p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + arm + ["--steps", "1", "--warmup", "0"],
                            env=env, capture_output=True, text=True, timeout=120)
