@@ -391,7 +391,8 @@ static int gen_key(Ctx *c, u64 g) {
 }
 
 int ensure_galois_key(Ctx *c, u64 g) {
-    if (!c->have_sk) return set_err(c, HEGMM_ENOKEY, "no keys: call hegmm_keygen first");
+    if (c->keys.count(g)) return HEGMM_OK;  // generated or imported
+    if (!c->have_sk) return set_err(c, HEGMM_ENOKEY, "missing key and no secret key to make it");
     return gen_key(c, g);
 }
 

@@ -58,6 +58,7 @@ def test_key_checkpoint_warm_start(H):
     m, l, n = 4, 8, 6
     src.hegmm_set_keyswitch_mode(7)
     src.hegmm_keygen(5, [(m, l, n)], 0)
+    src.hegmm_keygen_rotations([1])
     A, B = W.matrices(m, l, n, 0, 15, seed=8)
     ca = src.hegmm_encrypt(src.hegmm_encode(H.ROLE_A, A, m, l, n), 6, 0)
     cb = src.hegmm_encrypt(src.hegmm_encode(H.ROLE_B, B, m, l, n), 6, 1)
@@ -76,6 +77,14 @@ def test_key_checkpoint_warm_start(H):
     assert (got == (A @ B) % pre.t).all()
     with pytest.raises(H.HegmmError) as e:  # no secret key in the warm-started context
         dst.hegmm_decrypt(D, m, l, n)
+    assert e.value.code == -4
+    # a transformation needing an imported rotation key runs; one needing a missing key cannot make it
+    shift1 = [j + 1 for j in range(16)]
+    r_src, r_dst = src.hegmm_lintrans(ca, shift1), dst.hegmm_lintrans(da, shift1)
+    assert (dst.hegmm_ct_export(r_dst) == src.hegmm_ct_export(r_src)).all()
+    z = next(z for z in range(2, dst.S) if pow(5, z, 2 * dst.N) not in ids)  # an offset without a key
+    with pytest.raises(H.HegmmError) as e:
+        dst.hegmm_lintrans(da, [j + z for j in range(16)])
     assert e.value.code == -4
     with pytest.raises(H.HegmmError) as e:  # a residue that is not below its prime
         dst.hegmm_key_import(0, np.full_like(src.hegmm_key_export(0), np.uint64(2**63)))
