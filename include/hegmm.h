@@ -490,6 +490,15 @@ int hegmm_plan_counts(int m, int l, int n, int alg, int slots, hegmm_opcount *ou
 int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int cap);
 int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t,
                       uint64_t *out, int cap);
+/* hegmm_plan_slot_map writes the slot map hegmm_to_layout (role 0: A,
+ * 1: B) or hegmm_from_result (role 2) applies for the plan: for every
+ * destination slot the source slot it copies, -1 for zero (plain matrices
+ * column-major, slot i + j rows = M_ij), into buf[cap]; returns its length.
+ * hegmm_plan_result_layout writes {result rows, result columns,
+ * column-major} of the plan (where C_ij sits; hegmm_matmul_sum groups
+ * products with equal triples). */
+int hegmm_plan_slot_map(int m, int l, int n, int alg, int slots, int role, int *buf, int cap);
+int hegmm_plan_result_layout(int m, int l, int n, int alg, int slots, int *rows_cols_col);
 
 /* Per-kernel device timing: while enabled, every launch of the library's
  * kernels is bracketed by CUDA events on the context stream and its

@@ -1482,39 +1482,29 @@ int hegmm_lintrans(hegmm_ctx *h, const hegmm_ct *ct, const int *src, int count, 
 // The operand layout of a product as a slot map from the plain column-major
 // matrix: the layout of an index matrix whose entry (i, j) holds its plain
 // slot i + j rows plus 1 names every destination's source (-1: zero).
-static int layout_source(Ctx *c, int role, int m, int l, int n, int alg, std::vector<int> &src) {
+static int operand_map(Ctx *c, int role, int m, int l, int n, int alg, std::vector<int> &src) {
     if (role != HEGMM_ROLE_A && role != HEGMM_ROLE_B) return set_err(c, HEGMM_EINVAL, "role must be A or B");
     if (m <= 0 || l <= 0 || n <= 0) return set_err(c, HEGMM_EINVAL, "dimensions must be positive");
     const int a = resolve_alg(m, l, n, alg, c->S);
     if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
-    const HostPlan P = make_host_plan(m, l, n, a);
-    const int rows = role == HEGMM_ROLE_A ? m : l, cols = role == HEGMM_ROLE_A ? l : n;
-    std::vector<int64_t> idx((size_t)rows * cols);
-    for (int i = 0; i < rows; i++)
-        for (int j = 0; j < cols; j++) idx[(size_t)i * cols + j] = 1 + i + (int64_t)j * rows;
-    const std::vector<uint64_t> v = role == HEGMM_ROLE_A ? P.a_slots(idx.data(), c->t) : P.b_slots(idx.data(), c->t);
-    src.assign(v.size(), -1);
-    for (size_t d = 0; d < v.size(); d++) src[d] = (int)v[d] - 1;
+    src = operand_source(make_host_plan(m, l, n, a), role == HEGMM_ROLE_A ? 0 : 1);
     return HEGMM_OK;
 }
 
 // The result of a product as a slot map into the plain column-major m x n
 // matrix: destination i + j m takes the result slot of C_ij.
-static int result_source(Ctx *c, int m, int l, int n, int alg, std::vector<int> &src) {
+static int result_map(Ctx *c, int m, int l, int n, int alg, std::vector<int> &src) {
     if (m <= 0 || l <= 0 || n <= 0) return set_err(c, HEGMM_EINVAL, "dimensions must be positive");
     const int a = resolve_alg(m, l, n, alg, c->S);
     if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
-    const HostPlan P = make_host_plan(m, l, n, a);
-    src.assign((size_t)m * n, -1);
-    for (int i = 0; i < m; i++)
-        for (int j = 0; j < n; j++) src[(size_t)i + (size_t)j * m] = P.result_slot(i, j);
+    src = result_source(make_host_plan(m, l, n, a));
     return HEGMM_OK;
 }
 
 int hegmm_to_layout(hegmm_ctx *h, const hegmm_ct *ct, int role, int m, int l, int n, int alg, hegmm_ct **out) {
     if (!h || !ct || !out) return HEGMM_EINVAL;
     std::vector<int> src;
-    if (int rc = layout_source(&h->c, role, m, l, n, alg, src)) return rc;
+    if (int rc = operand_map(&h->c, role, m, l, n, alg, src)) return rc;
     return lintrans(&h->c, ct, src.data(), (int)src.size(), out);
 }
 
@@ -1525,8 +1515,8 @@ int hegmm_chain_operand(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, i
     if (role == HEGMM_ROLE_A ? (m2 != m || l2 != n) : (l2 != m || n2 != n))
         return set_err(c, HEGMM_EINVAL, "the result's m x n is not the operand's shape");
     std::vector<int> res, lay;
-    if (int rc = result_source(c, m, l, n, alg, res)) return rc;
-    if (int rc = layout_source(c, role, m2, l2, n2, alg2, lay)) return rc;
+    if (int rc = result_map(c, m, l, n, alg, res)) return rc;
+    if (int rc = operand_map(c, role, m2, l2, n2, alg2, lay)) return rc;
     for (int &s : lay) s = s >= 0 ? res[s] : -1;  // one transformation: result -> plain -> operand
     return lintrans(c, ct, lay.data(), (int)lay.size(), out);
 }
@@ -1534,7 +1524,7 @@ int hegmm_chain_operand(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, i
 int hegmm_from_result(hegmm_ctx *h, const hegmm_ct *ct, int m, int l, int n, int alg, hegmm_ct **out) {
     if (!h || !ct || !out) return HEGMM_EINVAL;
     std::vector<int> src;
-    if (int rc = result_source(&h->c, m, l, n, alg, src)) return rc;
+    if (int rc = result_map(&h->c, m, l, n, alg, src)) return rc;
     return lintrans(&h->c, ct, src.data(), (int)src.size(), out);
 }
 

@@ -53,6 +53,25 @@ void result_layout(int m, int l, int n, int alg, int &rows, int &cols, bool &col
     col = kase != 'B';
 }
 
+std::vector<int> operand_source(const HostPlan &P, int role) {
+    const int rows = role == 0 ? P.m : P.l, cols = role == 0 ? P.l : P.n;
+    std::vector<int64_t> idx((size_t)rows * cols);
+    for (int i = 0; i < rows; i++)
+        for (int j = 0; j < cols; j++) idx[(size_t)i * cols + j] = 1 + i + (int64_t)j * rows;
+    const uint64_t big = (uint64_t)1 << 30;  // above every index (< slots + 1): no reduction
+    const std::vector<uint64_t> v = role == 0 ? P.a_slots(idx.data(), big) : P.b_slots(idx.data(), big);
+    std::vector<int> src(v.size());
+    for (size_t d = 0; d < v.size(); d++) src[d] = (int)v[d] - 1;
+    return src;
+}
+
+std::vector<int> result_source(const HostPlan &P) {
+    std::vector<int> src((size_t)P.m * P.n, -1);
+    for (int i = 0; i < P.m; i++)
+        for (int j = 0; j < P.n; j++) src[(size_t)i + (size_t)j * P.m] = P.result_slot(i, j);
+    return src;
+}
+
 int resolve_alg(int m, int l, int n, int alg, int S) {
     if (m <= 0 || l <= 0 || n <= 0) return 0;
     if (alg == 1) return alg1_length(m, l, n) <= S ? 1 : 0;
@@ -310,6 +329,27 @@ int hegmm_plan_describe(int m, int l, int n, int alg, int slots, int *buf, int c
         for (int j = 0; j < n; j++) v.push_back(P.result_slot(i, j));
     for (int i = 0; i < cap && i < (int)v.size(); i++) buf[i] = v[i];
     return (int)v.size();
+}
+
+int hegmm_plan_slot_map(int m, int l, int n, int alg, int slots, int role, int *buf, int cap) {
+    if (slots <= 0 || m <= 0 || l <= 0 || n <= 0 || role < 0 || role > 2 || cap < 0 || (cap > 0 && !buf))
+        return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    const HostPlan P = make_host_plan(m, l, n, a);
+    const std::vector<int> v = role == 2 ? result_source(P) : operand_source(P, role);
+    for (int i = 0; i < cap && i < (int)v.size(); i++) buf[i] = v[i];
+    return (int)v.size();
+}
+
+int hegmm_plan_result_layout(int m, int l, int n, int alg, int slots, int *rows_cols_col) {
+    if (slots <= 0 || m <= 0 || l <= 0 || n <= 0 || !rows_cols_col) return HEGMM_EINVAL;
+    const int a = resolve_alg(m, l, n, alg, slots);
+    if (!a) return HEGMM_ESHAPE;
+    bool col;
+    result_layout(m, l, n, a, rows_cols_col[0], rows_cols_col[1], col);
+    rows_cols_col[2] = col ? 1 : 0;
+    return HEGMM_OK;
 }
 
 int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t, uint64_t *out,

@@ -80,5 +80,14 @@ HostPlan make_host_plan(int m, int l, int n, int alg);
 // i + j rows (col) or i cols + j (!col) of a rows x cols matrix; Algorithm 1
 // gives m x n column-major for every l.
 void result_layout(int m, int l, int n, int alg, int &rows, int &cols, bool &col);
+// The operand layout of role 0 (A, m x l) or 1 (B, l x n) as a slot map from
+// the plain column-major matrix (slot i + j rows holds M_ij): for every slot
+// of the layout the plain slot it copies, -1 for zero.  An index matrix
+// whose entry (i, j) holds its plain slot + 1, carried through the
+// client-side layout, names each destination's source.
+std::vector<int> operand_source(const HostPlan &P, int role);
+// The result of a product as a slot map into the plain column-major m x n
+// matrix: destination i + j m takes the result slot of C_ij.
+std::vector<int> result_source(const HostPlan &P);
 
 }  // namespace hg

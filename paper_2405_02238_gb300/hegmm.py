@@ -150,6 +150,8 @@ _SIGS = {
                                         ctypes.c_int, ctypes.c_int, intp, ctypes.c_int]),
     "hegmm_plan_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, i64p, ctypes.c_uint64, u64p, ctypes.c_int]),
+    "hegmm_plan_slot_map": (ctypes.c_int, [ctypes.c_int] * 6 + [intp, ctypes.c_int]),
+    "hegmm_plan_result_layout": (ctypes.c_int, [ctypes.c_int] * 5 + [intp]),
 }
 
 EXPORTS = tuple(_SIGS)
@@ -209,6 +211,24 @@ def hegmm_plan_layout(m: int, l: int, n: int, alg: int, slots: int, role: int, m
     out = np.zeros(need, dtype=np.uint64)
     lib.hegmm_plan_layout(m, l, n, alg, slots, role, a.ctypes.data_as(i64p), t, out.ctypes.data_as(u64p), need)
     return out
+
+
+def hegmm_plan_slot_map(m: int, l: int, n: int, alg: int, slots: int, role: int) -> List[int]:
+    lib = load()
+    need = lib.hegmm_plan_slot_map(m, l, n, alg, slots, role, None, 0)
+    if need < 0:
+        raise HegmmError(need, "plan_slot_map")
+    buf = (ctypes.c_int * max(1, need))()
+    lib.hegmm_plan_slot_map(m, l, n, alg, slots, role, buf, need)
+    return list(buf)[:need]
+
+
+def hegmm_plan_result_layout(m: int, l: int, n: int, alg: int, slots: int):
+    out = (ctypes.c_int * 3)()
+    rc = load().hegmm_plan_result_layout(m, l, n, alg, slots, out)
+    if rc != HEGMM_OK:
+        raise HegmmError(rc, "plan_result_layout")
+    return out[0], out[1], "col" if out[2] else "row"
 
 
 def _u64(a) -> np.ndarray:

@@ -95,6 +95,21 @@ def test_host_layouts_match_oracle(H):
             assert (got_b.astype(np.int64) == p.b_layout(B) % 65537).all()
 
 
+def test_host_slot_maps_match_oracle(H):
+    # the maps behind hegmm_to_layout / hegmm_from_result / hegmm_chain_operand
+    # and the result layouts hegmm_matmul_sum groups by, for every shape <= 6^3
+    for m in range(1, 7):
+        for l in range(1, 7):
+            for n in range(1, 7):
+                for alg in (1, 2):
+                    for role in (0, 1):
+                        assert H.hegmm_plan_slot_map(m, l, n, alg, 256, role) == SL.layout_source(role, m, l, n, alg)
+                    assert H.hegmm_plan_slot_map(m, l, n, alg, 256, 2) == SL.result_source(m, l, n, alg)
+                    assert H.hegmm_plan_result_layout(m, l, n, alg, 256) == SL.result_layout(SL.make_plan(m, l, n, alg))
+    with pytest.raises(H.HegmmError):
+        H.hegmm_plan_slot_map(3, 3, 3, 1, 256, 3)
+
+
 def test_auto_algorithm_and_shape_errors(H):
     # 32x128x16 does not fit Algorithm 2 at 8192 slots: AUTO gives Algorithm 1.
     assert H.hegmm_plan_describe(32, 128, 16, H.ALG_AUTO, 8192)[0] == 1
