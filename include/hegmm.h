@@ -54,6 +54,16 @@ extern "C" {
 #define HEGMM_ALG_AUTO 0 /* Algorithm 2 if it fits S slots, else Algorithm 1 */
 #define HEGMM_ALG_1 1    /* Algorithm 1 (HEGMM) */
 #define HEGMM_ALG_2 2    /* Algorithm 2 (HEGMM-Enhanced) */
+/* Algorithm 1 with an extended pre-layout (not in the paper): sigma(A) is
+ * stored over l + n - 1 columns, column c holding sigma(A)'s column c mod l,
+ * so every eps^k is one rotation by k m under one mask (Algorithm 1 needs up
+ * to two diagonals per eps^k); needs m (l + n - 1) <= S.  omega^k, the loop
+ * and the result layout are Algorithm 1's.  In this version the planner
+ * (hegmm_plan_*), hegmm_encode, hegmm_keygen, hegmm_decrypt and the
+ * ciphertext-side transformations accept it; the product entry points
+ * (hegmm_matmul*, the server) refuse it with HEGMM_EINVAL until its device
+ * parity has been run. */
+#define HEGMM_ALG_1X 3
 
 #define HEGMM_ROLE_A 0
 #define HEGMM_ROLE_B 1

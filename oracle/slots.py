@@ -364,6 +364,30 @@ def plan_alg1(m: int, l: int, n: int, order: str = "col") -> Plan:
     )
 
 
+def plan_alg1x(m: int, l: int, n: int) -> Plan:
+    """Algorithm 1 with an extended pre-layout (a cost-reducing mode, not in
+    the paper): sigma(A) is stored over W = l + n - 1 columns, column c
+    holding sigma(A)'s column c mod l.  eps^k_{m x n}(sigma(A))_{i,j} =
+    sigma(A)_{i,[j+k]_l} (Eq. def:eps) is then the stored entry (i, j + k),
+    so in column-major order every eps^k is one rotation by k m under one
+    mask; omega^k, the loop and the result layout are Algorithm 1's."""
+    W = l + n - 1
+
+    def a_matrix(A):
+        return sigma(A)[:, [c % l for c in range(W)]]
+
+    iters = []
+    for k in range(l):
+        e = diagonals_of_map(slot_map((m, n), (m, W), "col", lambda i, j, k=k: (i, j + k)))
+        o = diagonals_of_map(slot_map((m, n), (l, n), "col", omega_src(k, l)))
+        iters.append((e, o))
+    return Plan(
+        m=m, l=l, n=n, alg=3, case="X", order="col", p=l, t=1, M=m, Np=n,
+        a_shape=(m, W), b_shape=(l, n), a_matrix=a_matrix, b_matrix=tau,
+        iters=iters, extract=[], res_shape=(m, n), length=max(m * W, l * n),
+    )
+
+
 def alg2_case(m: int, l: int, n: int) -> Tuple[str, int, int]:
     """(case, p, t) of Algorithm 2; p = m is checked first, then p = n."""
     p = min(m, l, n)
@@ -446,6 +470,8 @@ def plan_alg2(m: int, l: int, n: int) -> Plan:
 def fits(m: int, l: int, n: int, alg: int, S: int) -> bool:
     if alg == 1:
         return max(m * l, l * n, m * n) <= S
+    if alg == 3:
+        return max(m * (l + n - 1), l * n) <= S
     return alg2_length(m, l, n) <= S
 
 
@@ -459,6 +485,8 @@ def choose_alg(m: int, l: int, n: int, S: int) -> int:
 
 
 def make_plan(m: int, l: int, n: int, alg: int, order: str = "col") -> Plan:
+    if alg == 3:
+        return plan_alg1x(m, l, n)
     return plan_alg1(m, l, n, order) if alg == 1 else plan_alg2(m, l, n)
 
 

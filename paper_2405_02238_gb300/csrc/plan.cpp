@@ -14,6 +14,7 @@ static inline int imod(long long a, int b) {
 }
 
 int alg1_length(int m, int l, int n) { return std::max(m * l, std::max(l * n, m * n)); }
+int alg1x_length(int m, int l, int n) { return std::max(m * (l + n - 1), l * n); }
 
 static void alg2_shape(int m, int l, int n, char &kase, int &p, int &t, int &M, int &Np, int &WA, int &HB) {
     p = std::min(m, std::min(l, n));
@@ -41,7 +42,7 @@ int alg2_length(int m, int l, int n) {
 }
 
 void result_layout(int m, int l, int n, int alg, int &rows, int &cols, bool &col) {
-    if (alg == 1) {
+    if (alg == 1 || alg == 3) {
         rows = m;
         cols = n;
         col = true;
@@ -76,6 +77,8 @@ int resolve_alg(int m, int l, int n, int alg, int S) {
     if (m <= 0 || l <= 0 || n <= 0) return 0;
     if (alg == 1) return alg1_length(m, l, n) <= S ? 1 : 0;
     if (alg == 2) return alg2_length(m, l, n) <= S ? 2 : 0;
+    if (alg == 3) return alg1x_length(m, l, n) <= S ? 3 : 0;
+    if (alg != 0) return 0;
     if (alg2_length(m, l, n) <= S) return 2;
     if (alg1_length(m, l, n) <= S) return 1;
     return 0;
@@ -133,6 +136,39 @@ HostPlan make_host_plan(int m, int l, int n, int alg) {
         }
         return P;
     }
+    if (alg == 3) {
+        // Algorithm 1 with sigma(A) stored over W = l + n - 1 columns (column
+        // c holds sigma(A)'s column c mod l): eps^k_{m x n}: (i, j) <- (i, j + k),
+        // one rotation by k m in column-major order; omega^k as Algorithm 1.
+        const int W = l + n - 1;
+        P.kase = 'X';
+        P.col = true;
+        P.p = l;
+        P.t = 1;
+        P.M = m;
+        P.Np = n;
+        P.a_rows = m;
+        P.a_cols = W;
+        P.b_rows = l;
+        P.b_cols = n;
+        P.res_rows = m;
+        P.res_cols = n;
+        P.length = alg1x_length(m, l, n);
+        for (int k = 0; k < l; k++) {
+            std::vector<std::pair<int, int>> e, o;
+            for (int i = 0; i < m; i++)
+                for (int j = 0; j < n; j++) {
+                    const int dst = P.flat(i, j, m, n);
+                    e.push_back({dst, P.flat(i, j + k, m, W)});
+                    o.push_back({dst, P.flat((i + k) % l, j, l, n)});
+                }
+            PlanIter it;
+            it.eps = group(e);
+            it.omg = group(o);
+            P.iters.push_back(it);
+        }
+        return P;
+    }
     alg2_shape(m, l, n, P.kase, P.p, P.t, P.M, P.Np, P.WA, P.HB);
     P.col = P.kase != 'B';
     P.a_rows = P.M;
@@ -178,7 +214,8 @@ std::vector<uint64_t> HostPlan::a_slots(const int64_t *A, uint64_t tm) const {
     std::vector<uint64_t> v((size_t)a_rows * a_cols, 0);
     for (int i = 0; i < a_rows; i++)
         for (int c = 0; c < a_cols; c++) {
-            // Algorithm 1: sigma(A)_{i,c} = A_{i,[i+c]_l}.
+            // Algorithm 1: sigma(A)_{i,c} = A_{i,[i+c]_l} (with the extended
+            // layout, c < l + n - 1: sigma(A)'s column c mod l, the same entry).
             // Algorithm 2: eps^0(sigma(Abar))_{i,c} = Abar_{i,[i+c]_l}, Abar row i = A row i mod m.
             const int src_row = (alg == 2 && kase == 'A') ? i % m : i;
             const int64_t x = A[(size_t)src_row * l + imod((long long)i + c, l)];

@@ -73,6 +73,7 @@ std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S, int cost =
 // Number of slots Algorithm 1 / 2 needs for (m, l, n).
 int alg1_length(int m, int l, int n);
 int alg2_length(int m, int l, int n);
+int alg1x_length(int m, int l, int n);
 // AUTO: Algorithm 2 if it fits S slots, else Algorithm 1, else 0.
 int resolve_alg(int m, int l, int n, int alg, int S);
 HostPlan make_host_plan(int m, int l, int n, int alg);

@@ -20,6 +20,7 @@ HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
+ALG_1X = 3  # Algorithm 1 with the extended pre-layout (planner / encoding only in this version)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_ONE = 1, 2, 3, 4, 5, 6
 TUNE_WAIT_LIMIT, TUNE_TEST_DROP = 7, 8
 ROLE_A, ROLE_B = 0, 1

@@ -64,14 +64,14 @@ def oracle_describe(m, l, n, alg, S):
 
 def test_host_planner_matches_oracle_small_shapes(H):
     for m, l, n in itertools.product(range(1, 8), repeat=3):
-        for alg in (1, 2):
+        for alg in (1, 2, 3):
             assert H.hegmm_plan_describe(m, l, n, alg, 4096) == oracle_describe(m, l, n, alg, 4096), (m, l, n, alg)
 
 
 @pytest.mark.parametrize("shape", W.TINY_SHAPES + W.MEDIUM_SHAPES + [(64, 64, 64), (128, 16, 64), (2, 5, 7), (5, 4, 2)])
 def test_host_planner_matches_oracle_config_shapes(H, shape):
     m, l, n = shape
-    for alg in (1, 2):
+    for alg in (1, 2, 3):
         S = 8192
         if not SL.fits(m, l, n, alg, S):
             continue
@@ -87,7 +87,7 @@ def test_host_layouts_match_oracle(H):
     for m, l, n in [(4, 8, 6), (5, 3, 9), (7, 5, 2), (3, 3, 3), (6, 2, 4)]:
         A = rng.integers(-8, 8, size=(m, l))
         B = rng.integers(-8, 8, size=(l, n))
-        for alg in (1, 2):
+        for alg in (1, 2, 3):
             p = SL.make_plan(m, l, n, alg)
             got_a = H.hegmm_plan_layout(m, l, n, alg, 4096, 0, A, 65537)
             got_b = H.hegmm_plan_layout(m, l, n, alg, 4096, 1, B, 65537)
@@ -101,7 +101,7 @@ def test_host_slot_maps_match_oracle(H):
     for m in range(1, 7):
         for l in range(1, 7):
             for n in range(1, 7):
-                for alg in (1, 2):
+                for alg in (1, 2, 3):
                     for role in (0, 1):
                         assert H.hegmm_plan_slot_map(m, l, n, alg, 256, role) == SL.layout_source(role, m, l, n, alg)
                     assert H.hegmm_plan_slot_map(m, l, n, alg, 256, 2) == SL.result_source(m, l, n, alg)
