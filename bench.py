@@ -1,15 +1,19 @@
 """Benchmark: encrypted HEGMM products per second on one GB300 (or N replicas).
 
-Workload (the medium configuration): ring N=8192, t=65537, five chain primes
-below 2^40 plus one special prime (dnum=5); products A 16x32 . B 32x24 and
-A 32x8 . B 8x48, each with Algorithm 1 (HEGMM) and Algorithm 2
-(HEGMM-Enhanced), entries uniform in [-8, 7] mod t, seed 0.  One step = these
-four encrypted products.  Operands are encrypted before the timed region and
-stay resident in HBM; the per-step working set (Galois keys of all four
-plans, about 2.4 GB) is far larger than L2, and L2 is also flushed between
-timed steps (outside the per-step CUDA events).
+Default workload (the paper-scale configuration): ring N=16384, t=65537,
+eight chain primes below 2^50 plus two special primes (hybrid key switching,
+dnum=4); products A 64x64 . B 64x64, A 32x128 . B 128x16 (Algorithm 1:
+Algorithm 2 would need 16384 > 8192 slots) and A 128x16 . B 16x64
+(Algorithm 2), entries uniform in [0, 255], seed 0.  One step = these three
+encrypted products in one batched call.  Operands are encrypted before the
+timed region and stay resident in HBM; the per-step working set (Galois keys,
+masks) is far larger than L2, and L2 is also flushed between timed steps
+(outside the per-step CUDA events).  The one-product-per-launch path is timed
+beside it (``per_product_path``), and the medium configuration (N=8192,
+16x32x24 and 32x8x48 under both algorithms) under ``medium_workload``.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload paper|medium|batch|serve|blocked|product]
 
 Prints one JSON line.  --impl reference times the plain CPU oracle
 (oracle/) on this host's cores on a bounded sample of the same workload.
@@ -19,6 +23,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -33,9 +38,6 @@ sys.path.insert(0, ROOT)
 
 import workload as W  # noqa: E402
 
-PRESET = W.MEDIUM
-SHAPES = W.MEDIUM_SHAPES
-ALGS = (1, 2)
 METRIC = "HEGMM encrypted matmuls/s (N=8192 ring, 16x32x24 + 32x8x48, Alg 1 + Alg 2)"
 METRIC_BATCH = "HEGMM encrypted matmuls/s (batch of 512 mixed shapes, N=8192 ring)"
 METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 128x16x64, AUTO algorithm)"
@@ -44,16 +46,30 @@ KEY_SEED = 7
 SERVE_ARENA_GIB = 16  # server workspace, split over its streams
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
+COUNTERS = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 # hegmm_set_keyswitch_mode flags per --ks-mode (KS_DOUBLE = 1, KS_LAZY_RELIN = 2, KS_SHARED = 4)
 KS_MODES = {"double+lazy+shared": 7, "double+lazy": 3, "double": 1, "single": 0, "single+lazy": 2,
             "single+shared": 4}
+
+
+def workload_products(kind):
+    """[(m, l, n, alg)] of a throughput workload (alg 0 = AUTO)."""
+    if kind == "paper":
+        return [(m, l, n, 0) for (m, l, n) in W.PAPER_SHAPES]
+    if kind == "medium":
+        return [(m, l, n, a) for (m, l, n) in W.MEDIUM_SHAPES for a in (1, 2)]
+    raise ValueError(kind)
+
+
+def workload_preset(kind):
+    return {"paper": W.PAPER, "medium": W.MEDIUM, "batch": W.MEDIUM}[kind]
 
 
 def workload_config(extra=None):
     cfg = {
         "workload": "medium: N=8192, t=65537, 5x40-bit + 1 special prime, dnum=5; "
                     "A16x32.B32x24 and A32x8.B8x48, Algorithm 1 and Algorithm 2 each; entries U[-8,7] seed 0",
-        "products_per_step": len(SHAPES) * len(ALGS),
+        "products_per_step": len(workload_products("medium")),
         "l2": "flushed between timed steps (256 MiB write) and per-step key working set > L2",
         "launch": "each cached product plan replayed as one CUDA graph; per-kernel times from a second pass of the "
                   "same steps launched kernel by kernel with CUDA events on the library stream",
@@ -148,36 +164,40 @@ class ClockSampler:
 
 
 _oracle_cache = {}
+SAMPLE_KEYS = 4  # distinct rotation offsets of the sample (a rotation's cost does not depend on it)
 
 
-def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2, preset=None):
-    """Times the oracle on a bounded sample of the workload.
+def oracle_sample(prods, preset, nrot=6, ncm=6, nmul=2):
+    """Times the oracle on a bounded sample of a workload.
 
     The oracle executes a product as a fixed sequence of HE-Rot, HE-CMult,
-    HE-Add and HE-Mult calls (no reuse between iterations), so its time per
-    step is the op counts of the four plans times the measured time of each
-    op.  The sample runs ``nrot`` rotations (distinct offsets), ``ncm``
-    mask products and additions and ``nmul`` relinearised products at the
-    workload's parameters; key generation is excluded.
-    Returns (estimated seconds per step, description).
+    HE-Add and HE-Mult calls (no reuse between iterations: the paper's cost
+    model), so its time per workload step is the plans' op counts times the
+    measured time of each op.  The sample runs ``nrot`` rotations (cycling
+    over SAMPLE_KEYS offsets), ``ncm`` mask products and additions and
+    ``nmul`` relinearised products at the workload's parameters; key
+    generation is excluded.  prods: [(m, l, n, alg)], alg 0 = AUTO.
+    Returns (extrapolated seconds per workload step, description, seconds
+    the sample itself took).
     """
     from oracle import he as OH
     from oracle import slots as SL
 
-    pre = preset or PRESET
+    pre = preset
     if pre.name not in _oracle_cache:
         o = OH.Oracle(pre)
         o.keygen(KEY_SEED)
-        for z in range(1, nrot + 1):
+        for z in range(1, SAMPLE_KEYS + 1):
             o.add_galois_key(o.galois(z))
         _oracle_cache[pre.name] = o
     o = _oracle_cache[pre.name]
     x = np.arange(o.S) % o.t
     ct = o.encrypt(o.encode(x), 1, 0)
     pt = o.plaintext_eval(o.encode((x * 3) % o.t), o.L)
+    s0 = time.perf_counter()
     t0 = time.perf_counter()
-    for z in range(1, nrot + 1):
-        o.rotate(ct, z)
+    for i in range(nrot):
+        o.rotate(ct, 1 + i % SAMPLE_KEYS)
     t_rot = (time.perf_counter() - t0) / nrot
     t0 = time.perf_counter()
     for _ in range(ncm):
@@ -191,18 +211,98 @@ def oracle_sample(prods=None, nrot=6, ncm=6, nmul=2, preset=None):
     for _ in range(nmul):
         o.mult_relin(ct, r)
     t_mul = (time.perf_counter() - t0) / nmul
+    sample_s = time.perf_counter() - s0
     total = 0.0
-    if prods is None:
-        prods = [(m, l, n, alg) for (m, l, n) in SHAPES for alg in ALGS]
     for (m, l, n, alg) in prods:
         a = alg if alg else SL.choose_alg(m, l, n, o.S)
         c = SL.make_plan(m, l, n, a).counts()
         total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
-    desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=%d/L=%d; "
-            "per-step time = op counts of the %d plans x measured op times (%.1f/%.1f/%.1f/%.1f ms "
-            "rot/cmult/add/mult); keygen excluded" % (nrot, ncm, nmul, o.N, o.L, len(prods), t_rot * 1e3,
-                                                       t_cm * 1e3, t_add * 1e3, t_mul * 1e3))
-    return total, desc
+    desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=%d/L=%d timed (%.1f s); "
+            "per-step time = op counts of the %d plans (the oracle's single-mode op sequence) x measured op times "
+            "(%.1f/%.2f/%.2f/%.1f ms rot/cmult/add/mult); keygen excluded"
+            % (nrot, ncm, nmul, o.N, o.L, sample_s, len(prods), t_rot * 1e3, t_cm * 1e3, t_add * 1e3, t_mul * 1e3))
+    return total, desc, sample_s
+
+
+def _oracle_worker(args):
+    """One all-cores worker (spawned process): set-up, then the sample once
+    the parent releases every worker together."""
+    prods, preset_name, nrot, ncm, nmul, ready, go = args
+    pre = W.PRESETS[preset_name]
+    oracle_sample(prods, pre, 1, 1, 1)  # keys and tables, untimed
+    ready.put(1)
+    go.wait()
+    sec, _, sample_s = oracle_sample(prods, pre, nrot, ncm, nmul)
+    return sec, sample_s
+
+
+def cpu_baseline(prods, preset, single=(40, 40, 12), each=(16, 16, 4)):
+    """The oracle on this host's cores: the single-core sample (about 10 s
+    of CPU work at N=2^14), then every core running the smaller sample at
+    once (spawned processes, released together).  Both are extrapolated from
+    timed op samples to the workload step (see oracle_sample)."""
+    sec, desc, sample_s = oracle_sample(prods, preset, *single)
+    one = len(prods) / sec
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    out = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle", "method": "extrapolated",
+           "sample": desc, "sample_s": sample_s}
+    if cores > 1:
+        ctx = mp.get_context("spawn")
+        with ctx.Manager() as man:
+            go, ready = man.Event(), man.Queue()
+            with ctx.Pool(cores) as pool:
+                res = pool.map_async(_oracle_worker, [(prods, preset.name, *each, ready, go)] * cores)
+                for _ in range(cores):  # every worker has finished its set-up
+                    ready.get(timeout=600)
+                w0 = time.perf_counter()
+                go.set()
+                got = res.get(timeout=600)
+                wall = time.perf_counter() - w0
+        allv = sum(len(prods) / sec_i for sec_i, _ in got)
+        out = {"value": allv, "unit": UNIT, "cores": cores, "kind": "oracle", "method": "extrapolated",
+               "sample": "every core at once (spawned processes released together, %.1f s wall): %d rotations, "
+                         "%d mask products + adds, %d relinearised products each, extrapolated per core as the "
+                         "single-core figure and summed" % (wall, *each),
+               "single_core": out}
+    return out
+
+
+def run_reference(args):
+    """The reference arm: the plain CPU oracle (there is no other
+    implementation of the paper's method; its own code is not published) on
+    this host's cores, on the bench's workload.  Each step is a bounded
+    sample of the workload's operations, timed; the line's ms_per_step is
+    that sample's measured time and its value the throughput the sample
+    extrapolates to for the whole workload step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    kind = args.workload if args.workload in ("paper", "medium") else "paper"
+    prods = workload_products(kind)
+    pre = workload_preset(kind)
+    for _ in range(args.warmup):
+        oracle_sample(prods, pre)
+    secs, samples = [], []
+    desc = ""
+    for _ in range(args.steps):
+        sec, desc, sample_s = oracle_sample(prods, pre)
+        secs.append(sec)
+        samples.append(sample_s)
+    sec = statistics.mean(secs)
+    value = len(prods) / sec
+    cfg = (paper_config if kind == "paper" else workload_config)()
+    line = {
+        "impl": "reference", "metric": METRIC_PAPER if kind == "paper" else METRIC, "value": value, "unit": UNIT,
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(samples) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": cfg,
+        "value_method": "extrapolated: each step times an op sample of the workload (ms_per_step) and scales it by "
+                        "the plans' op counts to a whole workload step (%.1f s per step on one core)" % sec,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "method": "extrapolated",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
 
 
 def max_over_ranks(ms: float, world: int, dist=None, device="cpu") -> float:
@@ -219,30 +319,6 @@ def max_over_ranks(ms: float, world: int, dist=None, device="cpu") -> float:
 def whole_job_value(products_per_rank: int, world: int, ms: float) -> float:
     """Matmuls per second over all ranks (replicas: each rank runs its own products)."""
     return products_per_rank * world / (ms / 1e3)
-
-
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    for _ in range(args.warmup):
-        oracle_sample()
-    times = []
-    desc = ""
-    for _ in range(args.steps):
-        t, desc = oracle_sample()
-        times.append(t)
-    sec = statistics.mean(times)
-    value = len(SHAPES) * len(ALGS) / sec
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": workload_config(),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
 
 
 # ----------------------------------------------------------------------------- serving
@@ -484,10 +560,10 @@ def kernel_source_sha():
 
 
 def run_product(args):
-    """One product of --shape on the medium ring, run once and then --reps
-    times; prints the per-kernel times of the repeated runs (the small case
-    of the ncu captures: with --reps 1 the second product's launches are the
-    captured ones, about 2 GB on the device)."""
+    """One product of --shape on the --ring preset (medium by default), run
+    once and then --reps times; prints the per-kernel times of the repeated
+    runs (the small case of the ncu captures: with --reps 1 the second
+    product's launches are the captured ones, a few GB on the device)."""
     import torch
 
     from paper_2405_02238_gb300 import build as B
@@ -497,7 +573,7 @@ def run_product(args):
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    pre = PRESET
+    pre = W.PRESETS[args.ring]
     ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
     ctx.hegmm_set_keyswitch_mode(KS_MODES[args.ks_mode])
     if args.lt_kernel >= 0:
@@ -507,7 +583,7 @@ def run_product(args):
     if args.lt_chunk >= 0:
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, args.lt_chunk)
     m, l, n = (int(v) for v in args.shape.lower().split("x"))
-    A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
+    A, Bm = W.matrices(m, l, n, *(W.PAPER_RANGE if args.ring == "paper" else W.MEDIUM_RANGE))
     ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
     ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, args.alg), 1, 0)
     cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, args.alg), 1, 1)
@@ -515,15 +591,17 @@ def run_product(args):
     torch.cuda.synchronize()
     ctx.hegmm_kernel_reset()
     ctx.hegmm_set_timing(True)
+    torch.cuda.profiler.start()  # a profiler started with capture off records these products only
     for _ in range(max(1, args.reps)):
         c, _ = ctx.hegmm_matmul(ca, cb, m, l, n, args.alg)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     ctx.hegmm_set_timing(False)
     if not (ctx.hegmm_decrypt(c, m, l, n, args.alg).astype(np.int64) == (A @ Bm) % pre.t).all():
         raise SystemExit("product: decrypted result differs from A @ B mod t")
     ks = {k: {"ms": v[0], "launches": v[1], "algorithmic_bytes": v[2], "butterflies": v[3]}
           for k, v in ctx.hegmm_kernel_stats().items() if v[1]}
-    print(json.dumps({"workload": "product %dx%dx%d, algorithm %d, medium ring" % (m, l, n, args.alg),
+    print(json.dumps({"workload": "product %dx%dx%d, algorithm %d, %s ring" % (m, l, n, args.alg, args.ring),
                       "keyswitch_mode": args.ks_mode, "lt_kernel": args.lt_kernel, "lt_one": args.lt_one, "reps": args.reps,
                       "kernels": ks}))
 
@@ -531,113 +609,115 @@ def run_product(args):
 # ----------------------------------------------------------------------------- GPU arm
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "batch", "serve", "paper", "product", "blocked"],
-                    help="medium: the four medium-ring products (default); batch: 512 mixed shapes; "
-                         "serve: Poisson arrivals on the N=16384 ring; product: one product of --shape on the "
-                         "medium ring, run twice (the small case the ncu captures use); blocked: the 100x100 "
-                         "products of Section 4.4 split as P1 and P2 (N=16384 ring)")
-    ap.add_argument("--shape", default="16x32x24", help="m x l x n of --workload product")
-    ap.add_argument("--alg", type=int, default=1, help="algorithm of --workload product (1, 2; 0 = auto)")
-    ap.add_argument("--lt-kernel", type=int, default=-1,
-                    help="HEGMM_TUNE_LT_KERNEL variant (-1: autotuned, or the default for --workload product); "
-                         "--lt-kernel / --lt-chunk / --lt-one given replace the autotuner")
-    ap.add_argument("--lt-chunk", type=int, default=-1, help="HEGMM_TUNE_LT_CHUNK entries per item (-1: autotuned)")
-    ap.add_argument("--reps", type=int, default=1, help="--workload product: timed products after the first")
-    ap.add_argument("--lt-one", type=int, default=-1,
-                    help="HEGMM_TUNE_LT_ONE one-output kernel (-1: autotuned, or the default for --workload product)")
-    ap.add_argument("--rates", default="10,30,100,300,1000,2000")
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--max-requests", type=int, default=1000)
-    ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
-    ap.add_argument("--max-batch", type=int, default=64)
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning instead of hegmm_autotune")
-    ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
-                    help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "serve":
-        if int(os.environ.get("RANK", "0")) != 0:
-            return None  # the serving sweep runs on one GPU: other ranks exit without work
-        return run_serve(args)
-    if args.workload == "product":
-        if int(os.environ.get("RANK", "0")) != 0:
-            return None  # one GPU: other ranks exit without work
-        return run_product(args)
-    if args.workload == "blocked":
-        if int(os.environ.get("RANK", "0")) != 0:
-            return None  # one GPU: other ranks exit without work
-        return run_blocked(args)
+def load_counters():
+    """ncu counters of the current kernel sources (profiles/ncu_traffic.json):
+    DRAM traffic per algorithmic byte and warp-instructions per butterfly,
+    per kernel; empty when the sources changed since they were taken."""
+    if not os.path.exists(COUNTERS):
+        return {}
+    try:
+        tj = json.load(open(COUNTERS))
+    except Exception:
+        return {}
+    return tj if tj.get("kernels_sha") == kernel_source_sha() else {}
 
+
+def roofline(name, stats, hbm_peak, bfly_peak, issue_peak, counters):
+    """Roofline entry of one kernel bucket from the per-kernel pass: HBM
+    kernels against the measured copy rate; NTT-family kernels (integer
+    pipes) against the chip's warp-instruction issue rate (SMs x 4 schedulers
+    x 1 instruction per cycle x the sampled SM clock) divided by the
+    kernel's warp-instructions per butterfly from ncu, with the in-library
+    register-only butterfly probe beside it."""
+    kms, kn, kbytes, kwork = stats[name]
+    r = {"kernel": name, "launches": kn, "avg_launch_us": kms * 1e3 / max(kn, 1),
+         "share_of_kernel_time": kms / max(sum(v[0] for v in stats.values()), 1e-9)}
+    if kwork > 0:
+        bps = kwork / (kms / 1e3)
+        ipb = counters.get("warp_inst_per_butterfly", {}).get(name)
+        r.update({"bound": "alu", "unit": "Gbutterfly/s", "achieved": bps / 1e9,
+                  "butterflies_per_launch": kwork / max(kn, 1),
+                  "butterfly_probe_peak": bfly_peak / 1e9, "frac_of_butterfly_probe": bps / bfly_peak})
+        if ipb:
+            r.update({"peak": issue_peak["warp_inst_per_s"] / ipb / 1e9, "warp_inst_per_butterfly": ipb,
+                      "peak_source": "derived: %d SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (median "
+                                     "SM clock in the timed region) / %.1f warp-instructions per butterfly (ncu, "
+                                     "these kernel sources)" % (issue_peak["sms"], issue_peak["mhz"], ipb)})
+        else:
+            r.update({"peak": bfly_peak / 1e9, "peak_source": "measured: hegmm_peak_butterflies (register-only "
+                                                               "lazy Shoup butterflies on every SM)"})
+    else:
+        r.update({"bound": "hbm", "unit": "GB/s", "achieved": kbytes / (kms / 1e3) / 1e9,
+                  "peak": hbm_peak or HBM_FALLBACK,
+                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else "fallback"})
+    r["frac"] = r["achieved"] / r["peak"]
+    r["algorithmic_bytes_per_launch"] = kbytes / max(kn, 1)
+    tr = counters.get("traffic_per_algorithmic_byte", {}).get(name)
+    r["traffic"] = tr * r["algorithmic_bytes_per_launch"] if tr else None
+    return r
+
+
+def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
+    """Times one throughput workload (paper, medium or batch): autotune,
+    warm-up with a decryption check of every product, the timed steps (CUDA
+    events on the library stream around graph replays, L2 flushed between
+    steps), a per-kernel pass, the plain per-product path, e2e through host
+    buffers; with full, the other key-switch order and two-row packing too.
+    Returns the JSON line's fields."""
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2405_02238_gb300 import build as B
-
-    B.build()
-    from paper_2405_02238_gb300 import hegmm as H
-
-    stream = torch.cuda.Stream(device=dev)
-    paper = args.workload == "paper"
-    pre = W.PAPER if paper else PRESET
+    pre = workload_preset(kind)
     ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
     ks_code = KS_MODES
     ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
     prods = []
-    if args.workload == "batch":
+    if kind == "batch":
         for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
             A, Bm = W.matrices(m, l, n, *W.BATCH_RANGE, seed=i)
             prods.append((m, l, n, H.ALG_AUTO, A, Bm))
-        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods], H.ALG_AUTO)
-    elif paper:
-        for (m, l, n) in W.PAPER_SHAPES:
-            A, Bm = W.matrices(m, l, n, *W.PAPER_RANGE)
-            prods.append((m, l, n, H.ALG_AUTO, A, Bm))
-        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods], H.ALG_AUTO)
+        rng = W.BATCH_RANGE
     else:
-        for (m, l, n) in SHAPES:
-            A, Bm = W.matrices(m, l, n, *W.MEDIUM_RANGE)
-            for alg in ALGS:
-                prods.append((m, l, n, alg, A, Bm))
-        ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_1)
-        ctx.hegmm_keygen(KEY_SEED, [(m, l, n) for (m, l, n, _, _, _) in prods[::2]], H.ALG_2)
+        rng = W.PAPER_RANGE if kind == "paper" else W.MEDIUM_RANGE
+        for (m, l, n, alg) in workload_products(kind):
+            A, Bm = W.matrices(m, l, n, *rng)
+            prods.append((m, l, n, alg, A, Bm))
+    for alg in sorted({p[3] for p in prods}):
+        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods if p[3] == alg], alg)
     ops = []
     for i, (m, l, n, alg, A, Bm) in enumerate(prods):
         ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 1 + rank, 2 * i)
         cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, alg), 1 + rank, 2 * i + 1)
         ops.append((ca, cb))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    # one step = every product of the workload in one hegmm_matmul_batch_algs call
-
     algs = [p[3] for p in prods]
 
-    def step():
+    def step():  # one step = every product of the workload in one call
         return ctx.hegmm_matmul_batch_algs([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs)
 
     def single_path(sample):
         """The plain path: one hegmm_matmul call per product."""
-        outs, cnts = [], []
+        outs = []
         for i in sample:
             (m, l, n, alg, _, _), (ca, cb) = prods[i], ops[i]
-            c, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, alg)
-            outs.append(c)
-            cnts.append(cnt)
-        return outs, cnts
+            outs.append(ctx.hegmm_matmul(ca, cb, m, l, n, alg)[0])
+        return outs
+
+    def timed(fn, steps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            r = fn()
+            ev[k][1].record(stream)
+            del r
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def check(outs, what):
+        for (m, l, n, alg, A, Bm), c in zip(prods, outs):
+            got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
+            assert (got == (A @ Bm) % pre.t).all(), "wrong product %dx%dx%d alg %d (%s)" % (m, l, n, alg, what)
 
     # the library's autotuner picks the bit-neutral kernel knobs on this
     # workload, unless they are given (a profiler's serialised launches would
@@ -653,54 +733,37 @@ def main():
     elif not args.no_autotune:
         tuning = ctx.hegmm_autotune([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs,
                                     reps=3 if len(prods) <= 64 else 1)
-    # warm-up (builds plans, masks) and a correctness check of every product
-    for w in range(max(args.warmup, 1)):
+    for _ in range(max(args.warmup, 1)):  # builds plans and masks, captures graphs
         outs = step()
-    for (m, l, n, alg, A, Bm), c in zip(prods, outs):
-        got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
-        assert (got == (A @ Bm) % pre.t).all(), "wrong product %dx%dx%d alg %d" % (m, l, n, alg)
+    check(outs, args.ks_mode)
     del outs
     sample = list(range(len(prods))) if len(prods) <= 8 else list(range(0, len(prods), len(prods) // 32))
-    _, cnts = single_path(sample)
-    sc = [H.hegmm_plan_counts(m, l, n, alg, ctx.S) for (m, l, n, alg, _, _) in prods]
-    ksw_per_step = sum(c["ksw"] for c in sc)
-    paper_rot_per_step = sum(c["rot"] for c in sc)
-    # plain per-product path on the sample (warm), for comparison
-    torch.cuda.synchronize()
+    check_sample = single_path(sample)
+    for i, c in zip(sample, check_sample):
+        m, l, n, alg, A, Bm = prods[i]
+        assert (ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64) == (A @ Bm) % pre.t).all()
+    del check_sample
+    sc = [H.hegmm_plan_counts(m, l, n, alg if alg else 0, ctx.S) for (m, l, n, alg, _, _) in prods]
     for _ in range(2):
         single_path(sample)
-    torch.cuda.synchronize()
-    s_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    s_ev[0].record(stream)
-    for _ in range(3):
-        single_path(sample)
-    s_ev[1].record(stream)
-    torch.cuda.synchronize()
-    single_value = 3 * len(sample) / (s_ev[0].elapsed_time(s_ev[1]) / 1e3)
+    single_ms = sum(timed(lambda: single_path(sample), 3)) / 3
+    single_value = len(sample) / (single_ms / 1e3)
 
-    clk = ClockSampler(local)
+    clk = ClockSampler(dev.index or 0)
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     clk.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     t_wall0 = time.perf_counter()
     torch.cuda.profiler.start()  # profilers started with capture off record the timed steps only
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-        ev[k][0].record(stream)
-        outs = step()
-        ev[k][1].record(stream)
-        del outs
-    torch.cuda.synchronize()
+    step_ms = timed(step, args.steps)
     if world > 1:
         dist.barrier()
     torch.cuda.profiler.stop()
     wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dist if world > 1 else None, dev)
     per_step = len(prods)
     value = whole_job_value(per_step, world, ms)
@@ -709,71 +772,62 @@ def main():
     # replay each plan as one CUDA graph)
     ctx.hegmm_kernel_reset()
     ctx.hegmm_set_timing(True)
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-        outs = step()
-        del outs
-    torch.cuda.synchronize()
+    timed(step, args.steps)
     ctx.hegmm_set_timing(False)
     stats = ctx.hegmm_kernel_stats()
 
-    # the other key-switch evaluation order on the same products, for comparison
-    other = "single" if args.ks_mode != "single" else "double+lazy+shared"
-    ctx.hegmm_set_keyswitch_mode(ks_code[other])
-    outs = step()
-    for (m, l, n, alg, A, Bm), c in zip(prods, outs):
-        got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
-        assert (got == (A @ Bm) % pre.t).all(), "wrong product (%s mode)" % other
-    del outs
-    o_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-        o_ev[k][0].record(stream)
+    out = {"value": value, "ms_per_step": ms, "products_per_step": per_step, "tuning": tuning or "defaults",
+           "clocks": clocks, "wall_s_timed": wall,
+           "keyswitches_per_step": sum(c["ksw"] for c in sc), "paper_rotations_per_step": sum(c["rot"] for c in sc),
+           "per_product_path": {"value": single_value * world, "unit": UNIT, "ms_per_product": single_ms / len(sample),
+                                "how": "one hegmm_matmul call per product, %d of the %d products, warm"
+                                       % (len(sample), len(prods))},
+           "batch_over_per_product": value / (single_value * world)}
+    out["keyswitches_per_s"] = out["keyswitches_per_step"] * world / (ms / 1e3)
+
+    if full:
+        # the other key-switch evaluation order on the same products
+        other = "single" if args.ks_mode != "single" else "double+lazy+shared"
+        ctx.hegmm_set_keyswitch_mode(ks_code[other])
         outs = step()
-        o_ev[k][1].record(stream)
+        check(outs, other)
         del outs
-    torch.cuda.synchronize()
-    other_ms = sum(a.elapsed_time(b) for a, b in o_ev) / args.steps
-    ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
+        other_ms = sum(timed(step, args.steps)) / args.steps
+        ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
+        out["other_keyswitch_mode"] = {"mode": other, "value": per_step * world / (other_ms / 1e3), "unit": UNIT,
+                                       "ms_per_step": other_ms}
+        # two products per ciphertext pair (slot rows 0 and 1): every product of
+        # the workload with a second one of its shape, the same launches per step
+        pk_ops, pk_mats = [], []
+        for i, (m, l, n, alg, A, Bm) in enumerate(prods):
+            A2, B2 = W.matrices(m, l, n, *rng, seed=1000 + i)
+            pa = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_A, A, A2, m, l, n, alg), 1 + rank, 2 * i)
+            pb = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_B, Bm, B2, m, l, n, alg), 1 + rank, 2 * i + 1)
+            pk_ops.append((pa, pb))
+            pk_mats.append((A2, B2))
 
-    # two products per ciphertext pair (slot rows 0 and 1): every product of
-    # the workload with a second one of its shape, the same launches per step
-    pk_ops, pk_mats = [], []
-    for i, (m, l, n, alg, A, Bm) in enumerate(prods):
-        rng_lo_hi = W.BATCH_RANGE if args.workload == "batch" else (W.PAPER_RANGE if paper else W.MEDIUM_RANGE)
-        A2, B2 = W.matrices(m, l, n, *rng_lo_hi, seed=1000 + i)
-        pa = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_A, A, A2, m, l, n, alg), 1 + rank, 2 * i)
-        pb = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_B, Bm, B2, m, l, n, alg), 1 + rank, 2 * i + 1)
-        pk_ops.append((pa, pb))
-        pk_mats.append((A2, B2))
+        def packed_step():
+            return ctx.hegmm_matmul_batch_algs([a for a, _ in pk_ops], [b for _, b in pk_ops], [p[:3] for p in prods],
+                                               algs)
 
-    def packed_step():
-        return ctx.hegmm_matmul_batch_algs([a for a, _ in pk_ops], [b for _, b in pk_ops], [p[:3] for p in prods], algs)
-
-    outs = packed_step()
-    for (m, l, n, alg, A, Bm), (A2, B2), c in zip(prods, pk_mats, outs):
-        r0, r1 = ctx.hegmm_decrypt_pair(c, m, l, n, alg)
-        assert (r0.astype(np.int64) == (A @ Bm) % pre.t).all() and (r1.astype(np.int64) == (A2 @ B2) % pre.t).all()
-    del outs
-    p_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 0xFF)
-        p_ev[k][0].record(stream)
         outs = packed_step()
-        p_ev[k][1].record(stream)
+        for (m, l, n, alg, A, Bm), (A2, B2), c in zip(prods, pk_mats, outs):
+            r0, r1 = ctx.hegmm_decrypt_pair(c, m, l, n, alg)
+            assert (r0.astype(np.int64) == (A @ Bm) % pre.t).all() and (r1.astype(np.int64) == (A2 @ B2) % pre.t).all()
         del outs
-    torch.cuda.synchronize()
-    packed_ms = sum(a.elapsed_time(b) for a, b in p_ev) / args.steps
+        packed_ms = sum(timed(packed_step, args.steps)) / args.steps
+        out["two_row_packing"] = {"value": 2 * per_step * world / (packed_ms / 1e3), "unit": UNIT,
+                                  "ms_per_step": packed_ms, "products_per_step": 2 * per_step,
+                                  "how": "each ciphertext pair carries a second product of the same shape in slot "
+                                         "row 1 (hegmm_encode_pair); same calls, both rows checked by "
+                                         "hegmm_decrypt_pair"}
+        del pk_ops
 
     # e2e: host ciphertexts (coefficient domain, pinned) -> import -> product -> export
     host_in = []
-    for (m, l, n, alg, _, _), (ca, cb) in zip(prods, ops):
-        ha = torch.from_numpy(ctx.hegmm_ct_export(ca)).pin_memory()
-        hb = torch.from_numpy(ctx.hegmm_ct_export(cb)).pin_memory()
-        host_in.append((ha, hb))
+    for ca, cb in ops:
+        host_in.append((torch.from_numpy(ctx.hegmm_ct_export(ca)).pin_memory(),
+                        torch.from_numpy(ctx.hegmm_ct_export(cb)).pin_memory()))
     lv1 = ctx.level_after_product
     host_out = [torch.empty((2, lv1, ctx.N), dtype=torch.uint64).pin_memory() for _ in prods]
     h2d = sum(a.numel() * 8 + b.numel() * 8 for a, b in host_in)
@@ -793,79 +847,118 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - e0) * 1e3 / args.steps
+    out["e2e"] = {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
 
-    # roofline of the dominant kernel (and of the key inner product, the
-    # HBM-bound part of key switching)
+    # roofline of the dominant kernel, of the key inner product (the HBM
+    # part of key switching) and of the linear-transformation kernel
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm_peak = peaks.get("hbm_gbs")
-    bfly_peak = ctx.hegmm_peak_butterflies() / 1e9
-    total_kms = max(sum(v[0] for v in stats.values()), 1e-9)
-
-    def roofline(name):
-        kms, kn, kbytes, kwork = stats[name]
-        r = {"kernel": name, "launches": kn, "avg_launch_us": kms * 1e3 / max(kn, 1),
-             "share_of_kernel_time": kms / total_kms}
-        if kwork > 0:
-            r.update({"bound": "alu", "unit": "Gbutterfly/s", "achieved": kwork / (kms / 1e3) / 1e9,
-                      "peak": bfly_peak, "peak_source": "measured: hegmm_peak_butterflies (register-only "
-                      "lazy Shoup butterflies on every SM)"})
-        else:
-            peak = hbm_peak or HBM_FALLBACK
-            r.update({"bound": "hbm", "unit": "GB/s", "achieved": kbytes / (kms / 1e3) / 1e9, "peak": peak,
-                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_peak else "fallback"})
-        r["frac"] = r["achieved"] / r["peak"]
-        r["algorithmic_bytes_per_launch"] = kbytes / max(kn, 1)
-        return r
-
+    bfly_peak = ctx.hegmm_peak_butterflies()
+    props = torch.cuda.get_device_properties(dev)
+    mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    issue = {"sms": props.multi_processor_count, "mhz": mhz,
+             "warp_inst_per_s": props.multi_processor_count * 4 * mhz * 1e6}
+    counters = load_counters()
     name = max(stats.items(), key=lambda kv: kv[1][0])[0]
-    roof = roofline(name)
-    roof["traffic"] = None
-    src_sha = kernel_source_sha()
-    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            if tj.get("kernels_sha") == src_sha and name in tj.get("traffic_per_algorithmic_byte", {}):
-                roof["traffic"] = tj["traffic_per_algorithmic_byte"][name] * roof["algorithmic_bytes_per_launch"]
-        except Exception:
-            pass
+    out["roofline"] = roofline(name, stats, hbm_peak, bfly_peak, issue, counters)
+    for extra, key in (("ksw_inner_product", "roofline_key_inner_product"), ("lt_keyswitch", "roofline_lt_keyswitch"),
+                       ("divround_ntt", "roofline_moddown"), ("modup", "roofline_modup"), ("ntt_inv", "roofline_ntt_inv")):
+        if extra != name and stats.get(extra, (0, 0))[1]:
+            out[key] = roofline(extra, stats, hbm_peak, bfly_peak, issue, counters)
+    out["kernels"] = {k: {"ms": v[0], "launches": v[1]} for k, v in stats.items() if v[1]}
+    out["gpu_launches"] = int(sum(v[1] for v in stats.values()) / max(args.steps, 1)) * args.steps
+    out["prods"] = [p[:4] for p in prods]
+    out["preset"] = pre
+    del ops
+    ctx.close()
+    return out
 
-    batch = args.workload == "batch"
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-medium", action="store_true", help="skip the medium workload's extra key")
+    ap.add_argument("--workload", default="paper", choices=["paper", "medium", "batch", "serve", "product", "blocked"],
+                    help="paper: the three N=16384 products (default); medium: the four N=8192 products; batch: 512 "
+                         "mixed shapes; serve: Poisson arrivals on the N=16384 ring; product: one product of --shape "
+                         "on --ring, run twice (the small case the ncu captures use); blocked: the 100x100 products "
+                         "of Section 4.4 split as P1 and P2 (N=16384 ring)")
+    ap.add_argument("--shape", default="16x32x24", help="m x l x n of --workload product")
+    ap.add_argument("--ring", default="medium", choices=list(W.PRESETS), help="ring preset of --workload product")
+    ap.add_argument("--alg", type=int, default=1, help="algorithm of --workload product (1, 2, 3; 0 = auto)")
+    ap.add_argument("--lt-kernel", type=int, default=-1,
+                    help="HEGMM_TUNE_LT_KERNEL variant (-1: autotuned, or the default for --workload product); "
+                         "--lt-kernel / --lt-chunk / --lt-one given replace the autotuner")
+    ap.add_argument("--lt-chunk", type=int, default=-1, help="HEGMM_TUNE_LT_CHUNK entries per item (-1: autotuned)")
+    ap.add_argument("--reps", type=int, default=1, help="--workload product: timed products after the first")
+    ap.add_argument("--lt-one", type=int, default=-1,
+                    help="HEGMM_TUNE_LT_ONE one-output kernel (-1: autotuned, or the default for --workload product)")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--max-requests", type=int, default=1000)
+    ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
+    ap.add_argument("--max-batch", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning instead of hegmm_autotune")
+    ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
+                    help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    single_gpu = {"serve": run_serve, "product": run_product, "blocked": run_blocked}
+    if args.workload in single_gpu:
+        if int(os.environ.get("RANK", "0")) != 0:
+            return None  # these workloads run on one GPU: other ranks exit without work
+        return single_gpu[args.workload](args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm as H
+
+    stream = torch.cuda.Stream(device=dev)
+    kind = args.workload
+    r = measure_throughput(kind, args, H, dev, stream, world, rank, full=True)
+    cfg = {"paper": paper_config, "medium": workload_config, "batch": batch_config}[kind]
     line = {
-        "metric": METRIC_BATCH if batch else (METRIC_PAPER if paper else METRIC), "value": value, "unit": UNIT,
-        "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": (batch_config if batch else (paper_config if paper else workload_config))({
-                                                                "parallelism": "replicas" if world > 1 else "single-gpu",
-                                                                "keyswitch_mode": args.ks_mode,
-                                                                "tuning": tuning or "defaults"}),
-        "other_keyswitch_mode": {"mode": other, "value": per_step * world / (other_ms / 1e3), "unit": UNIT,
-                                 "ms_per_step": other_ms},
-        "two_row_packing": {"value": 2 * per_step * world / (packed_ms / 1e3), "unit": UNIT, "ms_per_step": packed_ms,
-                            "products_per_step": 2 * per_step,
-                            "how": "each ciphertext pair carries a second product of the same shape in slot row 1 "
-                                   "(hegmm_encode_pair); same calls, both rows checked by hegmm_decrypt_pair"},
-        "keyswitches_per_s": ksw_per_step * world / (ms / 1e3),
-        "paper_rotations_per_step": paper_rot_per_step,
-        "keyswitches_per_step": ksw_per_step,
-        "per_product_path": {"value": single_value * world, "unit": UNIT,
-                             "how": "one hegmm_matmul call per product, %d of the %d products, warm" % (
-                                 len(sample), len(prods))},
-        "wall_s_timed": wall,
-        "e2e": {"value": per_step * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-        "gpu_launches": int(sum(v[1] for v in stats.values()) / max(args.steps, 1)) * args.steps,
-        "roofline": roof,
-        "roofline_key_inner_product": roofline("ksw_inner_product") if stats["ksw_inner_product"][1] else None,
-        "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in stats.items() if v[1]},
-        "clocks": clocks,
+        "metric": {"paper": METRIC_PAPER, "medium": METRIC, "batch": METRIC_BATCH}[kind], "value": r["value"],
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": cfg({"parallelism": "replicas" if world > 1 else "single-gpu", "keyswitch_mode": args.ks_mode,
+                       "tuning": r["tuning"]}),
     }
+    for k in ("per_product_path", "batch_over_per_product", "other_keyswitch_mode", "two_row_packing",
+              "keyswitches_per_s", "keyswitches_per_step", "paper_rotations_per_step", "wall_s_timed", "e2e",
+              "gpu_launches", "roofline", "roofline_key_inner_product", "roofline_lt_keyswitch", "roofline_moddown",
+              "roofline_modup", "roofline_ntt_inv", "kernels", "clocks"):
+        if k in r:
+            line[k] = r[k]
+    if kind == "paper" and not args.no_medium:
+        # the medium configuration, measured the same way (fewer extras)
+        m = measure_throughput("medium", args, H, dev, stream, world, rank, full=False)
+        line["medium_workload"] = {
+            "workload": workload_config()["workload"], "metric": METRIC, "value": m["value"], "unit": UNIT,
+            "ms_per_step": m["ms_per_step"], "products_per_step": m["products_per_step"], "tuning": m["tuning"],
+            "per_product_path": m["per_product_path"], "e2e": m["e2e"], "keyswitches_per_step": m["keyswitches_per_step"],
+            "roofline": m["roofline"], "roofline_key_inner_product": m.get("roofline_key_inner_product"),
+            "kernels": m["kernels"], "clocks": m["clocks"]}
     if rank == 0 and not args.no_cpu_baseline:
-        # a bounded sample of about 10-30 s of single-core CPU work
-        sec, desc = oracle_sample([p[:4] for p in prods], nrot=40, ncm=40, nmul=12, preset=pre)
-        line["cpu_baseline"] = {"value": len(prods) / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc}
+        line["cpu_baseline"] = cpu_baseline(r["prods"], r["preset"])
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

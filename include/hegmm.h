@@ -451,6 +451,17 @@ int hegmm_modswitch(hegmm_ctx *ctx, const hegmm_ct *ct, hegmm_ct **out);        
  * HEGMM_ENOKEY, HEGMM_ECUDA. */
 int hegmm_rotate_noalloc(hegmm_ctx *ctx, const hegmm_ct *in, int z, hegmm_ct *out);
 
+/* Device memory seen by the library, after synchronising its stream:
+ * out[0] bytes in use from the device's default stream-ordered pool (the
+ * pool every allocation of this library comes from), out[1] the pool's
+ * high-water mark of that use since the last reset, out[2] bytes the pool
+ * holds from the device, out[3] free device memory (cudaMemGetInfo).  With
+ * reset_high != 0 the high-water mark restarts from the current use after
+ * it is read, so a later call shows whether anything in between allocated
+ * from the pool.  out is caller-owned, 4 entries.  Errors: HEGMM_EINVAL,
+ * HEGMM_ECUDA. */
+int hegmm_device_memory(hegmm_ctx *ctx, int reset_high, uint64_t *out);
+
 /* Level (number of chain primes) of a ciphertext. */
 int hegmm_ct_level(const hegmm_ct *ct);
 

@@ -103,14 +103,14 @@ static LimbPat pat_mods(u64 *base, int n, const int *mods, int count_outer, long
 
 // ---------------------------------------------------------------- tables
 
-int build_modup_tab(Ctx *c, int lv) {
-    ModUpTab tb;
-    tb.lv = lv;
-    tb.ne = lv + c->K;
-    tb.nd = c->digits(lv);
-    const int a = c->alpha;
-    std::vector<u64> h((size_t)tb.nd * a * 2 + (size_t)tb.nd * a * tb.ne * 3, 0);
-    for (int j = 0; j < tb.nd; j++) {
+// ModUp conversion table of level lv (host copy): [nd][alpha] x {hinv,
+// hinv_sh}, then [nd][alpha][ne] x {hat mod r, shoup, q_i mod r}, where
+// hinv = (Q_j / q_i)^-1 mod q_i and hat = Q_j / q_i mod r for prime q_i of
+// digit j and prime r of the extended basis.
+std::vector<u64> modup_table_host(const Ctx *c, int lv) {
+    const int ne = lv + c->K, nd = c->digits(lv), a = c->alpha;
+    std::vector<u64> h((size_t)nd * a * 2 + (size_t)nd * a * ne * 3, 0);
+    for (int j = 0; j < nd; j++) {
         const int lo = j * a, hi = std::min(lo + a, lv);
         for (int ii = 0; ii < hi - lo; ii++) {
             const int i = lo + ii;
@@ -121,18 +121,79 @@ int build_modup_tab(Ctx *c, int lv) {
             const u64 hi_inv = hinv(hat_qi, qi);
             h[((size_t)j * a + ii) * 2] = hi_inv;
             h[((size_t)j * a + ii) * 2 + 1] = shoup(hi_inv, qi);
-            for (int e = 0; e < tb.ne; e++) {
+            for (int e = 0; e < ne; e++) {
                 const u64 r = c->q[c->gidx(lv, e)];
                 u64 hat_r = 1;
                 for (int i2 = lo; i2 < hi; i2++)
                     if (i2 != i) hat_r = hmul(hat_r, c->q[i2] % r, r);
-                u64 *dst = &h[(size_t)tb.nd * a * 2 + (((size_t)j * a + ii) * tb.ne + e) * 3];
+                u64 *dst = &h[(size_t)nd * a * 2 + (((size_t)j * a + ii) * ne + e) * 3];
                 dst[0] = hat_r;
                 dst[1] = shoup(hat_r, r);
                 dst[2] = qi % r;
             }
         }
     }
+    return h;
+}
+
+// Exact-division table (host copy) and its modulus lists.  kind 0: ModDown
+// at level lv (keep q_0..q_{lv-1}, drop the K special primes); kind 1:
+// modulus switch from lv (keep q_0..q_{lv-2}, drop q_{lv-1}).  Layout:
+// [ndrop] x {coef, coef_sh}; [nkeep][ndrop] x {hat, hat_sh, d_k mod q_i};
+// [nkeep] x {Dinv, Dinv_sh, t mod q_i, shoup}; then keep[nkeep], drop[ndrop].
+std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int> &keep, std::vector<int> &drop) {
+    keep.clear();
+    drop.clear();
+    if (kind == 0) {
+        for (int i = 0; i < lv; i++) keep.push_back(i);
+        for (int k = 0; k < c->K; k++) drop.push_back(c->L + k);
+    } else {
+        for (int i = 0; i < lv - 1; i++) keep.push_back(i);
+        drop.push_back(lv - 1);
+    }
+    const int nkeep = (int)keep.size(), ndrop = (int)drop.size();
+    std::vector<u64> h;
+    for (int k = 0; k < ndrop; k++) {
+        const u64 dk = c->q[drop[k]];
+        u64 hat = 1;
+        for (int k2 = 0; k2 < ndrop; k2++)
+            if (k2 != k) hat = hmul(hat, c->q[drop[k2]] % dk, dk);
+        const u64 coef = hmul(hinv(c->t % dk, dk), hinv(hat, dk), dk);
+        h.push_back(coef);
+        h.push_back(shoup(coef, dk));
+    }
+    for (int i = 0; i < nkeep; i++) {
+        const u64 qi = c->q[keep[i]];
+        for (int k = 0; k < ndrop; k++) {
+            u64 hat = 1;
+            for (int k2 = 0; k2 < ndrop; k2++)
+                if (k2 != k) hat = hmul(hat, c->q[drop[k2]] % qi, qi);
+            h.push_back(hat);
+            h.push_back(shoup(hat, qi));
+            h.push_back(c->q[drop[k]] % qi);
+        }
+    }
+    for (int i = 0; i < nkeep; i++) {
+        const u64 qi = c->q[keep[i]];
+        u64 D = 1;
+        for (int k = 0; k < ndrop; k++) D = hmul(D, c->q[drop[k]] % qi, qi);
+        const u64 Di = hinv(D, qi);
+        h.push_back(Di);
+        h.push_back(shoup(Di, qi));
+        h.push_back(c->t % qi);
+        h.push_back(shoup(c->t % qi, qi));
+    }
+    for (int i = 0; i < nkeep; i++) h.push_back((u64)keep[i]);
+    for (int k = 0; k < ndrop; k++) h.push_back((u64)drop[k]);
+    return h;
+}
+
+int build_modup_tab(Ctx *c, int lv) {
+    ModUpTab tb;
+    tb.lv = lv;
+    tb.ne = lv + c->K;
+    tb.nd = c->digits(lv);
+    const std::vector<u64> h = modup_table_host(c, lv);
     tb.d = dalloc(c, h.size());
     if (!tb.d) return set_err(c, HEGMM_ENOMEM, "modup table");
     cudaMemcpyAsync(tb.d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->st);
@@ -141,53 +202,12 @@ int build_modup_tab(Ctx *c, int lv) {
     return cuda_check(c, "modup table");
 }
 
-// kind 0: ModDown at level lv (keep q_0..q_{lv-1}, drop the K special primes)
-// kind 1: modulus switch from lv (keep q_0..q_{lv-2}, drop q_{lv-1})
 int build_div_tab(Ctx *c, int lv, int kind) {
     DivTab tb;
-    if (kind == 0) {
-        for (int i = 0; i < lv; i++) tb.keep.push_back(i);
-        for (int k = 0; k < c->K; k++) tb.drop.push_back(c->L + k);
-    } else {
-        for (int i = 0; i < lv - 1; i++) tb.keep.push_back(i);
-        tb.drop.push_back(lv - 1);
-    }
+    const std::vector<u64> h = div_table_host(c, lv, kind, tb.keep, tb.drop);
     tb.nkeep = (int)tb.keep.size();
     tb.ndrop = (int)tb.drop.size();
     if (tb.ndrop > 4) return set_err(c, HEGMM_EINVAL, "at most 4 special primes");
-    std::vector<u64> h;
-    for (int k = 0; k < tb.ndrop; k++) {
-        const u64 dk = c->q[tb.drop[k]];
-        u64 hat = 1;
-        for (int k2 = 0; k2 < tb.ndrop; k2++)
-            if (k2 != k) hat = hmul(hat, c->q[tb.drop[k2]] % dk, dk);
-        const u64 coef = hmul(hinv(c->t % dk, dk), hinv(hat, dk), dk);
-        h.push_back(coef);
-        h.push_back(shoup(coef, dk));
-    }
-    for (int i = 0; i < tb.nkeep; i++) {
-        const u64 qi = c->q[tb.keep[i]];
-        for (int k = 0; k < tb.ndrop; k++) {
-            u64 hat = 1;
-            for (int k2 = 0; k2 < tb.ndrop; k2++)
-                if (k2 != k) hat = hmul(hat, c->q[tb.drop[k2]] % qi, qi);
-            h.push_back(hat);
-            h.push_back(shoup(hat, qi));
-            h.push_back(c->q[tb.drop[k]] % qi);
-        }
-    }
-    for (int i = 0; i < tb.nkeep; i++) {
-        const u64 qi = c->q[tb.keep[i]];
-        u64 D = 1;
-        for (int k = 0; k < tb.ndrop; k++) D = hmul(D, c->q[tb.drop[k]] % qi, qi);
-        const u64 Di = hinv(D, qi);
-        h.push_back(Di);
-        h.push_back(shoup(Di, qi));
-        h.push_back(c->t % qi);
-        h.push_back(shoup(c->t % qi, qi));
-    }
-    for (int i = 0; i < tb.nkeep; i++) h.push_back((u64)tb.keep[i]);
-    for (int k = 0; k < tb.ndrop; k++) h.push_back((u64)tb.drop[k]);
     tb.d = dalloc(c, h.size());
     if (!tb.d) return set_err(c, HEGMM_ENOMEM, "div table");
     cudaMemcpyAsync(tb.d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->st);
@@ -212,6 +232,11 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         p->alpha < 1 || p->alpha > 4 || p->L % p->alpha != 0 || p->K < p->alpha || p->K > 4 || p->eta < 1 ||
         p->eta > 31 || p->ms_drop < 0 || p->ms_drop > 1 || (p->ms_drop && p->L < 3))
         return set_err(c, HEGMM_EINVAL, "parameters outside the supported limits");
+    // ModUp's new limbs of one ciphertext form one limb pattern (pat_nonown)
+    if ((p->L / p->alpha) * (p->L + p->K) - p->L > PAT_MAX)
+        return set_err(c, HEGMM_EINVAL,
+                       "parameters outside the supported limits: digits(L) (L + K) - L ModUp limbs exceed " +
+                           std::to_string(PAT_MAX));
     const u64 two_n = 2 * (u64)c->N;
     if (!is_prime(p->t) || (p->t - 1) % two_n != 0) return set_err(c, HEGMM_EINVAL, "t must be a prime = 1 mod 2N");
     c->dnum = p->L / p->alpha;
@@ -979,6 +1004,33 @@ int hegmm_set_budgets(hegmm_ctx *h, uint64_t mask_bytes, uint64_t plan_bytes, ui
     if (mask_bytes) h->c.mask_budget = mask_bytes;
     if (plan_bytes) h->c.plan_cache_budget = plan_bytes;
     if (chunk_bytes) h->c.ws_budget = std::max<uint64_t>(chunk_bytes, (uint64_t)1 << 24);
+    return HEGMM_OK;
+}
+
+int hegmm_device_memory(hegmm_ctx *h, int reset_high, uint64_t *out) {
+    if (!h || !out) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_check(c, "device_memory");
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess)
+        return cuda_check(c, "device_memory: pool");
+    uint64_t used = 0, high = 0, reserved = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess)
+        return cuda_check(c, "device_memory: pool attributes");
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_check(c, "device_memory: cudaMemGetInfo");
+    out[0] = used;
+    out[1] = high;
+    out[2] = reserved;
+    out[3] = fr;
+    if (reset_high) {
+        uint64_t zero = 0;  // the high-water mark restarts from the current use
+        if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess)
+            return cuda_check(c, "device_memory: reset");
+    }
     return HEGMM_OK;
 }
 

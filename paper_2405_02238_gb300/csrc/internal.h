@@ -17,7 +17,10 @@ typedef uint32_t u32;
 namespace hg {
 
 constexpr int MAXM = 25;      // L + K primes plus t
-constexpr int PAT_MAX = 64;   // inner entries of a limb pattern
+// inner entries of a limb pattern; the largest pattern is the ModUp's
+// limbs outside each digit's own primes, digits(L) (L + K) - L entries, which
+// context creation checks against this bound
+constexpr int PAT_MAX = 128;
 
 // Per-modulus constants in device memory.
 struct ModDev {
@@ -203,6 +206,7 @@ struct Ctx {
     size_t plan_cache_budget = (size_t)48 << 30;  // workspace kept by cached batch plans
     u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
     std::map<int, u64 *> crt;        // level -> CRT-to-t table
+    std::map<int, std::vector<u64>> noalloc_tabs;  // level -> host tables of the scratch-free rotation
 
     bool timing = false;
     struct Pending {
@@ -298,6 +302,9 @@ int permute_limbs(Ctx *c, int nlimb, const u64 *in, u64 *out, u32 g);
 // ---------------------------------------------------------------- tables / memory
 int build_modup_tab(Ctx *c, int lv);
 int build_div_tab(Ctx *c, int lv, int kind);
+// host copies of the same tables (layouts at their definitions in ctx.cu)
+std::vector<u64> modup_table_host(const Ctx *c, int lv);
+std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int> &keep, std::vector<int> &drop);
 u64 *dalloc(Ctx *c, size_t words);
 void dfree(Ctx *c, void *p);
 int set_err(Ctx *c, int code, const std::string &msg);

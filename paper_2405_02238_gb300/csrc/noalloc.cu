@@ -34,20 +34,6 @@ static __device__ __align__(256) u64 g_noalloc_scratch[NOALLOC_WORDS];
 constexpr int NOALLOC_MAX_DEV = 64;
 static u64 *s_scratch[NOALLOC_MAX_DEV];
 
-typedef unsigned __int128 u128;
-static u64 nm(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
-static u64 npow(u64 a, u64 e, u64 q) {
-    u64 r = 1 % q;
-    a %= q;
-    for (; e; e >>= 1) {
-        if (e & 1) r = nm(r, a, q);
-        a = nm(a, a, q);
-    }
-    return r;
-}
-static u64 ninv(u64 a, u64 q) { return npow(a, q - 2, q); }
-static u64 nsh(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
-
 }  // namespace hg
 
 using namespace hg;
@@ -71,10 +57,20 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     auto kit = c->keys.find(g);
     if (kit == c->keys.end()) return set_err(c, HEGMM_ENOKEY, "rotate_noalloc: missing Galois key");
 
+    // A call under stream capture would record the header upload below
+    // against a host buffer that the capture does not own.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->st, &cap) != cudaSuccess) return cuda_check(c, "rotate_noalloc: capture status");
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_err(c, HEGMM_EINVAL, "rotate_noalloc: the context stream is capturing; call it outside capture");
+
     // Set-up, once per device: the device address of the scratch array.
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV)
-        return cuda_check(c, "rotate_noalloc: device");
+    if (cudaGetDevice(&dev) != cudaSuccess) return cuda_check(c, "rotate_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAX_DEV)
+        return set_err(c, HEGMM_EINVAL,
+                       "rotate_noalloc: device ordinal " + std::to_string(dev) + " beyond the scratch table (" +
+                           std::to_string(NOALLOC_MAX_DEV) + " devices)");
     if (!s_scratch[dev]) {
         u64 *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
@@ -88,8 +84,19 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     u64 *u = D + (size_t)nd * ne * N;
     u64 *tmp = u + (size_t)2 * ne * N;
 
-    // Header: RotDesc at word 0, two DivDesc at word 6, ModUp table at word
-    // 16, ModDown table after it (same layouts as the context's tables).
+    // Header: RotDesc at word 0, two DivDesc at word 6, then the ModUp and
+    // ModDown tables of this level (the context's table layouts, built by
+    // the same host functions and kept per level in host memory).
+    auto tit = c->noalloc_tabs.find(lv);
+    if (tit == c->noalloc_tabs.end()) {
+        std::vector<int> keep, drop;
+        std::vector<u64> t = modup_table_host(c, lv);
+        const std::vector<u64> dv = div_table_host(c, lv, 0, keep, drop);
+        t.insert(t.end(), dv.begin(), dv.end());
+        tit = c->noalloc_tabs.emplace(lv, std::move(t)).first;
+    }
+    const std::vector<u64> &tabs = tit->second;
+    const size_t n_mu = (size_t)nd * a * 2 + (size_t)nd * a * ne * 3;  // ModUp table words
     std::vector<u64> hdr(16, 0);
     RotDesc rd{D, kit->second, u, nullptr, nullptr, (u32)g, 0u};
     DivDesc dd[2];
@@ -104,66 +111,8 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     static_assert(sizeof(RotDesc) == 48 && sizeof(DivDesc) == 40, "descriptor layout");
     memcpy(&hdr[0], &rd, sizeof(rd));
     memcpy(&hdr[6], dd, sizeof(dd));
-    // ModUp table: [nd][a] {hinv, shoup}, [nd][a][ne] {hat mod r, shoup, q_i mod r}
-    const size_t o_mu = hdr.size();
-    hdr.resize(o_mu + (size_t)nd * a * 2 + (size_t)nd * a * ne * 3, 0);
-    for (int j = 0; j < nd; j++) {
-        const int lo = j * a, hi = std::min(lo + a, lv);
-        for (int ii = 0; ii < hi - lo; ii++) {
-            const int i = lo + ii;
-            const u64 qi = c->q[i];
-            u64 hq = 1;
-            for (int i2 = lo; i2 < hi; i2++)
-                if (i2 != i) hq = nm(hq, c->q[i2] % qi, qi);
-            const u64 hv = ninv(hq, qi);
-            hdr[o_mu + ((size_t)j * a + ii) * 2] = hv;
-            hdr[o_mu + ((size_t)j * a + ii) * 2 + 1] = nsh(hv, qi);
-            for (int e = 0; e < ne; e++) {
-                const u64 r = c->q[c->gidx(lv, e)];
-                u64 hr = 1;
-                for (int i2 = lo; i2 < hi; i2++)
-                    if (i2 != i) hr = nm(hr, c->q[i2] % r, r);
-                u64 *dst = &hdr[o_mu + (size_t)nd * a * 2 + (((size_t)j * a + ii) * ne + e) * 3];
-                dst[0] = hr;
-                dst[1] = nsh(hr, r);
-                dst[2] = qi % r;
-            }
-        }
-    }
-    // ModDown table: drop = special primes, keep = q_0..q_{lv-1}
-    const size_t o_dv = hdr.size();
-    for (int k = 0; k < K; k++) {
-        const u64 dk = c->q[c->L + k];
-        u64 hat = 1;
-        for (int k2 = 0; k2 < K; k2++)
-            if (k2 != k) hat = nm(hat, c->q[c->L + k2] % dk, dk);
-        const u64 coef = nm(ninv(c->t % dk, dk), ninv(hat, dk), dk);
-        hdr.push_back(coef);
-        hdr.push_back(nsh(coef, dk));
-    }
-    for (int i = 0; i < lv; i++) {
-        const u64 qi = c->q[i];
-        for (int k = 0; k < K; k++) {
-            u64 hat = 1;
-            for (int k2 = 0; k2 < K; k2++)
-                if (k2 != k) hat = nm(hat, c->q[c->L + k2] % qi, qi);
-            hdr.push_back(hat);
-            hdr.push_back(nsh(hat, qi));
-            hdr.push_back(c->q[c->L + k] % qi);
-        }
-    }
-    for (int i = 0; i < lv; i++) {
-        const u64 qi = c->q[i];
-        u64 P = 1;
-        for (int k = 0; k < K; k++) P = nm(P, c->q[c->L + k] % qi, qi);
-        const u64 Pi = ninv(P, qi);
-        hdr.push_back(Pi);
-        hdr.push_back(nsh(Pi, qi));
-        hdr.push_back(c->t % qi);
-        hdr.push_back(nsh(c->t % qi, qi));
-    }
-    for (int i = 0; i < lv; i++) hdr.push_back((u64)i);
-    for (int k = 0; k < K; k++) hdr.push_back((u64)(c->L + k));
+    const size_t o_mu = hdr.size(), o_dv = o_mu + n_mu;
+    hdr.insert(hdr.end(), tabs.begin(), tabs.end());
     if (hdr.size() > NOALLOC_HDR) return set_err(c, HEGMM_EINVAL, "rotate_noalloc: table header too large");
     // Every scratch word the kernels read is written earlier in this call, so
     // nothing has to be cleared; the header is rewritten on every call.
@@ -188,33 +137,11 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     if ((rc = modup_conv_tab(c, mt, 1, xc, (long long)lv * N, in->d + (size_t)lv * N, (long long)lv * N, D,
                              (long long)nd * ne * N)))
         return rc;
-    LimbPat pn{};
-    pn.base = D;
-    pn.outer_stride = (long long)nd * ne * N;
-    int k = 0;
-    for (int j = 0; j < nd; j++) {
-        const int lo = j * a, hi = std::min(lo + a, lv);
-        for (int e = 0; e < ne; e++) {
-            if (e >= lo && e < hi) continue;
-            pn.off[k] = (unsigned short)(j * ne + e);
-            pn.mod[k] = (unsigned char)c->gidx(lv, e);
-            k++;
-        }
-    }
-    pn.inner = k;
-    pn.count = k;
+    const LimbPat pn = pat_nonown(c, lv, D, 1, (long long)nd * ne * N);
     if ((rc = ntt_fwd(c, pn))) return rc;
     // inner product with the Galois key (fused automorphism), ModDown
     if ((rc = ksw_ip(c, lv, d_rd, 1))) return rc;
-    LimbPat pd{};
-    pd.base = u;
-    pd.outer_stride = (long long)ne * N;
-    pd.inner = K;
-    pd.count = 2 * K;
-    for (int q = 0; q < K; q++) {
-        pd.off[q] = (unsigned short)(lv + q);
-        pd.mod[q] = (unsigned char)(c->L + q);
-    }
+    const LimbPat pd = pat_drop_special(c, lv, u, 2);
     if ((rc = ntt_inv(c, pd))) return rc;
     if ((rc = div_conv(c, dt, d_dd, 2))) return rc;
     if ((rc = ntt_fwd(c, pat_ct(c, tmp, 2, lv)))) return rc;

@@ -110,6 +110,7 @@ _SIGS = {
     "hegmm_rotate": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_rotate_many": (ctypes.c_int, [vp, vp, intp, ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_rotate_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
+    "hegmm_device_memory": (ctypes.c_int, [vp, ctypes.c_int, u64p]),
     "hegmm_cmult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_add": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_mult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
@@ -567,6 +568,13 @@ class Context:
 
     def hegmm_kernel_reset(self):
         self._check(self.lib.hegmm_kernel_reset(self.h), "kernel_reset")
+
+    def hegmm_device_memory(self, reset_high: bool = False) -> dict:
+        """{pool_used, pool_used_high, pool_reserved, device_free} in bytes."""
+        out = np.zeros(4, dtype=np.uint64)
+        self._check(self.lib.hegmm_device_memory(self.h, int(bool(reset_high)), out.ctypes.data_as(u64p)),
+                    "device_memory")
+        return dict(zip(("pool_used", "pool_used_high", "pool_reserved", "device_free"), (int(v) for v in out)))
 
     def hegmm_peak_butterflies(self) -> float:
         v = ctypes.c_double()

@@ -165,3 +165,15 @@ def test_host_shared_baby_steps_match_oracle(H):
                 for cost in (1, 3, 40):
                     assert H.hegmm_plan_giant(m, l, n, alg, S, role, cost) == \
                         oracle_giant(m, l, n, alg, S, role, cost), (m, l, n, alg, role, cost)
+
+
+def test_context_refuses_more_modup_limbs_than_a_limb_pattern_holds(H):
+    # L = 12, K = 4, alpha = 1: digits(L) (L + K) - L = 180 new limbs per
+    # ModUp, more than one limb pattern holds; refused before any CUDA call
+    import ctypes
+
+    lib = H.load()
+    prm = H.hegmm_params(14, 65537, 12, 50, 4, 1, 21, 0)
+    h = ctypes.c_void_p()
+    rc = lib.hegmm_ctx_create(ctypes.byref(prm), ctypes.c_void_p(0), ctypes.byref(h))
+    assert rc == -1 and not h.value
