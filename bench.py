@@ -52,10 +52,51 @@ KS_MODES = {"double+lazy+shared": 7, "double+lazy": 3, "double": 1, "single": 0,
             "single+shared": 4}
 
 
-def workload_products(kind):
-    """[(m, l, n, alg)] of a throughput workload (alg 0 = AUTO)."""
+def shared_keyswitches(H, m, l, n, alg, slots):
+    """Key switches one product executes in the shared-baby-step order
+    (distinct baby offsets and giant rotations of both operands, one
+    relinearisation, the extraction rotations), from the host planner."""
+    ksw = 1 + H.hegmm_plan_counts(m, l, n, alg, slots)["extract"]
+    for role in (0, 1):
+        v = H.hegmm_plan_giant(m, l, n, alg, slots, role)
+        pos, babies, giants = 1, set(), 0
+        for _ in range(v[0]):
+            g, nt = v[pos], v[pos + 1]
+            pos += 2
+            giants += g != 0
+            for _ in range(nt):
+                b, c = v[pos], v[pos + 1]
+                pos += 2 + c
+                if b:
+                    babies.add(b)
+        ksw += len(babies) + giants
+    return ksw
+
+
+def fewest_keyswitch_alg(H, m, l, n, slots):
+    """Of Algorithm 2, Algorithm 1 with the extended pre-layout and
+    Algorithm 1 (in that order of preference), the one that fits the slots
+    and executes the fewest key switches in the shared-baby-step order."""
+    best = None
+    for alg in (2, 3, 1):
+        try:
+            k = shared_keyswitches(H, m, l, n, alg, slots)
+        except Exception:
+            continue  # does not fit
+        if best is None or k < best[1]:
+            best = (alg, k)
+    return best[0]
+
+
+def workload_products(kind, H=None, slots=None):
+    """[(m, l, n, alg)] of a throughput workload (alg 0 = AUTO).  The
+    paper-scale products take, per shape, the algorithm with the fewest
+    executed key switches (fewest_keyswitch_alg) when the library is at
+    hand (H), else AUTO."""
     if kind == "paper":
-        return [(m, l, n, 0) for (m, l, n) in W.PAPER_SHAPES]
+        if H is None:
+            return [(m, l, n, 0) for (m, l, n) in W.PAPER_SHAPES]
+        return [(m, l, n, fewest_keyswitch_alg(H, m, l, n, slots)) for (m, l, n) in W.PAPER_SHAPES]
     if kind == "medium":
         return [(m, l, n, a) for (m, l, n) in W.MEDIUM_SHAPES for a in (1, 2)]
     raise ValueError(kind)
@@ -82,9 +123,10 @@ def workload_config(extra=None):
 def paper_config(extra=None):
     cfg = {
         "workload": "paper: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; A64x64.B64x64, A32x128.B128x16 "
-                    "(Algorithm 1: Algorithm 2 would need 16384 > 8192 slots), A128x16.B16x64 (Algorithm 2); entries "
-                    "U[0,255] seed 0; one hegmm_matmul_batch_algs call per step; per_product_path = the plain "
-                    "one-product-per-launch path",
+                    "(Algorithm 2 would need 16384 > 8192 slots), A128x16.B16x64; per shape the algorithm (2, 1 with "
+                    "the extended pre-layout = 3, or 1) with the fewest executed key switches (see algorithms); "
+                    "entries U[0,255] seed 0; one hegmm_matmul_batch_algs call per step; per_product_path = the "
+                    "plain one-product-per-launch path",
         "products_per_step": len(W.PAPER_SHAPES),
         "l2": "flushed between timed steps (256 MiB write); per-step key working set (about 19 GB) >> L2",
         "launch": "the cached plan replayed as one CUDA graph; per-kernel times from a second pass of the same "
@@ -279,6 +321,17 @@ def run_reference(args):
         return
     kind = args.workload if args.workload in ("paper", "medium") else "paper"
     prods = workload_products(kind)
+    if kind == "paper" and not args.paper_auto:
+        # the algorithms the GPU arm picks (host planner queries only; no GPU)
+        try:
+            from paper_2405_02238_gb300 import build as B
+
+            B.build()
+            from paper_2405_02238_gb300 import hegmm as H
+
+            prods = workload_products(kind, H, W.PAPER.slots)
+        except Exception:
+            pass
     pre = workload_preset(kind)
     for _ in range(args.warmup):
         oracle_sample(prods, pre)
@@ -678,7 +731,7 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
         rng = W.BATCH_RANGE
     else:
         rng = W.PAPER_RANGE if kind == "paper" else W.MEDIUM_RANGE
-        for (m, l, n, alg) in workload_products(kind):
+        for (m, l, n, alg) in workload_products(kind, None if args.paper_auto else H, ctx.S):
             A, Bm = W.matrices(m, l, n, *rng)
             prods.append((m, l, n, alg, A, Bm))
     for alg in sorted({p[3] for p in prods}):
@@ -883,6 +936,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-medium", action="store_true", help="skip the medium workload's extra key")
+    ap.add_argument("--paper-auto", action="store_true",
+                    help="paper workload: AUTO algorithm per shape instead of the fewest-key-switch choice")
     ap.add_argument("--workload", default="paper", choices=["paper", "medium", "batch", "serve", "product", "blocked"],
                     help="paper: the three N=16384 products (default); medium: the four N=8192 products; batch: 512 "
                          "mixed shapes; serve: Poisson arrivals on the N=16384 ring; product: one product of --shape "
@@ -940,7 +995,8 @@ def main():
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": cfg({"parallelism": "replicas" if world > 1 else "single-gpu", "keyswitch_mode": args.ks_mode,
-                       "tuning": r["tuning"]}),
+                       "tuning": r["tuning"],
+                       "algorithms": {"%dx%dx%d" % p[:3]: p[3] for p in r["prods"]} if kind != "batch" else "AUTO"}),
     }
     for k in ("per_product_path", "batch_over_per_product", "other_keyswitch_mode", "two_row_packing",
               "keyswitches_per_s", "keyswitches_per_step", "paper_rotations_per_step", "wall_s_timed", "e2e",

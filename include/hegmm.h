@@ -58,11 +58,9 @@ extern "C" {
  * stored over l + n - 1 columns, column c holding sigma(A)'s column c mod l,
  * so every eps^k is one rotation by k m under one mask (Algorithm 1 needs up
  * to two diagonals per eps^k); needs m (l + n - 1) <= S.  omega^k, the loop
- * and the result layout are Algorithm 1's.  In this version the planner
- * (hegmm_plan_*), hegmm_encode, hegmm_keygen, hegmm_decrypt and the
- * ciphertext-side transformations accept it; the product entry points
- * (hegmm_matmul*, the server) refuse it with HEGMM_EINVAL until its device
- * parity has been run. */
+ * and the result layout are Algorithm 1's.  Accepted wherever an algorithm
+ * is (planner, encoding, keys, products, sums, the server, decryption,
+ * transformations); AUTO never picks it. */
 #define HEGMM_ALG_1X 3
 
 #define HEGMM_ROLE_A 0
@@ -78,8 +76,10 @@ typedef struct hegmm_ct hegmm_ct;   /* device ciphertext [2][level][N], NTT doma
  * consecutive chain primes (dnum = L / alpha digits).  Errors are centred
  * binomial with parameter eta; the secret is ternary.  ms_drop chain primes
  * are removed by a modulus switch before every ciphertext product (0 or 1).
- * Limits: 10 <= logN <= 14, 2 <= L, 1 <= K, L + K <= 24, qbits <= 60,
- * alpha divides L, K >= alpha (so P >= every digit modulus up to a bit). */
+ * Limits: 10 <= logN <= 14, 2 <= L, 1 <= K, L + K <= 24, 20 <= qbits <= 56
+ * (the NTTs reduce their values only when they leave a transform, which
+ * needs 128 q < 2^63), alpha divides L, K >= alpha (so P >= every digit
+ * modulus up to a bit), K <= 4, digits (L + K) - L <= 128. */
 typedef struct {
     int logN;
     uint64_t t;
@@ -120,6 +120,30 @@ int hegmm_get_primes(const hegmm_ctx *ctx, uint64_t *out);
  * adds keys; a different seed replaces all keys.  Keys stay resident in
  * device memory.  Errors: HEGMM_ESHAPE if a shape fits no algorithm. */
 int hegmm_keygen(hegmm_ctx *ctx, uint64_t seed, const int *shapes_mln, int n_shapes, int alg);
+
+/* Key policy of products (the fallback to Algorithm 1 of Section 3.3 can
+ * need thousands of distinct rotation offsets, one Galois key each: about
+ * 7300 for 128 x 16 x 64 at N = 2^14, 10 MiB per key).
+ *   HEGMM_KEYS_DIRECT (default): one key per rotation offset a plan uses.
+ *   HEGMM_KEYS_POW2: only the keys of rotations by +-2^i (2^i < S, at most
+ *     2 log2 S keys); every rotation of a product (the diagonals of each
+ *     linear transformation, giant and extraction rotations) is the chain of
+ *     HE-Rot by the signed powers of two of the non-adjacent form of its
+ *     offset z mod S, or of the same rotation written z - S when that has
+ *     fewer digits, least significant first (hegmm_plan_pow2_steps).  The
+ *     chains of one operand share their common prefixes; a linear
+ *     transformation is then the sum over its diagonals of the mask product
+ *     of the chained rotation, in every key-switch mode (the double mode's
+ *     lifted sum over PQ would divide back to the same value), and Algorithm
+ *     2's extraction adds the chained rotations of C_acc.  Bit-exact with the
+ *     oracle's key_policy "pow2".
+ * Applies to hegmm_keygen and to products started after the call; with a
+ * secret key the power-of-two keys are made at once.  The ciphertext-side
+ * transformations (hegmm_lintrans ...) keep using direct keys.  Errors:
+ * HEGMM_EINVAL. */
+#define HEGMM_KEYS_DIRECT 0
+#define HEGMM_KEYS_POW2 1
+int hegmm_set_key_policy(hegmm_ctx *ctx, int policy);
 
 /* Adds Galois keys for left rotations by z[0..count) (negative z rotates
  * right); requires a previous hegmm_keygen. */
@@ -267,7 +291,7 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in
- * {HEGMM_ALG_AUTO, 1, 2} (algs may be NULL: AUTO for all).  Products of
+ * {HEGMM_ALG_AUTO, 1, 2, 3} (algs may be NULL: AUTO for all).  Products of
  * both algorithms share each stage's launches. */
 int hegmm_matmul_batch_algs(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B,
                             const int *mln, const int *algs, hegmm_ct **C);
@@ -520,6 +544,10 @@ int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const i
  * products with equal triples). */
 int hegmm_plan_slot_map(int m, int l, int n, int alg, int slots, int role, int *buf, int cap);
 int hegmm_plan_result_layout(int m, int l, int n, int alg, int slots, int *rows_cols_col);
+/* hegmm_plan_pow2_steps writes the chain of signed power-of-two rotation
+ * offsets that HEGMM_KEYS_POW2 applies for a left rotation by z over `slots`
+ * slots into buf[cap] and returns its length (0 for z = 0 mod slots). */
+int hegmm_plan_pow2_steps(long long z, int slots, int *buf, int cap);
 
 /* Per-kernel device timing: while enabled, every launch of the library's
  * kernels is bracketed by CUDA events on the context stream and its

@@ -310,6 +310,15 @@ class Oracle:
         self.counts["rot"] = self.counts.get("rot", 0) + 1
         return out
 
+    def rotate_pow2(self, ct: np.ndarray, z: int) -> np.ndarray:
+        """Rotation under the power-of-two key policy: the chain of HE-Rot by
+        the steps of slots.pow2_steps(z, S), least significant first; only
+        keys of +-2^i rotations are used."""
+        out = ct.copy()
+        for step in SL.pow2_steps(z, self.S):
+            out = self.rotate(out, step)
+        return out
+
     def cmult(self, ct: np.ndarray, pt_eval: np.ndarray) -> np.ndarray:
         lv = ct.shape[1]
         out = np.zeros_like(ct)
@@ -445,7 +454,7 @@ class HEGMM:
     MODES = ("single", "double")
 
     def __init__(self, o: Oracle, mode: str = "single", lazy_relin: bool = False, giant: bool = False,
-                 giant_cost: int = SL.GIANT_COST):
+                 giant_cost: int = SL.GIANT_COST, key_policy: str = "direct"):
         """mode "single": every key switch ends in its own ModDown, as the
         HE operations Rot, CMult, Mult and Add compose (the paper's cost
         model).  mode "double": the sums of key-switched terms (each linear
@@ -459,9 +468,18 @@ class HEGMM:
         giant: every linear transformation of an operand is evaluated as
         Rot(sum_d u'_d (.) Rot(ct, b_d), g) with the offsets b_d shared by all
         iterations (``slots.giant_factor``); the inner sum is evaluated in the
-        chosen mode, the outer rotation is one HE-Rot."""
+        chosen mode, the outer rotation is one HE-Rot.
+        key_policy "direct": one Galois key per rotation offset; "pow2": only
+        keys of rotations by +-2^i, every rotation is Oracle.rotate_pow2 (a
+        chain of HE-Rot).  Under pow2 a linear transformation is the sum of
+        the mask products of its chained rotations in either mode (the
+        double mode's sum over PQ of lifted ciphertexts P x is divided back
+        exactly, ModDown(P x) = x), and so is the extraction sum."""
         if mode not in self.MODES:
             raise ValueError(mode)
+        if key_policy not in ("direct", "pow2"):
+            raise ValueError(key_policy)
+        self.pow2 = key_policy == "pow2"
         self.o = o
         self.mode = mode
         self.lazy_relin = lazy_relin
@@ -481,11 +499,20 @@ class HEGMM:
         return self._mask_cache[key]
 
     def galois_needed(self, plan: SL.Plan) -> List[int]:
+        """Galois elements of every rotation the run key-switches: the plan's
+        diagonals and extraction offsets, and in the shared-baby-step order
+        the baby offsets and giant rotations of its factorisation."""
+        if self.pow2:
+            return sorted({self.o.galois(z) for z in SL.pow2_offsets(self.o.S)})
         zs = set()
         for e, om in plan.iters:
             zs.update(d for d in e if d % self.o.S)
             zs.update(d for d in om if d % self.o.S)
         zs.update(z for z in plan.extract if z % self.o.S)
+        if self.giant:
+            for s in (0, 1):
+                for g, terms in SL.giant_factor([it[s] for it in plan.iters], self.o.S, self.giant_cost):
+                    zs.update(z for z in [g] + [b for b, _ in terms] if z % self.o.S)
         return sorted({self.o.galois(z) for z in zs})
 
     def encrypt_inputs(self, plan: SL.Plan, A, B, seed: int = 1, streams=(0, 1)):
@@ -531,14 +558,18 @@ class HEGMM:
                 o.pq_mac(acc[comp], v[comp], m)
         return o.moddown_pair(acc)
 
+    def rot(self, ct: np.ndarray, z: int) -> np.ndarray:
+        """HE-Rot under the executor's key policy."""
+        return self.o.rotate_pow2(ct, z) if self.pow2 else self.o.rotate(ct, z)
+
     def lt_terms(self, ct: np.ndarray, terms: List[Tuple[int, List[int]]], scale: int) -> np.ndarray:
         """sum over terms (d, slots) of u (.) Rot(ct, d), in the given order."""
-        if self.mode == "double":
+        if self.mode == "double" and not self.pow2:
             return self.lt_double(ct, terms, scale)
         lv = ct.shape[1]
         acc = None
         for d, dst in terms:
-            r = self.o.rotate(ct, d)
+            r = self.rot(ct, d)
             term = self.o.cmult(r, self.mask_eval(dst, scale, lv))
             acc = term if acc is None else self.o.add(acc, term)
         return acc
@@ -551,7 +582,7 @@ class HEGMM:
         """Rot(sum_b u'_b (.) Rot(ct, b), g) for one factored transformation."""
         g, terms = fact
         inner = self.lt_terms(ct, terms, scale)
-        return self.o.rotate(inner, g) if g % self.o.S else inner
+        return self.rot(inner, g) if g % self.o.S else inner
 
     def run(self, plan: SL.Plan, ctA: np.ndarray, ctB: np.ndarray) -> np.ndarray:
         o = self.o
@@ -599,6 +630,11 @@ class HEGMM:
             C = o.moddown_pair(acc)
             if not plan.extract:
                 return C
+            if self.pow2:
+                out = C
+                for z in plan.extract:
+                    out = o.add(out, self.rot(C, z))
+                return out
             lv = C.shape[1]
             D = o.modup(C[1])
             ex = None
@@ -613,7 +649,7 @@ class HEGMM:
             return o.add(C, o.moddown_pair(ex))
         out = C
         for z in plan.extract:
-            out = o.add(out, o.rotate(C, z))
+            out = o.add(out, self.rot(C, z))
         return out
 
     def lintrans(self, ct: np.ndarray, src: List[int]) -> np.ndarray:

@@ -340,6 +340,47 @@ def giant_factor(outputs: List[Dict[int, List[int]]], S: int,
     return out
 
 
+def naf(z: int) -> List[Tuple[int, int]]:
+    """Non-adjacent form of an integer z: [(sign, i)] with z = sum sign 2^i,
+    signs +-1, no two consecutive positions i, ascending i (least
+    significant first).  The standard recoding: while z != 0, an odd z takes
+    the digit 2 - (z mod 4), which leaves z - digit divisible by 4."""
+    out = []
+    i = 0
+    while z:
+        if z & 1:
+            d = 2 - (z % 4)
+            out.append((d, i))
+            z -= d
+        z //= 2
+        i += 1
+    return out
+
+
+def pow2_steps(z: int, S: int) -> List[int]:
+    """The power-of-two key policy's decomposition of a left rotation by z
+    over S slots: the signed powers of two d 2^i of the NAF of z mod S or of
+    (z mod S) - S (the same rotation), whichever has fewer digits (ties: the
+    non-negative one), in ascending i.  Rot(x, z) is the chain of HE-Rot by
+    these steps."""
+    a = z % S
+    fa, fb = naf(a), naf(a - S)
+    best = fb if len(fb) < len(fa) else fa
+    return [d * (1 << i) for d, i in best]
+
+
+def pow2_offsets(S: int) -> List[int]:
+    """Every rotation step the power-of-two policy can use (its keys):
+    +-2^i for 2^i < S, as left-rotation offsets mod S."""
+    out = set()
+    i = 0
+    while (1 << i) < S:
+        out.add((1 << i) % S)
+        out.add((-(1 << i)) % S)
+        i += 1
+    return sorted(out)
+
+
 def apply_terms(x: np.ndarray, terms: List[Tuple[int, List[int]]], S: int, mod: int, scale: int = 1) -> np.ndarray:
     """sum over (b, slots) of u (.) Rot(x, b), u = scale on the slots."""
     y = np.zeros(S, dtype=np.int64)

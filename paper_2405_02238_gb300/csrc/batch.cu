@@ -113,6 +113,22 @@ struct RelinChunk {
     SumDesc *d_sum = nullptr;
 };
 
+// Power-of-two key policy: rotation chains of one level evaluated as trees
+// (build_tree); chunks run in order, a chunk with `gather` set first copies
+// its parents together and hoists their ModUp.
+struct TreeChunk {
+    bool gather = false;
+    int npar = 0, n = 0;
+    u64 **d_par = nullptr;
+    RotDesc *d_rot = nullptr;
+    DivDesc *d_div = nullptr;
+};
+struct RotTree {
+    int lv = 0;
+    u64 *nodes = nullptr, *stage = nullptr, *xc = nullptr, *D = nullptr, *u = nullptr;
+    std::vector<TreeChunk> chunks;
+};
+
 struct BatchPlan {
     std::vector<ShapeData *> shp;
     int B = 0, lv0 = 0, lv1 = 0, O = 0, E = 0, X = 0;
@@ -159,6 +175,18 @@ struct BatchPlan {
     int runs = 0;
     bool graph_failed = false;
     cudaGraphExec_t exec = nullptr;
+    // power-of-two key policy (pow2): the operands' rotation trees, one
+    // accumulation launch over every linear transformation's terms, and the
+    // extraction's trees with one group-sum launch
+    int pow2 = 0;
+    RotTree optree, xtree;
+    LtTerm *d_p2_terms = nullptr;
+    int *d_p2_off = nullptr;
+    u64 **d_p2_outs = nullptr;
+    u64 *p2x = nullptr;
+    const u64 **d_p2x_src = nullptr;
+    int *d_p2x_first = nullptr;
+    u64 **d_p2x_out = nullptr;
     // descriptor staging while the plan is built (see plan_upload)
     char *dblk = nullptr;
     size_t dblk_cap = 0, dblk_used = 0;
@@ -222,6 +250,167 @@ static void free_bplan(Ctx *c, BatchPlan *P) {
     for (ShapeData *s : uniq) s->refs--;
     for (void *a : P->allocs) dfree(c, a);
     delete P;
+}
+
+// The rotation chains of the power-of-two key policy, as one tree per root:
+// a node is a distinct prefix (root, steps[0..t]) of the chains; the nodes of
+// depth t + 1 are one batched rotation of their parents (depth 1: the roots,
+// whose hoisted digits root_D exist; deeper: the parents gathered into a
+// staging buffer, one hoisted ModUp each), with P tau(c0) folded into the
+// inner product and one ModDown per node.  Each chain therefore equals the
+// chain of single HE-Rots by its steps, bit for bit.  leaf[i] receives the
+// node that ends chain i (its root when the chain is empty); nodes counts the
+// key switches.
+static int build_tree(Ctx *c, BatchPlan *P, RotTree &T, int lv, const std::vector<const u64 *> &root_ct,
+                      const std::vector<const u64 *> &root_D,
+                      const std::vector<std::pair<int, std::vector<int>>> &chains, std::vector<const u64 *> &leaf,
+                      long long &nodes) {
+    const int N = c->N, ne = lv + c->K, nd = c->digits(lv);
+    T.lv = lv;
+    // nodes by depth, ordered by (root, steps): children follow their parents' order
+    std::vector<std::map<std::vector<int>, int>> depth;
+    for (const auto &ch : chains) {
+        std::vector<int> key{ch.first};
+        for (size_t t = 0; t < ch.second.size(); t++) {
+            key.push_back(ch.second[t]);
+            if (depth.size() <= t) depth.emplace_back();
+            depth[t][key] = 0;
+        }
+    }
+    std::vector<size_t> first(depth.size() + 1, 0);
+    std::vector<std::vector<std::vector<int>>> keys(depth.size());
+    for (size_t t = 0; t < depth.size(); t++) {
+        int i = 0;
+        for (auto &kv : depth[t]) {
+            kv.second = i++;
+            keys[t].push_back(kv.first);
+        }
+        first[t + 1] = first[t] + (size_t)i;
+    }
+    nodes = (long long)first[depth.size()];
+    const size_t ct_w = (size_t)2 * lv * N;
+    if (nodes) {
+        T.nodes = (u64 *)plan_alloc(c, P, (size_t)nodes * ct_w * 8);
+        if (!T.nodes) return set_err(c, HEGMM_ENOMEM, "rotation tree nodes");
+    }
+    auto node_ptr = [&](size_t t, int i) { return T.nodes + (first[t] + (size_t)i) * ct_w; };
+    leaf.assign(chains.size(), nullptr);
+    for (size_t i = 0; i < chains.size(); i++) {
+        const auto &st = chains[i].second;
+        if (st.empty()) {
+            leaf[i] = root_ct[chains[i].first];
+            continue;
+        }
+        std::vector<int> key{chains[i].first};
+        key.insert(key.end(), st.begin(), st.end());
+        leaf[i] = node_ptr(st.size() - 1, depth[st.size() - 1].at(key));
+    }
+    // chunks: at most PC parents gathered and hoisted at once, at most CC
+    // inner products (and ModDowns) at once
+    struct Part {
+        size_t t, c0, c1;
+        bool gather;
+        std::vector<int> par;     // depth t - 1 indices of the gathered parents
+        std::vector<int> par_of;  // per node c0..c1: parent slot (a root index at depth 0)
+    };
+    std::vector<Part> parts;
+    const size_t per_par = (size_t)(3 * lv + nd * ne) * N * 8, per_node = (size_t)2 * ne * N * 8;
+    const size_t PC = std::max<size_t>(1, c->ws_budget / per_par), CC = std::max<size_t>(1, c->ws_budget / per_node);
+    size_t max_par = 0, max_n = 1;
+    for (size_t t = 0; t < depth.size(); t++) {
+        const auto &K = keys[t];
+        size_t a = 0;
+        while (a < K.size()) {
+            std::vector<int> par, par_of;
+            size_t b = a;
+            std::vector<int> last;
+            while (b < K.size()) {
+                std::vector<int> pk(K[b].begin(), K[b].end() - 1);
+                if (b == a || pk != last) {
+                    if (t > 0 && par.size() == PC) break;
+                    last = pk;
+                    if (t > 0) par.push_back(depth[t - 1].at(pk));
+                }
+                par_of.push_back(t > 0 ? (int)par.size() - 1 : pk[0]);
+                b++;
+            }
+            max_par = std::max(max_par, par.size());
+            for (size_t c0 = a; c0 < b; c0 += CC) {
+                Part pt;
+                pt.t = t;
+                pt.c0 = c0;
+                pt.c1 = std::min(b, c0 + CC);
+                pt.gather = t > 0 && c0 == a;
+                pt.par = par;
+                pt.par_of.assign(par_of.begin() + (c0 - a), par_of.begin() + (pt.c1 - a));
+                max_n = std::max(max_n, pt.c1 - c0);
+                parts.push_back(std::move(pt));
+            }
+            a = b;
+        }
+    }
+    if (!nodes) return HEGMM_OK;
+    if (max_par) {
+        T.stage = (u64 *)plan_alloc(c, P, max_par * ct_w * 8);
+        T.xc = (u64 *)plan_alloc(c, P, max_par * lv * N * 8);
+        T.D = (u64 *)plan_alloc(c, P, max_par * nd * ne * N * 8);
+        if (!T.stage || !T.xc || !T.D) return set_err(c, HEGMM_ENOMEM, "rotation tree scratch");
+    }
+    T.u = (u64 *)plan_alloc(c, P, max_n * 2 * ne * N * 8);
+    if (!T.u) return set_err(c, HEGMM_ENOMEM, "rotation tree scratch");
+    for (const Part &pt : parts) {
+        TreeChunk ch;
+        ch.gather = pt.gather;
+        ch.npar = (int)pt.par.size();
+        ch.n = (int)(pt.c1 - pt.c0);
+        if (pt.gather) {
+            std::vector<u64 *> pv;
+            for (int i : pt.par) pv.push_back(node_ptr(pt.t - 1, i));
+            ch.d_par = plan_upload(c, P, pv);
+        }
+        std::vector<RotDesc> rd;
+        std::vector<DivDesc> dd;
+        for (size_t x = pt.c0; x < pt.c1; x++) {
+            const int r = (int)(x - pt.c0), slot = pt.par_of[r];
+            const u64 g = galois_of(c, keys[pt.t][x].back());
+            auto kit = c->keys.find(g);
+            if (kit == c->keys.end()) return set_err(c, HEGMM_ENOKEY, "missing key of a power-of-two rotation");
+            RotDesc d{};
+            d.D = pt.t > 0 ? T.D + (size_t)slot * nd * ne * N : root_D[slot];
+            d.key = kit->second;
+            d.u = T.u + (size_t)r * 2 * ne * N;
+            d.add0 = pt.t > 0 ? T.stage + (size_t)slot * ct_w : root_ct[slot];  // P tau_g(c0) folded in
+            d.g = (u32)g;
+            rd.push_back(d);
+            u64 *out = node_ptr(pt.t, (int)x);
+            for (int comp = 0; comp < 2; comp++) {
+                DivDesc v{};
+                v.u = T.u + ((size_t)2 * r + comp) * ne * N;
+                v.out = out + (size_t)comp * lv * N;
+                v.g = 1;
+                dd.push_back(v);
+            }
+        }
+        ch.d_rot = plan_upload(c, P, rd);
+        ch.d_div = plan_upload(c, P, dd);
+        if (!ch.d_rot || !ch.d_div || (pt.gather && !ch.d_par))
+            return set_err(c, HEGMM_ENOMEM, "rotation tree descriptors");
+        T.chunks.push_back(ch);
+    }
+    return HEGMM_OK;
+}
+
+static int run_tree(Ctx *c, const RotTree &T) {
+    const int N = c->N, lv = T.lv;
+    int rc;
+    for (const TreeChunk &ch : T.chunks) {
+        if (ch.gather) {
+            if ((rc = gather_cts(c, lv, ch.d_par, ch.npar, T.stage))) return rc;
+            if ((rc = modup(c, lv, ch.npar, T.stage + (size_t)lv * N, (long long)2 * lv * N, T.xc, T.D))) return rc;
+        }
+        if ((rc = ksw_moddown(c, lv, ch.d_rot, ch.d_div, ch.n, T.u, nullptr))) return rc;
+    }
+    return HEGMM_OK;
 }
 
 static void free_shape(Ctx *c, ShapeData *s) {
@@ -330,7 +519,8 @@ static int encode_masks(Ctx *c, int lv, const std::vector<const std::vector<int>
 }
 
 static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData **out) {
-    auto key = std::make_tuple(m, l, n, alg, shared);
+    const int pow2 = c->key_pow2;
+    auto key = std::make_tuple(m, l, n, alg, shared, pow2);
     auto it = c->shapes.find(key);
     if (it != c->shapes.end()) {
         it->second->last_use = ++c->bplan_clock;
@@ -373,7 +563,13 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
         delete sd;
         return set_err(c, code, msg);
     };
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < 2 && pow2; s++)  // only the +-2^i keys, made on first use
+        for (int z : pow2_offsets(S))
+            if (int rc = ensure_galois_key(c, galois_of(c, z))) {
+                delete sd;
+                return rc;
+            }
+    for (int s = 0; s < 2 && !pow2; s++) {
         // the plan's own offsets come from hegmm_keygen; those of a
         // shared-baby-step factorisation (which depends on the giant cost)
         // are made from the secret key on first use
@@ -394,9 +590,9 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
             }
     }
     for (int z : hp.extract)
-        if (!c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
+        if (!pow2 && !c->keys.count(galois_of(c, z))) return fail(HEGMM_ENOKEY, "missing Galois key for extraction");
     if (!c->keys.count(0)) return fail(HEGMM_ENOKEY, "no relinearisation key");
-    for (int s = 0; s < 2; s++)
+    for (int s = 0; s < 2 && !pow2; s++)
         for (long long z : sd->zs[s]) {
             const u64 g = galois_of(c, z);
             sd->zgal[s].push_back((u32)g);
@@ -452,6 +648,30 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
         for (int g : sd->giant[s]) ngiant += g != 0;
     ct.ksw = (long long)sd->zs[0].size() + (long long)sd->zs[1].size() + ngiant + ni + ne;
     ct.modup = 2 + ngiant + ni + (ne > 0 ? 1 : 0);
+    if (pow2) {
+        // the chains of each operand share their prefixes (one key switch per
+        // distinct prefix); giants and extraction rotations are chains too
+        std::set<std::vector<int>> pre[2], xpre;
+        for (int s = 0; s < 2; s++)
+            for (long long z : sd->zs[s]) {
+                std::vector<int> st = pow2_steps(z, S), p;
+                for (int x : st) {
+                    p.push_back(x);
+                    pre[s].insert(p);
+                }
+            }
+        long long gsteps = 0;
+        for (int s = 0; s < 2; s++)
+            for (int g : sd->giant[s]) gsteps += (long long)pow2_steps(g, S).size();
+        for (int z : hp.extract) {
+            std::vector<int> st = pow2_steps(z, S), p;
+            for (int x : st) {
+                p.push_back(x);
+                xpre.insert(p);
+            }
+        }
+        ct.ksw = (long long)pre[0].size() + (long long)pre[1].size() + gsteps + ni + (long long)xpre.size();
+    }
     ct.modswitch = c->prm.ms_drop ? 2 * ni : 0;
     c->shapes[key] = sd;
     *out = sd;
@@ -478,6 +698,8 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     BatchPlan *P = new BatchPlan;
     P->dbl = dbl;
     P->lazy = lazy;
+    P->pow2 = c->key_pow2;
+    const int pow2 = P->pow2;
     auto fail_rc = [&](int rc) {
         free_bplan(c, P);
         return rc;
@@ -534,7 +756,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     for (int p = 0; p < B; p++)
         for (int s = 0; s < 2; s++) {
             rbase[p][s] = (int)ritems.size();
-            for (int zi = 0; zi < (int)P->shp[p]->zs[s].size(); zi++) ritems.push_back({p, s, zi});
+            for (int zi = 0; zi < (int)P->shp[p]->zs[s].size() && !pow2; zi++) ritems.push_back({p, s, zi});
         }
     std::vector<std::pair<int, int>> litems;
     for (int p = 0; p < B && !lazy; p++)
@@ -592,7 +814,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     };
     std::vector<GGroup> groups;
     size_t npart = 0;
-    P->fused = dbl && c->lt_fused && (unsigned __int128)(TC + 2) * c->q[0] < ((unsigned __int128)1 << 64);
+    P->fused = !pow2 && dbl && c->lt_fused && (unsigned __int128)(TC + 2) * c->q[0] < ((unsigned __int128)1 << 64);
     if (P->fused) {
         for (ShapeData *sd : held) {
             if (sd->groups_tc == TC) continue;
@@ -782,7 +1004,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // identity (d = 0) terms over all outputs; this launch also zero-initialises
-    if (!fused) {
+    if (!fused && !pow2) {
         std::vector<LtTerm> terms;
         std::vector<int> offs{0};
         std::vector<u64 *> outs;
@@ -860,33 +1082,87 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     // giant rotations: each transformation output with g != 0 is rotated in
     // place (gathered copy -> hoisted ModUp -> key switch with P tau_g(c0)
     // folded in -> ModDown into the output)
-    for (int g0 = 0; g0 < G; g0 += GCH) {
-        GiantChunk ch;
-        ch.cnt = std::min(GCH, G - g0);
-        std::vector<u64 *> src;
-        std::vector<RotDesc> rd;
-        std::vector<DivDesc> dd;
-        for (int r = 0; r < ch.cnt; r++) {
-            const auto &gi = gitems[g0 + r];
-            u64 *o = out_ct(gi[0], gi[1], gi[2]);
-            src.push_back(o);
-            const u64 g = galois_of(c, gi[3]);
-            rd.push_back({P->gD + (size_t)r * nd0 * ne0 * N, c->keys[g], P->gu + (size_t)r * 2 * ne0 * N,
-                          P->gst + (size_t)r * 2 * lv0 * N, nullptr, (u32)g, 0u});
-            for (int comp = 0; comp < 2; comp++) {
-                DivDesc v{};
-                v.u = P->gu + ((size_t)2 * r + comp) * ne0 * N;
-                v.out = o + (size_t)comp * lv0 * N;
-                v.g = 1;
-                dd.push_back(v);
-            }
+    // (power-of-two key policy: each giant is a chain of rotations by its
+    // steps, one round of in-place rotations per step)
+    std::vector<std::vector<std::pair<u64 *, int>>> grounds;
+    for (const auto &gi : gitems) {
+        const std::vector<int> steps = pow2 ? pow2_steps(gi[3], c->S) : std::vector<int>{gi[3]};
+        for (size_t r = 0; r < steps.size(); r++) {
+            if (grounds.size() <= r) grounds.emplace_back();
+            grounds[r].push_back({out_ct(gi[0], gi[1], gi[2]), steps[r]});
         }
-        ch.d_src = plan_upload(c, P, src);
-        ch.d_rot = plan_upload(c, P, rd);
-        ch.d_div = plan_upload(c, P, dd);
-        if (!keep(ch.d_src) || !keep(ch.d_rot) || !keep(ch.d_div))
+    }
+    for (const auto &round : grounds)
+        for (int g0 = 0; g0 < (int)round.size(); g0 += GCH) {
+            GiantChunk ch;
+            ch.cnt = std::min(GCH, (int)round.size() - g0);
+            std::vector<u64 *> src;
+            std::vector<RotDesc> rd;
+            std::vector<DivDesc> dd;
+            for (int r = 0; r < ch.cnt; r++) {
+                u64 *o = round[g0 + r].first;
+                src.push_back(o);
+                const u64 g = galois_of(c, round[g0 + r].second);
+                auto kit = c->keys.find(g);
+                if (kit == c->keys.end()) return fail_rc(set_err(c, HEGMM_ENOKEY, "missing key of a giant rotation"));
+                rd.push_back({P->gD + (size_t)r * nd0 * ne0 * N, kit->second, P->gu + (size_t)r * 2 * ne0 * N,
+                              P->gst + (size_t)r * 2 * lv0 * N, nullptr, (u32)g, 0u});
+                for (int comp = 0; comp < 2; comp++) {
+                    DivDesc v{};
+                    v.u = P->gu + ((size_t)2 * r + comp) * ne0 * N;
+                    v.out = o + (size_t)comp * lv0 * N;
+                    v.g = 1;
+                    dd.push_back(v);
+                }
+            }
+            ch.d_src = plan_upload(c, P, src);
+            ch.d_rot = plan_upload(c, P, rd);
+            ch.d_div = plan_upload(c, P, dd);
+            if (!keep(ch.d_src) || !keep(ch.d_rot) || !keep(ch.d_div))
+                return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+            P->gchunks.push_back(ch);
+        }
+    // power-of-two key policy: the rotations of every operand as chains
+    // (rotation trees rooted at the operands, whose ModUp is step 1), then
+    // every output of the linear transformations as one accumulation over Q
+    // of mask (.) chained rotation (and mask (.) ct for d = 0), for either
+    // mode: ModDown(P x) = x makes the double mode's sum of lifted terms
+    // equal to this sum
+    if (pow2) {
+        std::vector<const u64 *> roots, rootD;
+        std::vector<std::pair<int, std::vector<int>>> chains;
+        std::vector<std::vector<int>> chain_of(2 * (size_t)B);
+        for (int p = 0; p < B; p++)
+            for (int s = 0; s < 2; s++) {
+                roots.push_back(in_ct(p, s));
+                rootD.push_back(P->D + ((size_t)2 * p + s) * nd0 * ne0 * N);
+                for (long long z : P->shp[p]->zs[s]) {
+                    chain_of[2 * p + s].push_back((int)chains.size());
+                    chains.push_back({2 * p + s, pow2_steps(z, c->S)});
+                }
+            }
+        std::vector<const u64 *> leaf;
+        long long nn = 0;
+        if (int rc = build_tree(c, P, P->optree, lv0, roots, rootD, chains, leaf, nn)) return fail_rc(rc);
+        std::vector<LtTerm> terms;
+        std::vector<int> offs{0};
+        std::vector<u64 *> outs;
+        for (int p = 0; p < B; p++) {
+            const ShapeData *sd = P->shp[p];
+            for (int s = 0; s < 2; s++)
+                for (int k = 0; k < niter[p]; k++) {
+                    for (const auto &dr : sd->dref[s][k])
+                        terms.push_back({dr.zi < 0 ? in_ct(p, s) : leaf[chain_of[2 * p + s][dr.zi]],
+                                         sd->mask_at(c, dr.mask)});
+                    offs.push_back((int)terms.size());
+                    outs.push_back(out_ct(p, s, k));
+                }
+        }
+        P->d_p2_terms = plan_upload(c, P, terms);
+        P->d_p2_off = plan_upload(c, P, offs);
+        P->d_p2_outs = plan_upload(c, P, outs);
+        if (!keep(P->d_p2_terms) || !keep(P->d_p2_off) || !keep(P->d_p2_outs))
             return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
-        P->gchunks.push_back(ch);
     }
     // double mode: one ModDown per accumulated polynomial (u over PQ -> out over Q)
     auto moddown_descs = [&](u64 *u, int ne, u64 *outp, int lv, int npoly) {
@@ -900,9 +1176,10 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
         return plan_upload(c, P, dd);
     };
     if (dbl) {
-        P->d_ltdiv = moddown_descs(P->acc, ne0, P->outs, lv0, 2 * O);
+        P->d_ltdiv = pow2 ? nullptr : moddown_descs(P->acc, ne0, P->outs, lv0, 2 * O);
         P->d_cdiv = moddown_descs(P->cpq, ne1, P->cacc, lv1, 2 * B);
-        if (!keep(P->d_ltdiv) || !keep(P->d_cdiv)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        if ((!pow2 && !keep(P->d_ltdiv)) || !keep(P->d_cdiv))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
     }
     // modulus switch of all 2 O polynomials
     if (lv1 != lv0) {
@@ -1002,8 +1279,40 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             P->cnt.modup -= niter[p] - 1;
         }
     }
-    // extraction rotations (Algorithm 2)
-    if (X > 0) {
+    // extraction rotations (Algorithm 2); under the power-of-two key policy
+    // chains from each accumulator (rotation trees), then one group sum of
+    // C_acc and its rotated copies per product
+    if (X > 0 && pow2) {
+        std::vector<const u64 *> roots, rootD;
+        std::vector<std::pair<int, std::vector<int>>> chains;
+        for (int e = 0; e < E; e++) {
+            roots.push_back(P->cacc + (size_t)e * 2 * lv1 * N);
+            rootD.push_back(P->eD + (size_t)e * nd1 * ne1 * N);
+        }
+        for (int p = 0; p < B; p++)
+            for (int h = 0; h < next[p]; h++) chains.push_back({cslot[p], pow2_steps(P->shp[p]->hp.extract[h], c->S)});
+        std::vector<const u64 *> leaf;
+        long long nn = 0;
+        if (int rc = build_tree(c, P, P->xtree, lv1, roots, rootD, chains, leaf, nn)) return fail_rc(rc);
+        P->p2x = (u64 *)plan_alloc(c, P, (size_t)E * 2 * lv1 * N * 8);
+        if (!P->p2x) return fail_rc(set_err(c, HEGMM_ENOMEM, "extraction sums"));
+        std::vector<const u64 *> src;
+        std::vector<int> gfirst{0};
+        std::vector<u64 *> gout;
+        size_t ci = 0;
+        for (int e = 0; e < E; e++) {
+            src.push_back(roots[e]);
+            for (; ci < chains.size() && chains[ci].first == e; ci++) src.push_back(leaf[ci]);
+            gfirst.push_back((int)src.size());
+            gout.push_back(P->p2x + (size_t)e * 2 * lv1 * N);
+        }
+        P->d_p2x_src = plan_upload(c, P, src);
+        P->d_p2x_first = plan_upload(c, P, gfirst);
+        P->d_p2x_out = plan_upload(c, P, gout);
+        if (!keep(P->d_p2x_src) || !keep(P->d_p2x_first) || !keep(P->d_p2x_out))
+            return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+    }
+    if (X > 0 && !pow2) {
         std::vector<RotDesc> rd;
         std::vector<DivDesc> dd;
         for (int p = 0; p < B; p++) {
@@ -1050,7 +1359,11 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     for (int p = 0; p < B; p++) {
         SumDesc s{};
         s.init = P->cacc + (size_t)cslot[p] * 2 * lv1 * N;
-        if (dbl) {
+        if (pow2) {
+            if (next[p]) s.init = P->p2x + (size_t)cslot[p] * 2 * lv1 * N;
+            s.items = s.init;
+            s.count = 0;
+        } else if (dbl) {
             s.items = next[p] ? P->xout + (size_t)cslot[p] * 2 * lv1 * N : s.init;
             s.count = next[p] ? 1 : 0;
         } else {
@@ -1076,7 +1389,7 @@ static int moddown_polys(Ctx *c, int lv, u64 *u, const DivDesc *d_div, int npoly
     const DivTab *tb = div_tab(c, lv, 0);
     if (!tb) return HEGMM_ENOMEM;
     int rc;
-    if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, npoly)))) return rc;
+    if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, npoly), tb->d))) return rc;  // times [t^-1 (P/p_k)^-1]_{p_k}
     return divround_ntt(c, *tb, d_div, npoly);
 }
 
@@ -1092,8 +1405,12 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
     if ((rc = modup(c, lv0, 2 * B, P->in + (size_t)lv0 * N, (long long)2 * lv0 * N, P->xc, P->D))) return rc;
     // 2. linear transformations eps^k(A), omega^k(B) of every iteration
     // (double mode: the d = 0 terms enter as P ct and the rotations as their
-    // inner-product outputs u + P tau(c0), all over PQ; one ModDown per output)
-    if (P->fused) {
+    // inner-product outputs u + P tau(c0), all over PQ; one ModDown per output;
+    // power-of-two keys: chained rotations, then one accumulation over Q)
+    if (P->pow2) {
+        if ((rc = run_tree(c, P->optree))) return rc;
+        if ((rc = lt_accumulate(c, lv0, lv0, lv0, 0, P->d_p2_terms, P->d_p2_off, P->d_p2_outs, P->O, 0))) return rc;
+    } else if (P->fused) {
         if ((rc = lt_group(c, lv0, 1, P->d_lents, P->d_litems[0], P->lt_nitems[0], P->lt_bytes[0]))) return rc;
         if ((rc = lt_group(c, lv0, LT_GROUP, P->d_lents, P->d_litems[1], P->lt_nitems[1], P->lt_bytes[1]))) return rc;
         if ((rc = sum_desc(c, lv0, P->d_ltsum, P->ltsum_n, np0))) return rc;
@@ -1108,7 +1425,7 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
         }
         if ((rc = lt_accumulate(c, lv0, np0, np0, 0, ch.d_terms, ch.d_off, ch.d_outs, ch.nout, 1))) return rc;
     }
-    if (dbl && (rc = moddown_polys(c, lv0, P->acc, P->d_ltdiv, 2 * P->O))) return rc;
+    if (dbl && !P->pow2 && (rc = moddown_polys(c, lv0, P->acc, P->d_ltdiv, 2 * P->O))) return rc;
     // 2b. giant rotations of the shared-baby-step order
     for (auto &ch : P->gchunks) {
         if ((rc = gather_cts(c, lv0, ch.d_src, ch.cnt, P->gst))) return rc;
@@ -1144,7 +1461,10 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
     // 5. Algorithm 2 extraction, and the results
     if (P->X > 0) {
         if ((rc = modup(c, lv1, P->E, P->cacc + (size_t)lv1 * N, (long long)2 * lv1 * N, P->exc, P->eD))) return rc;
-        if (dbl) {
+        if (P->pow2) {
+            if ((rc = run_tree(c, P->xtree))) return rc;
+            if ((rc = sum_groups(c, lv1, P->d_p2x_src, P->d_p2x_first, P->d_p2x_out, P->E))) return rc;
+        } else if (dbl) {
             if ((rc = ksw_ip(c, lv1, P->d_erot, P->X))) return rc;
             if ((rc = sum_desc(c, lv1, P->d_xsum, P->E, lv1 + K))) return rc;
             if ((rc = moddown_polys(c, lv1, P->xacc, P->d_xdiv, 2 * P->E))) return rc;
@@ -1214,7 +1534,7 @@ size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
     // iterations and extractions of the shape: from its plan data when
     // prepared, else from a host plan built once per shape
     size_t ni, ne;
-    auto sit = c->shapes.find(std::make_tuple(m, l, n, a, c->lt_shared ? c->giant_cost : 0));
+    auto sit = c->shapes.find(std::make_tuple(m, l, n, a, c->lt_shared ? c->giant_cost : 0, c->key_pow2));
     if (sit != c->shapes.end()) {
         ni = sit->second->hp.iters.size();
         ne = sit->second->hp.extract.size();
@@ -1247,7 +1567,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     for (int i = 0; i < count; i++) {
         const int m = mln[3 * i], l = mln[3 * i + 1], n = mln[3 * i + 2];
         const int ai = algs ? algs[i] : alg;
-        if (ai < 0 || ai > 2) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1 or 2");
+        if (ai < 0 || ai > 3) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1, 2 or 3");
         const int a = resolve_alg(m, l, n, ai, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
         if (!A[i] || !B[i]) return set_err(c, HEGMM_EINVAL, "null operand");
@@ -1265,6 +1585,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(dbl ? c->lt_one : 0);
     key.push_back(c->wait_limit);  // kernel arguments captured in the graph
     key.push_back(c->test_drop_entry);
+    key.push_back(c->key_pow2);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
@@ -1390,7 +1711,7 @@ int matmul_sum(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
         if (g < 0 || g >= ngroups) return set_err(c, HEGMM_EINVAL, "group index out of range");
         const int m = mln[3 * p], l = mln[3 * p + 1], n = mln[3 * p + 2];
         const int ai = algs ? algs[p] : HEGMM_ALG_AUTO;
-        if (ai < 0 || ai > 2) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1 or 2");
+        if (ai < 0 || ai > 3) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1, 2 or 3");
         const int a = resolve_alg(m, l, n, ai, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
         int rows, cols;
@@ -1698,6 +2019,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
 int hegmm_prepare(hegmm_ctx *h, const int *mln, int n_shapes, int alg) {
     if (!h || n_shapes < 0 || (n_shapes && !mln)) return HEGMM_EINVAL;
     Ctx *c = &h->c;
+    if (alg < 0 || alg > 3) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1, 2 or 3");
     for (int i = 0; i < n_shapes; i++) {
         const int a = resolve_alg(mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], alg, c->S);
         if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");

@@ -133,6 +133,14 @@ std::vector<u64> modup_table_host(const Ctx *c, int lv) {
             }
         }
     }
+    // then [nd][alpha][ne] x {r - q_i mod 2^64}: the centred lift of a value
+    // below q_i into [0, r) when q_i < 2 r (centred_narrow)
+    for (int j = 0; j < nd; j++)
+        for (int ii = 0; ii < a; ii++)
+            for (int e = 0; e < ne; e++) {
+                const int i = j * a + ii;
+                h.push_back(i < lv ? c->q[c->gidx(lv, e)] - c->q[i] : 0);
+            }
     return h;
 }
 
@@ -185,6 +193,21 @@ std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int>
     }
     for (int i = 0; i < nkeep; i++) h.push_back((u64)keep[i]);
     for (int k = 0; k < ndrop; k++) h.push_back((u64)drop[k]);
+    // then the fused kernel's [nkeep][ndrop] x {t (D/d_k) mod q_i, shoup,
+    // q_i - d_k mod 2^64} (its conversion yields t y~ directly; the last
+    // word lifts a value below d_k centred into [0, q_i) when d_k < 2 q_i)
+    for (int i = 0; i < nkeep; i++) {
+        const u64 qi = c->q[keep[i]];
+        for (int k = 0; k < ndrop; k++) {
+            u64 hat = 1;
+            for (int k2 = 0; k2 < ndrop; k2++)
+                if (k2 != k) hat = hmul(hat, c->q[drop[k2]] % qi, qi);
+            const u64 ht = hmul(hat, c->t % qi, qi);
+            h.push_back(ht);
+            h.push_back(shoup(ht, qi));
+            h.push_back(qi - c->q[drop[k]]);
+        }
+    }
     return h;
 }
 
@@ -194,6 +217,11 @@ int build_modup_tab(Ctx *c, int lv) {
     tb.ne = lv + c->K;
     tb.nd = c->digits(lv);
     const std::vector<u64> h = modup_table_host(c, lv);
+    tb.ext = (size_t)tb.nd * c->alpha * 2 + (size_t)tb.nd * c->alpha * tb.ne * 3;
+    tb.narrow = 1;
+    for (int i = 0; i < lv; i++)
+        for (int e = 0; e < tb.ne; e++)
+            if (c->q[i] >= 2 * c->q[c->gidx(lv, e)]) tb.narrow = 0;
     tb.d = dalloc(c, h.size());
     if (!tb.d) return set_err(c, HEGMM_ENOMEM, "modup table");
     cudaMemcpyAsync(tb.d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->st);
@@ -208,6 +236,11 @@ int build_div_tab(Ctx *c, int lv, int kind) {
     tb.nkeep = (int)tb.keep.size();
     tb.ndrop = (int)tb.drop.size();
     if (tb.ndrop > 4) return set_err(c, HEGMM_EINVAL, "at most 4 special primes");
+    tb.ext = (size_t)2 * tb.ndrop + (size_t)3 * tb.nkeep * tb.ndrop + (size_t)5 * tb.nkeep + tb.ndrop;
+    tb.narrow = 1;
+    for (int k : tb.drop)
+        for (int i : tb.keep)
+            if (c->q[k] >= 2 * c->q[i]) tb.narrow = 0;
     tb.d = dalloc(c, h.size());
     if (!tb.d) return set_err(c, HEGMM_ENOMEM, "div table");
     cudaMemcpyAsync(tb.d, h.data(), h.size() * 8, cudaMemcpyHostToDevice, c->st);
@@ -228,7 +261,7 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
     c->alpha = p->alpha;
     c->t = p->t;
     c->st = (cudaStream_t)stream;
-    if (p->logN < 10 || p->logN > 14 || p->L < 2 || p->K < 1 || p->L + p->K > 24 || p->qbits < 20 || p->qbits > 60 ||
+    if (p->logN < 10 || p->logN > 14 || p->L < 2 || p->K < 1 || p->L + p->K > 24 || p->qbits < 20 || p->qbits > 56 ||
         p->alpha < 1 || p->alpha > 4 || p->L % p->alpha != 0 || p->K < p->alpha || p->K > 4 || p->eta < 1 ||
         p->eta > 31 || p->ms_drop < 0 || p->ms_drop > 1 || (p->ms_drop && p->L < 3))
         return set_err(c, HEGMM_EINVAL, "parameters outside the supported limits");
@@ -298,28 +331,10 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
         u64 thr = ~0ull;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    // twiddles
+    // twiddles: [modulus][forward, inverse, inverse output factor][N] pairs
     const int N = c->N;
-    std::vector<u64> tw((size_t)c->nmod * 4 * N);
-    std::vector<u64> pw(N), ipw(N);
-    for (int m = 0; m < c->nmod; m++) {
-        const u64 q = c->q[m], psi = c->psi[m], ipsi = hinv(psi, q);
-        pw[0] = 1;
-        ipw[0] = 1;
-        for (int i = 1; i < N; i++) {
-            pw[i] = hmul(pw[i - 1], psi, q);
-            ipw[i] = hmul(ipw[i - 1], ipsi, q);
-        }
-        // [m][0 = forward, 1 = inverse][k] pairs {psi^(+-brev(k)), Shoup companion}
-        u64 *T = &tw[(size_t)m * 4 * N];
-        for (int k = 0; k < N; k++) {
-            const u32 b = brev_bits((u32)k, c->logN);
-            T[2 * k] = pw[b];
-            T[2 * k + 1] = shoup(pw[b], q);
-            T[2 * N + 2 * k] = ipw[b];
-            T[2 * N + 2 * k + 1] = shoup(ipw[b], q);
-        }
-    }
+    std::vector<u64> tw((size_t)c->nmod * 6 * N);
+    for (int m = 0; m < c->nmod; m++) build_twiddles_host(c->q[m], c->psi[m], c->logN, &tw[(size_t)m * 6 * N]);
     c->d_tw = dalloc(c, tw.size());
     void *dm = nullptr;
     if (cudaMallocAsync(&dm, sizeof(ModDev) * c->nmod, c->st) != cudaSuccess || !c->d_tw)
@@ -645,6 +660,15 @@ int hegmm_keygen(hegmm_ctx *h, uint64_t seed, const int *mln, int n_shapes, int 
     if (!c->have_sk || c->key_seed != seed) {
         if ((rc = gen_secret(c, seed))) return rc;
     }
+    if (c->key_pow2) {
+        // only the +-2^i rotations: every rotation of a product is a chain of them
+        for (int s = 0; s < n_shapes; s++)
+            if (!resolve_alg(mln[3 * s], mln[3 * s + 1], mln[3 * s + 2], alg, c->S))
+                return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
+        for (int z : pow2_offsets(c->S))
+            if ((rc = gen_key(c, galois_of(c, z)))) return rc;
+        return cuda_check(c, "keygen");
+    }
     for (int s = 0; s < n_shapes; s++) {
         const int m = mln[3 * s], l = mln[3 * s + 1], n = mln[3 * s + 2];
         const int a = resolve_alg(m, l, n, alg, c->S);
@@ -670,6 +694,18 @@ int hegmm_keygen(hegmm_ctx *h, uint64_t seed, const int *mln, int n_shapes, int 
             if ((rc = gen_key(c, g))) return rc;
     }
     return cuda_check(c, "keygen");
+}
+
+int hegmm_set_key_policy(hegmm_ctx *h, int policy) {
+    if (!h) return HEGMM_EINVAL;
+    Ctx *c = &h->c;
+    if (policy != HEGMM_KEYS_DIRECT && policy != HEGMM_KEYS_POW2)
+        return set_err(c, HEGMM_EINVAL, "key policy must be HEGMM_KEYS_DIRECT or HEGMM_KEYS_POW2");
+    c->key_pow2 = policy == HEGMM_KEYS_POW2;
+    if (c->key_pow2 && c->have_sk)
+        for (int z : pow2_offsets(c->S))
+            if (int rc = gen_key(c, galois_of(c, z))) return rc;
+    return cuda_check(c, "key policy");
 }
 
 int hegmm_keygen_rotations(hegmm_ctx *h, const int *z, int count) {

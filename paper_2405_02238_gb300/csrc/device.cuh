@@ -6,6 +6,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <vector>
+
 typedef uint64_t u64;
 typedef uint32_t u32;
 
@@ -119,6 +121,7 @@ HDI u32 auto_src(u32 c, u32 g, int logN) {
     return brev_bits((eg - 1u) >> 1, logN);
 }
 
+#ifdef __CUDACC__
 // mbarrier and bulk-copy (TMA engine) helpers.  A bulk copy moves bytes
 // (a multiple of 16, both addresses 16-byte aligned) from global to shared
 // memory and reports completion to an mbarrier as transaction bytes.
@@ -158,66 +161,46 @@ __device__ __forceinline__ bool mbar_wait_bounded(u64 *bar, u32 parity, int limi
     return false;
 }
 
+#endif  // __CUDACC__
+
+// Shoup product with an approximate quotient: a w mod q left in [0, 4q),
+// for a < 2^64, w < q < 2^62, wp = floor(w 2^64 / q).  The quotient
+// floor(a wp / 2^64) is taken from three of the four 32 x 32-bit partial
+// products (a1 p1 + hi(a1 p0) + hi(a0 p1)); the dropped low parts make it
+// smaller by 0, 1 or 2, so the remainder a w - h q is the Shoup remainder
+// ([0, 2q)) plus at most 2q.  Host and device compute the same h.
+HDI u64 mulsh_approx(u64 a, u64 w, u64 wp, u64 q) {
+#ifdef __CUDA_ARCH__
+    u64 h;
+    asm("{\n\t"
+        ".reg .u32 a0, a1, p0, p1, t1, t2, s0, s1;\n\t"
+        ".reg .u64 s;\n\t"
+        "mov.b64 {a0, a1}, %1;\n\t"
+        "mov.b64 {p0, p1}, %2;\n\t"
+        "mul.hi.u32 t1, a1, p0;\n\t"
+        "mul.hi.u32 t2, a0, p1;\n\t"
+        "add.cc.u32 s0, t1, t2;\n\t"
+        "addc.u32 s1, 0, 0;\n\t"
+        "mov.b64 s, {s0, s1};\n\t"
+        "mad.wide.u32 %0, a1, p1, s;\n\t"
+        "}"
+        : "=l"(h)
+        : "l"(a), "l"(wp));
+#else
+    const u64 a0 = (u32)a, a1 = a >> 32, p0 = (u32)wp, p1 = wp >> 32;
+    const u64 h = a1 * p1 + ((a1 * p0) >> 32) + ((a0 * p1) >> 32);
+#endif
+    return a * w - h * q;
+}
+
+// Centred lift of v in [0, p) into [0, r) when p < 2 r (every prime of a
+// context has the same bit length): v itself below p / 2, else v - p + r;
+// d = r - p mod 2^64.
+HDI u64 centred_narrow(u64 v, u64 half_p, u64 d) { return v > half_p ? v + d : v; }
+
 // Padded shared-memory index: one spare word every 16 keeps the strided
 // butterfly accesses of every pass at two wavefronts per warp.
 HDI int pad16(int i) { return i + (i >> 4); }
-
-// Forward negacyclic NTT (Cooley-Tukey, bit-reversed psi powers): one group
-// of 2^R elements through stages s0 .. s0+R-1.  Group g covers elements
-// base + k tl, k < 2^R.  psi[k] = psi^brev(k), psis its Shoup companion.
-template <int R>
-HDI void ntt_fwd_group(u64 *sm, int g, int s0, int logN, const u64 *psi, const u64 *psis, u64 q) {
-    const int ltl = logN - s0 - R;
-    const int tl = 1 << ltl;
-    const int B = g >> ltl, o = g & (tl - 1);
-    const int base = (B << (ltl + R)) + o;
-    u64 x[1 << R];
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int half = 1 << (R - 1 - r);
-#pragma unroll
-        for (int k = 0; k < (1 << R); k++) {
-            if (k & half) continue;
-            const int idx = ((1 << s0) << r) + (B << r) + (k >> (R - r));
-            const u64 w = psi[idx], wp = psis[idx];
-            const u64 U = x[k];
-            const u64 V = mulsh(x[k + half], w, wp, q);
-            x[k] = addm(U, V, q);
-            x[k + half] = subm(U, V, q);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
-}
-
-// Inverse negacyclic NTT (Gentleman-Sande, bit-reversed psi^-1 powers): one
-// group through the stages of butterfly distance 2^u0 .. 2^(u0+R-1).
-template <int R>
-HDI void ntt_inv_group(u64 *sm, int g, int u0, int logN, const u64 *ipsi, const u64 *ipsis, u64 q) {
-    const int tl = 1 << u0;
-    const int B = g >> u0, o = g & (tl - 1);
-    const int base = (B << (u0 + R)) + o;
-    u64 x[1 << R];
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int dist = 1 << r;
-#pragma unroll
-        for (int k = 0; k < (1 << R); k++) {
-            if (k & dist) continue;
-            const int idx = (1 << (logN - u0 - r - 1)) + (B << (R - 1 - r)) + (k >> (r + 1));
-            const u64 w = ipsi[idx], wp = ipsis[idx];
-            const u64 U = x[k], V = x[k + dist];
-            x[k] = addm(U, V, q);
-            x[k + dist] = mulsh(subm(U, V, q), w, wp, q);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
-}
 
 // A twiddle and its Shoup companion, loaded together (one 16-byte load).
 struct alignas(16) TwPair {
@@ -227,24 +210,32 @@ struct alignas(16) TwPair {
 // a w mod q left in [0, 2q) (Shoup without the final correction).
 HDI u64 mulsh_lazy(u64 a, u64 w, u64 wp, u64 q) { return a * w - mulhi(a, wp) * q; }
 
-// Lazy forward butterflies (Harvey) of one group of 2^R elements held in
-// registers, through stages s0 .. s0+R-1 (B: the group's block index):
-// inputs and outputs in [0, 4q), q < 2^62.
+// Lazy butterflies.  Each butterfly leaves its outputs at most 4q above its
+// inputs (T = w Y mod q in [0, 4q) from mulsh_approx; X + T and X - T + 4q)
+// and reduces nothing, so after the log2 N <= 14 stages of a transform the
+// values stay below (input bound + 56) q; with q < 2^56 and inputs below
+// 16 q everything stays below 128 q < 2^63.  Values are reduced once, when
+// they leave the transform.
+HDI void bfly_ct(u64 &X, u64 &Y, const TwPair &t, u64 q4, u64 q) {
+    const u64 T = mulsh_approx(Y, t.w, t.wp, q);
+    const u64 x = X;
+    X = x + T;
+    Y = x + (q4 - T);
+}
+
+// Forward negacyclic NTT (Cooley-Tukey, bit-reversed psi powers): one group
+// of 2^R elements held in registers through stages s0 .. s0+R-1; B is the
+// group's block index, tw[k] = psi^brev(k) with its Shoup companion.
 template <int R>
 HDI void ntt_fwd_regs(u64 *x, int B, int s0, const TwPair *tw, u64 q) {
-    const u64 q2 = 2 * q;
+    const u64 q4 = 4 * q;
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int half = 1 << (R - 1 - r);
 #pragma unroll
         for (int k = 0; k < (1 << R); k++) {
             if (k & half) continue;
-            const TwPair t = tw[((1 << s0) << r) + (B << r) + (k >> (R - r))];
-            u64 X = x[k];
-            X = X >= q2 ? X - q2 : X;
-            const u64 T = mulsh_lazy(x[k + half], t.w, t.wp, q);
-            x[k] = X + T;
-            x[k + half] = X - T + q2;
+            bfly_ct(x[k], x[k + half], tw[((1 << s0) << r) + (B << r) + (k >> (R - r))], q4, q);
         }
     }
 }
@@ -265,44 +256,75 @@ HDI void ntt_fwd_group_lazy(u64 *sm, int g, int s0, int logN, const TwPair *tw, 
     for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
 }
 
-// Lazy inverse butterflies (Harvey) of one group in registers, through the
-// stages of butterfly distance 2^u0 .. 2^(u0+R-1): inputs and outputs in
-// [0, 2q).
+// Inverse transform as a cyclic inverse DFT in Cooley-Tukey
+// (decimation-in-time) form: the NTT domain holds the evaluations at
+// psi omega^k (omega = psi^2) in bit-reversed order, which is the order this
+// form reads; its output (natural order) is multiplied by N^-1 psi^-i when
+// it leaves (a_i = N^-1 psi^-i sum_k a^_k omega^-ik).  One group of 2^R
+// elements in registers: element k of the group is element base + k 2^u0
+// of the limb, base = B 2^(u0+R) + o with o < 2^u0; stage r pairs k and
+// k + 2^r (span 2^(u0+r) in the limb) with omega^(-j N / 2^(u0+r+1)),
+// j = o + (k mod 2^r) 2^u0, stored at tw[2^(u0+r) + j].
 template <int R>
-HDI void ntt_inv_regs(u64 *x, int B, int u0, int logN, const TwPair *tw, u64 q) {
-    const u64 q2 = 2 * q;
+HDI void ntt_inv_ct_regs(u64 *x, int o, int u0, const TwPair *tw, u64 q) {
+    const u64 q4 = 4 * q;
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        const int dist = 1 << r;
+        const int h = 1 << r;
 #pragma unroll
         for (int k = 0; k < (1 << R); k++) {
-            if (k & dist) continue;
-            const TwPair t = tw[(1 << (logN - u0 - r - 1)) + (B << (R - 1 - r)) + (k >> (r + 1))];
-            const u64 U = x[k], V = x[k + dist];
-            u64 X = U + V;
-            x[k] = X >= q2 ? X - q2 : X;
-            x[k + dist] = mulsh_lazy(U - V + q2, t.w, t.wp, q);
+            if (k & h) continue;
+            bfly_ct(x[k], x[k + h], tw[(1 << (u0 + r)) + o + ((k & (h - 1)) << u0)], q4, q);
         }
     }
 }
 
 template <int R>
-HDI void ntt_inv_group_lazy(u64 *sm, int g, int u0, int logN, const TwPair *tw, u64 q) {
+HDI void ntt_inv_ct_group(u64 *sm, int g, int u0, const TwPair *tw, u64 q) {
     const int tl = 1 << u0;
     const int B = g >> u0, o = g & (tl - 1);
     const int base = (B << (u0 + R)) + o;
     u64 x[1 << R];
 #pragma unroll
     for (int k = 0; k < (1 << R); k++) x[k] = sm[pad16(base + k * tl)];
-    ntt_inv_regs<R>(x, B, u0, logN, tw, q);
+    ntt_inv_ct_regs<R>(x, o, u0, tw, q);
 #pragma unroll
     for (int k = 0; k < (1 << R); k++) sm[pad16(base + k * tl)] = x[k];
 }
 
-// Reduce a value in [0, 4q) to [0, q).
-HDI u64 reduce4(u64 x, u64 q) {
-    x = x >= 2 * q ? x - 2 * q : x;
-    return x >= q ? x - q : x;
+// Twiddle tables of one prime (host side; shared by the context and by host
+// checks of the transforms): out[3][N] pairs {w, floor(w 2^64 / q)}:
+// [0][k] = psi^brev(k) (forward), [1][h + j] = omega^(-j N / (2h)) for
+// h = 1, 2, .., N/2 and j < h (inverse, index 0 unused), [2][i] =
+// N^-1 psi^-i (the inverse's output factor).  psi: a primitive 2N-th root.
+inline void build_twiddles_host(u64 q, u64 psi, int logN, u64 *out) {
+    const int N = 1 << logN;
+    auto mm = [q](u64 a, u64 b) { return (u64)((unsigned __int128)a * b % q); };
+    auto sh = [q](u64 w) { return (u64)(((unsigned __int128)w << 64) / q); };
+    u64 ipsi = 1, ninv = 1;  // psi^-1 = psi^(2N-1), N^-1 = q - (q-1)/N (q = 1 mod 2N)
+    for (int i = 0; i < 2 * N - 1; i++) ipsi = mm(ipsi, psi);
+    ninv = q - (q - 1) / (u64)N;
+    std::vector<u64> pw((size_t)N), ipw((size_t)N);
+    pw[0] = ipw[0] = 1;
+    for (int i = 1; i < N; i++) {
+        pw[i] = mm(pw[i - 1], psi);
+        ipw[i] = mm(ipw[i - 1], ipsi);
+    }
+    u64 *T0 = out, *T1 = out + 2 * (size_t)N, *T2 = out + 4 * (size_t)N;
+    for (int k = 0; k < N; k++) {
+        const u64 w = pw[brev_bits((u32)k, logN)];
+        T0[2 * k] = w;
+        T0[2 * k + 1] = sh(w);
+        T2[2 * k] = mm(ninv, ipw[k]);
+        T2[2 * k + 1] = sh(T2[2 * k]);
+    }
+    T1[0] = T1[1] = 0;
+    for (int h = 1; h < N; h <<= 1)
+        for (int j = 0; j < h; j++) {
+            const u64 w = ipw[(size_t)j * (N / h)];  // omega^-(j N / 2h) = psi^-(j N / h)
+            T1[2 * (h + j)] = w;
+            T1[2 * (h + j) + 1] = sh(w);
+        }
 }
 
 // SplitMix64 (Steele, Lea, Flood 2014) in counter mode.

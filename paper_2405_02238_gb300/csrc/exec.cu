@@ -74,9 +74,11 @@ int modup(Ctx *c, int lv, int n, const u64 *xn, long long xn_stride, u64 *xc, u6
         cudaMemcpy2DAsync(xc, (size_t)lv * N * 8, xn, (size_t)xn_stride * 8, (size_t)lv * N * 8, n,
                           cudaMemcpyDeviceToDevice, c->st);
     }
-    if ((rc = ntt_inv(c, pat_ct(c, xc, n, lv)))) return rc;
     const ModUpTab *tb = modup_tab(c, lv);
     if (!tb) return HEGMM_ENOMEM;
+    // the inverse NTT also multiplies limb i by [(Q_j/q_i)^-1]_{q_i} (the
+    // table's first pairs; 1 when a digit is one prime)
+    if ((rc = ntt_inv(c, pat_ct(c, xc, n, lv), c->alpha > 1 ? tb->d : nullptr))) return rc;
     return modup_ntt(c, *tb, pat_nonown(c, lv, D, n, (long long)nd * ne * N), xc, (long long)lv * N, xn, xn_stride, D,
                      (long long)nd * ne * N, n);
 }
@@ -89,7 +91,8 @@ int ksw_moddown(Ctx *c, int lv, const RotDesc *d_rots, const DivDesc *d_div, int
     int rc;
     (void)tmp;
     if ((rc = ksw_ip(c, lv, d_rots, nrot))) return rc;
-    if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, 2 * nrot)))) return rc;
+    // the special limbs' inverse NTT also multiplies them by [t^-1 (P/p_k)^-1]_{p_k}
+    if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, 2 * nrot), tb->d))) return rc;
     return divround_ntt(c, *tb, d_div, 2 * nrot);
 }
 
@@ -202,7 +205,7 @@ int modswitch_polys(Ctx *c, int lv, u64 *in, int npoly, u64 *tmp, u64 *out, DivD
     pd.mod[0] = (unsigned char)(lv - 1);
     int rc;
     (void)tmp;
-    if ((rc = ntt_inv(c, pd))) return rc;
+    if ((rc = ntt_inv(c, pd, tb->d))) return rc;  // times [t^-1]_{q_{lv-1}}
     return divround_ntt(c, *tb, d_desc, npoly);
 }
 

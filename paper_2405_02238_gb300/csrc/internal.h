@@ -136,13 +136,17 @@ enum KernelKind {
 
 struct ModUpTab {
     int lv = 0, ne = 0, nd = 0;
-    u64 *d = nullptr;  // see build_modup_tab
+    u64 *d = nullptr;  // see modup_table_host
+    size_t ext = 0;    // word offset of the narrow-lift constants in d
+    int narrow = 0;    // every digit prime < 2 x every prime of the basis
 };
 
 struct DivTab {
     int nkeep = 0, ndrop = 0;
     std::vector<int> keep, drop;  // global modulus indices
-    u64 *d = nullptr;             // see build_div_tab
+    u64 *d = nullptr;             // see div_table_host
+    size_t ext = 0;               // word offset of the fused kernel's constants in d
+    int narrow = 0;               // every dropped prime < 2 x every kept prime
 };
 
 struct ShapeData;
@@ -166,7 +170,7 @@ struct Ctx {
     u64 psi[MAXM]{};
     ModDev hmod[MAXM]{};
     ModDev *d_mods = nullptr;
-    u64 *d_tw = nullptr;  // [nmod][fwd, inv][N] x {psi^(+-brev(k)), Shoup companion}
+    u64 *d_tw = nullptr;  // [nmod][3][N] x {w, Shoup companion}: see build_twiddles_host (device.cuh)
     cudaStream_t st = nullptr;
     std::string err;
     int nsm = 148;
@@ -181,7 +185,7 @@ struct Ctx {
     std::map<std::pair<int, int>, DivTab> divs;  // (level, 0 = ModDown / 1 = modswitch)
     std::vector<int> slot_pos0, slot_pos1;       // slot -> NTT position mod t
     int *d_slot_pos = nullptr;                   // device copy of slot_pos0 then slot_pos1 (N entries)
-    std::map<std::tuple<int, int, int, int, int>, ShapeData *> shapes;  // per (shape, order): plan + masks
+    std::map<std::tuple<int, int, int, int, int, int>, ShapeData *> shapes;  // per (shape, order, key policy): plan + masks
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     std::map<std::tuple<int, int, int, int>, std::pair<size_t, size_t>> shape_counts;  // iterations, extractions
     unsigned long long bplan_clock = 0;
@@ -190,6 +194,7 @@ struct Ctx {
     int lazy_relin = 0;                        // products: one relinearisation of the summed tensors
     int lt_shared = 0;                         // products: shared baby steps + giant rotations
     int giant_cost = 8;                        // shared baby steps: giant rotation cost in the greedy rule
+    int key_pow2 = 0;                          // power-of-two key policy: rotations as chains of +-2^i
     int use_graphs = 1;                        // replay cached plans as CUDA graphs
     int *d_err = nullptr;                      // set by a kernel whose bounded wait ran out
     int wait_limit = 1 << 22;                  // polls of a bounded mbarrier wait
@@ -206,7 +211,9 @@ struct Ctx {
     size_t plan_cache_budget = (size_t)48 << 30;  // workspace kept by cached batch plans
     u64 *d_Pmod = nullptr;           // [np] x {P mod q_i, shoup}
     std::map<int, u64 *> crt;        // level -> CRT-to-t table
-    std::map<int, std::vector<u64>> noalloc_tabs;  // level -> host tables of the scratch-free rotation
+    // level -> host tables of the scratch-free rotation: the ModUp table, then
+    // the ModDown table from word `first`
+    std::map<int, std::pair<size_t, std::vector<u64>>> noalloc_tabs;
 
     bool timing = false;
     struct Pending {
@@ -249,7 +256,9 @@ int peak_butterflies(Ctx *c, double *per_s);
 // ---------------------------------------------------------------- kernels.cu
 int init_kernels(Ctx *c);
 int ntt_fwd(Ctx *c, const LimbPat &p);
-int ntt_inv(Ctx *c, const LimbPat &p);
+// inverse NTT; scale (may be null): a {w, Shoup companion} pair per inner
+// entry of the pattern, multiplied into that entry's limbs
+int ntt_inv(Ctx *c, const LimbPat &p, const u64 *scale = nullptr);
 // ModUp base conversion of n inputs: xc (coeff, lv limbs) and xn (NTT, lv
 // limbs) -> D [nd][ne][N] (own limbs copied from xn in NTT form, others in
 // coefficient form, to be forward transformed).

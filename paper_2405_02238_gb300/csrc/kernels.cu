@@ -113,51 +113,67 @@ __device__ __forceinline__ void inv_middle(u64 *sm, const TwPair *__restrict__ T
     constexpr int N = 1 << LOGN, LAST = NttPasses<LOGN>::LAST;
 #pragma unroll
     for (int u0 = 3; u0 < LAST; u0 += 3) {
-        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, u0, LOGN, T, q);
+        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_ct_group<3>(sm, g, u0, T, q);
         __syncthreads();
     }
 }
 
-// Twiddle table layout: [modulus][0 = forward psi^brev(k), 1 = inverse][N] pairs.
-__device__ __forceinline__ const TwPair *tw_of(const TwPair *tw, int mi, int inv, int N) {
-    return tw + ((size_t)mi * 2 + inv) * N;
+// Twiddle table layout: [modulus][0 = forward psi^brev(k), 1 = inverse
+// omega^-j by span, 2 = inverse output factor N^-1 psi^-i][N] pairs
+// (build_twiddles_host).
+__device__ __forceinline__ const TwPair *tw_of(const TwPair *tw, int mi, int which, int N) {
+    return tw + ((size_t)mi * 3 + which) * N;
 }
 
+// One CTA per limb.  Forward: values leave reduced to [0, q).  Inverse: the
+// output is the coefficient vector in [0, q), multiplied by scale[i] (a
+// {w, Shoup companion} pair per inner entry i of the pattern) when scale is
+// not null.
 template <int LOGN, bool INV, int NT>
 __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_ntt(LimbPat p, const ModDev *__restrict__ mods,
-                                                                 const TwPair *__restrict__ tw) {
+                                                                 const TwPair *__restrict__ tw,
+                                                                 const TwPair *__restrict__ scale) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
     int mi;
     u64 *ptr = pat_ptr(p, blockIdx.x, N, mi);
     const u64 q = mods[mi].q;
-    const TwPair *T = tw_of(tw, mi, INV ? 1 : 0, N);
     if (INV) {
-        // coalesced 16-byte loads into shared memory (the first inverse pass
-        // reads 8 consecutive coefficients per group)
-#pragma unroll 4
-        for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(ptr + i);
-            const int pi = pad16(i);
-            sm[pi] = v.x;
-            sm[pi + 1] = v.y;
+        const TwPair *T = tw_of(tw, mi, 1, N);
+        // first pass on registers: group g is the 8 consecutive elements 8g .. 8g+7
+        for (int g = threadIdx.x; g < N / 8; g += NT) {
+            u64 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(ptr + 8 * g + k));
+                x[k] = v.x;
+                x[k + 1] = v.y;
+            }
+            ntt_inv_ct_regs<3>(x, 0, 0, T, q);
+#pragma unroll
+            for (int k = 0; k < 8; k++) sm[pad16(8 * g + k)] = x[k];
         }
-        __syncthreads();
-        for (int g = threadIdx.x; g < N / 8; g += NT) ntt_inv_group_lazy<3>(sm, g, 0, LOGN, T, q);
         __syncthreads();
         inv_middle<LOGN, NT>(sm, T, q);
-        for (int g = threadIdx.x; g < (N >> RL); g += NT) ntt_inv_group_lazy<RL>(sm, g, LAST, LOGN, T, q);
-        __syncthreads();
-        // scaling by N^-1 with coalesced 16-byte stores
-        const u64 ninv = mods[mi].ninv, ninv_sh = mods[mi].ninv_sh;
-        for (int i = threadIdx.x * 2; i < N; i += NT * 2) {
-            const int pi = pad16(i);
-            ulonglong2 v;
-            v.x = mulsh(sm[pi], ninv, ninv_sh, q);
-            v.y = mulsh(sm[pi + 1], ninv, ninv_sh, q);
-            *reinterpret_cast<ulonglong2 *>(ptr + i) = v;
+        // last pass on registers, then the output factor N^-1 psi^-i (and the
+        // optional limb scale), stored in natural order
+        const TwPair *F = tw_of(tw, mi, 2, N);
+        TwPair sc{0, 0};
+        if (scale) sc = scale[blockIdx.x / (p.count / p.inner)];
+        for (int g = threadIdx.x; g < (N >> RL); g += NT) {
+            u64 x[1 << RL];
+#pragma unroll
+            for (int k = 0; k < (1 << RL); k++) x[k] = sm[pad16(g + (k << LAST))];
+            ntt_inv_ct_regs<RL>(x, g, LAST, T, q);
+#pragma unroll
+            for (int k = 0; k < (1 << RL); k++) {
+                const int e = g + (k << LAST);
+                const TwPair f = F[e];
+                ptr[e] = scale ? mulsh(mulsh_lazy(x[k], f.w, f.wp, q), sc.w, sc.wp, q) : mulsh(x[k], f.w, f.wp, q);
+            }
         }
     } else {
+        const TwPair *T = tw_of(tw, mi, 0, N);
         for (int g = threadIdx.x; g < N / 8; g += NT) {
             u64 x[8];
 #pragma unroll
@@ -168,26 +184,31 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_ntt(LimbPat p, cons
         }
         __syncthreads();
         fwd_middle<LOGN, NT>(sm, T, q);
+        const u64 barr = mods[mi].barr;
         for (int g = threadIdx.x; g < (N >> RL); g += NT) {
             u64 x[1 << RL];
 #pragma unroll
             for (int k = 0; k < (1 << RL); k++) x[k] = sm[pad16((g << RL) + k)];
             ntt_fwd_regs<RL>(x, g, LAST, T, q);
 #pragma unroll
-            for (int k = 0; k < (1 << RL); k++) ptr[(g << RL) + k] = reduce4(x[k], q);
+            for (int k = 0; k < (1 << RL); k++) ptr[(g << RL) + k] = redc64(x[k], q, barr);
         }
     }
 }
 
 // ModDown / modulus switch, fused: one CTA per (polynomial, kept prime q_i).
-// Prologue: y~_i = sum_k centred([u_k t^-1 (D/d_k)^-1]_{d_k}) (D/d_k) mod q_i
-// from the coefficient-form dropped limbs; forward NTT in shared memory;
-// epilogue: out_i = (u_i - t y~_i) D^-1 (+ add_i at the automorphism's index).
-// Table layout as k_div_conv (build_div_tab).
-template <int LOGN, int NT>
+// The dropped limbs arrive in coefficient form already multiplied by
+// [t^-1 (D/d_k)^-1]_{d_k} (the scale of their inverse NTT), z_k.
+// Prologue: t y~_i = sum_k centred(z_k) [t (D/d_k)]_{q_i}, kept lazily below
+// 4 ndrop q_i; forward NTT in shared memory (values grow by at most 4 q_i a
+// stage); epilogue: out_i = (u_i - t y~_i) D^-1 (+ add_i at the
+// automorphism's index), computed as (u_i + 128 q_i - t y~_i) D^-1 with one
+// reducing Shoup product.  Table layout: build_div_tab; NARROW: every
+// dropped prime below twice every kept one (centred_narrow).
+template <int LOGN, int NT, bool NARROW>
 __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nkeep, int ndrop,
                                                                           const ModDev *__restrict__ mods,
-                                                                          const u64 *__restrict__ tab,
+                                                                          const u64 *__restrict__ tab, int ext,
                                                                           const DivDesc *__restrict__ desc,
                                                                           const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
@@ -195,13 +216,13 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
     const int npoly = gridDim.x / nkeep;  // prime-major block order (twiddles stay in L1)
     const int i = blockIdx.x / npoly, b = blockIdx.x - i * npoly;
     const DivDesc d = desc[b];
-    const u64 *tA = tab;
-    const u64 *tB = tA + 2 * ndrop;
+    const u64 *tB = tab + 2 * ndrop;
     const u64 *tC = tB + (size_t)3 * nkeep * ndrop;
     const u64 *tI = tC + (size_t)4 * nkeep;
     const int mi = (int)tI[i];
     const ModDev M = mods[mi];
     const u64 *hB = tB + (size_t)i * ndrop * 3;
+    const u64 *hE = tab + ext + (size_t)i * ndrop * 3;
     const TwPair *T = tw_of(tw, mi, 0, N);
     constexpr int RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
     // prologue fused with the first pass: the conversion of the group's 8 coefficients
@@ -213,9 +234,10 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
             u64 acc = 0;
             for (int kk = 0; kk < ndrop; kk++) {
                 const u64 dk = mods[tI[nkeep + kk]].q;
-                const u64 z = mulsh(d.u[(size_t)(nkeep + kk) * N + c], __ldg(tA + 2 * kk), __ldg(tA + 2 * kk + 1), dk);
-                const u64 *h = hB + 3 * kk;
-                acc = addm(acc, mulsh(centred(z, dk, __ldg(h + 2), M.q, M.barr), __ldg(h), __ldg(h + 1), M.q), M.q);
+                const u64 z = d.u[(size_t)(nkeep + kk) * N + c];
+                const u64 v = NARROW ? centred_narrow(z, dk >> 1, __ldg(hE + 3 * kk + 2))
+                                     : centred(z, dk, __ldg(hB + 3 * kk + 2), M.q, M.barr);
+                acc += mulsh_approx(v, __ldg(hE + 3 * kk), __ldg(hE + 3 * kk + 1), M.q);
             }
             x[k] = acc;
         }
@@ -226,10 +248,10 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
     __syncthreads();
     fwd_middle<LOGN, NT>(sm, T, M.q);
     const u64 *k4 = tC + 4 * i;
-    const u64 Di = k4[0], Dis = k4[1], tq = k4[2], tqs = k4[3];
+    const u64 Di = k4[0], Dis = k4[1], q128 = M.q << 7;
     const u64 *ui = d.u + (size_t)i * N;
     u64 *oi = d.out + (size_t)i * N;
-    // last pass fused with the epilogue: out = (u - t y~) D^-1 (+ add at the automorphism's index)
+    // last pass fused with the epilogue
     for (int g = threadIdx.x; g < (N >> RL); g += NT) {
         u64 x[1 << RL];
         const int base = g << RL;
@@ -239,8 +261,7 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
 #pragma unroll
         for (int k = 0; k < (1 << RL); k++) {
             const int c = base + k;
-            u64 v = subm(ui[c], mulsh(x[k], tq, tqs, M.q), M.q);
-            v = mulsh(v, Di, Dis, M.q);
+            u64 v = mulsh(ui[c] + (q128 - x[k]), Di, Dis, M.q);
             if (d.add) v = addm(v, d.add[(size_t)i * N + (d.g == 1 ? (u32)c : auto_src((u32)c, d.g, LOGN))], M.q);
             oi[c] = v;
         }
@@ -249,12 +270,15 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
 
 // ModUp, fused: one CTA per (input, digit j, prime e outside digit j):
 // prologue computes the digit's centred fast base conversion into prime e
-// from the coefficient-form source limbs, then forward NTT, then store.
-// Limb selection follows a LimbPat whose off[] = j * ne + e.
-template <int LOGN, int NT>
+// from the coefficient-form source limbs, which arrive already multiplied
+// by [(Q_j/q_i)^-1]_{q_i} (the scale of their inverse NTT), summed lazily
+// below 4 alpha r; then forward NTT, then the reduced store.  Limb
+// selection follows a LimbPat whose off[] = j * ne + e.  NARROW: every
+// source prime below twice every target prime (centred_narrow).
+template <int LOGN, int NT, bool NARROW>
 __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha,
                                                                        int L, const ModDev *__restrict__ mods,
-                                                                       const u64 *__restrict__ tab,
+                                                                       const u64 *__restrict__ tab, int ext,
                                                                        const u64 *__restrict__ xc, long long xc_stride,
                                                                        const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
@@ -267,8 +291,8 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p
     const u64 *x = xc + outer * xc_stride;
     const int lo = j * alpha, ns = min(alpha, lv - lo);
     const ModDev R = mods[mi];
-    const u64 *tinv = tab + (size_t)j * alpha * 2;
     const u64 *thm = tab + (size_t)nd * alpha * 2 + (size_t)j * alpha * ne * 3;
+    const u64 *tex = tab + ext + (size_t)j * alpha * ne;
     const TwPair *T = tw_of(tw, mi, 0, N);
     constexpr int RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
     // prologue fused with the first pass: the digit's conversion of the group's coefficients
@@ -280,9 +304,11 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p
             u64 acc = 0;
             for (int ii = 0; ii < ns; ii++) {
                 const u64 sq = mods[lo + ii].q;
-                const u64 y = mulsh(x[(size_t)(lo + ii) * N + c], __ldg(tinv + 2 * ii), __ldg(tinv + 2 * ii + 1), sq);
+                const u64 y = x[(size_t)(lo + ii) * N + c];
                 const u64 *h = thm + ((size_t)ii * ne + e) * 3;
-                acc = addm(acc, mulsh(centred(y, sq, __ldg(h + 2), R.q, R.barr), __ldg(h), __ldg(h + 1), R.q), R.q);
+                const u64 v = NARROW ? centred_narrow(y, sq >> 1, __ldg(tex + (size_t)ii * ne + e))
+                                     : centred(y, sq, __ldg(h + 2), R.q, R.barr);
+                acc += mulsh_approx(v, __ldg(h), __ldg(h + 1), R.q);
             }
             xv[k] = acc;
         }
@@ -299,7 +325,7 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p
         for (int k = 0; k < (1 << RL); k++) xv[k] = sm[pad16(base + k)];
         ntt_fwd_regs<RL>(xv, g, LAST, T, R.q);
 #pragma unroll
-        for (int k = 0; k < (1 << RL); k++) dst[base + k] = reduce4(xv[k], R.q);
+        for (int k = 0; k < (1 << RL); k++) dst[base + k] = redc64(xv[k], R.q, R.barr);
     }
 }
 
@@ -316,10 +342,13 @@ __global__ void k_modup_own(int lv, int ne, int alpha, int logN, const u64 *__re
 template <int LOGN, int NT>
 static int set_smem_attrs_nt() {
     const int sm = (int)NttCfg<LOGN>::SMEM;
-    if (cudaFuncSetAttribute(k_ntt<LOGN, false, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_ntt<LOGN, true, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_divround_ntt<LOGN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_modup_ntt<LOGN, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (cudaFuncSetAttribute(k_ntt<LOGN, false, NT>, A, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_ntt<LOGN, true, NT>, A, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_divround_ntt<LOGN, NT, false>, A, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_divround_ntt<LOGN, NT, true>, A, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_modup_ntt<LOGN, NT, false>, A, sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_modup_ntt<LOGN, NT, true>, A, sm) != cudaSuccess)
         return 1;
     return 0;
 }
@@ -364,39 +393,49 @@ static bool ntt_wide(const Ctx *c, long long ctas) {
 }
 
 template <int LG, bool INV>
-static void launch_ntt(Ctx *c, const LimbPat &p, const TwPair *tw) {
+static void launch_ntt(Ctx *c, const LimbPat &p, const TwPair *tw, const TwPair *scale) {
     constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
     constexpr size_t SM = NttCfg<LG>::SMEM;
     if (ntt_wide<LG>(c, p.count))
-        k_ntt<LG, INV, NW><<<p.count, NW, SM, c->st>>>(p, c->d_mods, tw);
+        k_ntt<LG, INV, NW><<<p.count, NW, SM, c->st>>>(p, c->d_mods, tw, scale);
     else
-        k_ntt<LG, INV, NT><<<p.count, NT, SM, c->st>>>(p, c->d_mods, tw);
+        k_ntt<LG, INV, NT><<<p.count, NT, SM, c->st>>>(p, c->d_mods, tw, scale);
 }
 
 int ntt_fwd(Ctx *c, const LimbPat &p) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_FWD, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
-    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, false>(c, p, tw)));
+    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, false>(c, p, tw, nullptr)));
     return cuda_check(c, "ntt_fwd");
 }
 
-int ntt_inv(Ctx *c, const LimbPat &p) {
+int ntt_inv(Ctx *c, const LimbPat &p, const u64 *scale) {
     if (p.count <= 0) return HEGMM_OK;
     Launch t(c, K_NTT_INV, 2.0 * p.count * c->limb_bytes(), p.count * ntt_bfly(c));
     const TwPair *tw = reinterpret_cast<const TwPair *>(c->d_tw);
-    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, true>(c, p, tw)));
+    const TwPair *sc = reinterpret_cast<const TwPair *>(scale);
+    HG_DISPATCH_LOGN(c->logN, (launch_ntt<LG, true>(c, p, tw, sc)));
     return cuda_check(c, "ntt_inv");
+}
+
+template <int LG, int NT, bool NARROW>
+static void launch_divround_t(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
+    k_divround_ntt<LG, NT, NARROW><<<grid, NT, NttCfg<LG>::SMEM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d,
+                                                                       (int)tab.ext, d_desc, tw);
 }
 
 template <int LG>
 static void launch_divround(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
     constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
-    constexpr size_t SM = NttCfg<LG>::SMEM;
-    if (ntt_wide<LG>(c, grid))
-        k_divround_ntt<LG, NW><<<grid, NW, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw);
-    else
-        k_divround_ntt<LG, NT><<<grid, NT, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d, d_desc, tw);
+    const bool w = ntt_wide<LG>(c, grid);
+    if (tab.narrow) {
+        if (w) launch_divround_t<LG, NW, true>(c, grid, tab, d_desc, tw);
+        else launch_divround_t<LG, NT, true>(c, grid, tab, d_desc, tw);
+    } else {
+        if (w) launch_divround_t<LG, NW, false>(c, grid, tab, d_desc, tw);
+        else launch_divround_t<LG, NT, false>(c, grid, tab, d_desc, tw);
+    }
 }
 
 int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
@@ -410,19 +449,30 @@ int divround_ntt(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly) {
     return cuda_check(c, "divround_ntt");
 }
 
+template <int LG, int NT, bool NARROW>
+static void launch_modup_t(Ctx *c, const LimbPat &nonown, const ModUpTab &tb, const u64 *xc, long long xc_stride,
+                           const TwPair *tw) {
+    k_modup_ntt<LG, NT, NARROW><<<nonown.count, NT, NttCfg<LG>::SMEM, c->st>>>(
+        nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods, tb.d, (int)tb.ext, xc, xc_stride, tw);
+}
+
 template <int LG>
 static void launch_modup(Ctx *c, const LimbPat &nonown, const ModUpTab &tb, const u64 *xc, long long xc_stride,
                          const TwPair *tw) {
     constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
-    constexpr size_t SM = NttCfg<LG>::SMEM;
-    if (ntt_wide<LG>(c, nonown.count))
-        k_modup_ntt<LG, NW><<<nonown.count, NW, SM, c->st>>>(nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods,
-                                                             tb.d, xc, xc_stride, tw);
-    else
-        k_modup_ntt<LG, NT><<<nonown.count, NT, SM, c->st>>>(nonown, tb.lv, tb.ne, tb.nd, c->alpha, c->L, c->d_mods,
-                                                             tb.d, xc, xc_stride, tw);
+    const bool w = ntt_wide<LG>(c, nonown.count);
+    if (tb.narrow) {
+        if (w) launch_modup_t<LG, NW, true>(c, nonown, tb, xc, xc_stride, tw);
+        else launch_modup_t<LG, NT, true>(c, nonown, tb, xc, xc_stride, tw);
+    } else {
+        if (w) launch_modup_t<LG, NW, false>(c, nonown, tb, xc, xc_stride, tw);
+        else launch_modup_t<LG, NT, false>(c, nonown, tb, xc, xc_stride, tw);
+    }
 }
 
+// xc: the coefficient form of the inputs, each limb i already multiplied by
+// [(Q_j/q_i)^-1]_{q_i} (modup() scales its inverse NTT by the table's first
+// pairs).
 int modup_ntt(Ctx *c, const ModUpTab &tb, const LimbPat &nonown, const u64 *xc, long long xc_stride, const u64 *xn,
               long long xn_stride, u64 *D, long long D_stride, int n) {
     Launch t(c, K_MODUP, (double)n * (tb.lv + 2.0 * (tb.nd * tb.ne)) * c->limb_bytes(), nonown.count * ntt_bfly(c));
@@ -1262,35 +1312,31 @@ __global__ void k_scatter_slots(const int *__restrict__ off, const int *__restri
     }
 }
 
-// Butterfly throughput probe: the lazy forward butterfly of the NTT kernels,
-// repeated on registers (12 per round, the stages of one radix-8 group).
-__device__ __forceinline__ void bfly_lazy(u64 &X, u64 &Y, const TwPair &t, u64 q, u64 q2) {
-    u64 a = X >= q2 ? X - q2 : X;
-    const u64 T = mulsh_lazy(Y, t.w, t.wp, q);
-    X = a + T;
-    Y = a - T + q2;
-}
-
+// Butterfly throughput probe: the lazy butterfly of the NTT kernels
+// (bfly_ct), repeated on registers (12 per round, the stages of one radix-8
+// group); the values are reduced every round so that they stay in range.
 __global__ void __launch_bounds__(256) k_bfly_peak(u64 q, const TwPair *__restrict__ tw, int iters, u64 *out) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     u64 x[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) x[k] = ((u64)gid * 8 + k) % q;
     const TwPair t0 = tw[1], t1 = tw[2], t2 = tw[3], t3 = tw[4], t4 = tw[5], t5 = tw[6], t6 = tw[7];
-    const u64 q2 = 2 * q;
+    const u64 q4 = 4 * q, q16 = 16 * q;
     for (int it = 0; it < iters; it++) {
-        bfly_lazy(x[0], x[4], t0, q, q2);
-        bfly_lazy(x[1], x[5], t0, q, q2);
-        bfly_lazy(x[2], x[6], t0, q, q2);
-        bfly_lazy(x[3], x[7], t0, q, q2);
-        bfly_lazy(x[0], x[2], t1, q, q2);
-        bfly_lazy(x[1], x[3], t1, q, q2);
-        bfly_lazy(x[4], x[6], t2, q, q2);
-        bfly_lazy(x[5], x[7], t2, q, q2);
-        bfly_lazy(x[0], x[1], t3, q, q2);
-        bfly_lazy(x[2], x[3], t4, q, q2);
-        bfly_lazy(x[4], x[5], t5, q, q2);
-        bfly_lazy(x[6], x[7], t6, q, q2);
+        bfly_ct(x[0], x[4], t0, q4, q);
+        bfly_ct(x[1], x[5], t0, q4, q);
+        bfly_ct(x[2], x[6], t0, q4, q);
+        bfly_ct(x[3], x[7], t0, q4, q);
+        bfly_ct(x[0], x[2], t1, q4, q);
+        bfly_ct(x[1], x[3], t1, q4, q);
+        bfly_ct(x[4], x[6], t2, q4, q);
+        bfly_ct(x[5], x[7], t2, q4, q);
+        bfly_ct(x[0], x[1], t3, q4, q);
+        bfly_ct(x[2], x[3], t4, q4, q);
+        bfly_ct(x[4], x[5], t5, q4, q);
+        bfly_ct(x[6], x[7], t6, q4, q);
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = x[k] >= q16 ? x[k] - q16 : x[k];  // bounded below 40 q
     }
     out[gid] = x[0] ^ x[1] ^ x[2] ^ x[3] ^ x[4] ^ x[5] ^ x[6] ^ x[7];
 }

@@ -43,7 +43,7 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     Ctx *c = &h->c;
     if (out->level != in->level) return set_err(c, HEGMM_EINVAL, "rotate_noalloc: output level differs from input");
     if (out->d == in->d) return set_err(c, HEGMM_EINVAL, "rotate_noalloc: output must not alias the input");
-    const int lv = in->level, N = c->N, K = c->K, ne = lv + K, nd = c->digits(lv), a = c->alpha;
+    const int lv = in->level, N = c->N, K = c->K, ne = lv + K, nd = c->digits(lv);
     const size_t need = NOALLOC_HDR + (size_t)lv * N + (size_t)nd * ne * N + (size_t)2 * ne * N + (size_t)2 * lv * N;
     if (need > NOALLOC_WORDS)
         return set_err(c, HEGMM_EINVAL,
@@ -91,12 +91,20 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
     if (tit == c->noalloc_tabs.end()) {
         std::vector<int> keep, drop;
         std::vector<u64> t = modup_table_host(c, lv);
+        const size_t first = t.size();
         const std::vector<u64> dv = div_table_host(c, lv, 0, keep, drop);
         t.insert(t.end(), dv.begin(), dv.end());
-        tit = c->noalloc_tabs.emplace(lv, std::move(t)).first;
+        // the kernels read modulus indices from the ModDown table: check
+        // where they sit before the table goes to the device
+        const size_t idx = first + (size_t)2 * K + (size_t)3 * lv * K + (size_t)4 * lv;
+        bool ok = t.size() >= idx + lv + K;
+        for (int i = 0; ok && i < lv; i++) ok = t[idx + i] == (u64)i;
+        for (int k = 0; ok && k < K; k++) ok = t[idx + lv + k] == (u64)(c->L + k);
+        if (!ok) return set_err(c, HEGMM_EINVAL, "rotate_noalloc: ModDown table layout mismatch");
+        tit = c->noalloc_tabs.emplace(lv, std::make_pair(first, std::move(t))).first;
     }
-    const std::vector<u64> &tabs = tit->second;
-    const size_t n_mu = (size_t)nd * a * 2 + (size_t)nd * a * ne * 3;  // ModUp table words
+    const size_t n_mu = tit->second.first;  // words of the ModUp table (with its extension)
+    const std::vector<u64> &tabs = tit->second.second;
     std::vector<u64> hdr(16, 0);
     RotDesc rd{D, kit->second, u, nullptr, nullptr, (u32)g, 0u};
     DivDesc dd[2];

@@ -13,6 +13,41 @@ static inline int imod(long long a, int b) {
     return (int)(r < 0 ? r + b : r);
 }
 
+// Non-adjacent form of v: signed digits, least significant first, as the
+// signed powers of two themselves.  An odd v takes the digit +1 when
+// v = 1 mod 4 and -1 when v = 3 mod 4, so that v - digit is a multiple of 4.
+static std::vector<long long> naf_steps(long long v) {
+    std::vector<long long> out;
+    long long pw = 1;
+    while (v != 0) {
+        if (v & 1) {
+            const long long r = ((v % 4) + 4) % 4;
+            const long long d = r == 1 ? 1 : -1;
+            out.push_back(d * pw);
+            v -= d;
+        }
+        v /= 2;  // exact: v is even here
+        pw *= 2;
+    }
+    return out;
+}
+
+std::vector<int> pow2_steps(long long z, int S) {
+    const long long a = ((z % S) + S) % S;
+    std::vector<long long> fa = naf_steps(a), fb = naf_steps(a - S);
+    const std::vector<long long> &best = fb.size() < fa.size() ? fb : fa;
+    return std::vector<int>(best.begin(), best.end());
+}
+
+std::vector<int> pow2_offsets(int S) {
+    std::set<int> out;
+    for (long long p = 1; p < S; p *= 2) {
+        out.insert((int)(p % S));
+        out.insert((int)(((-p) % S + S) % S));
+    }
+    return std::vector<int>(out.begin(), out.end());
+}
+
 int alg1_length(int m, int l, int n) { return std::max(m * l, std::max(l * n, m * n)); }
 int alg1x_length(int m, int l, int n) { return std::max(m * (l + n - 1), l * n); }
 
@@ -387,6 +422,13 @@ int hegmm_plan_result_layout(int m, int l, int n, int alg, int slots, int *rows_
     result_layout(m, l, n, a, rows_cols_col[0], rows_cols_col[1], col);
     rows_cols_col[2] = col ? 1 : 0;
     return HEGMM_OK;
+}
+
+int hegmm_plan_pow2_steps(long long z, int slots, int *buf, int cap) {
+    if (slots <= 0 || (cap > 0 && !buf)) return HEGMM_EINVAL;
+    const std::vector<int> v = pow2_steps(z, slots);
+    for (int i = 0; i < cap && i < (int)v.size(); i++) buf[i] = v[i];
+    return (int)v.size();
 }
 
 int hegmm_plan_layout(int m, int l, int n, int alg, int slots, int role, const int64_t *mat, uint64_t t, uint64_t *out,

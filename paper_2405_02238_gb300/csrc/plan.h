@@ -70,6 +70,15 @@ std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &
 // The factorisation of operand s (0: eps / A, 1: omega / B) of a plan.
 std::vector<GiantLT> giant_factor_of(const HostPlan &P, int s, int S, int cost = GIANT_COST);
 
+// Power-of-two key policy: a left rotation by z over S slots as a chain of
+// rotations by signed powers of two, least significant first: the
+// non-adjacent form of z mod S or of (z mod S) - S (the same rotation),
+// whichever has fewer digits (ties: the non-negative one).  Empty for
+// z = 0 mod S.  pow2_offsets: every step the policy uses (+-2^i, 2^i < S),
+// as offsets in [0, S).
+std::vector<int> pow2_steps(long long z, int S);
+std::vector<int> pow2_offsets(int S);
+
 // Number of slots Algorithm 1 / 2 needs for (m, l, n).
 int alg1_length(int m, int l, int n);
 int alg2_length(int m, int l, int n);

@@ -229,7 +229,7 @@ int hegmm_server_submit(hegmm_server *s, const hegmm_ct *A, const hegmm_ct *B, i
                         uint64_t *ticket) {
     if (!s || !A || !B || !ticket) return HEGMM_EINVAL;
     Ctx *c = s->c;
-    if (alg < 0 || alg > 2) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1 or 2");
+    if (alg < 0 || alg > 3) return set_err(c, HEGMM_EINVAL, "algorithm must be 0 (auto), 1, 2 or 3");
     const int a = resolve_alg(m, l, n, alg, c->S);
     if (!a) return set_err(c, HEGMM_ESHAPE, "shape does not fit one slot row");
     if (A->level != c->L || B->level != c->L) return set_err(c, HEGMM_EINVAL, "operand level does not match");

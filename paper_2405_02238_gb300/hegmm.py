@@ -20,10 +20,11 @@ HEGMM_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ESHAPE", -4: "ENOKEY", -5: "ECUDA", -6: "ETIMEOUT"}
 ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
-ALG_1X = 3  # Algorithm 1 with the extended pre-layout (planner / encoding only in this version)
+ALG_1X = 3  # Algorithm 1 with the extended pre-layout (not in the paper; AUTO never picks it)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_ONE = 1, 2, 3, 4, 5, 6
 TUNE_WAIT_LIMIT, TUNE_TEST_DROP = 7, 8
 ROLE_A, ROLE_B = 0, 1
+KEYS_DIRECT, KEYS_POW2 = 0, 1  # hegmm_set_key_policy
 
 
 class HegmmError(RuntimeError):
@@ -111,6 +112,8 @@ _SIGS = {
     "hegmm_rotate_many": (ctypes.c_int, [vp, vp, intp, ctypes.c_int, ctypes.POINTER(vp)]),
     "hegmm_rotate_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, vp]),
     "hegmm_device_memory": (ctypes.c_int, [vp, ctypes.c_int, u64p]),
+    "hegmm_set_key_policy": (ctypes.c_int, [vp, ctypes.c_int]),
+    "hegmm_plan_pow2_steps": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, intp, ctypes.c_int]),
     "hegmm_cmult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_add": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
     "hegmm_mult": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(vp)]),
@@ -192,6 +195,16 @@ def hegmm_plan_describe(m: int, l: int, n: int, alg: int, slots: int) -> List[in
     buf = (ctypes.c_int * need)()
     lib.hegmm_plan_describe(m, l, n, alg, slots, buf, need)
     return list(buf)
+
+
+def hegmm_plan_pow2_steps(z: int, slots: int) -> List[int]:
+    lib = load()
+    need = lib.hegmm_plan_pow2_steps(z, slots, None, 0)
+    if need < 0:
+        raise HegmmError(need, "plan_pow2_steps")
+    buf = (ctypes.c_int * max(need, 1))()
+    lib.hegmm_plan_pow2_steps(z, slots, buf, need)
+    return list(buf)[:need]
 
 
 def hegmm_plan_giant(m: int, l: int, n: int, alg: int, slots: int, role: int, cost: int = 0) -> List[int]:
@@ -568,6 +581,9 @@ class Context:
 
     def hegmm_kernel_reset(self):
         self._check(self.lib.hegmm_kernel_reset(self.h), "kernel_reset")
+
+    def hegmm_set_key_policy(self, policy: int):
+        self._check(self.lib.hegmm_set_key_policy(self.h, policy), "set_key_policy")
 
     def hegmm_device_memory(self, reset_high: bool = False) -> dict:
         """{pool_used, pool_used_high, pool_reserved, device_free} in bytes."""

@@ -177,3 +177,9 @@ def test_context_refuses_more_modup_limbs_than_a_limb_pattern_holds(H):
     h = ctypes.c_void_p()
     rc = lib.hegmm_ctx_create(ctypes.byref(prm), ctypes.c_void_p(0), ctypes.byref(h))
     assert rc == -1 and not h.value
+
+
+def test_host_pow2_steps_match_oracle(H):
+    for S in (8, 64, 2048, 4096, 8192):
+        for z in list(range(-40, 300)) + [S - 1, S // 2, 3 * S // 4 + 1, S + 5]:
+            assert H.hegmm_plan_pow2_steps(z, S) == SL.pow2_steps(z, S), (S, z)
