@@ -1,0 +1,174 @@
+"""GPU parity of the products the benchmark times, and of Algorithm 1 with
+the extended pre-layout (HEGMM_ALG_1X), bit for bit against the oracle.
+
+The benchmark runs the medium products (16x32x24, 32x8x48) and the
+paper-scale products (64x64x64, 32x128x16, 128x16x64) in the
+double-hoisting + lazy-relinearisation + shared-baby-step order with the
+kernel knobs the autotuner picks.  The oracle needs minutes for the larger
+of these, so their expected ciphertexts are stored as digests written by
+tests/golden/make_product_digests.py (which runs the oracle only): the test
+computes the same product on the GPU from the same seeds, under several
+settings of the bit-neutral knobs, and compares the SHA-256 of the exported
+ciphertext and 64 sampled coefficients with the stored ones.  Smaller
+extended-pre-layout products are compared with the oracle run live, element
+by element.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workload as W
+from oracle import he as OH
+from oracle import slots as SL
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DIGEST_FILE = os.path.join(ROOT, "tests", "golden", "product_digests.json")
+# the cases tests/golden/make_product_digests.py writes: (preset, m, l, n, alg)
+CASES = [("medium", 16, 32, 24, 1), ("medium", 32, 8, 48, 1), ("medium", 16, 32, 24, 3), ("medium", 32, 8, 48, 3),
+         ("paper", 64, 64, 64, 0), ("paper", 128, 16, 64, 0), ("paper", 32, 128, 16, 0), ("paper", 64, 64, 64, 3),
+         ("paper", 32, 128, 16, 3)]
+KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
+BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
+# (LT kernel variant, entries per item, one-output kernel): the autotuner's
+# usual choice, the library default, and a plain-load variant
+KNOBS = [(7, 32, 0), (6, 32, 0), (0, 64, 2)]
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2405_02238_gb300 import build as B
+
+    B.build()
+    from paper_2405_02238_gb300 import hegmm
+
+    return hegmm
+
+
+_ctx = {}
+
+
+def context(H, name):
+    if name not in _ctx:
+        c = H.Context.from_preset(W.PRESETS[name])
+        c.hegmm_keygen(KEY_SEED)
+        _ctx[name] = c
+    return _ctx[name]
+
+
+def set_knobs(H, ctx, knobs):
+    v, ch, one = knobs
+    ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, v)
+    ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, ch)
+    ctx.hegmm_set_tuning(H.TUNE_LT_ONE, one)
+
+
+def gpu_product(H, name, m, l, n, alg, mode=BENCH_MODE):
+    pre = W.PRESETS[name]
+    ctx = context(H, name)
+    ctx.hegmm_set_keyswitch_mode(mode)
+    rng = W.PAPER_RANGE if name == "paper" else (W.MEDIUM_RANGE if name == "medium" else W.TINY_RANGE)
+    A, B = W.matrices(m, l, n, *rng, seed=0)
+    ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], alg)
+    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), ENC_SEED, STREAMS[0])
+    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, alg), ENC_SEED, STREAMS[1])
+    cc, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, alg)
+    got = ctx.hegmm_decrypt(cc, m, l, n, alg).astype(np.int64)
+    assert (got == (A @ B) % pre.t).all()
+    return ctx, cc, cnt, (A, B)
+
+
+@pytest.mark.parametrize("case_args", CASES)
+def test_benchmarked_products_match_the_oracle_digests(H, case_args):
+    name, m, l, n, alg = case_args
+    key = "%s %dx%dx%d alg %d double+lazy+shared" % case_args
+    case = json.load(open(DIGEST_FILE))["cases"][key]
+    knob_sets = KNOBS if name == "medium" else KNOBS[:2]
+    try:
+        for knobs in knob_sets:
+            ctx = context(H, name)
+            set_knobs(H, ctx, knobs)
+            ctx, cc, cnt, _ = gpu_product(H, name, m, l, n, alg)
+            ct = np.ascontiguousarray(ctx.hegmm_ct_export(cc), dtype="<u8")
+            assert list(ct.shape) == case["shape"]
+            flat = ct.reshape(-1)
+            for i, v in case["samples"]:
+                assert int(flat[i]) == v, (key, knobs, i)
+            assert hashlib.sha256(ct.tobytes()).hexdigest() == case["sha256"], (key, knobs)
+    finally:
+        set_knobs(H, context(H, name), (6, 32, 0))
+
+
+MODES = {"single": (0, "single", False, False), "double": (1, "double", False, False),
+         "single+shared": (4, "single", False, True), "double+lazy+shared": (7, "double", True, True)}
+
+
+def live(H, name, m, l, n, mode, seed=0):
+    """The extended pre-layout product on the GPU and in the oracle, element by element."""
+    flags, base, lazy, shared = MODES[mode]
+    pre = W.PRESETS[name]
+    ctx = context(H, name)
+    ctx.hegmm_set_keyswitch_mode(flags)
+    rng = W.MEDIUM_RANGE if name == "medium" else W.TINY_RANGE
+    A, B = W.matrices(m, l, n, *rng, seed=seed)
+    ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], H.ALG_1X)
+    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, H.ALG_1X), ENC_SEED, STREAMS[0])
+    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, H.ALG_1X), ENC_SEED, STREAMS[1])
+    cc, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, H.ALG_1X)
+    assert (ctx.hegmm_decrypt(cc, m, l, n, H.ALG_1X).astype(np.int64) == (A @ B) % pre.t).all()
+    o = OH.Oracle(pre)
+    o.keygen(KEY_SEED)
+    plan = SL.make_plan(m, l, n, 3)
+    ex = OH.HEGMM(o, mode=base, lazy_relin=lazy, giant=shared)
+    ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=ENC_SEED, streams=STREAMS)
+    assert (ctx.hegmm_ct_export(ca) == ctA).all()
+    assert (ctx.hegmm_ct_export(cc) == ex.run(plan, ctA, ctB)).all()
+    pc = plan.counts()
+    assert cnt["rot"] == pc["rot"] and cnt["mult"] == pc["mult"] and cnt["cmult"] == pc["cmult"]
+    return cnt
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("shape", [(4, 8, 6), (3, 2, 5), (1, 1, 1), (5, 12, 7), (7, 3, 9)])
+def test_extended_prelayout_tiny_bitexact(H, shape, mode):
+    live(H, "tiny", *shape, mode, seed=sum(shape))
+
+
+@pytest.mark.parametrize("mode", ["single+shared", "double+lazy+shared"])
+def test_extended_prelayout_medium_bitexact(H, mode):
+    live(H, "medium", 6, 10, 9, mode)
+
+
+def test_extended_prelayout_takes_fewer_key_switches(H):
+    # one rotation per eps^k: fewer executed key switches than Algorithm 1
+    ctx = context(H, "medium")
+    for (m, l, n) in W.MEDIUM_SHAPES:
+        c1 = H.hegmm_plan_counts(m, l, n, 1, ctx.S)
+        c3 = H.hegmm_plan_counts(m, l, n, 3, ctx.S)
+        assert c3["rot"] < c1["rot"] and c3["ksw"] < c1["ksw"]
+
+
+def test_extended_prelayout_in_a_mixed_batch(H):
+    # products of Algorithms 1, 2 and the extended pre-layout share a batch;
+    # each result is the one it has alone
+    ctx = context(H, "tiny")
+    ctx.hegmm_set_keyswitch_mode(BENCH_MODE)
+    shapes = [(4, 8, 6), (4, 8, 6), (3, 5, 2), (5, 4, 7)]
+    algs = [3, 1, 2, 3]
+    As, Bs, mats = [], [], []
+    for i, ((m, l, n), a) in enumerate(zip(shapes, algs)):
+        ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], a)
+        A, B = W.matrices(m, l, n, 0, 15, seed=i)
+        mats.append((A, B))
+        As.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, a), 21, 2 * i))
+        Bs.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, a), 21, 2 * i + 1))
+    outs = ctx.hegmm_matmul_batch_algs(As, Bs, shapes, algs)
+    for i, ((m, l, n), a) in enumerate(zip(shapes, algs)):
+        single, _ = ctx.hegmm_matmul(As[i], Bs[i], m, l, n, a)
+        assert (ctx.hegmm_ct_export(outs[i]) == ctx.hegmm_ct_export(single)).all()
+        A, B = mats[i]
+        assert (ctx.hegmm_decrypt(outs[i], m, l, n, a).astype(np.int64) == (A @ B) % 65537).all()
