@@ -258,7 +258,10 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     memory by bulk asynchronous copies (TMA engine, double-buffered with
  *     mbarriers), 2 CTAs per SM, for dnum <= 8 (else variant 0); 7 = the
  *     same with a producer warp and full / empty mbarriers over 3 stages
- *     instead of a block barrier per entry.
+ *     instead of a block barrier per entry; 8 = the form of 7 as one
+ *     persistent launch (two CTAs per SM) that walks the flattened queue of
+ *     every (work item, limb, 256-coefficient slice) unit, items of one
+ *     output included (HEGMM_TUNE_LT_ONE then has no effect).
  *   HEGMM_TUNE_LT_ONE: kernel of the items of one output: 0 (default) plain
  *     loads, 6 CTAs per SM (40 registers); 1 = key rows and masks staged by
  *     bulk asynchronous copies, 3 CTAs per SM (only with variants 6 and 7,
@@ -288,6 +291,13 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     touched; the GPU and the context stay usable. */
 #define HEGMM_TUNE_WAIT_LIMIT 7
 #define HEGMM_TUNE_TEST_DROP 8
+/*   HEGMM_TUNE_NTT_THREADS: threads of each CTA of the NTT-family kernels
+ *     (one CTA per limb): 0 (default) picks by launch size (1024 at
+ *     N = 2^14; at N = 2^13 512, or 1024 when a launch has no more CTAs than
+ *     SMs), 512 or 1024 force that form where the ring has it (N / 8 of at
+ *     least that many); at N = 2^14 the 512-thread form has 128 registers a
+ *     thread instead of 64. */
+#define HEGMM_TUNE_NTT_THREADS 9
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in
@@ -365,15 +375,18 @@ int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows
 
 /* Autotuner of the bit-neutral tuning knobs: runs the given products (as
  * hegmm_matmul_batch_algs would) under every candidate (kernel variant 0, 3,
- * 6, 7; entries per item 16, 32, 64; one-output kernel 0, and 1 with
+ * 6, 7, 8; entries per item 16, 32, 64; one-output kernel 0, and 1 with
  * variants 6 / 7), then, from the fastest, the one-output kernels 2 and 3;
  * each candidate is timed over reps calls with CUDA events on the context
  * stream after a plan-building and a graph-capturing call, and the fastest
- * is kept in the context.  chosen (may be NULL) receives {kernel variant,
- * entries per item, one-output kernel}.  Results stay bit for bit the same (every
- * candidate is an execution order of the same sums).  Only the
- * HEGMM_KS_DOUBLE kernels have knobs; in single mode it returns at once.
- * Cached product plans are released (they are rebuilt on the next call). */
+ * is kept in the context; then, with the fastest of those, the NTT-family
+ * thread counts (HEGMM_TUNE_NTT_THREADS 0, 512, 1024, on rings where both
+ * forms exist).  chosen (may be NULL, else 4 ints) receives {kernel
+ * variant, entries per item, one-output kernel, NTT threads}.  Results stay
+ * bit for bit the same (every candidate is an execution order of the same
+ * sums).  The linear-transformation knobs only steer the HEGMM_KS_DOUBLE
+ * kernels; in single mode only the NTT threads are tuned.  Cached product
+ * plans are released (they are rebuilt on the next call). */
 int hegmm_autotune(hegmm_ctx *ctx, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
                    const int *algs, int reps, int *chosen);
 

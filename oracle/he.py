@@ -74,6 +74,8 @@ def lib():
         L.or_gen_evk.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, i64p, u64p, u64p]
         L.or_encrypt.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, i64p, i64p, u64p]
         L.or_decrypt_residues.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, u64p, u64p]
+        L.or_encrypt_scaled.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, i64p, i64p, u64p, u64p]
+        L.or_set_error_factor.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
         L.or_automorph.argtypes = [ctypes.c_void_p, ctypes.c_int, intp, u64p, ctypes.c_uint64, u64p]
         L.or_automorph_int.argtypes = [ctypes.c_void_p, i64p, ctypes.c_uint64, i64p]
         L.or_modup.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, u64p]
@@ -436,6 +438,151 @@ class Oracle:
 # --------------------------------------------------------------------------
 
 
+class OracleBFV(Oracle):
+    """The BFV variant (the paper's own scheme, Section 4.1: Pyfhel's BFV):
+    the same ring, keys, key switching and slot encoding, with the message
+    scaled instead of the noise:
+
+    * encryption c0 = -a s + e + Delta m, c1 = a, Delta = floor(Q / t);
+      decryption m = round(t [c0 + c1 s]_Q / Q) mod t (exact, big integers);
+    * switching keys b_j = -a_j s + e_j + [P]_{q_i} s' (no factor t) and a
+      ModDown with plain centred rounding: the BGV operations of the C
+      oracle with its error factor set to 1;
+    * HE-Mult: the tensor of the centred lifts of both operands over Z,
+      (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1), scaled by t / Q and
+      rounded to the nearest integer (never a tie: Q is odd), reduced mod
+      Q, then d2 relinearised with the relinearisation key.  The exact
+      tensor is computed modulo enough auxiliary NTT primes and put together
+      by the Chinese remainder theorem (an exact product by multi-modular
+      arithmetic).
+    """
+
+    bfv = True
+
+    def __init__(self, preset):
+        super().__init__(preset)
+        if preset.ms_drop:
+            raise ValueError("the BFV variant has no modulus switch")
+        lib().or_set_error_factor(self.ctx, 1)
+        self.Q = 1
+        for q in self.primes[: self.L]:
+            self.Q *= q
+        self.delta = self.Q // self.t
+        self.delta_res = np.array([self.delta % q for q in self.primes[: self.L]], dtype=np.uint64)
+        # auxiliary primes for exact products: their product exceeds
+        # 2 (N Q^2 / 2) + margin, the bound of a lazy sum of up to 2^12 tensors
+        need = self.pre.logN + 2 * self.Q.bit_length() + 16
+        naux = -(-need // 59)
+        self.aux = lib().or_new(self.pre.logN, self.t, naux, 60, 1, 1, self.pre.eta)
+        if not self.aux:
+            raise RuntimeError("oracle: no auxiliary primes")
+        pr = np.zeros(naux + 1, dtype=np.uint64)
+        lib().or_get_primes(self.aux, P(pr))
+        self.aux_primes = [int(x) for x in pr[:naux]]
+        self.aux_M = 1
+        for p in self.aux_primes:
+            self.aux_M *= p
+
+    def __del__(self):
+        try:
+            if getattr(self, "aux", None):
+                lib().or_free(self.aux)
+        except Exception:
+            pass
+        super().__del__()
+
+    def encrypt(self, m: np.ndarray, seed: int, stream: int) -> np.ndarray:
+        ct = np.zeros((2, self.L, self.N), dtype=np.uint64)
+        mm = np.ascontiguousarray(m, dtype=np.int64)
+        lib().or_encrypt_scaled(self.ctx, seed, stream, PI(self.sk), PI(mm), P(self.delta_res), P(ct))
+        return ct
+
+    def _centred(self, res: np.ndarray) -> np.ndarray:
+        """Residues [lv][N] over q_0..q_{lv-1} -> centred integers (object)."""
+        lv = res.shape[0]
+        Q = 1
+        for i in range(lv):
+            Q *= self.primes[i]
+        acc = np.zeros(self.N, dtype=object)
+        for i in range(lv):
+            qi = self.primes[i]
+            Qi = Q // qi
+            acc = acc + res[i].astype(object) * (Qi * pow(Qi % qi, -1, qi))
+        acc = acc % Q
+        return np.where(acc > Q // 2, acc - Q, acc)
+
+    def decrypt(self, ct: np.ndarray, lv: Optional[int] = None):
+        """Returns (plaintext coefficients mod t, noise bits, budget bits):
+        m = round(t v / Q) mod t for v = [c0 + c1 s]_Q centred; the noise is
+        v - Delta m' (m' = round(t v / Q)), the budget log2(Q / (2 t))."""
+        lv = ct.shape[1] if lv is None else lv
+        v = np.zeros((lv, self.N), dtype=np.uint64)
+        lib().or_decrypt_residues(self.ctx, lv, PI(self.sk), P(np.ascontiguousarray(ct)), P(v))
+        vc = self._centred(v)
+        Q = self.Q
+        mr = [(2 * self.t * int(x) + Q) // (2 * Q) for x in vc]
+        noise = max(abs(int(x) - self.delta * r) for x, r in zip(vc, mr))
+        m = np.array([r % self.t for r in mr], dtype=np.int64)
+        return m, (math.log2(noise) if noise > 0 else 0.0), math.log2(Q / (2 * self.t))
+
+    def tensor_exact(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """(a0 b0, a0 b1 + a1 b0, a1 b1) over Z of the centred lifts of two
+        ciphertexts, exact: computed modulo the auxiliary primes (negacyclic
+        NTT products) and recombined by CRT; object array [3][N]."""
+        ac = [self._centred(np.ascontiguousarray(a[i])) for i in range(2)]
+        bc = [self._centred(np.ascontiguousarray(b[i])) for i in range(2)]
+        res = np.zeros((3, len(self.aux_primes), self.N), dtype=np.uint64)
+        for j, p in enumerate(self.aux_primes):
+            ar = [(x % p).astype(np.uint64) for x in ac]
+            br = [(x % p).astype(np.uint64) for x in bc]
+            prod = {}
+            for (u, v) in ((0, 0), (0, 1), (1, 0), (1, 1)):
+                o = np.zeros(self.N, dtype=np.uint64)
+                lib().or_polymul(self.aux, j, P(ar[u]), P(br[v]), P(o))
+                prod[(u, v)] = o.astype(object)
+            res[0, j] = (prod[(0, 0)] % p).astype(np.uint64)
+            res[1, j] = ((prod[(0, 1)] + prod[(1, 0)]) % p).astype(np.uint64)
+            res[2, j] = (prod[(1, 1)] % p).astype(np.uint64)
+        M = self.aux_M
+        out = np.zeros((3, self.N), dtype=object)
+        for k in range(3):
+            acc = np.zeros(self.N, dtype=object)
+            for j, p in enumerate(self.aux_primes):
+                Mj = M // p
+                acc = acc + res[k, j].astype(object) * (Mj * pow(Mj % p, -1, p))
+            acc = acc % M
+            out[k] = np.where(acc > M // 2, acc - M, acc)
+        return out
+
+    def scale_round(self, d: np.ndarray) -> np.ndarray:
+        """round(t d / Q) of exact integers d [3][N], as residues [3][L][N]."""
+        Q, t = self.Q, self.t
+        out = np.zeros((d.shape[0], self.L, self.N), dtype=np.uint64)
+        for k in range(d.shape[0]):
+            z = np.array([(2 * t * int(x) + Q) // (2 * Q) for x in d[k]], dtype=object)
+            for i in range(self.L):
+                out[k, i] = (z % self.primes[i]).astype(np.uint64)
+        return out
+
+    def tensor(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        """HE-Mult before relinearisation: the scaled, rounded tensor."""
+        return self.scale_round(self.tensor_exact(a, b))
+
+    def mult_relin(self, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+        d = self.tensor(a, b)
+        ks = self.keyswitch(d[2], 0)
+        self.counts["mult"] = self.counts.get("mult", 0) + 1
+        return self.add(np.ascontiguousarray(d[:2]), ks)
+
+    def modswitch(self, ct: np.ndarray) -> np.ndarray:
+        raise ValueError("the BFV variant has no modulus switch")
+
+
+def make_oracle(preset) -> Oracle:
+    """The oracle of a preset's scheme (BGV, or the BFV variant)."""
+    return OracleBFV(preset) if getattr(preset, "scheme", 0) == 1 else Oracle(preset)
+
+
 def mask_scale(o: Oracle) -> int:
     """Mask entry value: 1, or [q_drop]_t when the product level drops primes.
 
@@ -606,6 +753,11 @@ class HEGMM:
                 a = o.modswitch(a)
                 b = o.modswitch(b)
             if self.lazy_relin:
+                if getattr(o, "bfv", False):
+                    # BFV: the exact tensors are summed and scaled once
+                    d = o.tensor_exact(a, b)
+                    dsum = d if dsum is None else dsum + d
+                    continue
                 d = o.tensor(a, b)
                 dsum = d if dsum is None else o.add(dsum, d)
                 continue
@@ -619,6 +771,8 @@ class HEGMM:
             prod = o.mult_relin(a, b)
             C = prod if C is None else o.add(C, prod)
         if self.lazy_relin:
+            if getattr(o, "bfv", False):
+                dsum = o.scale_round(dsum)
             # one relinearisation of the summed tensor (Eq. elementwise's
             # sum taken before the key switch)
             if self.mode == "double":

@@ -144,6 +144,7 @@ enum { DOM_SK = 1, DOM_KEY_A = 2, DOM_KEY_E = 3, DOM_ENC_A = 4, DOM_ENC_E = 5 };
 typedef struct {
     int logN, N, L, K, alpha, eta;
     u64 t;
+    u64 te;          /* factor of every error term and of the rounding correction: t (BGV), 1 (BFV) */
     u64 prime[MAXP]; /* q_0 .. q_{L-1}, p_0 .. p_{K-1} */
     u64 psi[MAXP];   /* a primitive 2N-th root of unity mod each prime */
     u64 psi_t;       /* zeta = 3^((t-1)/2N) mod t */
@@ -169,6 +170,7 @@ or_ctx *or_new(int logN, u64 t, int L, int qbits, int K, int alpha, int eta) {
     c->alpha = alpha;
     c->eta = eta;
     c->t = t;
+    c->te = t;
     if (or_find_primes(logN, qbits, L + K, c->prime) != L + K) { free(c); return 0; }
     for (int i = 0; i < L + K; i++) c->psi[i] = find_psi(c->prime[i], c->N);
     c->psi_t = powmod(3, (t - 1) / (2 * (u64)c->N), t);
@@ -176,6 +178,10 @@ or_ctx *or_new(int logN, u64 t, int L, int qbits, int K, int alpha, int eta) {
 }
 
 void or_free(or_ctx *c) { free(c); }
+
+/* The scheme's error factor: t for BGV (errors t e, ModDown and modulus
+ * switch rounding corrected by t), 1 for BFV (errors e, plain rounding). */
+void or_set_error_factor(or_ctx *c, u64 te) { c->te = te; }
 void or_get_primes(const or_ctx *c, u64 *out) { memcpy(out, c->prime, sizeof(u64) * (c->L + c->K)); }
 u64 or_get_psi(const or_ctx *c, int pi) { return pi < 0 ? c->psi_t : c->psi[pi]; }
 
@@ -295,7 +301,7 @@ void or_gen_evk(const or_ctx *c, u64 seed, u64 gtag, const i64 *s, const u64 *sp
             for (int k = 0; k < K; k++) Pmod = mulmod(Pmod, c->prime[L + k] % q, q);
             int in_digit = pi < L && pi / c->alpha == j;
             for (int i = 0; i < N; i++) {
-                u64 v = submod(mulmod(c->t % q, smod(e[i], q), q), as[i], q);
+                u64 v = submod(mulmod(c->te % q, smod(e[i], q), q), as[i], q);
                 if (in_digit) v = addmod(v, mulmod(Pmod, sprime[(size_t)pi * N + i], q), q);
                 b[i] = v;
             }
@@ -321,7 +327,33 @@ void or_encrypt(const or_ctx *c, u64 seed, u64 stream_id, const i64 *s, const i6
         for (int i = 0; i < N; i++) sres[i] = smod(s[i], q);
         or_polymul(c, pi, c1, sres, as);
         for (int i = 0; i < N; i++) {
-            u64 v = addmod(mulmod(c->t % q, smod(e[i], q), q), smod(m[i], q), q);
+            u64 v = addmod(mulmod(c->te % q, smod(e[i], q), q), smod(m[i], q), q);
+            c0[i] = submod(v, as[i], q);
+        }
+    }
+    free(e);
+    free(sres);
+    free(as);
+}
+
+/* BFV secret-key encryption: c1 = a, c0 = -a s + e + Delta m over the L
+ * chain primes, Delta = floor(Q / t) given by its residues delta[L]; m holds
+ * the centred coefficients of the plaintext. */
+void or_encrypt_scaled(const or_ctx *c, u64 seed, u64 stream_id, const i64 *s, const i64 *m, const u64 *delta,
+                       u64 *ct) {
+    int N = c->N, L = c->L;
+    u64 sta = or_stream(seed, DOM_ENC_A, stream_id), ste = or_stream(seed, DOM_ENC_E, stream_id);
+    i64 *e = (i64 *)malloc(sizeof(i64) * N);
+    u64 *sres = (u64 *)malloc(sizeof(u64) * N), *as = (u64 *)malloc(sizeof(u64) * N);
+    for (int i = 0; i < N; i++) e[i] = cbd(or_draw(ste, (u64)i), c->eta);
+    for (int pi = 0; pi < L; pi++) {
+        u64 q = c->prime[pi];
+        u64 *c0 = ct + (size_t)pi * N, *c1 = ct + ((size_t)L + pi) * N;
+        for (int i = 0; i < N; i++) c1[i] = or_draw(sta, (u64)pi * N + i) % q;
+        for (int i = 0; i < N; i++) sres[i] = smod(s[i], q);
+        or_polymul(c, pi, c1, sres, as);
+        for (int i = 0; i < N; i++) {
+            u64 v = addmod(mulmod(c->te % q, smod(e[i], q), q), mulmod(delta[pi] % q, smod(m[i], q), q), q);
             c0[i] = submod(v, as[i], q);
         }
     }
@@ -448,7 +480,7 @@ static void divide_round_t(const or_ctx *c, int ne, int first, const int *pidx, 
         u64 q = c->prime[pidx[i]];
         u64 Dmod = 1;
         for (int k = 0; k < nd; k++) Dmod = mulmod(Dmod, c->prime[pidx[first + k]] % q, q);
-        u64 Dinv = invmod(Dmod, q), tq = c->t % q;
+        u64 Dinv = invmod(Dmod, q), tq = c->te % q;
         u64 *o = out + (size_t)i * N;
         for (int x = 0; x < N; x++) o[x] = 0;
         for (int k = 0; k < nd; k++) {
@@ -460,7 +492,7 @@ static void divide_round_t(const or_ctx *c, int ne, int first, const int *pidx, 
                     hat_dk = mulmod(hat_dk, d2 % dk, dk);
                     hat_q = mulmod(hat_q, d2 % q, q);
                 }
-            u64 coef = mulmod(invmod(c->t % dk, dk), invmod(hat_dk, dk), dk);
+            u64 coef = mulmod(invmod(c->te % dk, dk), invmod(hat_dk, dk), dk);
             const u64 *ud = in + (size_t)(first + k) * N;
             for (int x = 0; x < N; x++) {
                 u64 z = mulmod(ud[x], coef, dk);

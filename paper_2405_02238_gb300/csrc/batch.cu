@@ -141,6 +141,7 @@ struct BatchPlan {
     int fused = 0;  // double mode: every linear transformation in one k_lt_grp launch
     LtEntry *d_lents = nullptr;
     LtItem *d_litems[2] = {nullptr, nullptr};  // items of one output, items of several outputs
+    LtItem *d_litems_all = nullptr;             // both lists (several outputs first), for the persistent kernel
     int lt_nitems[2] = {0, 0};  // work items: outputs x at most lt_chunk entries
     double lt_bytes[2] = {0, 0};  // algorithmic bytes of each launch
     u64 *part = nullptr;    // partial sums of outputs split into several items
@@ -992,6 +993,12 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             return a0 != b0 ? a0 < b0 : key_of(a, 1) < key_of(b, 1);
         });
         P->ltsum_n = (int)sums.size();
+        if (c->lt_kernel == 8) {  // one persistent launch: the items of several outputs first
+            std::vector<LtItem> all(items[1]);
+            all.insert(all.end(), items[0].begin(), items[0].end());
+            P->d_litems_all = plan_upload(c, P, all);
+            if (!keep(P->d_litems_all)) return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        }
         P->d_lents = plan_upload(c, P, ents);
         for (int kind = 0; kind < 2; kind++) {
             P->lt_nitems[kind] = (int)items[kind].size();
@@ -1410,6 +1417,11 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
     if (P->pow2) {
         if ((rc = run_tree(c, P->optree))) return rc;
         if ((rc = lt_accumulate(c, lv0, lv0, lv0, 0, P->d_p2_terms, P->d_p2_off, P->d_p2_outs, P->O, 0))) return rc;
+    } else if (P->fused && P->d_litems_all) {
+        if ((rc = lt_group_persistent(c, lv0, P->d_lents, P->d_litems_all, P->lt_nitems[0] + P->lt_nitems[1],
+                                      P->lt_bytes[0] + P->lt_bytes[1])))
+            return rc;
+        if ((rc = sum_desc(c, lv0, P->d_ltsum, P->ltsum_n, np0))) return rc;
     } else if (P->fused) {
         if ((rc = lt_group(c, lv0, 1, P->d_lents, P->d_litems[0], P->lt_nitems[0], P->lt_bytes[0]))) return rc;
         if ((rc = lt_group(c, lv0, LT_GROUP, P->d_lents, P->d_litems[1], P->lt_nitems[1], P->lt_bytes[1]))) return rc;
@@ -1583,6 +1595,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(dbl ? c->lt_fused : 0);
     key.push_back(dbl ? c->lt_kernel : 0);  // launch choices are baked into a plan's graph
     key.push_back(dbl ? c->lt_one : 0);
+    key.push_back(c->ntt_threads);
     key.push_back(c->wait_limit);  // kernel arguments captured in the graph
     key.push_back(c->test_drop_entry);
     key.push_back(c->key_pow2);
@@ -1887,16 +1900,16 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (!h || count <= 0 || !A || !B || !mln) return HEGMM_EINVAL;
     Ctx *c = &h->c;
     if (reps < 1) reps = 3;
-    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one;
+    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one, nt0 = c->ntt_threads;
     auto report = [&]() {
         if (chosen) {
             chosen[0] = c->lt_kernel;
             chosen[1] = c->lt_chunk;
             chosen[2] = c->lt_one;
+            chosen[3] = c->ntt_threads;
         }
         return HEGMM_OK;
     };
-    if (!c->ks_double) return report();  // the knobs only steer the double-hoisted kernels
     const bool timing = c->timing;
     c->timing = false;
     std::vector<hegmm_ct *> C((size_t)count, nullptr);
@@ -1914,12 +1927,13 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bk = k0, bc = ch0, bs = s0, rc = HEGMM_OK;
+    int bk = k0, bc = ch0, bs = s0, bn = nt0, rc = HEGMM_OK;
     // times one candidate; false when a run failed (rc holds the error)
-    auto trial = [&](int kv, int chunk, int one) {
+    auto trial = [&](int kv, int chunk, int one, int nt) {
         c->lt_kernel = kv;
         c->lt_chunk = chunk;
         c->lt_one = one;
+        c->ntt_threads = nt;
         for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
         if (rc) return false;
         cudaEventRecord(e0, c->st);
@@ -1933,21 +1947,28 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
             bk = kv;
             bc = chunk;
             bs = one;
+            bn = nt;
         }
         drop_plans();
         return true;
     };
     bool ok = true;
-    for (int kv : {0, 3, 6, 7})
-        for (int chunk : {16, 32, 64})
-            for (int one : {0, 1}) {
-                if (one && kv < 6) continue;  // staging one-output items only exists with variants 6 and 7
-                if (ok) ok = trial(kv, chunk, one);
-            }
-    // the plain one-output kernel at lower occupancy, with the best of the rest
-    if (ok && bs == 0)
-        for (int one : {2, 3})
-            if (ok) ok = trial(bk, bc, one);
+    if (c->ks_double) {  // the linear-transformation knobs only steer the double-hoisted kernels
+        for (int kv : {0, 3, 6, 7, 8})
+            for (int chunk : {16, 32, 64})
+                for (int one : {0, 1}) {
+                    if (one && (kv < 6 || kv == 8)) continue;  // staged one-output kernel: variants 6 and 7 only
+                    if (ok) ok = trial(kv, chunk, one, nt0);
+                }
+        // the plain one-output kernel at lower occupancy, with the best of the rest
+        if (ok && bs == 0 && bk != 8)
+            for (int one : {2, 3})
+                if (ok) ok = trial(bk, bc, one, nt0);
+    }
+    // threads of the NTT-family CTAs (rings with N / 8 >= 1024 have two forms)
+    if (c->N / 8 >= 1024)
+        for (int nt : {0, 512, 1024})
+            if (ok && (nt != bn || best > 1e29f)) ok = trial(bk, bc, bs, nt);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_plans();
@@ -1955,6 +1976,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     c->lt_kernel = rc ? k0 : bk;
     c->lt_chunk = rc ? ch0 : bc;
     c->lt_one = rc ? s0 : bs;
+    c->ntt_threads = rc ? nt0 : bn;
     if (rc) return rc;
     return report();
 }
@@ -1979,7 +2001,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_KERNEL) {
-        if (value < 0 || value > 7) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..7");
+        if (value < 0 || value > 8) return set_err(c, HEGMM_EINVAL, "lt_kernel must be in 0..8");
         c->lt_kernel = (int)value;
         return HEGMM_OK;
     }
@@ -2006,6 +2028,12 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_GRAPHS) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "graphs must be 0 or 1");
         c->use_graphs = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_NTT_THREADS) {
+        if (value != 0 && value != 512 && value != 1024)
+            return set_err(c, HEGMM_EINVAL, "ntt threads must be 0 (by launch size), 512 or 1024");
+        c->ntt_threads = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_FUSED) {

@@ -203,6 +203,7 @@ struct Ctx {
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
     int lt_kernel = 6;                         // grouped fused kernel variant (6: operands staged by TMA)
     int lt_one = 0;                            // one-output kernel: 0/2/3 plain loads at 6/5/4 CTAs per SM, 1 staged
+    int ntt_threads = 0;                       // threads of an NTT-family CTA: 0 = by launch size, 512 or 1024
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;
     size_t mask_budget = (size_t)96 << 30;     // resident plan masks (LRU beyond this)
@@ -291,6 +292,8 @@ int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n);
 // bytes: the algorithmic HBM bytes of the launch (keys, masks, outputs).
 // group: 1 for items of one output each, LT_GROUP otherwise.
 int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes);
+// The same for items of any output count in one persistent launch (variant 8).
+int lt_group_persistent(Ctx *c, int lv, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes);
 // out[poly] = sum_k in[k][poly] over nk inputs with stride in_stride words; npolylimbs = 2*lv
 int sum_cts(Ctx *c, int lv, const u64 *in, long long in_stride, int nk, u64 *out, int accumulate);
 // pointwise helpers over [npoly][lv][N]

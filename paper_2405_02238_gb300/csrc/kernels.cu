@@ -71,18 +71,26 @@ static inline dim3 grid_coef(int N, int y, int z) { return dim3((unsigned)((N + 
 // A launch of no more CTAs than SMs leaves every CTA an SM of its own; there
 // the NT_WIDE form (one radix-8 group per thread and pass, up to 1024
 // threads) halves the latency of each pass at N = 2^13.
+//
+// Every kernel exists in two thread counts, NT_A (up to 512) and NT_B (up to
+// 1024); HEGMM_TUNE_NTT_THREADS forces one of them (hegmm_autotune tries
+// both), else NT at N = 2^14 and the rule above below it.
 template <int LOGN>
 struct NttCfg {
     static constexpr int N = 1 << LOGN;
-    static constexpr int NT = LOGN >= 14 ? 1024 : ((N / 8) < 512 ? (N / 8) : 512);
-    static constexpr int NT_WIDE = (N / 8) < 1024 ? (N / 8) : 1024;
+    static constexpr int NT_A = (N / 8) < 512 ? (N / 8) : 512;
+    static constexpr int NT_B = (N / 8) < 1024 ? (N / 8) : 1024;
+    static constexpr int NT = LOGN >= 14 ? NT_B : NT_A;
+    static constexpr int NT_WIDE = NT_B;
     static constexpr size_t SMEM = (size_t)(N + N / 16) * 8;
 };
 
-// CTAs per SM the register budget is set for: two up to 512 threads.
-template <int NT>
+// CTAs per SM the register budget is set for: one for 1024 threads or when
+// the limb takes more than half of the SM's shared memory (N = 2^14: 512
+// threads then get 128 registers each), else two.
+template <int LOGN, int NT>
 struct NttMinBlocks {
-    static constexpr int V = NT >= 1024 ? 1 : 2;
+    static constexpr int V = (NT >= 1024 || 2 * NttCfg<LOGN>::SMEM > (size_t)227 * 1024) ? 1 : 2;
 };
 
 // Fused pass layout of the kernels below: the first radix-8 pass (stages
@@ -130,7 +138,7 @@ __device__ __forceinline__ const TwPair *tw_of(const TwPair *tw, int mi, int whi
 // {w, Shoup companion} pair per inner entry i of the pattern) when scale is
 // not null.
 template <int LOGN, bool INV, int NT>
-__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_ntt(LimbPat p, const ModDev *__restrict__ mods,
+__global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_ntt(LimbPat p, const ModDev *__restrict__ mods,
                                                                  const TwPair *__restrict__ tw,
                                                                  const TwPair *__restrict__ scale) {
     extern __shared__ u64 sm[];
@@ -206,7 +214,7 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_ntt(LimbPat p, cons
 // reducing Shoup product.  Table layout: build_div_tab; NARROW: every
 // dropped prime below twice every kept one (centred_narrow).
 template <int LOGN, int NT, bool NARROW>
-__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nkeep, int ndrop,
+__global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_divround_ntt(int nkeep, int ndrop,
                                                                           const ModDev *__restrict__ mods,
                                                                           const u64 *__restrict__ tab, int ext,
                                                                           const DivDesc *__restrict__ desc,
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_divround_ntt(int nk
 // selection follows a LimbPat whose off[] = j * ne + e.  NARROW: every
 // source prime below twice every target prime (centred_narrow).
 template <int LOGN, int NT, bool NARROW>
-__global__ void __launch_bounds__(NT, NttMinBlocks<NT>::V) k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha,
+__global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_modup_ntt(LimbPat p, int lv, int ne, int nd, int alpha,
                                                                        int L, const ModDev *__restrict__ mods,
                                                                        const u64 *__restrict__ tab, int ext,
                                                                        const u64 *__restrict__ xc, long long xc_stride,
@@ -355,7 +363,7 @@ static int set_smem_attrs_nt() {
 
 template <int LOGN>
 static int set_smem_attrs() {
-    return set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT>() || set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_WIDE>();
+    return set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_A>() || set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_B>();
 }
 
 static int init_staged_kernels();
@@ -385,21 +393,24 @@ int init_kernels(Ctx *c) {
         default: break;                     \
     }
 
-// Thread count of a launch of `ctas` limb CTAs (NttCfg: the wide form when
-// every CTA has an SM of its own).
+// Thread count of a launch of `ctas` limb CTAs: the tuned one when set,
+// else NttCfg's rule (the wide form when every CTA has an SM of its own).
+// True: NT_B, false: NT_A.
 template <int LG>
 static bool ntt_wide(const Ctx *c, long long ctas) {
+    if (c->ntt_threads && NttCfg<LG>::NT_B > NttCfg<LG>::NT_A) return c->ntt_threads >= NttCfg<LG>::NT_B;
+    if (NttCfg<LG>::NT == NttCfg<LG>::NT_B) return true;
     return NttCfg<LG>::NT_WIDE > NttCfg<LG>::NT && ctas <= c->nsm;
 }
 
 template <int LG, bool INV>
 static void launch_ntt(Ctx *c, const LimbPat &p, const TwPair *tw, const TwPair *scale) {
-    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr int NA = NttCfg<LG>::NT_A, NB = NttCfg<LG>::NT_B;
     constexpr size_t SM = NttCfg<LG>::SMEM;
     if (ntt_wide<LG>(c, p.count))
-        k_ntt<LG, INV, NW><<<p.count, NW, SM, c->st>>>(p, c->d_mods, tw, scale);
+        k_ntt<LG, INV, NB><<<p.count, NB, SM, c->st>>>(p, c->d_mods, tw, scale);
     else
-        k_ntt<LG, INV, NT><<<p.count, NT, SM, c->st>>>(p, c->d_mods, tw, scale);
+        k_ntt<LG, INV, NA><<<p.count, NA, SM, c->st>>>(p, c->d_mods, tw, scale);
 }
 
 int ntt_fwd(Ctx *c, const LimbPat &p) {
@@ -427,7 +438,7 @@ static void launch_divround_t(Ctx *c, int grid, const DivTab &tab, const DivDesc
 
 template <int LG>
 static void launch_divround(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
-    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr int NT = NttCfg<LG>::NT_A, NW = NttCfg<LG>::NT_B;
     const bool w = ntt_wide<LG>(c, grid);
     if (tab.narrow) {
         if (w) launch_divround_t<LG, NW, true>(c, grid, tab, d_desc, tw);
@@ -459,7 +470,7 @@ static void launch_modup_t(Ctx *c, const LimbPat &nonown, const ModUpTab &tb, co
 template <int LG>
 static void launch_modup(Ctx *c, const LimbPat &nonown, const ModUpTab &tb, const u64 *xc, long long xc_stride,
                          const TwPair *tw) {
-    constexpr int NT = NttCfg<LG>::NT, NW = NttCfg<LG>::NT_WIDE;
+    constexpr int NT = NttCfg<LG>::NT_A, NW = NttCfg<LG>::NT_B;
     const bool w = ntt_wide<LG>(c, nonown.count);
     if (tb.narrow) {
         if (w) launch_modup_t<LG, NW, true>(c, nonown, tb, xc, xc_stride, tw);
@@ -997,6 +1008,158 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_ws(int lv, int ne, int nd, in
     }
 }
 
+// Persistent form of k_lt_grp_ws: one launch of gridDim.x CTAs (a few per
+// SM) walks the flattened queue of every (item, limb, 256-coefficient slice)
+// work unit of the call, CTA b taking units b, b + gridDim.x, ... (limb
+// major, then item, then slice, the order of the one-launch-per-kind grid),
+// so the items of several outputs and of one output share a single launch
+// with no tail between them.  The producer warp keeps filling the S-stage
+// ring across units (stage = running entry count mod S), the consumers
+// zero their sums at each unit's start and write its outputs at its end.
+// Bounded waits as k_lt_grp_ws; `drop` leaves entry number `drop` of every
+// unit unarmed (a test of those waits).
+template <int G, int S>
+__global__ void __launch_bounds__(288, 2) k_lt_grp_pws(int lv, int ne, int nd, int np, int L, int logN,
+                                                     const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
+                                                     const LtItem *__restrict__ items, int nitems, int *err, int spin,
+                                                     int drop) {
+    extern __shared__ __align__(128) u64 tsm[];
+    const int N = 1 << logN, nsl = N >> 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long nunits = (long long)nitems * ne * nsl;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N;
+    const size_t sw = tma_stage_words(nd, G);
+    u64 *full = tsm + S * sw, *empty = full + S;
+    if (tid == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 8);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool bad = false;
+    if (warp == 8) {
+        if (lane == 0) {
+            long long cnt = 0, issued = 0;  // entries through the ring so far
+            for (long long w = blockIdx.x; w < nunits && !bad; w += gridDim.x) {
+                const int e = (int)(w / ((long long)nitems * nsl));
+                const long long rem = w - (long long)e * nitems * nsl;
+                const LtItem *it = items + rem / nsl;
+                const int c0 = (int)(rem % nsl) * 256;
+                const int gm = e < lv ? e : L + (e - lv);
+                const size_t moff = (size_t)gm * N + c0;
+                for (int i = 0; i < it->count; i++, cnt++) {
+                    const int s = (int)(cnt % S);
+                    if (cnt >= S && !mbar_wait_bounded(&empty[s], (u32)((cnt / S - 1) & 1), spin)) {
+                        bad = true;
+                        break;
+                    }
+                    issued = cnt + 1;
+                    if (i == drop) continue;  // left unarmed (a test of the bounded waits)
+                    const LtEntry *E = ents + it->first + i;
+                    u64 *st = tsm + s * sw;
+                    const bool live = E->key || e < lv;
+                    u32 bytes = 0;
+                    if (live) {
+                        if (E->key) bytes += 2u * nd * 2048u;
+#pragma unroll
+                        for (int j = 0; j < G; j++)
+                            if (E->mask[j]) bytes += 2048u;
+                    }
+                    fence_proxy_async();
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    if (live) {
+                        if (E->key)
+                            for (int r = 0; r < 2 * nd; r++)
+                                bulk_g2s(st + (size_t)r * 256, E->key + (size_t)r * kstep + moff, 2048u, &full[s]);
+#pragma unroll
+                        for (int j = 0; j < G; j++)
+                            if (E->mask[j]) bulk_g2s(st + (size_t)(2 * nd + j) * 256, E->mask[j] + moff, 2048u, &full[s]);
+                    }
+                }
+            }
+            // every issued copy lands before the CTA can leave
+            for (long long i = issued - S > 0 ? issued - S : 0; i < issued; i++)
+                if (!mbar_wait_bounded(&full[i % S], (u32)((i / S) & 1), spin)) bad = true;
+        }
+    } else {
+        long long cnt = 0;
+        for (long long w = blockIdx.x; w < nunits && !bad; w += gridDim.x) {
+            const int e = (int)(w / ((long long)nitems * nsl));
+            const long long rem = w - (long long)e * nitems * nsl;
+            const LtItem *it = items + rem / nsl;
+            const int c = (int)(rem % nsl) * 256 + tid;
+            const int gm = e < lv ? e : L + (e - lv);
+            const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
+            Acc s0[G], s1[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) s0[j] = s1[j] = Acc{0, 0};
+            for (int i = 0; i < it->count; i++, cnt++) {
+                const int s = (int)(cnt % S);
+                const LtEntry *E = ents + it->first + i;
+                const u64 *key = E->key;
+                const bool live = key || e < lv;
+                u64 xd[TMA_MAX_ND], x0 = 0, x1 = 0;
+                if (key) {
+                    const u32 src = auto_src((u32)c, E->g, logN);
+                    const u64 *Dp = E->D + (size_t)e * N + src;
+#pragma unroll
+                    for (int j = 0; j < TMA_MAX_ND; j++)
+                        if (j < nd) xd[j] = __ldg(Dp + (size_t)j * dstep);
+                    if (e < lv) x0 = __ldg(E->ct + (size_t)e * N + src);
+                } else if (e < lv) {
+                    x0 = __ldg(E->ct + (size_t)e * N + c);
+                    x1 = __ldg(E->ct + ((size_t)lv + e) * N + c);
+                }
+                if (!mbar_wait_bounded(&full[s], (u32)((cnt / S) & 1), spin)) {
+                    bad = true;
+                    break;
+                }
+                if (live) {
+                    const u64 *st = tsm + s * sw;
+                    u64 u0, u1;
+                    if (key) {
+                        Acc a0{0, 0}, a1{0, 0};
+                        if (e < lv) mac(a0, x0, pR);
+#pragma unroll
+                        for (int j = 0; j < TMA_MAX_ND; j++)
+                            if (j < nd) {
+                                mac(a0, xd[j], st[(size_t)(2 * j) * 256 + tid]);
+                                mac(a1, xd[j], st[(size_t)(2 * j + 1) * 256 + tid]);
+                            }
+                        u0 = montred(a0, q, qinv);
+                        u1 = montred(a1, q, qinv);
+                    } else {
+                        u0 = montmul(x0, pR, q, qinv);
+                        u1 = montmul(x1, pR, q, qinv);
+                    }
+                    const u32 used = E->used;
+#pragma unroll
+                    for (int j = 0; j < G; j++)
+                        if (used >> j & 1u) {
+                            const u64 m = st[(size_t)(2 * nd + j) * 256 + tid];
+                            mac(s0[j], u0, m);
+                            mac(s1[j], u1, m);
+                        }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            if (bad) break;
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                u64 *o = it->out[j];
+                if (o) {
+                    o[(size_t)e * N + c] = montred(s0[j], q, qinv);
+                    o[((size_t)ne + e) * N + c] = montred(s1[j], q, qinv);
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicExch(err, 1);
+}
+
 constexpr int WS_STAGES = 3;
 
 static int init_staged_kernels() {
@@ -1007,7 +1170,25 @@ static int init_staged_kernels() {
                cudaSuccess ||
            cudaFuncSetAttribute(k_lt_grp_ws<LT_GROUP, WS_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smemw) != cudaSuccess ||
+           cudaFuncSetAttribute(k_lt_grp_pws<LT_GROUP, WS_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smemw) != cudaSuccess ||
            cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess;
+}
+
+// Every item (of one or several outputs) in one launch of the persistent
+// kernel: two CTAs per SM walk the units.
+int lt_group_persistent(Ctx *c, int lv, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes) {
+    if (nitems <= 0) return HEGMM_OK;
+    const int ne = lv + c->K, nd = c->digits(lv);
+    if (nd > TMA_MAX_ND) return set_err(c, HEGMM_EINVAL, "persistent linear-transformation kernel: too many digits");
+    Launch t(c, K_LT_KSW, bytes);
+    const long long units = (long long)nitems * ne * (c->N >> 8);
+    const int grid = (int)std::min<long long>(units, 2LL * c->nsm);
+    const size_t smem = (WS_STAGES * (size_t)(2 * nd + LT_GROUP) * 256 + 2 * WS_STAGES) * 8;
+    k_lt_grp_pws<LT_GROUP, WS_STAGES><<<grid, 288, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents,
+                                                                 d_items, nitems, c->d_err, c->wait_limit,
+                                                                 c->test_drop_entry);
+    return cuda_check(c, "lt_group_persistent");
 }
 
 int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_items, int nitems, double bytes) {

@@ -22,7 +22,7 @@ def H():
     return hegmm
 
 
-@pytest.mark.parametrize("variant", [6, 7])
+@pytest.mark.parametrize("variant", [6, 7, 8])
 def test_bounded_wait_reports_timeout_and_context_survives(H, variant):
     ctx = H.Context.from_preset(W.MEDIUM)
     ctx.hegmm_keygen(SEED, [(6, 10, 9)], H.ALG_1)

@@ -168,7 +168,7 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
 @pytest.mark.parametrize("chunk,variant,fused,one", [(1, 0, 1, 0), (3, 1, 1, 0), (4096, 2, 1, 0), (32, 3, 1, 0),
                                                       (5, 4, 1, 0), (32, 5, 1, 0), (32, 6, 1, 0), (3, 6, 1, 1),
                                                       (32, 7, 1, 0), (2, 7, 1, 1), (32, 7, 1, 2), (5, 0, 1, 3),
-                                                      (32, 0, 0, 0)])
+                                                      (32, 0, 0, 0), (32, 8, 1, 0), (3, 8, 1, 0)])
 def test_double_mode_executor_settings(H, chunk, variant, fused, one):
     # work-item size, fused-kernel variants and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
@@ -300,3 +300,22 @@ def test_batched_import_export_equal_single(H):
         single = ctx.hegmm_ct_import(h)
         assert (ctx.hegmm_ct_export(single) == h).all()
     assert rng is not None
+
+
+@pytest.mark.parametrize("name", ["medium", "paper"])
+def test_ntt_thread_counts_change_no_bit(H, name):
+    # both CTA forms of the NTT-family kernels (and the launch-size rule)
+    # give the same product, which is the oracle's (a rotation checks the
+    # key-switch path alone)
+    pre, ctx, o = get_pair(H, name)
+    x = rand_slots(o, 12)
+    ct, co = enc_pair(ctx, o, x, 8, 0)
+    ctx.hegmm_keygen_rotations([5])
+    ref = o.rotate(co, 5)
+    try:
+        for nt in (512, 1024, 0):
+            ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, nt)
+            assert (ctx.hegmm_ct_export(ctx.hegmm_rotate(ct, 5)) == ref).all(), nt
+            assert (ctx.hegmm_ct_export(ctx.hegmm_mult(ct, ct)) == o.mult_relin(co, co)).all(), nt
+    finally:
+        ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, 0)

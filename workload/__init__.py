@@ -14,6 +14,9 @@ build is measured on:
 * ``tiny``   N=4096,  t=65537, 3 chain primes < 2^30, 1 special prime, dnum=3
 * ``medium`` N=8192,  t=65537, 5 chain primes < 2^40, 1 special prime, dnum=5
 * ``paper``  N=16384, t=65537, 8 chain primes < 2^50, 2 special primes, dnum=4
+
+and the same three rings under the BFV variant (``tiny_bfv``, ``medium_bfv``,
+``paper_bfv``).
 """
 from __future__ import annotations
 
@@ -44,6 +47,7 @@ class Preset:
     alpha: int
     eta: int = 21
     ms_drop: int = 0
+    scheme: int = 0  # 0: BGV, 1: BFV (the paper's scheme; no modulus switch)
 
     @property
     def N(self) -> int:
@@ -61,7 +65,12 @@ class Preset:
 TINY = Preset("tiny", logN=12, t=65537, L=3, qbits=30, K=1, alpha=1, ms_drop=1)
 MEDIUM = Preset("medium", logN=13, t=65537, L=5, qbits=40, K=1, alpha=1)
 PAPER = Preset("paper", logN=14, t=65537, L=8, qbits=50, K=2, alpha=2)
-PRESETS = {p.name: p for p in (TINY, MEDIUM, PAPER)}
+# The BFV variant on the same rings (the tiny ring needs no modulus switch
+# under BFV: its noise stays about 9 bits below log2(Q / 2t)).
+TINY_BFV = Preset("tiny_bfv", logN=12, t=65537, L=3, qbits=30, K=1, alpha=1, scheme=1)
+MEDIUM_BFV = Preset("medium_bfv", logN=13, t=65537, L=5, qbits=40, K=1, alpha=1, scheme=1)
+PAPER_BFV = Preset("paper_bfv", logN=14, t=65537, L=8, qbits=50, K=2, alpha=2, scheme=1)
+PRESETS = {p.name: p for p in (TINY, MEDIUM, PAPER, TINY_BFV, MEDIUM_BFV, PAPER_BFV)}
 
 # Matrix shapes (m, l, n) and entry ranges of the workloads.
 TINY_SHAPES: List[Tuple[int, int, int]] = [(4, 8, 6)]
