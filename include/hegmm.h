@@ -79,7 +79,21 @@ typedef struct hegmm_ct hegmm_ct;   /* device ciphertext [2][level][N], NTT doma
  * Limits: 10 <= logN <= 14, 2 <= L, 1 <= K, L + K <= 24, 20 <= qbits <= 56
  * (the NTTs reduce their values only when they leave a transform, which
  * needs 128 q < 2^63), alpha divides L, K >= alpha (so P >= every digit
- * modulus up to a bit), K <= 4, digits (L + K) - L <= 128. */
+ * modulus up to a bit), K <= 4, digits (L + K) - L <= 128.
+ * scheme: HEGMM_SCHEME_BGV (0) or HEGMM_SCHEME_BFV (1), the paper's own
+ * scheme (Section 4.1).  Under BFV the message is scaled instead of the
+ * noise: c0 + c1 s = Delta m + e with Delta = floor(Q / t); switching keys
+ * carry plain errors and ModDown rounds plainly; decryption is
+ * round(t [c0 + c1 s]_Q / Q) mod t; HE-Mult extends both operands from Q to
+ * an auxiliary base B of L + 2 more primes (the next ones below the special
+ * primes), forms the tensor over Q u B and returns round(t/Q x tensor) (an
+ * RNS computation of the nearest integer: a floating-point sum of at most L
+ * fractions decides it, so it can differ from the exact nearest integer
+ * only when t x tensor / Q lies within about L 2^-52 of a half-integer) before
+ * relinearising; a lazy sum of tensors is formed over Q u B and rounded
+ * once.  BFV needs ms_drop = 0 and 2 L + K + 3 <= 25. */
+#define HEGMM_SCHEME_BGV 0
+#define HEGMM_SCHEME_BFV 1
 typedef struct {
     int logN;
     uint64_t t;
@@ -89,6 +103,7 @@ typedef struct {
     int alpha;
     int eta;
     int ms_drop;
+    int scheme;
 } hegmm_params;
 
 /* Operation counts of one product.  rot/cmult/mult follow the paper's

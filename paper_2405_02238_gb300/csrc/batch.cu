@@ -108,6 +108,9 @@ struct RotChunk {
 struct RelinChunk {
     int cnt = 0, nsum = 0;
     Tensor3 *d_tens = nullptr;
+    // BFV: the operands' pointers and the tensors over Q and B into the scratch
+    u64 **d_ops = nullptr;
+    Tensor3 *d_tq = nullptr, *d_tb = nullptr;
     RotDesc *d_rot = nullptr;
     DivDesc *d_div = nullptr;
     SumDesc *d_sum = nullptr;
@@ -181,6 +184,11 @@ struct BatchPlan {
     // extraction's trees with one group-sum launch
     int pow2 = 0;
     RotTree optree, xtree;
+    // BFV HE-Mult (bfv_tensor): scratch, and the lazy sums' operands and descriptors
+    u64 *bfs = nullptr;
+    u64 **d_lops = nullptr;
+    TensorSum *d_lsq = nullptr, *d_lsb = nullptr;
+    int lops_n = 0;
     LtTerm *d_p2_terms = nullptr;
     int *d_p2_off = nullptr;
     u64 **d_p2_outs = nullptr;
@@ -1203,6 +1211,15 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
     // tensor + relinearisation chunks
     const u64 *A1 = lv1 != lv0 ? P->ms : P->outs;
     const u64 *rlk = c->keys[0];
+    if (c->bfv) {
+        // BFV: scratch of the tensors' base extension and rounding
+        int itot = 0;
+        for (int p = 0; p < B; p++) itot += niter[p];
+        const size_t w = lazy ? bfv_tensor_words(c, itot, B) : bfv_tensor_words(c, std::max(1, std::min(RK, I)),
+                                                                               std::max(1, std::min(RK, I)));
+        P->bfs = (u64 *)plan_alloc(c, P, w * 8);
+        if (!P->bfs) return fail_rc(set_err(c, HEGMM_ENOMEM, "BFV tensor scratch"));
+    }
     for (int i0 = 0; i0 < I; i0 += RK) {
         RelinChunk ch;
         ch.cnt = std::min(RK, I - i0);
@@ -1241,6 +1258,26 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
             sv.back().count++;
         }
         ch.nsum = (int)sv.size();
+        if (c->bfv) {
+            // bfv_tensor's layout: operands over Q and B, then the tensors over Q and B
+            const int n = ch.cnt, L = lv1, nb = c->nb;
+            u64 *xb = P->bfs + (size_t)n * 4 * L * N, *dq = xb + (size_t)n * 4 * nb * N;
+            u64 *db = dq + (size_t)n * 3 * L * N;
+            std::vector<u64 *> ops;
+            std::vector<Tensor3> tq, tb;
+            for (int r = 0; r < n; r++) {
+                ops.push_back(const_cast<u64 *>(tv[r].a));
+                ops.push_back(const_cast<u64 *>(tv[r].b));
+                tq.push_back({tv[r].a, tv[r].b, dq + (size_t)r * 3 * L * N});
+                u64 *xr = xb + (size_t)r * 4 * nb * N;
+                tb.push_back({xr, xr + (size_t)2 * nb * N, db + (size_t)r * 3 * nb * N});
+            }
+            ch.d_ops = plan_upload(c, P, ops);
+            ch.d_tq = plan_upload(c, P, tq);
+            ch.d_tb = plan_upload(c, P, tb);
+            if (!keep(ch.d_ops) || !keep(ch.d_tq) || !keep(ch.d_tb))
+                return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
+        }
         ch.d_tens = plan_upload(c, P, tv);
         ch.d_rot = plan_upload(c, P, rd);
         ch.d_div = dbl ? nullptr : plan_upload(c, P, dd);
@@ -1273,6 +1310,41 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
                 v.g = 1;
                 dd.push_back(v);
             }
+        }
+        if (c->bfv) {
+            // BFV: every iteration's operands extended to the auxiliary base, the
+            // tensors of each product summed over Q and over B, rounded once
+            int itot = 0;
+            for (int p = 0; p < B; p++) itot += niter[p];
+            const int L = lv1, nb = c->nb;
+            u64 *xb = P->bfs + (size_t)itot * 4 * L * N, *dq = xb + (size_t)itot * 4 * nb * N;
+            u64 *db = dq + (size_t)B * 3 * L * N;
+            std::vector<u64 *> ops;
+            std::vector<TensorSum> sq, sb;
+            int first = 0;
+            for (int p = 0; p < B; p++) {
+                for (int k = 0; k < niter[p]; k++) {
+                    ops.push_back(const_cast<u64 *>(ts[p].a) + (size_t)k * ts[p].stride);
+                    ops.push_back(const_cast<u64 *>(ts[p].b) + (size_t)k * ts[p].stride);
+                }
+                TensorSum q = ts[p];
+                q.d = dq + (size_t)p * 3 * L * N;
+                sq.push_back(q);
+                TensorSum bsum{};
+                bsum.a = xb + (size_t)first * 4 * nb * N;
+                bsum.b = bsum.a + (size_t)2 * nb * N;
+                bsum.stride = (long long)4 * nb * N;
+                bsum.d = db + (size_t)p * 3 * nb * N;
+                bsum.count = niter[p];
+                sb.push_back(bsum);
+                first += niter[p];
+            }
+            P->lops_n = itot;
+            P->d_lops = plan_upload(c, P, ops);
+            P->d_lsq = plan_upload(c, P, sq);
+            P->d_lsb = plan_upload(c, P, sb);
+            if (!keep(P->d_lops) || !keep(P->d_lsq) || !keep(P->d_lsb))
+                return fail_rc(set_err(c, HEGMM_ENOMEM, "batch descriptors"));
         }
         P->d_tsum = plan_upload(c, P, ts);
         P->d_lrot = plan_upload(c, P, rd);
@@ -1393,7 +1465,7 @@ static int build_bplan(Ctx *c, const std::vector<std::array<int, 4>> &shapes, in
 
 // ModDown of npoly accumulated polynomials over the extended basis of level lv
 static int moddown_polys(Ctx *c, int lv, u64 *u, const DivDesc *d_div, int npoly) {
-    const DivTab *tb = div_tab(c, lv, 0);
+    const DivTab *tb = div_tab(c, lv, c->bfv ? 2 : 0);
     if (!tb) return HEGMM_ENOMEM;
     int rc;
     if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, npoly), tb->d))) return rc;  // times [t^-1 (P/p_k)^-1]_{p_k}
@@ -1449,7 +1521,12 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
         if ((rc = modswitch_polys(c, lv0, P->outs, 2 * P->O, nullptr, P->ms, P->d_msdiv))) return rc;
     // 4. HE-Mult of every iteration and the sum per product
     if (P->lazy) {
-        if ((rc = tensor_sum(c, lv1, P->d_tsum, B))) return rc;
+        if (c->bfv) {
+            if ((rc = bfv_tensor(c, P->lops_n, P->d_lops, P->d3s, P->bfs, nullptr, nullptr, P->d_lsq, P->d_lsb, B)))
+                return rc;
+        } else if ((rc = tensor_sum(c, lv1, P->d_tsum, B))) {
+            return rc;
+        }
         if ((rc = modup(c, lv1, B, P->d3s + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->lxc, P->lD))) return rc;
         if (dbl) {
             if ((rc = ksw_ip(c, lv1, P->d_lrot, B))) return rc;
@@ -1460,7 +1537,11 @@ static int run_bplan_kernels(Ctx *c, BatchPlan *P) {
         cudaMemsetAsync(dbl ? P->cpq : P->cacc, 0, (size_t)B * 2 * np1 * N * 8, c->st);
     }
     for (auto &ch : P->lchunks) {
-        if ((rc = tensor(c, lv1, ch.d_tens, ch.cnt))) return rc;
+        if (c->bfv) {
+            if ((rc = bfv_tensor(c, ch.cnt, ch.d_ops, P->d3, P->bfs, ch.d_tq, ch.d_tb, nullptr, nullptr, 0))) return rc;
+        } else if ((rc = tensor(c, lv1, ch.d_tens, ch.cnt))) {
+            return rc;
+        }
         if ((rc = modup(c, lv1, ch.cnt, P->d3 + (size_t)2 * lv1 * N, (long long)3 * lv1 * N, P->rxc, P->rD))) return rc;
         if (dbl) {
             if ((rc = ksw_ip(c, lv1, ch.d_rot, ch.cnt))) return rc;

@@ -146,13 +146,15 @@ std::vector<u64> modup_table_host(const Ctx *c, int lv) {
 
 // Exact-division table (host copy) and its modulus lists.  kind 0: ModDown
 // at level lv (keep q_0..q_{lv-1}, drop the K special primes); kind 1:
-// modulus switch from lv (keep q_0..q_{lv-2}, drop q_{lv-1}).  Layout:
+// modulus switch from lv (keep q_0..q_{lv-2}, drop q_{lv-1}); kind 2: the
+// ModDown of kind 0 with plain rounding (correction factor 1, BFV).  Layout:
 // [ndrop] x {coef, coef_sh}; [nkeep][ndrop] x {hat, hat_sh, d_k mod q_i};
 // [nkeep] x {Dinv, Dinv_sh, t mod q_i, shoup}; then keep[nkeep], drop[ndrop].
 std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int> &keep, std::vector<int> &drop) {
     keep.clear();
     drop.clear();
-    if (kind == 0) {
+    const u64 tt = kind == 2 ? 1 : c->t;  // the rounding correction: t, or 1 for BFV's plain ModDown
+    if (kind == 0 || kind == 2) {
         for (int i = 0; i < lv; i++) keep.push_back(i);
         for (int k = 0; k < c->K; k++) drop.push_back(c->L + k);
     } else {
@@ -166,7 +168,7 @@ std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int>
         u64 hat = 1;
         for (int k2 = 0; k2 < ndrop; k2++)
             if (k2 != k) hat = hmul(hat, c->q[drop[k2]] % dk, dk);
-        const u64 coef = hmul(hinv(c->t % dk, dk), hinv(hat, dk), dk);
+        const u64 coef = hmul(hinv(tt % dk, dk), hinv(hat, dk), dk);
         h.push_back(coef);
         h.push_back(shoup(coef, dk));
     }
@@ -188,8 +190,8 @@ std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int>
         const u64 Di = hinv(D, qi);
         h.push_back(Di);
         h.push_back(shoup(Di, qi));
-        h.push_back(c->t % qi);
-        h.push_back(shoup(c->t % qi, qi));
+        h.push_back(tt % qi);
+        h.push_back(shoup(tt % qi, qi));
     }
     for (int i = 0; i < nkeep; i++) h.push_back((u64)keep[i]);
     for (int k = 0; k < ndrop; k++) h.push_back((u64)drop[k]);
@@ -202,7 +204,7 @@ std::vector<u64> div_table_host(const Ctx *c, int lv, int kind, std::vector<int>
             u64 hat = 1;
             for (int k2 = 0; k2 < ndrop; k2++)
                 if (k2 != k) hat = hmul(hat, c->q[drop[k2]] % qi, qi);
-            const u64 ht = hmul(hat, c->t % qi, qi);
+            const u64 ht = hmul(hat, tt % qi, qi);
             h.push_back(ht);
             h.push_back(shoup(ht, qi));
             h.push_back(qi - c->q[drop[k]]);
@@ -249,6 +251,99 @@ int build_div_tab(Ctx *c, int lv, int kind) {
     return cuda_check(c, "div table");
 }
 
+// BFV constants (layout: BfvTab in internal.h).
+static int build_bfv_tab(Ctx *c) {
+    const int nq = c->L, nb = c->nb;
+    BfvTab &T = c->bt;
+    size_t w = 0;
+    auto take = [&](size_t n) {
+        size_t o = w;
+        w += n;
+        return o;
+    };
+    T.qt = take(2 * nq);
+    T.tt = take(nq);
+    T.qd = take(nq);
+    T.qbm = take((size_t)nq * nb);
+    T.qb = take(nb);
+    T.qim = take((size_t)nq * nb);
+    T.qib = take(2 * nb);
+    T.tb = take(2 * nb);
+    T.bt = take(2 * nb);
+    T.bd = take(nb);
+    T.bqm = take((size_t)nb * nq);
+    T.bq = take(nq);
+    T.dl = take(2 * nq);
+    T.words = w;
+    std::vector<u64> h(w, 0);
+    auto qv = [&](int i) { return c->q[i]; };            // chain prime i
+    auto bv = [&](int j) { return c->q[c->b0 + j]; };    // auxiliary prime j
+    auto r64 = [&](u64 m) { return (u64)(((u128)1 << 64) % m); };
+    auto dbits = [](double d) {
+        u64 b;
+        memcpy(&b, &d, 8);
+        return b;
+    };
+    const u64 t = c->t;
+    u64 Qt = 1;  // Q mod t
+    for (int i = 0; i < nq; i++) Qt = hmul(Qt, qv(i) % t, t);
+    for (int i = 0; i < nq; i++) {
+        const u64 qi = qv(i);
+        u64 hat = 1;
+        for (int i2 = 0; i2 < nq; i2++)
+            if (i2 != i) hat = hmul(hat, qv(i2) % qi, qi);
+        const u64 hi = hinv(hat, qi);
+        h[T.qt + 2 * i] = hi;
+        h[T.qt + 2 * i + 1] = shoup(hi, qi);
+        h[T.tt + i] = (u64)(((u128)t << 64) / qi);
+        h[T.qd + i] = dbits(1.0 / (double)qi);
+        u64 Bq = 1;
+        for (int j = 0; j < nb; j++) Bq = hmul(Bq, bv(j) % qi, qi);
+        h[T.bq + i] = Bq;
+        // Delta = (Q - (Q mod t)) / t, so Delta mod q_i = -(Q mod t) t^-1 mod q_i
+        const u64 dl = hmul((qi - Qt % qi) % qi, hinv(t % qi, qi), qi);
+        h[T.dl + 2 * i] = dl;
+        h[T.dl + 2 * i + 1] = shoup(dl, qi);
+    }
+    for (int j = 0; j < nb; j++) {
+        const u64 bj = bv(j), r1 = r64(bj);
+        u64 Qb = 1;
+        for (int i = 0; i < nq; i++) Qb = hmul(Qb, qv(i) % bj, bj);
+        h[T.qb + j] = Qb;
+        const u64 Qi = hinv(Qb, bj);
+        h[T.qib + 2 * j] = Qi;
+        h[T.qib + 2 * j + 1] = shoup(Qi, bj);
+        h[T.tb + 2 * j] = t % bj;
+        h[T.tb + 2 * j + 1] = shoup(t % bj, bj);
+        for (int i = 0; i < nq; i++) {
+            u64 hat = 1;  // Q / q_i mod b_j
+            for (int i2 = 0; i2 < nq; i2++)
+                if (i2 != i) hat = hmul(hat, qv(i2) % bj, bj);
+            h[T.qbm + (size_t)i * nb + j] = hmul(hat, r1, bj);
+            h[T.qim + (size_t)i * nb + j] = hmul(hinv(qv(i) % bj, bj), r1, bj);
+        }
+        u64 hatb = 1;  // B / b_j mod b_j
+        for (int j2 = 0; j2 < nb; j2++)
+            if (j2 != j) hatb = hmul(hatb, bv(j2) % bj, bj);
+        const u64 bt = hinv(hatb, bj);
+        h[T.bt + 2 * j] = bt;
+        h[T.bt + 2 * j + 1] = shoup(bt, bj);
+        h[T.bd + j] = dbits(1.0 / (double)bj);
+        for (int i = 0; i < nq; i++) {
+            const u64 qi = qv(i);
+            u64 hb = 1;  // B / b_j mod q_i
+            for (int j2 = 0; j2 < nb; j2++)
+                if (j2 != j) hb = hmul(hb, bv(j2) % qi, qi);
+            h[T.bqm + (size_t)j * nq + i] = hmul(hb, r64(qi), qi);
+        }
+    }
+    c->d_bfv = dalloc(c, w);
+    if (!c->d_bfv) return set_err(c, HEGMM_ENOMEM, "BFV tables");
+    cudaMemcpyAsync(c->d_bfv, h.data(), w * 8, cudaMemcpyHostToDevice, c->st);
+    cudaStreamSynchronize(c->st);
+    return cuda_check(c, "BFV tables");
+}
+
 // ---------------------------------------------------------------- context
 
 static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
@@ -272,19 +367,27 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
                            std::to_string(PAT_MAX));
     const u64 two_n = 2 * (u64)c->N;
     if (!is_prime(p->t) || (p->t - 1) % two_n != 0) return set_err(c, HEGMM_EINVAL, "t must be a prime = 1 mod 2N");
+    if (p->scheme != HEGMM_SCHEME_BGV && p->scheme != HEGMM_SCHEME_BFV)
+        return set_err(c, HEGMM_EINVAL, "scheme must be HEGMM_SCHEME_BGV or HEGMM_SCHEME_BFV");
+    c->bfv = p->scheme == HEGMM_SCHEME_BFV;
+    if (c->bfv && p->ms_drop) return set_err(c, HEGMM_EINVAL, "the BFV variant has no modulus switch (ms_drop = 0)");
     c->dnum = p->L / p->alpha;
     c->np = p->L + p->K;
     c->tmod = c->np;
-    c->nmod = c->np + 1;
-    // primes: largest below 2^qbits, = 1 mod 2N, descending
+    c->nb = c->bfv ? p->L + 2 : 0;
+    c->b0 = c->np + 1;
+    c->nmod = c->np + 1 + c->nb;
+    if (c->nmod > MAXM) return set_err(c, HEGMM_EINVAL, "too many primes (BFV: 2 L + K + 3 <= 25)");
+    // primes: largest below 2^qbits, = 1 mod 2N, descending: chain, special,
+    // then (BFV) the auxiliary base, which sits after t in q[]
     u64 cand = ((((u64)1 << p->qbits) - 1) / two_n) * two_n + 1;
     if (cand >= ((u64)1 << p->qbits)) cand -= two_n;
     int got = 0;
-    while (got < c->np && cand > two_n) {
-        if (is_prime(cand) && cand != p->t) c->q[got++] = cand;
+    while (got < c->np + c->nb && cand > two_n) {
+        if (is_prime(cand) && cand != p->t) c->q[got < c->np ? got : got + 1] = cand, got++;
         cand -= two_n;
     }
-    if (got != c->np) return set_err(c, HEGMM_EINVAL, "not enough NTT primes");
+    if (got != c->np + c->nb) return set_err(c, HEGMM_EINVAL, "not enough NTT primes");
     // the key inner product sums dnum products (+ one folded term) below q 2^64 before one reduction
     if ((u128)(c->dnum + 2) * c->q[0] >= ((u128)1 << 64))
         return set_err(c, HEGMM_EINVAL, "primes too large for dnum: (dnum + 2) q must stay below 2^64");
@@ -365,7 +468,8 @@ static int ctx_init(Ctx *c, const hegmm_params *p, void *stream) {
     c->d_slot_pos = upload(c, both);
     if (!c->d_slot_pos) return set_err(c, HEGMM_ENOMEM, "slot table");
     cudaStreamSynchronize(c->st);
-    return cuda_check(c, "slot table");
+    if (int rc = cuda_check(c, "slot table")) return rc;
+    return c->bfv ? build_bfv_tab(c) : HEGMM_OK;
 }
 
 u64 galois_of(Ctx *c, long long z) {
@@ -420,7 +524,8 @@ static int gen_key(Ctx *c, u64 g) {
         u64 *ka = key + ((size_t)j * 2 + 1) * np * N;
         LimbPat pa = pat_mods(ka, np, mods.data(), 1, 0), pb = pat_mods(kb, np, mods.data(), 1, 0);
         if ((rc = sample_uniform(c, pa, rng_stream(c->key_seed, DOM_KEY_A, g * 256 + (u64)j), nullptr))) return rc;
-        if ((rc = sample_cbd_t(c, pb, rng_stream(c->key_seed, DOM_KEY_E, g * 256 + (u64)j), c->prm.eta))) return rc;
+        const u64 est = rng_stream(c->key_seed, DOM_KEY_E, g * 256 + (u64)j);
+        if ((rc = c->bfv ? sample_cbd(c, pb, est, c->prm.eta) : sample_cbd_t(c, pb, est, c->prm.eta))) return rc;
         if ((rc = ntt_fwd(c, pa))) return rc;
         if ((rc = ntt_fwd(c, pb))) return rc;
         if ((rc = key_digit_combine(c, kb, ka, sp, Pm, j * c->alpha, std::min((j + 1) * c->alpha, c->L)))) return rc;
@@ -526,7 +631,8 @@ static int encrypt(Ctx *c, const hegmm_pt *pt, u64 seed, u64 sid, hegmm_ct **out
     LimbPat p0 = pat_ct(c, ct->d, 1, L), p1 = pat_ct(c, ct->d + (size_t)L * c->N, 1, L);
     int rc;
     if ((rc = sample_uniform(c, p1, rng_stream(seed, DOM_ENC_A, sid), nullptr))) return rc;
-    if ((rc = sample_cbd_t(c, p0, rng_stream(seed, DOM_ENC_E, sid), c->prm.eta))) return rc;
+    const u64 est = rng_stream(seed, DOM_ENC_E, sid);
+    if ((rc = c->bfv ? sample_cbd(c, p0, est, c->prm.eta) : sample_cbd_t(c, p0, est, c->prm.eta))) return rc;
     if ((rc = ntt_fwd(c, pat_ct(c, ct->d, 2, L)))) return rc;
     if ((rc = encrypt_combine(c, L, ct->d, pt->d))) return rc;
     *out = ct;
@@ -572,7 +678,12 @@ static int decrypt_slots(Ctx *c, const hegmm_ct *ct, std::vector<u64> &slots) {
     int rc;
     if ((rc = decrypt_dot(c, lv, ct->d, v))) return rc;
     if ((rc = ntt_inv(c, pat_ct(c, v, 1, lv)))) return rc;
-    if ((rc = crt_to_t(c, lv, v, crt_tab(c, lv), m))) return rc;
+    if (c->bfv) {
+        if (lv != c->L) return set_err(c, HEGMM_EINVAL, "BFV ciphertexts are at the top level");
+        if ((rc = bfv_decode(c, v, m))) return rc;  // round(t v / Q) mod t
+    } else if ((rc = crt_to_t(c, lv, v, crt_tab(c, lv), m))) {
+        return rc;
+    }
     int tm = c->tmod;
     if ((rc = ntt_fwd(c, pat_mods(m, 1, &tm, 1, 0)))) return rc;
     std::vector<u64> ev(N);
@@ -632,6 +743,7 @@ void hegmm_ctx_destroy(hegmm_ctx *h) {
     for (auto &kv : c->divs) dfree(c, kv.second.d);
     for (auto &kv : c->crt) dfree(c, kv.second);
     dfree(c, c->d_Pmod);
+    dfree(c, c->d_bfv);
     dfree(c, c->d_slot_pos);
     dfree(c, c->d_tw);
     dfree(c, c->d_mods);

@@ -86,7 +86,7 @@ int modup(Ctx *c, int lv, int n, const u64 *xn, long long xn_stride, u64 *xc, u6
 // Inner product + ModDown for nrot key switches whose descriptors are on
 // the device; u/tmp are [2*nrot] polynomial scratch laid out contiguously.
 int ksw_moddown(Ctx *c, int lv, const RotDesc *d_rots, const DivDesc *d_div, int nrot, u64 *u, u64 *tmp) {
-    const DivTab *tb = div_tab(c, lv, 0);
+    const DivTab *tb = div_tab(c, lv, c->bfv ? 2 : 0);
     if (!tb) return HEGMM_ENOMEM;
     int rc;
     (void)tmp;
@@ -94,6 +94,65 @@ int ksw_moddown(Ctx *c, int lv, const RotDesc *d_rots, const DivDesc *d_div, int
     // the special limbs' inverse NTT also multiplies them by [t^-1 (P/p_k)^-1]_{p_k}
     if ((rc = ntt_inv(c, pat_drop_special(c, lv, u, 2 * nrot), tb->d))) return rc;
     return divround_ntt(c, *tb, d_div, 2 * nrot);
+}
+
+// ---------------------------------------------------------------- BFV HE-Mult
+
+// Scratch of bfv_tensor: the operands in coefficient form over Q and over
+// the auxiliary base B ([n][4][L][N], [n][4][nb][N]), the tensors over Q and
+// over B ([nout][3][L][N], [nout][3][nb][N]) and the rounded tensors over B
+// ([nout][3][nb][N]); nout = n, or the number of sums.
+size_t bfv_tensor_words(const Ctx *c, int n, int nout) {
+    return (size_t)c->N * ((size_t)n * 4 * (c->L + c->nb) + (size_t)nout * 3 * (c->L + 2 * c->nb));
+}
+
+// The limbs over the auxiliary base of npoly polynomials at stride nb N.
+static LimbPat pat_aux(Ctx *c, u64 *base, int npoly) {
+    LimbPat p{};
+    p.base = base;
+    p.outer_stride = (long long)c->nb * c->N;
+    p.inner = c->nb;
+    p.count = c->nb * npoly;
+    for (int i = 0; i < c->nb; i++) {
+        p.off[i] = (unsigned short)i;
+        p.mod[i] = (unsigned char)(c->b0 + i);
+    }
+    return p;
+}
+
+// HE-Mult before relinearisation under BFV, for n products a_k (x) b_k at
+// level L (ciphertexts in the NTT domain; d_ops = {a_0, b_0, a_1, ...}):
+// both operands' centred values are extended from Q to the auxiliary base
+// B (exact base conversion), the tensors are formed over Q u B (the exact
+// integer tensors, QB exceeding twice their size), each of d0, d1, d2 is
+// rounded to round(t y / Q) over B and converted back to Q, and `out`
+// receives the results [nout][3][L][N] in the NTT domain.  d_tq / d_tb:
+// n Tensor3 descriptors over Q (operands a_k, b_k) and over B (operands in
+// the scratch); or, with sums != 0, d_sq / d_sb: nout = sums TensorSum
+// descriptors whose tensors are summed before the rounding (the lazy
+// relinearisation of several iterations).
+int bfv_tensor(Ctx *c, int n, u64 *const *d_ops, u64 *out, u64 *scratch, const Tensor3 *d_tq, const Tensor3 *d_tb,
+               const TensorSum *d_sq, const TensorSum *d_sb, int sums) {
+    const int L = c->L, nb = c->nb, N = c->N, nout = sums ? sums : n;
+    u64 *xq = scratch, *xb = xq + (size_t)n * 4 * L * N, *dq = xb + (size_t)n * 4 * nb * N;
+    u64 *db = dq + (size_t)nout * 3 * L * N, *zb = db + (size_t)nout * 3 * nb * N;
+    int rc;
+    if ((rc = gather_cts(c, L, d_ops, 2 * n, xq))) return rc;
+    if ((rc = ntt_inv(c, pat_ct(c, xq, 4 * n, L)))) return rc;
+    if ((rc = bfv_conv_q_to_b(c, xq, (long long)L * N, xb, (long long)nb * N, 4 * n))) return rc;
+    if ((rc = ntt_fwd(c, pat_aux(c, xb, 4 * n)))) return rc;
+    if (sums) {
+        if ((rc = tensor_sum(c, L, d_sq, nout, 0))) return rc;
+        if ((rc = tensor_sum(c, nb, d_sb, nout, c->b0))) return rc;
+    } else {
+        if ((rc = tensor(c, L, d_tq, n, 0))) return rc;
+        if ((rc = tensor(c, nb, d_tb, n, c->b0))) return rc;
+    }
+    if ((rc = ntt_inv(c, pat_ct(c, dq, 3 * nout, L)))) return rc;
+    if ((rc = ntt_inv(c, pat_aux(c, db, 3 * nout)))) return rc;
+    if ((rc = bfv_scale(c, dq, (long long)L * N, db, (long long)nb * N, zb, (long long)nb * N, 3 * nout))) return rc;
+    if ((rc = bfv_conv_b_to_q(c, zb, (long long)nb * N, out, (long long)L * N, 3 * nout))) return rc;
+    return ntt_fwd(c, pat_ct(c, out, 3 * nout, L));
 }
 
 // ---------------------------------------------------------------- single operations
@@ -168,6 +227,20 @@ int mult_relin(Ctx *c, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out) {
     u64 *tmp = dalloc(c, (size_t)2 * lv * N);
     if (!o || !d3 || !xc || !D || !u || !tmp) return set_err(c, HEGMM_ENOMEM, "mult");
     std::vector<Tensor3> tv{{a->d, b->d, d3}};
+    u64 *bs = nullptr;
+    u64 **d_ops = nullptr;
+    Tensor3 *d_tb = nullptr;
+    if (c->bfv) {
+        if (lv != c->L) return set_err(c, HEGMM_EINVAL, "BFV products need operands at the top level");
+        bs = dalloc(c, bfv_tensor_words(c, 1, 1));
+        if (!bs) return set_err(c, HEGMM_ENOMEM, "mult");
+        std::vector<u64 *> ops{a->d, b->d};
+        d_ops = upload(c, ops);
+        u64 *xb = bs + (size_t)4 * c->L * N, *db = xb + (size_t)4 * c->nb * N + (size_t)3 * c->L * N;
+        std::vector<Tensor3> tb{{xb, xb + (size_t)2 * c->nb * N, db}};
+        tv[0].d = xb + (size_t)4 * c->nb * N;  // the tensor over Q goes to the scratch
+        d_tb = upload(c, tb);
+    }
     // d0 / d1 enter the inner product as P d0, P d1
     std::vector<RotDesc> rd{{D, kit->second, u, d3, d3 + (size_t)lv * N, 1u, 0u}};
     std::vector<DivDesc> dd(2);
@@ -182,10 +255,15 @@ int mult_relin(Ctx *c, const hegmm_ct *a, const hegmm_ct *b, hegmm_ct **out) {
     RotDesc *d_r = upload(c, rd);
     DivDesc *d_d = upload(c, dd);
     int rc;
-    if ((rc = tensor(c, lv, d_t, 1))) return rc;
+    if (c->bfv) {
+        if ((rc = bfv_tensor(c, 1, d_ops, d3, bs, d_t, d_tb, nullptr, nullptr, 0))) return rc;
+    } else if ((rc = tensor(c, lv, d_t, 1))) {
+        return rc;
+    }
     if ((rc = modup(c, lv, 1, d3 + (size_t)2 * lv * N, (long long)lv * N, xc, D))) return rc;
     if ((rc = ksw_moddown(c, lv, d_r, d_d, 1, u, tmp))) return rc;
-    for (void *p : {(void *)d_t, (void *)d_r, (void *)d_d, (void *)d3, (void *)xc, (void *)D, (void *)u, (void *)tmp})
+    for (void *p : {(void *)d_t, (void *)d_r, (void *)d_d, (void *)d3, (void *)xc, (void *)D, (void *)u, (void *)tmp,
+                    (void *)bs, (void *)d_ops, (void *)d_tb})
         dfree(c, p);
     *out = o;
     return cuda_check(c, "mult");
@@ -211,6 +289,7 @@ int modswitch_polys(Ctx *c, int lv, u64 *in, int npoly, u64 *tmp, u64 *out, DivD
 
 int modswitch(Ctx *c, const hegmm_ct *in, hegmm_ct **out) {
     const int lv = in->level, N = c->N;
+    if (c->bfv) return set_err(c, HEGMM_EINVAL, "the BFV variant has no modulus switch");
     if (lv < 2) return set_err(c, HEGMM_EINVAL, "no prime left to drop");
     hegmm_ct *o = new_ct(c, lv - 1);
     u64 *cp = dalloc(c, (size_t)2 * lv * N);

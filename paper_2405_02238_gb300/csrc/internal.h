@@ -16,7 +16,7 @@ typedef uint32_t u32;
 
 namespace hg {
 
-constexpr int MAXM = 25;      // L + K primes plus t
+constexpr int MAXM = 25;      // L + K primes, t, and (BFV) the auxiliary base
 // inner entries of a limb pattern; the largest pattern is the ModUp's
 // limbs outside each digit's own primes, digits(L) (L + K) - L entries, which
 // context creation checks against this bound
@@ -162,8 +162,26 @@ struct SumDesc {
     int pad;
 };
 
+// BFV constants (HEGMM_SCHEME_BFV) on the device, word offsets into Ctx::d_bfv
+// (nq = L chain primes q_i, nb auxiliary primes b_j; Montgomery = times
+// 2^64 mod the target prime; pairs = {w, Shoup companion}):
+//   qt  [nq] pairs (Q/q_i)^-1 mod q_i      tt [nq] floor(t 2^64 / q_i)
+//   qd  [nq] 1/q_i as double bits           qbm [nq][nb] Q/q_i mod b_j, Montgomery
+//   qb  [nb] Q mod b_j                      qim [nq][nb] q_i^-1 mod b_j, Montgomery
+//   qib [nb] pairs Q^-1 mod b_j             tb [nb] pairs t mod b_j
+//   bt  [nb] pairs (B/b_j)^-1 mod b_j       bd [nb] 1/b_j as double bits
+//   bqm [nb][nq] B/b_j mod q_i, Montgomery  bq [nq] B mod q_i
+//   dl  [nq] pairs Delta mod q_i, Delta = floor(Q / t)
+struct BfvTab {
+    size_t qt, tt, qd, qbm, qb, qim, qib, tb, bt, bd, bqm, bq, dl, words;
+};
+
 struct Ctx {
     hegmm_params prm{};
+    int bfv = 0;           // HEGMM_SCHEME_BFV
+    int nb = 0, b0 = 0;    // BFV: auxiliary primes at q[b0 .. b0 + nb)
+    u64 *d_bfv = nullptr;  // BFV constants (BfvTab)
+    BfvTab bt{};
     int logN = 0, N = 0, S = 0, L = 0, K = 0, alpha = 0, dnum = 0, np = 0, tmod = 0, nmod = 0;
     u64 t = 0;
     u64 q[MAXM]{};
@@ -284,9 +302,28 @@ int div_combine(Ctx *c, const DivTab &tab, const DivDesc *d_desc, int npoly);
 // extended basis (the sum is multiplied by P; special limbs are zero).
 int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_terms, const int *d_off,
                   u64 *const *d_outs, int nout, int accumulate);
-int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n);
+// limb i of the operands in modulus m0 + i (0: the chain primes; BFV's
+// auxiliary base: Ctx::b0)
+int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n, int m0 = 0);
 // n tensor sums (lazy 128-bit: (2 count + 2) q < 2^64)
-int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n);
+int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n, int m0 = 0);
+// BFV (HEGMM_SCHEME_BFV): decryption's rounding to t, the exact base
+// conversions Q -> B and B -> Q of centred values, and HE-Mult's
+// round(t y / Q) from y over Q u B to B; coefficient form, npoly polynomials
+// of nq (resp. nb) limbs at the given polynomial strides (words).
+int bfv_decode(Ctx *c, const u64 *v, u64 *out);
+int bfv_conv_q_to_b(Ctx *c, const u64 *in, long long in_pstride, u64 *out, long long out_pstride, int npoly);
+int bfv_conv_b_to_q(Ctx *c, const u64 *in, long long in_pstride, u64 *out, long long out_pstride, int npoly);
+int bfv_scale(Ctx *c, const u64 *yq, long long yq_pstride, const u64 *yb, long long yb_pstride, u64 *zb,
+              long long zb_pstride, int npoly);
+// The HE-Mult tensors of n products at level L, BFV: ops holds 2 n device
+// pointers (a_k, b_k, ciphertexts [2][L][N], NTT domain), d_out n results
+// [3][L][N] (NTT) at stride 3 L N words from `out`; scratch: see
+// bfv_tensor_words.  sum != 0: the n tensors are summed over Q u B and
+// rounded once into `out` (one result).
+size_t bfv_tensor_words(const Ctx *c, int n, int nout);
+int bfv_tensor(Ctx *c, int n, u64 *const *d_ops, u64 *out, u64 *scratch, const Tensor3 *d_tq, const Tensor3 *d_tb,
+               const TensorSum *d_sq, const TensorSum *d_sb, int sum);
 // Every item's output sums over the extended basis of level lv.  Needs
 // (entries per item + 2) * q < 2^64 for every prime (lazy 128-bit sums).
 // bytes: the algorithmic HBM bytes of the launch (keys, masks, outputs).
@@ -304,6 +341,7 @@ int pw_from_mont(Ctx *c, const LimbPat &p);                // x R -> x
 int sample_uniform(Ctx *c, const LimbPat &p, u64 stream, const int *gprime_of_inner);
 int sample_cbd_t(Ctx *c, const LimbPat &p, u64 stream, int eta);   // t * e mod q
 int sample_ternary(Ctx *c, const LimbPat &p, u64 stream);
+int sample_cbd(Ctx *c, const LimbPat &p, u64 stream, int eta);     // e mod q (BFV errors)
 int key_digit_combine(Ctx *c, u64 *kb, u64 *ka, const u64 *sprime, const u64 *d_Pmod, int lo, int hi);
 int encrypt_combine(Ctx *c, int lv, u64 *ct, const u64 *pt);
 int decrypt_dot(Ctx *c, int lv, const u64 *ct, u64 *v);

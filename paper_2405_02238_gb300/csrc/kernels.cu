@@ -1353,13 +1353,14 @@ int lt_accumulate(Ctx *c, int lv, int np, int src_np, int lift, const LtTerm *d_
 
 // ------------------------------------------------------------------ tensor (HE-Mult before relinearisation)
 
-__global__ void k_tensor(int lv, int logN, const ModDev *__restrict__ mods, const Tensor3 *__restrict__ ts) {
+// limb i of the operands is in modulus m0 + i (m0 = 0: the chain primes).
+__global__ void k_tensor(int lv, int m0, int logN, const ModDev *__restrict__ mods, const Tensor3 *__restrict__ ts) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int i = blockIdx.y;
     const Tensor3 T = ts[blockIdx.z];
-    const ModDev M = mods[i];
+    const ModDev M = mods[m0 + i];
     const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
     const u64 a0 = T.a[o0], a1 = T.a[o1];
     const u64 b0 = montmul(T.b[o0], M.r2, M.q, M.qinv);  // b R
@@ -1371,13 +1372,14 @@ __global__ void k_tensor(int lv, int logN, const ModDev *__restrict__ mods, cons
 
 // One thread per coefficient of one limb of one sum; the products of all
 // iterations are summed lazily (Montgomery, b taken to b R first).
-__global__ void k_tensor_sum(int lv, int logN, const ModDev *__restrict__ mods, const TensorSum *__restrict__ ts) {
+__global__ void k_tensor_sum(int lv, int m0, int logN, const ModDev *__restrict__ mods,
+                             const TensorSum *__restrict__ ts) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int i = blockIdx.y;
     const TensorSum T = ts[blockIdx.z];
-    const ModDev M = mods[i];
+    const ModDev M = mods[m0 + i];
     Acc s0{0, 0}, s1{0, 0}, s2{0, 0};
     const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
     for (int k = 0; k < T.count; k++) {
@@ -1395,21 +1397,159 @@ __global__ void k_tensor_sum(int lv, int logN, const ModDev *__restrict__ mods, 
     T.d[((size_t)2 * lv + i) * N + c] = montred(s2, M.q, M.qinv);
 }
 
-int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n) {
+int tensor_sum(Ctx *c, int lv, const TensorSum *d_t, int n, int m0) {
     if (n <= 0) return HEGMM_OK;
     Launch t(c, K_TENSOR, 0.0);
     for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
-        k_tensor_sum<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, c->logN, c->d_mods,
+        k_tensor_sum<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, m0, c->logN, c->d_mods,
                                                                                             d_t + i0);
     return cuda_check(c, "tensor_sum");
 }
 
-int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n) {
+int tensor(Ctx *c, int lv, const Tensor3 *d_t, int n, int m0) {
     if (n <= 0) return HEGMM_OK;
     Launch t(c, K_TENSOR, (double)n * 7.0 * lv * c->limb_bytes());
     for (int i0 = 0; i0 < n; i0 += kMaxGridZ)
-        k_tensor<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, c->logN, c->d_mods, d_t + i0);
+        k_tensor<<<grid_coef(c->N, lv, std::min(kMaxGridZ, n - i0)), 256, 0, c->st>>>(lv, m0, c->logN, c->d_mods,
+                                                                                        d_t + i0);
     return cuda_check(c, "tensor");
+}
+
+// ------------------------------------------------------------------ BFV (HEGMM_SCHEME_BFV)
+
+constexpr int BFV_MAXB = 16;  // chain or auxiliary primes a conversion handles in registers
+
+// round(sum_i w_i t / q_i) over the nq chain primes (w_i < q_i): each integer
+// part exactly -- a = floor(w_i T_i / 2^64) with T_i = floor(t 2^64 / q_i) is
+// the quotient or one less, the remainder w_i t - a q_i (exact mod 2^64,
+// below 2 q_i) corrects it -- and the remainders' fractions r_i / q_i summed
+// in double precision, so the result is the nearest integer unless that
+// sum lies within about nq 2^-52 of a half-integer.
+__device__ __forceinline__ u64 bfv_round_sum(const u64 *w, int nq, const u64 *__restrict__ tt,
+                                             const u64 *__restrict__ qd, const ModDev *__restrict__ mods, u64 t) {
+    u64 whole = 0;
+    double frac = 0.0;
+    for (int i = 0; i < nq; i++) {
+        const u64 q = mods[i].q;
+        u64 a = mulhi(w[i], tt[i]);
+        u64 r = w[i] * t - a * q;
+        if (r >= q) {
+            r -= q;
+            a++;
+        }
+        whole += a;
+        frac += (double)r * __longlong_as_double((long long)qd[i]);
+    }
+    return whole + (u64)floor(frac + 0.5);
+}
+
+// Decryption: v (coefficient form over the nq chain primes) -> round(t v / Q)
+// mod t: with w_i = [v_i (Q/q_i)^-1]_{q_i}, t v / Q = sum_i w_i t / q_i - t u
+// for an integer u, so round(t v / Q) = round(sum_i w_i t / q_i) mod t.
+__global__ void k_bfv_decode(int nq, int logN, const ModDev *__restrict__ mods, const u64 *__restrict__ tab,
+                             BfvTab bt, u64 t, const u64 *__restrict__ v, u64 *__restrict__ out) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    u64 w[BFV_MAXB];
+    for (int i = 0; i < nq; i++)
+        w[i] = mulsh(v[(size_t)i * N + c], tab[bt.qt + 2 * i], tab[bt.qt + 2 * i + 1], mods[i].q);
+    out[c] = bfv_round_sum(w, nq, tab + bt.tt, tab + bt.qd, mods, t) % t;
+}
+
+int bfv_decode(Ctx *c, const u64 *v, u64 *out) {
+    Launch t(c, K_CODEC, (double)(c->L + 1) * c->limb_bytes());
+    k_bfv_decode<<<grid_coef(c->N, 1, 1), 256, 0, c->st>>>(c->L, c->logN, c->d_mods, c->d_bfv, c->bt, c->t, v, out);
+    return cuda_check(c, "bfv_decode");
+}
+
+// Exact base conversion of each coefficient's centred value from basis X
+// (moduli x0 .. x0+nx-1) to basis Y (y0 .. y0+ny-1): w_i = [x_i (X/x_i)^-1]_{x_i},
+// v = round(sum_i w_i / x_i) (double precision), out_j = sum_i w_i [X/x_i]_{y_j}
+// - v [X]_{y_j} mod y_j -- the representative in (-X/2, X/2] unless the
+// value lies within about nx 2^-52 X of +-X/2.  xt: [nx] pairs, xd: [nx]
+// doubles, cross: [nx][ny] Montgomery, Xy: [ny].  One thread per
+// coefficient of one polynomial (grid.y).
+__global__ void k_bconv(int nx, int ny, int x0, int y0, int logN, const ModDev *__restrict__ mods,
+                        const u64 *__restrict__ xt, const u64 *__restrict__ xd, const u64 *__restrict__ cross,
+                        const u64 *__restrict__ Xy, const u64 *__restrict__ in, long long in_pstride,
+                        u64 *__restrict__ out, long long out_pstride) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const u64 *ip = in + blockIdx.y * in_pstride;
+    u64 *op = out + blockIdx.y * out_pstride;
+    u64 w[BFV_MAXB];
+    double f = 0.0;
+    for (int i = 0; i < nx; i++) {
+        w[i] = mulsh(ip[(size_t)i * N + c], xt[2 * i], xt[2 * i + 1], mods[x0 + i].q);
+        f += (double)w[i] * __longlong_as_double((long long)xd[i]);
+    }
+    const u64 v = (u64)floor(f + 0.5);
+    for (int j = 0; j < ny; j++) {
+        const ModDev M = mods[y0 + j];
+        Acc a{0, 0};
+        for (int i = 0; i < nx; i++) mac(a, w[i], cross[(size_t)i * ny + j]);
+        const u64 r = montred(a, M.q, M.qinv);
+        op[(size_t)j * N + c] = subm(r, redc64(v * Xy[j], M.q, M.barr), M.q);
+    }
+}
+
+// HE-Mult's rounding: y given by its residues over the chain (yq, nq limbs)
+// and the auxiliary base (yb, nb limbs), coefficient form; zb receives
+// round(t y / Q) over the auxiliary base.  With w_i = [y_i (Q/q_i)^-1]_{q_i}
+// and Y = sum_i w_i Q/q_i = y + u Q: round(t y / Q) = round(sum_i w_i t / q_i)
+// - t u, u = (Y - y) Q^-1 = sum_i w_i q_i^-1 - y Q^-1 mod b_j.
+__global__ void k_bfv_scale(int nq, int nb, int b0, int logN, const ModDev *__restrict__ mods,
+                            const u64 *__restrict__ tab, BfvTab bt, u64 t, const u64 *__restrict__ yq,
+                            long long yq_pstride, const u64 *__restrict__ yb, long long yb_pstride,
+                            u64 *__restrict__ zb, long long zb_pstride) {
+    const int N = 1 << logN;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const u64 *q_in = yq + blockIdx.y * yq_pstride, *b_in = yb + blockIdx.y * yb_pstride;
+    u64 *z = zb + blockIdx.y * zb_pstride;
+    u64 w[BFV_MAXB];
+    for (int i = 0; i < nq; i++)
+        w[i] = mulsh(q_in[(size_t)i * N + c], tab[bt.qt + 2 * i], tab[bt.qt + 2 * i + 1], mods[i].q);
+    const u64 r = bfv_round_sum(w, nq, tab + bt.tt, tab + bt.qd, mods, t);
+    for (int j = 0; j < nb; j++) {
+        const ModDev M = mods[b0 + j];
+        Acc a{0, 0};
+        for (int i = 0; i < nq; i++) mac(a, w[i], tab[bt.qim + (size_t)i * nb + j]);
+        const u64 y = b_in[(size_t)j * N + c];
+        const u64 u = subm(montred(a, M.q, M.qinv), mulsh(y, tab[bt.qib + 2 * j], tab[bt.qib + 2 * j + 1], M.q), M.q);
+        z[(size_t)j * N + c] = subm(redc64(r, M.q, M.barr), mulsh(u, tab[bt.tb + 2 * j], tab[bt.tb + 2 * j + 1], M.q), M.q);
+    }
+}
+
+int bfv_conv_q_to_b(Ctx *c, const u64 *in, long long in_pstride, u64 *out, long long out_pstride, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    const BfvTab &T = c->bt;
+    Launch t(c, K_CODEC, (double)npoly * (c->L + c->nb) * c->limb_bytes());
+    k_bconv<<<grid_coef(c->N, npoly, 1), 256, 0, c->st>>>(c->L, c->nb, 0, c->b0, c->logN, c->d_mods, c->d_bfv + T.qt,
+                                                           c->d_bfv + T.qd, c->d_bfv + T.qbm, c->d_bfv + T.qb, in,
+                                                           in_pstride, out, out_pstride);
+    return cuda_check(c, "bfv_conv_q_to_b");
+}
+
+int bfv_conv_b_to_q(Ctx *c, const u64 *in, long long in_pstride, u64 *out, long long out_pstride, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    const BfvTab &T = c->bt;
+    Launch t(c, K_CODEC, (double)npoly * (c->L + c->nb) * c->limb_bytes());
+    k_bconv<<<grid_coef(c->N, npoly, 1), 256, 0, c->st>>>(c->nb, c->L, c->b0, 0, c->logN, c->d_mods, c->d_bfv + T.bt,
+                                                           c->d_bfv + T.bd, c->d_bfv + T.bqm, c->d_bfv + T.bq, in,
+                                                           in_pstride, out, out_pstride);
+    return cuda_check(c, "bfv_conv_b_to_q");
+}
+
+int bfv_scale(Ctx *c, const u64 *yq, long long yq_pstride, const u64 *yb, long long yb_pstride, u64 *zb,
+              long long zb_pstride, int npoly) {
+    if (npoly <= 0) return HEGMM_OK;
+    Launch t(c, K_CODEC, (double)npoly * (c->L + 2.0 * c->nb) * c->limb_bytes());
+    k_bfv_scale<<<grid_coef(c->N, npoly, 1), 256, 0, c->st>>>(c->L, c->nb, c->b0, c->logN, c->d_mods, c->d_bfv, c->bt,
+                                                               c->t, yq, yq_pstride, yb, yb_pstride, zb, zb_pstride);
+    return cuda_check(c, "bfv_scale");
 }
 
 // ------------------------------------------------------------------ sums and pointwise ops
@@ -1641,7 +1781,7 @@ int permute_limbs(Ctx *c, int nlimb, const u64 *in, u64 *out, u32 g) {
 
 // ------------------------------------------------------------------ sampling (coefficient domain)
 
-template <int KIND>  // 0 uniform mod q (index gp N + c), 1 t * CBD(eta), 2 ternary
+template <int KIND>  // 0 uniform mod q (index gp N + c), 1 t * CBD(eta), 2 ternary, 3 CBD(eta)
 __global__ void k_sample(LimbPat p, int logN, const ModDev *__restrict__ mods, u64 stream, int eta) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1652,10 +1792,10 @@ __global__ void k_sample(LimbPat p, int logN, const ModDev *__restrict__ mods, u
     u64 v;
     if (KIND == 0) {
         v = rng_draw(stream, (u64)mi * N + c) % M.q;
-    } else if (KIND == 1) {
+    } else if (KIND == 1 || KIND == 3) {
         const long long e = cbd_sample(rng_draw(stream, (u64)c), eta);
         const u64 r = e >= 0 ? (u64)e : M.q - (u64)(-e);
-        v = mulsh(r, M.tq, M.tq_sh, M.q);
+        v = KIND == 1 ? mulsh(r, M.tq, M.tq_sh, M.q) : r;
     } else {
         const u64 r = rng_draw(stream, (u64)c) % 3;
         v = r == 0 ? M.q - 1 : (r == 1 ? 0 : 1);
@@ -1672,6 +1812,12 @@ int sample_uniform(Ctx *c, const LimbPat &p, u64 stream, const int *) {
 int sample_cbd_t(Ctx *c, const LimbPat &p, u64 stream, int eta) {
     Launch t(c, K_SAMPLE, 1.0 * p.count * c->limb_bytes());
     k_sample<1><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods, stream, eta);
+    return cuda_check(c, "sample_cbd");
+}
+
+int sample_cbd(Ctx *c, const LimbPat &p, u64 stream, int eta) {
+    Launch t(c, K_SAMPLE, 1.0 * p.count * c->limb_bytes());
+    k_sample<3><<<grid_coef(c->N, p.count, 1), 256, 0, c->st>>>(p, c->logN, c->d_mods, stream, eta);
     return cuda_check(c, "sample_cbd");
 }
 
@@ -1709,22 +1855,25 @@ int key_digit_combine(Ctx *c, u64 *kb, u64 *ka, const u64 *sprime, const u64 *d_
     return cuda_check(c, "key_combine");
 }
 
-// c0 = t e + m - a s (NTT domain), c1 = a.
+// c0 = e' + m' - a s (NTT domain), c1 = a: e' = t e and m' = m (BGV), or
+// e' = e and m' = Delta m with delta[i] = {Delta mod q_i, Shoup} (BFV).
 __global__ void k_enc_combine(int lv, int logN, const ModDev *__restrict__ mods, u64 *ct, const u64 *__restrict__ pt,
-                              const u64 *__restrict__ sR) {
+                              const u64 *__restrict__ sR, const u64 *__restrict__ delta) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int i = blockIdx.y;
     const ModDev M = mods[i];
     const size_t o0 = (size_t)i * N + c, o1 = ((size_t)lv + i) * N + c;
-    const u64 v = addm(ct[o0], pt[o0], M.q);
+    const u64 m = delta ? mulsh(pt[o0], delta[2 * i], delta[2 * i + 1], M.q) : pt[o0];
+    const u64 v = addm(ct[o0], m, M.q);
     ct[o0] = subm(v, montmul(ct[o1], sR[o0], M.q, M.qinv), M.q);
 }
 
 int encrypt_combine(Ctx *c, int lv, u64 *ct, const u64 *pt) {
     Launch t(c, K_POINTWISE, 4.0 * lv * c->limb_bytes());
-    k_enc_combine<<<grid_coef(c->N, lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, ct, pt, c->d_sR);
+    k_enc_combine<<<grid_coef(c->N, lv, 1), 256, 0, c->st>>>(lv, c->logN, c->d_mods, ct, pt, c->d_sR,
+                                                            c->bfv ? c->d_bfv + c->bt.dl : nullptr);
     return cuda_check(c, "enc_combine");
 }
 

@@ -92,7 +92,7 @@ extern "C" int hegmm_rotate_noalloc(hegmm_ctx *h, const hegmm_ct *in, int z, heg
         std::vector<int> keep, drop;
         std::vector<u64> t = modup_table_host(c, lv);
         const size_t first = t.size();
-        const std::vector<u64> dv = div_table_host(c, lv, 0, keep, drop);
+        const std::vector<u64> dv = div_table_host(c, lv, c->bfv ? 2 : 0, keep, drop);
         t.insert(t.end(), dv.begin(), dv.end());
         // the kernels read modulus indices from the ModDown table: check
         // where they sit before the table goes to the device

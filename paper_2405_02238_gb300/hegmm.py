@@ -43,6 +43,7 @@ class hegmm_params(ctypes.Structure):
         ("alpha", ctypes.c_int),
         ("eta", ctypes.c_int),
         ("ms_drop", ctypes.c_int),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -257,9 +258,9 @@ def _ptr(a: np.ndarray, t=u64p):
 class Context:
     """Owns one hegmm_ctx; methods are thin wrappers of the C entry points."""
 
-    def __init__(self, logN, t, L, qbits, K, alpha, eta=21, ms_drop=0, stream=None):
+    def __init__(self, logN, t, L, qbits, K, alpha, eta=21, ms_drop=0, stream=None, scheme=0):
         self.lib = load()
-        self.params = hegmm_params(logN, t, L, qbits, K, alpha, eta, ms_drop)
+        self.params = hegmm_params(logN, t, L, qbits, K, alpha, eta, ms_drop, scheme)
         if stream is None:
             import torch
 
@@ -279,7 +280,7 @@ class Context:
 
     @classmethod
     def from_preset(cls, p, stream=None):
-        return cls(p.logN, p.t, p.L, p.qbits, p.K, p.alpha, p.eta, p.ms_drop, stream)
+        return cls(p.logN, p.t, p.L, p.qbits, p.K, p.alpha, p.eta, p.ms_drop, stream, getattr(p, "scheme", 0))
 
     def close(self):
         if getattr(self, "h", None):
