@@ -723,6 +723,8 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
     ctx = H.Context.from_preset(pre, stream=stream.cuda_stream)
     ks_code = KS_MODES
     ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
+    if args.giant_cost:
+        ctx.hegmm_set_tuning(H.TUNE_GIANT_COST, args.giant_cost)
     prods = []
     if kind == "batch":
         for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
@@ -959,6 +961,9 @@ def main():
     ap.add_argument("--mask-gib", type=int, default=190, help="resident mask budget for the serve workload")
     ap.add_argument("--max-batch", type=int, default=64)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning instead of hegmm_autotune")
+    ap.add_argument("--giant-cost", type=int, default=0,
+                    help="HEGMM_TUNE_GIANT_COST of the shared-baby-step order (0: the library default, 8); it selects "
+                         "the factorisation, so it changes the ciphertext bits")
     ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
                     help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
@@ -995,6 +1000,7 @@ def main():
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": cfg({"parallelism": "replicas" if world > 1 else "single-gpu", "keyswitch_mode": args.ks_mode,
+                       "giant_cost": args.giant_cost or 8,
                        "tuning": r["tuning"],
                        "algorithms": {"%dx%dx%d" % p[:3]: p[3] for p in r["prods"]} if kind != "batch" else "AUTO"}),
     }
