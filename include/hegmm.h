@@ -444,6 +444,11 @@ typedef struct {
 typedef struct {
     long long submitted, completed, failed, batches, queued, in_flight, max_batch;
     double p50_ms, p99_ms, mean_ms, max_ms; /* submit-to-completion latency */
+    long long max_batches_in_flight;        /* most batches launched and not yet retired at once */
+    long long overlapped_batches;           /* retired batches whose device interval (from a timed event
+                                               before its first launch to one after its last, on its
+                                               stream) intersected that of a batch on another stream;
+                                               each is compared with the 64 batches retired before it */
 } hegmm_server_stats;
 
 int hegmm_server_create(hegmm_ctx *ctx, const hegmm_server_opts *opts, hegmm_server **out);
@@ -494,8 +499,9 @@ int hegmm_modswitch(hegmm_ctx *ctx, const hegmm_ct *ct, hegmm_ct **out);        
  * inside the library, which every GPU that loads the library keeps until the
  * process exits; parameter sets whose rotation needs more scratch than that
  * are rejected with HEGMM_EINVAL and a message.  The first call on a device
- * looks up that array's device address (with that device current); make
- * this first call before any stream capture.  Every call reuses the same
+ * looks up that array's device address (with that device current); a call
+ * while the context's stream is capturing is refused with HEGMM_EINVAL, as
+ * is a device ordinal beyond the library's table.  Every call reuses the same
  * array and leaves its contents behind (nothing in it needs clearing: each
  * call writes every word it reads), so calls whose GPU work overlaps -- on
  * different streams, contexts or threads -- race and give wrong results.

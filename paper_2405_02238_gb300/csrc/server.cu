@@ -40,11 +40,18 @@ struct SrvReq {
 
 struct SrvBatch {
     int stream;
-    cudaEvent_t done;
+    cudaEvent_t start, done;  // timed: the batch's first and last point on its stream
     std::vector<SrvReq> reqs;
     std::vector<hegmm_ct *> outs;
     std::vector<BatchPlan *> plans;  // one per algorithm group of the batch
     size_t bytes;
+};
+
+// A retired batch's device interval, in ms after the server's origin event.
+struct SrvSpan {
+    double t0, t1;
+    int stream;
+    bool overlapped;
 };
 
 struct SrvDone {
@@ -63,6 +70,9 @@ struct hegmm_server {
     std::vector<char *> arena;  // per stream: workspace of its current batch
     size_t arena_cap = 0;
     cudaEvent_t inputs_ready = nullptr;
+    cudaEvent_t origin = nullptr;  // timed, recorded at creation
+    std::deque<hg::SrvSpan> spans;  // the most recent retired batches' intervals
+    long long max_flight = 0, overlapped = 0;
     std::deque<hg::SrvReq> queue;
     std::vector<hg::SrvBatch> flight;
     std::map<uint64_t, hg::SrvDone> done;
@@ -86,6 +96,24 @@ static int retire(hegmm_server *s, bool block) {
         }
         if (q != cudaSuccess) return cuda_check(s->c, "server batch");
         const double t = now_ms();
+        // The batch's device interval, and whether it intersects that of
+        // another stream's batch: both were then queued on the device at once.
+        float a = 0.f, e = 0.f;
+        if (cudaEventElapsedTime(&a, s->origin, b.start) == cudaSuccess &&
+            cudaEventElapsedTime(&e, s->origin, b.done) == cudaSuccess) {
+            SrvSpan sp{a, e, b.stream, false};
+            for (SrvSpan &o : s->spans)
+                if (o.stream != sp.stream && sp.t0 < o.t1 && o.t0 < sp.t1) {
+                    if (!o.overlapped) s->overlapped++;
+                    o.overlapped = true;
+                    if (!sp.overlapped) s->overlapped++;
+                    sp.overlapped = true;
+                }
+            s->spans.push_back(sp);
+            if (s->spans.size() > 64) s->spans.pop_front();
+        } else {
+            cudaGetLastError();
+        }
         for (size_t k = 0; k < b.reqs.size(); k++) {
             const double lm = t - b.reqs[k].t_submit;
             s->done[b.reqs[k].id] = {b.outs[k], lm, HEGMM_OK};
@@ -97,6 +125,7 @@ static int retire(hegmm_server *s, bool block) {
         for (BatchPlan *p : b.plans) release_plan(s->c, p);
         s->c->st = old;
         cudaEventDestroy(b.done);
+        cudaEventDestroy(b.start);
         s->inflight_bytes -= b.bytes;
         s->busy[b.stream] = 0;
         s->flight.erase(s->flight.begin() + (long)i);
@@ -143,6 +172,9 @@ static int admit(hegmm_server *s) {
         c->arena_cap = s->arena_cap;
         c->arena_used = 0;
         cudaStreamWaitEvent(c->st, s->inputs_ready, 0);
+        SrvBatch sb;
+        cudaEventCreate(&sb.start);
+        cudaEventRecord(sb.start, c->st);
         // one executor call for the whole batch; each request carries its
         // resolved algorithm
         std::vector<int> algs;
@@ -153,10 +185,9 @@ static int admit(hegmm_server *s) {
                             outs.data(), nullptr, false, &plan);
         if (!rc) plans.push_back(plan);
         c->arena = nullptr;
-        SrvBatch sb;
         sb.stream = st;
         sb.bytes = bytes;
-        cudaEventCreateWithFlags(&sb.done, cudaEventDisableTiming);
+        cudaEventCreate(&sb.done);
         cudaEventRecord(sb.done, c->st);
         c->st = old;
         if (rc) {
@@ -166,6 +197,7 @@ static int admit(hegmm_server *s) {
                 c->st = old;
             }
             cudaEventDestroy(sb.done);
+            cudaEventDestroy(sb.start);
             for (size_t k = 0; k < reqs.size(); k++) {
                 hegmm_ct_destroy(outs[k]);
                 s->done[reqs[k].id] = {nullptr, 0.0, rc};
@@ -181,6 +213,7 @@ static int admit(hegmm_server *s) {
         s->batches++;
         s->max_batch_seen = std::max<long long>(s->max_batch_seen, (long long)reqs.size());
         s->flight.push_back(sb);
+        s->max_flight = std::max<long long>(s->max_flight, (long long)s->flight.size());
         launched++;
     }
     return launched;
@@ -220,6 +253,8 @@ int hegmm_server_create(hegmm_ctx *h, const hegmm_server_opts *opts, hegmm_serve
         s->arena.push_back((char *)a);
     }
     cudaEventCreateWithFlags(&s->inputs_ready, cudaEventDisableTiming);
+    cudaEventCreate(&s->origin);
+    cudaEventRecord(s->origin, c->st);
     cudaStreamSynchronize(c->st);  // keys and tables are complete before other streams use them
     *out = s;
     return cuda_check(c, "server create");
@@ -292,6 +327,8 @@ int hegmm_server_stats_get(hegmm_server *s, hegmm_server_stats *st) {
     for (double x : v) sum += x;
     st->mean_ms = v.empty() ? 0.0 : sum / v.size();
     st->max_ms = v.empty() ? 0.0 : v.back();
+    st->max_batches_in_flight = s->max_flight;
+    st->overlapped_batches = s->overlapped;
     return HEGMM_OK;
 }
 
@@ -305,6 +342,7 @@ void hegmm_server_destroy(hegmm_server *s) {
     }
     for (char *a : s->arena) cudaFreeAsync(a, s->c->st);
     cudaEventDestroy(s->inputs_ready);
+    cudaEventDestroy(s->origin);
     delete s;
 }
 

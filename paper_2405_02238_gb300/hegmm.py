@@ -62,7 +62,8 @@ class hegmm_server_opts(ctypes.Structure):
 class hegmm_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in
                 ("submitted", "completed", "failed", "batches", "queued", "in_flight", "max_batch")] + \
-               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms")]
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "mean_ms", "max_ms")] + \
+               [(n, ctypes.c_longlong) for n in ("max_batches_in_flight", "overlapped_batches")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

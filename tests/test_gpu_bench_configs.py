@@ -34,9 +34,10 @@ CASES = [("medium", 16, 32, 24, 1), ("medium", 32, 8, 48, 1), ("medium", 16, 32,
          ("paper", 32, 128, 16, 3)]
 KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
 BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
-# (LT kernel variant, entries per item, one-output kernel): the autotuner's
-# usual choice, the library default, and a plain-load variant
-KNOBS = [(7, 32, 0), (6, 32, 0), (0, 64, 2)]
+# (LT kernel variant, entries per item, one-output kernel, NTT threads): the
+# autotuner's usual choice, the library default, the persistent kernel with
+# the 512-thread NTT form, and a plain-load variant
+KNOBS = [(7, 32, 0, 0), (6, 32, 0, 0), (8, 32, 0, 512), (0, 64, 2, 0)]
 
 
 @pytest.fixture(scope="module")
@@ -61,10 +62,11 @@ def context(H, name):
 
 
 def set_knobs(H, ctx, knobs):
-    v, ch, one = knobs
+    v, ch, one, nt = knobs
     ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, v)
     ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, ch)
     ctx.hegmm_set_tuning(H.TUNE_LT_ONE, one)
+    ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, nt)
 
 
 def gpu_product(H, name, m, l, n, alg, mode=BENCH_MODE):
@@ -87,7 +89,7 @@ def test_benchmarked_products_match_the_oracle_digests(H, case_args):
     name, m, l, n, alg = case_args
     key = "%s %dx%dx%d alg %d double+lazy+shared" % case_args
     case = json.load(open(DIGEST_FILE))["cases"][key]
-    knob_sets = KNOBS if name == "medium" else KNOBS[:2]
+    knob_sets = KNOBS if name == "medium" else KNOBS[:3]
     try:
         for knobs in knob_sets:
             ctx = context(H, name)
@@ -100,7 +102,7 @@ def test_benchmarked_products_match_the_oracle_digests(H, case_args):
                 assert int(flat[i]) == v, (key, knobs, i)
             assert hashlib.sha256(ct.tobytes()).hexdigest() == case["sha256"], (key, knobs)
     finally:
-        set_knobs(H, context(H, name), (6, 32, 0))
+        set_knobs(H, context(H, name), KNOBS[1])
 
 
 MODES = {"single": (0, "single", False, False), "double": (1, "double", False, False),

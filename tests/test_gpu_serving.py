@@ -69,6 +69,63 @@ def test_serving_mix_equals_alone(H):
     srv.close()
 
 
+def test_serving_batches_overlap_on_the_device(H):
+    """Two streams, batches of two medium products: with the plans cached by
+    a first pass, the second stream's batch is launched while the first
+    one's products still run, so their device intervals intersect."""
+    pre = W.MEDIUM
+    ctx = H.Context.from_preset(pre)
+    shapes = [(16, 32, 24)] * 8
+    ctx.hegmm_keygen(SEED, shapes[:1])
+    reqs = make_requests(ctx, H, pre, shapes, -8, 7, 700)
+    for rnd in range(2):  # the first round builds and caches the batch plans
+        srv = H.Server(ctx, max_batch=2, streams=2)
+        tickets = [srv.hegmm_server_submit(ca, cb, m, l, n) for (m, l, n), _, _, ca, cb in reqs]
+        srv.hegmm_server_poll(wait=True)
+        st = srv.hegmm_server_stats_get()
+        assert st["completed"] == len(reqs) and st["batches"] == 4
+        outs = [srv.hegmm_server_result(t)[0] for t in tickets]
+        srv.close()
+    assert st["max_batches_in_flight"] == 2
+    assert st["overlapped_batches"] >= 2, st
+    ref, _ = ctx.hegmm_matmul(reqs[0][3], reqs[0][4], 16, 32, 24)
+    for ((m, l, n), A, B, ca, cb), c in zip(reqs, outs):
+        assert (ctx.hegmm_decrypt(c, m, l, n).astype(np.int64) == (A @ B) % pre.t).all()
+    assert (ctx.hegmm_ct_export(outs[0]) == ctx.hegmm_ct_export(ref)).all()
+
+
+def test_serving_paper_ring(H):
+    """The serving mix at N = 2^14 (small, medium and 128x16x64 requests):
+    every result decrypts to A.B mod t and equals the product alone."""
+    pre = W.PAPER
+    ctx = H.Context.from_preset(pre)
+    arrivals = W.serving_requests(24, 200.0, ctx.S, seed=5)
+    shapes = [s for _, s in arrivals]
+    if (128, 16, 64) not in shapes:
+        shapes[-1] = (128, 16, 64)
+    ctx.hegmm_keygen(SEED, shapes)
+    reqs = make_requests(ctx, H, pre, shapes, *W.PAPER_RANGE, 800)
+    srv = H.Server(ctx, max_batch=8, streams=2)
+    t0 = time.perf_counter()
+    tickets = []
+    for (at, _), ((m, l, n), _, _, ca, cb) in zip(arrivals, reqs):
+        while time.perf_counter() - t0 < at:
+            srv.hegmm_server_poll()
+        tickets.append(srv.hegmm_server_submit(ca, cb, m, l, n))
+        srv.hegmm_server_poll()
+    srv.hegmm_server_poll(wait=True)
+    st = srv.hegmm_server_stats_get()
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["batches"] >= 2
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    for i, (t, ((m, l, n), A, B, ca, cb)) in enumerate(zip(tickets, reqs)):
+        c, _ = srv.hegmm_server_result(t)
+        assert (ctx.hegmm_decrypt(c, m, l, n).astype(np.int64) == (A @ B) % pre.t).all(), (m, l, n)
+        if i % 4 == 0 or (m, l, n) == (128, 16, 64):
+            alone, _ = ctx.hegmm_matmul(ca, cb, m, l, n)
+            assert (ctx.hegmm_ct_export(c) == ctx.hegmm_ct_export(alone)).all(), (m, l, n)
+    srv.close()
+
+
 def test_serving_poisson_medium(H):
     pre = W.MEDIUM
     ctx = H.Context.from_preset(pre)
