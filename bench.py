@@ -40,7 +40,7 @@ import workload as W  # noqa: E402
 
 METRIC = "HEGMM encrypted matmuls/s (N=8192 ring, 16x32x24 + 32x8x48, Alg 1 + Alg 2)"
 METRIC_BATCH = "HEGMM encrypted matmuls/s (batch of 512 mixed shapes, N=8192 ring)"
-METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 128x16x64, AUTO algorithm)"
+METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 128x16x64)"
 UNIT = "matmul/s"
 KEY_SEED = 7
 SERVE_ARENA_GIB = 16  # server workspace, split over its streams
@@ -612,6 +612,68 @@ def kernel_source_sha():
     return h.hexdigest()[:12]
 
 
+# The library's kernel buckets (hegmm_kernel_stats) of the CUDA kernels an
+# ncu log names, first match wins.
+NCU_BUCKETS = [("k_ntt<", lambda n: "ntt_inv" if n.split("<")[1].split(",")[1].strip() in ("1", "true") else "ntt_fwd"),
+               ("k_modup_", "modup"), ("k_divround_ntt", "divround_ntt"), ("k_ksw_ip", "ksw_inner_product"),
+               ("k_lt_grp", "lt_keyswitch"), ("k_lt_acc", "lt_accumulate"), ("k_tensor", "tensor"),
+               ("k_sum", "sum")]
+NCU_UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "inst": 1, "Kinst": 1e3, "Minst": 1e6,
+             "Ginst": 1e9, "": 1}
+
+
+def ncu_bucket(kernel_name):
+    name = kernel_name.split("(")[0].replace("void ", "").replace("hg::", "").strip()
+    for prefix, b in NCU_BUCKETS:
+        if name.startswith(prefix):
+            return b(name) if callable(b) else b
+    return None
+
+
+def ingest_ncu(pairs):
+    """Per kernel bucket, summed over the given product runs: DRAM bytes
+    (read + write) over the library's algorithmic bytes, and warp-
+    instructions over butterflies; written with the hash of the kernel
+    sources to profiles/ncu_traffic.json, which the roofline entries read."""
+    import csv
+    import io
+
+    sums = {}
+    for pair in pairs:
+        csv_path, json_path = pair.split(":")
+        txt = open(csv_path).read()
+        rows = list(csv.DictReader(io.StringIO(txt[txt.index('"ID"'):])))
+        for r in rows:
+            b = ncu_bucket(r["Kernel Name"])
+            if b is None:
+                continue
+            if r["Metric Name"] not in ("dram__bytes_read.sum", "dram__bytes_write.sum", "smsp__inst_executed.sum"):
+                continue
+            v = float(r["Metric Value"].replace(",", "")) * NCU_UNITS[r["Metric Unit"]]
+            d = sums.setdefault(b, {"dram": 0.0, "inst": 0.0, "bytes": 0.0, "bfly": 0.0})
+            if r["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                d["dram"] += v
+            elif r["Metric Name"] == "smsp__inst_executed.sum":
+                d["inst"] += v
+        line = [ln for ln in open(json_path).read().splitlines() if ln.startswith("{")][-1]
+        for b, k in json.loads(line)["kernels"].items():
+            if b in sums:
+                sums[b]["bytes"] += k["algorithmic_bytes"]
+                sums[b]["bfly"] += k["butterflies"]
+    out = {"kernels_sha": kernel_source_sha(),
+           "traffic_per_algorithmic_byte": {b: round(d["dram"] / d["bytes"], 4) for b, d in sorted(sums.items())
+                                            if d["bytes"] > 0 and d["dram"] > 0},
+           "warp_inst_per_butterfly": {b: round(d["inst"] / d["bfly"], 4) for b, d in sorted(sums.items())
+                                       if d["bfly"] > 0 and d["inst"] > 0},
+           "source": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,smsp__inst_executed.sum of the timed "
+                     "launches of: " + "; ".join(os.path.basename(p.split(":")[1]) for p in pairs) +
+                     " (bench.py --workload product runs); sha over csrc/kernels.cu and csrc/device.cuh"}
+    with open(COUNTERS, "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps(out))
+
+
 def run_product(args):
     """One product of --shape on the --ring preset (medium by default), run
     once and then --reps times; prints the per-kernel times of the repeated
@@ -635,6 +697,8 @@ def run_product(args):
         ctx.hegmm_set_tuning(H.TUNE_LT_ONE, args.lt_one)
     if args.lt_chunk >= 0:
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, args.lt_chunk)
+    if args.ntt_threads >= 0:
+        ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, args.ntt_threads)
     m, l, n = (int(v) for v in args.shape.lower().split("x"))
     A, Bm = W.matrices(m, l, n, *(W.PAPER_RANGE if args.ring == "paper" else W.MEDIUM_RANGE))
     ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
@@ -778,10 +842,11 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
     # workload, unless they are given (a profiler's serialised launches would
     # mislead the autotuner: profiling runs pass the plain run's choice)
     tuning = None
-    fixed = {k: v for k, v in (("lt_kernel", args.lt_kernel), ("lt_chunk", args.lt_chunk), ("lt_one", args.lt_one))
-             if v >= 0}
+    fixed = {k: v for k, v in (("lt_kernel", args.lt_kernel), ("lt_chunk", args.lt_chunk), ("lt_one", args.lt_one),
+                               ("ntt_threads", args.ntt_threads)) if v >= 0}
     if fixed:
-        knob = {"lt_kernel": H.TUNE_LT_KERNEL, "lt_chunk": H.TUNE_LT_CHUNK, "lt_one": H.TUNE_LT_ONE}
+        knob = {"lt_kernel": H.TUNE_LT_KERNEL, "lt_chunk": H.TUNE_LT_CHUNK, "lt_one": H.TUNE_LT_ONE,
+                "ntt_threads": H.TUNE_NTT_THREADS}
         for k, v in fixed.items():
             ctx.hegmm_set_tuning(knob[k], v)
         tuning = dict(fixed, given=True)
@@ -955,6 +1020,13 @@ def main():
     ap.add_argument("--reps", type=int, default=1, help="--workload product: timed products after the first")
     ap.add_argument("--lt-one", type=int, default=-1,
                     help="HEGMM_TUNE_LT_ONE one-output kernel (-1: autotuned, or the default for --workload product)")
+    ap.add_argument("--ntt-threads", type=int, default=-1,
+                    help="HEGMM_TUNE_NTT_THREADS (0 by launch size, 512, 1024; -1: autotuned, or the library's choice "
+                         "for --workload product)")
+    ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV:JSON",
+                    help="write profiles/ncu_traffic.json for the current kernel sources from ncu CSV logs "
+                         "(dram__bytes_read.sum, dram__bytes_write.sum, smsp__inst_executed.sum of the timed "
+                         "launches of --workload product runs) and the JSON lines those runs printed")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--max-requests", type=int, default=1000)
@@ -967,6 +1039,8 @@ def main():
     ap.add_argument("--ks-mode", default="double+lazy+shared", choices=list(KS_MODES),
                     help="evaluation order of the key switches in a product (hegmm_set_keyswitch_mode)")
     args = ap.parse_args()
+    if args.ingest_ncu:
+        return ingest_ncu(args.ingest_ncu)
     if args.impl == "reference":
         return run_reference(args)
     single_gpu = {"serve": run_serve, "product": run_product, "blocked": run_blocked}
