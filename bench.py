@@ -73,32 +73,59 @@ def shared_keyswitches(H, m, l, n, alg, slots):
     return ksw
 
 
+def fewest_keyswitch_plan(H, m, l, n, slots):
+    """(alg, blocks) of a product: of Algorithm 2, Algorithm 1 with the
+    extended pre-layout and Algorithm 1 (in that order of preference), the
+    one that fits and executes the fewest key switches in the
+    shared-baby-step order; and where Algorithm 2 does not fit the slots,
+    also Algorithm 2 on the fewest equal l-blocks that fit, summed
+    (C = sum_k A_k B_k, Section 4.4's split; the client encodes each block
+    pair for Algorithm 2)."""
+    cands = []
+    for order, alg in enumerate((2, 3, 1)):
+        try:
+            cands.append((shared_keyswitches(H, m, l, n, alg, slots), order, alg, 1))
+        except Exception:
+            continue  # does not fit
+    if not any(c[2] == 2 for c in cands):
+        for b in range(2, l + 1):
+            if l % b:
+                continue
+            try:
+                cands.append((b * shared_keyswitches(H, m, l // b, n, 2, slots), 3, 2, b))
+                break
+            except Exception:
+                continue
+    best = min(cands)
+    return best[2], best[3]
+
+
 def fewest_keyswitch_alg(H, m, l, n, slots):
-    """Of Algorithm 2, Algorithm 1 with the extended pre-layout and
-    Algorithm 1 (in that order of preference), the one that fits the slots
-    and executes the fewest key switches in the shared-baby-step order."""
+    """The algorithm of fewest_keyswitch_plan among unblocked plans."""
     best = None
     for alg in (2, 3, 1):
         try:
             k = shared_keyswitches(H, m, l, n, alg, slots)
         except Exception:
-            continue  # does not fit
+            continue
         if best is None or k < best[1]:
             best = (alg, k)
     return best[0]
 
 
-def workload_products(kind, H=None, slots=None):
-    """[(m, l, n, alg)] of a throughput workload (alg 0 = AUTO).  The
-    paper-scale products take, per shape, the algorithm with the fewest
-    executed key switches (fewest_keyswitch_alg) when the library is at
-    hand (H), else AUTO."""
+def workload_products(kind, H=None, slots=None, blocks=True):
+    """[(m, l, n, alg, blocks)] of a throughput workload (alg 0 = AUTO).  The
+    paper-scale products take, per shape, the plan with the fewest executed
+    key switches (fewest_keyswitch_plan; blocks=False: unblocked plans only)
+    when the library is at hand (H), else AUTO."""
     if kind == "paper":
         if H is None:
-            return [(m, l, n, 0) for (m, l, n) in W.PAPER_SHAPES]
-        return [(m, l, n, fewest_keyswitch_alg(H, m, l, n, slots)) for (m, l, n) in W.PAPER_SHAPES]
+            return [(m, l, n, 0, 1) for (m, l, n) in W.PAPER_SHAPES]
+        if not blocks:
+            return [(m, l, n, fewest_keyswitch_alg(H, m, l, n, slots), 1) for (m, l, n) in W.PAPER_SHAPES]
+        return [(m, l, n) + fewest_keyswitch_plan(H, m, l, n, slots) for (m, l, n) in W.PAPER_SHAPES]
     if kind == "medium":
-        return [(m, l, n, a) for (m, l, n) in W.MEDIUM_SHAPES for a in (1, 2)]
+        return [(m, l, n, a, 1) for (m, l, n) in W.MEDIUM_SHAPES for a in (1, 2)]
     raise ValueError(kind)
 
 
@@ -123,12 +150,15 @@ def workload_config(extra=None):
 def paper_config(extra=None):
     cfg = {
         "workload": "paper: N=16384, t=65537, 8x50-bit + 2 special primes, dnum=4; A64x64.B64x64, A32x128.B128x16 "
-                    "(Algorithm 2 would need 16384 > 8192 slots), A128x16.B16x64; per shape the algorithm (2, 1 with "
-                    "the extended pre-layout = 3, or 1) with the fewest executed key switches (see algorithms); "
-                    "entries U[0,255] seed 0; one hegmm_matmul_batch_algs call per step; per_product_path = the "
-                    "plain one-product-per-launch path",
+                    "(Algorithm 2 would need 16384 > 8192 slots), A128x16.B16x64; per shape the plan with the fewest "
+                    "executed key switches (see algorithms): Algorithm 2, 1 with the extended pre-layout (3) or 1, "
+                    "or, where Algorithm 2 does not fit, Algorithm 2 on the fewest equal l-blocks that fit, summed "
+                    "(Section 4.4's split; the client encrypts each block pair); entries U[0,255] seed 0; one "
+                    "hegmm_matmul_sum (or hegmm_matmul_batch_algs when nothing is blocked) call per step; "
+                    "per_product_path = the plain one-product-per-launch path (hegmm_matmul per block, hegmm_add); "
+                    "unblocked_plans = the same products with one ciphertext per matrix",
         "products_per_step": len(W.PAPER_SHAPES),
-        "l2": "flushed between timed steps (256 MiB write); per-step key working set (about 19 GB) >> L2",
+        "l2": "flushed between timed steps (256 MiB write); per-step key working set (key_bytes) >> L2",
         "launch": "the cached plan replayed as one CUDA graph; per-kernel times from a second pass of the same "
                   "steps launched kernel by kernel with CUDA events on the library stream",
     }
@@ -218,7 +248,8 @@ def oracle_sample(prods, preset, nrot=6, ncm=6, nmul=2):
     measured time of each op.  The sample runs ``nrot`` rotations (cycling
     over SAMPLE_KEYS offsets), ``ncm`` mask products and additions and
     ``nmul`` relinearised products at the workload's parameters; key
-    generation is excluded.  prods: [(m, l, n, alg)], alg 0 = AUTO.
+    generation is excluded.  prods: [(m, l, n, alg[, blocks])], alg 0 =
+    AUTO; a product of b blocks runs b products of l / b and b - 1 adds.
     Returns (extrapolated seconds per workload step, description, seconds
     the sample itself took).
     """
@@ -255,10 +286,13 @@ def oracle_sample(prods, preset, nrot=6, ncm=6, nmul=2):
     t_mul = (time.perf_counter() - t0) / nmul
     sample_s = time.perf_counter() - s0
     total = 0.0
-    for (m, l, n, alg) in prods:
-        a = alg if alg else SL.choose_alg(m, l, n, o.S)
-        c = SL.make_plan(m, l, n, a).counts()
-        total += c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add)
+    for pr in prods:
+        m, l, n, alg = pr[:4]
+        nb = pr[4] if len(pr) > 4 else 1
+        a = alg if alg else SL.choose_alg(m, l // nb, n, o.S)
+        c = SL.make_plan(m, l // nb, n, a).counts()
+        total += nb * (c["rot"] * t_rot + c["cmult"] * (t_cm + t_add) + c["mult"] * (t_mul + t_add))
+        total += (nb - 1) * t_add  # the block sum
     desc = ("%d rotations, %d mask products + adds, %d relinearised products at N=%d/L=%d timed (%.1f s); "
             "per-step time = op counts of the %d plans (the oracle's single-mode op sequence) x measured op times "
             "(%.1f/%.2f/%.2f/%.1f ms rot/cmult/add/mult); keygen excluded"
@@ -789,37 +823,65 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
     ctx.hegmm_set_keyswitch_mode(ks_code[args.ks_mode])
     if args.giant_cost:
         ctx.hegmm_set_tuning(H.TUNE_GIANT_COST, args.giant_cost)
-    prods = []
+    prods = []  # (m, l, n, alg, blocks, A, B)
     if kind == "batch":
         for i, (m, l, n) in enumerate(W.batch_shapes(W.BATCH_COUNT, ctx.S)):
             A, Bm = W.matrices(m, l, n, *W.BATCH_RANGE, seed=i)
-            prods.append((m, l, n, H.ALG_AUTO, A, Bm))
+            prods.append((m, l, n, H.ALG_AUTO, 1, A, Bm))
         rng = W.BATCH_RANGE
     else:
         rng = W.PAPER_RANGE if kind == "paper" else W.MEDIUM_RANGE
-        for (m, l, n, alg) in workload_products(kind, None if args.paper_auto else H, ctx.S):
+        for (m, l, n, alg, nb) in workload_products(kind, None if args.paper_auto else H, ctx.S,
+                                                    blocks=not args.no_blocks):
             A, Bm = W.matrices(m, l, n, *rng)
-            prods.append((m, l, n, alg, A, Bm))
-    for alg in sorted({p[3] for p in prods}):
-        ctx.hegmm_keygen(KEY_SEED, [p[:3] for p in prods if p[3] == alg], alg)
+            prods.append((m, l, n, alg, nb, A, Bm))
+    # the products the library runs: a product of b blocks is b products of
+    # l / b (A's column blocks times B's row blocks), summed
+    units, group = [], []  # (m, l / b, n, alg, A_k, B_k), the product each belongs to
+    for i, (m, l, n, alg, nb, A, Bm) in enumerate(prods):
+        lb = l // nb
+        for k in range(nb):
+            units.append((m, lb, n, alg, A[:, k * lb:(k + 1) * lb], Bm[k * lb:(k + 1) * lb, :]))
+            group.append(i)
+    blocked = any(p[4] > 1 for p in prods)
+    for alg in sorted({u[3] for u in units}):
+        ctx.hegmm_keygen(KEY_SEED, [u[:3] for u in units if u[3] == alg], alg)
     ops = []
-    for i, (m, l, n, alg, A, Bm) in enumerate(prods):
+    for i, (m, l, n, alg, A, Bm) in enumerate(units):
         ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), 1 + rank, 2 * i)
         cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bm, m, l, n, alg), 1 + rank, 2 * i + 1)
         ops.append((ca, cb))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    algs = [p[3] for p in prods]
+    algs = [u[3] for u in units]
+    ushapes = [u[:3] for u in units]
+    first_unit = [group.index(i) for i in range(len(prods))]
+
+    def run(A_cts, B_cts):
+        """Every product of the workload in one call: hegmm_matmul_batch_algs,
+        or hegmm_matmul_sum when a product is blocked (one result each)."""
+        if blocked:
+            return ctx.hegmm_matmul_sum(A_cts, B_cts, ushapes, group, len(prods), algs)
+        return ctx.hegmm_matmul_batch_algs(A_cts, B_cts, ushapes, algs)
 
     def step():  # one step = every product of the workload in one call
-        return ctx.hegmm_matmul_batch_algs([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs)
+        return run([a for a, _ in ops], [b for _, b in ops])
 
     def single_path(sample):
-        """The plain path: one hegmm_matmul call per product."""
+        """The plain path: one hegmm_matmul call per product (per block, and
+        hegmm_add for the block sums)."""
         outs = []
         for i in sample:
-            (m, l, n, alg, _, _), (ca, cb) = prods[i], ops[i]
-            outs.append(ctx.hegmm_matmul(ca, cb, m, l, n, alg)[0])
+            c = None
+            for u in (j for j in range(len(units)) if group[j] == i):
+                m, l, n, alg = units[u][:4]
+                r = ctx.hegmm_matmul(ops[u][0], ops[u][1], m, l, n, alg)[0]
+                c = r if c is None else ctx.hegmm_add(c, r)
+            outs.append(c)
         return outs
+
+    def decrypt(i, c, pair=False):
+        m, l, n, alg = units[first_unit[i]][:4]
+        return (ctx.hegmm_decrypt_pair if pair else ctx.hegmm_decrypt)(c, m, l, n, alg)
 
     def timed(fn, steps):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -834,8 +896,8 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
         return [a.elapsed_time(b) for a, b in ev]
 
     def check(outs, what):
-        for (m, l, n, alg, A, Bm), c in zip(prods, outs):
-            got = ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64)
+        for i, ((m, l, n, alg, nb, A, Bm), c) in enumerate(zip(prods, outs)):
+            got = decrypt(i, c).astype(np.int64)
             assert (got == (A @ Bm) % pre.t).all(), "wrong product %dx%dx%d alg %d (%s)" % (m, l, n, alg, what)
 
     # the library's autotuner picks the bit-neutral kernel knobs on this
@@ -851,8 +913,8 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
             ctx.hegmm_set_tuning(knob[k], v)
         tuning = dict(fixed, given=True)
     elif not args.no_autotune:
-        tuning = ctx.hegmm_autotune([a for a, _ in ops], [b for _, b in ops], [p[:3] for p in prods], algs,
-                                    reps=3 if len(prods) <= 64 else 1)
+        tuning = ctx.hegmm_autotune([a for a, _ in ops], [b for _, b in ops], ushapes, algs,
+                                    reps=3 if len(units) <= 64 else 1)
     for _ in range(max(args.warmup, 1)):  # builds plans and masks, captures graphs
         outs = step()
     check(outs, args.ks_mode)
@@ -860,10 +922,10 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
     sample = list(range(len(prods))) if len(prods) <= 8 else list(range(0, len(prods), len(prods) // 32))
     check_sample = single_path(sample)
     for i, c in zip(sample, check_sample):
-        m, l, n, alg, A, Bm = prods[i]
-        assert (ctx.hegmm_decrypt(c, m, l, n, alg).astype(np.int64) == (A @ Bm) % pre.t).all()
+        A, Bm = prods[i][5:]
+        assert (decrypt(i, c).astype(np.int64) == (A @ Bm) % pre.t).all()
     del check_sample
-    sc = [H.hegmm_plan_counts(m, l, n, alg if alg else 0, ctx.S) for (m, l, n, alg, _, _) in prods]
+    sc = [H.hegmm_plan_counts(m, l, n, alg if alg else 0, ctx.S) for (m, l, n, alg, _, _) in units]
     for _ in range(2):
         single_path(sample)
     single_ms = sum(timed(lambda: single_path(sample), 3)) / 3
@@ -919,20 +981,22 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
         # two products per ciphertext pair (slot rows 0 and 1): every product of
         # the workload with a second one of its shape, the same launches per step
         pk_ops, pk_mats = [], []
-        for i, (m, l, n, alg, A, Bm) in enumerate(prods):
-            A2, B2 = W.matrices(m, l, n, *rng, seed=1000 + i)
-            pa = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_A, A, A2, m, l, n, alg), 1 + rank, 2 * i)
-            pb = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_B, Bm, B2, m, l, n, alg), 1 + rank, 2 * i + 1)
+        for i, (m, l, n, alg, nb, A, Bm) in enumerate(prods):
+            pk_mats.append(W.matrices(m, l, n, *rng, seed=1000 + i))
+        for u, (m, lb, n, alg, A, Bm) in enumerate(units):
+            i, k = group[u], u - first_unit[group[u]]
+            A2 = pk_mats[i][0][:, k * lb:(k + 1) * lb]
+            B2 = pk_mats[i][1][k * lb:(k + 1) * lb, :]
+            pa = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_A, A, A2, m, lb, n, alg), 1 + rank, 2 * u)
+            pb = ctx.hegmm_encrypt(ctx.hegmm_encode_pair(H.ROLE_B, Bm, B2, m, lb, n, alg), 1 + rank, 2 * u + 1)
             pk_ops.append((pa, pb))
-            pk_mats.append((A2, B2))
 
         def packed_step():
-            return ctx.hegmm_matmul_batch_algs([a for a, _ in pk_ops], [b for _, b in pk_ops], [p[:3] for p in prods],
-                                               algs)
+            return run([a for a, _ in pk_ops], [b for _, b in pk_ops])
 
         outs = packed_step()
-        for (m, l, n, alg, A, Bm), (A2, B2), c in zip(prods, pk_mats, outs):
-            r0, r1 = ctx.hegmm_decrypt_pair(c, m, l, n, alg)
+        for i, ((m, l, n, alg, nb, A, Bm), (A2, B2), c) in enumerate(zip(prods, pk_mats, outs)):
+            r0, r1 = decrypt(i, c, pair=True)
             assert (r0.astype(np.int64) == (A @ Bm) % pre.t).all() and (r1.astype(np.int64) == (A2 @ B2) % pre.t).all()
         del outs
         packed_ms = sum(timed(packed_step, args.steps)) / args.steps
@@ -957,7 +1021,7 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
 
     def e2e_step():
         cts = ctx.hegmm_ct_import_batch(host_flat)
-        res = ctx.hegmm_matmul_batch_algs(cts[0::2], cts[1::2], [p[:3] for p in prods], algs)
+        res = run(cts[0::2], cts[1::2])
         ctx.hegmm_ct_export_batch(res, host_out_np)
 
     e2e_step()
@@ -988,7 +1052,9 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
             out[key] = roofline(extra, stats, hbm_peak, bfly_peak, issue, counters)
     out["kernels"] = {k: {"ms": v[0], "launches": v[1]} for k, v in stats.items() if v[1]}
     out["gpu_launches"] = int(sum(v[1] for v in stats.values()) / max(args.steps, 1)) * args.steps
-    out["prods"] = [p[:4] for p in prods]
+    out["prods"] = [p[:5] for p in prods]
+    dnum = -(-pre.L // pre.alpha)
+    out["key_bytes"] = (len(ctx.hegmm_key_list())) * dnum * 2 * (pre.L + pre.K) * ctx.N * 8
     out["preset"] = pre
     del ops
     ctx.close()
@@ -1005,6 +1071,8 @@ def main():
     ap.add_argument("--no-medium", action="store_true", help="skip the medium workload's extra key")
     ap.add_argument("--paper-auto", action="store_true",
                     help="paper workload: AUTO algorithm per shape instead of the fewest-key-switch choice")
+    ap.add_argument("--no-blocks", action="store_true",
+                    help="paper workload: unblocked plans only (one ciphertext per matrix for every product)")
     ap.add_argument("--workload", default="paper", choices=["paper", "medium", "batch", "serve", "product", "blocked"],
                     help="paper: the three N=16384 products (default); medium: the four N=8192 products; batch: 512 "
                          "mixed shapes; serve: Poisson arrivals on the N=16384 ring; product: one product of --shape "
@@ -1076,7 +1144,9 @@ def main():
         "config": cfg({"parallelism": "replicas" if world > 1 else "single-gpu", "keyswitch_mode": args.ks_mode,
                        "giant_cost": args.giant_cost or 8,
                        "tuning": r["tuning"],
-                       "algorithms": {"%dx%dx%d" % p[:3]: p[3] for p in r["prods"]} if kind != "batch" else "AUTO"}),
+                       "algorithms": ({"%dx%dx%d" % p[:3]: (p[3] if p[4] == 1 else "%d on %d l-blocks" % (p[3], p[4]))
+                                       for p in r["prods"]} if kind != "batch" else "AUTO"),
+                       "key_bytes": r["key_bytes"]}),
     }
     for k in ("per_product_path", "batch_over_per_product", "other_keyswitch_mode", "two_row_packing",
               "keyswitches_per_s", "keyswitches_per_step", "paper_rotations_per_step", "wall_s_timed", "e2e",
@@ -1084,6 +1154,16 @@ def main():
               "roofline_modup", "roofline_ntt_inv", "kernels", "clocks"):
         if k in r:
             line[k] = r[k]
+    if kind == "paper" and not args.no_blocks and any(p[4] > 1 for p in r["prods"]):
+        # the same products with one ciphertext per matrix (no blocked plan)
+        args.no_blocks = True
+        u = measure_throughput("paper", args, H, dev, stream, world, rank, full=False)
+        args.no_blocks = False
+        line["unblocked_plans"] = {
+            "value": u["value"], "unit": UNIT, "ms_per_step": u["ms_per_step"],
+            "algorithms": {"%dx%dx%d" % p[:3]: p[3] for p in u["prods"]}, "tuning": u["tuning"],
+            "per_product_path": u["per_product_path"], "e2e": u["e2e"], "keyswitches_per_step": u["keyswitches_per_step"],
+            "key_bytes": u["key_bytes"], "roofline": u["roofline"], "kernels": u["kernels"], "clocks": u["clocks"]}
     if kind == "paper" and not args.no_medium:
         # the medium configuration, measured the same way (fewer extras)
         m = measure_throughput("medium", args, H, dev, stream, world, rank, full=False)

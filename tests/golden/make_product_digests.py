@@ -36,7 +36,9 @@ ENC_SEED = 11
 STREAMS = (100, 101)
 GIANT_COST = 8
 
-# (preset, m, l, n, alg): alg 0 = AUTO (Algorithm 2 when it fits), 3 = the extended pre-layout
+# (preset, m, l, n, alg[, blocks]): alg 0 = AUTO (Algorithm 2 when it fits), 3 = the extended
+# pre-layout; blocks b > 1: the sum of the b products A_k B_k over equal l-blocks (A's column
+# blocks, B's row blocks; block k encrypted on streams 100 + 2k, 101 + 2k), in k order
 CASES = [
     ("medium", 16, 32, 24, 1),
     ("medium", 32, 8, 48, 1),
@@ -47,15 +49,20 @@ CASES = [
     ("paper", 32, 128, 16, 0),
     ("paper", 64, 64, 64, 3),
     ("paper", 32, 128, 16, 3),
+    ("paper", 32, 128, 16, 2, 2),
 ]
 
 
-def case_key(pre, m, l, n, alg):
+def case_key(pre, m, l, n, alg, blocks=1):
+    if blocks > 1:
+        return "%s %dx%dx%d alg %d on %d l-blocks double+lazy+shared" % (pre, m, l, n, alg, blocks)
     return "%s %dx%dx%d alg %d double+lazy+shared" % (pre, m, l, n, alg)
 
 
 def one(args):
-    idx, (pname, m, l, n, alg) = args
+    idx, case = args
+    pname, m, l, n, alg = case[:5]
+    nb = case[5] if len(case) > 5 else 1
     import workload as W
     from oracle import he as OH
     from oracle import slots as SL
@@ -66,16 +73,23 @@ def one(args):
     o.keygen(KEY_SEED)
     rng_lo_hi = W.PAPER_RANGE if pname == "paper" else W.MEDIUM_RANGE
     A, B = W.matrices(m, l, n, *rng_lo_hi, seed=0)
-    ralg = alg if alg else SL.choose_alg(m, l, n, o.S)
-    plan = SL.make_plan(m, l, n, ralg)
+    lb = l // nb
+    ralg = alg if alg else SL.choose_alg(m, lb, n, o.S)
+    plan = SL.make_plan(m, lb, n, ralg)
     ex = OH.HEGMM(o, mode="double", lazy_relin=True, giant=True, giant_cost=GIANT_COST)
-    ctA, ctB = ex.encrypt_inputs(plan, A, B, seed=ENC_SEED, streams=STREAMS)
-    ct = np.ascontiguousarray(ex.run(plan, ctA, ctB), dtype="<u8")
+    items = []
+    for k in range(nb):
+        ctA, ctB = ex.encrypt_inputs(plan, A[:, k * lb:(k + 1) * lb], B[k * lb:(k + 1) * lb, :], seed=ENC_SEED,
+                                     streams=(STREAMS[0] + 2 * k, STREAMS[1] + 2 * k))
+        items.append((plan, ctA, ctB))
+    ct = ex.run(plan, items[0][1], items[0][2]) if nb == 1 else ex.sum_products(items)
+    ct = np.ascontiguousarray(ct, dtype="<u8")
     assert (ex.result(plan, ct) == (A @ B) % o.t).all()
     flat = ct.reshape(-1)
     pos = np.sort(np.random.default_rng(idx).choice(flat.size, 64, replace=False))
-    return case_key(pname, m, l, n, alg), {
-        "preset": pname, "m": m, "l": l, "n": n, "alg": alg, "resolved_alg": ralg, "shape": list(ct.shape),
+    return case_key(*case), {
+        "preset": pname, "m": m, "l": l, "n": n, "alg": alg, "blocks": nb, "resolved_alg": ralg,
+        "shape": list(ct.shape),
         "sha256": hashlib.sha256(ct.tobytes()).hexdigest(),
         "samples": [[int(i), int(flat[i])] for i in pos], "oracle_s": round(time.time() - t0, 1)}
 

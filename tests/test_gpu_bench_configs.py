@@ -31,7 +31,7 @@ DIGEST_FILE = os.path.join(ROOT, "tests", "golden", "product_digests.json")
 # the cases tests/golden/make_product_digests.py writes: (preset, m, l, n, alg)
 CASES = [("medium", 16, 32, 24, 1), ("medium", 32, 8, 48, 1), ("medium", 16, 32, 24, 3), ("medium", 32, 8, 48, 3),
          ("paper", 64, 64, 64, 0), ("paper", 128, 16, 64, 0), ("paper", 32, 128, 16, 0), ("paper", 64, 64, 64, 3),
-         ("paper", 32, 128, 16, 3)]
+         ("paper", 32, 128, 16, 3), ("paper", 32, 128, 16, 2, 2)]
 KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
 BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
 # (LT kernel variant, entries per item, one-output kernel, NTT threads): the
@@ -69,32 +69,45 @@ def set_knobs(H, ctx, knobs):
     ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, nt)
 
 
-def gpu_product(H, name, m, l, n, alg, mode=BENCH_MODE):
+def gpu_product(H, name, m, l, n, alg, mode=BENCH_MODE, blocks=1):
+    """The product on the GPU from the digest script's seeds; with blocks > 1
+    the hegmm_matmul_sum of the products of equal l-blocks (block k on
+    streams 100 + 2k, 101 + 2k)."""
     pre = W.PRESETS[name]
     ctx = context(H, name)
     ctx.hegmm_set_keyswitch_mode(mode)
     rng = W.PAPER_RANGE if name == "paper" else (W.MEDIUM_RANGE if name == "medium" else W.TINY_RANGE)
     A, B = W.matrices(m, l, n, *rng, seed=0)
-    ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], alg)
-    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, m, l, n, alg), ENC_SEED, STREAMS[0])
-    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, m, l, n, alg), ENC_SEED, STREAMS[1])
-    cc, cnt = ctx.hegmm_matmul(ca, cb, m, l, n, alg)
-    got = ctx.hegmm_decrypt(cc, m, l, n, alg).astype(np.int64)
+    lb = l // blocks
+    ctx.hegmm_keygen(KEY_SEED, [(m, lb, n)], alg)
+    cas, cbs = [], []
+    for k in range(blocks):
+        Ak, Bk = A[:, k * lb:(k + 1) * lb], B[k * lb:(k + 1) * lb, :]
+        cas.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, Ak, m, lb, n, alg), ENC_SEED, STREAMS[0] + 2 * k))
+        cbs.append(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, Bk, m, lb, n, alg), ENC_SEED, STREAMS[1] + 2 * k))
+    if blocks == 1:
+        cc, cnt = ctx.hegmm_matmul(cas[0], cbs[0], m, l, n, alg)
+    else:
+        cc, = ctx.hegmm_matmul_sum(cas, cbs, [(m, lb, n)] * blocks, [0] * blocks, 1, [alg] * blocks)
+        cnt = None
+    got = ctx.hegmm_decrypt(cc, m, lb, n, alg).astype(np.int64)
     assert (got == (A @ B) % pre.t).all()
     return ctx, cc, cnt, (A, B)
 
 
 @pytest.mark.parametrize("case_args", CASES)
 def test_benchmarked_products_match_the_oracle_digests(H, case_args):
-    name, m, l, n, alg = case_args
-    key = "%s %dx%dx%d alg %d double+lazy+shared" % case_args
+    name, m, l, n, alg = case_args[:5]
+    blocks = case_args[5] if len(case_args) > 5 else 1
+    key = ("%s %dx%dx%d alg %d double+lazy+shared" % case_args if blocks == 1 else
+           "%s %dx%dx%d alg %d on %d l-blocks double+lazy+shared" % case_args)
     case = json.load(open(DIGEST_FILE))["cases"][key]
     knob_sets = KNOBS if name == "medium" else KNOBS[:3]
     try:
         for knobs in knob_sets:
             ctx = context(H, name)
             set_knobs(H, ctx, knobs)
-            ctx, cc, cnt, _ = gpu_product(H, name, m, l, n, alg)
+            ctx, cc, cnt, _ = gpu_product(H, name, m, l, n, alg, blocks=blocks)
             ct = np.ascontiguousarray(ctx.hegmm_ct_export(cc), dtype="<u8")
             assert list(ct.shape) == case["shape"]
             flat = ct.reshape(-1)
