@@ -44,6 +44,7 @@ METRIC_PAPER = "HEGMM encrypted matmuls/s (N=16384 ring, 64x64x64 + 32x128x16 + 
 UNIT = "matmul/s"
 KEY_SEED = 7
 SERVE_ARENA_GIB = 16  # server workspace, split over its streams
+SERVE_PLAN_GIB = 8  # workspace the plain path's cached plans may keep
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
 COUNTERS = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -442,13 +443,14 @@ def run_serve(args):
     t0 = time.perf_counter()
     ctx.hegmm_keygen(KEY_SEED, shapes, H.ALG_AUTO)
     torch.cuda.synchronize()
-    # masks take what the keys leave, less the server's arenas, the largest
-    # rate's operands and results (three ciphertexts a request) and a margin
+    # masks take what the keys leave, less the server's arenas, the cached
+    # plans of the plain path, the largest rate's operands and results (three
+    # ciphertexts a request) and a margin
     free_b, _ = torch.cuda.mem_get_info(dev)
     ct_b = 2 * pre.L * (1 << pre.logN) * 8
-    keep = (SERVE_ARENA_GIB + 8 << 30) + 3 * ct_b * max(len(v) for v in per_rate.values())
+    keep = (SERVE_ARENA_GIB + SERVE_PLAN_GIB + 8 << 30) + 3 * ct_b * max(len(v) for v in per_rate.values())
     mask_b = min(args.mask_gib << 30, max(1 << 30, free_b - keep))
-    ctx.hegmm_set_budgets(mask_bytes=mask_b)
+    ctx.hegmm_set_budgets(mask_bytes=mask_b, plan_bytes=SERVE_PLAN_GIB << 30)
     print("serve: %d shapes, %.1f GiB free after keys, mask budget %.1f GiB"
           % (len(shapes), free_b / 2**30, mask_b / 2**30), file=sys.stderr)
     ctx.hegmm_prepare(shapes, H.ALG_AUTO)

@@ -457,9 +457,11 @@ static void evict_shapes(Ctx *c, size_t incoming) {
 
 // Allocates from the context's stream-ordered pool.  When the device is
 // full, the least recently used masks that no plan references are released
-// (at least a GiB, or the request, at a time) and the pool gives its unused
-// memory back before the next attempt: resident masks are a cache, and a
-// plan's or a server's workspace comes before them.
+// (at least a GiB, or the request, at a time), then, when no such mask is
+// left, the least recently used cached batch plans (their workspace), and
+// the pool gives its unused memory back before the next attempt: resident
+// masks and cached plans are caches, and a running plan's or a server's
+// workspace comes before them.
 void *dalloc_evicting(Ctx *c, size_t bytes) {
     for (;;) {
         void *p = nullptr;
@@ -478,6 +480,19 @@ void *dalloc_evicting(Ctx *c, size_t bytes) {
             freed += lru->second->bytes;
             free_shape(c, lru->second);
             c->shapes.erase(lru);
+        }
+        while (freed < goal) {
+            // the plan being run stays
+            auto lru = c->bplans.end();
+            for (auto it = c->bplans.begin(); it != c->bplans.end(); ++it)
+                if (it->second != c->running_plan &&
+                    (lru == c->bplans.end() || it->second->last_use < lru->second->last_use))
+                    lru = it;
+            if (lru == c->bplans.end()) break;
+            freed += lru->second->ws_bytes;
+            c->bplan_bytes -= lru->second->ws_bytes;
+            free_bplan(c, lru->second);
+            c->bplans.erase(lru);
         }
         if (!freed) return nullptr;
         cudaStreamSynchronize(c->st);
@@ -1703,6 +1718,12 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
             *hold = nullptr;
         }
     };
+    struct Running {  // keeps P out of dalloc_evicting's reach while it runs
+        Ctx *c;
+        const BatchPlan *prev;
+        ~Running() { c->running_plan = prev; }
+    } running{c, c->running_plan};
+    c->running_plan = P;
     for (int i = 0; i < count; i++) {
         C[i] = new_ct(c, P->lv1);
         if (!C[i]) {

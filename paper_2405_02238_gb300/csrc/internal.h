@@ -207,6 +207,7 @@ struct Ctx {
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     std::map<std::tuple<int, int, int, int>, std::pair<size_t, size_t>> shape_counts;  // iterations, extractions
     unsigned long long bplan_clock = 0;
+    const BatchPlan *running_plan = nullptr;  // the cached plan matmul_run is executing (never evicted)
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
     int lazy_relin = 0;                        // products: one relinearisation of the summed tensors
