@@ -198,6 +198,12 @@ HDI u64 mulsh_approx(u64 a, u64 w, u64 wp, u64 q) {
 // d = r - p mod 2^64.
 HDI u64 centred_narrow(u64 v, u64 half_p, u64 d) { return v > half_p ? v + d : v; }
 
+#ifdef __CUDACC__
+// Brings the 128-byte line holding p into L2 (no register result, no fault
+// on the line's contents; p must point into an allocation).
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+#endif
+
 // Padded shared-memory index: one spare word every 16 keeps the strided
 // butterfly accesses of every pass at two wavefronts per warp.
 HDI int pad16(int i) { return i + (i >> 4); }

@@ -36,8 +36,9 @@ KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
 BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
 # (LT kernel variant, entries per item, one-output kernel, NTT threads): the
 # autotuner's usual choice, the library default, the persistent kernel with
-# the 512-thread NTT form, and a plain-load variant
-KNOBS = [(7, 32, 0, 0), (6, 32, 0, 0), (8, 32, 0, 512), (0, 64, 2, 0)]
+# the 512-thread NTT form, the two-coefficient one-output kernel, and a
+# plain-load variant
+KNOBS = [(7, 32, 0, 0), (6, 32, 0, 0), (8, 32, 0, 512), (3, 64, 4, 1024), (0, 64, 2, 0)]
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +103,7 @@ def test_benchmarked_products_match_the_oracle_digests(H, case_args):
     key = ("%s %dx%dx%d alg %d double+lazy+shared" % case_args if blocks == 1 else
            "%s %dx%dx%d alg %d on %d l-blocks double+lazy+shared" % case_args)
     case = json.load(open(DIGEST_FILE))["cases"][key]
-    knob_sets = KNOBS if name == "medium" else KNOBS[:3]
+    knob_sets = KNOBS if name == "medium" else KNOBS[:4]
     try:
         for knobs in knob_sets:
             ctx = context(H, name)
