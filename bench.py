@@ -810,7 +810,7 @@ def roofline(name, stats, hbm_peak, bfly_peak, issue_peak, counters):
     return r
 
 
-def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
+def measure_throughput(kind, args, H, dev, stream, world, rank, full=True, profile=True):
     """Times one throughput workload (paper, medium or batch): autotune,
     warm-up with a decryption check of every product, the timed steps (CUDA
     events on the library stream around graph replays, L2 flushed between
@@ -941,11 +941,13 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True):
     clk.start()
     time.sleep(0.3)
     t_wall0 = time.perf_counter()
-    torch.cuda.profiler.start()  # profilers started with capture off record the timed steps only
+    if profile:  # profilers started with capture off record the headline's timed steps only
+        torch.cuda.profiler.start()
     step_ms = timed(step, args.steps)
     if world > 1:
         dist.barrier()
-    torch.cuda.profiler.stop()
+    if profile:
+        torch.cuda.profiler.stop()
     wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
     ms = max_over_ranks(sum(step_ms) / len(step_ms), world, dist if world > 1 else None, dev)
@@ -1159,7 +1161,7 @@ def main():
     if kind == "paper" and not args.no_blocks and any(p[4] > 1 for p in r["prods"]):
         # the same products with one ciphertext per matrix (no blocked plan)
         args.no_blocks = True
-        u = measure_throughput("paper", args, H, dev, stream, world, rank, full=False)
+        u = measure_throughput("paper", args, H, dev, stream, world, rank, full=False, profile=False)
         args.no_blocks = False
         line["unblocked_plans"] = {
             "value": u["value"], "unit": UNIT, "ms_per_step": u["ms_per_step"],
@@ -1168,7 +1170,7 @@ def main():
             "key_bytes": u["key_bytes"], "roofline": u["roofline"], "kernels": u["kernels"], "clocks": u["clocks"]}
     if kind == "paper" and not args.no_medium:
         # the medium configuration, measured the same way (fewer extras)
-        m = measure_throughput("medium", args, H, dev, stream, world, rank, full=False)
+        m = measure_throughput("medium", args, H, dev, stream, world, rank, full=False, profile=False)
         line["medium_workload"] = {
             "workload": workload_config()["workload"], "metric": METRIC, "value": m["value"], "unit": UNIT,
             "ms_per_step": m["ms_per_step"], "products_per_step": m["products_per_step"], "tuning": m["tuning"],
