@@ -907,10 +907,10 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True, profi
     # mislead the autotuner: profiling runs pass the plain run's choice)
     tuning = None
     fixed = {k: v for k, v in (("lt_kernel", args.lt_kernel), ("lt_chunk", args.lt_chunk), ("lt_one", args.lt_one),
-                               ("ntt_threads", args.ntt_threads)) if v >= 0}
+                               ("ntt_threads", args.ntt_threads), ("groups", args.groups)) if v >= 0}
     if fixed:
         knob = {"lt_kernel": H.TUNE_LT_KERNEL, "lt_chunk": H.TUNE_LT_CHUNK, "lt_one": H.TUNE_LT_ONE,
-                "ntt_threads": H.TUNE_NTT_THREADS}
+                "ntt_threads": H.TUNE_NTT_THREADS, "groups": H.TUNE_GROUPS}
         for k, v in fixed.items():
             ctx.hegmm_set_tuning(knob[k], v)
         tuning = dict(fixed, given=True)
@@ -1095,6 +1095,8 @@ def main():
     ap.add_argument("--ntt-threads", type=int, default=-1,
                     help="HEGMM_TUNE_NTT_THREADS (0 by launch size, 512, 1024; -1: autotuned, or the library's choice "
                          "for --workload product)")
+    ap.add_argument("--groups", type=int, default=-1,
+                    help="HEGMM_TUNE_GROUPS concurrent sub-batches (1 or 2; -1: autotuned)")
     ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV:JSON",
                     help="write profiles/ncu_traffic.json for the current kernel sources from ncu CSV logs "
                          "(dram__bytes_read.sum, dram__bytes_write.sum, smsp__inst_executed.sum of the timed "

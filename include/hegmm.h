@@ -315,6 +315,15 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     least that many); at N = 2^14 the 512-thread form has 128 registers a
  *     thread instead of 64. */
 #define HEGMM_TUNE_NTT_THREADS 9
+/*   HEGMM_TUNE_GROUPS: 1 (default) runs a batch of products as one plan,
+ *     every stage one launch over all of them; 2 splits a batch of at least
+ *     two products into two sub-batches (by estimated workspace, largest
+ *     first to the lighter group), each with its own cached plan on a
+ *     stream of its own, forked from and joined back into the context
+ *     stream, so that one group's small launches run beside the other's
+ *     large ones.  Results are the same bits.  Not used while the context
+ *     stream is being captured, nor by the server. */
+#define HEGMM_TUNE_GROUPS 10
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in
@@ -398,8 +407,9 @@ int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows
  * stream after a plan-building and a graph-capturing call, and the fastest
  * is kept in the context; then, with the fastest of those, the NTT-family
  * thread counts (HEGMM_TUNE_NTT_THREADS 0, 512, 1024, on rings where both
- * forms exist).  chosen (may be NULL, else 4 ints) receives {kernel
- * variant, entries per item, one-output kernel, NTT threads}.  Results stay
+ * forms exist), then two sub-batches (HEGMM_TUNE_GROUPS 2) for two or more
+ * products.  chosen (may be NULL, else 5 ints) receives {kernel variant,
+ * entries per item, one-output kernel, NTT threads, sub-batches}.  Results stay
  * bit for bit the same (every candidate is an execution order of the same
  * sums).  The linear-transformation knobs only steer the HEGMM_KS_DOUBLE
  * kernels; in single mode only the NTT threads are tuned.  Cached product

@@ -455,6 +455,10 @@ static void evict_shapes(Ctx *c, size_t incoming) {
     }
 }
 
+static bool is_pinned(const Ctx *c, const BatchPlan *P) {
+    return std::find(c->pinned.begin(), c->pinned.end(), P) != c->pinned.end();
+}
+
 // Allocates from the context's stream-ordered pool.  When the device is
 // full, the least recently used masks that no plan references are released
 // (at least a GiB, or the request, at a time), then, when no such mask is
@@ -482,10 +486,10 @@ void *dalloc_evicting(Ctx *c, size_t bytes) {
             c->shapes.erase(lru);
         }
         while (freed < goal) {
-            // the plan being run stays
+            // plans in flight stay
             auto lru = c->bplans.end();
             for (auto it = c->bplans.begin(); it != c->bplans.end(); ++it)
-                if (it->second != c->running_plan &&
+                if (!is_pinned(c, it->second) &&
                     (lru == c->bplans.end() || it->second->last_use < lru->second->last_use))
                     lru = it;
             if (lru == c->bplans.end()) break;
@@ -1627,9 +1631,12 @@ static int run_bplan(Ctx *c, BatchPlan *P, const hegmm_ct *const *A, const hegmm
 
 static void evict_plans(Ctx *c, size_t incoming) {
     while (!c->bplans.empty() && c->bplan_bytes + incoming > c->plan_cache_budget) {
-        auto lru = c->bplans.begin();
+        auto lru = c->bplans.end();
         for (auto it = c->bplans.begin(); it != c->bplans.end(); ++it)
-            if (it->second->last_use < lru->second->last_use) lru = it;
+            if (!is_pinned(c, it->second) &&
+                (lru == c->bplans.end() || it->second->last_use < lru->second->last_use))
+                lru = it;
+        if (lru == c->bplans.end()) return;  // every cached plan is in flight
         c->bplan_bytes -= lru->second->ws_bytes;
         free_bplan(c, lru->second);
         c->bplans.erase(lru);
@@ -1666,9 +1673,11 @@ size_t estimate_bytes(Ctx *c, int m, int l, int n, int alg) {
 
 void release_plan(Ctx *c, BatchPlan *P) { free_bplan(c, P); }
 
-int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
-               const int *algs, hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold) {
+static int matmul_run_one(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                          int alg, const int *algs, hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold,
+                          BatchPlan **used) {
     for (int i = 0; i < count; i++) C[i] = nullptr;
+    if (used) *used = nullptr;
     if (count == 0) return HEGMM_OK;
     std::vector<std::array<int, 4>> shapes;
     std::vector<int> key;
@@ -1696,6 +1705,7 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
     key.push_back(c->test_drop_entry);
     key.push_back(c->key_pow2);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
+    key.push_back(c->par_slot);  // a plan's workspace is ordered on the stream it was built for
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
@@ -1718,12 +1728,15 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
             *hold = nullptr;
         }
     };
-    struct Running {  // keeps P out of dalloc_evicting's reach while it runs
+    struct Running {  // keeps P out of the evictions' reach while it runs
         Ctx *c;
-        const BatchPlan *prev;
-        ~Running() { c->running_plan = prev; }
-    } running{c, c->running_plan};
-    c->running_plan = P;
+        const BatchPlan *P;
+        ~Running() {
+            auto it = std::find(c->pinned.begin(), c->pinned.end(), P);
+            if (it != c->pinned.end()) c->pinned.erase(it);
+        }
+    } running{c, P};
+    c->pinned.push_back(P);
     for (int i = 0; i < count; i++) {
         C[i] = new_ct(c, P->lv1);
         if (!C[i]) {
@@ -1746,7 +1759,102 @@ int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *cons
         return rc;
     }
     if (cnt) *cnt = P->cnt;
+    if (used) *used = P;
     return HEGMM_OK;
+}
+
+// A cached batch as two concurrent sub-batches: the products are split by
+// their estimated workspace (largest first, to the lighter group), and each
+// group runs its own cached plan on a stream of its own, forked from and
+// joined back into the context stream by events.  The stages of one group
+// then overlap those of the other: the small launches of one group's
+// relinearisation or extraction run beside the other's large ones.  Each
+// product's result is the ciphertext the single batch gives (a plan's
+// arithmetic does not depend on its neighbours).
+static int matmul_run_groups(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln,
+                             int alg, const int *algs, hegmm_ct **C, hegmm_opcount *cnt) {
+    std::vector<std::pair<size_t, int>> w;
+    for (int i = 0; i < count; i++)
+        w.push_back({estimate_bytes(c, mln[3 * i], mln[3 * i + 1], mln[3 * i + 2], algs ? algs[i] : alg), i});
+    std::stable_sort(w.begin(), w.end(), [](const std::pair<size_t, int> &x, const std::pair<size_t, int> &y) {
+        return x.first > y.first;
+    });
+    std::vector<int> grp[2];
+    size_t load[2] = {0, 0};
+    for (auto &x : w) {
+        const int g = load[1] < load[0] ? 1 : 0;
+        grp[g].push_back(x.second);
+        load[g] += x.first;
+    }
+    for (int g = 0; g < 2; g++) std::sort(grp[g].begin(), grp[g].end());
+    for (int g = 0; g < 2; g++)
+        if (!c->par_st[g] && cudaStreamCreateWithFlags(&c->par_st[g], cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_check(c, "sub-batch stream");
+    for (auto &e : c->par_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_check(c, "sub-batch event");
+    const cudaStream_t st0 = c->st;
+    cudaEventRecord(c->par_ev[0], st0);
+    int rc = HEGMM_OK;
+    BatchPlan *used[2] = {nullptr, nullptr};
+    std::vector<hegmm_ct *> out[2];
+    hegmm_opcount gc[2]{};
+    for (int g = 0; g < 2 && !rc; g++) {
+        const int n = (int)grp[g].size();
+        std::vector<const hegmm_ct *> a, b;
+        std::vector<int> s, al;
+        for (int i : grp[g]) {
+            a.push_back(A[i]);
+            b.push_back(B[i]);
+            s.insert(s.end(), {mln[3 * i], mln[3 * i + 1], mln[3 * i + 2]});
+            al.push_back(algs ? algs[i] : alg);
+        }
+        out[g].assign((size_t)n, nullptr);
+        cudaStreamWaitEvent(c->par_st[g], c->par_ev[0], 0);
+        c->st = c->par_st[g];
+        c->par_slot = g + 1;
+        c->in_groups = true;
+        rc = matmul_run_one(c, n, a.data(), b.data(), s.data(), alg, al.data(), out[g].data(), &gc[g], true, nullptr,
+                            &used[g]);
+        c->st = st0;
+        c->par_slot = 0;
+        c->in_groups = false;
+        if (used[g]) c->pinned.push_back(used[g]);  // in flight on its stream until the join below
+    }
+    for (int g = 0; g < 2; g++) {
+        cudaEventRecord(c->par_ev[1 + g], c->par_st[g]);
+        cudaStreamWaitEvent(st0, c->par_ev[1 + g], 0);
+    }
+    for (int g = 0; g < 2; g++)
+        if (used[g]) {
+            auto it = std::find(c->pinned.begin(), c->pinned.end(), (const BatchPlan *)used[g]);
+            if (it != c->pinned.end()) c->pinned.erase(it);
+        }
+    if (rc) {
+        for (int g = 0; g < 2; g++)
+            for (auto *x : out[g]) hegmm_ct_destroy(x);
+        return rc;
+    }
+    for (int g = 0; g < 2; g++)
+        for (size_t k = 0; k < grp[g].size(); k++) C[grp[g][k]] = out[g][k];
+    if (cnt) {
+        *cnt = gc[0];
+        add_counts(*cnt, gc[1]);
+    }
+    return cuda_check(c, "sub-batches");
+}
+
+int matmul_run(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
+               const int *algs, hegmm_ct **C, hegmm_opcount *cnt, bool cache, BatchPlan **hold) {
+    if (cache && !hold && c->par_groups > 1 && count >= 2 && !c->in_groups) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+            for (int i = 0; i < count; i++) C[i] = nullptr;
+            return matmul_run_groups(c, count, A, B, mln, alg, algs, C, cnt);
+        }
+        cudaGetLastError();
+    }
+    return matmul_run_one(c, count, A, B, mln, alg, algs, C, cnt, cache, hold, nullptr);
 }
 
 int matmul_many(Ctx *c, int count, const hegmm_ct *const *A, const hegmm_ct *const *B, const int *mln, int alg,
@@ -2002,13 +2110,14 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (!h || count <= 0 || !A || !B || !mln) return HEGMM_EINVAL;
     Ctx *c = &h->c;
     if (reps < 1) reps = 3;
-    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one, nt0 = c->ntt_threads;
+    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one, nt0 = c->ntt_threads, g0 = c->par_groups;
     auto report = [&]() {
         if (chosen) {
             chosen[0] = c->lt_kernel;
             chosen[1] = c->lt_chunk;
             chosen[2] = c->lt_one;
             chosen[3] = c->ntt_threads;
+            chosen[4] = c->par_groups;
         }
         return HEGMM_OK;
     };
@@ -2021,6 +2130,8 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
         return rc;
     };
     auto drop_plans = [&]() {
+        for (cudaStream_t s : c->par_st)
+            if (s) cudaStreamSynchronize(s);  // plans of sub-batches ran there
         for (auto &kv : c->bplans) free_bplan(c, kv.second);
         c->bplans.clear();
         c->bplan_bytes = 0;
@@ -2029,13 +2140,15 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bk = k0, bc = ch0, bs = s0, bn = nt0, rc = HEGMM_OK;
+    int bk = k0, bc = ch0, bs = s0, bn = nt0, bg = g0, rc = HEGMM_OK;
+    c->par_groups = 1;
     // times one candidate; false when a run failed (rc holds the error)
-    auto trial = [&](int kv, int chunk, int one, int nt) {
+    auto trial = [&](int kv, int chunk, int one, int nt, int groups = 1) {
         c->lt_kernel = kv;
         c->lt_chunk = chunk;
         c->lt_one = one;
         c->ntt_threads = nt;
+        c->par_groups = groups;
         for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
         if (rc) return false;
         cudaEventRecord(e0, c->st);
@@ -2050,6 +2163,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
             bc = chunk;
             bs = one;
             bn = nt;
+            bg = groups;
         }
         drop_plans();
         return true;
@@ -2072,6 +2186,8 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (c->N / 8 >= 1024)
         for (int nt : {0, 512, 1024})
             if (ok && (nt != bn || best > 1e29f)) ok = trial(bk, bc, bs, nt);
+    // two concurrent sub-batches, with the best of the rest
+    if (ok && count >= 2) ok = trial(bk, bc, bs, bn, 2);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_plans();
@@ -2080,6 +2196,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     c->lt_chunk = rc ? ch0 : bc;
     c->lt_one = rc ? s0 : bs;
     c->ntt_threads = rc ? nt0 : bn;
+    c->par_groups = rc ? g0 : bg;
     if (rc) return rc;
     return report();
 }
@@ -2131,6 +2248,11 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_GRAPHS) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "graphs must be 0 or 1");
         c->use_graphs = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_GROUPS) {
+        if (value != 1 && value != 2) return set_err(c, HEGMM_EINVAL, "sub-batches must be 1 or 2");
+        c->par_groups = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_NTT_THREADS) {

@@ -737,6 +737,8 @@ int hegmm_ctx_create(const hegmm_params *params, void *cuda_stream, hegmm_ctx **
 void hegmm_ctx_destroy(hegmm_ctx *h) {
     if (!h) return;
     Ctx *c = &h->c;
+    for (cudaStream_t s : c->par_st)
+        if (s) cudaStreamSynchronize(s);  // sub-batch plans ran there
     free_plans(c);
     free_keys(c);
     for (auto &kv : c->modup) dfree(c, kv.second.d);
@@ -754,6 +756,10 @@ void hegmm_ctx_destroy(hegmm_ctx *h) {
         cudaEventDestroy(p.b);
     }
     for (auto e : c->evpool) cudaEventDestroy(e);
+    for (cudaStream_t s : c->par_st)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->par_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 

@@ -207,7 +207,12 @@ struct Ctx {
     std::map<std::vector<int>, BatchPlan *> bplans;                // per product list
     std::map<std::tuple<int, int, int, int>, std::pair<size_t, size_t>> shape_counts;  // iterations, extractions
     unsigned long long bplan_clock = 0;
-    const BatchPlan *running_plan = nullptr;  // the cached plan matmul_run is executing (never evicted)
+    std::vector<const BatchPlan *> pinned;     // cached plans in flight on a stream (never evicted)
+    int par_groups = 1;                        // concurrent sub-batches of a cached batch (1 or 2)
+    int par_slot = 0;                          // stream of the running sub-batch (0: st), part of plan keys
+    bool in_groups = false;
+    cudaStream_t par_st[2] = {nullptr, nullptr};
+    cudaEvent_t par_ev[3] = {nullptr, nullptr, nullptr};
     size_t bplan_bytes = 0;
     int ks_double = 0;                         // products: sums of key switches kept over PQ, one ModDown each
     int lazy_relin = 0;                        // products: one relinearisation of the summed tensors

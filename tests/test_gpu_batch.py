@@ -169,3 +169,42 @@ def test_autotune_keeps_results(H, medium):
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
         ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 0)
         ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
+
+
+@pytest.mark.parametrize("mode", ["double+lazy+shared", "single"])
+def test_sub_batches_equal_one_batch(H, medium, mode):
+    """HEGMM_TUNE_GROUPS 2 (two concurrent sub-batches on streams of their
+    own) gives every product the bits of the one-plan batch, in batches,
+    in sums of products (hegmm_matmul_sum) and on repeated calls (cached
+    plans, graph replays)."""
+    ctx = medium
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED if mode != "single" else H.KS_SINGLE)
+    shapes = [(16, 32, 24), (4, 8, 6), (9, 4, 11), (20, 10, 30), (12, 3, 9)]
+    ctx.hegmm_keygen(SEED, shapes)
+    As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=50, stream0=600)
+    ref = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_batch(As, Bs, shapes)]
+    # two blocks of one product, summed, beside a third product
+    A, B = W.matrices(8, 16, 6, *W.BATCH_RANGE, seed=9)
+    ctx.hegmm_keygen(SEED, [(8, 8, 6)], 2)
+    blk = [(ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A[:, 8 * k:8 * k + 8], 8, 8, 6, 2), 78, 700 + 2 * k),
+            ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B[8 * k:8 * k + 8, :], 8, 8, 6, 2), 78, 701 + 2 * k))
+           for k in range(2)]
+    sum_args = ([blk[0][0], blk[1][0], As[0]], [blk[0][1], blk[1][1], Bs[0]], [(8, 8, 6), (8, 8, 6), shapes[0]],
+                [0, 0, 1], 2, [2, 2, 0])
+    sref = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_sum(*sum_args)]
+    ctx.hegmm_set_tuning(H.TUNE_GROUPS, 2)
+    try:
+        for _ in range(3):
+            outs = ctx.hegmm_matmul_batch(As, Bs, shapes)
+            for i, c in enumerate(outs):
+                assert (ctx.hegmm_ct_export(c) == ref[i]).all(), shapes[i]
+            souts = ctx.hegmm_matmul_sum(*sum_args)
+            for g, c in enumerate(souts):
+                assert (ctx.hegmm_ct_export(c) == sref[g]).all(), g
+        for i, ((m, l, n), (Am, Bm)) in enumerate(zip(shapes, mats)):
+            assert (ctx.hegmm_decrypt(outs[i], m, l, n).astype(np.int64) == (Am @ Bm) % W.MEDIUM.t).all()
+        assert (ctx.hegmm_decrypt(souts[0], 8, 8, 6, 2).astype(np.int64) == (A @ B) % W.MEDIUM.t).all()
+        with pytest.raises(H.HegmmError):
+            ctx.hegmm_set_tuning(H.TUNE_GROUPS, 3)
+    finally:
+        ctx.hegmm_set_tuning(H.TUNE_GROUPS, 1)

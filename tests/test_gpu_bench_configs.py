@@ -36,9 +36,10 @@ KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
 BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
 # (LT kernel variant, entries per item, one-output kernel, NTT threads): the
 # autotuner's usual choice, the library default, the persistent kernel with
-# the 512-thread NTT form, the two-coefficient one-output kernel, and a
+# the 512-thread NTT form, the two-coefficient one-output kernel with two
+# concurrent sub-batches (the blocked product's two blocks), and a
 # plain-load variant
-KNOBS = [(7, 32, 0, 0), (6, 32, 0, 0), (8, 32, 0, 512), (3, 64, 4, 1024), (0, 64, 2, 0)]
+KNOBS = [(7, 32, 0, 0, 1), (6, 32, 0, 0, 1), (8, 32, 0, 512, 1), (3, 64, 4, 1024, 2), (0, 64, 2, 0, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -63,11 +64,12 @@ def context(H, name):
 
 
 def set_knobs(H, ctx, knobs):
-    v, ch, one, nt = knobs
+    v, ch, one, nt, groups = knobs
     ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, v)
     ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, ch)
     ctx.hegmm_set_tuning(H.TUNE_LT_ONE, one)
     ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, nt)
+    ctx.hegmm_set_tuning(H.TUNE_GROUPS, groups)
 
 
 def gpu_product(H, name, m, l, n, alg, mode=BENCH_MODE, blocks=1):
