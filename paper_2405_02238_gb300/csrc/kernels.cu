@@ -736,85 +736,6 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
 }
 
 
-// Items of one output, two adjacent coefficients per thread (the layout of
-// k_ksw_ip): the key rows and the mask are read with 16-byte loads and each
-// thread keeps two loads of every row in flight; the digits are gathered
-// at the automorphism's two indices.  Per coefficient the arithmetic is
-// k_lt_grp<1, ., false>'s in the same order, so the sums are the same bits.
-// grid (N / 512, items, limbs).
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_lt_one2(int lv, int ne, int nd, int np, int L, int logN,
-                                                    const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
-                                                    const LtItem *__restrict__ items) {
-    const int N = 1 << logN;
-    const int c = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (c >= N) return;
-    const int e = blockIdx.z;
-    const LtItem *it = items + blockIdx.y;
-    const int gm = e < lv ? e : L + (e - lv);
-    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
-    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
-    Acc s00{0, 0}, s01{0, 0}, s10{0, 0}, s11{0, 0};  // s<component><coefficient>
-    const int t0 = it->first, t1 = t0 + it->count;
-    for (int t = t0; t < t1; t++) {
-        const LtEntry *E = ents + t;
-        const u64 *key = E->key;
-        if (!key && e >= lv) continue;  // P ct is 0 on the special primes
-        const bool used = E->used & 1u;
-        ulonglong2 mv{0, 0};
-        if (used) mv = __ldg(reinterpret_cast<const ulonglong2 *>(E->mask[0] + moff));
-        u64 u00, u01, u10, u11;
-        if (key) {
-            const u32 src0 = auto_src((u32)c, E->g, logN), src1 = auto_src((u32)c + 1, E->g, logN);
-            const u64 *Dp = E->D + (size_t)e * N;
-            const u64 *Kp = key + moff;
-            Acc a00{0, 0}, a01{0, 0}, a10{0, 0}, a11{0, 0};
-            if (e < lv) {
-                mac(a00, __ldg(E->ct + (size_t)e * N + src0), pR);
-                mac(a01, __ldg(E->ct + (size_t)e * N + src1), pR);
-            }
-#pragma unroll 4
-            for (int j = 0; j < nd; j++) {
-                const u64 x0 = __ldg(Dp + (size_t)j * dstep + src0);
-                const u64 x1 = __ldg(Dp + (size_t)j * dstep + src1);
-                const ulonglong2 k0 = __ldcs(reinterpret_cast<const ulonglong2 *>(Kp + (size_t)(2 * j) * kstep));
-                const ulonglong2 k1 = __ldcs(reinterpret_cast<const ulonglong2 *>(Kp + (size_t)(2 * j + 1) * kstep));
-                mac(a00, x0, k0.x);
-                mac(a01, x1, k0.y);
-                mac(a10, x0, k1.x);
-                mac(a11, x1, k1.y);
-            }
-            u00 = montred(a00, q, qinv);
-            u01 = montred(a01, q, qinv);
-            u10 = montred(a10, q, qinv);
-            u11 = montred(a11, q, qinv);
-        } else {
-            const ulonglong2 y0 = __ldg(reinterpret_cast<const ulonglong2 *>(E->ct + (size_t)e * N + c));
-            const ulonglong2 y1 = __ldg(reinterpret_cast<const ulonglong2 *>(E->ct + ((size_t)lv + e) * N + c));
-            u00 = montmul(y0.x, pR, q, qinv);
-            u01 = montmul(y0.y, pR, q, qinv);
-            u10 = montmul(y1.x, pR, q, qinv);
-            u11 = montmul(y1.y, pR, q, qinv);
-        }
-        if (used) {
-            mac(s00, u00, mv.x);
-            mac(s01, u01, mv.y);
-            mac(s10, u10, mv.x);
-            mac(s11, u11, mv.y);
-        }
-    }
-    u64 *o = it->out[0];
-    if (o) {
-        ulonglong2 r0, r1;
-        r0.x = montred(s00, q, qinv);
-        r0.y = montred(s01, q, qinv);
-        r1.x = montred(s10, q, qinv);
-        r1.y = montred(s11, q, qinv);
-        *reinterpret_cast<ulonglong2 *>(o + (size_t)e * N + c) = r0;
-        *reinterpret_cast<ulonglong2 *>(o + ((size_t)ne + e) * N + c) = r1;
-    }
-}
-
 // The 8-output kernel with its streamed operands staged by the TMA engine:
 // one CTA per (256 coefficients, item, limb); thread 0 issues, for entry
 // t + 1, bulk copies of the key rows (2 nd rows of 2 KB) and of every used
@@ -1300,9 +1221,6 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
                 HG_LTG(1, 5, false);
             } else if (c->lt_one == 3) {
                 HG_LTG(1, 4, false);
-            } else if (c->lt_one == 4) {
-                const dim3 g2((unsigned)((c->N / 2 + 255) / 256), grid.y, grid.z);
-                k_lt_one2<3><<<g2, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }

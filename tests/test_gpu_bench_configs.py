@@ -36,10 +36,10 @@ KEY_SEED, ENC_SEED, STREAMS = 1234, 11, (100, 101)
 BENCH_MODE = 7  # KS_DOUBLE | KS_LAZY_RELIN | KS_SHARED
 # (LT kernel variant, entries per item, one-output kernel, NTT threads): the
 # autotuner's usual choice, the library default, the persistent kernel with
-# the 512-thread NTT form, the two-coefficient one-output kernel with two
+# the 512-thread NTT form, a lower-occupancy one-output kernel with two
 # concurrent sub-batches (the blocked product's two blocks), and a
 # plain-load variant
-KNOBS = [(7, 32, 0, 0, 1), (6, 32, 0, 0, 1), (8, 32, 0, 512, 1), (3, 64, 4, 1024, 2), (0, 64, 2, 0, 1)]
+KNOBS = [(7, 32, 0, 0, 1), (6, 32, 0, 0, 1), (8, 32, 0, 512, 1), (3, 64, 3, 1024, 2), (0, 64, 2, 0, 1)]
 
 
 @pytest.fixture(scope="module")
