@@ -322,11 +322,6 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     large ones.  Results are the same bits.  Not used while the context
  *     stream is being captured, nor by the server. */
 #define HEGMM_TUNE_GROUPS 10
-/*   HEGMM_TUNE_PREFETCH: 1 (default) lets the one-output linear-
- *     transformation kernel and the fused ModDown ask L2 for the operands of
- *     the CTAs about one wave ahead (prefetch.global.L2); 0 turns that off.
- *     Results are the same bits. */
-#define HEGMM_TUNE_PREFETCH 11
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
 /* As hegmm_matmul_batch, with one algorithm per product: algs[i] in

@@ -1706,7 +1706,6 @@ static int matmul_run_one(Ctx *c, int count, const hegmm_ct *const *A, const heg
     key.push_back(c->key_pow2);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     key.push_back(c->par_slot);  // a plan's workspace is ordered on the stream it was built for
-    key.push_back(c->prefetch);
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
@@ -2248,11 +2247,6 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_GRAPHS) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "graphs must be 0 or 1");
         c->use_graphs = (int)value;
-        return HEGMM_OK;
-    }
-    if (knob == HEGMM_TUNE_PREFETCH) {
-        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "prefetch must be 0 or 1");
-        c->prefetch = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_GROUPS) {

@@ -209,7 +209,6 @@ struct Ctx {
     unsigned long long bplan_clock = 0;
     std::vector<const BatchPlan *> pinned;     // cached plans in flight on a stream (never evicted)
     int par_groups = 1;                        // concurrent sub-batches of a cached batch (1 or 2)
-    int prefetch = 1;                          // L2 prefetch one wave ahead in the one-output and ModDown kernels
     int par_slot = 0;                          // stream of the running sub-batch (0: st), part of plan keys
     bool in_groups = false;
     cudaStream_t par_st[2] = {nullptr, nullptr};

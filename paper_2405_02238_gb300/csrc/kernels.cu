@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_divround_ntt(
                                                                           const ModDev *__restrict__ mods,
                                                                           const u64 *__restrict__ tab, int ext,
                                                                           const DivDesc *__restrict__ desc,
-                                                                          const TwPair *__restrict__ tw, int pf) {
+                                                                          const TwPair *__restrict__ tw) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN;
     const int npoly = gridDim.x / nkeep;  // prime-major block order (twiddles stay in L1)
@@ -238,14 +238,6 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_divround_ntt(
     for (int w = threadIdx.x * 16; w < N; w += NT * 16) {
         prefetch_l2(d.u + (size_t)i * N + w);
         if (d.add) prefetch_l2(d.add + (size_t)i * N + w);
-    }
-    // pf > 0: the same for the dropped limbs the CTA pf places ahead (about
-    // one wave of resident CTAs) reads in its prologue
-    if (pf > 0 && blockIdx.x + pf < gridDim.x) {
-        const int b2 = (blockIdx.x + pf) % npoly;
-        const u64 *u2 = desc[b2].u;
-        for (int kk = 0; kk < ndrop; kk++)
-            for (int w = threadIdx.x * 16; w < N; w += NT * 16) prefetch_l2(u2 + (size_t)(nkeep + kk) * N + w);
     }
     // prologue fused with the first pass: the conversion of the group's 8
     // coefficients, one dropped prime at a time (its constants loaded once)
@@ -451,10 +443,8 @@ int ntt_inv(Ctx *c, const LimbPat &p, const u64 *scale) {
 
 template <int LG, int NT, bool NARROW>
 static void launch_divround_t(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
-    // one CTA per SM is resident (the limb fills shared memory): nsm ahead is the next wave
     k_divround_ntt<LG, NT, NARROW><<<grid, NT, NttCfg<LG>::SMEM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d,
-                                                                       (int)tab.ext, d_desc, tw,
-                                                                       c->prefetch ? c->nsm : 0);
+                                                                       (int)tab.ext, d_desc, tw);
 }
 
 template <int LG>
@@ -670,13 +660,10 @@ int ksw_ip(Ctx *c, int lv, const RotDesc *d_rots, int nrot) {
 // of one limb.
 // RED: the output sums are kept reduced (one Montgomery product and a modular
 // add per use: half the registers of the lazy 128-bit sums).
-// pf > 0: the CTA also asks L2 for the key rows of its slice of the first
-// entry of item blockIdx.y + pf (about one wave of resident CTAs ahead), so
-// that the DRAM reads of the CTAs to come are under way while these run.
 template <int G, int MINB, bool RED>
 __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, int np, int L, int logN,
                                                    const ModDev *__restrict__ mods, const LtEntry *__restrict__ ents,
-                                                   const LtItem *__restrict__ items, int pf) {
+                                                   const LtItem *__restrict__ items) {
     const int N = 1 << logN;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
@@ -685,12 +672,6 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
     const int gm = e < lv ? e : L + (e - lv);
     const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
     const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
-    if (pf > 0 && blockIdx.y + pf < gridDim.y) {
-        const int row = threadIdx.x >> 4, line = threadIdx.x & 15;  // 16 lines of 128 bytes per 2 KB row
-        const LtItem *it2 = items + blockIdx.y + pf;
-        const u64 *key2 = it2->count > 0 ? ents[it2->first].key : nullptr;
-        if (key2 && row < 2 * nd) prefetch_l2(key2 + (size_t)row * kstep + (size_t)gm * N + blockIdx.x * 256 + line * 16);
-    }
     Acc s0[RED ? 1 : G], s1[RED ? 1 : G];
     u64 r0[RED ? G : 1], r1[RED ? G : 1];
 #pragma unroll
@@ -1228,10 +1209,8 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
     for (int i0 = 0; i0 < nitems; i0 += kMaxGridZ) {
         const dim3 grid((unsigned)((c->N + 255) / 256), (unsigned)std::min(kMaxGridZ, nitems - i0), (unsigned)ne);
         const LtItem *it = d_items + i0;
-        // items one wave of resident CTAs ahead (six 256-thread CTAs per SM)
-        const int pf = c->prefetch && group == 1 ? std::max(1, 6 * c->nsm / (int)grid.x) : 0;
 #define HG_LTG(G, MB, RED) \
-    k_lt_grp<G, MB, RED><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it, pf)
+    k_lt_grp<G, MB, RED><<<grid, 256, 0, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it)
         const bool staged = (c->lt_kernel == 6 || c->lt_kernel == 7) && nd <= TMA_MAX_ND;
         if (group == 1) {  // items of one output
             if (staged && c->lt_one == 1) {

@@ -22,7 +22,7 @@ ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
 ALG_1X = 3  # Algorithm 1 with the extended pre-layout (not in the paper; AUTO never picks it)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_ONE = 1, 2, 3, 4, 5, 6
-TUNE_WAIT_LIMIT, TUNE_TEST_DROP, TUNE_NTT_THREADS, TUNE_GROUPS, TUNE_PREFETCH = 7, 8, 9, 10, 11
+TUNE_WAIT_LIMIT, TUNE_TEST_DROP, TUNE_NTT_THREADS, TUNE_GROUPS = 7, 8, 9, 10
 ROLE_A, ROLE_B = 0, 1
 KEYS_DIRECT, KEYS_POW2 = 0, 1  # hegmm_set_key_policy
 
