@@ -406,7 +406,7 @@ int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows
  * is kept in the context; then, with the fastest of those, the NTT-family
  * thread counts (HEGMM_TUNE_NTT_THREADS 0, 512, 1024, on rings where both
  * forms exist), then two sub-batches (HEGMM_TUNE_GROUPS 2) for two or more
- * products.  chosen (may be NULL, else 5 ints) receives {kernel variant,
+ * products, kept only when at least 2% faster.  chosen (may be NULL, else 5 ints) receives {kernel variant,
  * entries per item, one-output kernel, NTT threads, sub-batches}.  Results stay
  * bit for bit the same (every candidate is an execution order of the same
  * sums).  The linear-transformation knobs only steer the HEGMM_KS_DOUBLE

@@ -2185,8 +2185,22 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (c->N / 8 >= 1024)
         for (int nt : {0, 512, 1024})
             if (ok && (nt != bn || best > 1e29f)) ok = trial(bk, bc, bs, nt);
-    // two concurrent sub-batches, with the best of the rest
-    if (ok && count >= 2) ok = trial(bk, bc, bs, bn, 2);
+    // two concurrent sub-batches, with the best of the rest; kept only when
+    // at least 2% faster (their kernels share the GPU, which blurs each
+    // kernel's own time, so a tie goes to the single plan)
+    if (ok && count >= 2) {
+        const float single = best;
+        const int b0[5] = {bk, bc, bs, bn, bg};
+        ok = trial(bk, bc, bs, bn, 2);
+        if (ok && bg == 2 && best > 0.98f * single) {
+            best = single;
+            bk = b0[0];
+            bc = b0[1];
+            bs = b0[2];
+            bn = b0[3];
+            bg = b0[4];
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     drop_plans();
