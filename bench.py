@@ -735,6 +735,8 @@ def run_product(args):
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, args.lt_chunk)
     if args.ntt_threads >= 0:
         ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, args.ntt_threads)
+    if args.moddown_split >= 0:
+        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, args.moddown_split)
     m, l, n = (int(v) for v in args.shape.lower().split("x"))
     A, Bm = W.matrices(m, l, n, *(W.PAPER_RANGE if args.ring == "paper" else W.MEDIUM_RANGE))
     ctx.hegmm_keygen(KEY_SEED, [(m, l, n)], args.alg)
@@ -907,10 +909,11 @@ def measure_throughput(kind, args, H, dev, stream, world, rank, full=True, profi
     # mislead the autotuner: profiling runs pass the plain run's choice)
     tuning = None
     fixed = {k: v for k, v in (("lt_kernel", args.lt_kernel), ("lt_chunk", args.lt_chunk), ("lt_one", args.lt_one),
-                               ("ntt_threads", args.ntt_threads), ("groups", args.groups)) if v >= 0}
+                               ("ntt_threads", args.ntt_threads), ("groups", args.groups),
+                               ("moddown_split", args.moddown_split)) if v >= 0}
     if fixed:
         knob = {"lt_kernel": H.TUNE_LT_KERNEL, "lt_chunk": H.TUNE_LT_CHUNK, "lt_one": H.TUNE_LT_ONE,
-                "ntt_threads": H.TUNE_NTT_THREADS, "groups": H.TUNE_GROUPS}
+                "ntt_threads": H.TUNE_NTT_THREADS, "groups": H.TUNE_GROUPS, "moddown_split": H.TUNE_MODDOWN_SPLIT}
         for k, v in fixed.items():
             ctx.hegmm_set_tuning(knob[k], v)
         tuning = dict(fixed, given=True)
@@ -1095,6 +1098,8 @@ def main():
     ap.add_argument("--ntt-threads", type=int, default=-1,
                     help="HEGMM_TUNE_NTT_THREADS (0 by launch size, 512, 1024; -1: autotuned, or the library's choice "
                          "for --workload product)")
+    ap.add_argument("--moddown-split", type=int, default=-1,
+                    help="HEGMM_TUNE_MODDOWN_SPLIT (0 or 1; -1: autotuned, or the library default for --workload product)")
     ap.add_argument("--groups", type=int, default=-1,
                     help="HEGMM_TUNE_GROUPS concurrent sub-batches (1 or 2; -1: autotuned)")
     ap.add_argument("--ingest-ncu", nargs="+", metavar="CSV:JSON",

@@ -1706,6 +1706,7 @@ static int matmul_run_one(Ctx *c, int count, const hegmm_ct *const *A, const heg
     key.push_back(c->key_pow2);
     key.push_back((int)std::min<size_t>(c->ws_budget >> 20, 1 << 30));
     key.push_back(c->par_slot);  // a plan's workspace is ordered on the stream it was built for
+    key.push_back(c->moddown_split);
     BatchPlan *P;
     auto it = cache ? c->bplans.find(key) : c->bplans.end();
     if (it != c->bplans.end()) {
@@ -2110,7 +2111,8 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (!h || count <= 0 || !A || !B || !mln) return HEGMM_EINVAL;
     Ctx *c = &h->c;
     if (reps < 1) reps = 3;
-    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one, nt0 = c->ntt_threads, g0 = c->par_groups;
+    const int k0 = c->lt_kernel, ch0 = c->lt_chunk, s0 = c->lt_one, nt0 = c->ntt_threads, g0 = c->par_groups,
+              md0 = c->moddown_split;
     auto report = [&]() {
         if (chosen) {
             chosen[0] = c->lt_kernel;
@@ -2118,6 +2120,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
             chosen[2] = c->lt_one;
             chosen[3] = c->ntt_threads;
             chosen[4] = c->par_groups;
+            chosen[5] = c->moddown_split;
         }
         return HEGMM_OK;
     };
@@ -2140,15 +2143,17 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bk = k0, bc = ch0, bs = s0, bn = nt0, bg = g0, rc = HEGMM_OK;
+    int bk = k0, bc = ch0, bs = s0, bn = nt0, bg = g0, bm = md0, rc = HEGMM_OK;
     c->par_groups = 1;
+    c->moddown_split = 0;
     // times one candidate; false when a run failed (rc holds the error)
-    auto trial = [&](int kv, int chunk, int one, int nt, int groups = 1) {
+    auto trial = [&](int kv, int chunk, int one, int nt, int groups = 1, int split = 0) {
         c->lt_kernel = kv;
         c->lt_chunk = chunk;
         c->lt_one = one;
         c->ntt_threads = nt;
         c->par_groups = groups;
+        c->moddown_split = split;
         for (int w = 0; w < 2 && !rc; w++) rc = run();  // plan build, then graph capture
         if (rc) return false;
         cudaEventRecord(e0, c->st);
@@ -2164,6 +2169,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
             bs = one;
             bn = nt;
             bg = groups;
+            bm = split;
         }
         drop_plans();
         return true;
@@ -2185,13 +2191,15 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (c->N / 8 >= 1024)
         for (int nt : {0, 512, 1024})
             if (ok && (nt != bn || best > 1e29f)) ok = trial(bk, bc, bs, nt);
+    // the fused ModDown as two half-limb CTAs per limb
+    if (ok && c->N >= 8192) ok = trial(bk, bc, bs, bn, 1, 1);
     // two concurrent sub-batches, with the best of the rest; kept only when
     // at least 2% faster (their kernels share the GPU, which blurs each
     // kernel's own time, so a tie goes to the single plan)
     if (ok && count >= 2) {
         const float single = best;
-        const int b0[5] = {bk, bc, bs, bn, bg};
-        ok = trial(bk, bc, bs, bn, 2);
+        const int b0[6] = {bk, bc, bs, bn, bg, bm};
+        ok = trial(bk, bc, bs, bn, 2, bm);
         if (ok && bg == 2 && best > 0.98f * single) {
             best = single;
             bk = b0[0];
@@ -2199,6 +2207,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
             bs = b0[2];
             bn = b0[3];
             bg = b0[4];
+            bm = b0[5];
         }
     }
     cudaEventDestroy(e0);
@@ -2210,6 +2219,7 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     c->lt_one = rc ? s0 : bs;
     c->ntt_threads = rc ? nt0 : bn;
     c->par_groups = rc ? g0 : bg;
+    c->moddown_split = rc ? md0 : bm;
     if (rc) return rc;
     return report();
 }
@@ -2261,6 +2271,11 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
     if (knob == HEGMM_TUNE_GRAPHS) {
         if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "graphs must be 0 or 1");
         c->use_graphs = (int)value;
+        return HEGMM_OK;
+    }
+    if (knob == HEGMM_TUNE_MODDOWN_SPLIT) {
+        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "moddown split must be 0 or 1");
+        c->moddown_split = (int)value;
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_GROUPS) {

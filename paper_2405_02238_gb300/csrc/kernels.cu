@@ -284,6 +284,117 @@ __global__ void __launch_bounds__(NT, NttMinBlocks<LOGN, NT>::V) k_divround_ntt(
     }
 }
 
+// The same ModDown with each output limb split between two CTAs of 512
+// threads, one per half of the limb (the forward transform's first stage
+// pairs c with c + N/2; every later stage stays inside a half).  Each CTA
+// converts all N coefficients (the first stage needs both halves), computes
+// that stage's outputs for its own half only, runs the remaining stages on
+// N/2 values and writes its half; the values it produces are those of
+// k_divround_ntt, stage for stage.  A half limb takes 69.6 KB of shared
+// memory at N = 2^14, so two CTAs share an SM and one's loads and barriers
+// overlap the other's butterflies.  Grid: 2 CTAs per (polynomial, kept
+// prime), prime-major as k_divround_ntt.
+template <int LOGN>
+struct DivHalfCfg {
+    static constexpr int N = 1 << LOGN, NT = 512;
+    static constexpr size_t SMEM = (size_t)(N / 2 + N / 32) * 8;
+};
+
+template <int LOGN, bool NARROW>
+__global__ void __launch_bounds__(512, 2) k_divround_half(int nkeep, int ndrop, const ModDev *__restrict__ mods,
+                                                          const u64 *__restrict__ tab, int ext,
+                                                          const DivDesc *__restrict__ desc,
+                                                          const TwPair *__restrict__ tw) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = 512, HALF = N / 2, G = N / 8;
+    constexpr int RL = NttPasses<LOGN>::RL, LAST = NttPasses<LOGN>::LAST;
+    const int h = blockIdx.x & 1, cta = blockIdx.x >> 1;
+    const int npoly = (gridDim.x >> 1) / nkeep;
+    const int i = cta / npoly, b = cta - i * npoly;
+    const DivDesc d = desc[b];
+    const u64 *tB = tab + 2 * ndrop;
+    const u64 *tC = tB + (size_t)3 * nkeep * ndrop;
+    const u64 *tI = tC + (size_t)4 * nkeep;
+    const int mi = (int)tI[i];
+    const ModDev M = mods[mi];
+    const u64 *hB = tB + (size_t)i * ndrop * 3;
+    const u64 *hE = tab + ext + (size_t)i * ndrop * 3;
+    const TwPair *T = tw_of(tw, mi, 0, N);
+    const int off = h * HALF;  // first element of this CTA's half
+    for (int w = threadIdx.x * 16; w < HALF; w += NT * 16) {
+        prefetch_l2(d.u + (size_t)i * N + off + w);
+        if (d.add) prefetch_l2(d.add + (size_t)i * N + off + w);
+    }
+    // prologue: the conversion of the group's 8 coefficients (both halves),
+    // the first stage for this half's 4, then stages 1 and 2 on them
+    const u64 q4 = 4 * M.q;
+    for (int g = threadIdx.x; g < G; g += NT) {
+        u64 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = 0;
+        for (int kk = 0; kk < ndrop; kk++) {
+            const u64 dk = mods[tI[nkeep + kk]].q;
+            const u64 lc = NARROW ? __ldg(hE + 3 * kk + 2) : __ldg(hB + 3 * kk + 2);
+            const u64 w = __ldg(hE + 3 * kk), ws = __ldg(hE + 3 * kk + 1);
+            const u64 *zp = d.u + (size_t)(nkeep + kk) * N + g;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const u64 z = zp[k * (N / 8)];
+                const u64 v = NARROW ? centred_narrow(z, dk >> 1, lc) : centred(z, dk, lc, M.q, M.barr);
+                x[k] += mulsh_approx(v, w, ws, M.q);
+            }
+        }
+        const TwPair t1 = T[1];
+        u64 y[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const u64 t = mulsh_approx(x[k + 4], t1.w, t1.wp, M.q);
+            y[k] = h ? x[k] + (q4 - t) : x[k] + t;
+        }
+        ntt_fwd_regs<2>(y, h, 1, T, M.q);
+#pragma unroll
+        for (int k = 0; k < 4; k++) sm[pad16(g + k * (N / 8))] = y[k];
+    }
+    __syncthreads();
+    // middle passes on this half's groups
+#pragma unroll
+    for (int s0 = 3; s0 < LAST; s0 += 3) {
+        const int ltl = LOGN - s0 - 3, tl = 1 << ltl;
+        for (int gl = threadIdx.x; gl < G / 2; gl += NT) {
+            const int g = gl + h * (G / 2);
+            const int B = g >> ltl, o = g & (tl - 1);
+            const int base = (B << (ltl + 3)) + o - off;
+            u64 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) x[k] = sm[pad16(base + k * tl)];
+            ntt_fwd_regs<3>(x, B, s0, T, M.q);
+#pragma unroll
+            for (int k = 0; k < 8; k++) sm[pad16(base + k * tl)] = x[k];
+        }
+        __syncthreads();
+    }
+    const u64 *k4 = tC + 4 * i;
+    const u64 Di = k4[0], Dis = k4[1], q128 = M.q << 7;
+    const u64 *ui = d.u + (size_t)i * N;
+    u64 *oi = d.out + (size_t)i * N;
+    // last pass fused with the epilogue
+    for (int gl = threadIdx.x; gl < (HALF >> RL); gl += NT) {
+        const int g = gl + h * (HALF >> RL);
+        u64 x[1 << RL];
+        const int base = g << RL;
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) x[k] = sm[pad16(base + k - off)];
+        ntt_fwd_regs<RL>(x, g, LAST, T, M.q);
+#pragma unroll
+        for (int k = 0; k < (1 << RL); k++) {
+            const int c = base + k;
+            u64 v = mulsh(ui[c] + (q128 - x[k]), Di, Dis, M.q);
+            if (d.add) v = addm(v, d.add[(size_t)i * N + (d.g == 1 ? (u32)c : auto_src((u32)c, d.g, LOGN))], M.q);
+            oi[c] = v;
+        }
+    }
+}
+
 // ModUp, fused: one CTA per (input, digit j, prime e outside digit j):
 // prologue computes the digit's centred fast base conversion into prime e
 // from the coefficient-form source limbs, which arrive already multiplied
@@ -374,7 +485,15 @@ static int set_smem_attrs_nt() {
 
 template <int LOGN>
 static int set_smem_attrs() {
-    return set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_A>() || set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_B>();
+    if (set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_A>() || set_smem_attrs_nt<LOGN, NttCfg<LOGN>::NT_B>()) return 1;
+    if constexpr (LOGN >= 13) {
+        const int sm = (int)DivHalfCfg<LOGN>::SMEM;
+        const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (cudaFuncSetAttribute(k_divround_half<LOGN, false>, A, sm) != cudaSuccess ||
+            cudaFuncSetAttribute(k_divround_half<LOGN, true>, A, sm) != cudaSuccess)
+            return 1;
+    }
+    return 0;
 }
 
 static int init_staged_kernels();
@@ -449,6 +568,18 @@ static void launch_divround_t(Ctx *c, int grid, const DivTab &tab, const DivDesc
 
 template <int LG>
 static void launch_divround(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
+    if constexpr (LG >= 13) {
+        if (c->moddown_split) {  // two half-limb CTAs per output limb
+            constexpr size_t SM = DivHalfCfg<LG>::SMEM;
+            if (tab.narrow)
+                k_divround_half<LG, true><<<2 * grid, 512, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d,
+                                                                         (int)tab.ext, d_desc, tw);
+            else
+                k_divround_half<LG, false><<<2 * grid, 512, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d,
+                                                                          (int)tab.ext, d_desc, tw);
+            return;
+        }
+    }
     constexpr int NT = NttCfg<LG>::NT_A, NW = NttCfg<LG>::NT_B;
     const bool w = ntt_wide<LG>(c, grid);
     if (tab.narrow) {

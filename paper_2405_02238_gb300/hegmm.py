@@ -22,7 +22,7 @@ ALG_AUTO, ALG_1, ALG_2 = 0, 1, 2
 KS_SINGLE, KS_DOUBLE, KS_LAZY_RELIN, KS_SHARED = 0, 1, 2, 4  # hegmm_set_keyswitch_mode (flags combine)
 ALG_1X = 3  # Algorithm 1 with the extended pre-layout (not in the paper; AUTO never picks it)
 TUNE_LT_CHUNK, TUNE_LT_FUSED, TUNE_LT_KERNEL, TUNE_GIANT_COST, TUNE_GRAPHS, TUNE_LT_ONE = 1, 2, 3, 4, 5, 6
-TUNE_WAIT_LIMIT, TUNE_TEST_DROP, TUNE_NTT_THREADS, TUNE_GROUPS = 7, 8, 9, 10
+TUNE_WAIT_LIMIT, TUNE_TEST_DROP, TUNE_NTT_THREADS, TUNE_GROUPS, TUNE_MODDOWN_SPLIT = 7, 8, 9, 10, 11
 ROLE_A, ROLE_B = 0, 1
 KEYS_DIRECT, KEYS_POW2 = 0, 1  # hegmm_set_key_policy
 
@@ -325,12 +325,12 @@ class Context:
         pb = (vp * n)(*[b.h for b in Bs])
         mln = np.ascontiguousarray(np.array(shapes, dtype=np.int32).reshape(-1))
         al = None if algs is None else np.ascontiguousarray(np.array(algs, dtype=np.int32))
-        chosen = np.zeros(5, dtype=np.int32)
+        chosen = np.zeros(6, dtype=np.int32)
         self._check(self.lib.hegmm_autotune(self.h, n, pa, pb, mln.ctypes.data_as(intp),
                                             None if al is None else al.ctypes.data_as(intp), int(reps),
                                             chosen.ctypes.data_as(intp)), "autotune")
         return {"lt_kernel": int(chosen[0]), "lt_chunk": int(chosen[1]), "lt_one": int(chosen[2]),
-                "ntt_threads": int(chosen[3]), "groups": int(chosen[4])}
+                "ntt_threads": int(chosen[3]), "groups": int(chosen[4]), "moddown_split": int(chosen[5])}
 
     def hegmm_set_tuning(self, knob: int, value: int):
         self._check(self.lib.hegmm_set_tuning(self.h, int(knob), int(value)), "set_tuning")

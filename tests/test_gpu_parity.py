@@ -319,3 +319,33 @@ def test_ntt_thread_counts_change_no_bit(H, name):
             assert (ctx.hegmm_ct_export(ctx.hegmm_mult(ct, ct)) == o.mult_relin(co, co)).all(), nt
     finally:
         ctx.hegmm_set_tuning(H.TUNE_NTT_THREADS, 0)
+
+
+@pytest.mark.parametrize("name", ["medium", "paper"])
+def test_moddown_split_changes_no_bit(H, name):
+    # the fused ModDown as two half-limb CTAs per limb gives the oracle's
+    # rotation and relinearised product, and a double-hoisted product (whose
+    # outputs all go through the fused ModDown) equal to the one-CTA form's
+    pre, ctx, o = get_pair(H, name)
+    x = rand_slots(o, 13)
+    ct, co = enc_pair(ctx, o, x, 9, 0)
+    ctx.hegmm_keygen_rotations([7])
+    shape = (16, 32, 24) if name == "medium" else (32, 64, 16)
+    ctx.hegmm_keygen(SEED, [shape], 2)
+    A, B = W.matrices(*shape, 0, 15, seed=2)
+    ca = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_A, A, *shape, 2), 9, 10)
+    cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, *shape, 2), 9, 11)
+    ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED)
+    try:
+        ref, _ = ctx.hegmm_matmul(ca, cb, *shape, 2)
+        ref = ctx.hegmm_ct_export(ref)
+        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 1)
+        for _ in range(2):
+            assert (ctx.hegmm_ct_export(ctx.hegmm_rotate(ct, 7)) == o.rotate(co, 7)).all()
+            assert (ctx.hegmm_ct_export(ctx.hegmm_mult(ct, ct)) == o.mult_relin(co, co)).all()
+            c, _ = ctx.hegmm_matmul(ca, cb, *shape, 2)
+            assert (ctx.hegmm_ct_export(c) == ref).all()
+        assert (ctx.hegmm_decrypt(c, *shape, 2).astype(np.int64) == (A @ B) % pre.t).all()
+    finally:
+        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 0)
+        ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
