@@ -2182,9 +2182,10 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
                     if (one && (kv < 6 || kv == 8)) continue;  // staged one-output kernel: variants 6 and 7 only
                     if (ok) ok = trial(kv, chunk, one, nt0);
                 }
-        // the plain one-output kernel at lower occupancy, with the best of the rest
+        // the plain one-output kernel at lower occupancy, and with its operands
+        // fetched by asynchronous copies, with the best of the rest
         if (ok && bs == 0 && bk != 8)
-            for (int one : {2, 3})
+            for (int one : {2, 3, 4, 5})
                 if (ok) ok = trial(bk, bc, one, nt0);
     }
     // threads of the NTT-family CTAs (rings with N / 8 >= 1024 have two forms)
@@ -2254,7 +2255,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_ONE) {
-        if (value < 0 || value > 3) return set_err(c, HEGMM_EINVAL, "lt_one must be in 0..3");
+        if (value < 0 || value > 5) return set_err(c, HEGMM_EINVAL, "lt_one must be in 0..5");
         c->lt_one = (int)value;
         return HEGMM_OK;
     }

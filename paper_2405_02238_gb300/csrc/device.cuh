@@ -126,6 +126,13 @@ HDI u32 auto_src(u32 c, u32 g, int logN) {
 // (a multiple of 16, both addresses 16-byte aligned) from global to shared
 // memory and reports completion to an mbarrier as transaction bytes.
 __device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+
+// One 8-byte asynchronous copy global -> shared (no register is held while
+// it is in flight); cp_async_wait_all waits for the calling thread's copies.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void mbar_init(u64 *bar, u32 count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }

@@ -867,6 +867,81 @@ __global__ void __launch_bounds__(256, MINB) k_lt_grp(int lv, int ne, int nd, in
 }
 
 
+// Items of one output with every operand of an entry fetched by per-thread
+// asynchronous copies into shared memory (cp.async): the key words, the
+// gathered digits, c0 and the mask are all in flight at once without
+// holding registers, so the CTA count per SM, not the register budget,
+// sets how many loads are outstanding.  Each thread reads back only the
+// slots it filled (slot k of thread t at lsm[k 256 + t]), so no barrier is
+// needed.  The sums are those of k_lt_grp<1, ., false> (exact 128-bit
+// accumulations).  Shared memory: (3 nd + 2) 2 KB.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_lt_one_cpa(int lv, int ne, int nd, int np, int L, int logN,
+                                                       const ModDev *__restrict__ mods,
+                                                       const LtEntry *__restrict__ ents,
+                                                       const LtItem *__restrict__ items) {
+    extern __shared__ u64 lsm[];
+    const int N = 1 << logN;
+    const int tid = threadIdx.x;
+    const int c = blockIdx.x * 256 + tid;  // N is a multiple of 256
+    const int e = blockIdx.z;
+    const LtItem *it = items + blockIdx.y;
+    const int gm = e < lv ? e : L + (e - lv);
+    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
+    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
+    u64 *my = lsm + tid;
+    const int sD = 2 * nd, sC = 3 * nd, sM = 3 * nd + 1;
+    Acc s0{0, 0}, s1{0, 0};
+    const int t0 = it->first, t1 = t0 + it->count;
+    for (int t = t0; t < t1; t++) {
+        const LtEntry *E = ents + t;
+        const u64 *key = E->key;
+        if (!key && e >= lv) continue;  // P ct is 0 on the special primes
+        const bool used = E->used & 1u;
+        if (key) {
+            const u32 src = auto_src((u32)c, E->g, logN);
+            const u64 *Dp = E->D + (size_t)e * N + src;
+            const u64 *Kp = key + moff;
+            for (int j = 0; j < nd; j++) {
+                cp_async8(my + (size_t)(2 * j) * 256, Kp + (size_t)(2 * j) * kstep);
+                cp_async8(my + (size_t)(2 * j + 1) * 256, Kp + (size_t)(2 * j + 1) * kstep);
+                cp_async8(my + (size_t)(sD + j) * 256, Dp + (size_t)j * dstep);
+            }
+            if (e < lv) cp_async8(my + (size_t)sC * 256, E->ct + (size_t)e * N + src);
+        } else {
+            cp_async8(my, E->ct + (size_t)e * N + c);
+            cp_async8(my + 256, E->ct + ((size_t)lv + e) * N + c);
+        }
+        if (used) cp_async8(my + (size_t)sM * 256, E->mask[0] + moff);
+        cp_async_wait_all();
+        u64 u0, u1;
+        if (key) {
+            Acc a0{0, 0}, a1{0, 0};
+            if (e < lv) mac(a0, my[(size_t)sC * 256], pR);
+            for (int j = 0; j < nd; j++) {
+                const u64 x = my[(size_t)(sD + j) * 256];
+                mac(a0, x, my[(size_t)(2 * j) * 256]);
+                mac(a1, x, my[(size_t)(2 * j + 1) * 256]);
+            }
+            u0 = montred(a0, q, qinv);
+            u1 = montred(a1, q, qinv);
+        } else {
+            u0 = montmul(my[0], pR, q, qinv);
+            u1 = montmul(my[256], pR, q, qinv);
+        }
+        if (used) {
+            const u64 mv = my[(size_t)sM * 256];
+            mac(s0, u0, mv);
+            mac(s1, u1, mv);
+        }
+    }
+    u64 *o = it->out[0];
+    if (o) {
+        o[(size_t)e * N + c] = montred(s0, q, qinv);
+        o[((size_t)ne + e) * N + c] = montred(s1, q, qinv);
+    }
+}
+
 // The 8-output kernel with its streamed operands staged by the TMA engine:
 // one CTA per (256 coefficients, item, limb); thread 0 issues, for entry
 // t + 1, bulk copies of the key rows (2 nd rows of 2 KB) and of every used
@@ -1303,6 +1378,7 @@ __global__ void __launch_bounds__(288, 2) k_lt_grp_pws(int lv, int ne, int nd, i
 }
 
 constexpr int WS_STAGES = 3;
+constexpr int LT_CPA_MAX_SMEM = (3 * TMA_MAX_ND + 2) * 256 * 8;  // k_lt_one_cpa's shared memory at nd = 8
 
 static int init_staged_kernels() {
     const int smem8 = (int)((2 * (size_t)(2 * TMA_MAX_ND + LT_GROUP) * 256 + 2) * 8);
@@ -1314,7 +1390,11 @@ static int init_staged_kernels() {
                                 smemw) != cudaSuccess ||
            cudaFuncSetAttribute(k_lt_grp_pws<LT_GROUP, WS_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 smemw) != cudaSuccess ||
-           cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess;
+           cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess ||
+           cudaFuncSetAttribute(k_lt_one_cpa<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_CPA_MAX_SMEM) !=
+               cudaSuccess ||
+           cudaFuncSetAttribute(k_lt_one_cpa<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_CPA_MAX_SMEM) !=
+               cudaSuccess;
 }
 
 // Every item (of one or several outputs) in one launch of the persistent
@@ -1352,6 +1432,12 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
                 HG_LTG(1, 5, false);
             } else if (c->lt_one == 3) {
                 HG_LTG(1, 4, false);
+            } else if ((c->lt_one == 4 || c->lt_one == 5) && nd <= TMA_MAX_ND) {
+                const size_t smem = (size_t)(3 * nd + 2) * 256 * 8;
+                if (c->lt_one == 4)
+                    k_lt_one_cpa<6><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
+                else
+                    k_lt_one_cpa<7><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }

@@ -168,7 +168,8 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
 @pytest.mark.parametrize("chunk,variant,fused,one", [(1, 0, 1, 0), (3, 1, 1, 0), (4096, 2, 1, 0), (32, 3, 1, 0),
                                                       (5, 4, 1, 0), (32, 5, 1, 0), (32, 6, 1, 0), (3, 6, 1, 1),
                                                       (32, 7, 1, 0), (2, 7, 1, 1), (32, 7, 1, 2), (5, 0, 1, 3),
-                                                      (32, 0, 0, 0), (32, 8, 1, 0), (3, 8, 1, 0)])
+                                                      (32, 0, 0, 0), (32, 8, 1, 0), (3, 8, 1, 0), (32, 7, 1, 4),
+                                                      (2, 0, 1, 5)])
 def test_double_mode_executor_settings(H, chunk, variant, fused, one):
     # work-item size, fused-kernel variants and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
