@@ -281,9 +281,11 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     loads, 6 CTAs per SM (40 registers); 1 = key rows and masks staged by
  *     bulk asynchronous copies, 3 CTAs per SM (only with variants 6 and 7,
  *     else as 0); 2 = plain loads, 5 CTAs per SM (48 registers);
- *     3 = plain loads, 4 CTAs per SM (64 registers); 4 / 5 = every
- *     operand of an entry fetched by per-thread asynchronous copies into
- *     shared memory, 6 / 7 CTAs per SM (at most 8 digits, else as 0). */
+ *     3 = plain loads, 4 CTAs per SM (64 registers); 4 = every operand
+ *     of an entry fetched by per-thread asynchronous copies into shared
+ *     memory, 6 CTAs per SM; 5 = the same with two items per CTA, both
+ *     items' copies in flight together (4 and 5: at most 8 digits, else
+ *     as 0). */
 #define HEGMM_TUNE_LT_KERNEL 3
 /*   HEGMM_TUNE_GIANT_COST: the cost of one giant rotation, in baby key
  *     switches, in the greedy rule of HEGMM_KS_SHARED (1..65536, default 8).
