@@ -277,15 +277,13 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     persistent launch (two CTAs per SM) that walks the flattened queue of
  *     every (work item, limb, 256-coefficient slice) unit, items of one
  *     output included (HEGMM_TUNE_LT_ONE then has no effect).
- *   HEGMM_TUNE_LT_ONE: kernel of the items of one output: 0 (default) plain
+ *   HEGMM_TUNE_LT_ONE: kernel of the items of one output: 0 plain
  *     loads, 6 CTAs per SM (40 registers); 1 = key rows and masks staged by
  *     bulk asynchronous copies, 3 CTAs per SM (only with variants 6 and 7,
  *     else as 0); 2 = plain loads, 5 CTAs per SM (48 registers);
- *     3 = plain loads, 4 CTAs per SM (64 registers); 4 = every operand
- *     of an entry fetched by per-thread asynchronous copies into shared
- *     memory, 6 CTAs per SM; 5 = the same with two items per CTA, both
- *     items' copies in flight together (4 and 5: at most 8 digits, else
- *     as 0). */
+ *     3 = plain loads, 4 CTAs per SM (64 registers); 4 (default) = every
+ *     operand of an entry fetched by per-thread asynchronous copies into
+ *     shared memory, 6 CTAs per SM (at most 8 digits, else as 0). */
 #define HEGMM_TUNE_LT_KERNEL 3
 /*   HEGMM_TUNE_GIANT_COST: the cost of one giant rotation, in baby key
  *     switches, in the greedy rule of HEGMM_KS_SHARED (1..65536, default 8).
@@ -409,8 +407,9 @@ int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows
 
 /* Autotuner of the bit-neutral tuning knobs: runs the given products (as
  * hegmm_matmul_batch_algs would) under every candidate (kernel variant 0, 3,
- * 6, 7, 8; entries per item 16, 32, 64; one-output kernel 0, and 1 with
- * variants 6 / 7), then, from the fastest, the one-output kernels 2 to 5;
+ * 6, 7, 8; entries per item 16, 32, 64; one-output kernel 4, and 1 with
+ * variants 6 / 7), then, from the fastest, the one-output kernels 0, 2 and
+ * 3;
  * each candidate is timed over reps calls with CUDA events on the context
  * stream after a plan-building and a graph-capturing call, and the fastest
  * is kept in the context; then, with the fastest of those, the NTT-family

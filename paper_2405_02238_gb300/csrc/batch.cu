@@ -2178,14 +2178,13 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (c->ks_double) {  // the linear-transformation knobs only steer the double-hoisted kernels
         for (int kv : {0, 3, 6, 7, 8})
             for (int chunk : {16, 32, 64})
-                for (int one : {0, 1}) {
-                    if (one && (kv < 6 || kv == 8)) continue;  // staged one-output kernel: variants 6 and 7 only
+                for (int one : {4, 1}) {
+                    if (one == 1 && (kv < 6 || kv == 8)) continue;  // staged one-output kernel: variants 6 and 7 only
                     if (ok) ok = trial(kv, chunk, one, nt0);
                 }
-        // the plain one-output kernel at lower occupancy, and with its operands
-        // fetched by asynchronous copies, with the best of the rest
-        if (ok && bs == 0 && bk != 8)
-            for (int one : {2, 3, 4, 5})
+        // the plain-load one-output kernels, with the best of the rest
+        if (ok && bs == 4 && bk != 8)
+            for (int one : {0, 2, 3})
                 if (ok) ok = trial(bk, bc, one, nt0);
     }
     // threads of the NTT-family CTAs (rings with N / 8 >= 1024 have two forms)
@@ -2255,7 +2254,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_LT_ONE) {
-        if (value < 0 || value > 5) return set_err(c, HEGMM_EINVAL, "lt_one must be in 0..5");
+        if (value < 0 || value > 4) return set_err(c, HEGMM_EINVAL, "lt_one must be in 0..4");
         c->lt_one = (int)value;
         return HEGMM_OK;
     }

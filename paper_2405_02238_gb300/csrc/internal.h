@@ -227,7 +227,7 @@ struct Ctx {
     int lt_chunk = 32;                         // double mode: entries per k_lt_grp work item
     int lt_fused = 1;                          // double mode: fused kernel (1) or chunked rotations (0)
     int lt_kernel = 6;                         // grouped fused kernel variant (6: operands staged by TMA)
-    int lt_one = 0;                            // one-output kernel: 0/2/3 plain loads at 6/5/4 CTAs per SM, 1 staged
+    int lt_one = 4;                            // one-output kernel: 4 asynchronous copies, 0/2/3 plain loads at 6/5/4 CTAs per SM, 1 staged
     int ntt_threads = 0;                       // threads of an NTT-family CTA: 0 = by launch size, 512 or 1024
     size_t ws_budget = (size_t)1 << 30;        // scratch per chunked stage
     size_t mask_bytes = 0;

@@ -942,99 +942,6 @@ __global__ void __launch_bounds__(256, MINB) k_lt_one_cpa(int lv, int ne, int nd
     }
 }
 
-// The same with two items per CTA row: every thread issues the copies of
-// both items' current entries (into two banks of slots) before it waits,
-// so one CTA's descriptor and memory latencies cover two items.  Per item
-// the sums are k_lt_grp<1, ., false>'s.  Shared memory: 2 (3 nd + 2) 2 KB.
-// grid (N / 256, ceil(items / 2), limbs).
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_lt_one_cpa2(int lv, int ne, int nd, int np, int L, int logN,
-                                                        const ModDev *__restrict__ mods,
-                                                        const LtEntry *__restrict__ ents,
-                                                        const LtItem *__restrict__ items, int nitems) {
-    extern __shared__ u64 lsm[];
-    const int N = 1 << logN;
-    const int tid = threadIdx.x;
-    const int c = blockIdx.x * 256 + tid;  // N is a multiple of 256
-    const int e = blockIdx.z;
-    const int i0 = 2 * blockIdx.y, ni = min(2, nitems - i0);
-    const int gm = e < lv ? e : L + (e - lv);
-    const u64 q = mods[gm].q, qinv = mods[gm].qinv, pR = mods[gm].pR;
-    const size_t dstep = (size_t)ne * N, kstep = (size_t)np * N, moff = (size_t)gm * N + c;
-    const int slots = 3 * nd + 2, sD = 2 * nd, sC = 3 * nd, sM = 3 * nd + 1;
-    Acc s0[2] = {{0, 0}, {0, 0}}, s1[2] = {{0, 0}, {0, 0}};
-    int t[2], t1[2];
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        const LtItem *it = items + i0 + (h < ni ? h : 0);
-        t[h] = it->first;
-        t1[h] = h < ni ? t[h] + it->count : t[h];
-    }
-    while (t[0] < t1[0] || t[1] < t1[1]) {
-        const LtEntry *E[2] = {nullptr, nullptr};
-#pragma unroll
-        for (int h = 0; h < 2; h++) {  // issue this round's copies of both items
-            if (t[h] >= t1[h]) continue;
-            const LtEntry *En = ents + t[h]++;
-            const u64 *key = En->key;
-            if (!key && e >= lv) continue;  // P ct is 0 on the special primes
-            E[h] = En;
-            u64 *my = lsm + (size_t)h * slots * 256 + tid;
-            if (key) {
-                const u32 src = auto_src((u32)c, En->g, logN);
-                const u64 *Dp = En->D + (size_t)e * N + src;
-                const u64 *Kp = key + moff;
-                for (int j = 0; j < nd; j++) {
-                    cp_async8(my + (size_t)(2 * j) * 256, Kp + (size_t)(2 * j) * kstep);
-                    cp_async8(my + (size_t)(2 * j + 1) * 256, Kp + (size_t)(2 * j + 1) * kstep);
-                    cp_async8(my + (size_t)(sD + j) * 256, Dp + (size_t)j * dstep);
-                }
-                if (e < lv) cp_async8(my + (size_t)sC * 256, En->ct + (size_t)e * N + src);
-            } else {
-                cp_async8(my, En->ct + (size_t)e * N + c);
-                cp_async8(my + 256, En->ct + ((size_t)lv + e) * N + c);
-            }
-            if (En->used & 1u) cp_async8(my + (size_t)sM * 256, En->mask[0] + moff);
-        }
-        cp_async_wait_all();
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const LtEntry *En = E[h];
-            if (!En) continue;
-            const u64 *my = lsm + (size_t)h * slots * 256 + tid;
-            u64 u0, u1;
-            if (En->key) {
-                Acc a0{0, 0}, a1{0, 0};
-                if (e < lv) mac(a0, my[(size_t)sC * 256], pR);
-                for (int j = 0; j < nd; j++) {
-                    const u64 x = my[(size_t)(sD + j) * 256];
-                    mac(a0, x, my[(size_t)(2 * j) * 256]);
-                    mac(a1, x, my[(size_t)(2 * j + 1) * 256]);
-                }
-                u0 = montred(a0, q, qinv);
-                u1 = montred(a1, q, qinv);
-            } else {
-                u0 = montmul(my[0], pR, q, qinv);
-                u1 = montmul(my[256], pR, q, qinv);
-            }
-            if (En->used & 1u) {
-                const u64 mv = my[(size_t)sM * 256];
-                mac(s0[h], u0, mv);
-                mac(s1[h], u1, mv);
-            }
-        }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-        if (h >= ni) break;
-        u64 *o = items[i0 + h].out[0];
-        if (o) {
-            o[(size_t)e * N + c] = montred(s0[h], q, qinv);
-            o[((size_t)ne + e) * N + c] = montred(s1[h], q, qinv);
-        }
-    }
-}
-
 // The 8-output kernel with its streamed operands staged by the TMA engine:
 // one CTA per (256 coefficients, item, limb); thread 0 issues, for entry
 // t + 1, bulk copies of the key rows (2 nd rows of 2 KB) and of every used
@@ -1485,8 +1392,6 @@ static int init_staged_kernels() {
                                 smemw) != cudaSuccess ||
            cudaFuncSetAttribute(k_lt_grp_tma<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1) != cudaSuccess ||
            cudaFuncSetAttribute(k_lt_one_cpa<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, LT_CPA_MAX_SMEM) !=
-               cudaSuccess ||
-           cudaFuncSetAttribute(k_lt_one_cpa2<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * LT_CPA_MAX_SMEM) !=
                cudaSuccess;
 }
 
@@ -1525,15 +1430,9 @@ int lt_group(Ctx *c, int lv, int group, const LtEntry *d_ents, const LtItem *d_i
                 HG_LTG(1, 5, false);
             } else if (c->lt_one == 3) {
                 HG_LTG(1, 4, false);
-            } else if ((c->lt_one == 4 || c->lt_one == 5) && nd <= TMA_MAX_ND) {
+            } else if (c->lt_one == 4 && nd <= TMA_MAX_ND) {
                 const size_t smem = (size_t)(3 * nd + 2) * 256 * 8;
-                if (c->lt_one == 4) {
-                    k_lt_one_cpa<6><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
-                } else {
-                    const dim3 g2(grid.x, (grid.y + 1) / 2, grid.z);
-                    k_lt_one_cpa2<4><<<g2, 256, 2 * smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents,
-                                                                   it, (int)grid.y);
-                }
+                k_lt_one_cpa<6><<<grid, 256, smem, c->st>>>(lv, ne, nd, c->np, c->L, c->logN, c->d_mods, d_ents, it);
             } else {
                 HG_LTG(1, 6, false);  // few registers, six CTAs per SM
             }

@@ -160,14 +160,14 @@ def test_autotune_keeps_results(H, medium):
         As, Bs, mats = encrypt_all(ctx, H, shapes, *W.BATCH_RANGE, seed0=40, stream0=400)
         before = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_batch(As, Bs, shapes)]
         chosen = ctx.hegmm_autotune(As, Bs, shapes, reps=1)
-        assert chosen["lt_kernel"] in (0, 3, 6, 7) and chosen["lt_chunk"] in (16, 32, 64) and chosen["lt_one"] in (0, 1, 2, 3)
+        assert chosen["lt_kernel"] in (0, 3, 6, 7) and chosen["lt_chunk"] in (16, 32, 64) and chosen["lt_one"] in (0, 1, 2, 3, 4)
         after = [ctx.hegmm_ct_export(c) for c in ctx.hegmm_matmul_batch(As, Bs, shapes)]
         for x, y in zip(before, after):
             assert (x == y).all()
     finally:
         ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 6)
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
-        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 0)
+        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 4)
         ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
 
 

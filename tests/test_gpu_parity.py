@@ -169,7 +169,7 @@ def test_hegmm_tiny_bitexact(H, alg, mode):
                                                       (5, 4, 1, 0), (32, 5, 1, 0), (32, 6, 1, 0), (3, 6, 1, 1),
                                                       (32, 7, 1, 0), (2, 7, 1, 1), (32, 7, 1, 2), (5, 0, 1, 3),
                                                       (32, 0, 0, 0), (32, 8, 1, 0), (3, 8, 1, 0), (32, 7, 1, 4),
-                                                      (2, 0, 1, 5)])
+                                                      (2, 0, 1, 4)])
 def test_double_mode_executor_settings(H, chunk, variant, fused, one):
     # work-item size, fused-kernel variants and the chunked path change no bit
     pre, ctx, o = get_pair(H, "tiny")
@@ -186,7 +186,7 @@ def test_double_mode_executor_settings(H, chunk, variant, fused, one):
         ctx.hegmm_set_tuning(H.TUNE_LT_CHUNK, 32)
         ctx.hegmm_set_tuning(H.TUNE_LT_KERNEL, 6)
         ctx.hegmm_set_tuning(H.TUNE_LT_FUSED, 1)
-        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 0)
+        ctx.hegmm_set_tuning(H.TUNE_LT_ONE, 4)
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 1), (3, 3, 3), (5, 12, 7), (9, 4, 11), (7, 9, 2), (2, 5, 7),
