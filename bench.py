@@ -651,8 +651,9 @@ def kernel_source_sha():
 # The library's kernel buckets (hegmm_kernel_stats) of the CUDA kernels an
 # ncu log names, first match wins.
 NCU_BUCKETS = [("k_ntt<", lambda n: "ntt_inv" if n.split("<")[1].split(",")[1].strip() in ("1", "true") else "ntt_fwd"),
-               ("k_modup_", "modup"), ("k_divround_ntt", "divround_ntt"), ("k_ksw_ip", "ksw_inner_product"),
-               ("k_lt_grp", "lt_keyswitch"), ("k_lt_acc", "lt_accumulate"), ("k_tensor", "tensor"),
+               ("k_modup_", "modup"), ("k_divround_", "divround_ntt"), ("k_ksw_ip", "ksw_inner_product"),
+               ("k_lt_grp", "lt_keyswitch"), ("k_lt_one", "lt_keyswitch"), ("k_lt_acc", "lt_accumulate"),
+               ("k_tensor", "tensor"),
                ("k_sum", "sum")]
 NCU_UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "inst": 1, "Kinst": 1e3, "Minst": 1e6,
              "Ginst": 1e9, "": 1}
