@@ -797,7 +797,7 @@ def roofline(name, stats, hbm_peak, bfly_peak, issue_peak, counters):
         if ipb:
             r.update({"peak": issue_peak["warp_inst_per_s"] / ipb / 1e9, "warp_inst_per_butterfly": ipb,
                       "peak_source": "derived: %d SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (median "
-                                     "SM clock in the timed region) / %.1f warp-instructions per butterfly (ncu, "
+                                     "SM clock in the timed region) / %.2f warp-instructions per butterfly (ncu, "
                                      "these kernel sources)" % (issue_peak["sms"], issue_peak["mhz"], ipb)})
         else:
             r.update({"peak": bfly_peak / 1e9, "peak_source": "measured: hegmm_peak_butterflies (register-only "
