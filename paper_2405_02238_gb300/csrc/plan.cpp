@@ -119,17 +119,36 @@ int resolve_alg(int m, int l, int n, int alg, int S) {
     return 0;
 }
 
-// Group a destination -> source slot map by offset d = src - dst.
+// Group a destination -> source slot map by offset d = src - dst:
+// ascending offsets, ascending destinations within each.  Every
+// destination appears once, so two counting passes (by destination, then
+// stably by offset) order it without comparisons.
 static std::vector<Diag> group(const std::vector<std::pair<int, int>> &dst_src) {
-    std::map<int, std::vector<int>> g;
-    for (auto &ds : dst_src) g[ds.second - ds.first].push_back(ds.first);
     std::vector<Diag> out;
-    for (auto &kv : g) {
-        Diag d;
-        d.d = kv.first;
-        d.dst = kv.second;
-        std::sort(d.dst.begin(), d.dst.end());
-        out.push_back(d);
+    if (dst_src.empty()) return out;
+    int lo = dst_src[0].second - dst_src[0].first, hi = lo, dmax = 0;
+    for (auto &ds : dst_src) {
+        const int d = ds.second - ds.first;
+        lo = std::min(lo, d);
+        hi = std::max(hi, d);
+        dmax = std::max(dmax, ds.first);
+    }
+    std::vector<int> src_of((size_t)dmax + 1, -1);
+    for (auto &ds : dst_src) src_of[(size_t)ds.first] = ds.second;
+    std::vector<int> cnt((size_t)(hi - lo) + 2, 0);
+    for (auto &ds : dst_src) cnt[(size_t)(ds.second - ds.first - lo) + 1]++;
+    for (size_t i = 1; i < cnt.size(); i++) cnt[i] += cnt[i - 1];  // cnt[d - lo] = start of offset d
+    std::vector<int> slots(dst_src.size());
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int x = 0; x <= dmax; x++)
+        if (src_of[(size_t)x] >= 0) slots[(size_t)pos[(size_t)(src_of[(size_t)x] - x - lo)]++] = x;
+    for (int d = lo; d <= hi; d++) {
+        const int b = cnt[(size_t)(d - lo)], e = cnt[(size_t)(d - lo) + 1];
+        if (b == e) continue;
+        Diag g;
+        g.d = d;
+        g.dst.assign(slots.begin() + b, slots.begin() + e);
+        out.push_back(std::move(g));
     }
     return out;
 }
@@ -158,6 +177,8 @@ HostPlan make_host_plan(int m, int l, int n, int alg) {
         P.length = alg1_length(m, l, n);
         for (int k = 0; k < l; k++) {
             std::vector<std::pair<int, int>> e, o;
+            e.reserve((size_t)m * n);
+            o.reserve((size_t)m * n);
             for (int i = 0; i < m; i++)
                 for (int j = 0; j < n; j++) {
                     const int dst = P.flat(i, j, m, n);
@@ -191,6 +212,8 @@ HostPlan make_host_plan(int m, int l, int n, int alg) {
         P.length = alg1x_length(m, l, n);
         for (int k = 0; k < l; k++) {
             std::vector<std::pair<int, int>> e, o;
+            e.reserve((size_t)m * n);
+            o.reserve((size_t)m * n);
             for (int i = 0; i < m; i++)
                 for (int j = 0; j < n; j++) {
                     const int dst = P.flat(i, j, m, n);
@@ -222,6 +245,8 @@ HostPlan make_host_plan(int m, int l, int n, int alg) {
             seen[ph] = 1;
         }
         std::vector<std::pair<int, int>> e, o;
+        e.reserve((size_t)P.M * P.Np);
+        o.reserve((size_t)P.M * P.Np);
         for (int i = 0; i < P.M; i++)
             for (int j = 0; j < P.Np; j++) {
                 const int dst = P.flat(i, j, P.M, P.Np);
@@ -287,34 +312,56 @@ long long HostPlan::paper_cmult() const {
 }
 
 std::vector<GiantLT> giant_factor(const std::vector<const std::vector<Diag> *> &outs, int S, int cost) {
-    std::set<int> baby;
+    std::vector<char> in_baby((size_t)S, 0), in_z((size_t)S, 0);
+    std::vector<int> baby;                // the non-zero offsets used so far
+    std::vector<int> hits((size_t)S, 0);  // g -> #{z : (z - g) mod S in B or 0}
+    std::vector<int> touched;
     std::vector<GiantLT> res;
     for (const auto *ds : outs) {
-        std::set<int> Z;
-        for (const auto &d : *ds) Z.insert(imod(d.d, S));
-        std::map<int, int> hits;  // g -> #{z : (z - g) mod S in B or 0}
+        std::vector<int> Z;
+        for (const auto &d : *ds) {
+            const int z = imod(d.d, S);
+            if (!in_z[(size_t)z]) {
+                in_z[(size_t)z] = 1;
+                Z.push_back(z);
+            }
+        }
+        for (int z : Z) in_z[(size_t)z] = 0;
+        touched.clear();
+        auto hit = [&](int g) {
+            if (hits[(size_t)g]++ == 0) touched.push_back(g);
+        };
         for (int z : Z) {
-            hits[z]++;  // b = 0
-            for (int b : baby) hits[imod((long long)z - b, S)]++;
+            hit(z);  // b = 0
+            for (int b : baby) hit(imod((long long)z - b, S));
         }
         const int nz = (int)Z.size();
-        int best_g = 0, best_c = nz - (hits.count(0) ? hits[0] : 0);
-        for (const auto &kv : hits) {
-            if (kv.first == 0) continue;
-            const int cst = nz - kv.second + cost;
-            if (cst < best_c) {
-                best_g = kv.first;
+        // g = 0 first; among the others the smallest g of the lowest cost
+        int best_g = 0, best_c = nz - hits[0];
+        for (int g : touched) {
+            if (g == 0) continue;
+            const int cst = nz - hits[(size_t)g] + cost;
+            if (cst < best_c || (cst == best_c && best_g != 0 && g < best_g)) {
+                best_g = g;
                 best_c = cst;
             }
         }
+        for (int g : touched) hits[(size_t)g] = 0;
         GiantLT f;
         f.g = best_g;
         for (const auto &d : *ds) {
             GTerm t;
             t.b = imod((long long)d.d - best_g, S);
-            for (int x : d.dst) t.dst.push_back(imod((long long)x + best_g, S));
-            std::sort(t.dst.begin(), t.dst.end());
-            if (t.b) baby.insert(t.b);
+            // destinations + g mod S, ascending: d.dst is ascending in
+            // [0, S), so the ones that wrap (x + g >= S) come first
+            const auto wrap = std::lower_bound(d.dst.begin(), d.dst.end(), S - best_g);
+            t.dst.reserve(d.dst.size());
+            for (auto it = wrap; it != d.dst.end(); ++it) t.dst.push_back(*it + best_g - S);
+            for (auto it = d.dst.begin(); it != wrap; ++it) t.dst.push_back(*it + best_g);
+            if (t.b && !in_baby[(size_t)t.b]) {
+                in_baby[(size_t)t.b] = 1;
+                baby.push_back(t.b);
+            }
             f.terms.push_back(std::move(t));
         }
         res.push_back(std::move(f));
