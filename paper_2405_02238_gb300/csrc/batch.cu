@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <unordered_map>
 #include <array>
 #include <map>
 #include <set>
@@ -61,7 +62,6 @@ struct ShapeData {
     HostPlan hp;
     std::vector<long long> zs[2];
     std::map<long long, int> zidx[2];
-    std::map<std::vector<int>, int> mask_of;
     u64 *masks = nullptr;
     int nmask = 0;
     size_t bytes = 0;
@@ -563,20 +563,22 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
     // per operand and iteration the terms (rotation offset mod S, destination
     // slots of the mask): the plan's diagonals, or the shared-baby-step
     // factorisation with its giant rotations
-    std::vector<std::vector<std::vector<std::pair<long long, std::vector<int>>>>> tl(2);
+    // (the slot lists stay where the plan or the factorisation holds them)
+    std::vector<GiantLT> fac[2];
+    std::vector<std::vector<std::vector<std::pair<long long, const std::vector<int> *>>>> tl(2);
     for (int s = 0; s < 2; s++) {
         tl[s].resize(hp.iters.size());
         sd->giant[s].assign(hp.iters.size(), 0);
         if (sd->shared) {
-            std::vector<GiantLT> f = giant_factor_of(hp, s, S, shared);
-            for (size_t k = 0; k < f.size(); k++) {
-                sd->giant[s][k] = f[k].g;
-                for (auto &t : f[k].terms) tl[s][k].push_back({t.b, t.dst});
+            fac[s] = giant_factor_of(hp, s, S, shared);
+            for (size_t k = 0; k < fac[s].size(); k++) {
+                sd->giant[s][k] = fac[s][k].g;
+                for (auto &t : fac[s][k].terms) tl[s][k].push_back({t.b, &t.dst});
             }
         } else {
             for (size_t k = 0; k < hp.iters.size(); k++)
                 for (auto &d : (s == 0 ? hp.iters[k].eps : hp.iters[k].omg))
-                    tl[s][k].push_back({((long long)d.d % S + S) % S, d.dst});
+                    tl[s][k].push_back({((long long)d.d % S + S) % S, &d.dst});
         }
         std::set<long long> zs;
         for (auto &v : tl[s])
@@ -629,19 +631,33 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
     // masks: one per distinct slot set; value = product of the dropped primes mod t
     u64 scale = 1;
     for (int i = 0; i < c->prm.ms_drop; i++) scale = (u64)((unsigned __int128)scale * (c->q[c->L - 1 - i] % c->t) % c->t);
+    // one mask per distinct slot set, in order of first use; slot sets are
+    // matched by a hash of their contents, then compared
     std::vector<const std::vector<int> *> mlist;
+    std::unordered_map<u64, std::vector<int>> by_hash;
+    auto mask_index = [&](const std::vector<int> *v) {
+        u64 h = 1469598103934665603ull ^ v->size();
+        for (int x : *v) h = (h ^ (u64)(unsigned)x) * 1099511628211ull;
+        std::vector<int> &cand = by_hash[h];
+        for (int mi : cand)
+            if (*mlist[(size_t)mi] == *v) return mi;
+        cand.push_back((int)mlist.size());
+        mlist.push_back(v);
+        return (int)mlist.size() - 1;
+    };
+    std::vector<std::vector<std::vector<int>>> midx(2);
+    for (int s = 0; s < 2; s++) midx[s].resize(hp.iters.size());
     for (size_t k = 0; k < hp.iters.size(); k++)
         for (int s = 0; s < 2; s++)
-            for (auto &t : tl[s][k])
-                if (!sd->mask_of.count(t.second)) {
-                    sd->mask_of[t.second] = (int)mlist.size();
-                    mlist.push_back(&sd->mask_of.find(t.second)->first);
-                }
+            for (auto &t : tl[s][k]) midx[s][k].push_back(mask_index(t.second));
     sd->nmask = (int)mlist.size();
     for (int s = 0; s < 2; s++) {
         sd->dref[s].resize(hp.iters.size());
         for (size_t k = 0; k < hp.iters.size(); k++)
-            for (auto &t : tl[s][k]) sd->dref[s][k].push_back({t.first ? sd->zidx[s].at(t.first) : -1, sd->mask_of.at(t.second)});
+            for (size_t u = 0; u < tl[s][k].size(); u++) {
+                const long long z = tl[s][k][u].first;
+                sd->dref[s][k].push_back({z ? sd->zidx[s].at(z) : -1, midx[s][k][u]});
+            }
     }
     const int nm = c->L + c->K;
     sd->bytes = (size_t)sd->nmask * nm * c->N * 8;
@@ -661,7 +677,6 @@ static int get_shape(Ctx *c, int m, int l, int n, int alg, int shared, ShapeData
     }
     c->mask_bytes += sd->bytes;
     mlist.clear();
-    sd->mask_of.clear();  // only the per-diagonal indices are needed from here on
     sd->last_use = ++c->bplan_clock;
     const long long ni = (long long)hp.iters.size(), ne = (long long)hp.extract.size();
     hegmm_opcount &ct = sd->cnt;
