@@ -324,11 +324,12 @@ int hegmm_set_keyswitch_mode(hegmm_ctx *ctx, int mode);
  *     large ones.  Results are the same bits.  Not used while the context
  *     stream is being captured, nor by the server. */
 #define HEGMM_TUNE_GROUPS 10
-/*   HEGMM_TUNE_MODDOWN_SPLIT: 0 (default) runs the fused ModDown with one
- *     CTA per output limb; 1 splits every limb between two CTAs of 512
- *     threads, one per half (rings with N >= 2^13; smaller rings ignore
- *     it): each converts the whole limb for the transform's first stage and
- *     finishes its half, so that two CTAs share an SM.  Same bits. */
+/*   HEGMM_TUNE_MODDOWN_SPLIT: 0 runs the fused ModDown with one CTA per
+ *     output limb; 1 splits every limb between two CTAs of 512 threads, one
+ *     per half (rings with N >= 2^13; smaller rings ignore it): each
+ *     converts the whole limb for the transform's first stage and finishes
+ *     its half, so that two CTAs share an SM; 2 (default) splits only
+ *     launches of fewer limbs than twice the SMs.  Same bits. */
 #define HEGMM_TUNE_MODDOWN_SPLIT 11
 int hegmm_set_tuning(hegmm_ctx *ctx, int knob, long long value);
 
@@ -414,8 +415,8 @@ int hegmm_matmul_blocked(hegmm_ctx *ctx, int nr, int nk, int nc, const int *rows
  * stream after a plan-building and a graph-capturing call, and the fastest
  * is kept in the context; then, with the fastest of those, the NTT-family
  * thread counts (HEGMM_TUNE_NTT_THREADS 0, 512, 1024, on rings where both
- * forms exist), then the half-limb ModDown (HEGMM_TUNE_MODDOWN_SPLIT 1, rings
- * with N >= 2^13), then two sub-batches (HEGMM_TUNE_GROUPS 2) for two or
+ * forms exist), then the half-limb ModDown always or never
+ * (HEGMM_TUNE_MODDOWN_SPLIT 1, 0; rings with N >= 2^13), then two sub-batches (HEGMM_TUNE_GROUPS 2) for two or
  * more products, kept only when at least 2% faster.  chosen (may be NULL,
  * else 6 ints) receives {kernel variant, entries per item, one-output
  * kernel, NTT threads, sub-batches, ModDown split}.  Results stay

@@ -2160,9 +2160,9 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     float best = 1e30f;
     int bk = k0, bc = ch0, bs = s0, bn = nt0, bg = g0, bm = md0, rc = HEGMM_OK;
     c->par_groups = 1;
-    c->moddown_split = 0;
+    c->moddown_split = 2;
     // times one candidate; false when a run failed (rc holds the error)
-    auto trial = [&](int kv, int chunk, int one, int nt, int groups = 1, int split = 0) {
+    auto trial = [&](int kv, int chunk, int one, int nt, int groups = 1, int split = 2) {
         c->lt_kernel = kv;
         c->lt_chunk = chunk;
         c->lt_one = one;
@@ -2206,8 +2206,10 @@ int hegmm_autotune(hegmm_ctx *h, int count, const hegmm_ct *const *A, const hegm
     if (c->N / 8 >= 1024)
         for (int nt : {0, 512, 1024})
             if (ok && (nt != bn || best > 1e29f)) ok = trial(bk, bc, bs, nt);
-    // the fused ModDown as two half-limb CTAs per limb
-    if (ok && c->N >= 8192) ok = trial(bk, bc, bs, bn, 1, 1);
+    // the fused ModDown as two half-limb CTAs per limb always, or never
+    if (c->N >= 8192)
+        for (int split : {1, 0})
+            if (ok) ok = trial(bk, bc, bs, bn, 1, split);
     // two concurrent sub-batches, with the best of the rest; kept only when
     // at least 2% faster (their kernels share the GPU, which blurs each
     // kernel's own time, so a tie goes to the single plan)
@@ -2289,7 +2291,7 @@ int hegmm_set_tuning(hegmm_ctx *h, int knob, long long value) {
         return HEGMM_OK;
     }
     if (knob == HEGMM_TUNE_MODDOWN_SPLIT) {
-        if (value != 0 && value != 1) return set_err(c, HEGMM_EINVAL, "moddown split must be 0 or 1");
+        if (value < 0 || value > 2) return set_err(c, HEGMM_EINVAL, "moddown split must be 0, 1 or 2");
         c->moddown_split = (int)value;
         return HEGMM_OK;
     }

@@ -209,7 +209,7 @@ struct Ctx {
     unsigned long long bplan_clock = 0;
     std::vector<const BatchPlan *> pinned;     // cached plans in flight on a stream (never evicted)
     int par_groups = 1;                        // concurrent sub-batches of a cached batch (1 or 2)
-    int moddown_split = 0;                     // fused ModDown as two half-limb CTAs per limb (N >= 2^13)
+    int moddown_split = 2;                     // fused ModDown as two half-limb CTAs per limb (N >= 2^13): 0 never, 1 always, 2 small launches
     int par_slot = 0;                          // stream of the running sub-batch (0: st), part of plan keys
     bool in_groups = false;
     cudaStream_t par_st[2] = {nullptr, nullptr};

@@ -569,7 +569,10 @@ static void launch_divround_t(Ctx *c, int grid, const DivTab &tab, const DivDesc
 template <int LG>
 static void launch_divround(Ctx *c, int grid, const DivTab &tab, const DivDesc *d_desc, const TwPair *tw) {
     if constexpr (LG >= 13) {
-        if (c->moddown_split) {  // two half-limb CTAs per output limb
+        // two half-limb CTAs per output limb: always (1), or (2) for launches
+        // of fewer than two waves of one-CTA limbs, where twice the CTAs fill
+        // the SMs
+        if (c->moddown_split == 1 || (c->moddown_split == 2 && grid < 2 * c->nsm)) {
             constexpr size_t SM = DivHalfCfg<LG>::SMEM;
             if (tab.narrow)
                 k_divround_half<LG, true><<<2 * grid, 512, SM, c->st>>>(tab.nkeep, tab.ndrop, c->d_mods, tab.d,

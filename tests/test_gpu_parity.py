@@ -338,15 +338,16 @@ def test_moddown_split_changes_no_bit(H, name):
     cb = ctx.hegmm_encrypt(ctx.hegmm_encode(H.ROLE_B, B, *shape, 2), 9, 11)
     ctx.hegmm_set_keyswitch_mode(H.KS_DOUBLE | H.KS_LAZY_RELIN | H.KS_SHARED)
     try:
+        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 0)
         ref, _ = ctx.hegmm_matmul(ca, cb, *shape, 2)
         ref = ctx.hegmm_ct_export(ref)
-        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 1)
-        for _ in range(2):
-            assert (ctx.hegmm_ct_export(ctx.hegmm_rotate(ct, 7)) == o.rotate(co, 7)).all()
-            assert (ctx.hegmm_ct_export(ctx.hegmm_mult(ct, ct)) == o.mult_relin(co, co)).all()
+        for split in (1, 2, 1):
+            ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, split)
+            assert (ctx.hegmm_ct_export(ctx.hegmm_rotate(ct, 7)) == o.rotate(co, 7)).all(), split
+            assert (ctx.hegmm_ct_export(ctx.hegmm_mult(ct, ct)) == o.mult_relin(co, co)).all(), split
             c, _ = ctx.hegmm_matmul(ca, cb, *shape, 2)
-            assert (ctx.hegmm_ct_export(c) == ref).all()
+            assert (ctx.hegmm_ct_export(c) == ref).all(), split
         assert (ctx.hegmm_decrypt(c, *shape, 2).astype(np.int64) == (A @ B) % pre.t).all()
     finally:
-        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 0)
+        ctx.hegmm_set_tuning(H.TUNE_MODDOWN_SPLIT, 2)
         ctx.hegmm_set_keyswitch_mode(H.KS_SINGLE)
