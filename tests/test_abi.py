@@ -167,6 +167,27 @@ def test_host_shared_baby_steps_match_oracle(H):
                         oracle_giant(m, l, n, alg, S, role, cost), (m, l, n, alg, role, cost)
 
 
+def test_host_planner_matches_oracle_serving_shapes(H):
+    # larger, uneven shapes of the serving mix (17..64 per dimension): the
+    # diagonals (grouped by counting passes) and the shared-baby-step
+    # factorisation (giant shifts rotate sorted slot lists) term for term
+    rng = np.random.default_rng(11)
+    shapes = []
+    while len(shapes) < 5:
+        m, l, n = (int(v) for v in rng.integers(17, 65, size=3))
+        if SL.fits(m, l, n, 1, 8192):
+            shapes.append((m, l, n))
+    for m, l, n in shapes:
+        for alg in (1, 2, 3):
+            if not SL.fits(m, l, n, alg, 8192):
+                continue
+            assert H.hegmm_plan_describe(m, l, n, alg, 8192) == oracle_describe(m, l, n, alg, 8192), (m, l, n, alg)
+            if alg != 3:
+                for role in (0, 1):
+                    assert H.hegmm_plan_giant(m, l, n, alg, 8192, role) == oracle_giant(m, l, n, alg, 8192, role), \
+                        (m, l, n, alg, role)
+
+
 def test_context_refuses_more_modup_limbs_than_a_limb_pattern_holds(H):
     # L = 12, K = 4, alpha = 1: digits(L) (L + K) - L = 180 new limbs per
     # ModUp, more than one limb pattern holds; refused before any CUDA call
